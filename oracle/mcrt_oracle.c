@@ -1,0 +1,812 @@
+/*
+ * mcrt_oracle.c -- plain, slow FP64 CPU oracle for Monte Carlo dust radiative
+ * transfer with Bjorkman-Wood re-emission and the modified random walk (MRW) of
+ * Min et al. 2009 (A&A 497, 155), Sect. 2.1-2.2.
+ *
+ * TEST INFRASTRUCTURE. Only the test suite, the package smoke check and the
+ * benchmark's CPU-baseline leg load this library. It shares no code with the
+ * CUDA path and is not part of the product.
+ *
+ * Everything is computed in double precision, one packet after another, in the
+ * order the method describes. Units: cgs (cm, g, s, K); wavelengths in micron.
+ *
+ * Random numbers: Philox4x32-10 written from Salmon, Moraes, Dror & Shaw,
+ * "Parallel random numbers: as easy as 1, 2, 3" (SC'11), Sect. 4. Key =
+ * (seed_lo, seed_hi); counter = (block, model, packet_lo, packet_hi). Each
+ * 32-bit output word w gives one uniform u = (floor(w / 2^9) + 1/2) * 2^-23,
+ * exactly representable in binary32 and binary64, in (0, 1). Words are used in
+ * order w0..w3 of block 0, then block 1, and so on, one stream per packet.
+ *
+ * Order of draws per packet (the CUDA path consumes them identically):
+ *   launch:      u_lambda (stellar bin), u_mu, u_phi (isotropic direction)
+ *   free flight: u_tau (tau = -ln u)
+ *   interaction: u_albedo; scatter -> u_mu, u_phi (isotropic or HG);
+ *                absorb -> u_lambda (BW bin), u_mu, u_phi (isotropic)
+ *   MRW jump:    u_P (escape-time quantile), u_mu, u_phi (point on sphere),
+ *                u_mu, u_phi (new direction), u_lambda (exit bin)
+ *   after each interaction (and its MRW chain) a new u_tau.
+ */
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+
+#define OR_PI 3.14159265358979323846
+#define OR_H 6.62607015e-27
+#define OR_C 2.99792458e10
+#define OR_KB 1.380649e-16
+/* Stefan-Boltzmann constant from its definition 2 pi^5 k^4 / (15 h^3 c^2) */
+#define OR_SIGMA (2.0 * OR_PI * OR_PI * OR_PI * OR_PI * OR_PI * OR_KB * OR_KB * OR_KB * OR_KB / (15.0 * OR_H * OR_H * OR_H * OR_C * OR_C))
+#define OR_EUNIT 65536.0 /* fixed-point counts per packet energy */
+#define OR_NINC 10       /* inclination bins of the escape SED, uniform in |cos i| */
+
+/* ------------------------------------------------------------------------- */
+/* Philox4x32-10 (Salmon et al. 2011, Sect. 4)                               */
+/* ------------------------------------------------------------------------- */
+void oracle_philox4x32_10(const uint32_t ctr_in[4], const uint32_t key_in[2], uint32_t out[4]) {
+  uint32_t c0 = ctr_in[0], c1 = ctr_in[1], c2 = ctr_in[2], c3 = ctr_in[3];
+  uint32_t k0 = key_in[0], k1 = key_in[1];
+  for (int round = 0; round < 10; ++round) {
+    if (round > 0) {
+      k0 += 0x9E3779B9u; /* Weyl key schedule */
+      k1 += 0xBB67AE85u;
+    }
+    uint64_t prod0 = (uint64_t)0xD2511F53u * (uint64_t)c0;
+    uint64_t prod1 = (uint64_t)0xCD9E8D57u * (uint64_t)c2;
+    uint32_t hi0 = (uint32_t)(prod0 >> 32), lo0 = (uint32_t)prod0;
+    uint32_t hi1 = (uint32_t)(prod1 >> 32), lo1 = (uint32_t)prod1;
+    uint32_t n0 = hi1 ^ c1 ^ k0;
+    uint32_t n1 = lo1;
+    uint32_t n2 = hi0 ^ c3 ^ k1;
+    uint32_t n3 = lo0;
+    c0 = n0; c1 = n1; c2 = n2; c3 = n3;
+  }
+  out[0] = c0; out[1] = c1; out[2] = c2; out[3] = c3;
+}
+
+typedef struct {
+  uint32_t key[2];
+  uint32_t ctr[4];
+  uint32_t buf[4];
+  int pos;
+} or_rng;
+
+static void rng_init(or_rng *r, uint64_t seed, uint32_t model, uint64_t packet) {
+  r->key[0] = (uint32_t)seed;
+  r->key[1] = (uint32_t)(seed >> 32);
+  r->ctr[0] = 0;
+  r->ctr[1] = model;
+  r->ctr[2] = (uint32_t)packet;
+  r->ctr[3] = (uint32_t)(packet >> 32);
+  r->pos = 4;
+}
+
+static double word_to_uniform(uint32_t w) { return ((double)(w >> 9) + 0.5) * (1.0 / 8388608.0); }
+
+static double U(or_rng *r) {
+  if (r->pos == 4) {
+    oracle_philox4x32_10(r->ctr, r->key, r->buf);
+    r->ctr[0] += 1u;
+    r->pos = 0;
+  }
+  return word_to_uniform(r->buf[r->pos++]);
+}
+
+/* First n uniforms of the stream of (seed, model, packet); used by tests. */
+void oracle_uniforms(uint64_t seed, uint32_t model, uint64_t packet, int n, double *out) {
+  or_rng r;
+  rng_init(&r, seed, model, packet);
+  for (int i = 0; i < n; ++i) out[i] = U(&r);
+}
+
+/* ------------------------------------------------------------------------- */
+/* Planck function integrated over wavelength bins                           */
+/* ------------------------------------------------------------------------- */
+/* Bernoulli numbers B_0..B_20 (odd ones beyond B_1 vanish). */
+static const double BERN[21] = {1.0, -0.5, 1.0 / 6, 0, -1.0 / 30, 0, 1.0 / 42, 0, -1.0 / 30, 0, 5.0 / 66,
+                                0, -691.0 / 2730, 0, 7.0 / 6, 0, -3617.0 / 510, 0, 43867.0 / 798, 0,
+                                -174611.0 / 330};
+
+/* G3(x) = int_x^inf t^3/(e^t-1) dt.  x >= 1: sum_n e^{-nx}(x^3/n + 3x^2/n^2 + 6x/n^3 + 6/n^4);
+ * x < 1: pi^4/15 - sum_k B_k x^{k+3} / (k! (k+3)) (Taylor series of t/(e^t-1)). */
+double oracle_G3(double x) {
+  if (x <= 0.0) return pow(OR_PI, 4) / 15.0;
+  if (x >= 1.0) {
+    double s = 0.0;
+    for (int n = 1; n < 400; ++n) {
+      double e = exp(-n * x);
+      double term = e * (x * x * x / n + 3.0 * x * x / ((double)n * n) + 6.0 * x / ((double)n * n * n) +
+                         6.0 / ((double)n * n * n * n));
+      s += term;
+      if (term < 1e-18 * s) break;
+    }
+    return s;
+  }
+  double s = 0.0, fact = 1.0;
+  for (int k = 0; k <= 20; ++k) {
+    if (k > 0) fact *= k;
+    if (BERN[k] != 0.0) s += BERN[k] * pow(x, k + 3) / (fact * (k + 3));
+  }
+  return pow(OR_PI, 4) / 15.0 - s;
+}
+
+/* G4(x) = int_x^inf t^4 e^t/(e^t-1)^2 dt.  x >= 1: sum_n e^{-nx}(x^4 + 4x^3/n + 12x^2/n^2 + 24x/n^3 + 24/n^4);
+ * x < 1: 4 pi^4/15 - sum_k B_k (1-k) x^{k+3} / (k! (k+3)). */
+double oracle_G4(double x) {
+  if (x <= 0.0) return 4.0 * pow(OR_PI, 4) / 15.0;
+  if (x >= 1.0) {
+    double s = 0.0;
+    for (int n = 1; n < 400; ++n) {
+      double e = exp(-n * x);
+      double term = e * (x * x * x * x + 4.0 * x * x * x / n + 12.0 * x * x / ((double)n * n) +
+                         24.0 * x / ((double)n * n * n) + 24.0 / ((double)n * n * n * n));
+      s += term;
+      if (term < 1e-18 * s) break;
+    }
+    return s;
+  }
+  double s = 0.0, fact = 1.0;
+  for (int k = 0; k <= 20; ++k) {
+    if (k > 0) fact *= k;
+    if (BERN[k] != 0.0) s += BERN[k] * (1.0 - k) * pow(x, k + 3) / (fact * (k + 3));
+  }
+  return 4.0 * pow(OR_PI, 4) / 15.0 - s;
+}
+
+/* x at a wavelength edge: h c / (lambda k T); edge 0 is taken at lambda -> 0 and
+ * edge nlam at lambda -> infinity, so the bins cover the whole spectrum. */
+static double edge_x(const double *lam_e, int nlam, int e, double T) {
+  if (e == 0) return INFINITY;
+  if (e == nlam) return 0.0;
+  return OR_H * OR_C / (lam_e[e] * 1e-4 * OR_KB * T);
+}
+
+/* Bin-integrated Planck function int_bin B_nu(T) dnu (erg s^-1 cm^-2 sr^-1), per bin. */
+void oracle_planck_bins(const double *lam_e, int nlam, double T, double *out) {
+  if (T <= 0.0) {
+    for (int b = 0; b < nlam; ++b) out[b] = 0.0;
+    return;
+  }
+  double pref = 2.0 * pow(OR_KB * T, 4) / (pow(OR_H, 3) * OR_C * OR_C);
+  double gprev = 0.0; /* G3 at edge 0 (x = inf) */
+  for (int b = 0; b < nlam; ++b) {
+    double x = edge_x(lam_e, nlam, b + 1, T);
+    double g = oracle_G3(x);
+    out[b] = pref * (g - gprev);
+    gprev = g;
+  }
+}
+
+/* Bin-integrated dB_nu/dT (erg s^-1 cm^-2 sr^-1 K^-1), per bin. */
+void oracle_dplanck_bins(const double *lam_e, int nlam, double T, double *out) {
+  double pref = 2.0 * pow(OR_KB, 4) * T * T * T / (pow(OR_H, 3) * OR_C * OR_C);
+  double gprev = 0.0;
+  for (int b = 0; b < nlam; ++b) {
+    double x = edge_x(lam_e, nlam, b + 1, T);
+    double g = oracle_G4(x);
+    out[b] = pref * (g - gprev);
+    gprev = g;
+  }
+}
+
+/* ------------------------------------------------------------------------- */
+/* Model                                                                     */
+/* ------------------------------------------------------------------------- */
+typedef struct {
+  int nr, nt, nlam;
+  const double *rf;   /* nr+1 radial faces (cm) */
+  const double *tf;   /* nt+1 polar faces (rad) */
+  const double *rho;  /* nr*nt, [ir*nt + it] */
+  const double *lam_e;/* nlam+1 (micron) */
+  const double *kabs, *ksca, *g; /* nlam */
+  double Tstar, Rstar;
+} oracle_model;
+
+typedef struct {
+  int mrw;              /* 0/1 */
+  double gamma;         /* Eq. 11 */
+  int nmin;             /* interactions in a cell before MRW may start */
+  uint64_t max_events;  /* per packet */
+  int want_sed;         /* gray dust: sample BW / exit bins only when the SED is wanted */
+  int mrw_exit_dir;     /* 0 isotropic, 1 cosine-weighted outward */
+} oracle_opts;
+
+typedef struct {
+  uint64_t *tally;  /* nr*nt fixed-point absorbed energy, 2^16 per packet energy */
+  uint64_t *visits; /* nr*nt packet entries */
+  uint64_t *nabs;   /* nr*nt absorption events */
+  uint64_t *sed;    /* nlam*NINC escaped packets [lam*NINC + incl] */
+  double *Tcell;    /* nr*nt current temperature (K) */
+  uint64_t cnt[10]; /* packets, events, absorptions, scatterings, crossings, mrw_jumps, capped, escaped,
+                       deposit_sum_lo32-free (sum of per-packet deposits), error flags */
+  /* optional event trace */
+  int trace_packets;     /* trace the first trace_packets packets of this call */
+  int trace_max;         /* events per traced packet */
+  int32_t *tr_type, *tr_cell, *tr_lam, *tr_n;
+  double *tr_pos;        /* [packet][event][3] */
+} oracle_state;
+
+enum { EV_LAUNCH = 0, EV_CROSS = 1, EV_SCATTER = 2, EV_ABSORB = 3, EV_MRW = 4, EV_ESCAPE = 5, EV_CAPPED = 6 };
+enum { CNT_PACKETS, CNT_EVENTS, CNT_ABS, CNT_SCA, CNT_CROSS, CNT_MRW, CNT_CAPPED, CNT_ESCAPED, CNT_DEPSUM, CNT_ERR };
+
+static int is_gray(const oracle_model *m) {
+  for (int b = 1; b < m->nlam; ++b)
+    if (m->kabs[b] != m->kabs[0] || m->ksca[b] != m->ksca[0] || m->g[b] != m->g[0]) return 0;
+  return 1;
+}
+
+static double cell_volume(const oracle_model *m, int ir, int it) {
+  double r1 = m->rf[ir], r2 = m->rf[ir + 1];
+  return 2.0 * OR_PI / 3.0 * (r2 * r2 * r2 - r1 * r1 * r1) * (cos(m->tf[it]) - cos(m->tf[it + 1]));
+}
+
+/* Absorbed luminosity per unit mass -> temperature. Radiative equilibrium
+ * 4 pi kappa_P(T) B(T) = 4 pi sum_b kappa_b Bbar_b(T) = q (Sect. 2.1, BW method). */
+static double Q_of_T(const oracle_model *m, double T, double *Bb) {
+  oracle_planck_bins(m->lam_e, m->nlam, T, Bb);
+  double s = 0.0;
+  for (int b = 0; b < m->nlam; ++b) s += m->kabs[b] * Bb[b];
+  return 4.0 * OR_PI * s;
+}
+
+static double dQ_of_T(const oracle_model *m, double T, double *Bb) {
+  oracle_dplanck_bins(m->lam_e, m->nlam, T, Bb);
+  double s = 0.0;
+  for (int b = 0; b < m->nlam; ++b) s += m->kabs[b] * Bb[b];
+  return 4.0 * OR_PI * s;
+}
+
+double oracle_T_of_q(const oracle_model *m, double q) {
+  if (!(q > 0.0)) return 0.0;
+  if (is_gray(m)) return pow(q / (4.0 * OR_SIGMA * m->kabs[0]), 0.25);
+  double *Bb = (double *)malloc(sizeof(double) * m->nlam);
+  double lo = 1e-3, hi = 1e7;
+  double T = pow(q / (4.0 * OR_SIGMA * m->kabs[0]), 0.25);
+  if (!(T > lo && T < hi)) T = sqrt(lo * hi);
+  for (int it = 0; it < 200; ++it) {
+    double f = Q_of_T(m, T, Bb) - q;
+    if (f > 0) hi = T; else lo = T;
+    double d = dQ_of_T(m, T, Bb);
+    double Tn = T - f / d;
+    if (!(Tn > lo && Tn < hi)) Tn = 0.5 * (lo + hi);
+    if (fabs(Tn - T) <= 1e-15 * T) { T = Tn; break; }
+    T = Tn;
+  }
+  free(Bb);
+  return T;
+}
+
+/* Temperature of cell c from its fixed-point tally; L_abs = tally/EUNIT * Lstar/N. */
+static double cell_T(const oracle_model *m, int c, uint64_t tally, double n_total) {
+  if (tally == 0) return 0.0;
+  int ir = c / m->nt, it = c % m->nt;
+  double mass = m->rho[c] * cell_volume(m, ir, it);
+  double Lstar = 4.0 * OR_PI * m->Rstar * m->Rstar * OR_SIGMA * pow(m->Tstar, 4);
+  double Labs = ((double)tally / OR_EUNIT) * Lstar / n_total;
+  return oracle_T_of_q(m, Labs / mass);
+}
+
+/* Per-cell temperature and statistical error 1/(4 sqrt(N_abs,eq)). */
+void oracle_temperatures(const oracle_model *m, const uint64_t *tally, double n_total, double *T, double *relerr) {
+  for (int c = 0; c < m->nr * m->nt; ++c) {
+    T[c] = (m->rho[c] > 0.0) ? cell_T(m, c, tally[c], n_total) : 0.0;
+    if (relerr) {
+      double n = (double)tally[c] / OR_EUNIT;
+      relerr[c] = n > 0 ? 0.25 / sqrt(n) : INFINITY;
+    }
+  }
+}
+
+/* ------------------------------------------------------------------------- */
+/* Diffusion coefficient and mean opacities, Sect. 2.2.3                     */
+/* ------------------------------------------------------------------------- */
+/* chi' = kappa + (1-g) sigma: isotropic-equivalent extinction, Eq. 16 with g' = 0. */
+static double chi_prime(const oracle_model *m, int b) { return m->kabs[b] + (1.0 - m->g[b]) * m->ksca[b]; }
+
+/* Iterate Eq. 13 as written, from the initial guess eta = kappa dB/dT. The right-hand
+ * side is affine in eta (the ratio term is scale free, the scattering term is not), so the
+ * iterate is not rescaled; at the fixed point sum eta = sum kappa dB/dT. */
+void oracle_eta_iterate(const oracle_model *m, double T, int iters, double *eta) {
+  int n = m->nlam;
+  double *dB = (double *)malloc(sizeof(double) * n), *nxt = (double *)malloc(sizeof(double) * n);
+  oracle_dplanck_bins(m->lam_e, n, T, dB);
+  for (int b = 0; b < n; ++b) eta[b] = m->kabs[b] * dB[b];
+  for (int k = 0; k < iters; ++k) {
+    double num = 0.0, den = 0.0;
+    for (int b = 0; b < n; ++b) { num += eta[b] * m->kabs[b] / chi_prime(m, b); den += eta[b]; }
+    double ratio = num / den, diff = 0.0, scale = 0.0;
+    for (int b = 0; b < n; ++b) {
+      double sig = (1.0 - m->g[b]) * m->ksca[b];
+      nxt[b] = m->kabs[b] * dB[b] * ratio + sig / chi_prime(m, b) * eta[b];
+    }
+    for (int b = 0; b < n; ++b) {
+      diff = fmax(diff, fabs(nxt[b] - eta[b]));
+      scale = fmax(scale, fabs(nxt[b]));
+      eta[b] = nxt[b];
+    }
+    if (diff <= 1e-17 * scale) break;
+  }
+  free(dB);
+  free(nxt);
+}
+
+/* D (cm^2 per unit c t) from Eq. 12, 14, 15, and kappa_bar from Eq. 10, at density rho. */
+void oracle_diffusion(const oracle_model *m, double T, double rho, double *D, double *kbar) {
+  int n = m->nlam;
+  if (is_gray(m)) {
+    *D = 1.0 / (3.0 * rho * chi_prime(m, 0));
+    *kbar = m->kabs[0];
+    return;
+  }
+  double *eta = (double *)malloc(sizeof(double) * n);
+  oracle_eta_iterate(m, T, 500, eta);
+  double d1 = 0.0, d2 = 0.0, e0 = 0.0, kn = 0.0, kd = 0.0;
+  for (int b = 0; b < n; ++b) {
+    double chi = chi_prime(m, b);
+    e0 += eta[b];
+    d1 += eta[b] / (rho * chi);
+    d2 += eta[b] / (rho * rho * chi * chi);
+    kn += m->kabs[b] / chi * eta[b];
+    kd += eta[b] / chi;
+  }
+  double avd = d1 / e0, avd2 = 2.0 * d2 / e0;
+  *D = avd2 / (6.0 * avd);
+  *kbar = kn / kd;
+  free(eta);
+}
+
+/* ------------------------------------------------------------------------- */
+/* MRW escape-time law, Eq. 7-8                                              */
+/* ------------------------------------------------------------------------- */
+/* P(x) = 2 sum_{n>=1} (-1)^{n+1} y^{n^2}, y = exp(-pi^2 x), x = D c t / R0^2. */
+double oracle_mrw_P(double x) {
+  if (x <= 0.0) return 1.0;
+  double s = 0.0;
+  for (int n = 1; n < 100000; ++n) {
+    double term = exp(-(double)n * n * OR_PI * OR_PI * x);
+    s += (n & 1) ? term : -term;
+    if (term < 1e-300 || term < 1e-19 * fabs(s)) break;
+  }
+  return 2.0 * s;
+}
+
+/* Solve P(x) = P0 by bisection. */
+double oracle_mrw_x(double P0) {
+  double lo = 0.0, hi = 1.0;
+  while (oracle_mrw_P(hi) > P0) hi *= 2.0;
+  for (int it = 0; it < 200; ++it) {
+    double mid = 0.5 * (lo + hi);
+    if (mid <= lo || mid >= hi) break;
+    if (oracle_mrw_P(mid) > P0) lo = mid; else hi = mid;
+  }
+  return 0.5 * (lo + hi);
+}
+
+/* ------------------------------------------------------------------------- */
+/* Geometry                                                                  */
+/* ------------------------------------------------------------------------- */
+static int is_midplane_face(double th) { return fabs(th - 0.5 * OR_PI) < 1e-12; }
+
+/* Distance along u from p to the sphere |x| = R where the ray leaves the ball: the larger
+ * root of s^2 + 2 b s + c = 0 (b = p.u, c = |p|^2 - R^2), from the cancellation-free pair
+ * q = -(b + sign(b) sqrt(b^2 - c)) and c/q. */
+static double sphere_far(const double p[3], const double u[3], double R) {
+  double b = p[0] * u[0] + p[1] * u[1] + p[2] * u[2];
+  double c = p[0] * p[0] + p[1] * p[1] + p[2] * p[2] - R * R;
+  double disc = b * b - c;
+  if (disc < 0) disc = 0;
+  double q = -(b + copysign(sqrt(disc), b));
+  if (q == 0.0) return 0.0;
+  double s = fmax(q, c / q);
+  return s > 0 ? s : 0.0;
+}
+
+/* Distance to the sphere |x| = R hit from outside (smaller root), or infinity. */
+static double sphere_near(const double p[3], const double u[3], double R) {
+  double b = p[0] * u[0] + p[1] * u[1] + p[2] * u[2];
+  if (!(b < 0)) return INFINITY;
+  double c = p[0] * p[0] + p[1] * p[1] + p[2] * p[2] - R * R;
+  double disc = b * b - c;
+  if (disc < 0) return INFINITY;
+  double q = -b + sqrt(disc);
+  double s = c / q;
+  return s > 0 ? s : 0.0;
+}
+
+/* Distance to cone face theta_f, crossing in the direction that leaves the cell.
+ * G(s) = sig*(cos^2 th (x^2+y^2) - sin^2 th z^2) along the ray; G >= 0 <=> theta >= th (own nappe).
+ * leaving_down = 1: cell lies at theta >= th, exit where G goes + -> -. */
+static double cone_exit(const double p[3], const double u[3], double th, int leaving_down) {
+  if (is_midplane_face(th)) {
+    /* plane z = 0 */
+    if (leaving_down) { /* cell below the plane (z < 0), exit upward */
+      if (u[2] <= 0) return INFINITY;
+    } else {
+      if (u[2] >= 0) return INFINITY;
+    }
+    double s = -p[2] / u[2];
+    return s > 0 ? s : 0.0;
+  }
+  double ct = cos(th), st = sin(th);
+  double c2 = ct * ct, s2 = st * st;
+  double sig = th < 0.5 * OR_PI ? 1.0 : -1.0;
+  double A = sig * (c2 * (u[0] * u[0] + u[1] * u[1]) - s2 * u[2] * u[2]);
+  double B = sig * (c2 * (p[0] * u[0] + p[1] * u[1]) - s2 * p[2] * u[2]);
+  double C = sig * (c2 * (p[0] * p[0] + p[1] * p[1]) - s2 * p[2] * p[2]);
+  double disc = B * B - A * C;
+  if (disc < 0) return INFINITY;
+  double q = -(B + copysign(sqrt(disc), B));
+  if (q == 0.0) return INFINITY;
+  double r1 = q / A, r2 = C / q;
+  /* sign bit of B clear: r1 is the + -> - root; set: r2 is (signbit, not B >= 0, so that
+   * B = -0 picks the root that copysign built). */
+  int bpos = !signbit(B);
+  double s;
+  if (leaving_down) s = bpos ? r1 : r2;
+  else s = bpos ? r2 : r1;
+  if (!(s >= 0.0) && !(s < 0.0)) return INFINITY; /* NaN */
+  if (s < 0) {
+    if (s > -1e-9 * sqrt(p[0] * p[0] + p[1] * p[1] + p[2] * p[2])) s = 0.0; /* rounding on the face */
+    else return INFINITY;
+  }
+  double z = p[2] + s * u[2];
+  if (sig * z < 0) return INFINITY; /* mirror nappe */
+  return s;
+}
+
+/* Smallest distance from p to the faces of cell (ir, it), Sect. 2.2.2 (d_min of Eq. 11). */
+double oracle_dmin(const oracle_model *m, const double p[3], int ir, int it) {
+  double r = sqrt(p[0] * p[0] + p[1] * p[1] + p[2] * p[2]);
+  double rc = sqrt(p[0] * p[0] + p[1] * p[1]);
+  double d = fmin(r - m->rf[ir], m->rf[ir + 1] - r);
+  if (it > 0) {
+    double th = m->tf[it];
+    d = fmin(d, fabs(rc * cos(th) - p[2] * sin(th)));
+  }
+  if (it + 1 < m->nt) {
+    double th = m->tf[it + 1];
+    d = fmin(d, fabs(rc * cos(th) - p[2] * sin(th)));
+  }
+  return d > 0 ? d : 0.0;
+}
+
+/* Distance along u to the face through which the ray leaves cell (ir, it);
+ * face = 0 inner sphere, 1 outer sphere, 2 lower polar face, 3 upper polar face. */
+static double next_face(const oracle_model *m, const double p[3], const double u[3], int ir, int it, int *face) {
+  double s_face = sphere_far(p, u, m->rf[ir + 1]);
+  *face = 1;
+  double sn = sphere_near(p, u, m->rf[ir]);
+  if (sn < s_face) { s_face = sn; *face = 0; }
+  if (it > 0) {
+    double sc = cone_exit(p, u, m->tf[it], 1);
+    if (sc < s_face) { s_face = sc; *face = 2; }
+  }
+  if (it + 1 < m->nt) {
+    double sc = cone_exit(p, u, m->tf[it + 1], 0);
+    if (sc < s_face) { s_face = sc; *face = 3; }
+  }
+  return s_face;
+}
+
+static int theta_cell(const oracle_model *m, const double p[3]) {
+  double r = sqrt(p[0] * p[0] + p[1] * p[1] + p[2] * p[2]);
+  double mu = p[2] / r;
+  int j = 0;
+  for (int k = 1; k < m->nt; ++k)
+    if (cos(m->tf[k]) >= mu) j = k;
+  return j;
+}
+
+static void iso_dir(or_rng *r, double u[3]) {
+  double mu = 2.0 * U(r) - 1.0;
+  double phi = 2.0 * OR_PI * U(r);
+  double st = sqrt(fmax(0.0, 1.0 - mu * mu));
+  u[0] = st * cos(phi);
+  u[1] = st * sin(phi);
+  u[2] = mu;
+}
+
+/* Rotate u by polar angle acos(mu) and azimuth phi about itself. */
+static void turn(double u[3], double mu, double phi) {
+  double st = sqrt(fmax(0.0, 1.0 - mu * mu));
+  double cp = cos(phi), sp = sin(phi);
+  if (fabs(u[2]) < 0.99999) {
+    double w = sqrt(1.0 - u[2] * u[2]);
+    double nx = st * (u[0] * u[2] * cp - u[1] * sp) / w + u[0] * mu;
+    double ny = st * (u[1] * u[2] * cp + u[0] * sp) / w + u[1] * mu;
+    double nz = -st * cp * w + u[2] * mu;
+    u[0] = nx; u[1] = ny; u[2] = nz;
+  } else {
+    double sgn = u[2] > 0 ? 1.0 : -1.0;
+    u[0] = st * cp;
+    u[1] = st * sp;
+    u[2] = sgn * mu;
+  }
+  double n = sqrt(u[0] * u[0] + u[1] * u[1] + u[2] * u[2]);
+  u[0] /= n; u[1] /= n; u[2] /= n;
+}
+
+/* Henyey-Greenstein cosine by inversion of its CDF. */
+static double hg_mu(double g, double xi) {
+  if (fabs(g) < 1e-6) return 2.0 * xi - 1.0;
+  double t = (1.0 - g * g) / (1.0 - g + 2.0 * g * xi);
+  double mu = (1.0 + g * g - t * t) / (2.0 * g);
+  return fmin(1.0, fmax(-1.0, mu));
+}
+
+/* smallest b with cumulative(w) >= xi * total */
+static int sample_bins(const double *w, int n, double xi) {
+  double tot = 0.0;
+  for (int b = 0; b < n; ++b) tot += w[b];
+  double target = xi * tot, c = 0.0;
+  for (int b = 0; b < n; ++b) {
+    c += w[b];
+    if (c >= target && w[b] > 0) return b;
+  }
+  for (int b = n - 1; b >= 0; --b)
+    if (w[b] > 0) return b;
+  return n - 1;
+}
+
+/* ------------------------------------------------------------------------- */
+/* Transport                                                                 */
+/* ------------------------------------------------------------------------- */
+typedef struct {
+  const oracle_model *m;
+  const oracle_opts *o;
+  oracle_state *st;
+  int gray;
+  double n_total;
+  double *w, *w2; /* nlam scratch */
+  double *star_w;
+} ctx_t;
+
+static void trace(ctx_t *x, int tp, int *ntr, int type, int cell, const double p[3], int lam) {
+  oracle_state *s = x->st;
+  if (tp < 0 || *ntr >= s->trace_max) return;
+  int k = tp * s->trace_max + *ntr;
+  s->tr_type[k] = type;
+  s->tr_cell[k] = cell;
+  s->tr_lam[k] = lam;
+  s->tr_pos[3 * k + 0] = p[0];
+  s->tr_pos[3 * k + 1] = p[1];
+  s->tr_pos[3 * k + 2] = p[2];
+  (*ntr)++;
+  s->tr_n[tp] = *ntr;
+}
+
+/* BW re-emission bin from kappa_b [Bbar_b(T_new) - Bbar_b(T_old)]. */
+static int bw_bin(ctx_t *x, double Told, double Tnew, double xi) {
+  const oracle_model *m = x->m;
+  oracle_planck_bins(m->lam_e, m->nlam, Tnew, x->w);
+  oracle_planck_bins(m->lam_e, m->nlam, Told, x->w2);
+  double tot = 0.0;
+  for (int b = 0; b < m->nlam; ++b) {
+    x->w[b] = m->kabs[b] * (x->w[b] - x->w2[b]);
+    if (x->w[b] < 0) x->w[b] = 0;
+    tot += x->w[b];
+  }
+  if (!(tot > 0)) {
+    oracle_dplanck_bins(m->lam_e, m->nlam, fmax(Tnew, 1.0), x->w);
+    for (int b = 0; b < m->nlam; ++b) x->w[b] *= m->kabs[b];
+  }
+  return sample_bins(x->w, m->nlam, xi);
+}
+
+/* MRW exit bin from the diffusion flux spectrum dBbar_b/dT / chi'_b. */
+static int exit_bin(ctx_t *x, double T, double xi) {
+  const oracle_model *m = x->m;
+  oracle_dplanck_bins(m->lam_e, m->nlam, fmax(T, 1.0), x->w);
+  for (int b = 0; b < m->nlam; ++b) x->w[b] /= chi_prime(m, b);
+  return sample_bins(x->w, m->nlam, xi);
+}
+
+static void deposit(ctx_t *x, int c, uint64_t units, uint64_t *pkt_dep) {
+  oracle_state *s = x->st;
+  uint64_t old = s->tally[c];
+  s->tally[c] = old + units;
+  if (s->tally[c] < old) s->cnt[CNT_ERR] |= 1u; /* overflow */
+  *pkt_dep += units;
+}
+
+static void run_packet(ctx_t *x, uint64_t k, uint64_t seed, uint32_t model, int tp) {
+  const oracle_model *m = x->m;
+  const oracle_opts *o = x->o;
+  oracle_state *s = x->st;
+  const int nt = m->nt;
+  or_rng r;
+  rng_init(&r, seed, model, k);
+  int ntr = 0;
+  uint64_t dep = 0, events = 0, crossings = 0;
+  double p[3] = {0, 0, 0}, u[3];
+  int lam = sample_bins(x->star_w, m->nlam, U(&r));
+  iso_dir(&r, u);
+  int ir = -1, it = -1, ninc = 0;
+  trace(x, tp, &ntr, EV_LAUNCH, -1, p, lam);
+  double tau = -log(U(&r));
+  s->cnt[CNT_PACKETS]++;
+  for (;;) {
+    if (++crossings > 4000000000ull) { s->cnt[CNT_ERR] |= 4u; s->cnt[CNT_CAPPED]++; break; }
+    if (ir < 0) {
+      /* inner cavity: free flight out to r_in */
+      double sf = sphere_far(p, u, m->rf[0]);
+      for (int d = 0; d < 3; ++d) p[d] += sf * u[d];
+      ir = 0;
+      it = theta_cell(m, p);
+      ninc = 0;
+      s->visits[ir * nt + it]++;
+      s->cnt[CNT_CROSS]++;
+      trace(x, tp, &ntr, EV_CROSS, ir * nt + it, p, lam);
+      continue;
+    }
+    int c = ir * nt + it;
+    double chi = m->kabs[lam] + m->ksca[lam];
+    double alpha = m->rho[c] * chi;
+    int face;
+    double s_face = next_face(m, p, u, ir, it, &face);
+    double s_int = alpha > 0 ? tau / alpha : INFINITY;
+    if (s_int < s_face) {
+      for (int d = 0; d < 3; ++d) p[d] += s_int * u[d];
+      /* interaction */
+      double omega = m->ksca[lam] / chi;
+      if (U(&r) < omega) {
+        double g = m->g[lam];
+        if (g != 0.0) {
+          double mu = hg_mu(g, U(&r));
+          double phi = 2.0 * OR_PI * U(&r);
+          turn(u, mu, phi);
+        } else {
+          iso_dir(&r, u);
+        }
+        s->cnt[CNT_SCA]++;
+        trace(x, tp, &ntr, EV_SCATTER, c, p, lam);
+      } else {
+        uint64_t before = s->tally[c];
+        deposit(x, c, (uint64_t)OR_EUNIT, &dep);
+        s->nabs[c]++;
+        double Told = s->Tcell[c];
+        double Tnew = cell_T(m, c, s->tally[c], x->n_total);
+        (void)before;
+        s->Tcell[c] = Tnew;
+        double xl = U(&r);
+        if (!x->gray || o->want_sed) lam = bw_bin(x, Told, Tnew, xl);
+        iso_dir(&r, u);
+        s->cnt[CNT_ABS]++;
+        trace(x, tp, &ntr, EV_ABSORB, c, p, lam);
+      }
+      events++;
+      ninc++;
+      /* modified random walk, Sect. 2.2.2 */
+      if (o->mrw && ninc >= o->nmin) {
+        for (;;) {
+          if (events >= o->max_events) break;
+          double dmin = oracle_dmin(m, p, ir, it);
+          double T = fmax(s->Tcell[c], 1.0);
+          double D, kbar;
+          oracle_diffusion(m, T, m->rho[c], &D, &kbar);
+          /* Eq. 11 with rho chi_R = 1/(3 D) */
+          if (!(dmin > o->gamma * 3.0 * D)) break;
+          double x0 = oracle_mrw_x(U(&r));
+          double ct = x0 * dmin * dmin / D;           /* path length c t */
+          double E = ct * m->rho[c] * kbar;             /* Eq. 9, in packet energies */
+          double units = floor(E * OR_EUNIT + 0.5);
+          if (units >= 1.8e19) { s->cnt[CNT_ERR] |= 2u; units = 1.8e19; }
+          deposit(x, c, (uint64_t)units, &dep);
+          s->Tcell[c] = cell_T(m, c, s->tally[c], x->n_total);
+          double uh[3];
+          iso_dir(&r, uh);
+          for (int d = 0; d < 3; ++d) p[d] += dmin * uh[d];
+          if (o->mrw_exit_dir == 1) {
+            double mu = sqrt(U(&r));
+            double phi = 2.0 * OR_PI * U(&r);
+            u[0] = uh[0]; u[1] = uh[1]; u[2] = uh[2];
+            turn(u, mu, phi);
+          } else {
+            iso_dir(&r, u);
+          }
+          double xl = U(&r);
+          if (!x->gray || o->want_sed) lam = exit_bin(x, s->Tcell[c], xl);
+          events++;
+          s->cnt[CNT_MRW]++;
+          trace(x, tp, &ntr, EV_MRW, c, p, lam);
+        }
+      }
+      if (events >= o->max_events) {
+        s->cnt[CNT_CAPPED]++;
+        trace(x, tp, &ntr, EV_CAPPED, c, p, lam);
+        break;
+      }
+      tau = -log(U(&r));
+    } else {
+      for (int d = 0; d < 3; ++d) p[d] += s_face * u[d];
+      tau -= alpha * s_face;
+      if (tau < 0) tau = 0;
+      s->cnt[CNT_CROSS]++;
+      if (face == 1) ir++;
+      else if (face == 0) ir--;
+      else if (face == 2) it--;
+      else it++;
+      if (ir >= m->nr) {
+        double az = fabs(u[2]);
+        int ib = (int)(az * OR_NINC);
+        if (ib >= OR_NINC) ib = OR_NINC - 1;
+        s->sed[lam * OR_NINC + ib]++;
+        s->cnt[CNT_ESCAPED]++;
+        trace(x, tp, &ntr, EV_ESCAPE, -1, p, lam);
+        break;
+      }
+      if (ir < 0) {
+        trace(x, tp, &ntr, EV_CROSS, -1, p, lam);
+        continue;
+      }
+      ninc = 0;
+      s->visits[ir * nt + it]++;
+      trace(x, tp, &ntr, EV_CROSS, ir * nt + it, p, lam);
+    }
+  }
+  s->cnt[CNT_EVENTS] += events;
+  s->cnt[CNT_DEPSUM] += dep;
+}
+
+/* Run packets first_id .. first_id+n-1. n_total sets the packet energy Lstar/n_total.
+ * The tallies and Tcell carry over between calls (resume). Returns 0. */
+int oracle_run(const oracle_model *m, const oracle_opts *o, oracle_state *s, uint64_t n, uint64_t first_id,
+               uint64_t n_total, uint64_t seed, uint32_t model) {
+  ctx_t x;
+  x.m = m;
+  x.o = o;
+  x.st = s;
+  x.gray = is_gray(m);
+  x.n_total = (double)n_total;
+  x.w = (double *)malloc(sizeof(double) * m->nlam);
+  x.w2 = (double *)malloc(sizeof(double) * m->nlam);
+  x.star_w = (double *)malloc(sizeof(double) * m->nlam);
+  oracle_planck_bins(m->lam_e, m->nlam, m->Tstar, x.star_w);
+  for (uint64_t i = 0; i < n; ++i) {
+    int tp = (i < (uint64_t)s->trace_packets) ? (int)i : -1;
+    run_packet(&x, first_id + i, seed, model, tp);
+  }
+  free(x.w);
+  free(x.w2);
+  free(x.star_w);
+  return 0;
+}
+
+/* Stellar bin of the first draw, for tests of the launch spectrum. */
+int oracle_star_bin(const oracle_model *m, double xi) {
+  double *w = (double *)malloc(sizeof(double) * m->nlam);
+  oracle_planck_bins(m->lam_e, m->nlam, m->Tstar, w);
+  int b = sample_bins(w, m->nlam, xi);
+  free(w);
+  return b;
+}
+
+/* Exposed for tests: face distances and HG sampling. */
+double oracle_cone_exit(const double p[3], const double u[3], double th, int leaving_down) {
+  return cone_exit(p, u, th, leaving_down);
+}
+double oracle_sphere_far(const double p[3], const double u[3], double R) { return sphere_far(p, u, R); }
+double oracle_sphere_near(const double p[3], const double u[3], double R) { return sphere_near(p, u, R); }
+double oracle_hg_mu(double g, double xi) { return hg_mu(g, xi); }
+
+/* Straight ray from p (inside cell (ir, it)) along u until it leaves the grid or
+ * enters the inner cavity; records up to nmax (cell, length) segments. Returns the
+ * number of segments. Used by tests of the face-distance geometry. */
+int oracle_march(const oracle_model *m, const double p0[3], const double u[3], int ir, int it, int nmax,
+                 int32_t *cells, double *lens) {
+  double p[3] = {p0[0], p0[1], p0[2]};
+  int n = 0;
+  while (n < nmax && ir >= 0 && ir < m->nr) {
+    int face;
+    double s = next_face(m, p, u, ir, it, &face);
+    cells[n] = ir * m->nt + it;
+    lens[n] = s;
+    n++;
+    for (int d = 0; d < 3; ++d) p[d] += s * u[d];
+    if (face == 1) ir++;
+    else if (face == 0) ir--;
+    else if (face == 2) it--;
+    else it++;
+  }
+  return n;
+}
