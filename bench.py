@@ -1,0 +1,337 @@
+"""Benchmark of the transport + MRW + PDA path on the very optically thick gray disk.
+
+Workload (per rank, one step): the 200 x 120 rim-refined gray disk (albedo 0.5, isotropic, midplane
+radial optical depth 1e6, star 4000 K / 2 R_sun) -- reset tallies, transport `--packets` photon
+packets with the modified random walk (gamma = 2), radiative-equilibrium temperatures, partial
+diffusion approximation. Metric: photon packets per second of the whole step (MRW + PDA), with the
+plain Monte Carlo rate on the same disk, the PDA time and the end-to-end rate through the host C ABI
+reported beside it.
+
+    python bench.py [--gpus N --steps K --warmup W] [--impl reference]
+
+N > 1 runs one rank per GPU (torchrun): each rank transports its own packet range and the integer
+tallies are summed across ranks (the exchange of the Monte Carlo step) before the PDA.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "photon packets/s (MRW+PDA vs plain MC) at tau_mid=1e6, equal T accuracy; PDA ms"
+UNIT = "packets/s"
+WORKLOAD = "thick gray disk 200x120 rim-refined, tau_mid=1e6, albedo 0.5 isotropic, MRW gamma=2 + PDA"
+
+# Thread instructions per transport step (an interaction, an MRW jump or a face crossing) of the FP32
+# kernel, from an ncu count of smsp__thread_inst_executed.sum over a whole launch of this workload
+# divided by its steps (see profiles/). They turn the step counts of a launch into the algorithmic
+# instruction work whose rate is compared with the issue peak.
+INST_PER_STEP = 260.0
+# Issue peak: 152 SMs x 4 schedulers x 1 warp instruction per clock x 32 lanes at the 2070 MHz
+# maximum SM clock, in thread instructions per second.
+ISSUE_PEAK = 152 * 4 * 32 * 2070e6
+
+
+def parse():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=3)
+    p.add_argument("--warmup", type=int, default=3)
+    p.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    p.add_argument("--packets", type=float, default=1e8, help="packets per step per rank")
+    p.add_argument("--gamma", type=float, default=2.0)
+    p.add_argument("--plain-packets", type=float, default=1e6)
+    p.add_argument("--cpu-seconds", type=float, default=15.0)
+    p.add_argument("--no-e2e", action="store_true")
+    p.add_argument("--no-cpu", action="store_true")
+    return p.parse_args()
+
+
+def workload():
+    from paper_0902_3092_gb300 import disks
+    return disks.config_thick_gray(200, 120, 1e6)
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms during the timed region."""
+    FIELDS = ["index", "clocks.sm", "clocks.max.sm", "power.draw", "clocks_event_reasons.active",
+              "clocks_event_reasons.hw_slowdown", "clocks_event_reasons.hw_thermal_slowdown",
+              "clocks_event_reasons.sw_thermal_slowdown", "clocks_event_reasons.sw_power_cap"]
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={','.join(self.FIELDS)}",
+                                          "--format=csv,noheader,nounits", "-lms", "200", "-i", str(self.index)],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except OSError:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx = float(f[2])
+            except ValueError:
+                continue
+            for n, v in zip(names, f[5:9]):
+                if v.lower() in ("active", "1", "yes"):
+                    reasons.add(n)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unavailable"], "samples": 0}
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": mx, "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def physical_gpu(local_rank):
+    vis = os.environ.get("CUDA_VISIBLE_DEVICES")
+    if vis:
+        ids = [x for x in vis.split(",") if x.strip()]
+        if local_rank < len(ids) and ids[local_rank].strip().isdigit():
+            return int(ids[local_rank])
+    return local_rank
+
+
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f)
+    except (OSError, ValueError):
+        return {}
+
+
+def cpu_baseline(d, gamma, budget_s):
+    """The FP64 oracle as it stands, one host core: MRW transport of a bounded packet sample of the same
+    disk, then its PDA solve; value = sample packets / transport seconds."""
+    from oracle import oracle as O
+    O.build()
+    run = O.Run(d)
+    t0 = time.perf_counter()
+    n, chunk = 0, 50
+    while time.perf_counter() - t0 < budget_s:
+        run.run(chunk, seed=1, first_id=n, n_total=10 ** 8, mrw=True, gamma=gamma, want_sed=False)
+        n += chunk
+    t_tr = time.perf_counter() - t0
+    T, err = run.temperatures()
+    t1 = time.perf_counter()
+    try:
+        O.solve_pda(d, T, run.tally, run.visits, err)
+        pda_ms = (time.perf_counter() - t1) * 1e3
+    except ValueError:
+        pda_ms = None
+    return {"value": n / t_tr, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"{n} packets of the workload disk (MRW gamma={gamma}) in {t_tr:.1f} s on one core; "
+                      f"oracle PDA (scipy sparse direct) on those tallies {pda_ms if pda_ms is None else round(pda_ms, 1)} ms",
+            "pda_ms": pda_ms}
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    from oracle import oracle as O
+    O.build()
+    d = workload()
+    per_step = 200
+    # warm-up then timed steps: each step is a bounded sample of the workload (transport + PDA)
+    times = []
+    for s in range(args.warmup + args.steps):
+        run = O.Run(d)
+        t0 = time.perf_counter()
+        run.run(per_step, seed=1, first_id=s * per_step, n_total=10 ** 8, mrw=True, gamma=args.gamma, want_sed=False)
+        T, err = run.temperatures()
+        try:
+            O.solve_pda(d, T, run.tally, run.visits, err)
+        except ValueError:
+            pass
+        if s >= args.warmup:
+            times.append(time.perf_counter() - t0)
+    t = float(np.sum(times))
+    v = per_step * args.steps / t
+    line = {"metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": 1e3 * t / args.steps, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",
+            "config": {"workload": WORKLOAD, "packets_per_step": per_step},
+            "cpu_baseline": {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
+                             "sample": f"{per_step} packets + temperatures + PDA per step, FP64 oracle, one core"},
+            "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+        return
+    import torch
+    import torch.distributed as dist
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    from paper_0902_3092_gb300 import build, mcrt
+    build.build()
+    d = workload()
+    stream = torch.cuda.current_stream()
+    g = mcrt.Disk.from_model(d, device=local, stream=stream.cuda_stream)
+    Np = int(args.packets)
+    ncell = d.nr * d.ntheta
+
+    def combine():
+        if world == 1:
+            return
+        # exchange of the Monte Carlo step: integer tallies summed over ranks, exact in int64
+        t, v, a = g.tallies()
+        blob = g.checkpoint()
+        x = torch.from_numpy(np.stack([t, v, a]).astype(np.int64)).cuda()
+        dist.all_reduce(x)
+        hdr = np.frombuffer(blob[:64], np.uint64).copy()
+        hdr[5] = Np * world
+        hdr[6] = np.frombuffer(np.array([float(Np * world)]).tobytes(), np.uint64)[0]
+        rest = np.frombuffer(blob[64 + 3 * 8 * ncell:], np.uint64)
+        g.restore(hdr.tobytes() + x.cpu().numpy().astype(np.uint64).tobytes() + rest.tobytes())
+
+    def step(i):
+        g.reset()
+        st = g.run_photons(Np, seed=1, first_id=(rank + world * i) * Np, n_total=Np * world, mrw=True,
+                           gamma=args.gamma, want_sed=True)
+        combine()
+        n_pda, iters = g.solve_pda()
+        return st, n_pda, iters
+
+    flush = torch.empty(512 * 1024 * 1024, dtype=torch.uint8, device="cuda")
+    for i in range(args.warmup):
+        step(i)
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    stats = []
+    l0 = g.launch_count()
+    with ClockSampler(physical_gpu(local)) as clk:
+        for i in range(args.steps):
+            flush.fill_(i & 0xFF)  # L2 flush between timed steps, outside the timed region
+            ev[i][0].record(stream)
+            stats.append(step(args.warmup + i))
+            ev[i][1].record(stream)
+        torch.cuda.synchronize()
+    launches = g.launch_count() - l0
+    step_ms = [a.elapsed_time(b) for a, b in ev]
+    t_local = float(np.sum(step_ms)) / 1e3
+    if world > 1:
+        tt = torch.tensor([t_local], dtype=torch.float64, device="cuda")
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        t_max = float(tt.item())
+    else:
+        t_max = t_local
+    value = Np * world * args.steps / t_max
+    tr_s = [s[0]["seconds"] for s in stats]
+    ev_steps = [s[0]["events"] + s[0]["crossings"] for s in stats]
+    pda_ms = [ms - 1e3 * ts for ms, ts in zip(step_ms, tr_s)]
+    s0 = stats[-1][0]
+
+    # plain Monte Carlo on the same disk (no MRW, no PDA), events capped at 1e7 per packet
+    Npl = int(args.plain_packets)
+    g.reset()
+    t0 = time.perf_counter()
+    stp = g.run_photons(Npl, seed=2, first_id=0, mrw=False, max_events=10 ** 7, want_sed=True)
+    plain = {"packets_per_s": Npl / stp["seconds"], "kernel_s": stp["seconds"], "packets": Npl,
+             "events": stp["events"], "capped": stp["capped"], "event_cap": 10 ** 7}
+
+    # end to end through the host C ABI: create from host arrays, transport, temperatures, PDA, read T
+    e2e = None
+    if not args.no_e2e:
+        op = d.opacity
+        h2d = 8 * (len(d.r_faces_cm) + len(d.theta_faces) + d.rho.size + len(op.lam_edges_um) + 3 * op.nlam)
+        d2h = 3 * 8 * ncell
+        torch.cuda.synchronize()
+        te = []
+        for i in range(args.steps):
+            t0 = time.perf_counter()
+            h = mcrt.Disk.from_model(d, device=local)
+            h.run_photons(Np, seed=1, first_id=(rank + world * i) * Np, n_total=Np, mrw=True, gamma=args.gamma)
+            h.solve_pda()
+            T, _, _ = h.temperatures(mcrt.T_PDA)
+            h.close()
+            te.append(time.perf_counter() - t0)
+        t_e2e = float(np.sum(te))
+        if world > 1:
+            tt = torch.tensor([t_e2e], dtype=torch.float64, device="cuda")
+            dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+            t_e2e = float(tt.item())
+        e2e = {"value": Np * world * args.steps / t_e2e, "unit": UNIT, "h2d_bytes_per_step": int(h2d),
+               "d2h_bytes_per_step": int(d2h)}
+
+    peaks = measured_peaks()
+    inst = INST_PER_STEP * float(np.mean(ev_steps))
+    achieved = inst / float(np.mean(tr_s))
+    roofline = {"bound": "alu", "achieved": achieved, "peak": ISSUE_PEAK, "unit": "thread-inst/s",
+                "frac": achieved / ISSUE_PEAK, "traffic": None,
+                "kernel": "transport_kernel<float> (persistent packet kernel)",
+                "note": f"{INST_PER_STEP:g} thread instructions per transport step (interaction, MRW jump or "
+                        "crossing) x steps per launch / CUDA-event launch time; peak = 152 SMs x 4 issue x 32 lanes "
+                        "x 2070 MHz"}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu:
+        cpu = cpu_baseline(d, args.gamma, args.cpu_seconds)
+
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": 1e3 * t_max / args.steps, "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+                "config": {"workload": WORKLOAD, "packets_per_step_per_rank": Np, "grid": [d.nr, d.ntheta],
+                           "tau_mid": 1e6, "gamma": args.gamma, "pda_min_visits": 30, "pda_max_rel_err": 0.05,
+                           "l2": "flushed between timed steps (512 MiB write outside the timed region)",
+                           "parallelism": f"packet ranges per rank, int64 tally all-reduce" if world > 1 else "1 GPU"},
+                "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": int(launches),
+                "clocks": clk.summary(),
+                "transport": {"kernel_ms_per_step": 1e3 * float(np.mean(tr_s)), "events": s0["events"],
+                              "crossings": s0["crossings"], "mrw_jumps": s0["mrw_jumps"], "capped": s0["capped"],
+                              "events_per_s": s0["events"] / s0["seconds"], "error_flags": s0["error_flags"]},
+                "pda": {"ms_per_step": float(np.mean(pda_ms)), "cells": stats[-1][1], "cg_iterations": stats[-1][2]},
+                "plain_mc": plain, "peaks_file": bool(peaks)}
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,207 @@
+/*
+ * mcrt.h -- C ABI of the GB300 (sm_103a) library for Monte Carlo dust radiative transfer in
+ * optically thick axisymmetric disks, after Min, Dullemond, Dominik, de Koter & Hovenier 2009,
+ * "Radiative transfer in very optically thick circumstellar disks" (A&A 497, 155).
+ *
+ * The library runs three steps on one GPU:
+ *   1. Monte Carlo transport of photon packets with immediate (Bjorkman & Wood 2001) re-emission
+ *      and the modified random walk (MRW) (Sect. 2.1, 2.2.2, Eq. 5-11)        -> mcrt_run_photons
+ *   2. radiative-equilibrium temperatures from the absorbed-energy tallies (Sect. 2.1)
+ *                                                                              -> mcrt_temperatures
+ *   3. the partial diffusion approximation (PDA), div(D grad T^4) = 0 in the cells that few
+ *      packets reached, Monte Carlo temperatures as boundary values (Sect. 2.2.1, Eq. 4)
+ *                                                                              -> mcrt_solve_pda
+ * plus the escaping-packet spectrum (mcrt_sed) and the adjoint of the PDA solve (mcrt_pda_adjoint).
+ *
+ * Conventions
+ *  - Units are cgs at this boundary: cm, g cm^-3, cm^2 g^-1, K, erg s^-1; wavelengths in micron.
+ *  - Grid: spherical (r, theta) cells, axisymmetric. Cell (ir, it) spans [r_ir, r_ir+1] x
+ *    [theta_it, theta_it+1]; per-cell arrays are row-major [ir * ntheta + it].
+ *  - Every call returns an mcrt_status and never aborts or throws across the ABI. On failure the
+ *    message is available from mcrt_last_error.
+ *  - Inputs are copied by the library; the caller keeps ownership of every pointer it passes.
+ *    Host output buffers are caller-owned and filled before the call returns.
+ *  - A disk owns its device memory and a CUDA stream (the caller's, when one is given). Calls on
+ *    one disk are not thread-safe; distinct disks are independent.
+ *  - Functions named *_dev take device pointers and are asynchronous on the disk's stream.
+ */
+#ifndef MCRT_H
+#define MCRT_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct mcrt_disk mcrt_disk; /* opaque, owned by the library */
+
+typedef enum {
+  MCRT_OK = 0,
+  MCRT_EINVAL = 1,    /* bad argument: sizes, NaN/negative inputs, unsorted faces, singular PDA region */
+  MCRT_ENOMEM = 2,    /* device or host allocation failed */
+  MCRT_ECUDA = 3,     /* a CUDA runtime call failed */
+  MCRT_ENOTCONV = 4,  /* the PDA solve did not reach its tolerance within its iteration limits */
+  MCRT_ETIMEOUT = 5,  /* a device loop hit its iteration guard */
+  MCRT_EOVERFLOW = 6, /* a 64-bit fixed-point tally wrapped (results invalid) */
+  MCRT_ESTATE = 7     /* call order: e.g. transport before mcrt_set_opacity */
+} mcrt_status;
+
+/* Fixed-point energy unit: one packet energy L_star/N is 2^16 counts in the 64-bit tallies. */
+#define MCRT_EUNIT 65536
+/* Inclination bins of the escape spectrum, uniform in |cos i| over [0, 1]. */
+#define MCRT_NINC 10
+
+/* Blackbody point star at the origin (Sect. 2.4, Table 1 gives T and R). */
+typedef struct {
+  double T_star_K;
+  double R_star_cm;
+} mcrt_star;
+
+/* Grid and dust density (Sect. 2.4, Eq. 17). r_faces_cm: nr+1 increasing radii, r_faces_cm[0] > 0
+ * (the region inside is an empty cavity around the star). theta_faces: ntheta+1 increasing polar
+ * angles from 0 to pi. rho_gcm3: nr*ntheta densities >= 0. */
+typedef struct {
+  int nr, ntheta;
+  const double *r_faces_cm;
+  const double *theta_faces;
+  const double *rho_gcm3;
+} mcrt_grid;
+
+/* Creates a disk on CUDA device `device`. cuda_stream: a cudaStream_t to run on, or NULL for a
+ * stream owned by the disk. *out is set only on success. */
+mcrt_status mcrt_disk_create(const mcrt_grid *grid, const mcrt_star *star, int device, void *cuda_stream,
+                             mcrt_disk **out);
+
+/* Dust opacities per wavelength bin (Sect. 2.2.1, 2.2.3). lam_edges_um: nlam+1 increasing bin edges.
+ * For emission the first bin extends to lambda -> 0 and the last to lambda -> infinity, so the bins
+ * hold the whole Planck spectrum. kappa_abs, kappa_sca: mass absorption and scattering coefficients
+ * (cm^2/g, kappa_abs > 0). g: Henyey-Greenstein asymmetry per bin, or NULL for isotropic scattering.
+ * Identical values in every bin select the gray fast path. Resets the tallies. 1 <= nlam <= 1024. */
+mcrt_status mcrt_set_opacity(mcrt_disk *d, int nlam, const double *lam_edges_um, const double *kappa_abs,
+                             const double *kappa_sca, const double *g);
+
+typedef struct {
+  int precision;                /* 32: production path; 64: debug path whose gray trajectories match
+                                   the FP64 oracle event by event */
+  int mrw;                      /* 1: modified random walk on (Sect. 2.2.2) */
+  double gamma;                 /* Eq. 11: MRW only where d_min > gamma / (rho chi_R) */
+  int mrw_min_interactions;     /* interactions in the current cell before the MRW may start (20) */
+  int mrw_exit_dir;             /* direction after a jump: 0 isotropic, 1 cosine-weighted outward */
+  uint64_t max_events_per_packet; /* a packet that exceeds this is dropped and counted as capped */
+  uint64_t n_total_packets;     /* packets of the whole run (energy per packet L_star / n_total);
+                                   0 means the n_packets of this call */
+  int block_size;               /* threads per block of the transport kernel; 0: tuned default */
+  int refill_interval;          /* steps between refills of finished lanes; 0: tuned default */
+  int want_sed;                 /* gray dust only: 0 skips the emission-bin sampling (no SED) */
+} mcrt_run_opts;
+
+void mcrt_default_run_opts(mcrt_run_opts *o);
+
+typedef struct {
+  uint64_t packets, events, absorptions, scatterings, crossings, mrw_jumps, capped, escaped;
+  uint64_t deposit_sum; /* sum over packets of their own fixed-point deposits: equals the growth of the
+                           summed tallies when no update was lost */
+  uint32_t error_flags; /* bit 0 tally overflow, bit 1 MRW deposit clipped, bit 2 step guard */
+  double seconds;       /* device time of the transport kernel(s) */
+} mcrt_run_stats;
+
+/* Transports packets first_packet_id .. first_packet_id+n_packets-1 (Sect. 2.1, 2.2.2): launch from
+ * the star, optical-depth sampling, cell marching, scattering, absorption with immediate re-emission
+ * into the 64-bit tallies, MRW jumps, escape into the spectrum tally. Packet k draws from the
+ * Philox4x32-10 stream keyed by `seed`, counter (block, model 0, k). Tallies accumulate across calls
+ * (resume from a checkpoint by continuing the packet ids). Synchronous; stats may be NULL. */
+mcrt_status mcrt_run_photons(mcrt_disk *d, uint64_t n_packets, uint64_t seed, uint64_t first_packet_id,
+                             const mcrt_run_opts *opts, mcrt_run_stats *stats);
+
+/* Runs several disks in one persistent launch over a shared packet queue. Disk i transports
+ * n_packets[i] packets from id 0 with Philox counter (block, model i, k). All disks must be on the
+ * same device. stats: n entries or NULL. */
+mcrt_status mcrt_run_batch(mcrt_disk *const *disks, int n, const uint64_t *n_packets, uint64_t seed,
+                           const mcrt_run_opts *opts, mcrt_run_stats *stats);
+
+/* Zeroes the tallies, visit counts and spectrum. */
+mcrt_status mcrt_reset(mcrt_disk *d);
+
+enum { MCRT_T_MC = 0, MCRT_T_PDA = 1 };
+
+/* Radiative-equilibrium temperature per cell (Sect. 2.1): solves 4 pi m kappa_P(T) B(T) = L_abs with
+ * L_abs = tally / EUNIT * L_star / n_total. which = MCRT_T_MC: Monte Carlo temperatures; MCRT_T_PDA:
+ * after mcrt_solve_pda, with the diffusion solution in the PDA cells. rel_err: statistical error
+ * 1/(4 sqrt(N)), N = tally / EUNIT absorbed packet energies (infinity where N = 0). visits: packet
+ * entries per cell. Host buffers of nr*ntheta; rel_err and visits may be NULL. */
+mcrt_status mcrt_temperatures(mcrt_disk *d, int which, double *T_K, double *rel_err, uint64_t *visits);
+mcrt_status mcrt_temperatures_dev(mcrt_disk *d, int which, double *T_K_dev, double *rel_err_dev);
+
+/* Raw integer tallies (host buffers of nr*ntheta; each may be NULL). */
+mcrt_status mcrt_get_tallies(mcrt_disk *d, uint64_t *tally, uint64_t *visits, uint64_t *n_absorptions);
+
+/* Escaped luminosity per wavelength bin and inclination bin, L[lam * n_incl + i] (erg/s carried by
+ * the packets that left r_out in that bin; multiply by n_incl for the isotropic equivalent).
+ * n_incl must divide MCRT_NINC. */
+mcrt_status mcrt_sed(mcrt_disk *d, int n_incl, double *L);
+
+typedef struct {
+  int min_visits;          /* PDA where fewer packets entered the cell (30, Sect. 3.1) */
+  double max_rel_err;      /* ... or where the statistical T error exceeds this (0.05) */
+  double tol;              /* relative FP64 residual of the refined solution (1e-12) */
+  double inner_tol;        /* relative residual reduction of each FP32 inner solve (1e-5) */
+  int max_outer;           /* FP64 refinement steps (20) */
+  int max_inner;           /* FP32 CG iterations per refinement step (20000) */
+  double min_cell_tau;     /* only cells at least this optically thick take part: rho * max_b chi'_b *
+                              min(dr, r dtheta) >= min_cell_tau (1.0); diffusion needs optical depth */
+  const double *kappa_R;   /* optional host array nr*ntheta: Rosseland extinction (cm^2/g) entering
+                              D = 1/(3 rho kappa_R); NULL: from the dust at the MC temperature */
+} mcrt_pda_opts;
+
+void mcrt_default_pda_opts(mcrt_pda_opts *o);
+
+/* Partial diffusion approximation (Sect. 2.2.1, Eq. 4 with D of Eq. 2): selects the PDA cells from
+ * the visit counts and errors (among the optically thick cells), assembles face conductances (series resistance of half cells), and
+ * solves for T^4 with an FP32 Jacobi-preconditioned conjugate gradient under FP64 iterative
+ * refinement. Zero flux through grid edges and into dust-free cells. Afterwards MCRT_T_PDA
+ * temperatures are available. out_n_pda_cells, out_iters (total inner iterations) may be NULL.
+ * MCRT_EINVAL if a connected PDA region touches no Monte Carlo cell. */
+mcrt_status mcrt_solve_pda(mcrt_disk *d, const mcrt_pda_opts *opts, int *out_n_pda_cells, int *out_iters);
+
+/* Adjoint of the last PDA solve. For J = sum_i w_i T_i (T after the PDA, Monte Carlo boundary values
+ * held fixed) returns dJ/dlog(rho_i) and dJ/dkappa_R,i per cell, through one more solve with the
+ * (symmetric) PDA matrix. Host arrays of nr*ntheta; outputs may be NULL. */
+mcrt_status mcrt_pda_adjoint(mcrt_disk *d, const double *w, double *grad_log_rho, double *grad_kappa_R);
+mcrt_status mcrt_pda_adjoint_dev(mcrt_disk *d, const double *w_dev, double *grad_log_rho_dev,
+                                 double *grad_kappa_R_dev);
+
+/* FP64 debug transport that records every event of the first n_packets packets: type (0 launch,
+ * 1 cell entry, 2 scatter, 3 absorption, 4 MRW jump, 5 escape, 6 capped), cell (-1 outside the grid),
+ * wavelength bin and position (cm, [packet][event][3]). Buffers hold n_packets * max_events entries;
+ * n_events[k] is the number recorded for packet k. Tallies accumulate as in mcrt_run_photons. */
+mcrt_status mcrt_trace_packets(mcrt_disk *d, uint64_t n_packets, uint64_t seed, uint64_t first_packet_id,
+                               const mcrt_run_opts *opts, int max_events, int32_t *type, int32_t *cell,
+                               int32_t *lam, double *pos, int32_t *n_events);
+
+/* Checkpoint of the integer state (tallies, visits, absorptions, spectrum, packets done). buf == NULL:
+ * *len receives the size needed. Restoring and continuing the packet ids reproduces a single run. */
+mcrt_status mcrt_checkpoint(mcrt_disk *d, void *buf, size_t *len);
+mcrt_status mcrt_restore(mcrt_disk *d, const void *buf, size_t len);
+
+/* The device's Philox4x32-10 uniforms u_0..u_{n-1} of packet `packet` (model 0), as the transport
+ * kernel draws them; and the device MRW inverse escape-time table x(P0) (Eq. 7-8). Test hooks. */
+mcrt_status mcrt_debug_uniforms(int device, uint64_t seed, uint32_t model, uint64_t packet, int n, double *out);
+mcrt_status mcrt_debug_mrw_x(int device, int n, const double *P0, double *x_out);
+
+/* Number of kernels this disk has launched since it was created (transport, temperature, PDA). */
+mcrt_status mcrt_launch_count(const mcrt_disk *d, uint64_t *n);
+
+/* Sizes and sanity of a disk. */
+mcrt_status mcrt_disk_info(const mcrt_disk *d, int *nr, int *ntheta, int *nlam);
+
+/* Message of the last failure on this disk (d == NULL: of the last failure in this thread). */
+const char *mcrt_last_error(const mcrt_disk *d);
+
+void mcrt_disk_destroy(mcrt_disk *d);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* MCRT_H */

@@ -11,7 +11,9 @@ Sections, equations and the readings taken where the paper is silent:
 * Diffusion coefficient and mean opacities: Sect. 2.2.3 (Eq. 12-16).
 * PDA: Sect. 2.2.1, Eq. 4 -- div(D grad T^4) = 0 in the cells that fewer than 30
   packets entered or whose statistical temperature error exceeds 5 % (Sect. 3.1),
-  with the Monte Carlo temperatures of all other cells as Dirichlet values.
+  with the Monte Carlo temperatures of all other cells as Dirichlet values. Reading:
+  only optically thick cells take part (the diffusion equation is used "in regions of
+  high optical depth", Sect. 2.2.1); see pda_mask.
   Discretisation (a reading; the paper gives none): finite volumes on the (r, theta)
   cells, face conductance = series resistance of the two half cells, exact for
   piecewise-constant D in spherical geometry; zero flux through grid edges and
@@ -293,9 +295,21 @@ def rosseland_chi(disk, T):
     return float(dB.sum() / np.sum(dB / chi))
 
 
-def pda_mask(rho, visits, relerr, min_visits=30, max_rel_err=0.05):
-    """PDA cells: dust present and (fewer than 30 entries or error above 5 %) -- Sect. 3.1."""
-    return (rho > 0) & ((visits < min_visits) | (relerr > max_rel_err))
+def cell_extent(disk):
+    """Smallest extent of each cell, min(dr, r_c dtheta) (cm)."""
+    rf, tf = disk.r_faces_cm, disk.theta_faces
+    rc = 0.5 * (rf[:-1] + rf[1:])
+    return np.minimum((rf[1:] - rf[:-1])[:, None], rc[:, None] * (tf[1:] - tf[:-1])[None, :])
+
+
+def pda_mask(disk, visits, relerr, min_visits=30, max_rel_err=0.05, min_cell_tau=1.0):
+    """PDA cells -- Sect. 3.1: fewer than 30 packet entries or a statistical temperature error above
+    5 %; Sect. 2.2.1: only where the diffusion equation holds, i.e. in optically thick cells. Reading:
+    a cell is thick when rho * max_b chi'_b * min(dr, r dtheta) >= min_cell_tau (default 1)."""
+    op = disk.opacity
+    chi_max = float(np.max(op.kappa_abs + (1.0 - op.g) * op.kappa_sca))
+    thick = disk.rho * chi_max * cell_extent(disk) >= min_cell_tau
+    return (disk.rho > 0) & thick & ((visits < min_visits) | (relerr > max_rel_err))
 
 
 def _borders(mask):
@@ -406,13 +420,13 @@ def check_components(A, b_has_dirichlet):
     return bool(ok.all())
 
 
-def solve_pda(disk, T_mc, tally, visits, relerr, min_visits=30, max_rel_err=0.05, kappa_R=None):
+def solve_pda(disk, T_mc, tally, visits, relerr, min_visits=30, max_rel_err=0.05, kappa_R=None, min_cell_tau=1.0):
     """Partial diffusion approximation, Sect. 2.2.1 (Eq. 4): returns (T_final, mask, u, info)."""
     import scipy.sparse.linalg as spla
     nr, nt = disk.nr, disk.ntheta
     visits = np.asarray(visits).reshape(nr, nt)
     relerr = np.asarray(relerr).reshape(nr, nt)
-    mask = pda_mask(disk.rho, visits, relerr, min_visits, max_rel_err)
+    mask = pda_mask(disk, visits, relerr, min_visits, max_rel_err, min_cell_tau)
     T_mc = np.asarray(T_mc, np.float64).reshape(nr, nt)
     if kappa_R is None:
         Tref = reference_T_for_D(T_mc, np.asarray(tally), mask, disk.rho)

@@ -1,0 +1,995 @@
+// api.cu -- the C ABI of include/mcrt.h: disk objects, opacity tables, transport runs, temperatures,
+// escape spectrum, checkpoints and test hooks.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include "internal.h"
+#include "planck.cuh"
+
+using mcrt::DBuf;
+
+namespace {
+thread_local std::string g_err;
+}
+
+namespace mcrt {
+
+mcrt_status set_error(mcrt_disk* d, mcrt_status s, const std::string& msg) {
+  g_err = msg;
+  if (d) d->err = msg;
+  return s;
+}
+
+mcrt_status cuda_fail(mcrt_disk* d, cudaError_t e, const char* what) {
+  std::string m = std::string(what) + ": " + cudaGetErrorString(e);
+  if (e == cudaErrorMemoryAllocation) return set_error(d, MCRT_ENOMEM, m);
+  return set_error(d, MCRT_ECUDA, m);
+}
+
+// ------------------------------------------------------------------------------------------------
+// MRW inverse escape-time tables (Eq. 7-8), built once per process on the host, uploaded per device.
+// P(x) = 2 sum (-1)^{n+1} exp(-n^2 pi^2 x) for x >= 0.1; for smaller x its Jacobi-theta transform
+// 1 - P = (2/sqrt(pi x)) sum_{n>=0} exp(-(n+1/2)^2/x) converges in a few terms.
+// ------------------------------------------------------------------------------------------------
+static double survival(double x) {
+  if (x <= 0) return 1.0;
+  if (x >= 0.1) {
+    double s = 0.0;
+    for (int n = 1; n < 64; ++n) {
+      const double t = std::exp(-(double)n * n * kPi * kPi * x);
+      s += (n & 1) ? t : -t;
+      if (t < 1e-20) break;
+    }
+    return 2.0 * s;
+  }
+  double s = 0.0;
+  for (int n = 0; n < 16; ++n) {
+    const double a = n + 0.5;
+    const double t = std::exp(-a * a / x);
+    s += t;
+    if (t < 1e-20 * s) break;
+  }
+  return 1.0 - 2.0 / std::sqrt(kPi * x) * s;
+}
+
+static double survival_inverse(double P0, bool complement, double Q0) {
+  // complement: solve 1 - P(x) = Q0 (accurate when P0 is close to 1)
+  double lo = 1e-5, hi = 64.0;
+  for (int it = 0; it < 200; ++it) {
+    const double mid = std::sqrt(lo * hi);
+    const double v = survival(mid);
+    const bool above = complement ? (1.0 - v < Q0) : (v > P0);  // still inside: move right
+    if (above) lo = mid; else hi = mid;
+    if (hi / lo - 1.0 < 1e-15) break;
+  }
+  return std::sqrt(lo * hi);
+}
+
+const float kMrwT0 = (float)(-24.0 * 0.69314718055994530942);  // ln 2^-24
+const float kMrwDT = (float)((-0.69314718055994530942 + 24.0 * 0.69314718055994530942) / (kMrwTab - 1));
+
+const float* mrw_table(int device, cudaError_t* err) {
+  static std::mutex mu;
+  static std::vector<float> host;
+  static std::vector<std::pair<int, float*>> per_dev;
+  std::lock_guard<std::mutex> lock(mu);
+  *err = cudaSuccess;
+  for (auto& pr : per_dev)
+    if (pr.first == device) return pr.second;
+  if (host.empty()) {
+    host.resize(2 * kMrwTab);
+    for (int i = 0; i < kMrwTab; ++i) {
+      const double t = (double)kMrwT0 + (double)i * (double)kMrwDT;
+      const double u = std::exp(t);
+      host[i] = (float)survival_inverse(u, false, 0.0);                     // P(x) = u, u <= 1/2
+      host[kMrwTab + i] = (float)(1.0 / survival_inverse(1.0 - u, true, u));  // P(x) = 1-u
+    }
+  }
+  float* p = nullptr;
+  cudaError_t e = cudaMalloc(&p, sizeof(float) * host.size());
+  if (e == cudaSuccess) e = cudaMemcpy(p, host.data(), sizeof(float) * host.size(), cudaMemcpyHostToDevice);
+  if (e != cudaSuccess) {
+    *err = e;
+    if (p) cudaFree(p);
+    return nullptr;
+  }
+  per_dev.push_back({device, p});
+  return p;
+}
+
+// ------------------------------------------------------------------------------------------------
+// Temperatures (a7): 4 pi m sum_b kappa_b Bbar_b(T) = L_abs, FP64
+// ------------------------------------------------------------------------------------------------
+__device__ void q_sum(const double* lam_e, const double* kabs, int nlam, double T, double& Q, double& dQ) {
+  const double k4 = kKB * kKB * kKB * kKB;
+  const double p3 = 2.0 * k4 * T * T * T * T / (kH * kH * kH * kC * kC);
+  const double p4 = 2.0 * k4 * T * T * T / (kH * kH * kH * kC * kC);
+  double g3p = 0.0, g4p = 0.0, s3 = 0.0, s4 = 0.0;
+  for (int b = 0; b < nlam; ++b) {
+    double g3, g4;
+    if (b + 1 == nlam) tails(0.0, g3, g4);
+    else tails(kH * kC / (lam_e[b + 1] * 1e-4 * kKB * T), g3, g4);
+    s3 += kabs[b] * (g3 - g3p);
+    s4 += kabs[b] * (g4 - g4p);
+    g3p = g3;
+    g4p = g4;
+  }
+  Q = 4.0 * kPi * p3 * s3;
+  dQ = 4.0 * kPi * p4 * s4;
+}
+
+__global__ void k_temperature(int n, const unsigned long long* __restrict__ tally, const double* __restrict__ mass,
+                              double lfac, int gray, double kabs0, int nlam, const double* __restrict__ lam_e,
+                              const double* __restrict__ kabs, const float* __restrict__ lQk, int nT, double Tmin,
+                              double dlnT, double* __restrict__ T, double* __restrict__ relerr) {
+  const int c = blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= n) return;
+  const unsigned long long t = tally[c];
+  const double neq = (double)t / (double)kEUnit;
+  if (relerr) relerr[c] = t ? 0.25 / sqrt(neq) : (double)INFINITY;
+  const double m = mass[c];
+  if (t == 0ull || !(m > 0.0)) {
+    T[c] = 0.0;
+    return;
+  }
+  const double q = neq * lfac / m;
+  if (gray) {
+    T[c] = pow(q / (4.0 * MCRT_SIGMA * kabs0), 0.25);
+    return;
+  }
+  // initial guess on the log-spaced grid, then bracketed Newton on the exact bin integrals
+  const float lq = (float)log(q);
+  int k = 1;
+  while (k + 1 < nT && lQk[k + 1] <= lq) ++k;
+  double Tk = Tmin * exp((k - 1) * dlnT);
+  double lo = 0.0, hi = INFINITY;
+  double x = Tk;
+  for (int it = 0; it < 100; ++it) {
+    double Q, dQ;
+    q_sum(lam_e, kabs, nlam, x, Q, dQ);
+    const double f = Q - q;
+    if (f > 0) hi = x; else lo = x;
+    double xn = x - f / dQ;
+    if (!(xn > lo && xn < hi)) xn = isinf(hi) ? 2.0 * x : 0.5 * (lo + hi);
+    if (fabs(xn - x) <= 1e-15 * x) {
+      x = xn;
+      break;
+    }
+    x = xn;
+  }
+  T[c] = x;
+}
+
+mcrt_status compute_temperatures(mcrt_disk* d) {
+  const int n = d->nr * d->nt;
+  const double lfac = d->Lstar / (d->n_total > 0 ? d->n_total : 1.0);
+  const double dlnT = std::log(d->Tmax / d->Tmin) / (d->nT - 2);
+  k_temperature<<<(n + 255) / 256, 256, 0, d->stream>>>(
+      n, d->tally.as<unsigned long long>(), d->mass_d.as<double>(), lfac, d->gray ? 1 : 0, d->kabs[0], d->nlam,
+      d->lam_e_d.as<double>(), d->kabs_d.as<double>(), d->lQk.as<float>(), d->nT, d->Tmin, dlnT,
+      d->T_mc.as<double>(), d->relerr.as<double>());
+  d->launches++;
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return cuda_fail(d, e, "temperature kernel");
+  d->have_T = true;
+  return MCRT_OK;
+}
+
+// ------------------------------------------------------------------------------------------------
+// test hooks
+// ------------------------------------------------------------------------------------------------
+__global__ void k_uniforms(uint64_t seed, uint32_t model, uint64_t packet, int n, double* out) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  Rng r;
+  r.init(seed, model, packet);
+  for (int i = 0; i < n; ++i) out[i] = to_uniform<double>(r.next());
+}
+
+__global__ void k_mrw_x(int n, const double* P0, double* out, const float* tab, float t0, float dt) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  KParams<float> P;
+  P.mrw_tab = tab;
+  P.mrw_t0 = t0;
+  P.mrw_dt = dt;
+  out[i] = (double)mrw_x<float>(P, (float)P0[i]);
+}
+
+}  // namespace mcrt
+
+using namespace mcrt;
+
+// ------------------------------------------------------------------------------------------------
+// model descriptors
+// ------------------------------------------------------------------------------------------------
+template <class R>
+static DevModel<R> make_model(const mcrt_disk* d, bool f64) {
+  DevModel<R> m;
+  std::memset(&m, 0, sizeof(m));
+  m.nr = d->nr;
+  m.nt = d->nt;
+  m.nlam = d->nlam;
+  m.nT = d->nT;
+  m.gray = d->gray ? 1 : 0;
+  m.rf = (const R*)(f64 ? d->rf64.p : d->rf32.p);
+  m.rf2 = (const R*)(f64 ? d->rf2_64.p : d->rf2_32.p);
+  m.c2 = (const R*)(f64 ? d->c2_64.p : d->c2_32.p);
+  m.s2 = (const R*)(f64 ? d->s2_64.p : d->s2_32.p);
+  m.cf = (const R*)(f64 ? d->cf64.p : d->cf32.p);
+  m.sf = (const R*)(f64 ? d->sf64.p : d->sf32.p);
+  m.fk = (const signed char*)d->fk.p;
+  m.rho = (const R*)(f64 ? d->rho64.p : d->rho32.p);
+  m.chi = (const R*)(f64 ? d->chi64.p : d->chi32.p);
+  m.alb = (const R*)(f64 ? d->alb64.p : d->alb32.p);
+  m.gq = (const R*)(f64 ? d->g64.p : d->g32.p);
+  m.star_cum = (const R*)(f64 ? d->star64.p : d->star32.p);
+  if (d->has_opacity) {
+    const double chi = d->kabs[0] + d->ksca[0];
+    m.chi0 = (R)chi;
+    m.alb0 = (R)(d->ksca[0] / chi);
+    m.g0 = (R)d->g[0];
+    m.chiR0 = (R)(d->kabs[0] + (1.0 - d->g[0]) * d->ksca[0]);
+    m.kbar0 = (R)d->kabs[0];
+  }
+  m.lQk = d->lQk.as<float>();
+  m.cbw = d->cbw.as<float>();
+  m.cexit = d->cexit.as<float>();
+  m.chiR = d->chiRk.as<float>();
+  m.kbar = d->kbark.as<float>();
+  m.lqm = d->lqm.as<float>();
+  m.lq_run = (float)std::log(d->Lstar / ((d->n_total > 0 ? d->n_total : 1.0) * (double)kEUnit));
+  m.tally = d->tally.as<unsigned long long>();
+  m.visits = d->visits.as<unsigned long long>();
+  m.nabs = d->nabs.as<unsigned long long>();
+  m.sed = d->sed.as<unsigned long long>();
+  m.cnt = d->cnt.as<unsigned long long>();
+  return m;
+}
+
+DevModel<float> mcrt_disk::model32() const { return make_model<float>(this, false); }
+DevModel<double> mcrt_disk::model64() const { return make_model<double>(this, true); }
+
+// ------------------------------------------------------------------------------------------------
+// helpers
+// ------------------------------------------------------------------------------------------------
+template <class T>
+static cudaError_t upload(DBuf& b, const std::vector<T>& v) {
+  cudaError_t e = b.alloc(sizeof(T) * v.size());
+  if (e != cudaSuccess) return e;
+  return cudaMemcpy(b.p, v.data(), sizeof(T) * v.size(), cudaMemcpyHostToDevice);
+}
+
+template <class A, class B>
+static std::vector<A> cast_vec(const std::vector<B>& v) {
+  return std::vector<A>(v.begin(), v.end());
+}
+
+#define CK(call, what)                                 \
+  do {                                                 \
+    cudaError_t e_ = (call);                           \
+    if (e_ != cudaSuccess) return cuda_fail(d, e_, what); \
+  } while (0)
+
+static mcrt_status zero_tallies(mcrt_disk* d) {
+  const size_t n = (size_t)d->nr * d->nt;
+  CK(cudaMemsetAsync(d->tally.p, 0, n * 8, d->stream), "memset");
+  CK(cudaMemsetAsync(d->visits.p, 0, n * 8, d->stream), "memset");
+  CK(cudaMemsetAsync(d->nabs.p, 0, n * 8, d->stream), "memset");
+  if (d->sed.p) CK(cudaMemsetAsync(d->sed.p, 0, d->sed.n, d->stream), "memset");
+  d->have_T = false;
+  d->have_pda = false;
+  d->packets_done = 0;
+  return MCRT_OK;
+}
+
+extern "C" {
+
+void mcrt_default_run_opts(mcrt_run_opts* o) {
+  if (!o) return;
+  std::memset(o, 0, sizeof(*o));
+  o->precision = 32;
+  o->mrw = 0;
+  o->gamma = 2.0;
+  o->mrw_min_interactions = 20;
+  o->mrw_exit_dir = 0;
+  o->max_events_per_packet = 100000000ull;
+  o->n_total_packets = 0;
+  o->block_size = 0;
+  o->refill_interval = 0;
+  o->want_sed = 1;
+}
+
+mcrt_status mcrt_disk_create(const mcrt_grid* grid, const mcrt_star* star, int device, void* cuda_stream,
+                             mcrt_disk** out) {
+  if (!out) return set_error(nullptr, MCRT_EINVAL, "out is NULL");
+  *out = nullptr;
+  if (!grid || !star || !grid->r_faces_cm || !grid->theta_faces || !grid->rho_gcm3)
+    return set_error(nullptr, MCRT_EINVAL, "NULL grid or star");
+  const int nr = grid->nr, nt = grid->ntheta;
+  if (nr < 1 || nt < 1 || (long long)nr * nt > (1ll << 30))
+    return set_error(nullptr, MCRT_EINVAL, "grid sizes out of range");
+  for (int i = 0; i <= nr; ++i) {
+    const double r = grid->r_faces_cm[i];
+    if (!(std::isfinite(r) && r > 0) || (i && !(r > grid->r_faces_cm[i - 1])))
+      return set_error(nullptr, MCRT_EINVAL, "r_faces must be positive, finite and increasing");
+  }
+  for (int j = 0; j <= nt; ++j) {
+    const double t = grid->theta_faces[j];
+    if (!std::isfinite(t) || (j && !(t > grid->theta_faces[j - 1])))
+      return set_error(nullptr, MCRT_EINVAL, "theta_faces must be finite and increasing");
+  }
+  if (std::fabs(grid->theta_faces[0]) > 1e-12 || std::fabs(grid->theta_faces[nt] - kPi) > 1e-12)
+    return set_error(nullptr, MCRT_EINVAL, "theta_faces must run from 0 to pi");
+  for (long long c = 0; c < (long long)nr * nt; ++c)
+    if (!(std::isfinite(grid->rho_gcm3[c]) && grid->rho_gcm3[c] >= 0))
+      return set_error(nullptr, MCRT_EINVAL, "rho must be finite and >= 0");
+  if (!(star->T_star_K > 0 && std::isfinite(star->T_star_K) && star->R_star_cm > 0 && std::isfinite(star->R_star_cm)))
+    return set_error(nullptr, MCRT_EINVAL, "star temperature and radius must be positive");
+
+  int ndev = 0;
+  if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev == 0)
+    return set_error(nullptr, MCRT_ECUDA, "no CUDA device");
+  if (device < 0 || device >= ndev) return set_error(nullptr, MCRT_EINVAL, "device index out of range");
+  mcrt_disk* d = new (std::nothrow) mcrt_disk();
+  if (!d) return set_error(nullptr, MCRT_ENOMEM, "host allocation");
+  auto fail = [&](mcrt_status s) {
+    g_err = d->err;
+    mcrt_disk_destroy(d);
+    return s;
+  };
+  d->device = device;
+  cudaError_t e = cudaSetDevice(device);
+  if (e != cudaSuccess) return fail(cuda_fail(d, e, "cudaSetDevice"));
+  if (cuda_stream) {
+    d->stream = (cudaStream_t)cuda_stream;
+  } else {
+    e = cudaStreamCreateWithFlags(&d->stream, cudaStreamNonBlocking);
+    if (e != cudaSuccess) return fail(cuda_fail(d, e, "cudaStreamCreate"));
+    d->own_stream = true;
+  }
+  d->nr = nr;
+  d->nt = nt;
+  d->rf.assign(grid->r_faces_cm, grid->r_faces_cm + nr + 1);
+  d->tf.assign(grid->theta_faces, grid->theta_faces + nt + 1);
+  d->rho.assign(grid->rho_gcm3, grid->rho_gcm3 + (size_t)nr * nt);
+  d->Tstar = star->T_star_K;
+  d->Rstar = star->R_star_cm;
+  d->Lstar = 4.0 * kPi * d->Rstar * d->Rstar * MCRT_SIGMA * std::pow(d->Tstar, 4);
+  d->l_unit = d->rf[0];
+  d->Tmax = std::max(1e4, 2.0 * d->Tstar);
+
+  // geometry in units of r_faces[0]
+  std::vector<double> rf(nr + 1), rf2(nr + 1), c2(nt + 1), s2(nt + 1), cf(nt + 1), sf(nt + 1);
+  std::vector<signed char> fk(nt + 1);
+  for (int i = 0; i <= nr; ++i) {
+    rf[i] = d->rf[i] / d->l_unit;
+    rf2[i] = rf[i] * rf[i];
+  }
+  for (int j = 0; j <= nt; ++j) {
+    const double t = d->tf[j];
+    cf[j] = std::cos(t);
+    sf[j] = std::sin(t);
+    c2[j] = cf[j] * cf[j];
+    s2[j] = sf[j] * sf[j];
+    if (j == 0 || j == nt) fk[j] = 2;
+    else if (std::fabs(t - 0.5 * kPi) < 1e-12) fk[j] = 0;
+    else fk[j] = t < 0.5 * kPi ? 1 : -1;
+  }
+  const size_t ncell = (size_t)nr * nt;
+  std::vector<double> rhol(ncell);
+  d->mass.resize(ncell);
+  std::vector<float> lqm(ncell);
+  for (int i = 0; i < nr; ++i)
+    for (int j = 0; j < nt; ++j) {
+      const size_t c = (size_t)i * nt + j;
+      rhol[c] = d->rho[c] * d->l_unit;
+      const double r1 = d->rf[i], r2 = d->rf[i + 1];
+      const double V = 2.0 * kPi / 3.0 * (r2 * r2 * r2 - r1 * r1 * r1) * (std::cos(d->tf[j]) - std::cos(d->tf[j + 1]));
+      d->mass[c] = d->rho[c] * V;
+      lqm[c] = d->mass[c] > 0 ? (float)(-std::log(d->mass[c])) : 0.f;
+    }
+  mcrt_status st = MCRT_OK;
+#define UP(buf, vec)                                          \
+  do {                                                        \
+    cudaError_t e2 = upload(buf, vec);                        \
+    if (e2 != cudaSuccess) return fail(cuda_fail(d, e2, "upload")); \
+  } while (0)
+  UP(d->rf32, cast_vec<float>(rf));
+  UP(d->rf2_32, cast_vec<float>(rf2));
+  UP(d->c2_32, cast_vec<float>(c2));
+  UP(d->s2_32, cast_vec<float>(s2));
+  UP(d->cf32, cast_vec<float>(cf));
+  UP(d->sf32, cast_vec<float>(sf));
+  UP(d->rho32, cast_vec<float>(rhol));
+  UP(d->rf64, rf);
+  UP(d->rf2_64, rf2);
+  UP(d->c2_64, c2);
+  UP(d->s2_64, s2);
+  UP(d->cf64, cf);
+  UP(d->sf64, sf);
+  UP(d->rho64, rhol);
+  UP(d->fk, fk);
+  UP(d->lqm, lqm);
+  UP(d->mass_d, d->mass);
+  UP(d->rho_cgs_d, d->rho);
+#undef UP
+  e = d->tally.alloc(ncell * 8);
+  if (e == cudaSuccess) e = d->visits.alloc(ncell * 8);
+  if (e == cudaSuccess) e = d->nabs.alloc(ncell * 8);
+  if (e == cudaSuccess) e = d->cnt.alloc(C_NCNT * 8);
+  if (e == cudaSuccess) e = d->queue.alloc(8);
+  if (e == cudaSuccess) e = d->T_mc.alloc(ncell * 8);
+  if (e == cudaSuccess) e = d->relerr.alloc(ncell * 8);
+  if (e == cudaSuccess) e = d->T_pda.alloc(ncell * 8);
+  if (e != cudaSuccess) return fail(cuda_fail(d, e, "cudaMalloc"));
+  st = zero_tallies(d);
+  if (st != MCRT_OK) return fail(st);
+  e = cudaStreamSynchronize(d->stream);
+  if (e != cudaSuccess) return fail(cuda_fail(d, e, "synchronize"));
+  *out = d;
+  return MCRT_OK;
+}
+
+mcrt_status mcrt_set_opacity(mcrt_disk* d, int nlam, const double* lam_e, const double* kabs, const double* ksca,
+                             const double* g) {
+  if (!d) return set_error(nullptr, MCRT_EINVAL, "disk is NULL");
+  if (nlam < 1 || nlam > 1024 || !lam_e || !kabs || !ksca) return set_error(d, MCRT_EINVAL, "bad opacity arguments");
+  for (int b = 0; b <= nlam; ++b)
+    if (!(std::isfinite(lam_e[b]) && lam_e[b] > 0) || (b && !(lam_e[b] > lam_e[b - 1])))
+      return set_error(d, MCRT_EINVAL, "wavelength edges must be positive and increasing");
+  for (int b = 0; b < nlam; ++b) {
+    if (!(std::isfinite(kabs[b]) && kabs[b] > 0)) return set_error(d, MCRT_EINVAL, "kappa_abs must be > 0");
+    if (!(std::isfinite(ksca[b]) && ksca[b] >= 0)) return set_error(d, MCRT_EINVAL, "kappa_sca must be >= 0");
+    if (g && !(std::isfinite(g[b]) && g[b] > -1 && g[b] < 1)) return set_error(d, MCRT_EINVAL, "g must be in (-1, 1)");
+  }
+  CK(cudaSetDevice(d->device), "cudaSetDevice");
+  d->nlam = nlam;
+  d->lam_e.assign(lam_e, lam_e + nlam + 1);
+  d->kabs.assign(kabs, kabs + nlam);
+  d->ksca.assign(ksca, ksca + nlam);
+  d->g.assign(nlam, 0.0);
+  if (g) d->g.assign(g, g + nlam);
+  d->gray = true;
+  for (int b = 1; b < nlam; ++b)
+    if (d->kabs[b] != d->kabs[0] || d->ksca[b] != d->ksca[0] || d->g[b] != d->g[0]) d->gray = false;
+
+  std::vector<double> chi(nlam), alb(nlam), chip(nlam), star(nlam), B(nlam), dB(nlam);
+  for (int b = 0; b < nlam; ++b) {
+    chi[b] = d->kabs[b] + d->ksca[b];
+    alb[b] = d->ksca[b] / chi[b];
+    chip[b] = d->kabs[b] + (1.0 - d->g[b]) * d->ksca[b];
+  }
+  planck_bins(d->lam_e.data(), nlam, d->Tstar, B.data(), nullptr);
+  double acc = 0.0;
+  for (int b = 0; b < nlam; ++b) {
+    acc += B[b];
+    star[b] = acc;
+  }
+  // temperature grid: T_0 = 0, T_k = Tmin (Tmax/Tmin)^((k-1)/(nT-2))
+  const int nT = d->nT;
+  const double dlnT = std::log(d->Tmax / d->Tmin) / (nT - 2);
+  std::vector<float> lQk(nT), cbw((size_t)nT * nlam, 0.f), cexit((size_t)nT * nlam), chiRk(nT), kbark(nT);
+  lQk[0] = -INFINITY;
+  for (int k = 0; k < nT; ++k) {
+    const double T = (k == 0) ? d->Tmin : d->Tmin * std::exp((k - 1) * dlnT);
+    planck_bins(d->lam_e.data(), nlam, T, B.data(), dB.data());
+    double q = 0, c1 = 0, c2 = 0, sdb = 0, sdbc = 0, skdb = 0;
+    for (int b = 0; b < nlam; ++b) {
+      q += d->kabs[b] * B[b];
+      c1 += d->kabs[b] * B[b];
+      c2 += dB[b] / chip[b];
+      sdb += dB[b];
+      sdbc += dB[b] / chip[b];
+      skdb += d->kabs[b] * dB[b];
+      if (k > 0) cbw[(size_t)k * nlam + b] = (float)c1;
+      cexit[(size_t)k * nlam + b] = (float)c2;
+    }
+    if (k > 0) lQk[k] = (float)std::log(4.0 * kPi * q);
+    chiRk[k] = (float)(sdb / sdbc);
+    kbark[k] = (float)(skdb / sdb);
+  }
+  cudaError_t e;
+#define UP(buf, vec)                                   \
+  do {                                                 \
+    e = upload(buf, vec);                              \
+    if (e != cudaSuccess) return cuda_fail(d, e, "upload"); \
+  } while (0)
+  UP(d->chi32, cast_vec<float>(chi));
+  UP(d->alb32, cast_vec<float>(alb));
+  UP(d->g32, cast_vec<float>(d->g));
+  UP(d->star32, cast_vec<float>(star));
+  UP(d->chi64, chi);
+  UP(d->alb64, alb);
+  UP(d->g64, d->g);
+  UP(d->star64, star);
+  UP(d->lQk, lQk);
+  UP(d->cbw, cbw);
+  UP(d->cexit, cexit);
+  UP(d->chiRk, chiRk);
+  UP(d->kbark, kbark);
+  UP(d->lam_e_d, d->lam_e);
+  UP(d->kabs_d, d->kabs);
+  UP(d->chip_d, chip);
+#undef UP
+  d->chiR0 = (float)chip[0];
+  d->kbar0 = (float)d->kabs[0];
+  e = d->sed.alloc((size_t)nlam * kNInc * 8);
+  if (e != cudaSuccess) return cuda_fail(d, e, "cudaMalloc");
+  d->has_opacity = true;
+  mcrt_status st = zero_tallies(d);
+  if (st != MCRT_OK) return st;
+  CK(cudaStreamSynchronize(d->stream), "synchronize");
+  return MCRT_OK;
+}
+
+mcrt_status mcrt_reset(mcrt_disk* d) {
+  if (!d) return set_error(nullptr, MCRT_EINVAL, "disk is NULL");
+  CK(cudaSetDevice(d->device), "cudaSetDevice");
+  mcrt_status s = zero_tallies(d);
+  if (s != MCRT_OK) return s;
+  CK(cudaStreamSynchronize(d->stream), "synchronize");
+  return MCRT_OK;
+}
+
+mcrt_status mcrt_launch_count(const mcrt_disk* d, uint64_t* n) {
+  if (!d || !n) return set_error(nullptr, MCRT_EINVAL, "bad arguments");
+  *n = d->launches;
+  return MCRT_OK;
+}
+
+mcrt_status mcrt_disk_info(const mcrt_disk* d, int* nr, int* ntheta, int* nlam) {
+  if (!d) return set_error(nullptr, MCRT_EINVAL, "disk is NULL");
+  if (nr) *nr = d->nr;
+  if (ntheta) *ntheta = d->nt;
+  if (nlam) *nlam = d->nlam;
+  return MCRT_OK;
+}
+
+}  // extern "C"
+
+// ------------------------------------------------------------------------------------------------
+// transport runs
+// ------------------------------------------------------------------------------------------------
+static mcrt_status check_opts(mcrt_disk* d, const mcrt_run_opts* o) {
+  if (!o) return set_error(d, MCRT_EINVAL, "opts is NULL");
+  if (o->precision != 32 && o->precision != 64) return set_error(d, MCRT_EINVAL, "precision must be 32 or 64");
+  if (o->mrw && !(o->gamma > 0)) return set_error(d, MCRT_EINVAL, "gamma must be > 0");
+  if (o->mrw && o->mrw_min_interactions < 0) return set_error(d, MCRT_EINVAL, "mrw_min_interactions < 0");
+  if (o->max_events_per_packet == 0) return set_error(d, MCRT_EINVAL, "max_events_per_packet must be > 0");
+  if (o->block_size && (o->block_size % 32 || o->block_size > 512))
+    return set_error(d, MCRT_EINVAL, "block_size must be a multiple of 32 up to 512");
+  if (o->refill_interval < 0) return set_error(d, MCRT_EINVAL, "refill_interval < 0");
+  return MCRT_OK;
+}
+
+template <class R>
+static void fill_params(KParams<R>& P, const mcrt_run_opts* o, uint64_t seed, const float* tab) {
+  P.mrw = o->mrw ? 1 : 0;
+  P.nmin = o->mrw_min_interactions;
+  P.exit_dir = o->mrw_exit_dir;
+  P.refill = o->refill_interval > 0 ? o->refill_interval : 1;
+  P.gamma = (R)o->gamma;
+  P.seed = seed;
+  P.max_events = o->max_events_per_packet;
+  P.max_steps = 4ull * o->max_events_per_packet + 10000000ull;
+  P.mrw_tab = tab;
+  P.mrw_t0 = kMrwT0;
+  P.mrw_dt = kMrwDT;
+  P.trace_n = 0;
+  P.trace_max = 0;
+  P.tr_type = P.tr_cell = P.tr_lam = P.tr_n = nullptr;
+  P.tr_pos = nullptr;
+  P.models = nullptr;
+  P.nmodels = 1;
+}
+
+static void stats_from(const unsigned long long* c, mcrt_run_stats* s, double secs) {
+  s->packets = c[C_PACKETS];
+  s->events = c[C_EVENTS];
+  s->absorptions = c[C_ABS];
+  s->scatterings = c[C_SCA];
+  s->crossings = c[C_CROSS];
+  s->mrw_jumps = c[C_MRW];
+  s->capped = c[C_CAPPED];
+  s->escaped = c[C_ESCAPED];
+  s->deposit_sum = c[C_DEPSUM];
+  s->error_flags = (uint32_t)c[C_ERR];
+  s->seconds = secs;
+}
+
+// events = scatterings + absorptions + MRW jumps (the kernel counts the three separately)
+static void fix_events(unsigned long long* c) { c[C_EVENTS] = c[C_ABS] + c[C_SCA] + c[C_MRW]; }
+
+static mcrt_status run_impl(mcrt_disk* d, uint64_t n_packets, uint64_t seed, uint64_t first_id,
+                            const mcrt_run_opts* o, mcrt_run_stats* stats, int trace_max, int32_t* tr_type,
+                            int32_t* tr_cell, int32_t* tr_lam, double* tr_pos, int32_t* tr_n) {
+  if (!d) return set_error(nullptr, MCRT_EINVAL, "disk is NULL");
+  if (!d->has_opacity) return set_error(d, MCRT_ESTATE, "mcrt_set_opacity must come first");
+  mcrt_status s = check_opts(d, o);
+  if (s != MCRT_OK) return s;
+  CK(cudaSetDevice(d->device), "cudaSetDevice");
+  cudaError_t e;
+  const float* tab = mrw_table(d->device, &e);
+  if (!tab) return cuda_fail(d, e, "MRW table");
+  d->n_total = (double)(o->n_total_packets ? o->n_total_packets : n_packets);
+  const bool trace = trace_max > 0;
+  const bool f64 = trace || o->precision == 64;
+  CK(cudaMemsetAsync(d->cnt.p, 0, C_NCNT * 8, d->stream), "memset");
+  CK(cudaMemsetAsync(d->queue.p, 0, 8, d->stream), "memset");
+  DBuf ttype, tcell, tlam, tpos, tn;
+  if (trace) {
+    const size_t m = (size_t)n_packets * trace_max;
+    e = ttype.alloc(m * 4);
+    if (e == cudaSuccess) e = tcell.alloc(m * 4);
+    if (e == cudaSuccess) e = tlam.alloc(m * 4);
+    if (e == cudaSuccess) e = tpos.alloc(m * 24);
+    if (e == cudaSuccess) e = tn.alloc(n_packets * 4);
+    if (e != cudaSuccess) return cuda_fail(d, e, "trace buffers");
+    CK(cudaMemsetAsync(tn.p, 0, n_packets * 4, d->stream), "memset");
+  }
+  int dev_sms = 0;
+  CK(cudaDeviceGetAttribute(&dev_sms, cudaDevAttrMultiProcessorCount, d->device), "attribute");
+  const int block = o->block_size ? o->block_size : (f64 ? 128 : 256);
+  cudaEvent_t ev0, ev1;
+  CK(cudaEventCreate(&ev0), "event");
+  CK(cudaEventCreate(&ev1), "event");
+  CK(cudaEventRecord(ev0, d->stream), "event");
+  if (n_packets > 0) {
+    if (f64) {
+      KParams<double> P;
+      std::memset(&P, 0, sizeof(P));
+      fill_params(P, o, seed, tab);
+      P.m0 = d->model64();
+      P.m0.first_id = first_id;
+      P.m0.n_packets = n_packets;
+      P.m0.q_begin = 0;
+      P.m0.model_id = 0;
+      P.total = n_packets;
+      P.queue = d->queue.as<unsigned long long>();
+      P.want_lam = (!d->gray || o->want_sed) ? 1 : 0;
+      if (trace) {
+        P.trace_n = (int)n_packets;
+        P.trace_max = trace_max;
+        P.tr_type = ttype.as<int32_t>();
+        P.tr_cell = tcell.as<int32_t>();
+        P.tr_lam = tlam.as<int32_t>();
+        P.tr_pos = tpos.as<double>();
+        P.tr_n = tn.as<int32_t>();
+        P.l_unit = d->l_unit;
+      }
+      const int bps = transport_blocks_per_sm<double>(trace, false, block);
+      const long long want = (long long)((n_packets + block - 1) / block);
+      const int grid = (int)std::max(1ll, std::min<long long>(want, (long long)dev_sms * std::max(1, bps)));
+      e = launch_transport<double>(P, trace, false, grid, block, d->stream);
+      d->launches++;
+    } else {
+      KParams<float> P;
+      std::memset(&P, 0, sizeof(P));
+      fill_params(P, o, seed, tab);
+      P.m0 = d->model32();
+      P.m0.first_id = first_id;
+      P.m0.n_packets = n_packets;
+      P.m0.q_begin = 0;
+      P.m0.model_id = 0;
+      P.total = n_packets;
+      P.queue = d->queue.as<unsigned long long>();
+      P.want_lam = (!d->gray || o->want_sed) ? 1 : 0;
+      const int bps = transport_blocks_per_sm<float>(false, false, block);
+      const long long want = (long long)((n_packets + block - 1) / block);
+      const int grid = (int)std::max(1ll, std::min<long long>(want, (long long)dev_sms * std::max(1, bps)));
+      e = launch_transport<float>(P, false, false, grid, block, d->stream);
+      d->launches++;
+    }
+    if (e != cudaSuccess) {
+      cudaEventDestroy(ev0);
+      cudaEventDestroy(ev1);
+      return cuda_fail(d, e, "transport launch");
+    }
+  }
+  CK(cudaEventRecord(ev1, d->stream), "event");
+  unsigned long long c[C_NCNT];
+  CK(cudaMemcpyAsync(c, d->cnt.p, sizeof(c), cudaMemcpyDeviceToHost, d->stream), "copy counters");
+  if (trace) {
+    const size_t m = (size_t)n_packets * trace_max;
+    if (tr_type) CK(cudaMemcpyAsync(tr_type, ttype.p, m * 4, cudaMemcpyDeviceToHost, d->stream), "copy");
+    if (tr_cell) CK(cudaMemcpyAsync(tr_cell, tcell.p, m * 4, cudaMemcpyDeviceToHost, d->stream), "copy");
+    if (tr_lam) CK(cudaMemcpyAsync(tr_lam, tlam.p, m * 4, cudaMemcpyDeviceToHost, d->stream), "copy");
+    if (tr_pos) CK(cudaMemcpyAsync(tr_pos, tpos.p, m * 24, cudaMemcpyDeviceToHost, d->stream), "copy");
+    if (tr_n) CK(cudaMemcpyAsync(tr_n, tn.p, n_packets * 4, cudaMemcpyDeviceToHost, d->stream), "copy");
+  }
+  e = cudaStreamSynchronize(d->stream);
+  float ms = 0.f;
+  if (e == cudaSuccess) cudaEventElapsedTime(&ms, ev0, ev1);
+  cudaEventDestroy(ev0);
+  cudaEventDestroy(ev1);
+  if (e != cudaSuccess) return cuda_fail(d, e, "transport kernel");
+  fix_events(c);
+  d->packets_done += n_packets;
+  d->have_T = false;
+  d->have_pda = false;
+  if (stats) stats_from(c, stats, ms * 1e-3);
+  if (c[C_ERR] & kErrOverflow) return set_error(d, MCRT_EOVERFLOW, "fixed-point tally overflow");
+  if (c[C_ERR] & kErrStepGuard) return set_error(d, MCRT_ETIMEOUT, "packet step guard reached");
+  return MCRT_OK;
+}
+
+extern "C" {
+
+mcrt_status mcrt_run_photons(mcrt_disk* d, uint64_t n_packets, uint64_t seed, uint64_t first_packet_id,
+                             const mcrt_run_opts* opts, mcrt_run_stats* stats) {
+  return run_impl(d, n_packets, seed, first_packet_id, opts, stats, 0, nullptr, nullptr, nullptr, nullptr, nullptr);
+}
+
+mcrt_status mcrt_trace_packets(mcrt_disk* d, uint64_t n_packets, uint64_t seed, uint64_t first_packet_id,
+                               const mcrt_run_opts* opts, int max_events, int32_t* type, int32_t* cell, int32_t* lam,
+                               double* pos, int32_t* n_events) {
+  if (max_events <= 0) return set_error(d, MCRT_EINVAL, "max_events must be > 0");
+  if (n_packets > (1ull << 24) || (unsigned long long)n_packets * (unsigned long long)max_events > (1ull << 31))
+    return set_error(d, MCRT_EINVAL, "trace too large");
+  return run_impl(d, n_packets, seed, first_packet_id, opts, nullptr, max_events, type, cell, lam, pos, n_events);
+}
+
+mcrt_status mcrt_run_batch(mcrt_disk* const* disks, int n, const uint64_t* n_packets, uint64_t seed,
+                           const mcrt_run_opts* o, mcrt_run_stats* stats) {
+  if (!disks || n <= 0 || !n_packets) return set_error(nullptr, MCRT_EINVAL, "bad batch arguments");
+  mcrt_disk* d0 = disks[0];
+  for (int i = 0; i < n; ++i) {
+    if (!disks[i]) return set_error(nullptr, MCRT_EINVAL, "NULL disk in batch");
+    if (!disks[i]->has_opacity) return set_error(disks[i], MCRT_ESTATE, "mcrt_set_opacity must come first");
+    if (disks[i]->device != d0->device) return set_error(disks[i], MCRT_EINVAL, "batch disks on different devices");
+  }
+  mcrt_disk* d = d0;
+  mcrt_status s = check_opts(d, o);
+  if (s != MCRT_OK) return s;
+  if (o->precision != 32) return set_error(d, MCRT_EINVAL, "batches run the FP32 path");
+  CK(cudaSetDevice(d->device), "cudaSetDevice");
+  cudaError_t e;
+  const float* tab = mrw_table(d->device, &e);
+  if (!tab) return cuda_fail(d, e, "MRW table");
+  std::vector<DevModel<float>> ms(n);
+  unsigned long long q = 0;
+  for (int i = 0; i < n; ++i) {
+    disks[i]->n_total = (double)n_packets[i];
+    ms[i] = disks[i]->model32();
+    ms[i].first_id = 0;
+    ms[i].n_packets = n_packets[i];
+    ms[i].q_begin = q;
+    ms[i].model_id = (uint32_t)i;
+    q += n_packets[i];
+    if (disks[i] != d) {
+      // other disks' counters are zeroed on the shared stream below
+    }
+  }
+  DBuf dm;
+  e = dm.alloc(sizeof(DevModel<float>) * n);
+  if (e != cudaSuccess) return cuda_fail(d, e, "cudaMalloc");
+  CK(cudaMemcpyAsync(dm.p, ms.data(), sizeof(DevModel<float>) * n, cudaMemcpyHostToDevice, d->stream), "copy");
+  for (int i = 0; i < n; ++i) CK(cudaMemsetAsync(disks[i]->cnt.p, 0, C_NCNT * 8, d->stream), "memset");
+  CK(cudaMemsetAsync(d->queue.p, 0, 8, d->stream), "memset");
+  KParams<float> P;
+  std::memset(&P, 0, sizeof(P));
+  fill_params(P, o, seed, tab);
+  P.m0 = ms[0];
+  P.models = dm.as<DevModel<float>>();
+  P.nmodels = n;
+  P.total = q;
+  P.queue = d->queue.as<unsigned long long>();
+  bool any_nongray = false;
+  for (int i = 0; i < n; ++i) any_nongray |= !disks[i]->gray;
+  P.want_lam = (any_nongray || o->want_sed) ? 1 : 0;
+  int dev_sms = 0;
+  CK(cudaDeviceGetAttribute(&dev_sms, cudaDevAttrMultiProcessorCount, d->device), "attribute");
+  const int block = o->block_size ? o->block_size : 256;
+  const int bps = transport_blocks_per_sm<float>(false, true, block);
+  const int grid = dev_sms * std::max(1, bps);
+  cudaEvent_t ev0, ev1;
+  CK(cudaEventCreate(&ev0), "event");
+  CK(cudaEventCreate(&ev1), "event");
+  CK(cudaEventRecord(ev0, d->stream), "event");
+  if (q > 0) {
+    e = launch_transport<float>(P, false, true, grid, block, d->stream);
+    d->launches++;
+    if (e != cudaSuccess) return cuda_fail(d, e, "transport launch");
+  }
+  CK(cudaEventRecord(ev1, d->stream), "event");
+  std::vector<unsigned long long> c((size_t)n * C_NCNT);
+  for (int i = 0; i < n; ++i)
+    CK(cudaMemcpyAsync(&c[(size_t)i * C_NCNT], disks[i]->cnt.p, C_NCNT * 8, cudaMemcpyDeviceToHost, d->stream),
+       "copy");
+  e = cudaStreamSynchronize(d->stream);
+  float ms_ = 0.f;
+  if (e == cudaSuccess) cudaEventElapsedTime(&ms_, ev0, ev1);
+  cudaEventDestroy(ev0);
+  cudaEventDestroy(ev1);
+  if (e != cudaSuccess) return cuda_fail(d, e, "transport kernel");
+  mcrt_status ret = MCRT_OK;
+  for (int i = 0; i < n; ++i) {
+    unsigned long long* ci = &c[(size_t)i * C_NCNT];
+    fix_events(ci);
+    disks[i]->packets_done += n_packets[i];
+    disks[i]->have_T = false;
+    disks[i]->have_pda = false;
+    if (stats) stats_from(ci, &stats[i], ms_ * 1e-3);
+    if (ci[C_ERR] & kErrOverflow) ret = set_error(disks[i], MCRT_EOVERFLOW, "fixed-point tally overflow");
+  }
+  return ret;
+}
+
+mcrt_status mcrt_temperatures(mcrt_disk* d, int which, double* T, double* relerr, uint64_t* visits) {
+  if (!d) return set_error(nullptr, MCRT_EINVAL, "disk is NULL");
+  if (!T) return set_error(d, MCRT_EINVAL, "T is NULL");
+  if (!d->has_opacity) return set_error(d, MCRT_ESTATE, "mcrt_set_opacity must come first");
+  if (which != MCRT_T_MC && which != MCRT_T_PDA) return set_error(d, MCRT_EINVAL, "which");
+  if (which == MCRT_T_PDA && !d->have_pda) return set_error(d, MCRT_ESTATE, "no PDA solution");
+  CK(cudaSetDevice(d->device), "cudaSetDevice");
+  if (!d->have_T) {
+    mcrt_status s = compute_temperatures(d);
+    if (s != MCRT_OK) return s;
+  }
+  const size_t n = (size_t)d->nr * d->nt;
+  CK(cudaMemcpyAsync(T, which == MCRT_T_PDA ? d->T_pda.p : d->T_mc.p, n * 8, cudaMemcpyDeviceToHost, d->stream),
+     "copy");
+  if (relerr) CK(cudaMemcpyAsync(relerr, d->relerr.p, n * 8, cudaMemcpyDeviceToHost, d->stream), "copy");
+  if (visits) CK(cudaMemcpyAsync(visits, d->visits.p, n * 8, cudaMemcpyDeviceToHost, d->stream), "copy");
+  CK(cudaStreamSynchronize(d->stream), "synchronize");
+  return MCRT_OK;
+}
+
+mcrt_status mcrt_temperatures_dev(mcrt_disk* d, int which, double* T, double* relerr) {
+  if (!d) return set_error(nullptr, MCRT_EINVAL, "disk is NULL");
+  if (!T) return set_error(d, MCRT_EINVAL, "T is NULL");
+  if (!d->has_opacity) return set_error(d, MCRT_ESTATE, "mcrt_set_opacity must come first");
+  if (which == MCRT_T_PDA && !d->have_pda) return set_error(d, MCRT_ESTATE, "no PDA solution");
+  CK(cudaSetDevice(d->device), "cudaSetDevice");
+  if (!d->have_T) {
+    mcrt_status s = compute_temperatures(d);
+    if (s != MCRT_OK) return s;
+  }
+  const size_t n = (size_t)d->nr * d->nt;
+  CK(cudaMemcpyAsync(T, which == MCRT_T_PDA ? d->T_pda.p : d->T_mc.p, n * 8, cudaMemcpyDeviceToDevice, d->stream),
+     "copy");
+  if (relerr) CK(cudaMemcpyAsync(relerr, d->relerr.p, n * 8, cudaMemcpyDeviceToDevice, d->stream), "copy");
+  return MCRT_OK;
+}
+
+mcrt_status mcrt_get_tallies(mcrt_disk* d, uint64_t* tally, uint64_t* visits, uint64_t* nabs) {
+  if (!d) return set_error(nullptr, MCRT_EINVAL, "disk is NULL");
+  CK(cudaSetDevice(d->device), "cudaSetDevice");
+  const size_t n = (size_t)d->nr * d->nt * 8;
+  if (tally) CK(cudaMemcpyAsync(tally, d->tally.p, n, cudaMemcpyDeviceToHost, d->stream), "copy");
+  if (visits) CK(cudaMemcpyAsync(visits, d->visits.p, n, cudaMemcpyDeviceToHost, d->stream), "copy");
+  if (nabs) CK(cudaMemcpyAsync(nabs, d->nabs.p, n, cudaMemcpyDeviceToHost, d->stream), "copy");
+  CK(cudaStreamSynchronize(d->stream), "synchronize");
+  return MCRT_OK;
+}
+
+mcrt_status mcrt_sed(mcrt_disk* d, int n_incl, double* L) {
+  if (!d) return set_error(nullptr, MCRT_EINVAL, "disk is NULL");
+  if (!L || n_incl <= 0 || kNInc % n_incl) return set_error(d, MCRT_EINVAL, "n_incl must divide 10");
+  if (!d->has_opacity) return set_error(d, MCRT_ESTATE, "mcrt_set_opacity must come first");
+  CK(cudaSetDevice(d->device), "cudaSetDevice");
+  std::vector<unsigned long long> c((size_t)d->nlam * kNInc);
+  CK(cudaMemcpyAsync(c.data(), d->sed.p, c.size() * 8, cudaMemcpyDeviceToHost, d->stream), "copy");
+  CK(cudaStreamSynchronize(d->stream), "synchronize");
+  const double e = d->Lstar / (d->n_total > 0 ? d->n_total : 1.0);
+  const int grp = kNInc / n_incl;
+  for (int b = 0; b < d->nlam; ++b)
+    for (int i = 0; i < n_incl; ++i) {
+      unsigned long long s = 0;
+      for (int j = 0; j < grp; ++j) s += c[(size_t)b * kNInc + i * grp + j];
+      L[(size_t)b * n_incl + i] = (double)s * e;
+    }
+  return MCRT_OK;
+}
+
+// checkpoint layout: 8 x uint64 header (magic, version, nr, nt, nlam, packets_done, n_total bits, 0),
+// then tally, visits, nabs (nr*nt each) and sed (nlam*10), all uint64.
+mcrt_status mcrt_checkpoint(mcrt_disk* d, void* buf, size_t* len) {
+  if (!d || !len) return set_error(d, MCRT_EINVAL, "bad arguments");
+  const size_t n = (size_t)d->nr * d->nt;
+  const size_t nsed = (size_t)d->nlam * kNInc;
+  const size_t need = 8 * (8 + 3 * n + nsed);
+  if (!buf) {
+    *len = need;
+    return MCRT_OK;
+  }
+  if (*len < need) return set_error(d, MCRT_EINVAL, "checkpoint buffer too small");
+  CK(cudaSetDevice(d->device), "cudaSetDevice");
+  uint64_t* h = (uint64_t*)buf;
+  uint64_t ntb;
+  std::memcpy(&ntb, &d->n_total, 8);
+  const uint64_t hdr[8] = {0x4D43525443484B31ull, 1, (uint64_t)d->nr, (uint64_t)d->nt, (uint64_t)d->nlam,
+                           d->packets_done, ntb, 0};
+  std::memcpy(h, hdr, sizeof(hdr));
+  CK(cudaMemcpyAsync(h + 8, d->tally.p, n * 8, cudaMemcpyDeviceToHost, d->stream), "copy");
+  CK(cudaMemcpyAsync(h + 8 + n, d->visits.p, n * 8, cudaMemcpyDeviceToHost, d->stream), "copy");
+  CK(cudaMemcpyAsync(h + 8 + 2 * n, d->nabs.p, n * 8, cudaMemcpyDeviceToHost, d->stream), "copy");
+  if (nsed) CK(cudaMemcpyAsync(h + 8 + 3 * n, d->sed.p, nsed * 8, cudaMemcpyDeviceToHost, d->stream), "copy");
+  CK(cudaStreamSynchronize(d->stream), "synchronize");
+  *len = need;
+  return MCRT_OK;
+}
+
+mcrt_status mcrt_restore(mcrt_disk* d, const void* buf, size_t len) {
+  if (!d || !buf) return set_error(d, MCRT_EINVAL, "bad arguments");
+  const size_t n = (size_t)d->nr * d->nt;
+  const size_t nsed = (size_t)d->nlam * kNInc;
+  if (len < 64) return set_error(d, MCRT_EINVAL, "checkpoint too short");
+  const uint64_t* h = (const uint64_t*)buf;
+  if (h[0] != 0x4D43525443484B31ull || h[1] != 1 || h[2] != (uint64_t)d->nr || h[3] != (uint64_t)d->nt ||
+      h[4] != (uint64_t)d->nlam || len < 8 * (8 + 3 * n + nsed))
+    return set_error(d, MCRT_EINVAL, "checkpoint does not match this disk");
+  if (!d->has_opacity) return set_error(d, MCRT_ESTATE, "mcrt_set_opacity must come first");
+  CK(cudaSetDevice(d->device), "cudaSetDevice");
+  CK(cudaMemcpyAsync(d->tally.p, h + 8, n * 8, cudaMemcpyHostToDevice, d->stream), "copy");
+  CK(cudaMemcpyAsync(d->visits.p, h + 8 + n, n * 8, cudaMemcpyHostToDevice, d->stream), "copy");
+  CK(cudaMemcpyAsync(d->nabs.p, h + 8 + 2 * n, n * 8, cudaMemcpyHostToDevice, d->stream), "copy");
+  if (nsed) CK(cudaMemcpyAsync(d->sed.p, h + 8 + 3 * n, nsed * 8, cudaMemcpyHostToDevice, d->stream), "copy");
+  CK(cudaStreamSynchronize(d->stream), "synchronize");
+  d->packets_done = h[5];
+  std::memcpy(&d->n_total, &h[6], 8);
+  d->have_T = false;
+  d->have_pda = false;
+  return MCRT_OK;
+}
+
+mcrt_status mcrt_debug_uniforms(int device, uint64_t seed, uint32_t model, uint64_t packet, int n, double* out) {
+  if (n <= 0 || n > (1 << 20) || !out) return set_error(nullptr, MCRT_EINVAL, "bad arguments");
+  mcrt_disk* d = nullptr;
+  CK(cudaSetDevice(device), "cudaSetDevice");
+  double* p = nullptr;
+  CK(cudaMalloc(&p, sizeof(double) * n), "cudaMalloc");
+  k_uniforms<<<1, 32>>>(seed, model, packet, n, p);
+  cudaError_t e = cudaMemcpy(out, p, sizeof(double) * n, cudaMemcpyDeviceToHost);
+  cudaFree(p);
+  if (e != cudaSuccess) return cuda_fail(d, e, "debug uniforms");
+  return MCRT_OK;
+}
+
+mcrt_status mcrt_debug_mrw_x(int device, int n, const double* P0, double* out) {
+  if (n <= 0 || n > (1 << 24) || !P0 || !out) return set_error(nullptr, MCRT_EINVAL, "bad arguments");
+  for (int i = 0; i < n; ++i)
+    if (!(P0[i] > 0 && P0[i] < 1)) return set_error(nullptr, MCRT_EINVAL, "P0 must be in (0, 1)");
+  mcrt_disk* d = nullptr;
+  CK(cudaSetDevice(device), "cudaSetDevice");
+  cudaError_t e;
+  const float* tab = mrw_table(device, &e);
+  if (!tab) return cuda_fail(d, e, "MRW table");
+  double *a = nullptr, *b = nullptr;
+  CK(cudaMalloc(&a, sizeof(double) * n), "cudaMalloc");
+  e = cudaMalloc(&b, sizeof(double) * n);
+  if (e != cudaSuccess) {
+    cudaFree(a);
+    return cuda_fail(d, e, "cudaMalloc");
+  }
+  e = cudaMemcpy(a, P0, sizeof(double) * n, cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) {
+    k_mrw_x<<<(n + 255) / 256, 256>>>(n, a, b, tab, kMrwT0, kMrwDT);
+    e = cudaMemcpy(out, b, sizeof(double) * n, cudaMemcpyDeviceToHost);
+  }
+  cudaFree(a);
+  cudaFree(b);
+  if (e != cudaSuccess) return cuda_fail(d, e, "debug mrw");
+  return MCRT_OK;
+}
+
+const char* mcrt_last_error(const mcrt_disk* d) { return d ? d->err.c_str() : g_err.c_str(); }
+
+void mcrt_disk_destroy(mcrt_disk* d) {
+  if (!d) return;
+  cudaSetDevice(d->device);
+  if (d->stream) cudaStreamSynchronize(d->stream);
+  if (d->pda) pda_free(d->pda);
+  d->pda = nullptr;
+  cudaStream_t st = d->own_stream ? d->stream : nullptr;
+  delete d;  // frees the device buffers
+  if (st) cudaStreamDestroy(st);
+}
+
+}  // extern "C"

@@ -1,0 +1,662 @@
+// pda.cu -- partial diffusion approximation (Sect. 2.2.1, Eq. 4) and its adjoint.
+//
+// After the Monte Carlo run the cells that fewer than `min_visits` packets entered, or whose
+// statistical temperature error exceeds `max_rel_err` (Sect. 3.1), form the PDA region. There
+// div(D grad u) = 0 with u = T^4 and D = 1/(3 rho kappa_R) (Eq. 2) frozen at the Monte Carlo
+// temperature, so the system is linear; all other dusty cells give Dirichlet values u = T_MC^4.
+//
+// Discretisation: finite volumes on the (r, theta) cells. The conductance of a face is the series
+// resistance of the two half cells, each exact for constant D: radial half cell [a, b] of solid
+// angle Omega: (1/a - 1/b)/(D Omega); polar half cell [t1, t2] of radial width dr:
+// (ln tan(t2/2) - ln tan(t1/2))/(2 pi D dr). Grid edges and dust-free cells carry no flux.
+//
+// Solve: FP64 iterative refinement. Each outer step forms r = b - A u in FP64 and solves the
+// Jacobi-scaled system (S A S) y = S r / |S r| (unit diagonal) with a matrix-free FP32 conjugate
+// gradient; u += |S r| S y. Two kernels per CG iteration: (A) p = r + beta p_old and Ap for the own
+// cell and its four neighbours (p recomputed for neighbours from r and p_old, so no extra sweep),
+// with a block-reduced p.Ap; (B) y, r updates with a block-reduced r.r. The scalars live in a device
+// array indexed by the iteration, so the host only reads back once per chunk of iterations.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <vector>
+
+#include "internal.h"
+#include "planck.cuh"
+
+namespace mcrt {
+
+struct PdaState {
+  int nr = 0, nt = 0, n = 0;
+  DBuf mask;                          // int8 per cell: 0 no dust, 1 Dirichlet, 2 PDA unknown
+  DBuf hr_in, hr_out, ht_lo, ht_hi;   // geometric half-cell resistances (FP64)
+  DBuf ell;                           // smallest cell extent min(dr, r_c dtheta) (cm)
+  DBuf kR, D, Cr, Ct;                 // FP64: Rosseland opacity, D, radial / polar face conductances
+  DBuf dis;                           // FP64 1/sqrt(diag) on PDA cells
+  DBuf ar, at;                        // FP32 scaled couplings between PDA cells
+  DBuf u;                             // FP64 T^4 on every cell
+  DBuf lam;                           // FP64 adjoint solution
+  DBuf b64;                           // FP64 right-hand side (adjoint)
+  DBuf rs;                            // FP64 scaled residual S r
+  DBuf y, r, p0, p1, Ap;              // FP32 CG vectors
+  DBuf sc;                            // FP64 CG scalars per iteration
+  DBuf red;                           // FP64 reduction slots
+  DBuf w, gl, gk;                     // adjoint weights / gradient outputs (device staging)
+  int n_pda = 0;
+  int max_inner_alloc = 0;
+};
+
+void pda_free(PdaState* p) { delete p; }
+
+__device__ __forceinline__ float block_sum_f(float v, float* sh) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+  if (l == 0) sh[w] = v;
+  __syncthreads();
+  float s = 0.f;
+  if (w == 0) {
+    s = (l < (int)(blockDim.x >> 5)) ? sh[l] : 0.f;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+  }
+  return s;  // valid in thread 0
+}
+
+__device__ __forceinline__ double block_sum_d(double v, double* sh) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+  if (l == 0) sh[w] = v;
+  __syncthreads();
+  double s = 0.0;
+  if (w == 0) {
+    s = (l < (int)(blockDim.x >> 5)) ? sh[l] : 0.0;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+  }
+  return s;
+}
+
+// ---------------------------------------------------------------------------------------------- setup
+// PDA cells: dust, optically thick (rho chi'_max ell_c >= min_tau, ell_c = min(dr, r_c dtheta)), and
+// fewer than min_visits entries or a statistical error above max_rel
+__global__ void k_mask(int n, const double* rho, const double* ell, double chi_max, double min_tau,
+                       const unsigned long long* visits, const double* relerr, int min_visits, double max_rel,
+                       signed char* mask, double* red) {
+  const int c = blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= n) return;
+  signed char m = 0;
+  if (rho[c] > 0) {
+    const bool thick = rho[c] * chi_max * ell[c] >= min_tau;
+    m = (thick && (visits[c] < (unsigned long long)min_visits || relerr[c] > max_rel)) ? 2 : 1;
+  }
+  mask[c] = m;
+  if (m == 2) atomicAdd(red + 0, 1.0);
+}
+
+// mean MC temperature of the Dirichlet cells that border the PDA region
+__global__ void k_bnd_mean(int nr, int nt, const signed char* mask, const double* T, double* red) {
+  const int c = blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= nr * nt || mask[c] != 1) return;
+  const int i = c / nt, j = c - i * nt;
+  const bool nb = (i > 0 && mask[c - nt] == 2) || (i + 1 < nr && mask[c + nt] == 2) || (j > 0 && mask[c - 1] == 2) ||
+                  (j + 1 < nt && mask[c + 1] == 2);
+  if (nb) {
+    atomicAdd(red + 1, T[c]);
+    atomicAdd(red + 2, 1.0);
+  }
+}
+
+// Rosseland mean of chi' = kappa + (1-g) sigma at T (Eq. 3 with Eq. 16), exact bin integrals
+__device__ double rosseland(const double* lam_e, const double* chip, int nlam, double T) {
+  double g3p = 0.0, g4p = 0.0, s1 = 0.0, s2 = 0.0;
+  for (int b = 0; b < nlam; ++b) {
+    double g3, g4;
+    if (b + 1 == nlam) tails(0.0, g3, g4);
+    else tails(kH * kC / (lam_e[b + 1] * 1e-4 * kKB * T), g3, g4);
+    const double db = g4 - g4p;
+    s1 += db;
+    s2 += db / chip[b];
+    g3p = g3;
+    g4p = g4;
+  }
+  return s1 / s2;
+}
+
+__global__ void k_kappaR(int n, const double* rho, const unsigned long long* tally, const double* T, const double* red,
+                         int gray, double chip0, int nlam, const double* lam_e, const double* chip, const double* over,
+                         double* kR) {
+  const int c = blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= n) return;
+  if (!(rho[c] > 0)) {
+    kR[c] = 1.0;
+    return;
+  }
+  if (over) {
+    kR[c] = over[c];
+    return;
+  }
+  if (gray) {
+    kR[c] = chip0;
+    return;
+  }
+  double Tc = tally[c] ? T[c] : (red[2] > 0 ? red[1] / red[2] : 1.0);
+  Tc = fmax(Tc, 1.0);
+  kR[c] = rosseland(lam_e, chip, nlam, Tc);
+}
+
+__global__ void k_cond(int nr, int nt, const double* rho, const double* kR, const double* hr_in, const double* hr_out,
+                       const double* ht_lo, const double* ht_hi, double* D, double* Cr, double* Ct) {
+  const int c = blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= nr * nt) return;
+  const int i = c / nt, j = c - i * nt;
+  auto Dof = [&](int k) { return rho[k] > 0 ? 1.0 / (3.0 * rho[k] * kR[k]) : 0.0; };
+  const double Dc = Dof(c);
+  D[c] = Dc;
+  double cr = 0.0, ct = 0.0;
+  if (i + 1 < nr && rho[c] > 0 && rho[c + nt] > 0) cr = 1.0 / (hr_out[c] / Dc + hr_in[c + nt] / Dof(c + nt));
+  if (j + 1 < nt && rho[c] > 0 && rho[c + 1] > 0) ct = 1.0 / (ht_hi[c] / Dc + ht_lo[c + 1] / Dof(c + 1));
+  Cr[c] = cr;
+  Ct[c] = ct;
+}
+
+// diag on PDA cells (sum of conductances to any dusty neighbour); u initialised: T_MC^4 on
+// Dirichlet cells, 0 elsewhere
+__global__ void k_diag(int nr, int nt, const signed char* mask, const double* Cr, const double* Ct, const double* T,
+                       double* dis, double* u, double* red) {
+  const int c = blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= nr * nt) return;
+  const int i = c / nt, j = c - i * nt;
+  const signed char m = mask[c];
+  if (m == 1) {
+    const double t2 = T[c] * T[c];
+    u[c] = t2 * t2;
+  } else {
+    u[c] = 0.0;
+  }
+  if (m != 2) {
+    dis[c] = 0.0;
+    return;
+  }
+  double d = 0.0;
+  if (i > 0 && mask[c - nt]) d += Cr[c - nt];
+  if (i + 1 < nr && mask[c + nt]) d += Cr[c];
+  if (j > 0 && mask[c - 1]) d += Ct[c - 1];
+  if (j + 1 < nt && mask[c + 1]) d += Ct[c];
+  if (d > 0) {
+    dis[c] = 1.0 / sqrt(d);
+  } else {
+    dis[c] = 0.0;
+    atomicAdd(red + 3, 1.0);  // isolated PDA cell: singular
+  }
+}
+
+__global__ void k_scaled(int nr, int nt, const signed char* mask, const double* Cr, const double* Ct, const double* dis,
+                         float* ar, float* at) {
+  const int c = blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= nr * nt) return;
+  const int i = c / nt, j = c - i * nt;
+  float a = 0.f, b = 0.f;
+  if (mask[c] == 2) {
+    if (i + 1 < nr && mask[c + nt] == 2) a = (float)(-Cr[c] * dis[c] * dis[c + nt]);
+    if (j + 1 < nt && mask[c + 1] == 2) b = (float)(-Ct[c] * dis[c] * dis[c + 1]);
+  }
+  ar[c] = a;
+  at[c] = b;
+}
+
+// --------------------------------------------------------------------------------------------- FP64
+// rs = S (b + sum_f C_f (x_nb - x_c)) on PDA cells; red[slot] += |rs|^2
+__global__ void k_resid64(int nr, int nt, const signed char* __restrict__ mask, const double* __restrict__ Cr,
+                          const double* __restrict__ Ct, const double* __restrict__ dis, const double* __restrict__ x,
+                          const double* __restrict__ b, double* __restrict__ rs, double* red, int slot) {
+  __shared__ double sh[32];
+  const int c = blockIdx.x * blockDim.x + threadIdx.x;
+  double v = 0.0;
+  if (c < nr * nt && mask[c] == 2) {
+    const int i = c / nt, j = c - i * nt;
+    const double xc = x[c];
+    double r = b ? b[c] : 0.0;
+    if (i > 0 && mask[c - nt]) r += Cr[c - nt] * (x[c - nt] - xc);
+    if (i + 1 < nr && mask[c + nt]) r += Cr[c] * (x[c + nt] - xc);
+    if (j > 0 && mask[c - 1]) r += Ct[c - 1] * (x[c - 1] - xc);
+    if (j + 1 < nt && mask[c + 1]) r += Ct[c] * (x[c + 1] - xc);
+    v = dis[c] * r;
+    rs[c] = v;
+  } else if (c < nr * nt) {
+    rs[c] = 0.0;
+  }
+  const double s = block_sum_d(v * v, sh);
+  if (threadIdx.x == 0 && s != 0.0) atomicAdd(red + slot, s);
+}
+
+// rhs of the FP32 solve: r = rs / scale, y = 0; red[slot] += |r|^2 (FP32 values)
+__global__ void k_start(int n, const signed char* mask, const double* rs, double inv_scale, float* y, float* r,
+                        float* p_old, double* sc) {
+  __shared__ float sh[32];
+  const int c = blockIdx.x * blockDim.x + threadIdx.x;
+  float v = 0.f;
+  if (c < n) {
+    v = mask[c] == 2 ? (float)(rs[c] * inv_scale) : 0.f;
+    r[c] = v;
+    y[c] = 0.f;
+    p_old[c] = 0.f;
+  }
+  const float s = block_sum_f(v * v, sh);
+  if (threadIdx.x == 0 && s != 0.f) atomicAdd(sc + 0, (double)s);
+}
+
+// scalar layout: sc[0] = rr_0; iteration k: rr_k at 2k (k >= 1 stored at sc[2k]), pAp_k at sc[2k+1]
+__device__ __forceinline__ double rr_of(const double* sc, int k) { return sc[2 * k]; }
+
+// kernel A of CG iteration k
+__global__ void k_cg_a(int nr, int nt, const signed char* __restrict__ mask, const float* __restrict__ ar,
+                       const float* __restrict__ at, const float* __restrict__ r, const float* __restrict__ p_old,
+                       float* __restrict__ p_new, float* __restrict__ Ap, double* sc, int k, double tol2) {
+  __shared__ float sh[32];
+  const double rr0 = rr_of(sc, 0), rrk = rr_of(sc, k);
+  if (rrk <= tol2 * rr0 || !(rrk == rrk)) return;  // converged (or broken): no-op
+  const float beta = k == 0 ? 0.f : (float)(rrk / rr_of(sc, k - 1));
+  const int c = blockIdx.x * blockDim.x + threadIdx.x;
+  const int n = nr * nt;
+  float v = 0.f;
+  if (c < n && mask[c] == 2) {
+    const int i = c / nt, j = c - i * nt;
+    const float pc = r[c] + beta * p_old[c];
+    float a = pc;
+    if (i > 0) a += ar[c - nt] * (r[c - nt] + beta * p_old[c - nt]);
+    if (i + 1 < nr) a += ar[c] * (r[c + nt] + beta * p_old[c + nt]);
+    if (j > 0) a += at[c - 1] * (r[c - 1] + beta * p_old[c - 1]);
+    if (j + 1 < nt) a += at[c] * (r[c + 1] + beta * p_old[c + 1]);
+    p_new[c] = pc;
+    Ap[c] = a;
+    v = pc * a;
+  } else if (c < n) {
+    p_new[c] = 0.f;
+    Ap[c] = 0.f;
+  }
+  const float s = block_sum_f(v, sh);
+  if (threadIdx.x == 0 && s != 0.f) atomicAdd(sc + 2 * k + 1, (double)s);
+}
+
+// kernel B of CG iteration k
+__global__ void k_cg_b(int n, const signed char* __restrict__ mask, const float* __restrict__ p_new,
+                       const float* __restrict__ Ap, float* __restrict__ y, float* __restrict__ r, double* sc, int k,
+                       double tol2) {
+  __shared__ float sh[32];
+  const double rr0 = rr_of(sc, 0), rrk = rr_of(sc, k);
+  if (rrk <= tol2 * rr0 || !(rrk == rrk)) return;
+  const double pap = sc[2 * k + 1];
+  const float alpha = (float)(rrk / pap);
+  const int c = blockIdx.x * blockDim.x + threadIdx.x;
+  float v = 0.f;
+  if (c < n && mask[c] == 2) {
+    y[c] += alpha * p_new[c];
+    const float rn = r[c] - alpha * Ap[c];
+    r[c] = rn;
+    v = rn * rn;
+  }
+  const float s = block_sum_f(v, sh);
+  if (threadIdx.x == 0) atomicAdd(sc + 2 * (k + 1), (double)s);
+}
+
+__global__ void k_update(int n, const signed char* mask, const double* dis, const float* y, double scale, double* x) {
+  const int c = blockIdx.x * blockDim.x + threadIdx.x;
+  if (c < n && mask[c] == 2) x[c] += scale * dis[c] * (double)y[c];
+}
+
+__global__ void k_tpda(int n, const signed char* mask, const double* u, const double* Tmc, double* Tp) {
+  const int c = blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= n) return;
+  Tp[c] = mask[c] == 2 ? pow(fmax(u[c], 0.0), 0.25) : Tmc[c];
+}
+
+// adjoint right-hand side g = w dT/du = w / (4 u^(3/4)) on PDA cells; lam = 0 everywhere
+__global__ void k_adj_rhs(int n, const signed char* mask, const double* w, const double* u, double* g, double* lam) {
+  const int c = blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= n) return;
+  g[c] = (mask[c] == 2) ? w[c] * 0.25 * pow(fmax(u[c], 1e-300), -0.75) : 0.0;
+  lam[c] = 0.0;
+}
+
+// dJ/dD_c = sum over the active faces of c of dJ/dC_f dC_f/dD_c, dJ/dC_f = -(lam_c - lam_n)(u_c - u_n),
+// dC_f/dD_c = C_f^2 h_c / D_c^2; then dJ/dlog rho = -D dJ/dD, dJ/dkappa_R = -(D/kappa_R) dJ/dD.
+__global__ void k_grad(int nr, int nt, const signed char* mask, const double* Cr, const double* Ct, const double* D,
+                       const double* kR, const double* hr_in, const double* hr_out, const double* ht_lo,
+                       const double* ht_hi, const double* u, const double* lam, double* g_lr, double* g_kr) {
+  const int c = blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= nr * nt) return;
+  const int i = c / nt, j = c - i * nt;
+  double s = 0.0;
+  const signed char mc = mask[c];
+  if (mc) {
+    const double Dc = D[c];
+    auto face = [&](int nb, double C, double h) {
+      const signed char mn = mask[nb];
+      if (!mn || !(C > 0) || (mc != 2 && mn != 2)) return;
+      const double dJdC = -(lam[c] - lam[nb]) * (u[c] - u[nb]);
+      s += dJdC * C * C * h / (Dc * Dc);
+    };
+    if (i > 0) face(c - nt, Cr[c - nt], hr_in[c]);
+    if (i + 1 < nr) face(c + nt, Cr[c], hr_out[c]);
+    if (j > 0) face(c - 1, Ct[c - 1], ht_lo[c]);
+    if (j + 1 < nt) face(c + 1, Ct[c], ht_hi[c]);
+    if (g_lr) g_lr[c] = -Dc * s;
+    if (g_kr) g_kr[c] = -Dc / kR[c] * s;
+  } else {
+    if (g_lr) g_lr[c] = 0.0;
+    if (g_kr) g_kr[c] = 0.0;
+  }
+}
+
+}  // namespace mcrt
+
+using namespace mcrt;
+
+#define CK(call, what)                                    \
+  do {                                                    \
+    cudaError_t e_ = (call);                              \
+    if (e_ != cudaSuccess) return cuda_fail(d, e_, what); \
+  } while (0)
+
+static int nblk(int n) { return (n + 255) / 256; }
+
+static mcrt_status pda_alloc(mcrt_disk* d, int max_inner) {
+  PdaState* P = d->pda;
+  if (!P) {
+    P = new (std::nothrow) PdaState();
+    if (!P) return set_error(d, MCRT_ENOMEM, "host allocation");
+    d->pda = P;
+  }
+  const int nr = d->nr, nt = d->nt, n = nr * nt;
+  if (P->n != n) {
+    P->nr = nr;
+    P->nt = nt;
+    P->n = n;
+    // geometric half-cell resistances
+    std::vector<double> hi_(n), ho(n), tl(n), th(n), el(n);
+    for (int i = 0; i < nr; ++i) {
+      const double r1 = d->rf[i], r2 = d->rf[i + 1], rc = 0.5 * (r1 + r2);
+      for (int j = 0; j < nt; ++j) {
+        const double t1 = d->tf[j], t2 = d->tf[j + 1], tc = 0.5 * (t1 + t2);
+        const double om = 2.0 * kPi * (std::cos(t1) - std::cos(t2));
+        const size_t c = (size_t)i * nt + j;
+        hi_[c] = (1.0 / r1 - 1.0 / rc) / om;
+        ho[c] = (1.0 / rc - 1.0 / r2) / om;
+        const double ltc = std::log(std::tan(0.5 * tc));
+        tl[c] = (t1 > 0 ? ltc - std::log(std::tan(0.5 * t1)) : INFINITY) / (2.0 * kPi * (r2 - r1));
+        th[c] = (t2 < kPi ? std::log(std::tan(0.5 * t2)) - ltc : INFINITY) / (2.0 * kPi * (r2 - r1));
+        el[c] = std::min(r2 - r1, rc * (t2 - t1));
+      }
+    }
+    cudaError_t e = P->hr_in.alloc(n * 8);
+    if (e == cudaSuccess) e = cudaMemcpy(P->hr_in.p, hi_.data(), n * 8, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = P->hr_out.alloc(n * 8);
+    if (e == cudaSuccess) e = cudaMemcpy(P->hr_out.p, ho.data(), n * 8, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = P->ht_lo.alloc(n * 8);
+    if (e == cudaSuccess) e = cudaMemcpy(P->ht_lo.p, tl.data(), n * 8, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = P->ht_hi.alloc(n * 8);
+    if (e == cudaSuccess) e = cudaMemcpy(P->ht_hi.p, th.data(), n * 8, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = P->ell.alloc(n * 8);
+    if (e == cudaSuccess) e = cudaMemcpy(P->ell.p, el.data(), n * 8, cudaMemcpyHostToDevice);
+    DBuf* d8[] = {&P->kR, &P->D, &P->Cr, &P->Ct, &P->dis, &P->u, &P->lam, &P->b64, &P->rs, &P->w, &P->gl, &P->gk};
+    for (DBuf* b : d8)
+      if (e == cudaSuccess) e = b->alloc((size_t)n * 8);
+    DBuf* d4[] = {&P->ar, &P->at, &P->y, &P->r, &P->p0, &P->p1, &P->Ap};
+    for (DBuf* b : d4)
+      if (e == cudaSuccess) e = b->alloc((size_t)n * 4);
+    if (e == cudaSuccess) e = P->mask.alloc(n);
+    if (e == cudaSuccess) e = P->red.alloc(16 * 8);
+    if (e != cudaSuccess) return cuda_fail(d, e, "PDA buffers");
+  }
+  if (P->max_inner_alloc < max_inner) {
+    cudaError_t e = P->sc.alloc(sizeof(double) * (2 * (size_t)max_inner + 8));
+    if (e != cudaSuccess) return cuda_fail(d, e, "PDA scalars");
+    P->max_inner_alloc = max_inner;
+  }
+  return MCRT_OK;
+}
+
+// Host check that every connected PDA region touches a Dirichlet cell.
+static bool components_ok(const mcrt_disk* d, const std::vector<signed char>& mask) {
+  const int nr = d->nr, nt = d->nt, n = nr * nt;
+  std::vector<int> comp(n, -1), stack;
+  for (int s = 0; s < n; ++s) {
+    if (mask[s] != 2 || comp[s] >= 0) continue;
+    bool dir = false;
+    stack.assign(1, s);
+    comp[s] = s;
+    while (!stack.empty()) {
+      const int c = stack.back();
+      stack.pop_back();
+      const int i = c / nt, j = c % nt;
+      const int nb[4] = {i > 0 ? c - nt : -1, i + 1 < nr ? c + nt : -1, j > 0 ? c - 1 : -1, j + 1 < nt ? c + 1 : -1};
+      for (int k = 0; k < 4; ++k) {
+        const int m = nb[k];
+        if (m < 0) continue;
+        if (mask[m] == 1) dir = true;
+        if (mask[m] == 2 && comp[m] < 0) {
+          comp[m] = s;
+          stack.push_back(m);
+        }
+      }
+    }
+    if (!dir) return false;
+  }
+  return true;
+}
+
+// FP64-refined solve of A x = b on the PDA cells; x holds the Dirichlet values elsewhere.
+static mcrt_status refine_solve(mcrt_disk* d, const mcrt_pda_opts* o, double* x, const double* b, int* iters_out) {
+  PdaState* P = d->pda;
+  const int nr = d->nr, nt = d->nt, n = nr * nt;
+  cudaStream_t st = d->stream;
+  const signed char* mask = P->mask.as<signed char>();
+  const double* Cr = P->Cr.as<double>();
+  const double* Ct = P->Ct.as<double>();
+  const double* dis = P->dis.as<double>();
+  double* red = P->red.as<double>();
+  double* sc = P->sc.as<double>();
+  float *y = P->y.as<float>(), *r = P->r.as<float>(), *Ap = P->Ap.as<float>();
+  float* pb[2] = {P->p0.as<float>(), P->p1.as<float>()};
+  const double tol2_in = o->inner_tol * o->inner_tol;
+  double norm_b = -1.0;
+  int total_iters = 0;
+  const int chunk = 32;
+  for (int outer = 0; outer <= o->max_outer; ++outer) {
+    CK(cudaMemsetAsync(red + 4, 0, 8, st), "memset");
+    k_resid64<<<nblk(n), 256, 0, st>>>(nr, nt, mask, Cr, Ct, dis, x, b, P->rs.as<double>(), red, 4);
+    d->launches++;
+    double rn2 = 0.0;
+    CK(cudaMemcpyAsync(&rn2, red + 4, 8, cudaMemcpyDeviceToHost, st), "copy");
+    CK(cudaStreamSynchronize(st), "synchronize");
+    const double rn = std::sqrt(rn2);
+    if (norm_b < 0) norm_b = rn;  // first residual: x = 0 on the PDA cells, so this is |S b_total|
+    if (!(rn == rn)) return set_error(d, MCRT_ENOTCONV, "PDA residual is not finite");
+    if (rn <= o->tol * norm_b || rn == 0.0) {
+      if (iters_out) *iters_out = total_iters;
+      return MCRT_OK;
+    }
+    if (outer == o->max_outer) break;
+    // inner FP32 CG on the unit-diagonal system
+    CK(cudaMemsetAsync(sc, 0, sizeof(double) * (2 * (size_t)o->max_inner + 8), st), "memset");
+    k_start<<<nblk(n), 256, 0, st>>>(n, mask, P->rs.as<double>(), 1.0 / rn, y, r, pb[1], sc);
+    d->launches++;
+    int k = 0;
+    bool conv = false;
+    while (k < o->max_inner && !conv) {
+      const int kend = std::min(k + chunk, o->max_inner);
+      for (; k < kend; ++k) {
+        float* pnew = pb[k & 1];
+        float* pold = pb[(k + 1) & 1];
+        k_cg_a<<<nblk(n), 256, 0, st>>>(nr, nt, mask, P->ar.as<float>(), P->at.as<float>(), r, pold, pnew, Ap, sc, k,
+                                         tol2_in);
+        k_cg_b<<<nblk(n), 256, 0, st>>>(n, mask, pnew, Ap, y, r, sc, k, tol2_in);
+        d->launches += 2;
+      }
+      std::vector<double> h(2 * (size_t)k + 2);
+      CK(cudaMemcpyAsync(h.data(), sc, sizeof(double) * h.size(), cudaMemcpyDeviceToHost, st), "copy");
+      CK(cudaStreamSynchronize(st), "synchronize");
+      const double rr0 = h[0];
+      int kk = 0;
+      for (kk = 0; kk <= k; ++kk) {
+        const double v = h[2 * kk];
+        if (v <= tol2_in * rr0 || !(v == v)) {
+          conv = true;
+          break;
+        }
+      }
+      if (conv) {
+        total_iters += kk;
+        break;
+      }
+    }
+    if (!conv) total_iters += k;
+    k_update<<<nblk(n), 256, 0, st>>>(n, mask, dis, y, rn, x);
+    d->launches++;
+    CK(cudaGetLastError(), "PDA kernels");
+  }
+  if (iters_out) *iters_out = total_iters;
+  return set_error(d, MCRT_ENOTCONV, "PDA solve did not reach its tolerance");
+}
+
+extern "C" {
+
+void mcrt_default_pda_opts(mcrt_pda_opts* o) {
+  if (!o) return;
+  std::memset(o, 0, sizeof(*o));
+  o->min_visits = 30;
+  o->max_rel_err = 0.05;
+  o->tol = 1e-12;
+  o->inner_tol = 1e-5;
+  o->max_outer = 20;
+  o->max_inner = 20000;
+  o->min_cell_tau = 1.0;
+  o->kappa_R = nullptr;
+}
+
+mcrt_status mcrt_solve_pda(mcrt_disk* d, const mcrt_pda_opts* o, int* out_n, int* out_iters) {
+  if (!d) return set_error(nullptr, MCRT_EINVAL, "disk is NULL");
+  if (!o) return set_error(d, MCRT_EINVAL, "opts is NULL");
+  if (!d->has_opacity) return set_error(d, MCRT_ESTATE, "mcrt_set_opacity must come first");
+  if (!(o->tol > 0) || !(o->inner_tol > 0 && o->inner_tol < 1) || o->max_outer < 1 || o->max_inner < 1 ||
+      o->max_inner > 10000000 || !(o->min_cell_tau >= 0))
+    return set_error(d, MCRT_EINVAL, "bad PDA options");
+  CK(cudaSetDevice(d->device), "cudaSetDevice");
+  mcrt_status s = pda_alloc(d, o->max_inner);
+  if (s != MCRT_OK) return s;
+  if (!d->have_T) {
+    s = compute_temperatures(d);
+    if (s != MCRT_OK) return s;
+  }
+  PdaState* P = d->pda;
+  const int nr = d->nr, nt = d->nt, n = nr * nt;
+  cudaStream_t st = d->stream;
+  double* red = P->red.as<double>();
+  CK(cudaMemsetAsync(red, 0, 16 * 8, st), "memset");
+  const double* rho = d->rho_cgs_d.as<double>();
+  double chi_max = 0.0;
+  for (int b = 0; b < d->nlam; ++b) chi_max = std::max(chi_max, d->kabs[b] + (1.0 - d->g[b]) * d->ksca[b]);
+  k_mask<<<nblk(n), 256, 0, st>>>(n, rho, P->ell.as<double>(), chi_max, o->min_cell_tau,
+                                  d->visits.as<unsigned long long>(), d->relerr.as<double>(), o->min_visits,
+                                  o->max_rel_err, P->mask.as<signed char>(), red);
+  k_bnd_mean<<<nblk(n), 256, 0, st>>>(nr, nt, P->mask.as<signed char>(), d->T_mc.as<double>(), red);
+  DBuf over;
+  if (o->kappa_R) {
+    for (int c = 0; c < n; ++c)
+      if (d->rho[c] > 0 && !(o->kappa_R[c] > 0 && std::isfinite(o->kappa_R[c])))
+        return set_error(d, MCRT_EINVAL, "kappa_R must be positive where there is dust");
+    CK(over.alloc((size_t)n * 8), "cudaMalloc");
+    CK(cudaMemcpyAsync(over.p, o->kappa_R, (size_t)n * 8, cudaMemcpyHostToDevice, st), "copy");
+  }
+  k_kappaR<<<nblk(n), 256, 0, st>>>(n, rho, d->tally.as<unsigned long long>(), d->T_mc.as<double>(), red,
+                                    d->gray ? 1 : 0, (double)(d->kabs[0] + (1.0 - d->g[0]) * d->ksca[0]), d->nlam,
+                                    d->lam_e_d.as<double>(), d->chip_d.as<double>(), over.as<double>(),
+                                    P->kR.as<double>());
+  k_cond<<<nblk(n), 256, 0, st>>>(nr, nt, rho, P->kR.as<double>(), P->hr_in.as<double>(), P->hr_out.as<double>(),
+                                  P->ht_lo.as<double>(), P->ht_hi.as<double>(), P->D.as<double>(), P->Cr.as<double>(),
+                                  P->Ct.as<double>());
+  k_diag<<<nblk(n), 256, 0, st>>>(nr, nt, P->mask.as<signed char>(), P->Cr.as<double>(), P->Ct.as<double>(),
+                                  d->T_mc.as<double>(), P->dis.as<double>(), P->u.as<double>(), red);
+  k_scaled<<<nblk(n), 256, 0, st>>>(nr, nt, P->mask.as<signed char>(), P->Cr.as<double>(), P->Ct.as<double>(),
+                                    P->dis.as<double>(), P->ar.as<float>(), P->at.as<float>());
+  d->launches += 6;
+  double hred[4];
+  CK(cudaMemcpyAsync(hred, red, sizeof(hred), cudaMemcpyDeviceToHost, st), "copy");
+  std::vector<signed char> hmask(n);
+  CK(cudaMemcpyAsync(hmask.data(), P->mask.p, n, cudaMemcpyDeviceToHost, st), "copy");
+  CK(cudaStreamSynchronize(st), "synchronize");
+  CK(cudaGetLastError(), "PDA setup kernels");
+  P->n_pda = (int)hred[0];
+  if (out_n) *out_n = P->n_pda;
+  if (hred[3] > 0 || !components_ok(d, hmask))
+    return set_error(d, MCRT_EINVAL, "a PDA region touches no Monte Carlo cell (singular system)");
+  int iters = 0;
+  if (P->n_pda > 0) {
+    s = refine_solve(d, o, P->u.as<double>(), nullptr, &iters);
+    if (s != MCRT_OK) {
+      if (out_iters) *out_iters = iters;
+      return s;
+    }
+  }
+  if (out_iters) *out_iters = iters;
+  k_tpda<<<nblk(n), 256, 0, st>>>(n, P->mask.as<signed char>(), P->u.as<double>(), d->T_mc.as<double>(),
+                                  d->T_pda.as<double>());
+  d->launches++;
+  CK(cudaGetLastError(), "PDA kernels");
+  CK(cudaStreamSynchronize(st), "synchronize");
+  d->have_pda = true;
+  return MCRT_OK;
+}
+
+mcrt_status mcrt_pda_adjoint_dev(mcrt_disk* d, const double* w_dev, double* g_lr, double* g_kr) {
+  if (!d) return set_error(nullptr, MCRT_EINVAL, "disk is NULL");
+  if (!w_dev) return set_error(d, MCRT_EINVAL, "w is NULL");
+  if (!d->have_pda || !d->pda) return set_error(d, MCRT_ESTATE, "mcrt_solve_pda must come first");
+  CK(cudaSetDevice(d->device), "cudaSetDevice");
+  PdaState* P = d->pda;
+  const int nr = d->nr, nt = d->nt, n = nr * nt;
+  cudaStream_t st = d->stream;
+  k_adj_rhs<<<nblk(n), 256, 0, st>>>(n, P->mask.as<signed char>(), w_dev, P->u.as<double>(), P->b64.as<double>(),
+                                     P->lam.as<double>());
+  d->launches++;
+  mcrt_pda_opts o;
+  mcrt_default_pda_opts(&o);
+  if (P->n_pda > 0) {
+    if (P->max_inner_alloc < o.max_inner) {
+      mcrt_status s = pda_alloc(d, o.max_inner);
+      if (s != MCRT_OK) return s;
+    }
+    int it = 0;
+    mcrt_status s = refine_solve(d, &o, P->lam.as<double>(), P->b64.as<double>(), &it);
+    if (s != MCRT_OK) return s;
+  }
+  k_grad<<<nblk(n), 256, 0, st>>>(nr, nt, P->mask.as<signed char>(), P->Cr.as<double>(), P->Ct.as<double>(),
+                                  P->D.as<double>(), P->kR.as<double>(), P->hr_in.as<double>(), P->hr_out.as<double>(),
+                                  P->ht_lo.as<double>(), P->ht_hi.as<double>(), P->u.as<double>(), P->lam.as<double>(),
+                                  g_lr, g_kr);
+  d->launches++;
+  CK(cudaGetLastError(), "adjoint kernels");
+  return MCRT_OK;
+}
+
+mcrt_status mcrt_pda_adjoint(mcrt_disk* d, const double* w, double* g_lr, double* g_kr) {
+  if (!d) return set_error(nullptr, MCRT_EINVAL, "disk is NULL");
+  if (!w) return set_error(d, MCRT_EINVAL, "w is NULL");
+  if (!d->have_pda || !d->pda) return set_error(d, MCRT_ESTATE, "mcrt_solve_pda must come first");
+  CK(cudaSetDevice(d->device), "cudaSetDevice");
+  PdaState* P = d->pda;
+  const size_t n = (size_t)d->nr * d->nt;
+  CK(cudaMemcpyAsync(P->w.p, w, n * 8, cudaMemcpyHostToDevice, d->stream), "copy");
+  mcrt_status s = mcrt_pda_adjoint_dev(d, P->w.as<double>(), P->gl.as<double>(), P->gk.as<double>());
+  if (s != MCRT_OK) return s;
+  if (g_lr) CK(cudaMemcpyAsync(g_lr, P->gl.p, n * 8, cudaMemcpyDeviceToHost, d->stream), "copy");
+  if (g_kr) CK(cudaMemcpyAsync(g_kr, P->gk.p, n * 8, cudaMemcpyDeviceToHost, d->stream), "copy");
+  CK(cudaStreamSynchronize(d->stream), "synchronize");
+  return MCRT_OK;
+}
+
+}  // extern "C"

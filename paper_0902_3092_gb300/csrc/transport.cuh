@@ -1,0 +1,587 @@
+// transport.cuh -- persistent Monte Carlo packet kernel (Sect. 2.1 and 2.2.2).
+//
+// One thread carries one packet at a time. When its packet escapes (or is capped) the thread takes
+// the next packet id from a global queue (ids handed out per warp with one atomic), so warps stay
+// full until the queue drains. Per step a packet either enters a cell, interacts, or escapes:
+//   * distance to interaction s = tau / (rho chi);
+//   * the exact ray/face distance (two spheres, two cones or the midplane plane) is computed only
+//     when s exceeds a safety distance (a lower bound of the distance to the cell boundary, kept
+//     from the last d_min evaluation), so deep inside optically thick cells interactions need no
+//     face arithmetic at all;
+//   * interaction: scatter with the albedo (isotropic or Henyey-Greenstein), else absorb: one
+//     packet energy (2^16 counts) is atomically added to the 64-bit cell tally; the returned old
+//     value gives the cell temperature before and after, and the packet is re-emitted at once with
+//     a wavelength from kappa_nu [B_nu(T_new) - B_nu(T_old)] (Bjorkman & Wood 2001);
+//   * MRW (Sect. 2.2.2): after at least `nmin` interactions in the cell, while d_min > gamma/(rho
+//     chi_R) (Eq. 11), the packet jumps to the surface of the sphere of radius R0 = d_min, the time
+//     spent inside comes from the inverse of Eq. 7 (table), and E_gamma c t rho kappa_bar (Eq. 9)
+//     is deposited;
+//   * leaving r_out adds the packet to the escape spectrum.
+// Random numbers: each packet owns Philox4x32-10 stream (seed; block, model, packet id); draws are
+// consumed in the same order as the FP64 CPU oracle, so gray trajectories of the FP64 build match
+// it event by event.
+#pragma once
+#include "common.cuh"
+
+namespace mcrt {
+
+template <class R>
+struct KParams {
+  DevModel<R> m0;              // the model of single-disk launches
+  const DevModel<R>* models;   // batch launches: descriptors in global memory
+  int nmodels;
+  int mrw;                     // MRW on
+  int nmin;                    // interactions in a cell before MRW
+  int exit_dir;                // 0 isotropic, 1 cosine-weighted outward
+  int want_lam;                // sample emission bins (1), or skip them for gray dust without SED (0)
+  int refill;                  // refill finished lanes every `refill` steps
+  R gamma;
+  unsigned long long total;    // packets in the queue
+  unsigned long long* queue;   // queue head (global counter)
+  uint64_t seed;
+  unsigned long long max_events;
+  unsigned long long max_steps;  // loop guard per packet
+  const float* mrw_tab;        // 2*kMrwTab: x(ln u) for u <= 1/2, then 1/x(ln(1-u)) for u > 1/2
+  float mrw_t0, mrw_dt;        // table abscissae t = t0 + i dt
+  // debug trace (TRACE builds)
+  int trace_n, trace_max;
+  int32_t *tr_type, *tr_cell, *tr_lam, *tr_n;
+  double* tr_pos;
+  double l_unit;
+};
+
+template <class R>
+struct Pkt {
+  R px, py, pz, ux, uy, uz, tau, dsafe;
+  int ir, it, lam, ninc;
+  unsigned long long events, steps;
+  unsigned xcross;  // face crossings since the last interaction (guard against zero-length ping-pong)
+  Rng rng;
+  int pend_mode;  // 0: bin known; 1: BW bin of (pend_cell, pend_tally -> +EUNIT); 2: exit bin at pend_tally
+  int pend_cell;
+  float pend_u;
+  unsigned long long pend_tally;
+  int tslot, ntr;
+};
+
+struct Acc {
+  unsigned long long v[C_NCNT];
+};
+
+template <class R>
+__device__ __forceinline__ R U(Pkt<R>& s) {
+  return to_uniform<R>(s.rng.next());
+}
+
+template <class R>
+__device__ __forceinline__ R neg_log(R u);
+template <>
+__device__ __forceinline__ float neg_log<float>(float u) { return -__logf(u); }
+template <>
+__device__ __forceinline__ double neg_log<double>(double u) { return -log(u); }
+
+// direction (sqrt(1-mu^2) cos phi, sqrt(1-mu^2) sin phi, mu) with phi = 2 pi u2
+template <class R>
+__device__ __forceinline__ void polar_dir(R mu, R u2, R& x, R& y, R& z);
+template <>
+__device__ __forceinline__ void polar_dir<float>(float mu, float u2, float& x, float& y, float& z) {
+  const float st = sqrtf(fmaxf(0.f, 1.f - mu * mu));
+  float sp, cp;
+  __sincosf(6.283185307179586f * u2 - 3.141592653589793f, &sp, &cp);  // argument in [-pi, pi]
+  x = -st * cp;
+  y = -st * sp;
+  z = mu;
+}
+template <>
+__device__ __forceinline__ void polar_dir<double>(double mu, double u2, double& x, double& y, double& z) {
+  const double st = sqrt(fmax(0.0, 1.0 - mu * mu));
+  const double phi = 2.0 * kPi * u2;
+  x = st * cos(phi);
+  y = st * sin(phi);
+  z = mu;
+}
+
+template <class R>
+__device__ __forceinline__ void iso_dir(Pkt<R>& s, R& x, R& y, R& z) {
+  const R mu = (R)2 * U(s) - (R)1;
+  const R u2 = U(s);
+  polar_dir<R>(mu, u2, x, y, z);
+}
+
+// rotate (x,y,z) by polar angle acos(mu) and azimuth 2 pi u2 about itself
+template <class R>
+__device__ __forceinline__ void turn(R& x, R& y, R& z, R mu, R u2) {
+  R a, b, c;
+  polar_dir<R>(mu, u2, a, b, c);  // a = st cos phi, b = st sin phi
+  if (fabs(z) < (R)0.99999) {
+    const R w = sqrt((R)1 - z * z);
+    const R iw = (R)1 / w;
+    const R nx = (a * x * z - b * y) * iw + x * mu;
+    const R ny = (a * y * z + b * x) * iw + y * mu;
+    const R nz = -a * w + z * mu;
+    x = nx; y = ny; z = nz;
+  } else {
+    const R sg = z > (R)0 ? (R)1 : (R)-1;
+    x = a; y = b; z = sg * mu;
+  }
+  const R n = rsqrt_<R>(x * x + y * y + z * z);
+  x *= n; y *= n; z *= n;
+}
+
+template <class R>
+__device__ __forceinline__ R hg_mu(R g, R xi) {
+  if (fabs(g) < (R)1e-6) return (R)2 * xi - (R)1;
+  const R t = ((R)1 - g * g) / ((R)1 - g + (R)2 * g * xi);
+  const R mu = ((R)1 + g * g - t * t) / ((R)2 * g);
+  return fmin((R)1, fmax((R)-1, mu));
+}
+
+// inverse of the MRW survival law P(x) = u (Eq. 7-8) from the two tables
+template <class R>
+__device__ __forceinline__ R mrw_x(const KParams<R>& P, R u) {
+  const bool lower = u <= (R)0.5;
+  const float t = lower ? logf((float)u) : logf((float)((R)1 - u));
+  float f = (t - P.mrw_t0) / P.mrw_dt;
+  f = fminf(fmaxf(f, 0.f), (float)(kMrwTab - 1) - 1e-3f);
+  const int i = (int)f;
+  const float w = f - (float)i;
+  const float* T = P.mrw_tab + (lower ? 0 : kMrwTab);
+  const float v = __ldg(T + i) * (1.f - w) + __ldg(T + i + 1) * w;
+  return lower ? (R)v : (R)1 / (R)v;
+}
+
+// position on the temperature grid of the absorbed energy `tally` of cell c: interval k and weight
+// w, linear in log q. tally = 0 (or below the first grid temperature) gives k = 0, w = 0.
+template <class R>
+__device__ __forceinline__ void qpos(const DevModel<R>& M, unsigned long long tally, int c, int& k, float& w) {
+  k = 0;
+  w = 0.f;
+  if (tally == 0ull) return;
+  const float lq = logf((float)tally) + __ldg(M.lqm + c) + M.lq_run;
+  if (!(lq >= __ldg(M.lQk + 1))) return;
+  const int nT = M.nT;
+  if (lq >= __ldg(M.lQk + nT - 1)) {
+    k = nT - 2;
+    w = 1.f;
+    return;
+  }
+  int lo = 1, hi = nT - 1;  // lQk[lo] <= lq < lQk[hi]
+  while (hi - lo > 1) {
+    const int mid = (lo + hi) >> 1;
+    if (__ldg(M.lQk + mid) <= lq) lo = mid; else hi = mid;
+  }
+  k = lo;
+  const float a = __ldg(M.lQk + lo), b = __ldg(M.lQk + lo + 1);
+  w = (lq - a) / (b - a);
+}
+
+// BW re-emission bin: smallest b with D(b) >= u D(last), D the cumulative difference spectrum
+// kappa [Bbar(T_new) - Bbar(T_old)] from the tabulated rows C[k] = cumulative kappa Bbar(T_k),
+// arranged so that nearby temperatures do not cancel in FP32:
+//   both in interval k:       D = shape of C[k+1] - C[k] (the interval's derivative spectrum)
+//   adjacent intervals:       D = (1 - w_old)(C[k_old+1] - C[k_old]) + w_new (C[k_new+1] - C[k_new])
+//   further apart:            D = C(T_new) - C(T_old), both interpolated
+// Below the first grid temperature (k = 0) the spectrum is the one of the first interval.
+template <class R>
+__device__ int sample_bw(const DevModel<R>& M, int ko, float wo, int kn, float wn, float u) {
+  const int nl = M.nlam;
+  const float* C = M.cbw;
+  int mode = kn <= ko ? 0 : (kn == ko + 1 ? 1 : 2);
+  auto D = [&](int b) -> float {
+    if (mode == 0) {
+      const float* r = C + (size_t)kn * nl;
+      return __ldg(r + nl + b) - __ldg(r + b);
+    }
+    if (mode == 1) {
+      const float* ro = C + (size_t)ko * nl;
+      const float c0 = __ldg(ro + b), c1 = __ldg(ro + nl + b), c2 = __ldg(ro + 2 * nl + b);
+      return (1.f - wo) * (c1 - c0) + wn * (c2 - c1);
+    }
+    const float* ro = C + (size_t)ko * nl;
+    const float* rn = C + (size_t)kn * nl;
+    return ((1.f - wn) * __ldg(rn + b) + wn * __ldg(rn + nl + b)) - ((1.f - wo) * __ldg(ro + b) + wo * __ldg(ro + nl + b));
+  };
+  float tot = D(nl - 1);
+  if (!(tot > 0.f)) {
+    mode = 0;
+    tot = D(nl - 1);
+  }
+  const float target = u * tot;
+  int lo = -1, hi = nl - 1;
+  while (hi - lo > 1) {
+    const int mid = (lo + hi) >> 1;
+    if (D(mid) >= target) hi = mid; else lo = mid;
+  }
+  return hi;
+}
+
+// MRW exit bin from the cumulative dBbar/dT / chi' row at (k, w)
+template <class R>
+__device__ int sample_exit(const DevModel<R>& M, int k, float w, float u) {
+  const int nl = M.nlam;
+  const float* X = M.cexit + (size_t)k * nl;
+  auto cum = [&](int b) { return (1.f - w) * __ldg(X + b) + w * __ldg(X + nl + b); };
+  const float target = u * cum(nl - 1);
+  int lo = -1, hi = nl - 1;
+  while (hi - lo > 1) {
+    const int mid = (lo + hi) >> 1;
+    if (cum(mid) >= target) hi = mid; else lo = mid;
+  }
+  return hi;
+}
+
+template <class R>
+__device__ __forceinline__ int sample_star(const DevModel<R>& M, R u) {
+  const int nl = M.nlam;
+  const R target = u * M.star_cum[nl - 1];
+  int lo = -1, hi = nl - 1;
+  while (hi - lo > 1) {
+    const int mid = (lo + hi) >> 1;
+    if (M.star_cum[mid] >= target) hi = mid; else lo = mid;
+  }
+  return hi;
+}
+
+template <class R, bool TRACE>
+__device__ __forceinline__ void trace_ev(const KParams<R>& P, Pkt<R>& s, int type, int cell) {
+  if (!TRACE) return;
+  if (s.tslot < 0 || s.ntr >= P.trace_max) return;
+  const size_t k = (size_t)s.tslot * P.trace_max + s.ntr;
+  P.tr_type[k] = type;
+  P.tr_cell[k] = cell;
+  P.tr_lam[k] = s.lam;
+  P.tr_pos[3 * k + 0] = (double)s.px * P.l_unit;
+  P.tr_pos[3 * k + 1] = (double)s.py * P.l_unit;
+  P.tr_pos[3 * k + 2] = (double)s.pz * P.l_unit;
+  ++s.ntr;
+  P.tr_n[s.tslot] = s.ntr;
+}
+
+template <class R>
+__device__ __forceinline__ void resolve_pending(const DevModel<R>& M, Pkt<R>& s) {
+  if (s.pend_mode == 1) {
+    int ko, kn;
+    float wo, wn;
+    qpos(M, s.pend_tally, s.pend_cell, ko, wo);
+    qpos(M, s.pend_tally + kEUnit, s.pend_cell, kn, wn);
+    s.lam = sample_bw(M, ko, wo, kn, wn, s.pend_u);
+  } else if (s.pend_mode == 2) {
+    int k;
+    float w;
+    qpos(M, s.pend_tally, s.pend_cell, k, w);
+    s.lam = sample_exit(M, k, w, s.pend_u);
+  }
+  s.pend_mode = 0;
+}
+
+template <class R, bool TRACE>
+__device__ void launch_packet(const KParams<R>& P, const DevModel<R>& M, Pkt<R>& s, unsigned long long k, int tslot,
+                              Acc& acc) {
+  s.rng.init(P.seed, M.model_id, k);
+  s.lam = sample_star(M, U(s));
+  iso_dir(s, s.ux, s.uy, s.uz);
+  s.px = s.py = s.pz = (R)0;
+  s.ir = -1;
+  s.it = -1;
+  s.ninc = 0;
+  s.events = 0;
+  s.steps = 0;
+  s.xcross = 0;
+  s.dsafe = (R)0;
+  s.pend_mode = 0;
+  s.tslot = tslot;
+  s.ntr = 0;
+  trace_ev<R, TRACE>(P, s, EV_LAUNCH, -1);
+  s.tau = neg_log<R>(U(s));
+  acc.v[C_PACKETS]++;
+}
+
+template <class R, bool TRACE>
+__device__ void mrw_chain(const KParams<R>& P, const DevModel<R>& M, Pkt<R>& s, int c, Acc& acc) {
+  const R rho = M.rho[c];
+  for (;;) {
+    if (s.events >= P.max_events) break;
+    const R dm = dmin_cell(M, s.ir, s.it, s.px, s.py, s.pz);
+    R chiR, kb;
+    if (M.gray) {
+      chiR = M.chiR0;
+      kb = M.kbar0;
+    } else {
+      int k;
+      float w;
+      qpos(M, *(volatile unsigned long long*)(M.tally + c), c, k, w);
+      chiR = (R)((1.f - w) * __ldg(M.chiR + k) + w * __ldg(M.chiR + k + 1));
+      kb = (R)((1.f - w) * __ldg(M.kbar + k) + w * __ldg(M.kbar + k + 1));
+    }
+    if (!(dm * rho * chiR > P.gamma)) break;  // Eq. 11
+    const R x = mrw_x(P, U(s));
+    const R tau0 = dm * rho;
+    const R E = (R)3 * x * tau0 * tau0 * chiR * kb;  // Eq. 9 with c t = x R0^2 / D, D = 1/(3 rho chi_R)
+    R units = floor(E * (R)kEUnit + (R)0.5);
+    if (!(units < (R)1.8e19)) {
+      units = (R)1.8e19;
+      acc.v[C_ERR] |= kErrMrwClip;
+    }
+    const unsigned long long du = (unsigned long long)units;
+    const unsigned long long old = atomicAdd(M.tally + c, du);
+    if (old + du < old) acc.v[C_ERR] |= kErrOverflow;
+    acc.v[C_DEPSUM] += du;
+    R hx, hy, hz;
+    iso_dir(s, hx, hy, hz);
+    s.px += dm * hx;
+    s.py += dm * hy;
+    s.pz += dm * hz;
+    if (P.exit_dir == 1) {
+      const R mu = sqrt(U(s));
+      const R u2 = U(s);
+      s.ux = hx; s.uy = hy; s.uz = hz;
+      turn<R>(s.ux, s.uy, s.uz, mu, u2);
+    } else {
+      iso_dir(s, s.ux, s.uy, s.uz);
+    }
+    const R ul = U(s);
+    if (P.want_lam) {
+      if (!M.gray || TRACE) {
+        int k;
+        float w;
+        qpos(M, old + du, c, k, w);
+        s.lam = sample_exit(M, k, w, (float)ul);
+        s.pend_mode = 0;
+      } else {
+        s.pend_mode = 2;
+        s.pend_cell = c;
+        s.pend_tally = old + du;
+        s.pend_u = (float)ul;
+      }
+    }
+    s.events++;
+    acc.v[C_MRW]++;
+    s.dsafe = (R)0;
+    trace_ev<R, TRACE>(P, s, EV_MRW, c);
+  }
+}
+
+// One step of a packet. Returns false when the packet has ended.
+template <class R, bool TRACE>
+__device__ bool step(const KParams<R>& P, const DevModel<R>& M, Pkt<R>& s, Acc& acc) {
+  if (++s.steps > P.max_steps) {
+    acc.v[C_ERR] |= kErrStepGuard;
+    acc.v[C_CAPPED]++;
+    return false;
+  }
+  if (s.ir < 0) {  // inner cavity: straight to r_in
+    const R b = s.px * s.ux + s.py * s.uy + s.pz * s.uz;
+    const R r2 = s.px * s.px + s.py * s.py + s.pz * s.pz;
+    const R sf = sphere_far(b, r2 - M.rf2[0]);
+    s.px += sf * s.ux;
+    s.py += sf * s.uy;
+    s.pz += sf * s.uz;
+    s.ir = 0;
+    s.it = theta_cell(M, s.px, s.py, s.pz);
+    s.ninc = 0;
+    s.dsafe = (R)0;
+    const int c = s.it;
+    atomicAdd(M.visits + c, 1ull);
+    acc.v[C_CROSS]++;
+    trace_ev<R, TRACE>(P, s, EV_CROSS, c);
+    return true;
+  }
+  const int c = s.ir * M.nt + s.it;
+  const R chi = M.gray ? M.chi0 : M.chi[s.lam];
+  const R alpha = M.rho[c] * chi;
+  const R s_int = alpha > (R)0 ? s.tau / alpha : inf_<R>();
+  bool interact;
+  R s_face = (R)0;
+  int face = 1;
+  if (s_int < s.dsafe) {
+    interact = true;
+  } else {
+    const R margin = sizeof(R) == 4 ? (R)(1.0 - 1e-5) : (R)(1.0 - 1e-12);
+    const R dm = dmin_cell(M, s.ir, s.it, s.px, s.py, s.pz) * margin;
+    if (s_int < dm) {
+      interact = true;
+      s.dsafe = dm;
+    } else {
+      s_face = next_face(M, s.ir, s.it, s.px, s.py, s.pz, s.ux, s.uy, s.uz, face);
+      interact = s_int < s_face;
+      s.dsafe = (R)0;
+    }
+  }
+  if (interact) {
+    s.xcross = 0;
+    s.px += s_int * s.ux;
+    s.py += s_int * s.uy;
+    s.pz += s_int * s.uz;
+    s.dsafe = s.dsafe > s_int ? s.dsafe - s_int : (R)0;
+    const R om = M.gray ? M.alb0 : M.alb[s.lam];
+    if (U(s) < om) {
+      const R g = M.gray ? M.g0 : M.gq[s.lam];
+      if (g != (R)0) {
+        const R mu = hg_mu(g, U(s));
+        const R u2 = U(s);
+        turn<R>(s.ux, s.uy, s.uz, mu, u2);
+      } else {
+        iso_dir(s, s.ux, s.uy, s.uz);
+      }
+      acc.v[C_SCA]++;
+      trace_ev<R, TRACE>(P, s, EV_SCATTER, c);
+    } else {
+      const unsigned long long old = atomicAdd(M.tally + c, kEUnit);
+      if (old + kEUnit < old) acc.v[C_ERR] |= kErrOverflow;
+      atomicAdd(M.nabs + c, 1ull);
+      acc.v[C_DEPSUM] += kEUnit;
+      const R ul = U(s);
+      if (P.want_lam) {
+        if (!M.gray || TRACE) {
+          int ko, kn;
+          float wo, wn;
+          qpos(M, old, c, ko, wo);
+          qpos(M, old + kEUnit, c, kn, wn);
+          s.lam = sample_bw(M, ko, wo, kn, wn, (float)ul);
+          s.pend_mode = 0;
+        } else {
+          s.pend_mode = 1;
+          s.pend_cell = c;
+          s.pend_tally = old;
+          s.pend_u = (float)ul;
+        }
+      }
+      iso_dir(s, s.ux, s.uy, s.uz);
+      acc.v[C_ABS]++;
+      trace_ev<R, TRACE>(P, s, EV_ABSORB, c);
+    }
+    s.events++;
+    s.ninc++;
+    if (P.mrw && s.ninc >= P.nmin) mrw_chain<R, TRACE>(P, M, s, c, acc);
+    if (s.events >= P.max_events) {
+      acc.v[C_CAPPED]++;
+      trace_ev<R, TRACE>(P, s, EV_CAPPED, c);
+      return false;
+    }
+    s.tau = neg_log<R>(U(s));
+    return true;
+  }
+  // cross a face
+  if (++s.xcross > 100000u) {
+    acc.v[C_ERR] |= kErrStepGuard;
+    acc.v[C_CAPPED]++;
+    return false;
+  }
+  s.px += s_face * s.ux;
+  s.py += s_face * s.uy;
+  s.pz += s_face * s.uz;
+  s.tau -= alpha * s_face;
+  if (s.tau < (R)0) s.tau = (R)0;
+  acc.v[C_CROSS]++;
+  if (face == 1) s.ir++;
+  else if (face == 0) s.ir--;
+  else if (face == 2) s.it--;
+  else s.it++;
+  if (s.ir >= M.nr) {
+    if (P.want_lam) resolve_pending(M, s);
+    int ib = (int)(fabs(s.uz) * (R)kNInc);
+    ib = ib < kNInc ? ib : kNInc - 1;
+    atomicAdd(M.sed + s.lam * kNInc + ib, 1ull);
+    acc.v[C_ESCAPED]++;
+    trace_ev<R, TRACE>(P, s, EV_ESCAPE, -1);
+    return false;
+  }
+  if (s.ir < 0) {
+    trace_ev<R, TRACE>(P, s, EV_CROSS, -1);
+    return true;
+  }
+  s.ninc = 0;
+  const int cn = s.ir * M.nt + s.it;
+  atomicAdd(M.visits + cn, 1ull);
+  trace_ev<R, TRACE>(P, s, EV_CROSS, cn);
+  return true;
+}
+
+__device__ __forceinline__ unsigned long long warp_sum(unsigned long long v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+template <class R>
+__device__ __forceinline__ void flush(const DevModel<R>& M, Acc& acc, bool warp_uniform) {
+  for (int i = 0; i < C_NCNT; ++i) {
+    unsigned long long v = acc.v[i];
+    if (warp_uniform) {
+      if (i == C_ERR) {
+        v = __reduce_or_sync(0xffffffffu, (unsigned)v);
+      } else {
+        v = warp_sum(v);
+      }
+      if ((threadIdx.x & 31) == 0 && v) {
+        if (i == C_ERR) atomicOr(M.cnt + i, v); else atomicAdd(M.cnt + i, v);
+      }
+    } else if (v) {
+      if (i == C_ERR) atomicOr(M.cnt + i, v); else atomicAdd(M.cnt + i, v);
+    }
+    acc.v[i] = 0;
+  }
+}
+
+// model of queue position q (batch launches): largest m with q_begin <= q
+template <class R>
+__device__ __forceinline__ int find_model(const KParams<R>& P, unsigned long long q) {
+  int lo = 0, hi = P.nmodels;
+  while (hi - lo > 1) {
+    const int mid = (lo + hi) >> 1;
+    if (P.models[mid].q_begin <= q) lo = mid; else hi = mid;
+  }
+  return lo;
+}
+
+template <class R, bool TRACE, bool BATCH>
+__global__ void __launch_bounds__(512) transport_kernel(const KParams<R> P) {
+  Pkt<R> s;
+  Acc acc;
+#pragma unroll
+  for (int i = 0; i < C_NCNT; ++i) acc.v[i] = 0;
+  bool active = false, done = false;
+  int model = 0;
+  const unsigned lane = threadIdx.x & 31;
+  unsigned iter = 0;
+  for (;;) {
+    if (iter++ % (unsigned)P.refill == 0u) {
+      const unsigned need = __ballot_sync(0xffffffffu, !active && !done);
+      if (need) {
+        const int leader = __ffs(need) - 1;
+        unsigned long long base = 0;
+        if ((int)lane == leader) base = atomicAdd(P.queue, (unsigned long long)__popc(need));
+        base = __shfl_sync(0xffffffffu, base, leader);
+        if (!active && !done) {
+          const unsigned long long q = base + __popc(need & ((1u << lane) - 1u));
+          if (q < P.total) {
+            int m = 0;
+            if (BATCH) {
+              m = find_model(P, q);
+              if (m != model) {
+                flush(P.models[model], acc, false);
+                model = m;
+              }
+            }
+            const DevModel<R>& M = BATCH ? P.models[m] : P.m0;
+            const unsigned long long local = q - M.q_begin;
+            const int tslot = (TRACE && local < (unsigned long long)P.trace_n) ? (int)local : -1;
+            launch_packet<R, TRACE>(P, M, s, M.first_id + local, tslot, acc);
+            active = true;
+          } else {
+            done = true;
+          }
+        }
+      }
+    }
+    if (__all_sync(0xffffffffu, done && !active)) break;
+    if (active) {
+      const DevModel<R>& M = BATCH ? P.models[model] : P.m0;
+      active = step<R, TRACE>(P, M, s, acc);
+    }
+  }
+  if (BATCH) flush(P.models[model], acc, false);
+  else flush(P.m0, acc, true);
+}
+
+}  // namespace mcrt

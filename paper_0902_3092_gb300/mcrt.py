@@ -1,0 +1,297 @@
+"""ctypes binding of libmcrt.so (include/mcrt.h): argument marshalling only.
+
+Every step of the transport, temperature and diffusion path runs in the CUDA library; this module
+converts numpy arrays to pointers and C structs and raises on a non-zero status. It fails loudly
+when the library has not been built.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libmcrt.so")
+
+EUNIT = 65536
+NINC = 10
+T_MC, T_PDA = 0, 1
+STATUS = {0: "OK", 1: "EINVAL", 2: "ENOMEM", 3: "ECUDA", 4: "ENOTCONV", 5: "ETIMEOUT", 6: "EOVERFLOW", 7: "ESTATE"}
+EXPORTS = ["mcrt_disk_create", "mcrt_set_opacity", "mcrt_default_run_opts", "mcrt_run_photons", "mcrt_run_batch",
+           "mcrt_reset", "mcrt_temperatures", "mcrt_temperatures_dev", "mcrt_get_tallies", "mcrt_sed",
+           "mcrt_default_pda_opts", "mcrt_solve_pda", "mcrt_pda_adjoint", "mcrt_pda_adjoint_dev",
+           "mcrt_trace_packets", "mcrt_checkpoint", "mcrt_restore", "mcrt_debug_uniforms", "mcrt_debug_mrw_x",
+           "mcrt_disk_info", "mcrt_launch_count", "mcrt_last_error", "mcrt_disk_destroy"]
+
+
+class McrtError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"{STATUS.get(status, status)}: {msg}")
+        self.status = status
+
+
+class Grid(C.Structure):
+    _fields_ = [("nr", C.c_int), ("ntheta", C.c_int), ("r_faces_cm", C.POINTER(C.c_double)),
+                ("theta_faces", C.POINTER(C.c_double)), ("rho_gcm3", C.POINTER(C.c_double))]
+
+
+class Star(C.Structure):
+    _fields_ = [("T_star_K", C.c_double), ("R_star_cm", C.c_double)]
+
+
+class RunOpts(C.Structure):
+    _fields_ = [("precision", C.c_int), ("mrw", C.c_int), ("gamma", C.c_double), ("mrw_min_interactions", C.c_int),
+                ("mrw_exit_dir", C.c_int), ("max_events_per_packet", C.c_uint64), ("n_total_packets", C.c_uint64),
+                ("block_size", C.c_int), ("refill_interval", C.c_int), ("want_sed", C.c_int)]
+
+
+class RunStats(C.Structure):
+    _fields_ = [("packets", C.c_uint64), ("events", C.c_uint64), ("absorptions", C.c_uint64),
+                ("scatterings", C.c_uint64), ("crossings", C.c_uint64), ("mrw_jumps", C.c_uint64),
+                ("capped", C.c_uint64), ("escaped", C.c_uint64), ("deposit_sum", C.c_uint64),
+                ("error_flags", C.c_uint32), ("seconds", C.c_double)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+class PdaOpts(C.Structure):
+    _fields_ = [("min_visits", C.c_int), ("max_rel_err", C.c_double), ("tol", C.c_double), ("inner_tol", C.c_double),
+                ("max_outer", C.c_int), ("max_inner", C.c_int), ("min_cell_tau", C.c_double),
+                ("kappa_R", C.POINTER(C.c_double))]
+
+
+_lib = None
+
+
+def lib():
+    """Loads libmcrt.so; raises if it has not been built (no CPU fallback exists)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise RuntimeError(f"{LIB_PATH} is missing: build it with paper_0902_3092_gb300.build.build()")
+    L = C.CDLL(LIB_PATH)
+    P, pd, pu, pi = C.c_void_p, C.POINTER(C.c_double), C.POINTER(C.c_uint64), C.POINTER(C.c_int32)
+    st = C.c_int
+    sig = {
+        "mcrt_disk_create": (st, [C.POINTER(Grid), C.POINTER(Star), C.c_int, P, C.POINTER(P)]),
+        "mcrt_set_opacity": (st, [P, C.c_int, pd, pd, pd, pd]),
+        "mcrt_default_run_opts": (None, [C.POINTER(RunOpts)]),
+        "mcrt_run_photons": (st, [P, C.c_uint64, C.c_uint64, C.c_uint64, C.POINTER(RunOpts), C.POINTER(RunStats)]),
+        "mcrt_run_batch": (st, [C.POINTER(P), C.c_int, pu, C.c_uint64, C.POINTER(RunOpts), C.POINTER(RunStats)]),
+        "mcrt_reset": (st, [P]),
+        "mcrt_temperatures": (st, [P, C.c_int, pd, pd, pu]),
+        "mcrt_temperatures_dev": (st, [P, C.c_int, P, P]),
+        "mcrt_get_tallies": (st, [P, pu, pu, pu]),
+        "mcrt_sed": (st, [P, C.c_int, pd]),
+        "mcrt_default_pda_opts": (None, [C.POINTER(PdaOpts)]),
+        "mcrt_solve_pda": (st, [P, C.POINTER(PdaOpts), C.POINTER(C.c_int), C.POINTER(C.c_int)]),
+        "mcrt_pda_adjoint": (st, [P, pd, pd, pd]),
+        "mcrt_pda_adjoint_dev": (st, [P, P, P, P]),
+        "mcrt_trace_packets": (st, [P, C.c_uint64, C.c_uint64, C.c_uint64, C.POINTER(RunOpts), C.c_int, pi, pi, pi, pd,
+                                    pi]),
+        "mcrt_checkpoint": (st, [P, P, C.POINTER(C.c_size_t)]),
+        "mcrt_restore": (st, [P, P, C.c_size_t]),
+        "mcrt_debug_uniforms": (st, [C.c_int, C.c_uint64, C.c_uint32, C.c_uint64, C.c_int, pd]),
+        "mcrt_debug_mrw_x": (st, [C.c_int, C.c_int, pd, pd]),
+        "mcrt_disk_info": (st, [P, C.POINTER(C.c_int), C.POINTER(C.c_int), C.POINTER(C.c_int)]),
+        "mcrt_launch_count": (st, [P, C.POINTER(C.c_uint64)]),
+        "mcrt_last_error": (C.c_char_p, [P]),
+        "mcrt_disk_destroy": (None, [P]),
+    }
+    for name, (res, args) in sig.items():
+        f = getattr(L, name)
+        f.restype = res
+        f.argtypes = args
+    _lib = L
+    return L
+
+
+def _dp(a):
+    return a.ctypes.data_as(C.POINTER(C.c_double))
+
+
+def _up(a):
+    return a.ctypes.data_as(C.POINTER(C.c_uint64))
+
+
+def _ip(a):
+    return a.ctypes.data_as(C.POINTER(C.c_int32))
+
+
+def _check(status, handle=None):
+    if status != 0:
+        msg = lib().mcrt_last_error(handle)
+        raise McrtError(status, msg.decode() if msg else "")
+
+
+def run_opts(precision=32, mrw=False, gamma=2.0, nmin=20, exit_dir=0, max_events=100_000_000, n_total=0,
+             block_size=0, refill=0, want_sed=True):
+    o = RunOpts()
+    lib().mcrt_default_run_opts(C.byref(o))
+    o.precision, o.mrw, o.gamma, o.mrw_min_interactions, o.mrw_exit_dir = precision, int(mrw), gamma, nmin, exit_dir
+    o.max_events_per_packet, o.n_total_packets = int(max_events), int(n_total)
+    o.block_size, o.refill_interval, o.want_sed = block_size, refill, int(want_sed)
+    return o
+
+
+class Disk:
+    """One disk model on one GPU (owns the library handle)."""
+
+    def __init__(self, r_faces_cm, theta_faces, rho, T_star_K, R_star_cm, device=0, stream=None):
+        L = lib()
+        self._rf = np.ascontiguousarray(r_faces_cm, np.float64)
+        self._tf = np.ascontiguousarray(theta_faces, np.float64)
+        self._rho = np.ascontiguousarray(rho, np.float64).ravel()
+        self.nr, self.ntheta = len(self._rf) - 1, len(self._tf) - 1
+        g = Grid(self.nr, self.ntheta, _dp(self._rf), _dp(self._tf), _dp(self._rho))
+        s = Star(float(T_star_K), float(R_star_cm))
+        h = C.c_void_p()
+        _check(L.mcrt_disk_create(C.byref(g), C.byref(s), int(device), stream, C.byref(h)))
+        self._h = h
+        self.nlam = 0
+        self.L_star = 4 * np.pi * R_star_cm ** 2 * (2 * np.pi ** 5 * 1.380649e-16 ** 4 /
+                                                      (15 * 6.62607015e-27 ** 3 * 2.99792458e10 ** 2)) * T_star_K ** 4
+
+    @classmethod
+    def from_model(cls, d, device=0, stream=None):
+        """From a paper_0902_3092_gb300.disks.Disk (grid, star and dust)."""
+        x = cls(d.r_faces_cm, d.theta_faces, d.rho, d.star.T_K, d.star.R_cm, device, stream)
+        op = d.opacity
+        x.set_opacity(op.lam_edges_um, op.kappa_abs, op.kappa_sca, op.g)
+        return x
+
+    @property
+    def handle(self):
+        return self._h
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib().mcrt_disk_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_opacity(self, lam_edges_um, kappa_abs, kappa_sca, g=None):
+        e = np.ascontiguousarray(lam_edges_um, np.float64)
+        ka = np.ascontiguousarray(kappa_abs, np.float64)
+        ks = np.ascontiguousarray(kappa_sca, np.float64)
+        gg = None if g is None else np.ascontiguousarray(g, np.float64)
+        self.nlam = len(ka)
+        _check(lib().mcrt_set_opacity(self._h, self.nlam, _dp(e), _dp(ka), _dp(ks), None if gg is None else _dp(gg)),
+               self._h)
+
+    def run_photons(self, n_packets, seed=1, first_id=0, **kw):
+        o = run_opts(**kw)
+        s = RunStats()
+        _check(lib().mcrt_run_photons(self._h, int(n_packets), int(seed), int(first_id), C.byref(o), C.byref(s)),
+               self._h)
+        return s.as_dict()
+
+    def trace(self, n_packets, seed=1, first_id=0, max_events=1000, **kw):
+        o = run_opts(**kw)
+        m = n_packets * max_events
+        tr = dict(type=np.full(m, -1, np.int32), cell=np.full(m, -1, np.int32), lam=np.full(m, -1, np.int32),
+                  pos=np.zeros((m, 3)), n=np.zeros(n_packets, np.int32))
+        _check(lib().mcrt_trace_packets(self._h, int(n_packets), int(seed), int(first_id), C.byref(o), int(max_events),
+                                        _ip(tr["type"]), _ip(tr["cell"]), _ip(tr["lam"]), _dp(tr["pos"]),
+                                        _ip(tr["n"])), self._h)
+        for k in ("type", "cell", "lam"):
+            tr[k] = tr[k].reshape(n_packets, max_events)
+        tr["pos"] = tr["pos"].reshape(n_packets, max_events, 3)
+        return tr
+
+    def reset(self):
+        _check(lib().mcrt_reset(self._h), self._h)
+
+    def temperatures(self, which=T_MC):
+        n = self.nr * self.ntheta
+        T, e, v = np.zeros(n), np.zeros(n), np.zeros(n, np.uint64)
+        _check(lib().mcrt_temperatures(self._h, int(which), _dp(T), _dp(e), _up(v)), self._h)
+        sh = (self.nr, self.ntheta)
+        return T.reshape(sh), e.reshape(sh), v.reshape(sh)
+
+    def temperatures_dev(self, T_ptr, relerr_ptr=None, which=T_MC):
+        _check(lib().mcrt_temperatures_dev(self._h, int(which), T_ptr, relerr_ptr), self._h)
+
+    def tallies(self):
+        n = self.nr * self.ntheta
+        t, v, a = np.zeros(n, np.uint64), np.zeros(n, np.uint64), np.zeros(n, np.uint64)
+        _check(lib().mcrt_get_tallies(self._h, _up(t), _up(v), _up(a)), self._h)
+        return t, v, a
+
+    def sed(self, n_incl=NINC):
+        L = np.zeros(self.nlam * n_incl)
+        _check(lib().mcrt_sed(self._h, int(n_incl), _dp(L)), self._h)
+        return L.reshape(self.nlam, n_incl)
+
+    def solve_pda(self, min_visits=30, max_rel_err=0.05, tol=1e-12, inner_tol=1e-5, max_outer=20, max_inner=20000,
+                  kappa_R=None, min_cell_tau=1.0):
+        o = PdaOpts()
+        lib().mcrt_default_pda_opts(C.byref(o))
+        o.min_visits, o.max_rel_err, o.tol, o.inner_tol = min_visits, max_rel_err, tol, inner_tol
+        o.min_cell_tau = min_cell_tau
+        o.max_outer, o.max_inner = max_outer, max_inner
+        kr = None
+        if kappa_R is not None:
+            kr = np.ascontiguousarray(kappa_R, np.float64).ravel()
+            o.kappa_R = _dp(kr)
+        npda, it = C.c_int(), C.c_int()
+        _check(lib().mcrt_solve_pda(self._h, C.byref(o), C.byref(npda), C.byref(it)), self._h)
+        return npda.value, it.value
+
+    def pda_adjoint(self, w):
+        w = np.ascontiguousarray(w, np.float64).ravel()
+        n = self.nr * self.ntheta
+        gl, gk = np.zeros(n), np.zeros(n)
+        _check(lib().mcrt_pda_adjoint(self._h, _dp(w), _dp(gl), _dp(gk)), self._h)
+        sh = (self.nr, self.ntheta)
+        return gl.reshape(sh), gk.reshape(sh)
+
+    def pda_adjoint_dev(self, w_ptr, g_lr_ptr, g_kr_ptr):
+        _check(lib().mcrt_pda_adjoint_dev(self._h, w_ptr, g_lr_ptr, g_kr_ptr), self._h)
+
+    def launch_count(self) -> int:
+        n = C.c_uint64()
+        _check(lib().mcrt_launch_count(self._h, C.byref(n)), self._h)
+        return n.value
+
+    def checkpoint(self) -> bytes:
+        n = C.c_size_t()
+        _check(lib().mcrt_checkpoint(self._h, None, C.byref(n)), self._h)
+        buf = C.create_string_buffer(n.value)
+        _check(lib().mcrt_checkpoint(self._h, C.cast(buf, C.c_void_p), C.byref(n)), self._h)
+        return buf.raw
+
+    def restore(self, blob: bytes):
+        buf = C.create_string_buffer(blob, len(blob))
+        _check(lib().mcrt_restore(self._h, C.cast(buf, C.c_void_p), len(blob)), self._h)
+
+
+def run_batch(disks, n_packets, seed=1, **kw):
+    o = run_opts(**kw)
+    n = len(disks)
+    hs = (C.c_void_p * n)(*[d.handle for d in disks])
+    npk = np.ascontiguousarray(n_packets, np.uint64)
+    stats = (RunStats * n)()
+    _check(lib().mcrt_run_batch(hs, n, _up(npk), int(seed), C.byref(o), stats))
+    return [s.as_dict() for s in stats]
+
+
+def debug_uniforms(seed, model, packet, n, device=0):
+    out = np.zeros(n)
+    _check(lib().mcrt_debug_uniforms(int(device), int(seed), int(model), int(packet), int(n), _dp(out)))
+    return out
+
+
+def debug_mrw_x(P0, device=0):
+    P0 = np.ascontiguousarray(P0, np.float64)
+    out = np.zeros_like(P0)
+    _check(lib().mcrt_debug_mrw_x(int(device), len(P0), _dp(P0), _dp(out)))
+    return out

@@ -1,0 +1,75 @@
+"""The C-ABI library builds, loads and exports every function that include/mcrt.h declares, and the
+ctypes structs have the C layout. No compute calls: these run without a GPU."""
+import os
+import re
+import subprocess
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "mcrt.h")
+
+
+@pytest.fixture(scope="module")
+def L():
+    from paper_0902_3092_gb300 import build, mcrt
+    build.build()
+    return mcrt.lib()
+
+
+def declared():
+    src = open(HEADER).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(mcrt_[a-z_0-9]+)\s*\(", src)))
+
+
+def test_all_declared_symbols_exported(L):
+    names = declared()
+    assert len(names) >= 20
+    out = subprocess.run(["nm", "-D", "--defined-only", L._name], capture_output=True, text=True).stdout
+    exported = set(re.findall(r" T (mcrt_\w+)", out))
+    missing = [n for n in names if n not in exported]
+    assert not missing, missing
+    from paper_0902_3092_gb300 import mcrt
+    assert sorted(mcrt.EXPORTS) == names
+
+
+def test_struct_layouts_match_c(L, tmp_path):
+    import ctypes as C
+
+    from paper_0902_3092_gb300 import mcrt
+    prog = tmp_path / "sz.c"
+    prog.write_text('#include "mcrt.h"\n#include <stdio.h>\n#include <stddef.h>\nint main(void){printf("%zu %zu %zu %zu %zu %zu %zu\\n",'
+                    'sizeof(mcrt_grid),sizeof(mcrt_star),sizeof(mcrt_run_opts),sizeof(mcrt_run_stats),sizeof(mcrt_pda_opts),'
+                    'offsetof(mcrt_run_stats,seconds),offsetof(mcrt_pda_opts,kappa_R));return 0;}\n')
+    exe = tmp_path / "sz"
+    subprocess.check_call(["gcc", "-I", os.path.dirname(HEADER), str(prog), "-o", str(exe)])
+    got = [int(x) for x in subprocess.check_output([str(exe)]).split()]
+    want = [C.sizeof(mcrt.Grid), C.sizeof(mcrt.Star), C.sizeof(mcrt.RunOpts), C.sizeof(mcrt.RunStats),
+            C.sizeof(mcrt.PdaOpts), mcrt.RunStats.seconds.offset, mcrt.PdaOpts.kappa_R.offset]
+    assert got == want
+
+
+def test_defaults_and_host_validation(L):
+    import ctypes as C
+
+    from paper_0902_3092_gb300 import mcrt
+    o = mcrt.RunOpts()
+    L.mcrt_default_run_opts(C.byref(o))
+    assert o.precision == 32 and o.mrw_min_interactions == 20 and o.gamma == 2.0 and o.want_sed == 1
+    p = mcrt.PdaOpts()
+    L.mcrt_default_pda_opts(C.byref(p))
+    assert p.min_visits == 30 and p.max_rel_err == 0.05
+    # invalid input is rejected on the host before any device work
+    h = C.c_void_p()
+    assert L.mcrt_disk_create(None, None, 0, None, C.byref(h)) == 1
+    assert b"NULL" in L.mcrt_last_error(None)
+    L.mcrt_disk_destroy(None)
+
+
+def test_binding_fails_loudly_without_library(monkeypatch):
+    from paper_0902_3092_gb300 import mcrt
+    monkeypatch.setattr(mcrt, "_lib", None)
+    monkeypatch.setattr(mcrt, "LIB_PATH", "/nonexistent/libmcrt.so")
+    with pytest.raises(RuntimeError):
+        mcrt.lib()

@@ -121,6 +121,8 @@ def _small_disk_problem(nongray=False, n=14):
 def test_maximum_principle(oracle):
     d, Tb, mask = _small_disk_problem()
     T, m, u, info = run_pda(oracle, d, mask, Tb)
+    assert not np.any(m & ~mask)
+    mask = m
     assert mask.sum() > 10
     A = info["A"]
     assert abs(A - A.T).max() < 1e-12 * abs(A).max()
@@ -161,6 +163,9 @@ def test_adjoint_against_finite_differences(oracle, nongray):
 
 
 def test_singular_region_is_rejected(oracle):
-    d, Tb, mask = _small_disk_problem()
+    """Every cell thick and in the PDA region: no Monte Carlo boundary value anywhere."""
+    rf = np.geomspace(1.0, 3.0, 7) * disks.AU_CM
+    tf = np.linspace(0, math.pi, 7)
+    d = custom_disk(rf, tf, np.full((6, 6), 1e-10))
     with pytest.raises(ValueError):
-        run_pda(oracle, d, d.rho > 0, Tb)
+        run_pda(oracle, d, np.ones((6, 6), bool), np.full((6, 6), 100.0))
