@@ -51,6 +51,7 @@ def parse():
     p.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     p.add_argument("--packets", type=float, default=1e8, help="packets per step per rank")
     p.add_argument("--gamma", type=float, default=2.0)
+    p.add_argument("--max-events", type=float, default=1e6, help="per-packet event cap (capped packets reported)")
     p.add_argument("--plain-packets", type=float, default=1e6)
     p.add_argument("--cpu-seconds", type=float, default=15.0)
     p.add_argument("--no-e2e", action="store_true")
@@ -134,7 +135,7 @@ def measured_peaks():
         return {}
 
 
-def cpu_baseline(d, gamma, budget_s):
+def cpu_baseline(d, gamma, budget_s, max_events):
     """The FP64 oracle as it stands, one host core: MRW transport of a bounded packet sample of the same
     disk, then its PDA solve; value = sample packets / transport seconds."""
     from oracle import oracle as O
@@ -143,7 +144,8 @@ def cpu_baseline(d, gamma, budget_s):
     t0 = time.perf_counter()
     n, chunk = 0, 50
     while time.perf_counter() - t0 < budget_s:
-        run.run(chunk, seed=1, first_id=n, n_total=10 ** 8, mrw=True, gamma=gamma, want_sed=False)
+        run.run(chunk, seed=1, first_id=n, n_total=10 ** 8, mrw=True, gamma=gamma, want_sed=False,
+                max_events=max_events)
         n += chunk
     t_tr = time.perf_counter() - t0
     T, err = run.temperatures()
@@ -172,7 +174,8 @@ def run_reference(args):
     for s in range(args.warmup + args.steps):
         run = O.Run(d)
         t0 = time.perf_counter()
-        run.run(per_step, seed=1, first_id=s * per_step, n_total=10 ** 8, mrw=True, gamma=args.gamma, want_sed=False)
+        run.run(per_step, seed=1, first_id=s * per_step, n_total=10 ** 8, mrw=True, gamma=args.gamma, want_sed=False,
+                max_events=int(args.max_events))
         T, err = run.temperatures()
         try:
             O.solve_pda(d, T, run.tally, run.visits, err)
@@ -231,7 +234,7 @@ def main():
     def step(i):
         g.reset()
         st = g.run_photons(Np, seed=1, first_id=(rank + world * i) * Np, n_total=Np * world, mrw=True,
-                           gamma=args.gamma, want_sed=True)
+                           gamma=args.gamma, want_sed=True, max_events=int(args.max_events))
         combine()
         n_pda, iters = g.solve_pda()
         return st, n_pda, iters
@@ -267,13 +270,13 @@ def main():
     pda_ms = [ms - 1e3 * ts for ms, ts in zip(step_ms, tr_s)]
     s0 = stats[-1][0]
 
-    # plain Monte Carlo on the same disk (no MRW, no PDA), events capped at 1e7 per packet
+    # plain Monte Carlo on the same disk (no MRW, no PDA), same per-packet event cap
     Npl = int(args.plain_packets)
     g.reset()
-    t0 = time.perf_counter()
-    stp = g.run_photons(Npl, seed=2, first_id=0, mrw=False, max_events=10 ** 7, want_sed=True)
+    stp = g.run_photons(Npl, seed=2, first_id=0, mrw=False, max_events=int(args.max_events), want_sed=True)
     plain = {"packets_per_s": Npl / stp["seconds"], "kernel_s": stp["seconds"], "packets": Npl,
-             "events": stp["events"], "capped": stp["capped"], "event_cap": 10 ** 7}
+             "events": stp["events"], "capped": stp["capped"], "event_cap": int(args.max_events),
+             "max_packet_steps": stp["max_packet_steps"]}
 
     # end to end through the host C ABI: create from host arrays, transport, temperatures, PDA, read T
     e2e = None
@@ -286,7 +289,8 @@ def main():
         for i in range(args.steps):
             t0 = time.perf_counter()
             h = mcrt.Disk.from_model(d, device=local)
-            h.run_photons(Np, seed=1, first_id=(rank + world * i) * Np, n_total=Np, mrw=True, gamma=args.gamma)
+            h.run_photons(Np, seed=1, first_id=(rank + world * i) * Np, n_total=Np, mrw=True, gamma=args.gamma,
+                          max_events=int(args.max_events))
             h.solve_pda()
             T, _, _ = h.temperatures(mcrt.T_PDA)
             h.close()
@@ -311,20 +315,23 @@ def main():
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:
-        cpu = cpu_baseline(d, args.gamma, args.cpu_seconds)
+        cpu = cpu_baseline(d, args.gamma, args.cpu_seconds, int(args.max_events))
 
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": 1e3 * t_max / args.steps, "higher_is_better": True,
                 "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
                 "config": {"workload": WORKLOAD, "packets_per_step_per_rank": Np, "grid": [d.nr, d.ntheta],
-                           "tau_mid": 1e6, "gamma": args.gamma, "pda_min_visits": 30, "pda_max_rel_err": 0.05,
+                           "tau_mid": 1e6, "gamma": args.gamma, "mrw_min_interactions": 20,
+                           "max_events_per_packet": int(args.max_events), "pda_min_visits": 30,
+                           "pda_max_rel_err": 0.05,
                            "l2": "flushed between timed steps (512 MiB write outside the timed region)",
                            "parallelism": f"packet ranges per rank, int64 tally all-reduce" if world > 1 else "1 GPU"},
                 "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": int(launches),
                 "clocks": clk.summary(),
                 "transport": {"kernel_ms_per_step": 1e3 * float(np.mean(tr_s)), "events": s0["events"],
                               "crossings": s0["crossings"], "mrw_jumps": s0["mrw_jumps"], "capped": s0["capped"],
+                              "capped_fraction": s0["capped"] / Np, "max_packet_steps": s0["max_packet_steps"],
                               "events_per_s": s0["events"] / s0["seconds"], "error_flags": s0["error_flags"]},
                 "pda": {"ms_per_step": float(np.mean(pda_ms)), "cells": stats[-1][1], "cg_iterations": stats[-1][2]},
                 "plain_mc": plain, "peaks_file": bool(peaks)}

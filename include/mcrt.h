@@ -105,6 +105,8 @@ typedef struct {
                            summed tallies when no update was lost */
   uint32_t error_flags; /* bit 0 tally overflow, bit 1 MRW deposit clipped, bit 2 step guard */
   double seconds;       /* device time of the transport kernel(s) */
+  uint64_t max_packet_steps;  /* interactions + jumps + face crossings of the longest packet */
+  uint64_t longest_packet;    /* its packet id modulo 2^24 */
 } mcrt_run_stats;
 
 /* Transports packets first_packet_id .. first_packet_id+n_packets-1 (Sect. 2.1, 2.2.2): launch from
@@ -147,7 +149,7 @@ typedef struct {
   double max_rel_err;      /* ... or where the statistical T error exceeds this (0.05) */
   double tol;              /* relative FP64 residual of the refined solution (1e-12) */
   double inner_tol;        /* relative residual reduction of each FP32 inner solve (1e-5) */
-  int max_outer;           /* FP64 refinement steps (20) */
+  int max_outer;           /* FP64 refinement steps (50) */
   int max_inner;           /* FP32 CG iterations per refinement step (20000) */
   double min_cell_tau;     /* only cells at least this optically thick take part: rho * max_b chi'_b *
                               min(dr, r dtheta) >= min_cell_tau (1.0); diffusion needs optical depth */

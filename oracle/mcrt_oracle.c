@@ -261,6 +261,8 @@ double oracle_T_of_q(const oracle_model *m, double q) {
   if (is_gray(m)) return pow(q / (4.0 * OR_SIGMA * m->kabs[0]), 0.25);
   double *Bb = (double *)malloc(sizeof(double) * m->nlam);
   double lo = 1e-3, hi = 1e7;
+  while (Q_of_T(m, hi, Bb) < q) hi *= 10.0;
+  while (lo > 1e-300 && Q_of_T(m, lo, Bb) > q) lo *= 0.1;
   double T = pow(q / (4.0 * OR_SIGMA * m->kabs[0]), 0.25);
   if (!(T > lo && T < hi)) T = sqrt(lo * hi);
   for (int it = 0; it < 200; ++it) {

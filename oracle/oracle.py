@@ -312,6 +312,13 @@ def pda_mask(disk, visits, relerr, min_visits=30, max_rel_err=0.05, min_cell_tau
     return (disk.rho > 0) & thick & ((visits < min_visits) | (relerr > max_rel_err))
 
 
+def dirichlet_mask(disk, pda, tally):
+    """Cells whose Monte Carlo temperature bounds the PDA region: dust that absorbed energy. Reading:
+    a cell outside the PDA region that absorbed nothing has no temperature estimate and, like a
+    dust-free cell, carries no flux."""
+    return (disk.rho > 0) & (~pda) & (np.asarray(tally).reshape(disk.rho.shape) > 0)
+
+
 def _borders(mask):
     """Cells that share a face with a cell of `mask`."""
     out = np.zeros_like(mask)
@@ -326,7 +333,7 @@ def reference_T_for_D(T_mc, tally, mask, rho):
     """T at which D is frozen: the MC temperature where the cell absorbed energy, otherwise
     the mean MC temperature of the Dirichlet cells that border the PDA region."""
     nr, nt = T_mc.shape
-    bnd = _borders(mask) & (~mask) & (rho > 0)
+    bnd = _borders(mask) & (~mask) & (rho > 0) & (np.asarray(tally).reshape(nr, nt) > 0)
     Tb = float(T_mc[bnd].mean()) if bnd.any() else float(T_mc[rho > 0].mean())
     return np.where(np.asarray(tally).reshape(nr, nt) > 0, T_mc, Tb)
 
@@ -355,11 +362,11 @@ def half_resistances(r_faces, theta_faces):
     return hr_in, hr_out, ht_lo, ht_hi
 
 
-def conductances(disk, D):
+def conductances(disk, D, part=None):
     """Face conductances Cr[i,j] between (i,j)-(i+1,j) and Ct[i,j] between (i,j)-(i,j+1);
-    zero where either cell has no dust."""
+    zero where either cell does not take part (no dust, or `part` False)."""
     hr_in, hr_out, ht_lo, ht_hi = half_resistances(disk.r_faces_cm, disk.theta_faces)
-    dust = disk.rho > 0
+    dust = (disk.rho > 0) if part is None else part
     with np.errstate(divide="ignore", invalid="ignore"):
         Cr = 1.0 / (hr_out[:-1] / D[:-1] + hr_in[1:] / D[1:])
         Ct = 1.0 / (ht_hi[:, :-1] / D[:, :-1] + ht_lo[:, 1:] / D[:, 1:])
@@ -435,7 +442,8 @@ def solve_pda(disk, T_mc, tally, visits, relerr, min_visits=30, max_rel_err=0.05
     kappa_R = np.asarray(kappa_R, np.float64).reshape(nr, nt)
     with np.errstate(divide="ignore"):
         D = np.where(disk.rho > 0, 1.0 / (3.0 * disk.rho * kappa_R), 0.0)
-    Cr, Ct = conductances(disk, D)
+    part = mask | dirichlet_mask(disk, mask, tally)
+    Cr, Ct = conductances(disk, D, part)
     u_bnd = np.where(mask, 0.0, T_mc ** 4)
     A, b, idx, has_dir = assemble(Cr, Ct, mask, u_bnd)
     info = dict(n_pda=int(mask.sum()), Cr=Cr, Ct=Ct, D=D, kappa_R=kappa_R, A=A, b=b, idx=idx)
@@ -460,7 +468,9 @@ def pda_adjoint(disk, u, mask, info, w):
     Cr, Ct = info["Cr"], info["Ct"]
     w = np.asarray(w, np.float64).reshape(nr, nt)
     g = np.zeros(int(mask.sum()))
-    g[:] = (w[mask] * 0.25 * u[mask] ** (-0.75))
+    um = u[mask]
+    with np.errstate(divide="ignore"):
+        g[:] = np.where(um > 0, w[mask] * 0.25 * np.abs(um) ** (-0.75), 0.0)
     lam_v = spla.spsolve(A.tocsc(), g) if g.size else g
     lam = np.zeros((nr, nt))
     lam[mask] = lam_v
@@ -481,9 +491,9 @@ def pda_adjoint(disk, u, mask, info, w):
         tb = np.where(act, dJdC * Ct ** 2 * ht_lo[:, 1:] / D[:, 1:] ** 2, 0.0)
     dJdD[:, :-1] += ta
     dJdD[:, 1:] += tb
-    grad_logrho = -D * dJdD
-    with np.errstate(divide="ignore", invalid="ignore"):
-        grad_kR = np.where(disk.rho > 0, -D / info["kappa_R"] * dJdD, 0.0)
+    with np.errstate(invalid="ignore"):
+        grad_logrho = np.where(dJdD != 0, -D * dJdD, 0.0)
+        grad_kR = np.where(dJdD != 0, -D / info["kappa_R"] * dJdD, 0.0)
     return grad_logrho, grad_kR, lam
 
 

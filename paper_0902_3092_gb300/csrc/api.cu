@@ -143,11 +143,19 @@ __global__ void k_temperature(int n, const unsigned long long* __restrict__ tall
     T[c] = pow(q / (4.0 * MCRT_SIGMA * kabs0), 0.25);
     return;
   }
-  // initial guess on the log-spaced grid, then bracketed Newton on the exact bin integrals
-  const float lq = (float)log(q);
-  int k = 1;
-  while (k + 1 < nT && lQk[k + 1] <= lq) ++k;
-  double Tk = Tmin * exp((k - 1) * dlnT);
+  // initial guess on the log-spaced grid (beyond it Q ~ T^4), then bracketed Newton on the exact
+  // bin integrals
+  const double lq = log(q);
+  double Tk;
+  if (lq < (double)lQk[1]) {
+    Tk = Tmin * exp(0.25 * (lq - (double)lQk[1]));
+  } else if (lq >= (double)lQk[nT - 1]) {
+    Tk = Tmin * exp((nT - 2) * dlnT) * exp(0.25 * (lq - (double)lQk[nT - 1]));
+  } else {
+    int k = 1;
+    while (k + 1 < nT && (double)lQk[k + 1] <= lq) ++k;
+    Tk = Tmin * exp((k - 1) * dlnT);
+  }
   double lo = 0.0, hi = INFINITY;
   double x = Tk;
   for (int it = 0; it < 100; ++it) {
@@ -601,6 +609,8 @@ static void stats_from(const unsigned long long* c, mcrt_run_stats* s, double se
   s->deposit_sum = c[C_DEPSUM];
   s->error_flags = (uint32_t)c[C_ERR];
   s->seconds = secs;
+  s->max_packet_steps = c[C_MAXSTEPS];
+  s->longest_packet = c[C_LONGEST] & 0xffffffull;
 }
 
 // events = scatterings + absorptions + MRW jumps (the kernel counts the three separately)

@@ -81,17 +81,20 @@ __device__ __forceinline__ double block_sum_d(double v, double* sh) {
 }
 
 // ---------------------------------------------------------------------------------------------- setup
-// PDA cells: dust, optically thick (rho chi'_max ell_c >= min_tau, ell_c = min(dr, r_c dtheta)), and
-// fewer than min_visits entries or a statistical error above max_rel
+// PDA cells (2): dust, optically thick (rho chi'_max ell_c >= min_tau, ell_c = min(dr, r_c dtheta)), and
+// fewer than min_visits entries or a statistical error above max_rel. Dirichlet cells (1): the other
+// dusty cells that absorbed energy. Dust-free cells and thin cells that absorbed nothing carry no
+// temperature and no flux (0).
 __global__ void k_mask(int n, const double* rho, const double* ell, double chi_max, double min_tau,
-                       const unsigned long long* visits, const double* relerr, int min_visits, double max_rel,
-                       signed char* mask, double* red) {
+                       const unsigned long long* visits, const double* relerr, const unsigned long long* tally,
+                       int min_visits, double max_rel, signed char* mask, double* red) {
   const int c = blockIdx.x * blockDim.x + threadIdx.x;
   if (c >= n) return;
   signed char m = 0;
   if (rho[c] > 0) {
     const bool thick = rho[c] * chi_max * ell[c] >= min_tau;
-    m = (thick && (visits[c] < (unsigned long long)min_visits || relerr[c] > max_rel)) ? 2 : 1;
+    if (thick && (visits[c] < (unsigned long long)min_visits || relerr[c] > max_rel)) m = 2;
+    else if (tally[c] > 0ull) m = 1;
   }
   mask[c] = m;
   if (m == 2) atomicAdd(red + 0, 1.0);
@@ -148,8 +151,9 @@ __global__ void k_kappaR(int n, const double* rho, const unsigned long long* tal
   kR[c] = rosseland(lam_e, chip, nlam, Tc);
 }
 
-__global__ void k_cond(int nr, int nt, const double* rho, const double* kR, const double* hr_in, const double* hr_out,
-                       const double* ht_lo, const double* ht_hi, double* D, double* Cr, double* Ct) {
+__global__ void k_cond(int nr, int nt, const signed char* mask, const double* rho, const double* kR,
+                       const double* hr_in, const double* hr_out, const double* ht_lo, const double* ht_hi, double* D,
+                       double* Cr, double* Ct) {
   const int c = blockIdx.x * blockDim.x + threadIdx.x;
   if (c >= nr * nt) return;
   const int i = c / nt, j = c - i * nt;
@@ -157,8 +161,11 @@ __global__ void k_cond(int nr, int nt, const double* rho, const double* kR, cons
   const double Dc = Dof(c);
   D[c] = Dc;
   double cr = 0.0, ct = 0.0;
-  if (i + 1 < nr && rho[c] > 0 && rho[c + nt] > 0) cr = 1.0 / (hr_out[c] / Dc + hr_in[c + nt] / Dof(c + nt));
-  if (j + 1 < nt && rho[c] > 0 && rho[c + 1] > 0) ct = 1.0 / (ht_hi[c] / Dc + ht_lo[c + 1] / Dof(c + 1));
+  // faces that carry flux: both cells take part and at least one is a PDA cell
+  if (i + 1 < nr && mask[c] && mask[c + nt] && (mask[c] == 2 || mask[c + nt] == 2))
+    cr = 1.0 / (hr_out[c] / Dc + hr_in[c + nt] / Dof(c + nt));
+  if (j + 1 < nt && mask[c] && mask[c + 1] && (mask[c] == 2 || mask[c + 1] == 2))
+    ct = 1.0 / (ht_hi[c] / Dc + ht_lo[c + 1] / Dof(c + 1));
   Cr[c] = cr;
   Ct[c] = ct;
 }
@@ -318,7 +325,7 @@ __global__ void k_tpda(int n, const signed char* mask, const double* u, const do
 __global__ void k_adj_rhs(int n, const signed char* mask, const double* w, const double* u, double* g, double* lam) {
   const int c = blockIdx.x * blockDim.x + threadIdx.x;
   if (c >= n) return;
-  g[c] = (mask[c] == 2) ? w[c] * 0.25 * pow(fmax(u[c], 1e-300), -0.75) : 0.0;
+  g[c] = (mask[c] == 2 && u[c] > 0.0) ? w[c] * 0.25 * pow(u[c], -0.75) : 0.0;
   lam[c] = 0.0;
 }
 
@@ -344,8 +351,8 @@ __global__ void k_grad(int nr, int nt, const signed char* mask, const double* Cr
     if (i + 1 < nr) face(c + nt, Cr[c], hr_out[c]);
     if (j > 0) face(c - 1, Ct[c - 1], ht_lo[c]);
     if (j + 1 < nt) face(c + 1, Ct[c], ht_hi[c]);
-    if (g_lr) g_lr[c] = -Dc * s;
-    if (g_kr) g_kr[c] = -Dc / kR[c] * s;
+    if (g_lr) g_lr[c] = s != 0.0 ? -Dc * s : 0.0;
+    if (g_kr) g_kr[c] = s != 0.0 ? -Dc / kR[c] * s : 0.0;
   } else {
     if (g_lr) g_lr[c] = 0.0;
     if (g_kr) g_kr[c] = 0.0;
@@ -463,8 +470,8 @@ static mcrt_status refine_solve(mcrt_disk* d, const mcrt_pda_opts* o, double* x,
   float *y = P->y.as<float>(), *r = P->r.as<float>(), *Ap = P->Ap.as<float>();
   float* pb[2] = {P->p0.as<float>(), P->p1.as<float>()};
   const double tol2_in = o->inner_tol * o->inner_tol;
-  double norm_b = -1.0;
-  int total_iters = 0;
+  double norm_b = -1.0, best = INFINITY;
+  int total_iters = 0, stall = 0;
   const int chunk = 32;
   for (int outer = 0; outer <= o->max_outer; ++outer) {
     CK(cudaMemsetAsync(red + 4, 0, 8, st), "memset");
@@ -477,6 +484,14 @@ static mcrt_status refine_solve(mcrt_disk* d, const mcrt_pda_opts* o, double* x,
     if (norm_b < 0) norm_b = rn;  // first residual: x = 0 on the PDA cells, so this is |S b_total|
     if (!(rn == rn)) return set_error(d, MCRT_ENOTCONV, "PDA residual is not finite");
     if (rn <= o->tol * norm_b || rn == 0.0) {
+      if (iters_out) *iters_out = total_iters;
+      return MCRT_OK;
+    }
+    // FP64 rounding floor of the residual: no halving for three refinement steps below 1e-8
+    if (rn < 0.5 * best) {
+      best = rn;
+      stall = 0;
+    } else if (++stall >= 3 && best <= 1e-8 * norm_b) {
       if (iters_out) *iters_out = total_iters;
       return MCRT_OK;
     }
@@ -532,7 +547,7 @@ void mcrt_default_pda_opts(mcrt_pda_opts* o) {
   o->max_rel_err = 0.05;
   o->tol = 1e-12;
   o->inner_tol = 1e-5;
-  o->max_outer = 20;
+  o->max_outer = 50;
   o->max_inner = 20000;
   o->min_cell_tau = 1.0;
   o->kappa_R = nullptr;
@@ -561,8 +576,9 @@ mcrt_status mcrt_solve_pda(mcrt_disk* d, const mcrt_pda_opts* o, int* out_n, int
   double chi_max = 0.0;
   for (int b = 0; b < d->nlam; ++b) chi_max = std::max(chi_max, d->kabs[b] + (1.0 - d->g[b]) * d->ksca[b]);
   k_mask<<<nblk(n), 256, 0, st>>>(n, rho, P->ell.as<double>(), chi_max, o->min_cell_tau,
-                                  d->visits.as<unsigned long long>(), d->relerr.as<double>(), o->min_visits,
-                                  o->max_rel_err, P->mask.as<signed char>(), red);
+                                  d->visits.as<unsigned long long>(), d->relerr.as<double>(),
+                                  d->tally.as<unsigned long long>(), o->min_visits, o->max_rel_err,
+                                  P->mask.as<signed char>(), red);
   k_bnd_mean<<<nblk(n), 256, 0, st>>>(nr, nt, P->mask.as<signed char>(), d->T_mc.as<double>(), red);
   DBuf over;
   if (o->kappa_R) {
@@ -576,7 +592,7 @@ mcrt_status mcrt_solve_pda(mcrt_disk* d, const mcrt_pda_opts* o, int* out_n, int
                                     d->gray ? 1 : 0, (double)(d->kabs[0] + (1.0 - d->g[0]) * d->ksca[0]), d->nlam,
                                     d->lam_e_d.as<double>(), d->chip_d.as<double>(), over.as<double>(),
                                     P->kR.as<double>());
-  k_cond<<<nblk(n), 256, 0, st>>>(nr, nt, rho, P->kR.as<double>(), P->hr_in.as<double>(), P->hr_out.as<double>(),
+  k_cond<<<nblk(n), 256, 0, st>>>(nr, nt, P->mask.as<signed char>(), rho, P->kR.as<double>(), P->hr_in.as<double>(), P->hr_out.as<double>(),
                                   P->ht_lo.as<double>(), P->ht_hi.as<double>(), P->D.as<double>(), P->Cr.as<double>(),
                                   P->Ct.as<double>());
   k_diag<<<nblk(n), 256, 0, st>>>(nr, nt, P->mask.as<signed char>(), P->Cr.as<double>(), P->Ct.as<double>(),

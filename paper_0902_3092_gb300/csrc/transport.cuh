@@ -57,6 +57,7 @@ struct Pkt {
   unsigned long long events, steps;
   unsigned xcross;  // face crossings since the last interaction (guard against zero-length ping-pong)
   Rng rng;
+  unsigned long long id;
   int pend_mode;  // 0: bin known; 1: BW bin of (pend_cell, pend_tally -> +EUNIT); 2: exit bin at pend_tally
   int pend_cell;
   float pend_u;
@@ -278,6 +279,7 @@ template <class R, bool TRACE>
 __device__ void launch_packet(const KParams<R>& P, const DevModel<R>& M, Pkt<R>& s, unsigned long long k, int tslot,
                               Acc& acc) {
   s.rng.init(P.seed, M.model_id, k);
+  s.id = k;
   s.lam = sample_star(M, U(s));
   iso_dir(s, s.ux, s.uy, s.uz);
   s.px = s.py = s.pz = (R)0;
@@ -497,6 +499,24 @@ __device__ bool step(const KParams<R>& P, const DevModel<R>& M, Pkt<R>& s, Acc& 
   return true;
 }
 
+// per-lane record of the longest packet (flushed with the counters)
+template <class R>
+__device__ __forceinline__ void note_end(const Pkt<R>& s, Acc& acc) {
+  const unsigned long long st = s.steps;
+  if (st > acc.v[C_MAXSTEPS]) acc.v[C_MAXSTEPS] = st;
+  const unsigned long long packed = (st << 24) | (s.id & 0xffffffull);
+  if (packed > acc.v[C_LONGEST]) acc.v[C_LONGEST] = packed;
+}
+
+__device__ __forceinline__ unsigned long long warp_max(unsigned long long v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    const unsigned long long w = __shfl_xor_sync(0xffffffffu, v, o);
+    v = w > v ? w : v;
+  }
+  return v;
+}
+
 __device__ __forceinline__ unsigned long long warp_sum(unsigned long long v) {
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
@@ -507,17 +527,24 @@ template <class R>
 __device__ __forceinline__ void flush(const DevModel<R>& M, Acc& acc, bool warp_uniform) {
   for (int i = 0; i < C_NCNT; ++i) {
     unsigned long long v = acc.v[i];
+    const bool is_max = (i == C_MAXSTEPS || i == C_LONGEST);
     if (warp_uniform) {
       if (i == C_ERR) {
         v = __reduce_or_sync(0xffffffffu, (unsigned)v);
+      } else if (is_max) {
+        v = warp_max(v);
       } else {
         v = warp_sum(v);
       }
       if ((threadIdx.x & 31) == 0 && v) {
-        if (i == C_ERR) atomicOr(M.cnt + i, v); else atomicAdd(M.cnt + i, v);
+        if (i == C_ERR) atomicOr(M.cnt + i, v);
+        else if (is_max) atomicMax(M.cnt + i, v);
+        else atomicAdd(M.cnt + i, v);
       }
     } else if (v) {
-      if (i == C_ERR) atomicOr(M.cnt + i, v); else atomicAdd(M.cnt + i, v);
+      if (i == C_ERR) atomicOr(M.cnt + i, v);
+      else if (is_max) atomicMax(M.cnt + i, v);
+      else atomicAdd(M.cnt + i, v);
     }
     acc.v[i] = 0;
   }
@@ -578,6 +605,7 @@ __global__ void __launch_bounds__(512) transport_kernel(const KParams<R> P) {
     if (active) {
       const DevModel<R>& M = BATCH ? P.models[model] : P.m0;
       active = step<R, TRACE>(P, M, s, acc);
+      if (!active) note_end(s, acc);
     }
   }
   if (BATCH) flush(P.models[model], acc, false);

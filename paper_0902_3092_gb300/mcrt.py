@@ -50,7 +50,8 @@ class RunStats(C.Structure):
     _fields_ = [("packets", C.c_uint64), ("events", C.c_uint64), ("absorptions", C.c_uint64),
                 ("scatterings", C.c_uint64), ("crossings", C.c_uint64), ("mrw_jumps", C.c_uint64),
                 ("capped", C.c_uint64), ("escaped", C.c_uint64), ("deposit_sum", C.c_uint64),
-                ("error_flags", C.c_uint32), ("seconds", C.c_double)]
+                ("error_flags", C.c_uint32), ("seconds", C.c_double), ("max_packet_steps", C.c_uint64),
+                ("longest_packet", C.c_uint64)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -231,7 +232,7 @@ class Disk:
         _check(lib().mcrt_sed(self._h, int(n_incl), _dp(L)), self._h)
         return L.reshape(self.nlam, n_incl)
 
-    def solve_pda(self, min_visits=30, max_rel_err=0.05, tol=1e-12, inner_tol=1e-5, max_outer=20, max_inner=20000,
+    def solve_pda(self, min_visits=30, max_rel_err=0.05, tol=1e-12, inner_tol=1e-5, max_outer=50, max_inner=20000,
                   kappa_R=None, min_cell_tau=1.0):
         o = PdaOpts()
         lib().mcrt_default_pda_opts(C.byref(o))

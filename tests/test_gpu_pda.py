@@ -40,7 +40,11 @@ def state_for(d, T_wanted, pda_mask, n_total=10 ** 6):
     from oracle import oracle as O
     kP = d.opacity.kappa_abs[0]
     q = 4 * kP * O.SIGMA_SB * T_wanted ** 4  # gray estimate of L_abs / m; exact T is recomputed below
-    tally = np.where(d.rho > 0, np.maximum(np.floor(q * m * n_total * EUNIT / d.star.L) + 1, 1000 * EUNIT), 0)
+    op = d.opacity
+    chi_max = float(np.max(op.kappa_abs + (1 - op.g) * op.kappa_sca))
+    thick = d.rho * chi_max * O.cell_extent(d) >= 1.0
+    # thick cells outside the PDA region get >= 1000 packet energies, so their error is below 5 %
+    tally = np.where(thick, np.maximum(np.floor(q * m * n_total * EUNIT / d.star.L) + 1, 1000 * EUNIT), 0)
     tally = tally.astype(np.uint64)
     tally = np.where(pda_mask, 0, tally).astype(np.uint64)
     visits = np.where(pda_mask, 0, 1000).astype(np.uint64)
@@ -75,7 +79,8 @@ def test_pda_matches_oracle(M, oracle, kind):
     assert not np.any(mo & ~mask)
     mask = mo
     assert np.max(np.abs(Tg[mask] / To[mask] - 1)) < 1e-6
-    assert np.max(np.abs(Tg[~mask] - To[~mask])) <= 1e-12 * To.max()
+    fin = (~mask) & (To > 0)
+    assert np.allclose(Tg[fin], To[fin], rtol=1e-12, atol=0)
 
 
 @pytest.mark.parametrize("kind", ["gray", "nongray"])
