@@ -192,6 +192,31 @@ mcrt_status mcrt_restore(mcrt_disk *d, const void *buf, size_t len);
 mcrt_status mcrt_debug_uniforms(int device, uint64_t seed, uint32_t model, uint64_t packet, int n, double *out);
 mcrt_status mcrt_debug_mrw_x(int device, int n, const double *P0, double *x_out);
 
+/* PDA solve that allocates nothing (the paper has no counterpart: this is a deployment variant of
+ * mcrt_solve_pda's solver). Some callers may not allocate device memory once they are running -- a host
+ * framework that owns every device byte through its own pool, or a service that fixes its memory at
+ * start-up -- and mcrt_solve_pda allocates its working vectors on first use. This entry point takes the
+ * assembled system in the caller's device buffers and keeps its working vectors in one file-scope
+ * device array of fixed size; it never calls cudaMalloc or cudaFree.
+ *   device:     CUDA device whose copy of the array is used (made current by the call).
+ *   nr, ntheta: grid; nr * ntheta <= 131072, or MCRT_EINVAL.
+ *   mask_dev:   int8 per cell: 2 unknown (PDA) cell, 1 cell with a fixed value, 0 no flux.
+ *   Cr_dev:     conductance of the face between (ir, it) and (ir+1, it), per cell (last row unused).
+ *   Ct_dev:     conductance of the face between (ir, it) and (ir, it+1), per cell (last column unused).
+ *   u_dev:      T^4 per cell: fixed values on mask-1 cells (read), the solution on mask-2 cells
+ *               (written; their input values are the starting guess, normally 0).
+ *   opts:       tol, inner_tol, max_outer, max_inner (<= 20000); the other fields are not used.
+ *   cuda_stream: stream to run on (NULL: the legacy default stream). The call returns when the solve
+ *               has finished on that stream.
+ * The first call on a device looks up the device address of the array (cudaGetSymbolAddress) with that
+ * device current; make that first call before any stream capture on the device. Every call shares the
+ * one array and starts by clearing what must be zero, so calls that overlap on the GPU (two streams,
+ * two threads) race and must not be issued. Errors: MCRT_EINVAL for sizes beyond the limit, NULL
+ * pointers or a PDA cell without a conducting face; MCRT_ENOTCONV as mcrt_solve_pda. */
+mcrt_status mcrt_pda_solve_static(int device, int nr, int ntheta, const signed char *mask_dev,
+                                  const double *Cr_dev, const double *Ct_dev, double *u_dev,
+                                  const mcrt_pda_opts *opts, void *cuda_stream, int *out_iters);
+
 /* Number of kernels this disk has launched since it was created (transport, temperature, PDA). */
 mcrt_status mcrt_launch_count(const mcrt_disk *d, uint64_t *n);
 

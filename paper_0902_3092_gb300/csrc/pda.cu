@@ -21,6 +21,7 @@
 #include <algorithm>
 #include <cmath>
 #include <cstring>
+#include <mutex>
 #include <vector>
 
 #include "internal.h"
@@ -676,3 +677,154 @@ mcrt_status mcrt_pda_adjoint(mcrt_disk* d, const double* w, double* g_lr, double
 }
 
 }  // extern "C"
+
+// ------------------------------------------------------------------------------------------------
+// PDA solve without allocation: the same FP64-refined FP32 CG, on a system the caller supplies in
+// its own device buffers, with all working vectors in one file-scope device array. For callers that
+// may not allocate device memory after start-up (a host framework that owns every device byte
+// through its own pool, or a service that fixes its memory at initialisation), so that no call here
+// ever reaches cudaMalloc/cudaFree.
+// ------------------------------------------------------------------------------------------------
+namespace {
+constexpr long long kStaticMaxCells = 131072;  // nr * ntheta limit of mcrt_pda_solve_static
+constexpr int kStaticMaxInner = 20000;          // CG iterations per refinement step
+constexpr size_t kStaticSc = 2 * (size_t)kStaticMaxInner + 8;
+// layout: dis, rs (f64 per cell) | ar, at, y, r, p0, p1, Ap (f32 per cell) | sc, red (f64)
+constexpr size_t kStaticBytes = 2 * 8 * kStaticMaxCells + 7 * 4 * kStaticMaxCells + 8 * (kStaticSc + 16);
+std::mutex g_static_mu;
+void* g_static_addr[64] = {};
+}  // namespace
+
+static __device__ __align__(256) unsigned char g_pda_static_scratch[kStaticBytes];
+
+namespace mcrt {
+__global__ void k_static_dis(int nr, int nt, const signed char* mask, const double* Cr, const double* Ct, double* dis,
+                             double* red) {
+  const int c = blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= nr * nt) return;
+  const int i = c / nt, j = c - i * nt;
+  if (mask[c] != 2) {
+    dis[c] = 0.0;
+    return;
+  }
+  double dsum = 0.0;
+  if (i > 0 && mask[c - nt]) dsum += Cr[c - nt];
+  if (i + 1 < nr && mask[c + nt]) dsum += Cr[c];
+  if (j > 0 && mask[c - 1]) dsum += Ct[c - 1];
+  if (j + 1 < nt && mask[c + 1]) dsum += Ct[c];
+  if (dsum > 0) {
+    dis[c] = 1.0 / sqrt(dsum);
+  } else {
+    dis[c] = 0.0;
+    atomicAdd(red + 3, 1.0);
+  }
+}
+}  // namespace mcrt
+
+extern "C" mcrt_status mcrt_pda_solve_static(int device, int nr, int ntheta, const signed char* mask_dev,
+                                             const double* Cr_dev, const double* Ct_dev, double* u_dev,
+                                             const mcrt_pda_opts* o, void* cuda_stream, int* out_iters) {
+  mcrt_disk* d = nullptr;  // errors go to the thread's last-error message
+  if (!mask_dev || !Cr_dev || !Ct_dev || !u_dev || !o) return set_error(nullptr, MCRT_EINVAL, "NULL argument");
+  if (nr < 1 || ntheta < 1 || (long long)nr * ntheta > kStaticMaxCells)
+    return set_error(nullptr, MCRT_EINVAL,
+                     "nr * ntheta must be between 1 and 131072 for mcrt_pda_solve_static (its fixed scratch size)");
+  if (!(o->tol > 0) || !(o->inner_tol > 0 && o->inner_tol < 1) || o->max_outer < 1 || o->max_inner < 1)
+    return set_error(nullptr, MCRT_EINVAL, "bad PDA options");
+  if (o->max_inner > kStaticMaxInner)
+    return set_error(nullptr, MCRT_EINVAL, "max_inner must be <= 20000 for mcrt_pda_solve_static");
+  if (device < 0 || device >= 64) return set_error(nullptr, MCRT_EINVAL, "device index out of range");
+  CK(cudaSetDevice(device), "cudaSetDevice");
+  unsigned char* base = nullptr;
+  {
+    std::lock_guard<std::mutex> lock(g_static_mu);
+    if (!g_static_addr[device]) {
+      void* a = nullptr;
+      const cudaError_t e = cudaGetSymbolAddress(&a, g_pda_static_scratch);
+      if (e != cudaSuccess) return cuda_fail(nullptr, e, "cudaGetSymbolAddress of the PDA scratch array");
+      g_static_addr[device] = a;
+    }
+    base = static_cast<unsigned char*>(g_static_addr[device]);
+  }
+  const int n = nr * ntheta;
+  const size_t N = (size_t)kStaticMaxCells;
+  double* dis = reinterpret_cast<double*>(base);
+  double* rs = dis + N;
+  float* ar = reinterpret_cast<float*>(rs + N);
+  float* at = ar + N;
+  float* y = at + N;
+  float* r = y + N;
+  float* pb[2] = {r + N, r + 2 * N};
+  float* Ap = r + 3 * N;
+  double* sc = reinterpret_cast<double*>(Ap + N);
+  double* red = sc + kStaticSc;
+  cudaStream_t st = (cudaStream_t)cuda_stream;
+  const int nt = ntheta;
+  // scratch keeps the previous call's contents: clear what must start at zero
+  CK(cudaMemsetAsync(red, 0, 16 * sizeof(double), st), "memset");
+  k_static_dis<<<nblk(n), 256, 0, st>>>(nr, nt, mask_dev, Cr_dev, Ct_dev, dis, red);
+  k_scaled<<<nblk(n), 256, 0, st>>>(nr, nt, mask_dev, Cr_dev, Ct_dev, dis, ar, at);
+  double singular = 0.0;
+  CK(cudaMemcpyAsync(&singular, red + 3, sizeof(double), cudaMemcpyDeviceToHost, st), "copy");
+  CK(cudaStreamSynchronize(st), "synchronize");
+  CK(cudaGetLastError(), "PDA kernels");
+  if (singular > 0) return set_error(nullptr, MCRT_EINVAL, "a PDA cell has no conducting face (singular system)");
+  const double tol2_in = o->inner_tol * o->inner_tol;
+  double norm_b = -1.0, best = INFINITY;
+  int total_iters = 0, stall = 0;
+  const int chunk = 32;
+  double h[2 * chunk + 2];
+  for (int outer = 0; outer <= o->max_outer; ++outer) {
+    CK(cudaMemsetAsync(red + 4, 0, sizeof(double), st), "memset");
+    k_resid64<<<nblk(n), 256, 0, st>>>(nr, nt, mask_dev, Cr_dev, Ct_dev, dis, u_dev, nullptr, rs, red, 4);
+    double rn2 = 0.0;
+    CK(cudaMemcpyAsync(&rn2, red + 4, sizeof(double), cudaMemcpyDeviceToHost, st), "copy");
+    CK(cudaStreamSynchronize(st), "synchronize");
+    const double rn = std::sqrt(rn2);
+    if (norm_b < 0) norm_b = rn;
+    if (!(rn == rn)) return set_error(nullptr, MCRT_ENOTCONV, "PDA residual is not finite");
+    if (rn <= o->tol * norm_b || rn == 0.0) {
+      if (out_iters) *out_iters = total_iters;
+      return MCRT_OK;
+    }
+    if (rn < 0.5 * best) {
+      best = rn;
+      stall = 0;
+    } else if (++stall >= 3 && best <= 1e-8 * norm_b) {
+      if (out_iters) *out_iters = total_iters;
+      return MCRT_OK;
+    }
+    if (outer == o->max_outer) break;
+    CK(cudaMemsetAsync(sc, 0, sizeof(double) * kStaticSc, st), "memset");
+    k_start<<<nblk(n), 256, 0, st>>>(n, mask_dev, rs, 1.0 / rn, y, r, pb[1], sc);
+    int k = 0;
+    bool conv = false;
+    while (k < o->max_inner && !conv) {
+      const int k0 = k;
+      const int kend = std::min(k + chunk, o->max_inner);
+      for (; k < kend; ++k) {
+        k_cg_a<<<nblk(n), 256, 0, st>>>(nr, nt, mask_dev, ar, at, r, pb[(k + 1) & 1], pb[k & 1], Ap, sc, k, tol2_in);
+        k_cg_b<<<nblk(n), 256, 0, st>>>(n, mask_dev, pb[k & 1], Ap, y, r, sc, k, tol2_in);
+      }
+      // rr_0 and rr_{k0..k}
+      double rr0 = 0.0;
+      CK(cudaMemcpyAsync(&rr0, sc, sizeof(double), cudaMemcpyDeviceToHost, st), "copy");
+      CK(cudaMemcpyAsync(h, sc + 2 * k0, sizeof(double) * (2 * (size_t)(k - k0) + 1), cudaMemcpyDeviceToHost, st),
+         "copy");
+      CK(cudaStreamSynchronize(st), "synchronize");
+      for (int kk = k0; kk <= k; ++kk) {
+        const double v = h[2 * (kk - k0)];
+        if ((kk > 0 || k0 > 0) && (v <= tol2_in * rr0 || !(v == v))) {
+          conv = true;
+          total_iters += kk;
+          break;
+        }
+      }
+    }
+    if (!conv) total_iters += k;
+    k_update<<<nblk(n), 256, 0, st>>>(n, mask_dev, dis, y, rn, u_dev);
+    CK(cudaGetLastError(), "PDA kernels");
+  }
+  if (out_iters) *out_iters = total_iters;
+  return set_error(nullptr, MCRT_ENOTCONV, "PDA solve did not reach its tolerance");
+}

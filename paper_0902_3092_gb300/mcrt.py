@@ -22,7 +22,8 @@ EXPORTS = ["mcrt_disk_create", "mcrt_set_opacity", "mcrt_default_run_opts", "mcr
            "mcrt_reset", "mcrt_temperatures", "mcrt_temperatures_dev", "mcrt_get_tallies", "mcrt_sed",
            "mcrt_default_pda_opts", "mcrt_solve_pda", "mcrt_pda_adjoint", "mcrt_pda_adjoint_dev",
            "mcrt_trace_packets", "mcrt_checkpoint", "mcrt_restore", "mcrt_debug_uniforms", "mcrt_debug_mrw_x",
-           "mcrt_disk_info", "mcrt_launch_count", "mcrt_last_error", "mcrt_disk_destroy"]
+           "mcrt_pda_solve_static", "mcrt_disk_info", "mcrt_launch_count", "mcrt_last_error",
+           "mcrt_disk_destroy"]
 
 
 class McrtError(RuntimeError):
@@ -99,6 +100,8 @@ def lib():
         "mcrt_debug_mrw_x": (st, [C.c_int, C.c_int, pd, pd]),
         "mcrt_disk_info": (st, [P, C.POINTER(C.c_int), C.POINTER(C.c_int), C.POINTER(C.c_int)]),
         "mcrt_launch_count": (st, [P, C.POINTER(C.c_uint64)]),
+        "mcrt_pda_solve_static": (st, [C.c_int, C.c_int, C.c_int, P, P, P, P, C.POINTER(PdaOpts), P,
+                                       C.POINTER(C.c_int)]),
         "mcrt_last_error": (C.c_char_p, [P]),
         "mcrt_disk_destroy": (None, [P]),
     }
@@ -283,6 +286,18 @@ def run_batch(disks, n_packets, seed=1, **kw):
     stats = (RunStats * n)()
     _check(lib().mcrt_run_batch(hs, n, _up(npk), int(seed), C.byref(o), stats))
     return [s.as_dict() for s in stats]
+
+
+def pda_solve_static(nr, ntheta, mask_ptr, Cr_ptr, Ct_ptr, u_ptr, device=0, stream=None, tol=1e-12,
+                     inner_tol=1e-5, max_outer=50, max_inner=20000):
+    """PDA solve on caller-owned device buffers with no device allocation (see include/mcrt.h)."""
+    o = PdaOpts()
+    lib().mcrt_default_pda_opts(C.byref(o))
+    o.tol, o.inner_tol, o.max_outer, o.max_inner = tol, inner_tol, max_outer, max_inner
+    it = C.c_int()
+    _check(lib().mcrt_pda_solve_static(int(device), int(nr), int(ntheta), mask_ptr, Cr_ptr, Ct_ptr, u_ptr,
+                                        C.byref(o), stream, C.byref(it)))
+    return it.value
 
 
 def debug_uniforms(seed, model, packet, n, device=0):
