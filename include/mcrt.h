@@ -123,6 +123,24 @@ mcrt_status mcrt_run_photons(mcrt_disk *d, uint64_t n_packets, uint64_t seed, ui
 mcrt_status mcrt_run_batch(mcrt_disk *const *disks, int n, const uint64_t *n_packets, uint64_t seed,
                            const mcrt_run_opts *opts, mcrt_run_stats *stats);
 
+/* A prepared batch: many disks (uneven grids and packet budgets) transported by one persistent launch
+ * over a shared packet queue, captured once as a CUDA graph and replayed. Disk i draws from the Philox
+ * counter (block, model i, k), k = 0 .. n_packets[i]-1, and its packet energy is L_star / n_packets[i].
+ * When opts->block_size == 0 the batch is autotuned on creation: block size (128, 256, 512) and refill
+ * interval (1, 4, 16) are timed on a short run (about 5 % of the packets) and the fastest is kept;
+ * the tuning runs are then removed again by zeroing the disks' tallies. All disks must share one device;
+ * the batch runs on the first disk's stream and must be destroyed before the disks. */
+typedef struct mcrt_batch mcrt_batch;
+mcrt_status mcrt_batch_create(mcrt_disk *const *disks, int n, const uint64_t *n_packets, const mcrt_run_opts *opts,
+                              mcrt_batch **out);
+/* Replays the graph with `seed` (synchronous); tallies accumulate like mcrt_run_photons. stats: n entries
+ * or NULL. */
+mcrt_status mcrt_batch_run(mcrt_batch *b, uint64_t seed, mcrt_run_stats *stats);
+/* The launch configuration chosen (block size, refill interval, grid) and the tuning time (s). */
+mcrt_status mcrt_batch_config(const mcrt_batch *b, int *block_size, int *refill_interval, int *grid,
+                              double *tune_seconds);
+void mcrt_batch_destroy(mcrt_batch *b);
+
 /* Zeroes the tallies, visit counts and spectrum. */
 mcrt_status mcrt_reset(mcrt_disk *d);
 
@@ -155,6 +173,9 @@ typedef struct {
                               min(dr, r dtheta) >= min_cell_tau (1.0); diffusion needs optical depth */
   const double *kappa_R;   /* optional host array nr*ntheta: Rosseland extinction (cm^2/g) entering
                               D = 1/(3 rho kappa_R); NULL: from the dust at the MC temperature */
+  const double *rho;       /* optional host array nr*ntheta: density (g/cm^3) entering D only; the PDA
+                              region and the Monte Carlo boundary values stay those of the disk.
+                              NULL: the disk's density. Used to differentiate with respect to rho. */
 } mcrt_pda_opts;
 
 void mcrt_default_pda_opts(mcrt_pda_opts *o);

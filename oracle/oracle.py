@@ -427,7 +427,8 @@ def check_components(A, b_has_dirichlet):
     return bool(ok.all())
 
 
-def solve_pda(disk, T_mc, tally, visits, relerr, min_visits=30, max_rel_err=0.05, kappa_R=None, min_cell_tau=1.0):
+def solve_pda(disk, T_mc, tally, visits, relerr, min_visits=30, max_rel_err=0.05, kappa_R=None, min_cell_tau=1.0,
+              rho_D=None):
     """Partial diffusion approximation, Sect. 2.2.1 (Eq. 4): returns (T_final, mask, u, info)."""
     import scipy.sparse.linalg as spla
     nr, nt = disk.nr, disk.ntheta
@@ -440,8 +441,9 @@ def solve_pda(disk, T_mc, tally, visits, relerr, min_visits=30, max_rel_err=0.05
         kappa_R = np.vectorize(lambda t: rosseland_chi(disk, t))(Tref) if not disk.opacity.is_gray() \
             else np.full((nr, nt), rosseland_chi(disk, 0.0))
     kappa_R = np.asarray(kappa_R, np.float64).reshape(nr, nt)
-    with np.errstate(divide="ignore"):
-        D = np.where(disk.rho > 0, 1.0 / (3.0 * disk.rho * kappa_R), 0.0)
+    rho_D = disk.rho if rho_D is None else np.asarray(rho_D, np.float64).reshape(nr, nt)
+    with np.errstate(divide="ignore", over="ignore"):
+        D = np.where(disk.rho > 0, 1.0 / (3.0 * rho_D * kappa_R), 0.0)
     part = mask | dirichlet_mask(disk, mask, tally)
     Cr, Ct = conductances(disk, D, part)
     u_bnd = np.where(mask, 0.0, T_mc ** 4)

@@ -3,6 +3,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <chrono>
 #include <cmath>
 #include <cstring>
 #include <mutex>
@@ -1000,6 +1001,260 @@ void mcrt_disk_destroy(mcrt_disk* d) {
   cudaStream_t st = d->own_stream ? d->stream : nullptr;
   delete d;  // frees the device buffers
   if (st) cudaStreamDestroy(st);
+}
+
+}  // extern "C"
+
+// ------------------------------------------------------------------------------------------------
+// prepared batches: descriptors built once, autotuned launch shape, CUDA graph replay
+// ------------------------------------------------------------------------------------------------
+struct mcrt_batch {
+  int n = 0, device = 0;
+  cudaStream_t stream = nullptr;
+  std::vector<mcrt_disk*> disks;
+  std::vector<uint64_t> npk;
+  unsigned long long total = 0;
+  DBuf models, queue;
+  KParams<float> P;
+  int block = 256, refill = 1, grid = 0;
+  double tune_seconds = 0.0;
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  cudaGraphNode_t knode = nullptr;
+  std::string err;
+  ~mcrt_batch() {
+    if (exec) cudaGraphExecDestroy(exec);
+    if (graph) cudaGraphDestroy(graph);
+  }
+};
+
+namespace {
+mcrt_status batch_fail(mcrt_batch* b, cudaError_t e, const char* what) {
+  mcrt_status s = cuda_fail(nullptr, e, what);
+  if (b) b->err = mcrt_last_error(nullptr);
+  return s;
+}
+
+// direct (uncaptured) launch of the batch kernel with a given shape, counters zeroed first
+cudaError_t batch_launch(mcrt_batch* b, const KParams<float>& P, int block, int grid) {
+  cudaError_t e;
+  for (auto* dk : b->disks) {
+    e = cudaMemsetAsync(dk->cnt.p, 0, C_NCNT * 8, b->stream);
+    if (e != cudaSuccess) return e;
+  }
+  e = cudaMemsetAsync(b->queue.p, 0, 8, b->stream);
+  if (e != cudaSuccess) return e;
+  return launch_transport<float>(P, false, true, grid, block, b->stream);
+}
+}  // namespace
+
+extern "C" {
+
+mcrt_status mcrt_batch_create(mcrt_disk* const* disks, int n, const uint64_t* n_packets, const mcrt_run_opts* o,
+                              mcrt_batch** out) {
+  if (!out) return set_error(nullptr, MCRT_EINVAL, "out is NULL");
+  *out = nullptr;
+  if (!disks || n <= 0 || !n_packets) return set_error(nullptr, MCRT_EINVAL, "bad batch arguments");
+  for (int i = 0; i < n; ++i) {
+    if (!disks[i]) return set_error(nullptr, MCRT_EINVAL, "NULL disk in batch");
+    if (!disks[i]->has_opacity) return set_error(disks[i], MCRT_ESTATE, "mcrt_set_opacity must come first");
+    if (disks[i]->device != disks[0]->device) return set_error(nullptr, MCRT_EINVAL, "disks on different devices");
+  }
+  mcrt_disk* d = disks[0];
+  mcrt_status s = check_opts(d, o);
+  if (s != MCRT_OK) return s;
+  if (o->precision != 32) return set_error(d, MCRT_EINVAL, "batches run the FP32 path");
+  CK(cudaSetDevice(d->device), "cudaSetDevice");
+  cudaError_t e;
+  const float* tab = mrw_table(d->device, &e);
+  if (!tab) return cuda_fail(d, e, "MRW table");
+  mcrt_batch* b = new (std::nothrow) mcrt_batch();
+  if (!b) return set_error(nullptr, MCRT_ENOMEM, "host allocation");
+  b->n = n;
+  b->device = d->device;
+  b->stream = d->stream;
+  b->disks.assign(disks, disks + n);
+  b->npk.assign(n_packets, n_packets + n);
+  std::vector<DevModel<float>> ms(n);
+  bool any_nongray = false;
+  for (int i = 0; i < n; ++i) {
+    disks[i]->n_total = (double)n_packets[i];
+    ms[i] = disks[i]->model32();
+    ms[i].first_id = 0;
+    ms[i].n_packets = n_packets[i];
+    ms[i].q_begin = b->total;
+    ms[i].model_id = (uint32_t)i;
+    b->total += n_packets[i];
+    any_nongray |= !disks[i]->gray;
+  }
+  e = b->models.alloc(sizeof(DevModel<float>) * n);
+  if (e == cudaSuccess) e = b->queue.alloc(8);
+  if (e == cudaSuccess)
+    e = cudaMemcpy(b->models.p, ms.data(), sizeof(DevModel<float>) * n, cudaMemcpyHostToDevice);
+  if (e != cudaSuccess) {
+    delete b;
+    return cuda_fail(d, e, "batch buffers");
+  }
+  std::memset(&b->P, 0, sizeof(b->P));
+  fill_params(b->P, o, 1, tab);
+  b->P.m0 = ms[0];
+  b->P.models = b->models.as<DevModel<float>>();
+  b->P.nmodels = n;
+  b->P.total = b->total;
+  b->P.queue = b->queue.as<unsigned long long>();
+  b->P.want_lam = (any_nongray || o->want_sed) ? 1 : 0;
+  int sms = 0;
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, d->device);
+  auto grid_for = [&](int block) { return sms * std::max(1, transport_blocks_per_sm<float>(false, true, block)); };
+  if (o->block_size) {
+    b->block = o->block_size;
+    b->refill = o->refill_interval > 0 ? o->refill_interval : 1;
+  } else {
+    // autotune on a short run of about 5 % of the packets (at least one per model)
+    std::vector<DevModel<float>> mt = ms;
+    unsigned long long tq = 0;
+    for (int i = 0; i < n; ++i) {
+      const unsigned long long k = std::max<unsigned long long>(1, n_packets[i] / 20);
+      mt[i].n_packets = k;
+      mt[i].q_begin = tq;
+      tq += k;
+    }
+    DBuf tm;
+    e = tm.alloc(sizeof(DevModel<float>) * n);
+    if (e == cudaSuccess) e = cudaMemcpy(tm.p, mt.data(), sizeof(DevModel<float>) * n, cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) {
+      delete b;
+      return cuda_fail(d, e, "tuning buffers");
+    }
+    KParams<float> T = b->P;
+    T.models = tm.as<DevModel<float>>();
+    T.total = tq;
+    cudaEvent_t e0, e1;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    float best = 1e30f;
+    const int blocks[3] = {128, 256, 512}, refills[3] = {1, 4, 16};
+    auto t_start = std::chrono::steady_clock::now();
+    for (int bi = 0; bi < 3; ++bi)
+      for (int ri = 0; ri < 3; ++ri) {
+        T.refill = refills[ri];
+        cudaEventRecord(e0, b->stream);
+        e = batch_launch(b, T, blocks[bi], grid_for(blocks[bi]));
+        cudaEventRecord(e1, b->stream);
+        if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+        if (e != cudaSuccess) {
+          cudaEventDestroy(e0);
+          cudaEventDestroy(e1);
+          delete b;
+          return cuda_fail(d, e, "autotune launch");
+        }
+        float ms_ = 0.f;
+        cudaEventElapsedTime(&ms_, e0, e1);
+        if (ms_ < best) {
+          best = ms_;
+          b->block = blocks[bi];
+          b->refill = refills[ri];
+        }
+      }
+    b->tune_seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t_start).count();
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    for (int i = 0; i < n; ++i) {
+      s = zero_tallies(disks[i]);
+      if (s != MCRT_OK) {
+        delete b;
+        return s;
+      }
+    }
+  }
+  b->P.refill = b->refill;
+  b->grid = grid_for(b->block);
+  // capture: counter resets + the persistent launch
+  e = cudaStreamSynchronize(b->stream);
+  if (e == cudaSuccess) e = cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal);
+  if (e == cudaSuccess) {
+    const cudaError_t el = batch_launch(b, b->P, b->block, b->grid);
+    e = cudaStreamEndCapture(b->stream, &b->graph);
+    if (el != cudaSuccess) e = el;
+  }
+  if (e == cudaSuccess) e = cudaGraphInstantiate(&b->exec, b->graph, 0);
+  if (e == cudaSuccess) {
+    size_t nn = 0;
+    e = cudaGraphGetNodes(b->graph, nullptr, &nn);
+    std::vector<cudaGraphNode_t> nodes(nn);
+    if (e == cudaSuccess) e = cudaGraphGetNodes(b->graph, nodes.data(), &nn);
+    for (size_t k = 0; e == cudaSuccess && k < nn; ++k) {
+      cudaGraphNodeType ty;
+      cudaGraphNodeGetType(nodes[k], &ty);
+      if (ty == cudaGraphNodeTypeKernel) b->knode = nodes[k];
+    }
+    if (e == cudaSuccess && !b->knode) e = cudaErrorInvalidValue;
+  }
+  if (e != cudaSuccess) {
+    delete b;
+    return cuda_fail(d, e, "graph capture");
+  }
+  *out = b;
+  return MCRT_OK;
+}
+
+mcrt_status mcrt_batch_run(mcrt_batch* b, uint64_t seed, mcrt_run_stats* stats) {
+  if (!b) return set_error(nullptr, MCRT_EINVAL, "batch is NULL");
+  mcrt_disk* d = b->disks[0];
+  CK(cudaSetDevice(b->device), "cudaSetDevice");
+  if (seed != b->P.seed) {
+    b->P.seed = seed;
+    cudaKernelNodeParams kp;
+    CK(cudaGraphKernelNodeGetParams(b->knode, &kp), "kernel node params");
+    void* args[1] = {&b->P};
+    kp.kernelParams = args;
+    CK(cudaGraphExecKernelNodeSetParams(b->exec, b->knode, &kp), "kernel node update");
+  }
+  cudaEvent_t e0, e1;
+  CK(cudaEventCreate(&e0), "event");
+  CK(cudaEventCreate(&e1), "event");
+  CK(cudaEventRecord(e0, b->stream), "event");
+  CK(cudaGraphLaunch(b->exec, b->stream), "graph launch");
+  CK(cudaEventRecord(e1, b->stream), "event");
+  std::vector<unsigned long long> c((size_t)b->n * C_NCNT);
+  for (int i = 0; i < b->n; ++i)
+    CK(cudaMemcpyAsync(&c[(size_t)i * C_NCNT], b->disks[i]->cnt.p, C_NCNT * 8, cudaMemcpyDeviceToHost, b->stream),
+       "copy");
+  cudaError_t e = cudaStreamSynchronize(b->stream);
+  float ms_ = 0.f;
+  if (e == cudaSuccess) cudaEventElapsedTime(&ms_, e0, e1);
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (e != cudaSuccess) return cuda_fail(d, e, "batch kernel");
+  d->launches++;
+  mcrt_status ret = MCRT_OK;
+  for (int i = 0; i < b->n; ++i) {
+    unsigned long long* ci = &c[(size_t)i * C_NCNT];
+    fix_events(ci);
+    b->disks[i]->packets_done += b->npk[i];
+    b->disks[i]->n_total = (double)b->npk[i];
+    b->disks[i]->have_T = false;
+    b->disks[i]->have_pda = false;
+    if (stats) stats_from(ci, &stats[i], ms_ * 1e-3);
+    if (ci[C_ERR] & kErrOverflow) ret = set_error(b->disks[i], MCRT_EOVERFLOW, "fixed-point tally overflow");
+  }
+  return ret;
+}
+
+mcrt_status mcrt_batch_config(const mcrt_batch* b, int* block, int* refill, int* grid, double* tune_seconds) {
+  if (!b) return set_error(nullptr, MCRT_EINVAL, "batch is NULL");
+  if (block) *block = b->block;
+  if (refill) *refill = b->refill;
+  if (grid) *grid = b->grid;
+  if (tune_seconds) *tune_seconds = b->tune_seconds;
+  return MCRT_OK;
+}
+
+void mcrt_batch_destroy(mcrt_batch* b) {
+  if (!b) return;
+  cudaSetDevice(b->device);
+  cudaStreamSynchronize(b->stream);
+  delete b;
 }
 
 }  // extern "C"

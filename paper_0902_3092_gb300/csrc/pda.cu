@@ -552,6 +552,7 @@ void mcrt_default_pda_opts(mcrt_pda_opts* o) {
   o->max_inner = 20000;
   o->min_cell_tau = 1.0;
   o->kappa_R = nullptr;
+  o->rho = nullptr;
 }
 
 mcrt_status mcrt_solve_pda(mcrt_disk* d, const mcrt_pda_opts* o, int* out_n, int* out_iters) {
@@ -593,7 +594,17 @@ mcrt_status mcrt_solve_pda(mcrt_disk* d, const mcrt_pda_opts* o, int* out_n, int
                                     d->gray ? 1 : 0, (double)(d->kabs[0] + (1.0 - d->g[0]) * d->ksca[0]), d->nlam,
                                     d->lam_e_d.as<double>(), d->chip_d.as<double>(), over.as<double>(),
                                     P->kR.as<double>());
-  k_cond<<<nblk(n), 256, 0, st>>>(nr, nt, P->mask.as<signed char>(), rho, P->kR.as<double>(), P->hr_in.as<double>(), P->hr_out.as<double>(),
+  DBuf rho_over;
+  const double* rhoD = rho;
+  if (o->rho) {
+    for (int c = 0; c < n; ++c)
+      if (d->rho[c] > 0 && !(o->rho[c] > 0 && std::isfinite(o->rho[c])))
+        return set_error(d, MCRT_EINVAL, "rho override must be positive where the disk has dust");
+    CK(rho_over.alloc((size_t)n * 8), "cudaMalloc");
+    CK(cudaMemcpyAsync(rho_over.p, o->rho, (size_t)n * 8, cudaMemcpyHostToDevice, st), "copy");
+    rhoD = rho_over.as<double>();
+  }
+  k_cond<<<nblk(n), 256, 0, st>>>(nr, nt, P->mask.as<signed char>(), rhoD, P->kR.as<double>(), P->hr_in.as<double>(), P->hr_out.as<double>(),
                                   P->ht_lo.as<double>(), P->ht_hi.as<double>(), P->D.as<double>(), P->Cr.as<double>(),
                                   P->Ct.as<double>());
   k_diag<<<nblk(n), 256, 0, st>>>(nr, nt, P->mask.as<signed char>(), P->Cr.as<double>(), P->Ct.as<double>(),

@@ -23,7 +23,7 @@ EXPORTS = ["mcrt_disk_create", "mcrt_set_opacity", "mcrt_default_run_opts", "mcr
            "mcrt_default_pda_opts", "mcrt_solve_pda", "mcrt_pda_adjoint", "mcrt_pda_adjoint_dev",
            "mcrt_trace_packets", "mcrt_checkpoint", "mcrt_restore", "mcrt_debug_uniforms", "mcrt_debug_mrw_x",
            "mcrt_pda_solve_static", "mcrt_disk_info", "mcrt_launch_count", "mcrt_last_error",
-           "mcrt_disk_destroy"]
+           "mcrt_disk_destroy", "mcrt_batch_create", "mcrt_batch_run", "mcrt_batch_config", "mcrt_batch_destroy"]
 
 
 class McrtError(RuntimeError):
@@ -61,7 +61,7 @@ class RunStats(C.Structure):
 class PdaOpts(C.Structure):
     _fields_ = [("min_visits", C.c_int), ("max_rel_err", C.c_double), ("tol", C.c_double), ("inner_tol", C.c_double),
                 ("max_outer", C.c_int), ("max_inner", C.c_int), ("min_cell_tau", C.c_double),
-                ("kappa_R", C.POINTER(C.c_double))]
+                ("kappa_R", C.POINTER(C.c_double)), ("rho", C.POINTER(C.c_double))]
 
 
 _lib = None
@@ -103,6 +103,11 @@ def lib():
         "mcrt_pda_solve_static": (st, [C.c_int, C.c_int, C.c_int, P, P, P, P, C.POINTER(PdaOpts), P,
                                        C.POINTER(C.c_int)]),
         "mcrt_last_error": (C.c_char_p, [P]),
+        "mcrt_batch_create": (st, [C.POINTER(P), C.c_int, pu, C.POINTER(RunOpts), C.POINTER(P)]),
+        "mcrt_batch_run": (st, [P, C.c_uint64, C.POINTER(RunStats)]),
+        "mcrt_batch_config": (st, [P, C.POINTER(C.c_int), C.POINTER(C.c_int), C.POINTER(C.c_int),
+                                   C.POINTER(C.c_double)]),
+        "mcrt_batch_destroy": (None, [P]),
         "mcrt_disk_destroy": (None, [P]),
     }
     for name, (res, args) in sig.items():
@@ -236,16 +241,19 @@ class Disk:
         return L.reshape(self.nlam, n_incl)
 
     def solve_pda(self, min_visits=30, max_rel_err=0.05, tol=1e-12, inner_tol=1e-5, max_outer=50, max_inner=20000,
-                  kappa_R=None, min_cell_tau=1.0):
+                  kappa_R=None, min_cell_tau=1.0, rho=None):
         o = PdaOpts()
         lib().mcrt_default_pda_opts(C.byref(o))
         o.min_visits, o.max_rel_err, o.tol, o.inner_tol = min_visits, max_rel_err, tol, inner_tol
         o.min_cell_tau = min_cell_tau
         o.max_outer, o.max_inner = max_outer, max_inner
-        kr = None
+        kr = rr = None
         if kappa_R is not None:
             kr = np.ascontiguousarray(kappa_R, np.float64).ravel()
             o.kappa_R = _dp(kr)
+        if rho is not None:
+            rr = np.ascontiguousarray(rho, np.float64).ravel()
+            o.rho = _dp(rr)
         npda, it = C.c_int(), C.c_int()
         _check(lib().mcrt_solve_pda(self._h, C.byref(o), C.byref(npda), C.byref(it)), self._h)
         return npda.value, it.value
@@ -298,6 +306,41 @@ def pda_solve_static(nr, ntheta, mask_ptr, Cr_ptr, Ct_ptr, u_ptr, device=0, stre
     _check(lib().mcrt_pda_solve_static(int(device), int(nr), int(ntheta), mask_ptr, Cr_ptr, Ct_ptr, u_ptr,
                                         C.byref(o), stream, C.byref(it)))
     return it.value
+
+
+class Batch:
+    """Disks transported together by one persistent launch, replayed from a captured CUDA graph."""
+
+    def __init__(self, disks, n_packets, **kw):
+        o = run_opts(**kw)
+        self.disks = list(disks)
+        self.n = len(self.disks)
+        hs = (C.c_void_p * self.n)(*[d.handle for d in self.disks])
+        self._npk = np.ascontiguousarray(n_packets, np.uint64)
+        h = C.c_void_p()
+        _check(lib().mcrt_batch_create(hs, self.n, _up(self._npk), C.byref(o), C.byref(h)))
+        self._h = h
+
+    def run(self, seed=1):
+        stats = (RunStats * self.n)()
+        _check(lib().mcrt_batch_run(self._h, int(seed), stats))
+        return [s.as_dict() for s in stats]
+
+    def config(self):
+        b, r, g, t = C.c_int(), C.c_int(), C.c_int(), C.c_double()
+        _check(lib().mcrt_batch_config(self._h, C.byref(b), C.byref(r), C.byref(g), C.byref(t)))
+        return {"block_size": b.value, "refill_interval": r.value, "grid": g.value, "tune_seconds": t.value}
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib().mcrt_batch_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 def debug_uniforms(seed, model, packet, n, device=0):
