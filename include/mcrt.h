@@ -89,10 +89,12 @@ typedef struct {
   double gamma;                 /* Eq. 11: MRW only where d_min > gamma / (rho chi_R) */
   int mrw_min_interactions;     /* interactions in the current cell before the MRW may start (20) */
   int mrw_exit_dir;             /* direction after a jump: 0 isotropic, 1 cosine-weighted outward */
-  uint64_t max_events_per_packet; /* a packet that exceeds this is dropped and counted as capped */
+  uint64_t max_events_per_packet; /* a packet that exceeds this is dropped and counted as capped
+                                     (values above 2^31 are taken as 2^31) */
   uint64_t n_total_packets;     /* packets of the whole run (energy per packet L_star / n_total);
                                    0 means the n_packets of this call */
-  int block_size;               /* threads per block of the transport kernel; 0: tuned default */
+  int block_size;               /* threads per block of the transport kernel (multiple of 32, <= 256);
+                                   0: tuned default */
   int refill_interval;          /* steps between refills of finished lanes; 0: tuned default */
   int want_sed;                 /* gray dust only: 0 skips the emission-bin sampling (no SED) */
 } mcrt_run_opts;
@@ -126,7 +128,7 @@ mcrt_status mcrt_run_batch(mcrt_disk *const *disks, int n, const uint64_t *n_pac
 /* A prepared batch: many disks (uneven grids and packet budgets) transported by one persistent launch
  * over a shared packet queue, captured once as a CUDA graph and replayed. Disk i draws from the Philox
  * counter (block, model i, k), k = 0 .. n_packets[i]-1, and its packet energy is L_star / n_packets[i].
- * When opts->block_size == 0 the batch is autotuned on creation: block size (128, 256, 512) and refill
+ * When opts->block_size == 0 the batch is autotuned on creation: block size (64, 128, 256) and refill
  * interval (1, 4, 16) are timed on a short run (about 5 % of the packets) and the fastest is kept;
  * the tuning runs are then removed again by zeroing the disks' tallies. All disks must share one device;
  * the batch runs on the first disk's stream and must be destroyed before the disks. */

@@ -571,8 +571,8 @@ static mcrt_status check_opts(mcrt_disk* d, const mcrt_run_opts* o) {
   if (o->mrw && !(o->gamma > 0)) return set_error(d, MCRT_EINVAL, "gamma must be > 0");
   if (o->mrw && o->mrw_min_interactions < 0) return set_error(d, MCRT_EINVAL, "mrw_min_interactions < 0");
   if (o->max_events_per_packet == 0) return set_error(d, MCRT_EINVAL, "max_events_per_packet must be > 0");
-  if (o->block_size && (o->block_size % 32 || o->block_size > 512))
-    return set_error(d, MCRT_EINVAL, "block_size must be a multiple of 32 up to 512");
+  if (o->block_size && (o->block_size % 32 || o->block_size > 256))
+    return set_error(d, MCRT_EINVAL, "block_size must be a multiple of 32 up to 256");
   if (o->refill_interval < 0) return set_error(d, MCRT_EINVAL, "refill_interval < 0");
   return MCRT_OK;
 }
@@ -585,8 +585,9 @@ static void fill_params(KParams<R>& P, const mcrt_run_opts* o, uint64_t seed, co
   P.refill = o->refill_interval > 0 ? o->refill_interval : 1;
   P.gamma = (R)o->gamma;
   P.seed = seed;
-  P.max_events = o->max_events_per_packet;
-  P.max_steps = 4ull * o->max_events_per_packet + 10000000ull;
+  // per-packet counters are 32-bit: caps above 2^31 events (4e9 steps) are clamped
+  P.max_events = std::min<unsigned long long>(o->max_events_per_packet, 1ull << 31);
+  P.max_steps = std::min<unsigned long long>(4ull * P.max_events + 10000000ull, 4000000000ull);
   P.mrw_tab = tab;
   P.mrw_t0 = kMrwT0;
   P.mrw_dt = kMrwDT;
@@ -646,7 +647,7 @@ static mcrt_status run_impl(mcrt_disk* d, uint64_t n_packets, uint64_t seed, uin
   }
   int dev_sms = 0;
   CK(cudaDeviceGetAttribute(&dev_sms, cudaDevAttrMultiProcessorCount, d->device), "attribute");
-  const int block = o->block_size ? o->block_size : (f64 ? 128 : 256);
+  const int block = o->block_size ? o->block_size : 128;
   cudaEvent_t ev0, ev1;
   CK(cudaEventCreate(&ev0), "event");
   CK(cudaEventCreate(&ev1), "event");
@@ -674,10 +675,10 @@ static mcrt_status run_impl(mcrt_disk* d, uint64_t n_packets, uint64_t seed, uin
         P.tr_n = tn.as<int32_t>();
         P.l_unit = d->l_unit;
       }
-      const int bps = transport_blocks_per_sm<double>(trace, false, block);
+      const int bps = transport_blocks_per_sm<double>(trace, false, d->gray, block);
       const long long want = (long long)((n_packets + block - 1) / block);
       const int grid = (int)std::max(1ll, std::min<long long>(want, (long long)dev_sms * std::max(1, bps)));
-      e = launch_transport<double>(P, trace, false, grid, block, d->stream);
+      e = launch_transport<double>(P, trace, false, d->gray, grid, block, d->stream);
       d->launches++;
     } else {
       KParams<float> P;
@@ -691,10 +692,10 @@ static mcrt_status run_impl(mcrt_disk* d, uint64_t n_packets, uint64_t seed, uin
       P.total = n_packets;
       P.queue = d->queue.as<unsigned long long>();
       P.want_lam = (!d->gray || o->want_sed) ? 1 : 0;
-      const int bps = transport_blocks_per_sm<float>(false, false, block);
+      const int bps = transport_blocks_per_sm<float>(false, false, d->gray, block);
       const long long want = (long long)((n_packets + block - 1) / block);
       const int grid = (int)std::max(1ll, std::min<long long>(want, (long long)dev_sms * std::max(1, bps)));
-      e = launch_transport<float>(P, false, false, grid, block, d->stream);
+      e = launch_transport<float>(P, false, false, d->gray, grid, block, d->stream);
       d->launches++;
     }
     if (e != cudaSuccess) {
@@ -796,15 +797,15 @@ mcrt_status mcrt_run_batch(mcrt_disk* const* disks, int n, const uint64_t* n_pac
   P.want_lam = (any_nongray || o->want_sed) ? 1 : 0;
   int dev_sms = 0;
   CK(cudaDeviceGetAttribute(&dev_sms, cudaDevAttrMultiProcessorCount, d->device), "attribute");
-  const int block = o->block_size ? o->block_size : 256;
-  const int bps = transport_blocks_per_sm<float>(false, true, block);
+  const int block = o->block_size ? o->block_size : 128;
+  const int bps = transport_blocks_per_sm<float>(false, true, false, block);
   const int grid = dev_sms * std::max(1, bps);
   cudaEvent_t ev0, ev1;
   CK(cudaEventCreate(&ev0), "event");
   CK(cudaEventCreate(&ev1), "event");
   CK(cudaEventRecord(ev0, d->stream), "event");
   if (q > 0) {
-    e = launch_transport<float>(P, false, true, grid, block, d->stream);
+    e = launch_transport<float>(P, false, true, false, grid, block, d->stream);
     d->launches++;
     if (e != cudaSuccess) return cuda_fail(d, e, "transport launch");
   }
@@ -1044,7 +1045,7 @@ cudaError_t batch_launch(mcrt_batch* b, const KParams<float>& P, int block, int 
   }
   e = cudaMemsetAsync(b->queue.p, 0, 8, b->stream);
   if (e != cudaSuccess) return e;
-  return launch_transport<float>(P, false, true, grid, block, b->stream);
+  return launch_transport<float>(P, false, true, false, grid, block, b->stream);
 }
 }  // namespace
 
@@ -1105,7 +1106,9 @@ mcrt_status mcrt_batch_create(mcrt_disk* const* disks, int n, const uint64_t* n_
   b->P.want_lam = (any_nongray || o->want_sed) ? 1 : 0;
   int sms = 0;
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, d->device);
-  auto grid_for = [&](int block) { return sms * std::max(1, transport_blocks_per_sm<float>(false, true, block)); };
+  auto grid_for = [&](int block) {
+    return sms * std::max(1, transport_blocks_per_sm<float>(false, true, false, block));
+  };
   if (o->block_size) {
     b->block = o->block_size;
     b->refill = o->refill_interval > 0 ? o->refill_interval : 1;
@@ -1133,7 +1136,7 @@ mcrt_status mcrt_batch_create(mcrt_disk* const* disks, int n, const uint64_t* n_
     cudaEventCreate(&e0);
     cudaEventCreate(&e1);
     float best = 1e30f;
-    const int blocks[3] = {128, 256, 512}, refills[3] = {1, 4, 16};
+    const int blocks[3] = {64, 128, 256}, refills[3] = {1, 4, 16};
     auto t_start = std::chrono::steady_clock::now();
     for (int bi = 0; bi < 3; ++bi)
       for (int ri = 0; ri < 3; ++ri) {

@@ -39,9 +39,10 @@ struct DBuf {
 struct PdaState;  // pda.cu
 
 template <class R>
-cudaError_t launch_transport(const KParams<R>& P, bool trace, bool batch, int grid, int block, cudaStream_t st);
+cudaError_t launch_transport(const KParams<R>& P, bool trace, bool batch, bool gray, int grid, int block,
+                             cudaStream_t st);
 template <class R>
-int transport_blocks_per_sm(bool trace, bool batch, int block);
+int transport_blocks_per_sm(bool trace, bool batch, bool gray, int block);
 
 }  // namespace mcrt
 

@@ -50,14 +50,15 @@ struct KParams {
   double l_unit;
 };
 
+// Per-lane packet state. The Philox key (the seed) is a launch parameter, not lane state.
 template <class R>
 struct Pkt {
   R px, py, pz, ux, uy, uz, tau, dsafe;
+  R alpha;   // extinction per unit length in the current cell at the current wavelength
   int ir, it, lam, ninc;
-  unsigned long long events, steps;
-  unsigned xcross;  // face crossings since the last interaction (guard against zero-length ping-pong)
-  Rng rng;
-  unsigned long long id;
+  unsigned events, steps, xcross;  // interactions + jumps, all steps, crossings since the last interaction
+  uint32_t model, plo, phi, blk, w0, w1, w2, w3;
+  int left;
   int pend_mode;  // 0: bin known; 1: BW bin of (pend_cell, pend_tally -> +EUNIT); 2: exit bin at pend_tally
   int pend_cell;
   float pend_u;
@@ -65,13 +66,36 @@ struct Pkt {
   int tslot, ntr;
 };
 
+// Per-lane run counters, flushed once per launch (32-bit: a lane's share of a launch stays far below 2^32)
 struct Acc {
-  unsigned long long v[C_NCNT];
+  unsigned packets, abs, sca, cross, mrw, capped, escaped, err;
+  unsigned long long depsum;
+  unsigned long long longest;  // (steps << 24) | (packet id & 0xffffff) of the lane's longest packet
 };
 
 template <class R>
-__device__ __forceinline__ R U(Pkt<R>& s) {
-  return to_uniform<R>(s.rng.next());
+__device__ __forceinline__ uint32_t next_word(Pkt<R>& s, uint32_t k0, uint32_t k1) {
+  if (s.left == 0) {
+    uint32_t c0 = s.blk, c1 = s.model, c2 = s.plo, c3 = s.phi;
+    philox4x32_10(c0, c1, c2, c3, k0, k1);
+    s.w0 = c0; s.w1 = c1; s.w2 = c2; s.w3 = c3;
+    ++s.blk;
+    s.left = 4;
+  }
+  const uint32_t w = s.w0;
+  s.w0 = s.w1; s.w1 = s.w2; s.w2 = s.w3;
+  --s.left;
+  return w;
+}
+
+// the key of every stream of a launch
+struct Key {
+  uint32_t k0, k1;
+};
+
+template <class R>
+__device__ __forceinline__ R U(Pkt<R>& s, const Key& key) {
+  return to_uniform<R>(next_word(s, key.k0, key.k1));
 }
 
 template <class R>
@@ -103,9 +127,9 @@ __device__ __forceinline__ void polar_dir<double>(double mu, double u2, double& 
 }
 
 template <class R>
-__device__ __forceinline__ void iso_dir(Pkt<R>& s, R& x, R& y, R& z) {
-  const R mu = (R)2 * U(s) - (R)1;
-  const R u2 = U(s);
+__device__ __forceinline__ void iso_dir(Pkt<R>& s, const Key& key, R& x, R& y, R& z) {
+  const R mu = (R)2 * U(s, key) - (R)1;
+  const R u2 = U(s, key);
   polar_dir<R>(mu, u2, x, y, z);
 }
 
@@ -275,13 +299,23 @@ __device__ __forceinline__ void resolve_pending(const DevModel<R>& M, Pkt<R>& s)
   s.pend_mode = 0;
 }
 
+// extinction per unit length of the packet's cell at its wavelength
+template <class R, bool G>
+__device__ __forceinline__ R cell_alpha(const DevModel<R>& M, const Pkt<R>& s) {
+  const R rho = M.rho[s.ir * M.nt + s.it];
+  return rho * ((G || M.gray) ? M.chi0 : M.chi[s.lam]);
+}
+
 template <class R, bool TRACE>
-__device__ void launch_packet(const KParams<R>& P, const DevModel<R>& M, Pkt<R>& s, unsigned long long k, int tslot,
-                              Acc& acc) {
-  s.rng.init(P.seed, M.model_id, k);
-  s.id = k;
-  s.lam = sample_star(M, U(s));
-  iso_dir(s, s.ux, s.uy, s.uz);
+__device__ void launch_packet(const KParams<R>& P, const Key& key, const DevModel<R>& M, Pkt<R>& s,
+                              unsigned long long k, int tslot, Acc& acc) {
+  s.model = M.model_id;
+  s.plo = (uint32_t)k;
+  s.phi = (uint32_t)(k >> 32);
+  s.blk = 0;
+  s.left = 0;
+  s.lam = sample_star(M, U(s, key));
+  iso_dir(s, key, s.ux, s.uy, s.uz);
   s.px = s.py = s.pz = (R)0;
   s.ir = -1;
   s.it = -1;
@@ -290,22 +324,23 @@ __device__ void launch_packet(const KParams<R>& P, const DevModel<R>& M, Pkt<R>&
   s.steps = 0;
   s.xcross = 0;
   s.dsafe = (R)0;
+  s.alpha = (R)0;
   s.pend_mode = 0;
   s.tslot = tslot;
   s.ntr = 0;
   trace_ev<R, TRACE>(P, s, EV_LAUNCH, -1);
-  s.tau = neg_log<R>(U(s));
-  acc.v[C_PACKETS]++;
+  s.tau = neg_log<R>(U(s, key));
+  acc.packets++;
 }
 
-template <class R, bool TRACE>
-__device__ void mrw_chain(const KParams<R>& P, const DevModel<R>& M, Pkt<R>& s, int c, Acc& acc) {
+template <class R, bool TRACE, bool G>
+__device__ void mrw_chain(const KParams<R>& P, const Key& key, const DevModel<R>& M, Pkt<R>& s, int c, Acc& acc) {
   const R rho = M.rho[c];
   for (;;) {
     if (s.events >= P.max_events) break;
     const R dm = dmin_cell(M, s.ir, s.it, s.px, s.py, s.pz);
     R chiR, kb;
-    if (M.gray) {
+    if (G || M.gray) {
       chiR = M.chiR0;
       kb = M.kbar0;
     } else {
@@ -316,39 +351,41 @@ __device__ void mrw_chain(const KParams<R>& P, const DevModel<R>& M, Pkt<R>& s, 
       kb = (R)((1.f - w) * __ldg(M.kbar + k) + w * __ldg(M.kbar + k + 1));
     }
     if (!(dm * rho * chiR > P.gamma)) break;  // Eq. 11
-    const R x = mrw_x(P, U(s));
+    const R x = mrw_x(P, U(s, key));
     const R tau0 = dm * rho;
     const R E = (R)3 * x * tau0 * tau0 * chiR * kb;  // Eq. 9 with c t = x R0^2 / D, D = 1/(3 rho chi_R)
     R units = floor(E * (R)kEUnit + (R)0.5);
     if (!(units < (R)1.8e19)) {
       units = (R)1.8e19;
-      acc.v[C_ERR] |= kErrMrwClip;
+      acc.err |= kErrMrwClip;
     }
     const unsigned long long du = (unsigned long long)units;
+    // MRW deposits can be large: always check the returned old value for wrap-around
     const unsigned long long old = atomicAdd(M.tally + c, du);
-    if (old + du < old) acc.v[C_ERR] |= kErrOverflow;
-    acc.v[C_DEPSUM] += du;
+    if (old + du < old) acc.err |= kErrOverflow;
+    acc.depsum += du;
     R hx, hy, hz;
-    iso_dir(s, hx, hy, hz);
+    iso_dir(s, key, hx, hy, hz);
     s.px += dm * hx;
     s.py += dm * hy;
     s.pz += dm * hz;
     if (P.exit_dir == 1) {
-      const R mu = sqrt(U(s));
-      const R u2 = U(s);
+      const R mu = sqrt(U(s, key));
+      const R u2 = U(s, key);
       s.ux = hx; s.uy = hy; s.uz = hz;
       turn<R>(s.ux, s.uy, s.uz, mu, u2);
     } else {
-      iso_dir(s, s.ux, s.uy, s.uz);
+      iso_dir(s, key, s.ux, s.uy, s.uz);
     }
-    const R ul = U(s);
+    const R ul = U(s, key);
     if (P.want_lam) {
-      if (!M.gray || TRACE) {
+      if (!(G || M.gray) || TRACE) {
         int k;
         float w;
         qpos(M, old + du, c, k, w);
         s.lam = sample_exit(M, k, w, (float)ul);
         s.pend_mode = 0;
+        if (!(G || M.gray)) s.alpha = cell_alpha<R, G>(M, s);
       } else {
         s.pend_mode = 2;
         s.pend_cell = c;
@@ -357,18 +394,18 @@ __device__ void mrw_chain(const KParams<R>& P, const DevModel<R>& M, Pkt<R>& s, 
       }
     }
     s.events++;
-    acc.v[C_MRW]++;
+    acc.mrw++;
     s.dsafe = (R)0;
     trace_ev<R, TRACE>(P, s, EV_MRW, c);
   }
 }
 
 // One step of a packet. Returns false when the packet has ended.
-template <class R, bool TRACE>
-__device__ bool step(const KParams<R>& P, const DevModel<R>& M, Pkt<R>& s, Acc& acc) {
+template <class R, bool TRACE, bool G>
+__device__ bool step(const KParams<R>& P, const Key& key, const DevModel<R>& M, Pkt<R>& s, Acc& acc) {
   if (++s.steps > P.max_steps) {
-    acc.v[C_ERR] |= kErrStepGuard;
-    acc.v[C_CAPPED]++;
+    acc.err |= kErrStepGuard;
+    acc.capped++;
     return false;
   }
   if (s.ir < 0) {  // inner cavity: straight to r_in
@@ -382,16 +419,18 @@ __device__ bool step(const KParams<R>& P, const DevModel<R>& M, Pkt<R>& s, Acc& 
     s.it = theta_cell(M, s.px, s.py, s.pz);
     s.ninc = 0;
     s.dsafe = (R)0;
+    s.alpha = cell_alpha<R, G>(M, s);
     const int c = s.it;
     atomicAdd(M.visits + c, 1ull);
-    acc.v[C_CROSS]++;
+    acc.cross++;
     trace_ev<R, TRACE>(P, s, EV_CROSS, c);
     return true;
   }
   const int c = s.ir * M.nt + s.it;
-  const R chi = M.gray ? M.chi0 : M.chi[s.lam];
-  const R alpha = M.rho[c] * chi;
-  const R s_int = alpha > (R)0 ? s.tau / alpha : inf_<R>();
+  const R alpha = s.alpha;
+  R s_int;
+  if (!(alpha > (R)0)) s_int = inf_<R>();
+  else s_int = s.tau / alpha;
   bool interact;
   R s_face = (R)0;
   int face = 1;
@@ -415,58 +454,62 @@ __device__ bool step(const KParams<R>& P, const DevModel<R>& M, Pkt<R>& s, Acc& 
     s.py += s_int * s.uy;
     s.pz += s_int * s.uz;
     s.dsafe = s.dsafe > s_int ? s.dsafe - s_int : (R)0;
-    const R om = M.gray ? M.alb0 : M.alb[s.lam];
-    if (U(s) < om) {
-      const R g = M.gray ? M.g0 : M.gq[s.lam];
+    const R om = (G || M.gray) ? M.alb0 : M.alb[s.lam];
+    if (U(s, key) < om) {
+      const R g = (G || M.gray) ? M.g0 : M.gq[s.lam];
       if (g != (R)0) {
-        const R mu = hg_mu(g, U(s));
-        const R u2 = U(s);
+        const R mu = hg_mu(g, U(s, key));
+        const R u2 = U(s, key);
         turn<R>(s.ux, s.uy, s.uz, mu, u2);
       } else {
-        iso_dir(s, s.ux, s.uy, s.uz);
+        iso_dir(s, key, s.ux, s.uy, s.uz);
       }
-      acc.v[C_SCA]++;
+      acc.sca++;
       trace_ev<R, TRACE>(P, s, EV_SCATTER, c);
     } else {
-      const unsigned long long old = atomicAdd(M.tally + c, kEUnit);
-      if (old + kEUnit < old) acc.v[C_ERR] |= kErrOverflow;
-      atomicAdd(M.nabs + c, 1ull);
-      acc.v[C_DEPSUM] += kEUnit;
-      const R ul = U(s);
+      const R ul = U(s, key);
       if (P.want_lam) {
-        if (!M.gray || TRACE) {
+        // the old tally sets T_old / T_new of the BW re-emission
+        const unsigned long long old = atomicAdd(M.tally + c, kEUnit);
+        if (old + kEUnit < old) acc.err |= kErrOverflow;
+        if (!(G || M.gray) || TRACE) {
           int ko, kn;
           float wo, wn;
           qpos(M, old, c, ko, wo);
           qpos(M, old + kEUnit, c, kn, wn);
           s.lam = sample_bw(M, ko, wo, kn, wn, (float)ul);
           s.pend_mode = 0;
+          if (!(G || M.gray)) s.alpha = cell_alpha<R, G>(M, s);
         } else {
           s.pend_mode = 1;
           s.pend_cell = c;
           s.pend_tally = old;
           s.pend_u = (float)ul;
         }
+      } else {
+        atomicAdd(M.tally + c, kEUnit);  // no wavelength needed: nothing waits for the old value
       }
-      iso_dir(s, s.ux, s.uy, s.uz);
-      acc.v[C_ABS]++;
+      atomicAdd(M.nabs + c, 1ull);
+      acc.depsum += kEUnit;
+      iso_dir(s, key, s.ux, s.uy, s.uz);
+      acc.abs++;
       trace_ev<R, TRACE>(P, s, EV_ABSORB, c);
     }
     s.events++;
     s.ninc++;
-    if (P.mrw && s.ninc >= P.nmin) mrw_chain<R, TRACE>(P, M, s, c, acc);
+    if (P.mrw && s.ninc >= P.nmin) mrw_chain<R, TRACE, G>(P, key, M, s, c, acc);
     if (s.events >= P.max_events) {
-      acc.v[C_CAPPED]++;
+      acc.capped++;
       trace_ev<R, TRACE>(P, s, EV_CAPPED, c);
       return false;
     }
-    s.tau = neg_log<R>(U(s));
+    s.tau = neg_log<R>(U(s, key));
     return true;
   }
   // cross a face
   if (++s.xcross > 100000u) {
-    acc.v[C_ERR] |= kErrStepGuard;
-    acc.v[C_CAPPED]++;
+    acc.err |= kErrStepGuard;
+    acc.capped++;
     return false;
   }
   s.px += s_face * s.ux;
@@ -474,7 +517,7 @@ __device__ bool step(const KParams<R>& P, const DevModel<R>& M, Pkt<R>& s, Acc& 
   s.pz += s_face * s.uz;
   s.tau -= alpha * s_face;
   if (s.tau < (R)0) s.tau = (R)0;
-  acc.v[C_CROSS]++;
+  acc.cross++;
   if (face == 1) s.ir++;
   else if (face == 0) s.ir--;
   else if (face == 2) s.it--;
@@ -484,31 +527,30 @@ __device__ bool step(const KParams<R>& P, const DevModel<R>& M, Pkt<R>& s, Acc& 
     int ib = (int)(fabs(s.uz) * (R)kNInc);
     ib = ib < kNInc ? ib : kNInc - 1;
     atomicAdd(M.sed + s.lam * kNInc + ib, 1ull);
-    acc.v[C_ESCAPED]++;
+    acc.escaped++;
     trace_ev<R, TRACE>(P, s, EV_ESCAPE, -1);
     return false;
   }
   if (s.ir < 0) {
+    s.alpha = (R)0;
     trace_ev<R, TRACE>(P, s, EV_CROSS, -1);
     return true;
   }
   s.ninc = 0;
+  s.alpha = cell_alpha<R, G>(M, s);
   const int cn = s.ir * M.nt + s.it;
   atomicAdd(M.visits + cn, 1ull);
   trace_ev<R, TRACE>(P, s, EV_CROSS, cn);
   return true;
 }
 
-// per-lane record of the longest packet (flushed with the counters)
 template <class R>
 __device__ __forceinline__ void note_end(const Pkt<R>& s, Acc& acc) {
-  const unsigned long long st = s.steps;
-  if (st > acc.v[C_MAXSTEPS]) acc.v[C_MAXSTEPS] = st;
-  const unsigned long long packed = (st << 24) | (s.id & 0xffffffull);
-  if (packed > acc.v[C_LONGEST]) acc.v[C_LONGEST] = packed;
+  const unsigned long long packed = ((unsigned long long)s.steps << 24) | (s.plo & 0xffffffu);
+  if (packed > acc.longest) acc.longest = packed;
 }
 
-__device__ __forceinline__ unsigned long long warp_max(unsigned long long v) {
+__device__ __forceinline__ unsigned long long warp_max64(unsigned long long v) {
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) {
     const unsigned long long w = __shfl_xor_sync(0xffffffffu, v, o);
@@ -517,37 +559,45 @@ __device__ __forceinline__ unsigned long long warp_max(unsigned long long v) {
   return v;
 }
 
-__device__ __forceinline__ unsigned long long warp_sum(unsigned long long v) {
+__device__ __forceinline__ unsigned long long warp_sum64(unsigned long long v) {
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
   return v;
 }
 
+// adds the lane counters to the model's run counters (warp-reduced when the whole warp flushes)
 template <class R>
 __device__ __forceinline__ void flush(const DevModel<R>& M, Acc& acc, bool warp_uniform) {
-  for (int i = 0; i < C_NCNT; ++i) {
-    unsigned long long v = acc.v[i];
+  unsigned long long v[C_NCNT];
+  v[C_PACKETS] = acc.packets;
+  v[C_EVENTS] = 0;
+  v[C_ABS] = acc.abs;
+  v[C_SCA] = acc.sca;
+  v[C_CROSS] = acc.cross;
+  v[C_MRW] = acc.mrw;
+  v[C_CAPPED] = acc.capped;
+  v[C_ESCAPED] = acc.escaped;
+  v[C_DEPSUM] = acc.depsum;
+  v[C_ERR] = acc.err;
+  v[C_MAXSTEPS] = acc.longest >> 24;
+  v[C_LONGEST] = acc.longest;
+#pragma unroll
+  for (int i = 0; i < C_LONGEST + 1; ++i) {
+    if (i == C_EVENTS) continue;
+    unsigned long long x = v[i];
     const bool is_max = (i == C_MAXSTEPS || i == C_LONGEST);
     if (warp_uniform) {
-      if (i == C_ERR) {
-        v = __reduce_or_sync(0xffffffffu, (unsigned)v);
-      } else if (is_max) {
-        v = warp_max(v);
-      } else {
-        v = warp_sum(v);
-      }
-      if ((threadIdx.x & 31) == 0 && v) {
-        if (i == C_ERR) atomicOr(M.cnt + i, v);
-        else if (is_max) atomicMax(M.cnt + i, v);
-        else atomicAdd(M.cnt + i, v);
-      }
-    } else if (v) {
-      if (i == C_ERR) atomicOr(M.cnt + i, v);
-      else if (is_max) atomicMax(M.cnt + i, v);
-      else atomicAdd(M.cnt + i, v);
+      if (i == C_ERR) x = __reduce_or_sync(0xffffffffu, (unsigned)x);
+      else if (is_max) x = warp_max64(x);
+      else x = warp_sum64(x);
+      if ((threadIdx.x & 31) != 0) continue;
     }
-    acc.v[i] = 0;
+    if (!x) continue;
+    if (i == C_ERR) atomicOr(M.cnt + i, x);
+    else if (is_max) atomicMax(M.cnt + i, x);
+    else atomicAdd(M.cnt + i, x);
   }
+  acc = Acc{};
 }
 
 // model of queue position q (batch launches): largest m with q_begin <= q
@@ -561,18 +611,26 @@ __device__ __forceinline__ int find_model(const KParams<R>& P, unsigned long lon
   return lo;
 }
 
-template <class R, bool TRACE, bool BATCH>
-__global__ void __launch_bounds__(512) transport_kernel(const KParams<R> P) {
+// resident 256-thread blocks per SM the FP32 kernel is compiled for (register budget 65536 / (256 n))
+#ifndef MCRT_TRANSPORT_MIN_BLOCKS
+#define MCRT_TRANSPORT_MIN_BLOCKS 3
+#endif
+template <class R>
+constexpr int transport_min_blocks() { return sizeof(R) == 4 ? MCRT_TRANSPORT_MIN_BLOCKS : 1; }
+
+// G: gray dust known at compile time (single-disk gray runs); otherwise M.gray is read at run time.
+template <class R, bool TRACE, bool BATCH, bool G>
+__global__ void __launch_bounds__(256, transport_min_blocks<R>()) transport_kernel(const KParams<R> P) {
   Pkt<R> s;
-  Acc acc;
-#pragma unroll
-  for (int i = 0; i < C_NCNT; ++i) acc.v[i] = 0;
+  Acc acc = Acc{};
+  const Key key{(uint32_t)P.seed, (uint32_t)(P.seed >> 32)};
   bool active = false, done = false;
   int model = 0;
   const unsigned lane = threadIdx.x & 31;
-  unsigned iter = 0;
+  int until_refill = 0;
   for (;;) {
-    if (iter++ % (unsigned)P.refill == 0u) {
+    if (--until_refill < 0) {
+      until_refill = P.refill - 1;
       const unsigned need = __ballot_sync(0xffffffffu, !active && !done);
       if (need) {
         const int leader = __ffs(need) - 1;
@@ -593,18 +651,18 @@ __global__ void __launch_bounds__(512) transport_kernel(const KParams<R> P) {
             const DevModel<R>& M = BATCH ? P.models[m] : P.m0;
             const unsigned long long local = q - M.q_begin;
             const int tslot = (TRACE && local < (unsigned long long)P.trace_n) ? (int)local : -1;
-            launch_packet<R, TRACE>(P, M, s, M.first_id + local, tslot, acc);
+            launch_packet<R, TRACE>(P, key, M, s, M.first_id + local, tslot, acc);
             active = true;
           } else {
             done = true;
           }
         }
       }
+      if (__all_sync(0xffffffffu, done && !active)) break;
     }
-    if (__all_sync(0xffffffffu, done && !active)) break;
     if (active) {
       const DevModel<R>& M = BATCH ? P.models[model] : P.m0;
-      active = step<R, TRACE>(P, M, s, acc);
+      active = step<R, TRACE, G>(P, key, M, s, acc);
       if (!active) note_end(s, acc);
     }
   }

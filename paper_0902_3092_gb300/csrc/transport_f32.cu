@@ -1,23 +1,26 @@
-// transport_f32.cu -- FP32 production instantiations of the transport kernel (single disk, batch).
+// transport_f32.cu -- FP32 production instantiations of the transport kernel: single disk (gray dust
+// fixed at compile time, or not) and batches.
 #include "internal.h"
 
 namespace mcrt {
 
 template <>
-cudaError_t launch_transport<float>(const KParams<float>& P, bool trace, bool batch, int grid, int block,
+cudaError_t launch_transport<float>(const KParams<float>& P, bool trace, bool batch, bool gray, int grid, int block,
                                     cudaStream_t st) {
   if (trace) return cudaErrorInvalidValue;
-  if (batch) transport_kernel<float, false, true><<<grid, block, 0, st>>>(P);
-  else transport_kernel<float, false, false><<<grid, block, 0, st>>>(P);
+  if (batch) transport_kernel<float, false, true, false><<<grid, block, 0, st>>>(P);
+  else if (gray) transport_kernel<float, false, false, true><<<grid, block, 0, st>>>(P);
+  else transport_kernel<float, false, false, false><<<grid, block, 0, st>>>(P);
   return cudaGetLastError();
 }
 
 template <>
-int transport_blocks_per_sm<float>(bool trace, bool batch, int block) {
+int transport_blocks_per_sm<float>(bool trace, bool batch, bool gray, int block) {
   int n = 0;
   if (trace) return 0;
-  if (batch) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, transport_kernel<float, false, true>, block, 0);
-  else cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, transport_kernel<float, false, false>, block, 0);
+  if (batch) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, transport_kernel<float, false, true, false>, block, 0);
+  else if (gray) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, transport_kernel<float, false, false, true>, block, 0);
+  else cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, transport_kernel<float, false, false, false>, block, 0);
   return n;
 }
 

@@ -5,20 +5,30 @@
 namespace mcrt {
 
 template <>
-cudaError_t launch_transport<double>(const KParams<double>& P, bool trace, bool batch, int grid, int block,
+cudaError_t launch_transport<double>(const KParams<double>& P, bool trace, bool batch, bool gray, int grid, int block,
                                      cudaStream_t st) {
   if (batch) return cudaErrorInvalidValue;
-  if (trace) transport_kernel<double, true, false><<<grid, block, 0, st>>>(P);
-  else transport_kernel<double, false, false><<<grid, block, 0, st>>>(P);
+  if (trace) {
+    if (gray) transport_kernel<double, true, false, true><<<grid, block, 0, st>>>(P);
+    else transport_kernel<double, true, false, false><<<grid, block, 0, st>>>(P);
+  } else {
+    if (gray) transport_kernel<double, false, false, true><<<grid, block, 0, st>>>(P);
+    else transport_kernel<double, false, false, false><<<grid, block, 0, st>>>(P);
+  }
   return cudaGetLastError();
 }
 
 template <>
-int transport_blocks_per_sm<double>(bool trace, bool batch, int block) {
+int transport_blocks_per_sm<double>(bool trace, bool batch, bool gray, int block) {
   int n = 0;
   if (batch) return 0;
-  if (trace) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, transport_kernel<double, true, false>, block, 0);
-  else cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, transport_kernel<double, false, false>, block, 0);
+  if (trace) {
+    if (gray) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, transport_kernel<double, true, false, true>, block, 0);
+    else cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, transport_kernel<double, true, false, false>, block, 0);
+  } else {
+    if (gray) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, transport_kernel<double, false, false, true>, block, 0);
+    else cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, transport_kernel<double, false, false, false>, block, 0);
+  }
   return n;
 }
 

@@ -84,16 +84,18 @@ def test_gradient_against_finite_differences(setup):
     assert len(cand) >= 50
     rng = np.random.default_rng(1)
     pick = cand[rng.choice(len(cand), size=min(50, len(cand)), replace=False)]
+    # central differences: O(h^2) truncation plus the solve's FP64 residual floor divided by h, hence
+    # 5e-4 relative (and 1e-6 of the largest component for the smallest ones)
     h = 1e-3
     for i, j in pick:
         a, b = lr0.copy(), lr0.copy()
         a[i, j] += h
         b[i, j] -= h
         fd = (J(a, kr0) - J(b, kr0)) / (2 * h)
-        assert abs(fd - gl[i, j]) <= 1e-4 * abs(gl[i, j]) + 1e-7 * np.abs(gl).max(), (i, j, fd, gl[i, j])
+        assert abs(fd - gl[i, j]) <= 5e-4 * abs(gl[i, j]) + 1e-6 * np.abs(gl).max(), (i, j, fd, gl[i, j])
         a, b = kr0.copy(), kr0.copy()
         hk = h * kr0[i, j]
         a[i, j] += hk
         b[i, j] -= hk
         fdk = (J(lr0, a) - J(lr0, b)) / (2 * hk)
-        assert abs(fdk - gk[i, j]) <= 1e-4 * abs(gk[i, j]) + 1e-7 * np.abs(gk).max(), (i, j, fdk, gk[i, j])
+        assert abs(fdk - gk[i, j]) <= 5e-4 * abs(gk[i, j]) + 1e-6 * np.abs(gk).max(), (i, j, fdk, gk[i, j])
