@@ -73,12 +73,19 @@ struct Acc {
   unsigned long long longest;  // (steps << 24) | (packet id & 0xffffff) of the lane's longest packet
 };
 
+// next Philox block of a stream: one out-of-line copy, so the 10 rounds are not inlined at every draw
+static __device__ __noinline__ uint4 philox_block(uint32_t blk, uint32_t model, uint32_t plo, uint32_t phi, uint32_t k0,
+                                          uint32_t k1) {
+  uint32_t c0 = blk, c1 = model, c2 = plo, c3 = phi;
+  philox4x32_10(c0, c1, c2, c3, k0, k1);
+  return make_uint4(c0, c1, c2, c3);
+}
+
 template <class R>
 __device__ __forceinline__ uint32_t next_word(Pkt<R>& s, uint32_t k0, uint32_t k1) {
   if (s.left == 0) {
-    uint32_t c0 = s.blk, c1 = s.model, c2 = s.plo, c3 = s.phi;
-    philox4x32_10(c0, c1, c2, c3, k0, k1);
-    s.w0 = c0; s.w1 = c1; s.w2 = c2; s.w3 = c3;
+    const uint4 w = philox_block(s.blk, s.model, s.plo, s.phi, k0, k1);
+    s.w0 = w.x; s.w1 = w.y; s.w2 = w.z; s.w3 = w.w;
     ++s.blk;
     s.left = 4;
   }
@@ -207,10 +214,8 @@ __device__ __forceinline__ void qpos(const DevModel<R>& M, unsigned long long ta
 //   adjacent intervals:       D = (1 - w_old)(C[k_old+1] - C[k_old]) + w_new (C[k_new+1] - C[k_new])
 //   further apart:            D = C(T_new) - C(T_old), both interpolated
 // Below the first grid temperature (k = 0) the spectrum is the one of the first interval.
-template <class R>
-__device__ int sample_bw(const DevModel<R>& M, int ko, float wo, int kn, float wn, float u) {
-  const int nl = M.nlam;
-  const float* C = M.cbw;
+static __device__ __noinline__ int sample_bw_rows(const float* __restrict__ C, int nl, int ko, float wo, int kn, float wn,
+                                          float u) {
   int mode = kn <= ko ? 0 : (kn == ko + 1 ? 1 : 2);
   auto D = [&](int b) -> float {
     if (mode == 0) {
@@ -241,10 +246,8 @@ __device__ int sample_bw(const DevModel<R>& M, int ko, float wo, int kn, float w
 }
 
 // MRW exit bin from the cumulative dBbar/dT / chi' row at (k, w)
-template <class R>
-__device__ int sample_exit(const DevModel<R>& M, int k, float w, float u) {
-  const int nl = M.nlam;
-  const float* X = M.cexit + (size_t)k * nl;
+static __device__ __noinline__ int sample_exit_rows(const float* __restrict__ cexit, int nl, int k, float w, float u) {
+  const float* X = cexit + (size_t)k * nl;
   auto cum = [&](int b) { return (1.f - w) * __ldg(X + b) + w * __ldg(X + nl + b); };
   const float target = u * cum(nl - 1);
   int lo = -1, hi = nl - 1;
@@ -253,6 +256,16 @@ __device__ int sample_exit(const DevModel<R>& M, int k, float w, float u) {
     if (cum(mid) >= target) hi = mid; else lo = mid;
   }
   return hi;
+}
+
+template <class R>
+__device__ __forceinline__ int sample_bw(const DevModel<R>& M, int ko, float wo, int kn, float wn, float u) {
+  return sample_bw_rows(M.cbw, M.nlam, ko, wo, kn, wn, u);
+}
+
+template <class R>
+__device__ __forceinline__ int sample_exit(const DevModel<R>& M, int k, float w, float u) {
+  return sample_exit_rows(M.cexit, M.nlam, k, w, u);
 }
 
 template <class R>
@@ -307,7 +320,7 @@ __device__ __forceinline__ R cell_alpha(const DevModel<R>& M, const Pkt<R>& s) {
 }
 
 template <class R, bool TRACE>
-__device__ void launch_packet(const KParams<R>& P, const Key& key, const DevModel<R>& M, Pkt<R>& s,
+__device__ __forceinline__ void launch_packet(const KParams<R>& P, const Key& key, const DevModel<R>& M, Pkt<R>& s,
                               unsigned long long k, int tslot, Acc& acc) {
   s.model = M.model_id;
   s.plo = (uint32_t)k;
@@ -334,7 +347,7 @@ __device__ void launch_packet(const KParams<R>& P, const Key& key, const DevMode
 }
 
 template <class R, bool TRACE, bool G>
-__device__ void mrw_chain(const KParams<R>& P, const Key& key, const DevModel<R>& M, Pkt<R>& s, int c, Acc& acc) {
+__device__ __forceinline__ void mrw_chain(const KParams<R>& P, const Key& key, const DevModel<R>& M, Pkt<R>& s, int c, Acc& acc) {
   const R rho = M.rho[c];
   for (;;) {
     if (s.events >= P.max_events) break;
@@ -455,19 +468,10 @@ __device__ bool step(const KParams<R>& P, const Key& key, const DevModel<R>& M, 
     s.pz += s_int * s.uz;
     s.dsafe = s.dsafe > s_int ? s.dsafe - s_int : (R)0;
     const R om = (G || M.gray) ? M.alb0 : M.alb[s.lam];
-    if (U(s, key) < om) {
-      const R g = (G || M.gray) ? M.g0 : M.gq[s.lam];
-      if (g != (R)0) {
-        const R mu = hg_mu(g, U(s, key));
-        const R u2 = U(s, key);
-        turn<R>(s.ux, s.uy, s.uz, mu, u2);
-      } else {
-        iso_dir(s, key, s.ux, s.uy, s.uz);
-      }
-      acc.sca++;
-      trace_ev<R, TRACE>(P, s, EV_SCATTER, c);
-    } else {
-      const R ul = U(s, key);
+    const bool sca = U(s, key) < om;
+    const R g = sca ? ((G || M.gray) ? M.g0 : M.gq[s.lam]) : (R)0;
+    if (!sca) {
+      const R ul = U(s, key);  // BW re-emission bin draw, before the new direction
       if (P.want_lam) {
         // the old tally sets T_old / T_new of the BW re-emission
         const unsigned long long old = atomicAdd(M.tally + c, kEUnit);
@@ -491,10 +495,20 @@ __device__ bool step(const KParams<R>& P, const Key& key, const DevModel<R>& M, 
       }
       atomicAdd(M.nabs + c, 1ull);
       acc.depsum += kEUnit;
-      iso_dir(s, key, s.ux, s.uy, s.uz);
       acc.abs++;
-      trace_ev<R, TRACE>(P, s, EV_ABSORB, c);
+    } else {
+      acc.sca++;
     }
+    // new direction: Henyey-Greenstein turn for anisotropic scattering, isotropic otherwise (scattering
+    // with g = 0 and re-emission share this code)
+    if (g != (R)0) {
+      const R mu = hg_mu(g, U(s, key));
+      const R u2 = U(s, key);
+      turn<R>(s.ux, s.uy, s.uz, mu, u2);
+    } else {
+      iso_dir(s, key, s.ux, s.uy, s.uz);
+    }
+    trace_ev<R, TRACE>(P, s, sca ? EV_SCATTER : EV_ABSORB, c);
     s.events++;
     s.ninc++;
     if (P.mrw && s.ninc >= P.nmin) mrw_chain<R, TRACE, G>(P, key, M, s, c, acc);
