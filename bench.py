@@ -217,23 +217,18 @@ def main():
     Np = int(args.packets)
     ncell = d.nr * d.ntheta
 
+    from paper_0902_3092_gb300 import dist as D
+
     def combine():
         if world == 1:
             return
-        # exchange of the Monte Carlo step: integer tallies summed over ranks, exact in int64
-        t, v, a = g.tallies()
-        blob = g.checkpoint()
-        x = torch.from_numpy(np.stack([t, v, a]).astype(np.int64)).cuda()
-        dist.all_reduce(x)
-        hdr = np.frombuffer(blob[:64], np.uint64).copy()
-        hdr[5] = Np * world
-        hdr[6] = np.frombuffer(np.array([float(Np * world)]).tobytes(), np.uint64)[0]
-        rest = np.frombuffer(blob[64 + 3 * 8 * ncell:], np.uint64)
-        g.restore(hdr.tobytes() + x.cpu().numpy().astype(np.uint64).tobytes() + rest.tobytes())
+        # the exchange of the Monte Carlo step: integer tallies summed over ranks (exact in int64)
+        g.restore(D.allreduce_blob(g.checkpoint()))
 
     def step(i):
         g.reset()
-        st = g.run_photons(Np, seed=1, first_id=(rank + world * i) * Np, n_total=Np * world, mrw=True,
+        first, _ = D.packet_range(rank, world, Np, i)
+        st = g.run_photons(Np, seed=1, first_id=first, n_total=Np * world, mrw=True,
                            gamma=args.gamma, want_sed=True, max_events=int(args.max_events))
         combine()
         n_pda, iters = g.solve_pda()

@@ -582,7 +582,7 @@ static void fill_params(KParams<R>& P, const mcrt_run_opts* o, uint64_t seed, co
   P.mrw = o->mrw ? 1 : 0;
   P.nmin = o->mrw_min_interactions;
   P.exit_dir = o->mrw_exit_dir;
-  P.refill = o->refill_interval > 0 ? o->refill_interval : 1;
+  P.refill = o->refill_interval > 0 ? o->refill_interval : 4;
   P.gamma = (R)o->gamma;
   P.seed = seed;
   // per-packet counters are 32-bit: caps above 2^31 events (4e9 steps) are clamped

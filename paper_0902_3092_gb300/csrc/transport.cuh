@@ -55,6 +55,7 @@ template <class R>
 struct Pkt {
   R px, py, pz, ux, uy, uz, tau, dsafe;
   R alpha;   // extinction per unit length in the current cell at the current wavelength
+  R ialpha;  // 1 / alpha (0 where alpha = 0)
   int ir, it, lam, ninc;
   unsigned events, steps, xcross;  // interactions + jumps, all steps, crossings since the last interaction
   uint32_t model, plo, phi, blk, w0, w1, w2, w3;
@@ -314,9 +315,10 @@ __device__ __forceinline__ void resolve_pending(const DevModel<R>& M, Pkt<R>& s)
 
 // extinction per unit length of the packet's cell at its wavelength
 template <class R, bool G>
-__device__ __forceinline__ R cell_alpha(const DevModel<R>& M, const Pkt<R>& s) {
+__device__ __forceinline__ void set_alpha(const DevModel<R>& M, Pkt<R>& s) {
   const R rho = M.rho[s.ir * M.nt + s.it];
-  return rho * ((G || M.gray) ? M.chi0 : M.chi[s.lam]);
+  s.alpha = rho * ((G || M.gray) ? M.chi0 : M.chi[s.lam]);
+  s.ialpha = s.alpha > (R)0 ? (R)1 / s.alpha : (R)0;
 }
 
 template <class R, bool TRACE>
@@ -338,6 +340,7 @@ __device__ __forceinline__ void launch_packet(const KParams<R>& P, const Key& ke
   s.xcross = 0;
   s.dsafe = (R)0;
   s.alpha = (R)0;
+  s.ialpha = (R)0;
   s.pend_mode = 0;
   s.tslot = tslot;
   s.ntr = 0;
@@ -398,7 +401,7 @@ __device__ __forceinline__ void mrw_chain(const KParams<R>& P, const Key& key, c
         qpos(M, old + du, c, k, w);
         s.lam = sample_exit(M, k, w, (float)ul);
         s.pend_mode = 0;
-        if (!(G || M.gray)) s.alpha = cell_alpha<R, G>(M, s);
+        if (!(G || M.gray)) set_alpha<R, G>(M, s);
       } else {
         s.pend_mode = 2;
         s.pend_cell = c;
@@ -432,7 +435,7 @@ __device__ bool step(const KParams<R>& P, const Key& key, const DevModel<R>& M, 
     s.it = theta_cell(M, s.px, s.py, s.pz);
     s.ninc = 0;
     s.dsafe = (R)0;
-    s.alpha = cell_alpha<R, G>(M, s);
+    set_alpha<R, G>(M, s);
     const int c = s.it;
     atomicAdd(M.visits + c, 1ull);
     acc.cross++;
@@ -443,7 +446,8 @@ __device__ bool step(const KParams<R>& P, const Key& key, const DevModel<R>& M, 
   const R alpha = s.alpha;
   R s_int;
   if (!(alpha > (R)0)) s_int = inf_<R>();
-  else s_int = s.tau / alpha;
+  else if (sizeof(R) == 8) s_int = s.tau / alpha;  // the FP64 path divides like the CPU reference
+  else s_int = s.tau * s.ialpha;
   bool interact;
   R s_face = (R)0;
   int face = 1;
@@ -483,7 +487,7 @@ __device__ bool step(const KParams<R>& P, const Key& key, const DevModel<R>& M, 
           qpos(M, old + kEUnit, c, kn, wn);
           s.lam = sample_bw(M, ko, wo, kn, wn, (float)ul);
           s.pend_mode = 0;
-          if (!(G || M.gray)) s.alpha = cell_alpha<R, G>(M, s);
+          if (!(G || M.gray)) set_alpha<R, G>(M, s);
         } else {
           s.pend_mode = 1;
           s.pend_cell = c;
@@ -547,11 +551,12 @@ __device__ bool step(const KParams<R>& P, const Key& key, const DevModel<R>& M, 
   }
   if (s.ir < 0) {
     s.alpha = (R)0;
+    s.ialpha = (R)0;
     trace_ev<R, TRACE>(P, s, EV_CROSS, -1);
     return true;
   }
   s.ninc = 0;
-  s.alpha = cell_alpha<R, G>(M, s);
+  set_alpha<R, G>(M, s);
   const int cn = s.ir * M.nt + s.it;
   atomicAdd(M.visits + cn, 1ull);
   trace_ev<R, TRACE>(P, s, EV_CROSS, cn);

@@ -75,3 +75,18 @@ def test_brute_force_random_walk(oracle):
     # quantiles of the walk against the inverse of Eq. 7 at the larger sphere
     for q in (0.25, 0.5, 0.75):
         assert abs(np.quantile(x24, q) - oracle.mrw_x(1 - q)) < 0.02
+
+
+def test_mrw_deposit_against_brute_force(oracle):
+    """Eq. 9: the energy absorbed while crossing the sphere is E_gamma c t rho kappa_bar, i.e. on average
+    kappa/chi times the path length in mean free paths: 3 E[x] tau0^2 (kappa/chi) = tau0^2 / 2 (kappa/chi)
+    for the escape-time law. A brute-force walk of tau0 = 20 mean free paths counts its absorptions
+    (albedo 1/2) and agrees once the 1/tau0 excess of small spheres is allowed for."""
+    rng = np.random.default_rng(9)
+    tau0, n = 20.0, 4000
+    x = _walk(tau0, n, rng)  # x = s/(3 tau0^2), s the path length in mean free paths
+    steps = 3 * x * tau0 ** 2
+    absorbed = rng.binomial(np.maximum(1, np.rint(steps)).astype(np.int64), 0.5)
+    law = 3 * (1 / 6) * tau0 ** 2 * 0.5  # Eq. 9 averaged over Eq. 7
+    ratio = absorbed.mean() / law
+    assert 1.0 < ratio < 1.0 + 3.0 / tau0

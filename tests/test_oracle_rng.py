@@ -59,3 +59,13 @@ def test_philox_avalanche(oracle):
         o2 = oracle.philox(c2, k)
         flips.append(sum(bin(a ^ b).count("1") for a, b in zip(o1, o2)))
     assert abs(np.mean(flips) - 64) < 2.0
+
+
+def test_henyey_greenstein_moments(oracle):
+    """HG phase function: <cos> = g and <cos^2> = (1 + 2 g^2)/3 for the oracle's inverse-CDF sampling."""
+    L = oracle.lib()
+    u = (np.arange(200000) + 0.5) / 200000
+    for g in (0.6, -0.3, 0.9):
+        mu = np.array([L.oracle_hg_mu(g, float(x)) for x in u])
+        assert abs(mu.mean() - g) < 2e-4
+        assert abs((mu ** 2).mean() - (1 + 2 * g * g) / 3) < 2e-4
