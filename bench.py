@@ -33,14 +33,18 @@ METRIC = "photon packets/s (MRW+PDA vs plain MC) at tau_mid=1e6, equal T accurac
 UNIT = "packets/s"
 WORKLOAD = "thick gray disk 200x120 rim-refined, tau_mid=1e6, albedo 0.5 isotropic, MRW gamma=2 + PDA"
 
-# Thread instructions per transport step (an interaction, an MRW jump or a face crossing) of the FP32
-# kernel, from an ncu count of smsp__thread_inst_executed.sum over a whole launch of this workload
-# divided by its steps (see profiles/). They turn the step counts of a launch into the algorithmic
-# instruction work whose rate is compared with the issue peak.
-INST_PER_STEP = 260.0
-# Issue peak: 152 SMs x 4 schedulers x 1 warp instruction per clock x 32 lanes at the 2070 MHz
-# maximum SM clock, in thread instructions per second.
-ISSUE_PEAK = 152 * 4 * 32 * 2070e6
+# Work per transport step (an interaction with its MRW jumps, or a face crossing) of the FP32 kernel on
+# this workload: ncu smsp__inst_executed.sum (warp instructions) and smsp__thread_inst_executed.sum
+# (thread instructions) over a whole 1e8-packet launch, divided by its steps (profiles/). The kernel is
+# bound by instruction issue (divergent, latency-bound integer/FP32 work, no DRAM traffic), so the
+# roofline is issue slots: 152 SMs x 4 schedulers x 1 warp instruction per clock at 2070 MHz.
+WARP_INST_PER_STEP = 74.0
+THREAD_INST_PER_STEP = 363.0
+ISSUE_PEAK = 152 * 4 * 2070e6           # warp instructions / s
+THREAD_ISSUE_PEAK = 32 * ISSUE_PEAK     # thread instructions / s (all lanes busy)
+# DRAM bytes of one transport launch (ncu dram__bytes_read.sum + dram__bytes_write.sum on a 1e7-packet
+# launch of this workload): the tallies and tables stay in L2, so traffic does not grow with packets.
+TRANSPORT_DRAM_BYTES = 1050368
 
 
 def parse():
@@ -299,14 +303,17 @@ def main():
                "d2h_bytes_per_step": int(d2h)}
 
     peaks = measured_peaks()
-    inst = INST_PER_STEP * float(np.mean(ev_steps))
-    achieved = inst / float(np.mean(tr_s))
-    roofline = {"bound": "alu", "achieved": achieved, "peak": ISSUE_PEAK, "unit": "thread-inst/s",
-                "frac": achieved / ISSUE_PEAK, "traffic": None,
-                "kernel": "transport_kernel<float> (persistent packet kernel)",
-                "note": f"{INST_PER_STEP:g} thread instructions per transport step (interaction, MRW jump or "
-                        "crossing) x steps per launch / CUDA-event launch time; peak = 152 SMs x 4 issue x 32 lanes "
-                        "x 2070 MHz"}
+    steps_per_launch = float(np.mean(ev_steps))
+    achieved = WARP_INST_PER_STEP * steps_per_launch / float(np.mean(tr_s))
+    thread_achieved = THREAD_INST_PER_STEP * steps_per_launch / float(np.mean(tr_s))
+    roofline = {"bound": "alu", "achieved": achieved, "peak": ISSUE_PEAK, "unit": "warp-inst/s",
+                "frac": achieved / ISSUE_PEAK, "traffic": TRANSPORT_DRAM_BYTES,
+                "kernel": "transport_kernel<float> (persistent packet kernel, gray)",
+                "thread_inst_frac": thread_achieved / THREAD_ISSUE_PEAK,
+                "note": f"issue-slot roofline: {WARP_INST_PER_STEP:g} warp instructions per transport step "
+                        f"(ncu count on this workload) x {steps_per_launch:.3e} steps per launch / CUDA-event launch "
+                        "time; peak = 152 SMs x 4 schedulers x 2070 MHz (no DRAM bound: tallies and tables are "
+                        f"L2-resident); thread_inst_frac counts active lanes ({THREAD_INST_PER_STEP:g} per step)"}
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:
