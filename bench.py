@@ -60,6 +60,9 @@ def parse():
     p.add_argument("--cpu-seconds", type=float, default=15.0)
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-cpu", action="store_true")
+    p.add_argument("--pda-min-visits", type=int, default=0,
+                   help="PDA visit threshold; 0 scales the paper's 30 entries at 1e5 packets with the packet count "
+                        "(Sect. 3.1 uses 30000 for its 1e8-packet runs)")
     return p.parse_args()
 
 
@@ -220,6 +223,7 @@ def main():
     g = mcrt.Disk.from_model(d, device=local, stream=stream.cuda_stream)
     Np = int(args.packets)
     ncell = d.nr * d.ntheta
+    min_visits = args.pda_min_visits or max(30, int(round(30 * Np * world / 1e5)))
 
     from paper_0902_3092_gb300 import dist as D
 
@@ -235,7 +239,7 @@ def main():
         st = g.run_photons(Np, seed=1, first_id=first, n_total=Np * world, mrw=True,
                            gamma=args.gamma, want_sed=True, max_events=int(args.max_events))
         combine()
-        n_pda, iters = g.solve_pda()
+        n_pda, iters = g.solve_pda(min_visits=min_visits)
         return st, n_pda, iters
 
     flush = torch.empty(512 * 1024 * 1024, dtype=torch.uint8, device="cuda")
@@ -290,7 +294,7 @@ def main():
             h = mcrt.Disk.from_model(d, device=local)
             h.run_photons(Np, seed=1, first_id=(rank + world * i) * Np, n_total=Np, mrw=True, gamma=args.gamma,
                           max_events=int(args.max_events))
-            h.solve_pda()
+            h.solve_pda(min_visits=min_visits)
             T, _, _ = h.temperatures(mcrt.T_PDA)
             h.close()
             te.append(time.perf_counter() - t0)
@@ -325,7 +329,7 @@ def main():
                 "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
                 "config": {"workload": WORKLOAD, "packets_per_step_per_rank": Np, "grid": [d.nr, d.ntheta],
                            "tau_mid": 1e6, "gamma": args.gamma, "mrw_min_interactions": 20,
-                           "max_events_per_packet": int(args.max_events), "pda_min_visits": 30,
+                           "max_events_per_packet": int(args.max_events), "pda_min_visits": min_visits,
                            "pda_max_rel_err": 0.05,
                            "l2": "flushed between timed steps (512 MiB write outside the timed region)",
                            "parallelism": f"packet ranges per rank, int64 tally all-reduce" if world > 1 else "1 GPU"},
