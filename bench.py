@@ -60,6 +60,9 @@ def parse():
     p.add_argument("--cpu-seconds", type=float, default=15.0)
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-cpu", action="store_true")
+    p.add_argument("--pda-stress", type=int, default=0,
+                   help="instead of the transport step: PDA solve on an N x N grid of the same disk (HBM roofline)")
+    p.add_argument("--pda-iters", type=int, default=2000)
     p.add_argument("--pda-min-visits", type=int, default=0,
                    help="PDA visit threshold; 0 scales the paper's 30 entries at 1e5 packets with the packet count "
                         "(Sect. 3.1 uses 30000 for its 1e8-packet runs)")
@@ -202,10 +205,75 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
+# algorithmic bytes per PDA cell and FP32 CG iteration: kernel A reads r, p_old and the two couplings and
+# writes p, Ap; kernel B reads p, Ap, y, r and writes y, r (4-byte values; neighbour values are re-reads)
+PDA_BYTES_PER_CELL_ITER = 4 * (4 + 2) + 4 * (4 + 2)
+
+
+def pda_stress(args):
+    """PDA solve on an N x N grid of the benchmark disk made 100 times more massive (midplane optical
+    depth 1e8), so that most cells of the midplane band |theta - pi/2| < 0.3 are optically thick at
+    this resolution: synthetic Monte Carlo state whose band has no packet entries, so that its thick
+    cells form the PDA region; times FP32 CG iterations."""
+    import torch
+    from paper_0902_3092_gb300 import disks, dist as D, mcrt
+    n = args.pda_stress
+    d = disks.make_disk(disks.log_r_faces(0.1, 100.0, n), disks.midplane_refined_theta_faces(n), disks.paper_star(),
+                        disks.gray_opacity(), 1e8, name=f"thickgray{n}x{n}")
+    rc, tc = disks.cell_centres(d.r_faces_cm, d.theta_faces)
+    band = (np.abs(tc - np.pi / 2) < 0.3)[None, :] & (d.rho > 0)
+    rf, tf = d.r_faces_cm, d.theta_faces
+    V = (2 * np.pi / 3) * (rf[1:] ** 3 - rf[:-1] ** 3)[:, None] * (np.cos(tf[:-1]) - np.cos(tf[1:]))[None, :]
+    T = 300.0 * (rc[:, None] / disks.AU_CM) ** -0.5 * (1 + 0.3 * np.cos(tc)[None, :] ** 2)
+    n_total = 10 ** 9
+    q = 4 * d.opacity.kappa_abs[0] * 5.6704e-5 * T ** 4
+    # every dusty cell carries a tally (unused in the band); the dusty cells outside the band are the
+    # Dirichlet cells that the band touches on both sides
+    tally = np.where(d.rho > 0, np.maximum(np.floor(q * d.rho * V * n_total * 65536 / d.star.L), 1e4 * 65536),
+                     0).astype(np.uint64)
+    visits = np.where(band, 0, 10 ** 6).astype(np.uint64)
+    z = np.zeros(n * n, np.uint64)
+    blob = D.make_blob(n, n, d.opacity.nlam, tally, visits, z, np.zeros(d.opacity.nlam * 10, np.uint64), n_total,
+                       n_total)
+    g = mcrt.Disk.from_model(d)
+    g.restore(blob)
+    m = args.pda_iters
+
+    def solve(k):
+        # one refinement step of k CG iterations; the iteration budget ends it before convergence
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        npda, it = g.solve_pda(max_outer=1, max_inner=k, inner_tol=1e-30, allow_notconv=True)
+        if it != k:
+            raise RuntimeError(f"PDA stress: {it} CG iterations instead of {k}")
+        return npda, time.perf_counter() - t0
+
+    solve(2 * m)  # allocation, temperatures and first-touch outside the timed calls
+    npda, t_a = solve(m)
+    _, t_b = solve(2 * m)
+    t_it = (t_b - t_a) / m  # the setup, the mask checks and the final residual cancel
+    byts = PDA_BYTES_PER_CELL_ITER * npda
+    peak = measured_peaks().get("hbm_gbs", 6800.0) * 1e9
+    line = {"metric": "PDA FP32 CG iteration bandwidth (stress grid)", "value": byts / t_it / 1e9, "unit": "GB/s",
+            "n_gpus": 1, "higher_is_better": True, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": f"PDA on a {n}x{n} gray disk of midplane optical depth 1e8, thick cells of the "
+                                   "midplane band |theta-pi/2|<0.3",
+                       "cells": n * n, "pda_cells": npda, "cg_iterations_timed": args.pda_iters},
+            "us_per_iteration": 1e6 * t_it, "setup_ms": 1e3 * (t_a - m * t_it),
+            "roofline": {"bound": "hbm", "achieved": byts / t_it / 1e9, "peak": peak / 1e9, "unit": "GB/s",
+                         "frac": byts / t_it / peak, "traffic": None,
+                         "note": f"{PDA_BYTES_PER_CELL_ITER} B per PDA cell per iteration (kernels A+B), "
+                                 "host-timed difference of two solves"}}
+    print(json.dumps(line), flush=True)
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         run_reference(args)
+        return
+    if args.pda_stress:
+        pda_stress(args)
         return
     import torch
     import torch.distributed as dist

@@ -1030,12 +1030,6 @@ struct mcrt_batch {
 };
 
 namespace {
-mcrt_status batch_fail(mcrt_batch* b, cudaError_t e, const char* what) {
-  mcrt_status s = cuda_fail(nullptr, e, what);
-  if (b) b->err = mcrt_last_error(nullptr);
-  return s;
-}
-
 // direct (uncaptured) launch of the batch kernel with a given shape, counters zeroed first
 cudaError_t batch_launch(mcrt_batch* b, const KParams<float>& P, int block, int grid) {
   cudaError_t e;

@@ -42,6 +42,9 @@ struct PdaState {
   DBuf b64;                           // FP64 right-hand side (adjoint)
   DBuf rs;                            // FP64 scaled residual S r
   DBuf y, r, p0, p1, Ap;              // FP32 CG vectors
+  DBuf tiles;                         // int32 active tiles of the CG kernels
+  std::vector<int> htiles;            // their host copy (source of the upload)
+  int ntiles = 0;
   DBuf sc;                            // FP64 CG scalars per iteration
   DBuf red;                           // FP64 reduction slots
   DBuf w, gl, gk;                     // adjoint weights / gradient outputs (device staging)
@@ -89,16 +92,20 @@ __device__ __forceinline__ double block_sum_d(double v, double* sh) {
 __global__ void k_mask(int n, const double* rho, const double* ell, double chi_max, double min_tau,
                        const unsigned long long* visits, const double* relerr, const unsigned long long* tally,
                        int min_visits, double max_rel, signed char* mask, double* red) {
-  const int c = blockIdx.x * blockDim.x + threadIdx.x;
-  if (c >= n) return;
-  signed char m = 0;
-  if (rho[c] > 0) {
-    const bool thick = rho[c] * chi_max * ell[c] >= min_tau;
-    if (thick && (visits[c] < (unsigned long long)min_visits || relerr[c] > max_rel)) m = 2;
-    else if (tally[c] > 0ull) m = 1;
+  __shared__ double sh[32];
+  double cnt = 0.0;
+  for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < n; c += gridDim.x * blockDim.x) {
+    signed char m = 0;
+    if (rho[c] > 0) {
+      const bool thick = rho[c] * chi_max * ell[c] >= min_tau;
+      if (thick && (visits[c] < (unsigned long long)min_visits || relerr[c] > max_rel)) m = 2;
+      else if (tally[c] > 0ull) m = 1;
+    }
+    mask[c] = m;
+    cnt += m == 2 ? 1.0 : 0.0;
   }
-  mask[c] = m;
-  if (m == 2) atomicAdd(red + 0, 1.0);
+  const double s = block_sum_d(cnt, sh);
+  if (threadIdx.x == 0 && s != 0.0) atomicAdd(red + 0, s);
 }
 
 // mean MC temperature of the Dirichlet cells that border the PDA region
@@ -116,7 +123,7 @@ __global__ void k_bnd_mean(int nr, int nt, const signed char* mask, const double
 
 // Rosseland mean of chi' = kappa + (1-g) sigma at T (Eq. 3 with Eq. 16), exact bin integrals
 __device__ double rosseland(const double* lam_e, const double* chip, int nlam, double T) {
-  double g3p = 0.0, g4p = 0.0, s1 = 0.0, s2 = 0.0;
+  double g4p = 0.0, s1 = 0.0, s2 = 0.0;
   for (int b = 0; b < nlam; ++b) {
     double g3, g4;
     if (b + 1 == nlam) tails(0.0, g3, g4);
@@ -124,7 +131,6 @@ __device__ double rosseland(const double* lam_e, const double* chip, int nlam, d
     const double db = g4 - g4p;
     s1 += db;
     s2 += db / chip[b];
-    g3p = g3;
     g4p = g4;
   }
   return s1 / s2;
@@ -222,90 +228,155 @@ __global__ void k_resid64(int nr, int nt, const signed char* __restrict__ mask, 
                           const double* __restrict__ Ct, const double* __restrict__ dis, const double* __restrict__ x,
                           const double* __restrict__ b, double* __restrict__ rs, double* red, int slot) {
   __shared__ double sh[32];
-  const int c = blockIdx.x * blockDim.x + threadIdx.x;
-  double v = 0.0;
-  if (c < nr * nt && mask[c] == 2) {
-    const int i = c / nt, j = c - i * nt;
-    const double xc = x[c];
-    double r = b ? b[c] : 0.0;
-    if (i > 0 && mask[c - nt]) r += Cr[c - nt] * (x[c - nt] - xc);
-    if (i + 1 < nr && mask[c + nt]) r += Cr[c] * (x[c + nt] - xc);
-    if (j > 0 && mask[c - 1]) r += Ct[c - 1] * (x[c - 1] - xc);
-    if (j + 1 < nt && mask[c + 1]) r += Ct[c] * (x[c + 1] - xc);
-    v = dis[c] * r;
+  double acc = 0.0;
+  for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < nr * nt; c += gridDim.x * blockDim.x) {
+    double v = 0.0;
+    if (mask[c] == 2) {
+      const int i = c / nt, j = c - i * nt;
+      const double xc = x[c];
+      double r = b ? b[c] : 0.0;
+      if (i > 0 && mask[c - nt]) r += Cr[c - nt] * (x[c - nt] - xc);
+      if (i + 1 < nr && mask[c + nt]) r += Cr[c] * (x[c + nt] - xc);
+      if (j > 0 && mask[c - 1]) r += Ct[c - 1] * (x[c - 1] - xc);
+      if (j + 1 < nt && mask[c + 1]) r += Ct[c] * (x[c + 1] - xc);
+      v = dis[c] * r;
+    }
     rs[c] = v;
-  } else if (c < nr * nt) {
-    rs[c] = 0.0;
+    acc += v * v;
   }
-  const double s = block_sum_d(v * v, sh);
+  const double s = block_sum_d(acc, sh);
   if (threadIdx.x == 0 && s != 0.0) atomicAdd(red + slot, s);
 }
 
-// rhs of the FP32 solve: r = rs / scale, y = 0; red[slot] += |r|^2 (FP32 values)
+// rhs of the FP32 solve: r = rs / scale, y = 0, all CG vectors zeroed (the iteration kernels only touch
+// PDA cells afterwards); sc[0] += |r|^2. Grid-stride over the cells.
 __global__ void k_start(int n, const signed char* mask, const double* rs, double inv_scale, float* y, float* r,
-                        float* p_old, double* sc) {
+                        float* p_old, float* p_new, float* Ap, double* sc) {
   __shared__ float sh[32];
-  const int c = blockIdx.x * blockDim.x + threadIdx.x;
   float v = 0.f;
-  if (c < n) {
-    v = mask[c] == 2 ? (float)(rs[c] * inv_scale) : 0.f;
-    r[c] = v;
+  for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < n; c += gridDim.x * blockDim.x) {
+    const float x = mask[c] == 2 ? (float)(rs[c] * inv_scale) : 0.f;
+    r[c] = x;
     y[c] = 0.f;
     p_old[c] = 0.f;
+    p_new[c] = 0.f;
+    Ap[c] = 0.f;
+    v += x * x;
   }
-  const float s = block_sum_f(v * v, sh);
+  const float s = block_sum_f(v, sh);
   if (threadIdx.x == 0 && s != 0.f) atomicAdd(sc + 0, (double)s);
 }
 
 // scalar layout: sc[0] = rr_0; iteration k: rr_k at 2k (k >= 1 stored at sc[2k]), pAp_k at sc[2k+1]
 __device__ __forceinline__ double rr_of(const double* sc, int k) { return sc[2 * k]; }
 
-// kernel A of CG iteration k
-__global__ void k_cg_a(int nr, int nt, const signed char* __restrict__ mask, const float* __restrict__ ar,
-                       const float* __restrict__ at, const float* __restrict__ r, const float* __restrict__ p_old,
-                       float* __restrict__ p_new, float* __restrict__ Ap, double* sc, int k, double tol2) {
+// The CG iteration kernels sweep "active tiles": runs of 32 consecutive cells (row-major, one warp
+// per tile, one lane per cell) that hold at least one PDA cell; `tiles` lists them in increasing
+// order (nullptr: every tile of the grid). They read no mask: outside the PDA region the vectors
+// are zero and so are the scaled couplings ar, at of every face that is not between two PDA cells,
+// including the faces beyond the last radial row / polar column, so the terms of non-PDA
+// neighbours vanish and non-PDA cells keep zero. Each warp walks its tiles grid-stride, kTileU
+// tiles per step with all their loads issued before the arithmetic, so that enough bytes are in
+// flight per SM for HBM; the grid is a few resident blocks per SM, so each reduction ends in about
+// a thousand atomics.
+constexpr int kTileU = 2;
+
+__device__ __forceinline__ float ld_or0(const float* __restrict__ a, int i, bool ok) { return ok ? __ldg(a + i) : 0.f; }
+
+// kernel A of CG iteration k: p = r + beta p_old and Ap (p recomputed for the four neighbours from r
+// and p_old), partial p.Ap
+__global__ void __launch_bounds__(256) k_cg_a(int n, int nt, int ntiles, const int* __restrict__ tiles,
+                                              const float* __restrict__ ar, const float* __restrict__ at,
+                                              const float* __restrict__ r, const float* __restrict__ p_old,
+                                              float* __restrict__ p_new, float* __restrict__ Ap, double* sc, int k,
+                                              double tol2) {
   __shared__ float sh[32];
   const double rr0 = rr_of(sc, 0), rrk = rr_of(sc, k);
   if (rrk <= tol2 * rr0 || !(rrk == rrk)) return;  // converged (or broken): no-op
   const float beta = k == 0 ? 0.f : (float)(rrk / rr_of(sc, k - 1));
-  const int c = blockIdx.x * blockDim.x + threadIdx.x;
-  const int n = nr * nt;
+  const int lane = threadIdx.x & 31, nw = gridDim.x * (blockDim.x >> 5);
   float v = 0.f;
-  if (c < n && mask[c] == 2) {
-    const int i = c / nt, j = c - i * nt;
-    const float pc = r[c] + beta * p_old[c];
-    float a = pc;
-    if (i > 0) a += ar[c - nt] * (r[c - nt] + beta * p_old[c - nt]);
-    if (i + 1 < nr) a += ar[c] * (r[c + nt] + beta * p_old[c + nt]);
-    if (j > 0) a += at[c - 1] * (r[c - 1] + beta * p_old[c - 1]);
-    if (j + 1 < nt) a += at[c] * (r[c + 1] + beta * p_old[c + 1]);
-    p_new[c] = pc;
-    Ap[c] = a;
-    v = pc * a;
-  } else if (c < n) {
-    p_new[c] = 0.f;
-    Ap[c] = 0.f;
+  for (int t0 = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); t0 < ntiles; t0 += kTileU * nw) {
+    int c[kTileU];
+    float rc[kTileU], pc[kTileU], aro[kTileU], ato[kTileU], ari[kTileU], ati[kTileU];
+    float rn[kTileU][4], pn[kTileU][4];
+#pragma unroll
+    for (int u = 0; u < kTileU; ++u) {
+      const int t = t0 + u * nw;
+      c[u] = t < ntiles ? (tiles ? __ldg(tiles + t) : t) * 32 + lane : n;
+    }
+#pragma unroll
+    for (int u = 0; u < kTileU; ++u) {
+      const int cc = c[u];
+      const bool in = cc < n, dn = in && cc >= nt, up = in && cc + nt < n, lo = in && cc > 0, hi = in && cc + 1 < n;
+      rc[u] = ld_or0(r, cc, in);
+      pc[u] = ld_or0(p_old, cc, in);
+      aro[u] = ld_or0(ar, cc, in);
+      ato[u] = ld_or0(at, cc, in);
+      ari[u] = ld_or0(ar, cc - nt, dn);
+      ati[u] = ld_or0(at, cc - 1, lo);
+      rn[u][0] = ld_or0(r, cc - nt, dn);
+      pn[u][0] = ld_or0(p_old, cc - nt, dn);
+      rn[u][1] = ld_or0(r, cc + nt, up);
+      pn[u][1] = ld_or0(p_old, cc + nt, up);
+      rn[u][2] = ld_or0(r, cc - 1, lo);
+      pn[u][2] = ld_or0(p_old, cc - 1, lo);
+      rn[u][3] = ld_or0(r, cc + 1, hi);
+      pn[u][3] = ld_or0(p_old, cc + 1, hi);
+    }
+#pragma unroll
+    for (int u = 0; u < kTileU; ++u) {
+      if (c[u] >= n) continue;
+      const float p = rc[u] + beta * pc[u];
+      float a = p;
+      a += ari[u] * (rn[u][0] + beta * pn[u][0]);
+      a += aro[u] * (rn[u][1] + beta * pn[u][1]);
+      a += ati[u] * (rn[u][2] + beta * pn[u][2]);
+      a += ato[u] * (rn[u][3] + beta * pn[u][3]);
+      p_new[c[u]] = p;
+      Ap[c[u]] = a;
+      v += p * a;
+    }
   }
   const float s = block_sum_f(v, sh);
   if (threadIdx.x == 0 && s != 0.f) atomicAdd(sc + 2 * k + 1, (double)s);
 }
 
-// kernel B of CG iteration k
-__global__ void k_cg_b(int n, const signed char* __restrict__ mask, const float* __restrict__ p_new,
-                       const float* __restrict__ Ap, float* __restrict__ y, float* __restrict__ r, double* sc, int k,
-                       double tol2) {
+// kernel B of CG iteration k: y += alpha p, r -= alpha Ap, partial r.r
+__global__ void __launch_bounds__(256) k_cg_b(int n, int ntiles, const int* __restrict__ tiles,
+                                              const float* __restrict__ p_new, const float* __restrict__ Ap,
+                                              float* __restrict__ y, float* __restrict__ r, double* sc, int k,
+                                              double tol2) {
   __shared__ float sh[32];
   const double rr0 = rr_of(sc, 0), rrk = rr_of(sc, k);
   if (rrk <= tol2 * rr0 || !(rrk == rrk)) return;
-  const double pap = sc[2 * k + 1];
-  const float alpha = (float)(rrk / pap);
-  const int c = blockIdx.x * blockDim.x + threadIdx.x;
+  const float alpha = (float)(rrk / sc[2 * k + 1]);
+  const int lane = threadIdx.x & 31, nw = gridDim.x * (blockDim.x >> 5);
   float v = 0.f;
-  if (c < n && mask[c] == 2) {
-    y[c] += alpha * p_new[c];
-    const float rn = r[c] - alpha * Ap[c];
-    r[c] = rn;
-    v = rn * rn;
+  for (int t0 = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); t0 < ntiles; t0 += kTileU * nw) {
+    int c[kTileU];
+    float pv[kTileU], av[kTileU], yv[kTileU], rv[kTileU];
+#pragma unroll
+    for (int u = 0; u < kTileU; ++u) {
+      const int t = t0 + u * nw;
+      c[u] = t < ntiles ? (tiles ? __ldg(tiles + t) : t) * 32 + lane : n;
+    }
+#pragma unroll
+    for (int u = 0; u < kTileU; ++u) {
+      const bool in = c[u] < n;
+      pv[u] = in ? p_new[c[u]] : 0.f;
+      av[u] = in ? Ap[c[u]] : 0.f;
+      yv[u] = in ? y[c[u]] : 0.f;
+      rv[u] = in ? r[c[u]] : 0.f;
+    }
+#pragma unroll
+    for (int u = 0; u < kTileU; ++u) {
+      if (c[u] >= n) continue;
+      y[c[u]] = yv[u] + alpha * pv[u];
+      const float rnew = rv[u] - alpha * av[u];
+      r[c[u]] = rnew;
+      v += rnew * rnew;
+    }
   }
   const float s = block_sum_f(v, sh);
   if (threadIdx.x == 0) atomicAdd(sc + 2 * (k + 1), (double)s);
@@ -372,6 +443,47 @@ using namespace mcrt;
 
 static int nblk(int n) { return (n + 255) / 256; }
 
+// grid of the grid-stride PDA kernels: a few resident blocks per SM, so every reduction ends in about a
+// thousand atomics instead of one per 256 cells
+static int sm_count() {
+  static int sms = 0;
+  if (!sms) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (sms <= 0) sms = 128;
+  }
+  return sms;
+}
+
+static int sgrid(int n) { return std::max(1, std::min(nblk(n), sm_count() * 8)); }
+
+// grid of a tile kernel: each resident block slot of the device once (blocks per SM from the
+// occupancy calculator), fewer when there are fewer tiles (8 warps, one tile each, per block)
+template <class K>
+static int tgrid(K kern, int ntiles) {
+  static int occ = 0;
+  if (!occ) {
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, 256, 0) != cudaSuccess || occ <= 0) occ = 1;
+  }
+  return std::max(1, std::min((ntiles + 7) / 8, sm_count() * occ));
+}
+
+// active tiles of a mask (32 consecutive cells with at least one PDA cell), in increasing order
+static std::vector<int> active_tiles(const std::vector<signed char>& mask) {
+  const int n = (int)mask.size();
+  std::vector<int> t;
+  for (int b = 0; b < n; b += 32) {
+    const int e = std::min(n, b + 32);
+    for (int c = b; c < e; ++c)
+      if (mask[c] == 2) {
+        t.push_back(b / 32);
+        break;
+      }
+  }
+  return t;
+}
+
 static mcrt_status pda_alloc(mcrt_disk* d, int max_inner) {
   PdaState* P = d->pda;
   if (!P) {
@@ -400,16 +512,16 @@ static mcrt_status pda_alloc(mcrt_disk* d, int max_inner) {
         el[c] = std::min(r2 - r1, rc * (t2 - t1));
       }
     }
-    cudaError_t e = P->hr_in.alloc(n * 8);
-    if (e == cudaSuccess) e = cudaMemcpy(P->hr_in.p, hi_.data(), n * 8, cudaMemcpyHostToDevice);
-    if (e == cudaSuccess) e = P->hr_out.alloc(n * 8);
-    if (e == cudaSuccess) e = cudaMemcpy(P->hr_out.p, ho.data(), n * 8, cudaMemcpyHostToDevice);
-    if (e == cudaSuccess) e = P->ht_lo.alloc(n * 8);
-    if (e == cudaSuccess) e = cudaMemcpy(P->ht_lo.p, tl.data(), n * 8, cudaMemcpyHostToDevice);
-    if (e == cudaSuccess) e = P->ht_hi.alloc(n * 8);
-    if (e == cudaSuccess) e = cudaMemcpy(P->ht_hi.p, th.data(), n * 8, cudaMemcpyHostToDevice);
-    if (e == cudaSuccess) e = P->ell.alloc(n * 8);
-    if (e == cudaSuccess) e = cudaMemcpy(P->ell.p, el.data(), n * 8, cudaMemcpyHostToDevice);
+    cudaError_t e = P->hr_in.alloc((size_t)n * 8);
+    if (e == cudaSuccess) e = cudaMemcpy(P->hr_in.p, hi_.data(), (size_t)n * 8, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = P->hr_out.alloc((size_t)n * 8);
+    if (e == cudaSuccess) e = cudaMemcpy(P->hr_out.p, ho.data(), (size_t)n * 8, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = P->ht_lo.alloc((size_t)n * 8);
+    if (e == cudaSuccess) e = cudaMemcpy(P->ht_lo.p, tl.data(), (size_t)n * 8, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = P->ht_hi.alloc((size_t)n * 8);
+    if (e == cudaSuccess) e = cudaMemcpy(P->ht_hi.p, th.data(), (size_t)n * 8, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = P->ell.alloc((size_t)n * 8);
+    if (e == cudaSuccess) e = cudaMemcpy(P->ell.p, el.data(), (size_t)n * 8, cudaMemcpyHostToDevice);
     DBuf* d8[] = {&P->kR, &P->D, &P->Cr, &P->Ct, &P->dis, &P->u, &P->lam, &P->b64, &P->rs, &P->w, &P->gl, &P->gk};
     for (DBuf* b : d8)
       if (e == cudaSuccess) e = b->alloc((size_t)n * 8);
@@ -417,6 +529,7 @@ static mcrt_status pda_alloc(mcrt_disk* d, int max_inner) {
     for (DBuf* b : d4)
       if (e == cudaSuccess) e = b->alloc((size_t)n * 4);
     if (e == cudaSuccess) e = P->mask.alloc(n);
+    if (e == cudaSuccess) e = P->tiles.alloc(((size_t)n + 31) / 32 * sizeof(int));
     if (e == cudaSuccess) e = P->red.alloc(16 * 8);
     if (e != cudaSuccess) return cuda_fail(d, e, "PDA buffers");
   }
@@ -471,12 +584,14 @@ static mcrt_status refine_solve(mcrt_disk* d, const mcrt_pda_opts* o, double* x,
   float *y = P->y.as<float>(), *r = P->r.as<float>(), *Ap = P->Ap.as<float>();
   float* pb[2] = {P->p0.as<float>(), P->p1.as<float>()};
   const double tol2_in = o->inner_tol * o->inner_tol;
+  const int* tiles = P->tiles.as<int>();
+  const int ga = tgrid(k_cg_a, P->ntiles), gb = tgrid(k_cg_b, P->ntiles);
   double norm_b = -1.0, best = INFINITY;
   int total_iters = 0, stall = 0;
   const int chunk = 32;
   for (int outer = 0; outer <= o->max_outer; ++outer) {
     CK(cudaMemsetAsync(red + 4, 0, 8, st), "memset");
-    k_resid64<<<nblk(n), 256, 0, st>>>(nr, nt, mask, Cr, Ct, dis, x, b, P->rs.as<double>(), red, 4);
+    k_resid64<<<sgrid(n), 256, 0, st>>>(nr, nt, mask, Cr, Ct, dis, x, b, P->rs.as<double>(), red, 4);
     d->launches++;
     double rn2 = 0.0;
     CK(cudaMemcpyAsync(&rn2, red + 4, 8, cudaMemcpyDeviceToHost, st), "copy");
@@ -499,7 +614,7 @@ static mcrt_status refine_solve(mcrt_disk* d, const mcrt_pda_opts* o, double* x,
     if (outer == o->max_outer) break;
     // inner FP32 CG on the unit-diagonal system
     CK(cudaMemsetAsync(sc, 0, sizeof(double) * (2 * (size_t)o->max_inner + 8), st), "memset");
-    k_start<<<nblk(n), 256, 0, st>>>(n, mask, P->rs.as<double>(), 1.0 / rn, y, r, pb[1], sc);
+    k_start<<<sgrid(n), 256, 0, st>>>(n, mask, P->rs.as<double>(), 1.0 / rn, y, r, pb[1], pb[0], Ap, sc);
     d->launches++;
     int k = 0;
     bool conv = false;
@@ -508,9 +623,9 @@ static mcrt_status refine_solve(mcrt_disk* d, const mcrt_pda_opts* o, double* x,
       for (; k < kend; ++k) {
         float* pnew = pb[k & 1];
         float* pold = pb[(k + 1) & 1];
-        k_cg_a<<<nblk(n), 256, 0, st>>>(nr, nt, mask, P->ar.as<float>(), P->at.as<float>(), r, pold, pnew, Ap, sc, k,
-                                         tol2_in);
-        k_cg_b<<<nblk(n), 256, 0, st>>>(n, mask, pnew, Ap, y, r, sc, k, tol2_in);
+        k_cg_a<<<ga, 256, 0, st>>>(n, nt, P->ntiles, tiles, P->ar.as<float>(), P->at.as<float>(), r, pold, pnew, Ap,
+                                   sc, k, tol2_in);
+        k_cg_b<<<gb, 256, 0, st>>>(n, P->ntiles, tiles, pnew, Ap, y, r, sc, k, tol2_in);
         d->launches += 2;
       }
       std::vector<double> h(2 * (size_t)k + 2);
@@ -577,7 +692,7 @@ mcrt_status mcrt_solve_pda(mcrt_disk* d, const mcrt_pda_opts* o, int* out_n, int
   const double* rho = d->rho_cgs_d.as<double>();
   double chi_max = 0.0;
   for (int b = 0; b < d->nlam; ++b) chi_max = std::max(chi_max, d->kabs[b] + (1.0 - d->g[b]) * d->ksca[b]);
-  k_mask<<<nblk(n), 256, 0, st>>>(n, rho, P->ell.as<double>(), chi_max, o->min_cell_tau,
+  k_mask<<<sgrid(n), 256, 0, st>>>(n, rho, P->ell.as<double>(), chi_max, o->min_cell_tau,
                                   d->visits.as<unsigned long long>(), d->relerr.as<double>(),
                                   d->tally.as<unsigned long long>(), o->min_visits, o->max_rel_err,
                                   P->mask.as<signed char>(), red);
@@ -622,6 +737,11 @@ mcrt_status mcrt_solve_pda(mcrt_disk* d, const mcrt_pda_opts* o, int* out_n, int
   if (out_n) *out_n = P->n_pda;
   if (hred[3] > 0 || !components_ok(d, hmask))
     return set_error(d, MCRT_EINVAL, "a PDA region touches no Monte Carlo cell (singular system)");
+  P->htiles = active_tiles(hmask);
+  P->ntiles = (int)P->htiles.size();
+  if (P->ntiles > 0)
+    CK(cudaMemcpyAsync(P->tiles.p, P->htiles.data(), P->htiles.size() * sizeof(int), cudaMemcpyHostToDevice, st),
+       "copy");
   int iters = 0;
   if (P->n_pda > 0) {
     s = refine_solve(d, o, P->u.as<double>(), nullptr, &iters);
@@ -781,13 +901,15 @@ extern "C" mcrt_status mcrt_pda_solve_static(int device, int nr, int ntheta, con
   CK(cudaGetLastError(), "PDA kernels");
   if (singular > 0) return set_error(nullptr, MCRT_EINVAL, "a PDA cell has no conducting face (singular system)");
   const double tol2_in = o->inner_tol * o->inner_tol;
+  const int ntiles = (n + 31) / 32;  // every tile of the grid
+  const int ga = tgrid(k_cg_a, ntiles), gb = tgrid(k_cg_b, ntiles);
   double norm_b = -1.0, best = INFINITY;
   int total_iters = 0, stall = 0;
   const int chunk = 32;
   double h[2 * chunk + 2];
   for (int outer = 0; outer <= o->max_outer; ++outer) {
     CK(cudaMemsetAsync(red + 4, 0, sizeof(double), st), "memset");
-    k_resid64<<<nblk(n), 256, 0, st>>>(nr, nt, mask_dev, Cr_dev, Ct_dev, dis, u_dev, nullptr, rs, red, 4);
+    k_resid64<<<sgrid(n), 256, 0, st>>>(nr, nt, mask_dev, Cr_dev, Ct_dev, dis, u_dev, nullptr, rs, red, 4);
     double rn2 = 0.0;
     CK(cudaMemcpyAsync(&rn2, red + 4, sizeof(double), cudaMemcpyDeviceToHost, st), "copy");
     CK(cudaStreamSynchronize(st), "synchronize");
@@ -807,15 +929,16 @@ extern "C" mcrt_status mcrt_pda_solve_static(int device, int nr, int ntheta, con
     }
     if (outer == o->max_outer) break;
     CK(cudaMemsetAsync(sc, 0, sizeof(double) * kStaticSc, st), "memset");
-    k_start<<<nblk(n), 256, 0, st>>>(n, mask_dev, rs, 1.0 / rn, y, r, pb[1], sc);
+    k_start<<<sgrid(n), 256, 0, st>>>(n, mask_dev, rs, 1.0 / rn, y, r, pb[1], pb[0], Ap, sc);
     int k = 0;
     bool conv = false;
     while (k < o->max_inner && !conv) {
       const int k0 = k;
       const int kend = std::min(k + chunk, o->max_inner);
       for (; k < kend; ++k) {
-        k_cg_a<<<nblk(n), 256, 0, st>>>(nr, nt, mask_dev, ar, at, r, pb[(k + 1) & 1], pb[k & 1], Ap, sc, k, tol2_in);
-        k_cg_b<<<nblk(n), 256, 0, st>>>(n, mask_dev, pb[k & 1], Ap, y, r, sc, k, tol2_in);
+        k_cg_a<<<ga, 256, 0, st>>>(n, nt, ntiles, nullptr, ar, at, r, pb[(k + 1) & 1], pb[k & 1], Ap, sc, k,
+                                   tol2_in);
+        k_cg_b<<<gb, 256, 0, st>>>(n, ntiles, nullptr, pb[k & 1], Ap, y, r, sc, k, tol2_in);
       }
       // rr_0 and rr_{k0..k}
       double rr0 = 0.0;

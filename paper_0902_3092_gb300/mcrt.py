@@ -241,7 +241,9 @@ class Disk:
         return L.reshape(self.nlam, n_incl)
 
     def solve_pda(self, min_visits=30, max_rel_err=0.05, tol=1e-12, inner_tol=1e-5, max_outer=50, max_inner=20000,
-                  kappa_R=None, min_cell_tau=1.0, rho=None):
+                  kappa_R=None, min_cell_tau=1.0, rho=None, allow_notconv=False):
+        """PDA solve (Sect. 2.2.1, Eq. 4); returns (PDA cells, CG iterations). With allow_notconv an
+        exhausted iteration budget returns normally instead of raising McrtError(ENOTCONV)."""
         o = PdaOpts()
         lib().mcrt_default_pda_opts(C.byref(o))
         o.min_visits, o.max_rel_err, o.tol, o.inner_tol = min_visits, max_rel_err, tol, inner_tol
@@ -255,7 +257,9 @@ class Disk:
             rr = np.ascontiguousarray(rho, np.float64).ravel()
             o.rho = _dp(rr)
         npda, it = C.c_int(), C.c_int()
-        _check(lib().mcrt_solve_pda(self._h, C.byref(o), C.byref(npda), C.byref(it)), self._h)
+        s = lib().mcrt_solve_pda(self._h, C.byref(o), C.byref(npda), C.byref(it))
+        if not (allow_notconv and s == 4):
+            _check(s, self._h)
         return npda.value, it.value
 
     def pda_adjoint(self, w):
