@@ -275,16 +275,24 @@ __device__ __forceinline__ double rr_of(const double* sc, int k) { return sc[2 *
 // order (nullptr: every tile of the grid). They read no mask: outside the PDA region the vectors
 // are zero and so are the scaled couplings ar, at of every face that is not between two PDA cells,
 // including the faces beyond the last radial row / polar column, so the terms of non-PDA
-// neighbours vanish and non-PDA cells keep zero. Each warp walks its tiles grid-stride, kTileU
-// tiles per step with all their loads issued before the arithmetic, so that enough bytes are in
-// flight per SM for HBM; the grid is a few resident blocks per SM, so each reduction ends in about
-// a thousand atomics.
-constexpr int kTileU = 2;
+// neighbours vanish and non-PDA cells keep zero. Warp w takes tiles w, w + nw, w + 2 nw, ... (nw
+// warps in the grid); lane l fetches the index of the warp's l-th next tile, so one load serves 32
+// tiles, and each step handles U tiles with all their loads issued before the arithmetic, so that
+// enough bytes are in flight per SM for HBM. The grid is the device's resident block slots, so each
+// reduction ends in about a thousand atomics.
+constexpr int kUA = 2, kUB = 4;
 
 __device__ __forceinline__ float ld_or0(const float* __restrict__ a, int i, bool ok) { return ok ? __ldg(a + i) : 0.f; }
 
+// first cell of the warp's (s0 + lane)-th tile, or -1 past the end
+__device__ __forceinline__ int tile_base(const int* __restrict__ tiles, int ntiles, int w, int nw, int s) {
+  const long long t = (long long)w + (long long)s * nw;
+  return t < ntiles ? (tiles ? __ldg(tiles + t) : (int)t) * 32 : -1;
+}
+
 // kernel A of CG iteration k: p = r + beta p_old and Ap (p recomputed for the four neighbours from r
 // and p_old), partial p.Ap
+template <int U>
 __global__ void __launch_bounds__(256) k_cg_a(int n, int nt, int ntiles, const int* __restrict__ tiles,
                                               const float* __restrict__ ar, const float* __restrict__ at,
                                               const float* __restrict__ r, const float* __restrict__ p_old,
@@ -295,47 +303,52 @@ __global__ void __launch_bounds__(256) k_cg_a(int n, int nt, int ntiles, const i
   if (rrk <= tol2 * rr0 || !(rrk == rrk)) return;  // converged (or broken): no-op
   const float beta = k == 0 ? 0.f : (float)(rrk / rr_of(sc, k - 1));
   const int lane = threadIdx.x & 31, nw = gridDim.x * (blockDim.x >> 5);
+  const int w = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
   float v = 0.f;
-  for (int t0 = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); t0 < ntiles; t0 += kTileU * nw) {
-    int c[kTileU];
-    float rc[kTileU], pc[kTileU], aro[kTileU], ato[kTileU], ari[kTileU], ati[kTileU];
-    float rn[kTileU][4], pn[kTileU][4];
+  for (int s0 = 0; w + (long long)s0 * nw < ntiles; s0 += 32) {
+    const int base = tile_base(tiles, ntiles, w, nw, s0 + lane);
+#pragma unroll 1
+    for (int u0 = 0; u0 < 32; u0 += U) {
+      int c[U];
 #pragma unroll
-    for (int u = 0; u < kTileU; ++u) {
-      const int t = t0 + u * nw;
-      c[u] = t < ntiles ? (tiles ? __ldg(tiles + t) : t) * 32 + lane : n;
-    }
+      for (int u = 0; u < U; ++u) {
+        const int b = __shfl_sync(0xffffffffu, base, u0 + u);
+        c[u] = b >= 0 ? b + lane : n;
+      }
+      if (__shfl_sync(0xffffffffu, base, u0) < 0) break;  // warp-uniform: later tiles are past the end too
+      float rc[U], pc[U], aro[U], ato[U], ari[U], ati[U], rn[U][4], pn[U][4];
 #pragma unroll
-    for (int u = 0; u < kTileU; ++u) {
-      const int cc = c[u];
-      const bool in = cc < n, dn = in && cc >= nt, up = in && cc + nt < n, lo = in && cc > 0, hi = in && cc + 1 < n;
-      rc[u] = ld_or0(r, cc, in);
-      pc[u] = ld_or0(p_old, cc, in);
-      aro[u] = ld_or0(ar, cc, in);
-      ato[u] = ld_or0(at, cc, in);
-      ari[u] = ld_or0(ar, cc - nt, dn);
-      ati[u] = ld_or0(at, cc - 1, lo);
-      rn[u][0] = ld_or0(r, cc - nt, dn);
-      pn[u][0] = ld_or0(p_old, cc - nt, dn);
-      rn[u][1] = ld_or0(r, cc + nt, up);
-      pn[u][1] = ld_or0(p_old, cc + nt, up);
-      rn[u][2] = ld_or0(r, cc - 1, lo);
-      pn[u][2] = ld_or0(p_old, cc - 1, lo);
-      rn[u][3] = ld_or0(r, cc + 1, hi);
-      pn[u][3] = ld_or0(p_old, cc + 1, hi);
-    }
+      for (int u = 0; u < U; ++u) {
+        const int cc = c[u];
+        const bool in = cc < n, dn = in && cc >= nt, up = in && cc + nt < n, lo = in && cc > 0, hi = in && cc + 1 < n;
+        rc[u] = ld_or0(r, cc, in);
+        pc[u] = ld_or0(p_old, cc, in);
+        aro[u] = ld_or0(ar, cc, in);
+        ato[u] = ld_or0(at, cc, in);
+        ari[u] = ld_or0(ar, cc - nt, dn);
+        ati[u] = ld_or0(at, cc - 1, lo);
+        rn[u][0] = ld_or0(r, cc - nt, dn);
+        pn[u][0] = ld_or0(p_old, cc - nt, dn);
+        rn[u][1] = ld_or0(r, cc + nt, up);
+        pn[u][1] = ld_or0(p_old, cc + nt, up);
+        rn[u][2] = ld_or0(r, cc - 1, lo);
+        pn[u][2] = ld_or0(p_old, cc - 1, lo);
+        rn[u][3] = ld_or0(r, cc + 1, hi);
+        pn[u][3] = ld_or0(p_old, cc + 1, hi);
+      }
 #pragma unroll
-    for (int u = 0; u < kTileU; ++u) {
-      if (c[u] >= n) continue;
-      const float p = rc[u] + beta * pc[u];
-      float a = p;
-      a += ari[u] * (rn[u][0] + beta * pn[u][0]);
-      a += aro[u] * (rn[u][1] + beta * pn[u][1]);
-      a += ati[u] * (rn[u][2] + beta * pn[u][2]);
-      a += ato[u] * (rn[u][3] + beta * pn[u][3]);
-      p_new[c[u]] = p;
-      Ap[c[u]] = a;
-      v += p * a;
+      for (int u = 0; u < U; ++u) {
+        if (c[u] >= n) continue;
+        const float p = rc[u] + beta * pc[u];
+        float a = p;
+        a += ari[u] * (rn[u][0] + beta * pn[u][0]);
+        a += aro[u] * (rn[u][1] + beta * pn[u][1]);
+        a += ati[u] * (rn[u][2] + beta * pn[u][2]);
+        a += ato[u] * (rn[u][3] + beta * pn[u][3]);
+        p_new[c[u]] = p;
+        Ap[c[u]] = a;
+        v += p * a;
+      }
     }
   }
   const float s = block_sum_f(v, sh);
@@ -343,6 +356,7 @@ __global__ void __launch_bounds__(256) k_cg_a(int n, int nt, int ntiles, const i
 }
 
 // kernel B of CG iteration k: y += alpha p, r -= alpha Ap, partial r.r
+template <int U>
 __global__ void __launch_bounds__(256) k_cg_b(int n, int ntiles, const int* __restrict__ tiles,
                                               const float* __restrict__ p_new, const float* __restrict__ Ap,
                                               float* __restrict__ y, float* __restrict__ r, double* sc, int k,
@@ -352,30 +366,36 @@ __global__ void __launch_bounds__(256) k_cg_b(int n, int ntiles, const int* __re
   if (rrk <= tol2 * rr0 || !(rrk == rrk)) return;
   const float alpha = (float)(rrk / sc[2 * k + 1]);
   const int lane = threadIdx.x & 31, nw = gridDim.x * (blockDim.x >> 5);
+  const int w = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
   float v = 0.f;
-  for (int t0 = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); t0 < ntiles; t0 += kTileU * nw) {
-    int c[kTileU];
-    float pv[kTileU], av[kTileU], yv[kTileU], rv[kTileU];
+  for (int s0 = 0; w + (long long)s0 * nw < ntiles; s0 += 32) {
+    const int base = tile_base(tiles, ntiles, w, nw, s0 + lane);
+#pragma unroll 1
+    for (int u0 = 0; u0 < 32; u0 += U) {
+      int c[U];
 #pragma unroll
-    for (int u = 0; u < kTileU; ++u) {
-      const int t = t0 + u * nw;
-      c[u] = t < ntiles ? (tiles ? __ldg(tiles + t) : t) * 32 + lane : n;
-    }
+      for (int u = 0; u < U; ++u) {
+        const int b = __shfl_sync(0xffffffffu, base, u0 + u);
+        c[u] = b >= 0 ? b + lane : n;
+      }
+      if (__shfl_sync(0xffffffffu, base, u0) < 0) break;
+      float pv[U], av[U], yv[U], rv[U];
 #pragma unroll
-    for (int u = 0; u < kTileU; ++u) {
-      const bool in = c[u] < n;
-      pv[u] = in ? p_new[c[u]] : 0.f;
-      av[u] = in ? Ap[c[u]] : 0.f;
-      yv[u] = in ? y[c[u]] : 0.f;
-      rv[u] = in ? r[c[u]] : 0.f;
-    }
+      for (int u = 0; u < U; ++u) {
+        const bool in = c[u] < n;
+        pv[u] = in ? __ldg(p_new + c[u]) : 0.f;
+        av[u] = in ? __ldg(Ap + c[u]) : 0.f;
+        yv[u] = in ? y[c[u]] : 0.f;
+        rv[u] = in ? r[c[u]] : 0.f;
+      }
 #pragma unroll
-    for (int u = 0; u < kTileU; ++u) {
-      if (c[u] >= n) continue;
-      y[c[u]] = yv[u] + alpha * pv[u];
-      const float rnew = rv[u] - alpha * av[u];
-      r[c[u]] = rnew;
-      v += rnew * rnew;
+      for (int u = 0; u < U; ++u) {
+        if (c[u] >= n) continue;
+        y[c[u]] = yv[u] + alpha * pv[u];
+        const float rnew = rv[u] - alpha * av[u];
+        r[c[u]] = rnew;
+        v += rnew * rnew;
+      }
     }
   }
   const float s = block_sum_f(v, sh);
@@ -585,7 +605,7 @@ static mcrt_status refine_solve(mcrt_disk* d, const mcrt_pda_opts* o, double* x,
   float* pb[2] = {P->p0.as<float>(), P->p1.as<float>()};
   const double tol2_in = o->inner_tol * o->inner_tol;
   const int* tiles = P->tiles.as<int>();
-  const int ga = tgrid(k_cg_a, P->ntiles), gb = tgrid(k_cg_b, P->ntiles);
+  const int ga = tgrid(k_cg_a<kUA>, P->ntiles), gb = tgrid(k_cg_b<kUB>, P->ntiles);
   double norm_b = -1.0, best = INFINITY;
   int total_iters = 0, stall = 0;
   const int chunk = 32;
@@ -623,9 +643,9 @@ static mcrt_status refine_solve(mcrt_disk* d, const mcrt_pda_opts* o, double* x,
       for (; k < kend; ++k) {
         float* pnew = pb[k & 1];
         float* pold = pb[(k + 1) & 1];
-        k_cg_a<<<ga, 256, 0, st>>>(n, nt, P->ntiles, tiles, P->ar.as<float>(), P->at.as<float>(), r, pold, pnew, Ap,
+        k_cg_a<kUA><<<ga, 256, 0, st>>>(n, nt, P->ntiles, tiles, P->ar.as<float>(), P->at.as<float>(), r, pold, pnew, Ap,
                                    sc, k, tol2_in);
-        k_cg_b<<<gb, 256, 0, st>>>(n, P->ntiles, tiles, pnew, Ap, y, r, sc, k, tol2_in);
+        k_cg_b<kUB><<<gb, 256, 0, st>>>(n, P->ntiles, tiles, pnew, Ap, y, r, sc, k, tol2_in);
         d->launches += 2;
       }
       std::vector<double> h(2 * (size_t)k + 2);
@@ -902,7 +922,7 @@ extern "C" mcrt_status mcrt_pda_solve_static(int device, int nr, int ntheta, con
   if (singular > 0) return set_error(nullptr, MCRT_EINVAL, "a PDA cell has no conducting face (singular system)");
   const double tol2_in = o->inner_tol * o->inner_tol;
   const int ntiles = (n + 31) / 32;  // every tile of the grid
-  const int ga = tgrid(k_cg_a, ntiles), gb = tgrid(k_cg_b, ntiles);
+  const int ga = tgrid(k_cg_a<kUA>, ntiles), gb = tgrid(k_cg_b<kUB>, ntiles);
   double norm_b = -1.0, best = INFINITY;
   int total_iters = 0, stall = 0;
   const int chunk = 32;
@@ -936,9 +956,9 @@ extern "C" mcrt_status mcrt_pda_solve_static(int device, int nr, int ntheta, con
       const int k0 = k;
       const int kend = std::min(k + chunk, o->max_inner);
       for (; k < kend; ++k) {
-        k_cg_a<<<ga, 256, 0, st>>>(n, nt, ntiles, nullptr, ar, at, r, pb[(k + 1) & 1], pb[k & 1], Ap, sc, k,
+        k_cg_a<kUA><<<ga, 256, 0, st>>>(n, nt, ntiles, nullptr, ar, at, r, pb[(k + 1) & 1], pb[k & 1], Ap, sc, k,
                                    tol2_in);
-        k_cg_b<<<gb, 256, 0, st>>>(n, ntiles, nullptr, pb[k & 1], Ap, y, r, sc, k, tol2_in);
+        k_cg_b<kUB><<<gb, 256, 0, st>>>(n, ntiles, nullptr, pb[k & 1], Ap, y, r, sc, k, tol2_in);
       }
       // rr_0 and rr_{k0..k}
       double rr0 = 0.0;
