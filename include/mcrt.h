@@ -44,7 +44,8 @@ typedef enum {
   MCRT_ECUDA = 3,     /* a CUDA runtime call failed */
   MCRT_ENOTCONV = 4,  /* the PDA solve did not reach its tolerance within its iteration limits */
   MCRT_ETIMEOUT = 5,  /* a device loop hit its iteration guard */
-  MCRT_EOVERFLOW = 6, /* a 64-bit fixed-point tally wrapped (results invalid) */
+  MCRT_EOVERFLOW = 6, /* a 64-bit fixed-point tally may have wrapped: the energy held by all tallies
+                         together (an upper bound of each) passed 2^64 (results invalid) */
   MCRT_ESTATE = 7     /* call order: e.g. transport before mcrt_set_opacity */
 } mcrt_status;
 
@@ -105,7 +106,7 @@ typedef struct {
   uint64_t packets, events, absorptions, scatterings, crossings, mrw_jumps, capped, escaped;
   uint64_t deposit_sum; /* sum over packets of their own fixed-point deposits: equals the growth of the
                            summed tallies when no update was lost */
-  uint32_t error_flags; /* bit 0 tally overflow, bit 1 MRW deposit clipped, bit 2 step guard */
+  uint32_t error_flags; /* bit 0 deposit sum passed 2^64, bit 1 MRW deposit clipped, bit 2 step guard */
   double seconds;       /* device time of the transport kernel(s) */
   uint64_t max_packet_steps;  /* interactions + jumps + face crossings of the longest packet */
   uint64_t longest_packet;    /* its packet id modulo 2^24 */

@@ -294,8 +294,19 @@ static mcrt_status zero_tallies(mcrt_disk* d) {
   d->have_T = false;
   d->have_pda = false;
   d->packets_done = 0;
+  d->tally_held = 0;
+  d->tally_wrapped = false;
   return MCRT_OK;
 }
+
+namespace mcrt {
+bool account_deposits(mcrt_disk* d, const unsigned long long* c) {
+  const unsigned long long before = d->tally_held;
+  d->tally_held += c[C_DEPSUM];
+  if (d->tally_held < before || (c[C_ERR] & kErrOverflow)) d->tally_wrapped = true;
+  return !d->tally_wrapped;
+}
+}  // namespace mcrt
 
 extern "C" {
 
@@ -726,7 +737,7 @@ static mcrt_status run_impl(mcrt_disk* d, uint64_t n_packets, uint64_t seed, uin
   d->have_T = false;
   d->have_pda = false;
   if (stats) stats_from(c, stats, ms * 1e-3);
-  if (c[C_ERR] & kErrOverflow) return set_error(d, MCRT_EOVERFLOW, "fixed-point tally overflow");
+  if (!account_deposits(d, c)) return set_error(d, MCRT_EOVERFLOW, "fixed-point tally overflow");
   if (c[C_ERR] & kErrStepGuard) return set_error(d, MCRT_ETIMEOUT, "packet step guard reached");
   return MCRT_OK;
 }
@@ -828,7 +839,7 @@ mcrt_status mcrt_run_batch(mcrt_disk* const* disks, int n, const uint64_t* n_pac
     disks[i]->have_T = false;
     disks[i]->have_pda = false;
     if (stats) stats_from(ci, &stats[i], ms_ * 1e-3);
-    if (ci[C_ERR] & kErrOverflow) ret = set_error(disks[i], MCRT_EOVERFLOW, "fixed-point tally overflow");
+    if (!account_deposits(disks[i], ci)) ret = set_error(disks[i], MCRT_EOVERFLOW, "fixed-point tally overflow");
   }
   return ret;
 }
@@ -946,6 +957,13 @@ mcrt_status mcrt_restore(mcrt_disk* d, const void* buf, size_t len) {
   CK(cudaStreamSynchronize(d->stream), "synchronize");
   d->packets_done = h[5];
   std::memcpy(&d->n_total, &h[6], 8);
+  d->tally_held = 0;
+  d->tally_wrapped = false;
+  for (size_t c = 0; c < n; ++c) {
+    const unsigned long long t = d->tally_held + h[8 + c];
+    if (t < d->tally_held) d->tally_wrapped = true;
+    d->tally_held = t;
+  }
   d->have_T = false;
   d->have_pda = false;
   return MCRT_OK;
@@ -1233,7 +1251,7 @@ mcrt_status mcrt_batch_run(mcrt_batch* b, uint64_t seed, mcrt_run_stats* stats) 
     b->disks[i]->have_T = false;
     b->disks[i]->have_pda = false;
     if (stats) stats_from(ci, &stats[i], ms_ * 1e-3);
-    if (ci[C_ERR] & kErrOverflow) ret = set_error(b->disks[i], MCRT_EOVERFLOW, "fixed-point tally overflow");
+    if (!account_deposits(b->disks[i], ci)) ret = set_error(b->disks[i], MCRT_EOVERFLOW, "fixed-point tally overflow");
   }
   return ret;
 }

@@ -74,6 +74,10 @@ struct mcrt_disk {
   bool have_T = false, have_pda = false;
   double n_total = 0;         // packet count that sets the packet energy of the tallies
   unsigned long long packets_done = 0;
+  // fixed-point energy held by all tallies together: an upper bound of every cell's tally, so no
+  // cell has wrapped while it has not (tally_wrapped: the bound itself passed 2^64)
+  unsigned long long tally_held = 0;
+  bool tally_wrapped = false;
   float chiR0 = 0, kbar0 = 0;
   mcrt::PdaState* pda = nullptr;
   unsigned long long launches = 0;  // kernels launched by this disk
@@ -88,5 +92,7 @@ mcrt_status cuda_fail(mcrt_disk* d, cudaError_t e, const char* what);
 const float* mrw_table(int device, cudaError_t* err);
 extern const float kMrwT0, kMrwDT;
 mcrt_status compute_temperatures(mcrt_disk* d);
+// adds a run's deposit sum (counters c) to the disk's held energy; false if a tally may have wrapped
+bool account_deposits(mcrt_disk* d, const unsigned long long* c);
 void pda_free(PdaState* p);
 }  // namespace mcrt

@@ -60,10 +60,10 @@ struct Pkt {
   unsigned events, steps, xcross;  // interactions + jumps, all steps, crossings since the last interaction
   uint32_t model, plo, phi, blk, w0, w1, w2, w3;
   int left;
-  int pend_mode;  // 0: bin known; 1: BW bin of (pend_cell, pend_tally -> +EUNIT); 2: exit bin at pend_tally
+  int pend_mode;  // 0: bin known; 1: BW bin of (pend_cell, pend_tally -> +EUNIT); 2: exit bin at pend_tally + pend_add
   int pend_cell;
   float pend_u;
-  unsigned long long pend_tally;
+  unsigned long long pend_tally, pend_add;  // the old tally returned by the deposit's atomic, and the deposit
   int tslot, ntr;
 };
 
@@ -73,6 +73,16 @@ struct Acc {
   unsigned long long depsum;
   unsigned long long longest;  // (steps << 24) | (packet id & 0xffffff) of the lane's longest packet
 };
+
+// Counts a fixed-point deposit. Tally overflow is detected on the sum of all deposits instead of on
+// every atomic's returned value (which would put an L2 round trip on each deposit's critical path):
+// the library adds the run's deposit sum to the energy the tallies already hold, and since every
+// cell's tally is at most that total, no cell wrapped while it stays below 2^64.
+__device__ __forceinline__ void add_deposit(Acc& acc, unsigned long long du) {
+  const unsigned long long t = acc.depsum + du;
+  if (t < du) acc.err |= kErrOverflow;
+  acc.depsum = t;
+}
 
 // next Philox block of a stream: one out-of-line copy, so the 10 rounds are not inlined at every draw
 static __device__ __noinline__ uint4 philox_block(uint32_t blk, uint32_t model, uint32_t plo, uint32_t phi, uint32_t k0,
@@ -173,7 +183,8 @@ __device__ __forceinline__ R hg_mu(R g, R xi) {
 template <class R>
 __device__ __forceinline__ R mrw_x(const KParams<R>& P, R u) {
   const bool lower = u <= (R)0.5;
-  const float t = lower ? logf((float)u) : logf((float)((R)1 - u));
+  const float a = lower ? (float)u : (float)((R)1 - u);
+  const float t = sizeof(R) == 4 ? __logf(a) : logf(a);
   float f = (t - P.mrw_t0) / P.mrw_dt;
   f = fminf(fmaxf(f, 0.f), (float)(kMrwTab - 1) - 1e-3f);
   const int i = (int)f;
@@ -190,7 +201,7 @@ __device__ __forceinline__ void qpos(const DevModel<R>& M, unsigned long long ta
   k = 0;
   w = 0.f;
   if (tally == 0ull) return;
-  const float lq = logf((float)tally) + __ldg(M.lqm + c) + M.lq_run;
+  const float lq = (sizeof(R) == 4 ? __logf((float)tally) : logf((float)tally)) + __ldg(M.lqm + c) + M.lq_run;
   if (!(lq >= __ldg(M.lQk + 1))) return;
   const int nT = M.nT;
   if (lq >= __ldg(M.lQk + nT - 1)) {
@@ -307,7 +318,7 @@ __device__ __forceinline__ void resolve_pending(const DevModel<R>& M, Pkt<R>& s)
   } else if (s.pend_mode == 2) {
     int k;
     float w;
-    qpos(M, s.pend_tally, s.pend_cell, k, w);
+    qpos(M, s.pend_tally + s.pend_add, s.pend_cell, k, w);
     s.lam = sample_exit(M, k, w, s.pend_u);
   }
   s.pend_mode = 0;
@@ -376,10 +387,8 @@ __device__ __forceinline__ void mrw_chain(const KParams<R>& P, const Key& key, c
       acc.err |= kErrMrwClip;
     }
     const unsigned long long du = (unsigned long long)units;
-    // MRW deposits can be large: always check the returned old value for wrap-around
-    const unsigned long long old = atomicAdd(M.tally + c, du);
-    if (old + du < old) acc.err |= kErrOverflow;
-    acc.depsum += du;
+    const unsigned long long old = atomicAdd(M.tally + c, du);  // waited for only where the bin is sampled now
+    add_deposit(acc, du);
     R hx, hy, hz;
     iso_dir(s, key, hx, hy, hz);
     s.px += dm * hx;
@@ -405,7 +414,8 @@ __device__ __forceinline__ void mrw_chain(const KParams<R>& P, const Key& key, c
       } else {
         s.pend_mode = 2;
         s.pend_cell = c;
-        s.pend_tally = old + du;
+        s.pend_tally = old;
+        s.pend_add = du;
         s.pend_u = (float)ul;
       }
     }
@@ -479,7 +489,6 @@ __device__ bool step(const KParams<R>& P, const Key& key, const DevModel<R>& M, 
       if (P.want_lam) {
         // the old tally sets T_old / T_new of the BW re-emission
         const unsigned long long old = atomicAdd(M.tally + c, kEUnit);
-        if (old + kEUnit < old) acc.err |= kErrOverflow;
         if (!(G || M.gray) || TRACE) {
           int ko, kn;
           float wo, wn;
@@ -498,7 +507,7 @@ __device__ bool step(const KParams<R>& P, const Key& key, const DevModel<R>& M, 
         atomicAdd(M.tally + c, kEUnit);  // no wavelength needed: nothing waits for the old value
       }
       atomicAdd(M.nabs + c, 1ull);
-      acc.depsum += kEUnit;
+      add_deposit(acc, kEUnit);
       acc.abs++;
     } else {
       acc.sca++;
@@ -584,6 +593,17 @@ __device__ __forceinline__ unsigned long long warp_sum64(unsigned long long v) {
   return v;
 }
 
+// warp sum that reports a wrap of any partial sum in `carry`
+__device__ __forceinline__ unsigned long long warp_sum64_carry(unsigned long long v, bool& carry) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    const unsigned long long w = __shfl_xor_sync(0xffffffffu, v, o);
+    carry |= v + w < v;
+    v += w;
+  }
+  return v;
+}
+
 // adds the lane counters to the model's run counters (warp-reduced when the whole warp flushes)
 template <class R>
 __device__ __forceinline__ void flush(const DevModel<R>& M, Acc& acc, bool warp_uniform) {
@@ -600,9 +620,19 @@ __device__ __forceinline__ void flush(const DevModel<R>& M, Acc& acc, bool warp_
   v[C_ERR] = acc.err;
   v[C_MAXSTEPS] = acc.longest >> 24;
   v[C_LONGEST] = acc.longest;
+  // the deposit sum first: a wrap of it sets the overflow bit of the error word
+  {
+    bool carry = false;
+    unsigned long long x = v[C_DEPSUM];
+    if (warp_uniform) x = warp_sum64_carry(x, carry);
+    if (!warp_uniform || (threadIdx.x & 31) == 0) {
+      if (x && atomicAdd(M.cnt + C_DEPSUM, x) + x < x) carry = true;
+    }
+    if (carry) v[C_ERR] |= kErrOverflow;
+  }
 #pragma unroll
   for (int i = 0; i < C_LONGEST + 1; ++i) {
-    if (i == C_EVENTS) continue;
+    if (i == C_EVENTS || i == C_DEPSUM) continue;
     unsigned long long x = v[i];
     const bool is_max = (i == C_MAXSTEPS || i == C_LONGEST);
     if (warp_uniform) {
@@ -678,6 +708,16 @@ __global__ void __launch_bounds__(256, transport_min_blocks<R>()) transport_kern
         }
       }
       if (__all_sync(0xffffffffu, done && !active)) break;
+      // a lane that found the queue empty means it is empty for every lane: from here each lane
+      // runs its packet to the end without the refill bookkeeping
+      if (__any_sync(0xffffffffu, done)) {
+        const DevModel<R>& M = BATCH ? P.models[model] : P.m0;
+        while (active) {
+          active = step<R, TRACE, G>(P, key, M, s, acc);
+          if (!active) note_end(s, acc);
+        }
+        break;
+      }
     }
     if (active) {
       const DevModel<R>& M = BATCH ? P.models[model] : P.m0;
@@ -685,6 +725,7 @@ __global__ void __launch_bounds__(256, transport_min_blocks<R>()) transport_kern
       if (!active) note_end(s, acc);
     }
   }
+  __syncwarp();
   if (BATCH) flush(P.models[model], acc, false);
   else flush(P.m0, acc, true);
 }
