@@ -247,6 +247,78 @@ __device__ __forceinline__ R dmin_cell(const DevModel<R>& M, int ir, int it, R p
   return d > (R)0 ? d : (R)0;
 }
 
+// FP32 versions of the three geometry functions above without branches: every candidate is computed
+// and the valid one selected, so the dependency chains of the four faces overlap (a packet that
+// runs alone on its SM is latency bound). They return what the generic versions return.
+template <>
+__device__ __forceinline__ float sphere_far<float>(float b, float c) {
+  const float disc = fmaxf(b * b - c, 0.f);
+  const float q = -(b + copysignf(sqrtf(disc), b));
+  const float s = fmaxf(q, c / q);
+  return q == 0.f ? 0.f : fmaxf(s, 0.f);
+}
+
+template <>
+__device__ __forceinline__ float sphere_near<float>(float b, float c) {
+  const float disc = b * b - c;
+  const float q = -b + sqrtf(fmaxf(disc, 0.f));
+  const float s = fmaxf(c / q, 0.f);
+  return (b < 0.f && disc >= 0.f) ? s : inf_<float>();
+}
+
+template <>
+__device__ __forceinline__ float cone_exit<float>(const DevModel<float>& M, int f, float px, float py, float pz, float ux,
+                                                  float uy, float uz, bool leaving_down) {
+  const int kind = M.fk[f];
+  const float sig = (float)kind, cc = M.c2[f], ss = M.s2[f];
+  // cone nappe (kind +-1)
+  const float A = sig * (cc * (ux * ux + uy * uy) - ss * uz * uz);
+  const float B = sig * (cc * (px * ux + py * uy) - ss * pz * uz);
+  const float C = sig * (cc * (px * px + py * py) - ss * pz * pz);
+  const float disc = B * B - A * C;
+  const float q = -(B + copysignf(sqrtf(fmaxf(disc, 0.f)), B));
+  const bool first = leaving_down == !signbit(B);
+  float s = (first ? q : C) / (first ? A : q);
+  const float r2 = px * px + py * py + pz * pz;
+  s = (s < 0.f && s * s < 1e-18f * r2) ? 0.f : s;
+  const bool cone_ok = disc >= 0.f && q != 0.f && s >= 0.f && sig * (pz + s * uz) >= 0.f;  // s >= 0 is false for NaN
+  // midplane plane (kind 0)
+  const bool toward = leaving_down ? uz > 0.f : uz < 0.f;
+  const float sp = fmaxf(-pz / uz, 0.f);
+  float res = cone_ok ? s : inf_<float>();
+  res = kind == 0 ? (toward ? sp : inf_<float>()) : res;
+  return kind == 2 ? inf_<float>() : res;
+}
+
+template <>
+__device__ __forceinline__ float next_face<float>(const DevModel<float>& M, int ir, int it, float px, float py, float pz,
+                                                  float ux, float uy, float uz, int& face) {
+  const float b = px * ux + py * uy + pz * uz;
+  const float r2 = px * px + py * py + pz * pz;
+  const float so = sphere_far<float>(b, r2 - M.rf2[ir + 1]);
+  const float si = sphere_near<float>(b, r2 - M.rf2[ir]);
+  // the axis faces (theta = 0, pi) have kind 2, so the first and last polar cells need no guard
+  const float sl = cone_exit<float>(M, it, px, py, pz, ux, uy, uz, true);
+  const float su = cone_exit<float>(M, it + 1, px, py, pz, ux, uy, uz, false);
+  float s = so;
+  face = 1;
+  if (si < s) { s = si; face = 0; }
+  if (sl < s) { s = sl; face = 2; }
+  if (su < s) { s = su; face = 3; }
+  return s;
+}
+
+template <>
+__device__ __forceinline__ float dmin_cell<float>(const DevModel<float>& M, int ir, int it, float px, float py, float pz) {
+  const float rc2 = px * px + py * py;
+  const float r = sqrtf(rc2 + pz * pz);
+  const float rc = sqrtf(rc2);
+  const float d0 = fminf(r - M.rf[ir], M.rf[ir + 1] - r);
+  const float dl = M.fk[it] != 2 ? fabsf(rc * M.cf[it] - pz * M.sf[it]) : inf_<float>();
+  const float du = M.fk[it + 1] != 2 ? fabsf(rc * M.cf[it + 1] - pz * M.sf[it + 1]) : inf_<float>();
+  return fmaxf(fminf(d0, fminf(dl, du)), 0.f);
+}
+
 // Polar cell containing the direction of p: the last face k in 1..nt-1 with cos theta_k >= z/r.
 template <class R>
 __device__ __forceinline__ int theta_cell(const DevModel<R>& M, R px, R py, R pz) {

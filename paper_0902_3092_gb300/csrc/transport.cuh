@@ -11,7 +11,8 @@
 //   * interaction: scatter with the albedo (isotropic or Henyey-Greenstein), else absorb: one
 //     packet energy (2^16 counts) is atomically added to the 64-bit cell tally; the returned old
 //     value gives the cell temperature before and after, and the packet is re-emitted at once with
-//     a wavelength from kappa_nu [B_nu(T_new) - B_nu(T_old)] (Bjorkman & Wood 2001);
+//     a wavelength from kappa_nu [B_nu(T_new) - B_nu(T_old)] (Bjorkman & Wood 2001); for gray dust,
+//     where the wavelength only shapes the escape spectrum, the bin is drawn at escape instead;
 //   * MRW (Sect. 2.2.2): after at least `nmin` interactions in the cell, while d_min > gamma/(rho
 //     chi_R) (Eq. 11), the packet jumps to the surface of the sphere of radius R0 = d_min, the time
 //     spent inside comes from the inverse of Eq. 7 (table), and E_gamma c t rho kappa_bar (Eq. 9)
@@ -60,10 +61,11 @@ struct Pkt {
   unsigned events, steps, xcross;  // interactions + jumps, all steps, crossings since the last interaction
   uint32_t model, plo, phi, blk, w0, w1, w2, w3;
   int left;
-  int pend_mode;  // 0: bin known; 1: BW bin of (pend_cell, pend_tally -> +EUNIT); 2: exit bin at pend_tally + pend_add
+  // gray dust: the wavelength only matters for the escape spectrum, so the bin of the last re-emission
+  // is sampled at escape. 0: bin known; 1: BW bin of cell pend_cell; 2: MRW exit bin of pend_cell
+  int pend_mode;
   int pend_cell;
   float pend_u;
-  unsigned long long pend_tally, pend_add;  // the old tally returned by the deposit's atomic, and the deposit
   int tslot, ntr;
 };
 
@@ -307,18 +309,24 @@ __device__ __forceinline__ void trace_ev(const KParams<R>& P, Pkt<R>& s, int typ
   P.tr_n[s.tslot] = s.ntr;
 }
 
+// Samples a pending gray re-emission bin from the cell's tally t at the packet's escape: the BW step
+// from t - EUNIT to t (the last packet energy the cell received), or the MRW exit spectrum at t. The
+// tally then includes the deposits other packets made since the re-emission; waiting for each
+// deposit's returned old value instead would stall every absorption for an L2 round trip.
 template <class R>
 __device__ __forceinline__ void resolve_pending(const DevModel<R>& M, Pkt<R>& s) {
+  if (s.pend_mode == 0) return;
+  const unsigned long long t = *(volatile unsigned long long*)(M.tally + s.pend_cell);
   if (s.pend_mode == 1) {
     int ko, kn;
     float wo, wn;
-    qpos(M, s.pend_tally, s.pend_cell, ko, wo);
-    qpos(M, s.pend_tally + kEUnit, s.pend_cell, kn, wn);
+    qpos(M, t >= kEUnit ? t - kEUnit : 0ull, s.pend_cell, ko, wo);
+    qpos(M, t, s.pend_cell, kn, wn);
     s.lam = sample_bw(M, ko, wo, kn, wn, s.pend_u);
-  } else if (s.pend_mode == 2) {
+  } else {
     int k;
     float w;
-    qpos(M, s.pend_tally + s.pend_add, s.pend_cell, k, w);
+    qpos(M, t, s.pend_cell, k, w);
     s.lam = sample_exit(M, k, w, s.pend_u);
   }
   s.pend_mode = 0;
@@ -387,7 +395,10 @@ __device__ __forceinline__ void mrw_chain(const KParams<R>& P, const Key& key, c
       acc.err |= kErrMrwClip;
     }
     const unsigned long long du = (unsigned long long)units;
-    const unsigned long long old = atomicAdd(M.tally + c, du);  // waited for only where the bin is sampled now
+    const bool lam_now = P.want_lam && (!(G || M.gray) || TRACE);  // the exit bin needs the tally now
+    unsigned long long old = 0;
+    if (lam_now) old = atomicAdd(M.tally + c, du);
+    else atomicAdd(M.tally + c, du);
     add_deposit(acc, du);
     R hx, hy, hz;
     iso_dir(s, key, hx, hy, hz);
@@ -403,21 +414,17 @@ __device__ __forceinline__ void mrw_chain(const KParams<R>& P, const Key& key, c
       iso_dir(s, key, s.ux, s.uy, s.uz);
     }
     const R ul = U(s, key);
-    if (P.want_lam) {
-      if (!(G || M.gray) || TRACE) {
-        int k;
-        float w;
-        qpos(M, old + du, c, k, w);
-        s.lam = sample_exit(M, k, w, (float)ul);
-        s.pend_mode = 0;
-        if (!(G || M.gray)) set_alpha<R, G>(M, s);
-      } else {
-        s.pend_mode = 2;
-        s.pend_cell = c;
-        s.pend_tally = old;
-        s.pend_add = du;
-        s.pend_u = (float)ul;
-      }
+    if (lam_now) {
+      int k;
+      float w;
+      qpos(M, old + du, c, k, w);
+      s.lam = sample_exit(M, k, w, (float)ul);
+      s.pend_mode = 0;
+      if (!(G || M.gray)) set_alpha<R, G>(M, s);
+    } else if (P.want_lam) {
+      s.pend_mode = 2;
+      s.pend_cell = c;
+      s.pend_u = (float)ul;
     }
     s.events++;
     acc.mrw++;
@@ -486,25 +493,23 @@ __device__ bool step(const KParams<R>& P, const Key& key, const DevModel<R>& M, 
     const R g = sca ? ((G || M.gray) ? M.g0 : M.gq[s.lam]) : (R)0;
     if (!sca) {
       const R ul = U(s, key);  // BW re-emission bin draw, before the new direction
-      if (P.want_lam) {
+      if (P.want_lam && (!(G || M.gray) || TRACE)) {
         // the old tally sets T_old / T_new of the BW re-emission
         const unsigned long long old = atomicAdd(M.tally + c, kEUnit);
-        if (!(G || M.gray) || TRACE) {
-          int ko, kn;
-          float wo, wn;
-          qpos(M, old, c, ko, wo);
-          qpos(M, old + kEUnit, c, kn, wn);
-          s.lam = sample_bw(M, ko, wo, kn, wn, (float)ul);
-          s.pend_mode = 0;
-          if (!(G || M.gray)) set_alpha<R, G>(M, s);
-        } else {
+        int ko, kn;
+        float wo, wn;
+        qpos(M, old, c, ko, wo);
+        qpos(M, old + kEUnit, c, kn, wn);
+        s.lam = sample_bw(M, ko, wo, kn, wn, (float)ul);
+        s.pend_mode = 0;
+        if (!(G || M.gray)) set_alpha<R, G>(M, s);
+      } else {
+        atomicAdd(M.tally + c, kEUnit);  // nothing waits for the old value
+        if (P.want_lam) {
           s.pend_mode = 1;
           s.pend_cell = c;
-          s.pend_tally = old;
           s.pend_u = (float)ul;
         }
-      } else {
-        atomicAdd(M.tally + c, kEUnit);  // no wavelength needed: nothing waits for the old value
       }
       atomicAdd(M.nabs + c, 1ull);
       add_deposit(acc, kEUnit);
