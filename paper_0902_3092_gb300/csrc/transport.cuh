@@ -368,12 +368,17 @@ __device__ __forceinline__ void launch_packet(const KParams<R>& P, const Key& ke
   acc.packets++;
 }
 
+// safety margin applied to d_min when it serves as the lower bound of the distance to the cell boundary
+template <class R>
+__device__ __forceinline__ R dsafe_margin() { return sizeof(R) == 4 ? (R)(1.0 - 1e-5) : (R)(1.0 - 1e-12); }
+
 template <class R, bool TRACE, bool G>
 __device__ __forceinline__ void mrw_chain(const KParams<R>& P, const Key& key, const DevModel<R>& M, Pkt<R>& s, int c, Acc& acc) {
   const R rho = M.rho[c];
   for (;;) {
     if (s.events >= P.max_events) break;
     const R dm = dmin_cell(M, s.ir, s.it, s.px, s.py, s.pz);
+    s.dsafe = dm * dsafe_margin<R>();  // d_min at the current position bounds the next flight's face test
     R chiR, kb;
     if (G || M.gray) {
       chiR = M.chiR0;
@@ -428,7 +433,7 @@ __device__ __forceinline__ void mrw_chain(const KParams<R>& P, const Key& key, c
     }
     s.events++;
     acc.mrw++;
-    s.dsafe = (R)0;
+    s.dsafe = (R)0;  // set again from d_min at the landing point by the next pass of the loop
     trace_ev<R, TRACE>(P, s, EV_MRW, c);
   }
 }
@@ -471,8 +476,7 @@ __device__ bool step(const KParams<R>& P, const Key& key, const DevModel<R>& M, 
   if (s_int < s.dsafe) {
     interact = true;
   } else {
-    const R margin = sizeof(R) == 4 ? (R)(1.0 - 1e-5) : (R)(1.0 - 1e-12);
-    const R dm = dmin_cell(M, s.ir, s.it, s.px, s.py, s.pz) * margin;
+    const R dm = dmin_cell(M, s.ir, s.it, s.px, s.py, s.pz) * dsafe_margin<R>();
     if (s_int < dm) {
       interact = true;
       s.dsafe = dm;
