@@ -322,6 +322,7 @@ void mcrt_default_run_opts(mcrt_run_opts* o) {
   o->n_total_packets = 0;
   o->block_size = 0;
   o->refill_interval = 0;
+  o->tail_warps_per_sm = 0;
   o->want_sed = 1;
 }
 
@@ -585,6 +586,8 @@ static mcrt_status check_opts(mcrt_disk* d, const mcrt_run_opts* o) {
   if (o->block_size && (o->block_size % 32 || o->block_size > 256))
     return set_error(d, MCRT_EINVAL, "block_size must be a multiple of 32 up to 256");
   if (o->refill_interval < 0) return set_error(d, MCRT_EINVAL, "refill_interval < 0");
+  if (o->tail_warps_per_sm < -1 || o->tail_warps_per_sm > 32)
+    return set_error(d, MCRT_EINVAL, "tail_warps_per_sm must be -1..32");
   return MCRT_OK;
 }
 
@@ -628,6 +631,29 @@ static void stats_from(const unsigned long long* c, mcrt_run_stats* s, double se
 
 // events = scatterings + absorptions + MRW jumps (the kernel counts the three separately)
 static void fix_events(unsigned long long* c) { c[C_EVENTS] = c[C_ABS] + c[C_SCA] + c[C_MRW]; }
+
+// sizes the tail pool for `cap` threads and clears its counters on the disk's stream; without it
+// (allocation failure, or tail kernel off) the transport kernel finishes every packet itself
+template <class R>
+static bool setup_pool(mcrt_disk* d, KParams<R>& P, unsigned cap, int tail_warps) {
+  P.pool = nullptr;
+  P.pool_ctr = nullptr;
+  P.pool_cap = 0;
+  if (tail_warps < 0) return false;
+  if (d->pool_cap < cap) {
+    d->pool_cap = 0;
+    if (d->pool.alloc((size_t)cap * sizeof(Pkt<double>)) != cudaSuccess || d->pool_ctr.alloc(16) != cudaSuccess) {
+      cudaGetLastError();
+      return false;
+    }
+    d->pool_cap = cap;
+  }
+  if (cudaMemsetAsync(d->pool_ctr.p, 0, 16, d->stream) != cudaSuccess) return false;
+  P.pool = d->pool.as<Pkt<R>>();
+  P.pool_ctr = d->pool_ctr.as<unsigned>();
+  P.pool_cap = cap;
+  return true;
+}
 
 static mcrt_status run_impl(mcrt_disk* d, uint64_t n_packets, uint64_t seed, uint64_t first_id,
                             const mcrt_run_opts* o, mcrt_run_stats* stats, int trace_max, int32_t* tr_type,
@@ -689,8 +715,13 @@ static mcrt_status run_impl(mcrt_disk* d, uint64_t n_packets, uint64_t seed, uin
       const int bps = transport_blocks_per_sm<double>(trace, false, d->gray, block);
       const long long want = (long long)((n_packets + block - 1) / block);
       const int grid = (int)std::max(1ll, std::min<long long>(want, (long long)dev_sms * std::max(1, bps)));
+      const bool tail = setup_pool(d, P, (unsigned)grid * block, o->tail_warps_per_sm);
       e = launch_transport<double>(P, trace, false, d->gray, grid, block, d->stream);
       d->launches++;
+      if (e == cudaSuccess && tail) {
+        e = launch_transport_tail<double>(P, trace, d->gray, dev_sms, o->tail_warps_per_sm, d->stream);
+        d->launches++;
+      }
     } else {
       KParams<float> P;
       std::memset(&P, 0, sizeof(P));
@@ -706,8 +737,13 @@ static mcrt_status run_impl(mcrt_disk* d, uint64_t n_packets, uint64_t seed, uin
       const int bps = transport_blocks_per_sm<float>(false, false, d->gray, block);
       const long long want = (long long)((n_packets + block - 1) / block);
       const int grid = (int)std::max(1ll, std::min<long long>(want, (long long)dev_sms * std::max(1, bps)));
+      const bool tail = setup_pool(d, P, (unsigned)grid * block, o->tail_warps_per_sm);
       e = launch_transport<float>(P, false, false, d->gray, grid, block, d->stream);
       d->launches++;
+      if (e == cudaSuccess && tail) {
+        e = launch_transport_tail<float>(P, false, d->gray, dev_sms, o->tail_warps_per_sm, d->stream);
+        d->launches++;
+      }
     }
     if (e != cudaSuccess) {
       cudaEventDestroy(ev0);

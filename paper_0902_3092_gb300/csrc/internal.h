@@ -43,6 +43,10 @@ cudaError_t launch_transport(const KParams<R>& P, bool trace, bool batch, bool g
                              cudaStream_t st);
 template <class R>
 int transport_blocks_per_sm(bool trace, bool batch, bool gray, int block);
+// tail kernel of a single-disk launch: 32-thread blocks, warps_per_sm of them per SM (0: 16)
+template <class R>
+cudaError_t launch_transport_tail(const KParams<R>& P, bool trace, bool gray, int sms, int warps_per_sm,
+                                  cudaStream_t st);
 
 }  // namespace mcrt
 
@@ -69,6 +73,8 @@ struct mcrt_disk {
   mcrt::DBuf mass_d, rho_cgs_d;
   // tallies
   mcrt::DBuf tally, visits, nabs, sed, cnt, queue;
+  mcrt::DBuf pool, pool_ctr;  // packets in flight when the queue drains (one slot per thread of the launch)
+  unsigned pool_cap = 0;
   // temperatures
   mcrt::DBuf T_mc, relerr, T_pda;
   bool have_T = false, have_pda = false;

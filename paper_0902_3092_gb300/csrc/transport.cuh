@@ -27,6 +27,9 @@
 namespace mcrt {
 
 template <class R>
+struct Pkt;
+
+template <class R>
 struct KParams {
   DevModel<R> m0;              // the model of single-disk launches
   const DevModel<R>* models;   // batch launches: descriptors in global memory
@@ -44,6 +47,10 @@ struct KParams {
   unsigned long long max_steps;  // loop guard per packet
   const float* mrw_tab;        // 2*kMrwTab: x(ln u) for u <= 1/2, then 1/x(ln(1-u)) for u > 1/2
   float mrw_t0, mrw_dt;        // table abscissae t = t0 + i dt
+  // packets in flight when the queue drains, handed to the tail kernel (single-disk launches)
+  Pkt<R>* pool;                // one slot per thread of the launch: long packets from the front,
+  unsigned* pool_ctr;          // the others from the back; [0] long, [1] others, [2] taken by the tail
+  unsigned pool_cap;
   // debug trace (TRACE builds)
   int trace_n, trace_max;
   int32_t *tr_type, *tr_cell, *tr_lam, *tr_n;
@@ -68,6 +75,9 @@ struct Pkt {
   float pend_u;
   int tslot, ntr;
 };
+
+// packets that had taken this many steps when the queue drained go first in the tail kernel
+constexpr unsigned kTailLongSteps = 20000u;
 
 // Per-lane run counters, flushed once per launch (32-bit: a lane's share of a launch stays far below 2^32)
 struct Acc {
@@ -669,6 +679,30 @@ __device__ __forceinline__ int find_model(const KParams<R>& P, unsigned long lon
   return lo;
 }
 
+// Tail of a single-disk launch. When the queue drains, the packets still in flight are mostly long
+// ones (a lane holds a long packet for long), and lanes of one warp that follow different branches
+// share its issue slots, so in the transport kernel a long packet would then advance at a fraction of
+// its speed alone. The transport kernel therefore stores them (state unchanged, so the random stream
+// and the result are the same) and this kernel runs them one per warp: lane 0 of each 32-thread block
+// takes packets from the pool, those that had taken at least kTailLongSteps steps first.
+template <class R, bool TRACE, bool G>
+__global__ void __launch_bounds__(32) transport_tail_kernel(const KParams<R> P) {
+  if (threadIdx.x != 0) return;
+  const Key key{(uint32_t)P.seed, (uint32_t)(P.seed >> 32)};
+  const DevModel<R>& M = P.m0;
+  Acc acc = Acc{};
+  const unsigned nlong = P.pool_ctr[0], nshort = P.pool_ctr[1];
+  for (;;) {
+    const unsigned k = atomicAdd(P.pool_ctr + 2, 1u);
+    if (k >= nlong + nshort) break;
+    Pkt<R> s = P.pool[k < nlong ? k : P.pool_cap - 1u - (k - nlong)];
+    while (step<R, TRACE, G>(P, key, M, s, acc)) {
+    }
+    note_end(s, acc);
+  }
+  flush(M, acc, false);
+}
+
 // resident 256-thread blocks per SM the FP32 kernel is compiled for (register budget 65536 / (256 n))
 #ifndef MCRT_TRANSPORT_MIN_BLOCKS
 #define MCRT_TRANSPORT_MIN_BLOCKS 3
@@ -717,9 +751,18 @@ __global__ void __launch_bounds__(256, transport_min_blocks<R>()) transport_kern
         }
       }
       if (__all_sync(0xffffffffu, done && !active)) break;
-      // a lane that found the queue empty means it is empty for every lane: from here each lane
-      // runs its packet to the end without the refill bookkeeping
+      // a lane that found the queue empty means it is empty for every lane: single-disk launches
+      // hand the packets still in flight to the tail kernel; batches run them to the end here
       if (__any_sync(0xffffffffu, done)) {
+        if (!BATCH && P.pool) {
+          if (active) {
+            const bool longp = s.steps >= kTailLongSteps;
+            const unsigned k = atomicAdd(P.pool_ctr + (longp ? 0 : 1), 1u);
+            const unsigned slot = longp ? k : P.pool_cap - 1u - k;  // the two ends never meet: one per thread
+            P.pool[slot] = s;
+          }
+          break;
+        }
         const DevModel<R>& M = BATCH ? P.models[model] : P.m0;
         while (active) {
           active = step<R, TRACE, G>(P, key, M, s, acc);
