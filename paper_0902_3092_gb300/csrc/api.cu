@@ -323,6 +323,7 @@ void mcrt_default_run_opts(mcrt_run_opts* o) {
   o->block_size = 0;
   o->refill_interval = 0;
   o->tail_warps_per_sm = 0;
+  o->interact_batch = 0;
   o->want_sed = 1;
 }
 
@@ -588,6 +589,7 @@ static mcrt_status check_opts(mcrt_disk* d, const mcrt_run_opts* o) {
   if (o->refill_interval < 0) return set_error(d, MCRT_EINVAL, "refill_interval < 0");
   if (o->tail_warps_per_sm < -1 || o->tail_warps_per_sm > 32)
     return set_error(d, MCRT_EINVAL, "tail_warps_per_sm must be -1..32");
+  if (o->interact_batch < 0 || o->interact_batch > 32) return set_error(d, MCRT_EINVAL, "interact_batch must be 0..32");
   return MCRT_OK;
 }
 
@@ -597,6 +599,7 @@ static void fill_params(KParams<R>& P, const mcrt_run_opts* o, uint64_t seed, co
   P.nmin = o->mrw_min_interactions;
   P.exit_dir = o->mrw_exit_dir;
   P.refill = o->refill_interval > 0 ? o->refill_interval : 4;
+  P.defer = o->interact_batch > 0 ? o->interact_batch : 8;
   P.gamma = (R)o->gamma;
   P.seed = seed;
   // per-packet counters are 32-bit: caps above 2^31 events (4e9 steps) are clamped

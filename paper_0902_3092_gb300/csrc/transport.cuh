@@ -39,6 +39,7 @@ struct KParams {
   int exit_dir;                // 0 isotropic, 1 cosine-weighted outward
   int want_lam;                // sample emission bins (1), or skip them for gray dust without SED (0)
   int refill;                  // refill finished lanes every `refill` steps
+  int defer;                   // a warp runs the interaction code once this many lanes wait at one
   R gamma;
   unsigned long long total;    // packets in the queue
   unsigned long long* queue;   // queue head (global counter)
@@ -74,6 +75,7 @@ struct Pkt {
   int pend_cell;
   float pend_u;
   int tslot, ntr;
+  int pend;  // 1: moved to an interaction point whose interaction has not run yet
 };
 
 // packets that had taken this many steps when the queue drained go first in the tail kernel
@@ -373,6 +375,7 @@ __device__ __forceinline__ void launch_packet(const KParams<R>& P, const Key& ke
   s.pend_mode = 0;
   s.tslot = tslot;
   s.ntr = 0;
+  s.pend = 0;
   trace_ev<R, TRACE>(P, s, EV_LAUNCH, -1);
   s.tau = neg_log<R>(U(s, key));
   acc.packets++;
@@ -448,13 +451,15 @@ __device__ __forceinline__ void mrw_chain(const KParams<R>& P, const Key& key, c
   }
 }
 
-// One step of a packet. Returns false when the packet has ended.
+// Moves a packet to its next event: enters the next cell (1), reaches an interaction point (2, the
+// interaction itself is left to interact()), or ends (0: escaped, or a step guard).
 template <class R, bool TRACE, bool G>
-__device__ bool step(const KParams<R>& P, const Key& key, const DevModel<R>& M, Pkt<R>& s, Acc& acc) {
+__device__ __forceinline__ int advance(const KParams<R>& P, const Key& key, const DevModel<R>& M, Pkt<R>& s,
+                                       Acc& acc) {
   if (++s.steps > P.max_steps) {
     acc.err |= kErrStepGuard;
     acc.capped++;
-    return false;
+    return 0;
   }
   if (s.ir < 0) {  // inner cavity: straight to r_in
     const R b = s.px * s.ux + s.py * s.uy + s.pz * s.uz;
@@ -472,91 +477,42 @@ __device__ bool step(const KParams<R>& P, const Key& key, const DevModel<R>& M, 
     atomicAdd(M.visits + c, 1ull);
     acc.cross++;
     trace_ev<R, TRACE>(P, s, EV_CROSS, c);
-    return true;
+    return 1;
   }
-  const int c = s.ir * M.nt + s.it;
   const R alpha = s.alpha;
   R s_int;
   if (!(alpha > (R)0)) s_int = inf_<R>();
   else if (sizeof(R) == 8) s_int = s.tau / alpha;  // the FP64 path divides like the CPU reference
   else s_int = s.tau * s.ialpha;
-  bool interact;
+  bool hit;  // the interaction comes before the cell boundary
   R s_face = (R)0;
   int face = 1;
   if (s_int < s.dsafe) {
-    interact = true;
+    hit = true;
   } else {
     const R dm = dmin_cell(M, s.ir, s.it, s.px, s.py, s.pz) * dsafe_margin<R>();
     if (s_int < dm) {
-      interact = true;
+      hit = true;
       s.dsafe = dm;
     } else {
       s_face = next_face(M, s.ir, s.it, s.px, s.py, s.pz, s.ux, s.uy, s.uz, face);
-      interact = s_int < s_face;
+      hit = s_int < s_face;
       s.dsafe = (R)0;
     }
   }
-  if (interact) {
+  if (hit) {
     s.xcross = 0;
     s.px += s_int * s.ux;
     s.py += s_int * s.uy;
     s.pz += s_int * s.uz;
     s.dsafe = s.dsafe > s_int ? s.dsafe - s_int : (R)0;
-    const R om = (G || M.gray) ? M.alb0 : M.alb[s.lam];
-    const bool sca = U(s, key) < om;
-    const R g = sca ? ((G || M.gray) ? M.g0 : M.gq[s.lam]) : (R)0;
-    if (!sca) {
-      const R ul = U(s, key);  // BW re-emission bin draw, before the new direction
-      if (P.want_lam && (!(G || M.gray) || TRACE)) {
-        // the old tally sets T_old / T_new of the BW re-emission
-        const unsigned long long old = atomicAdd(M.tally + c, kEUnit);
-        int ko, kn;
-        float wo, wn;
-        qpos(M, old, c, ko, wo);
-        qpos(M, old + kEUnit, c, kn, wn);
-        s.lam = sample_bw(M, ko, wo, kn, wn, (float)ul);
-        s.pend_mode = 0;
-        if (!(G || M.gray)) set_alpha<R, G>(M, s);
-      } else {
-        atomicAdd(M.tally + c, kEUnit);  // nothing waits for the old value
-        if (P.want_lam) {
-          s.pend_mode = 1;
-          s.pend_cell = c;
-          s.pend_u = (float)ul;
-        }
-      }
-      atomicAdd(M.nabs + c, 1ull);
-      add_deposit(acc, kEUnit);
-      acc.abs++;
-    } else {
-      acc.sca++;
-    }
-    // new direction: Henyey-Greenstein turn for anisotropic scattering, isotropic otherwise (scattering
-    // with g = 0 and re-emission share this code)
-    if (g != (R)0) {
-      const R mu = hg_mu(g, U(s, key));
-      const R u2 = U(s, key);
-      turn<R>(s.ux, s.uy, s.uz, mu, u2);
-    } else {
-      iso_dir(s, key, s.ux, s.uy, s.uz);
-    }
-    trace_ev<R, TRACE>(P, s, sca ? EV_SCATTER : EV_ABSORB, c);
-    s.events++;
-    s.ninc++;
-    if (P.mrw && s.ninc >= P.nmin) mrw_chain<R, TRACE, G>(P, key, M, s, c, acc);
-    if (s.events >= P.max_events) {
-      acc.capped++;
-      trace_ev<R, TRACE>(P, s, EV_CAPPED, c);
-      return false;
-    }
-    s.tau = neg_log<R>(U(s, key));
-    return true;
+    return 2;
   }
   // cross a face
   if (++s.xcross > 100000u) {
     acc.err |= kErrStepGuard;
     acc.capped++;
-    return false;
+    return 0;
   }
   s.px += s_face * s.ux;
   s.py += s_face * s.uy;
@@ -575,20 +531,89 @@ __device__ bool step(const KParams<R>& P, const Key& key, const DevModel<R>& M, 
     atomicAdd(M.sed + s.lam * kNInc + ib, 1ull);
     acc.escaped++;
     trace_ev<R, TRACE>(P, s, EV_ESCAPE, -1);
-    return false;
+    return 0;
   }
   if (s.ir < 0) {
     s.alpha = (R)0;
     s.ialpha = (R)0;
     trace_ev<R, TRACE>(P, s, EV_CROSS, -1);
-    return true;
+    return 1;
   }
   s.ninc = 0;
   set_alpha<R, G>(M, s);
   const int cn = s.ir * M.nt + s.it;
   atomicAdd(M.visits + cn, 1ull);
   trace_ev<R, TRACE>(P, s, EV_CROSS, cn);
+  return 1;
+}
+
+// The interaction at the packet's current point (Sect. 2.1): scattering or absorption with immediate
+// re-emission, then the MRW chain (Sect. 2.2.2) and the next optical depth. False: capped.
+template <class R, bool TRACE, bool G>
+__device__ __forceinline__ bool interact(const KParams<R>& P, const Key& key, const DevModel<R>& M, Pkt<R>& s,
+                                         Acc& acc) {
+  const int c = s.ir * M.nt + s.it;
+  const R om = (G || M.gray) ? M.alb0 : M.alb[s.lam];
+  const bool sca = U(s, key) < om;
+  const R g = sca ? ((G || M.gray) ? M.g0 : M.gq[s.lam]) : (R)0;
+  if (!sca) {
+    const R ul = U(s, key);  // BW re-emission bin draw, before the new direction
+    if (P.want_lam && (!(G || M.gray) || TRACE)) {
+      // the old tally sets T_old / T_new of the BW re-emission
+      const unsigned long long old = atomicAdd(M.tally + c, kEUnit);
+      int ko, kn;
+      float wo, wn;
+      qpos(M, old, c, ko, wo);
+      qpos(M, old + kEUnit, c, kn, wn);
+      s.lam = sample_bw(M, ko, wo, kn, wn, (float)ul);
+      s.pend_mode = 0;
+      if (!(G || M.gray)) set_alpha<R, G>(M, s);
+    } else {
+      atomicAdd(M.tally + c, kEUnit);  // nothing waits for the old value
+      if (P.want_lam) {
+        s.pend_mode = 1;
+        s.pend_cell = c;
+        s.pend_u = (float)ul;
+      }
+    }
+    atomicAdd(M.nabs + c, 1ull);
+    add_deposit(acc, kEUnit);
+    acc.abs++;
+  } else {
+    acc.sca++;
+  }
+  // new direction: Henyey-Greenstein turn for anisotropic scattering, isotropic otherwise (scattering
+  // with g = 0 and re-emission share this code)
+  if (g != (R)0) {
+    const R mu = hg_mu(g, U(s, key));
+    const R u2 = U(s, key);
+    turn<R>(s.ux, s.uy, s.uz, mu, u2);
+  } else {
+    iso_dir(s, key, s.ux, s.uy, s.uz);
+  }
+  trace_ev<R, TRACE>(P, s, sca ? EV_SCATTER : EV_ABSORB, c);
+  s.events++;
+  s.ninc++;
+  if (P.mrw && s.ninc >= P.nmin) mrw_chain<R, TRACE, G>(P, key, M, s, c, acc);
+  if (s.events >= P.max_events) {
+    acc.capped++;
+    trace_ev<R, TRACE>(P, s, EV_CAPPED, c);
+    return false;
+  }
+  s.tau = neg_log<R>(U(s, key));
   return true;
+}
+
+// One event of a packet, an interaction run at once. False when the packet has ended.
+template <class R, bool TRACE, bool G>
+__device__ __forceinline__ bool step(const KParams<R>& P, const Key& key, const DevModel<R>& M, Pkt<R>& s, Acc& acc) {
+  if (s.pend) {
+    s.pend = 0;
+    return interact<R, TRACE, G>(P, key, M, s, acc);
+  }
+  const int r = advance<R, TRACE, G>(P, key, M, s, acc);
+  if (r == 2) return interact<R, TRACE, G>(P, key, M, s, acc);
+  return r == 1;
 }
 
 template <class R>
@@ -771,10 +796,31 @@ __global__ void __launch_bounds__(256, transport_min_blocks<R>()) transport_kern
         break;
       }
     }
-    if (active) {
-      const DevModel<R>& M = BATCH ? P.models[model] : P.m0;
-      active = step<R, TRACE, G>(P, key, M, s, acc);
-      if (!active) note_end(s, acc);
+    // Lanes that reach an interaction point wait there until `defer` lanes of the warp (or every
+    // moving lane) do, so the long interaction code runs for many lanes at once while the others
+    // keep crossing cells; a packet's own sequence of events and random draws is unchanged.
+    const DevModel<R>& M = BATCH ? P.models[model] : P.m0;
+    if (active && !s.pend) {
+      const int r = advance<R, TRACE, G>(P, key, M, s, acc);
+      if (r == 0) {
+        active = false;
+        note_end(s, acc);
+      } else if (r == 2) {
+        s.pend = 1;
+      }
+    }
+    const unsigned waiting = __ballot_sync(0xffffffffu, active && s.pend);
+    if (waiting) {
+      const unsigned moving = __ballot_sync(0xffffffffu, active && !s.pend);
+      if (__popc(waiting) >= P.defer || !moving) {
+        if (active && s.pend) {
+          s.pend = 0;
+          if (!interact<R, TRACE, G>(P, key, M, s, acc)) {
+            active = false;
+            note_end(s, acc);
+          }
+        }
+      }
     }
   }
   __syncwarp();
