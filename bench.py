@@ -33,18 +33,21 @@ METRIC = "photon packets/s (MRW+PDA vs plain MC) at tau_mid=1e6, equal T accurac
 UNIT = "packets/s"
 WORKLOAD = "thick gray disk 200x120 rim-refined, tau_mid=1e6, albedo 0.5 isotropic, MRW gamma=2 + PDA"
 
-# Work per transport step (an interaction with its MRW jumps, or a face crossing) of the FP32 kernel on
+# Work per transport step (an interaction, an MRW jump or a face crossing) of one FP32 transport call on
 # this workload: ncu smsp__inst_executed.sum (warp instructions) and smsp__thread_inst_executed.sum
-# (thread instructions) over a whole 1e8-packet launch, divided by its steps (profiles/). The kernel is
-# bound by instruction issue (divergent, latency-bound integer/FP32 work, no DRAM traffic), so the
-# roofline is issue slots: 152 SMs x 4 schedulers x 1 warp instruction per clock at 2070 MHz.
-WARP_INST_PER_STEP = 74.0
-THREAD_INST_PER_STEP = 363.0
+# (thread instructions) of its two kernels (the persistent transport kernel and the tail kernel that
+# finishes the packets in flight when the queue drains) over a whole 1e8-packet call, divided by its
+# steps (profiles/). The kernels are bound by instruction issue (divergent, latency-bound integer/FP32
+# work, no DRAM traffic), so the roofline is issue slots: 152 SMs x 4 schedulers x 1 warp instruction
+# per clock at 2070 MHz.
+WARP_INST_PER_STEP = 59.0
+THREAD_INST_PER_STEP = 355.0
 ISSUE_PEAK = 152 * 4 * 2070e6           # warp instructions / s
 THREAD_ISSUE_PEAK = 32 * ISSUE_PEAK     # thread instructions / s (all lanes busy)
-# DRAM bytes of one transport launch (ncu dram__bytes_read.sum + dram__bytes_write.sum on a 1e7-packet
-# launch of this workload): the tallies and tables stay in L2, so traffic does not grow with packets.
-TRANSPORT_DRAM_BYTES = 1050368
+# DRAM bytes of one transport call (ncu dram__bytes_read.sum + dram__bytes_write.sum of its two kernels,
+# 1e7 packets of this workload): tables and tallies stay in L2; the tail kernel reads the ~1.2e5 packet
+# states stored at the drain (14 MB). Neither grows with the packet count.
+TRANSPORT_DRAM_BYTES = 1632000 + 16640 + 15819520 + 256
 
 
 def parse():
@@ -380,7 +383,7 @@ def main():
     thread_achieved = THREAD_INST_PER_STEP * steps_per_launch / float(np.mean(tr_s))
     roofline = {"bound": "alu", "achieved": achieved, "peak": ISSUE_PEAK, "unit": "warp-inst/s",
                 "frac": achieved / ISSUE_PEAK, "traffic": TRANSPORT_DRAM_BYTES,
-                "kernel": "transport_kernel<float> (persistent packet kernel, gray)",
+                "kernel": "transport_kernel<float> + transport_tail_kernel<float> (one transport call, gray)",
                 "thread_inst_frac": thread_achieved / THREAD_ISSUE_PEAK,
                 "note": f"issue-slot roofline: {WARP_INST_PER_STEP:g} warp instructions per transport step "
                         f"(ncu count on this workload) x {steps_per_launch:.3e} steps per launch / CUDA-event launch "
