@@ -14,17 +14,20 @@
  * "Parallel random numbers: as easy as 1, 2, 3" (SC'11), Sect. 4. Key =
  * (seed_lo, seed_hi); counter = (block, model, packet_lo, packet_hi). Each
  * 32-bit output word w gives one uniform u = (floor(w / 2^9) + 1/2) * 2^-23,
- * exactly representable in binary32 and binary64, in (0, 1). Words are used in
- * order w0..w3 of block 0, then block 1, and so on, one stream per packet.
+ * exactly representable in binary32 and binary64, in (0, 1). One stream per
+ * packet; every event takes the next whole block (blocks 0, 1, 2, ...), so the
+ * block an event uses depends only on how many events came before it.
  *
- * Order of draws per packet (the CUDA path consumes them identically):
- *   launch:      u_lambda (stellar bin), u_mu, u_phi (isotropic direction)
- *   free flight: u_tau (tau = -ln u)
- *   interaction: u_albedo; scatter -> u_mu, u_phi (isotropic or HG);
- *                absorb -> u_lambda (BW bin), u_mu, u_phi (isotropic)
- *   MRW jump:    u_P (escape-time quantile), u_mu, u_phi (point on sphere),
- *                u_mu, u_phi (new direction), u_lambda (exit bin)
- *   after each interaction (and its MRW chain) a new u_tau.
+ * Uniforms (w0, w1, w2, w3) of each event's block (the CUDA path uses them
+ * identically):
+ *   launch:      w0 stellar bin, (w1, w2) isotropic direction, w3 first tau
+ *   interaction: w0 albedo test a: scatter if a < omega, else absorb, and the BW
+ *                bin is drawn with (a - omega) / (1 - omega), the same uniform
+ *                conditioned on absorption; (w1, w2) new direction (isotropic, or
+ *                HG cosine and azimuth); w3 the next tau (-ln u), taken after the
+ *                interaction's MRW chain
+ *   MRW jump:    two blocks: w0 escape-time quantile P, (w1, w2) point on the
+ *                sphere, w3 exit bin; then (w0, w1) new direction, w2 and w3 unused
  */
 #include <math.h>
 #include <stdint.h>
@@ -90,6 +93,14 @@ static double U(or_rng *r) {
     r->pos = 0;
   }
   return word_to_uniform(r->buf[r->pos++]);
+}
+
+/* the four uniforms of the stream's next block */
+static void U4(or_rng *r, double w[4]) {
+  uint32_t b[4];
+  oracle_philox4x32_10(r->ctr, r->key, b);
+  r->ctr[0] += 1u;
+  for (int i = 0; i < 4; ++i) w[i] = word_to_uniform(b[i]);
 }
 
 /* First n uniforms of the stream of (seed, model, packet); used by tests. */
@@ -499,9 +510,10 @@ static int theta_cell(const oracle_model *m, const double p[3]) {
   return j;
 }
 
-static void iso_dir(or_rng *r, double u[3]) {
-  double mu = 2.0 * U(r) - 1.0;
-  double phi = 2.0 * OR_PI * U(r);
+/* isotropic direction from two uniforms: cos(theta) = 2 u1 - 1, phi = 2 pi u2 */
+static void iso_dir(double u1, double u2, double u[3]) {
+  double mu = 2.0 * u1 - 1.0;
+  double phi = 2.0 * OR_PI * u2;
   double st = sqrt(fmax(0.0, 1.0 - mu * mu));
   u[0] = st * cos(phi);
   u[1] = st * sin(phi);
@@ -620,12 +632,13 @@ static void run_packet(ctx_t *x, uint64_t k, uint64_t seed, uint32_t model, int 
   rng_init(&r, seed, model, k);
   int ntr = 0;
   uint64_t dep = 0, events = 0, crossings = 0;
-  double p[3] = {0, 0, 0}, u[3];
-  int lam = sample_bins(x->star_w, m->nlam, U(&r));
-  iso_dir(&r, u);
+  double p[3] = {0, 0, 0}, u[3], w[4];
+  U4(&r, w);
+  int lam = sample_bins(x->star_w, m->nlam, w[0]);
+  iso_dir(w[1], w[2], u);
   int ir = -1, it = -1, ninc = 0;
   trace(x, tp, &ntr, EV_LAUNCH, -1, p, lam);
-  double tau = -log(U(&r));
+  double tau = -log(w[3]);
   s->cnt[CNT_PACKETS]++;
   for (;;) {
     if (++crossings > 4000000000ull) { s->cnt[CNT_ERR] |= 4u; s->cnt[CNT_CAPPED]++; break; }
@@ -651,14 +664,15 @@ static void run_packet(ctx_t *x, uint64_t k, uint64_t seed, uint32_t model, int 
       for (int d = 0; d < 3; ++d) p[d] += s_int * u[d];
       /* interaction */
       double omega = m->ksca[lam] / chi;
-      if (U(&r) < omega) {
+      U4(&r, w);
+      if (w[0] < omega) {
         double g = m->g[lam];
         if (g != 0.0) {
-          double mu = hg_mu(g, U(&r));
-          double phi = 2.0 * OR_PI * U(&r);
+          double mu = hg_mu(g, w[1]);
+          double phi = 2.0 * OR_PI * w[2];
           turn(u, mu, phi);
         } else {
-          iso_dir(&r, u);
+          iso_dir(w[1], w[2], u);
         }
         s->cnt[CNT_SCA]++;
         trace(x, tp, &ntr, EV_SCATTER, c, p, lam);
@@ -670,9 +684,9 @@ static void run_packet(ctx_t *x, uint64_t k, uint64_t seed, uint32_t model, int 
         double Tnew = cell_T(m, c, s->tally[c], x->n_total);
         (void)before;
         s->Tcell[c] = Tnew;
-        double xl = U(&r);
+        double xl = (w[0] - omega) / (1.0 - omega);
         if (!x->gray || o->want_sed) lam = bw_bin(x, Told, Tnew, xl);
-        iso_dir(&r, u);
+        iso_dir(w[1], w[2], u);
         s->cnt[CNT_ABS]++;
         trace(x, tp, &ntr, EV_ABSORB, c, p, lam);
       }
@@ -688,7 +702,10 @@ static void run_packet(ctx_t *x, uint64_t k, uint64_t seed, uint32_t model, int 
           oracle_diffusion(m, T, m->rho[c], &D, &kbar);
           /* Eq. 11 with rho chi_R = 1/(3 D) */
           if (!(dmin > o->gamma * 3.0 * D)) break;
-          double x0 = oracle_mrw_x(U(&r));
+          double ja[4], jb[4];
+          U4(&r, ja);
+          U4(&r, jb);
+          double x0 = oracle_mrw_x(ja[0]);
           double ct = x0 * dmin * dmin / D;           /* path length c t */
           double E = ct * m->rho[c] * kbar;             /* Eq. 9, in packet energies */
           double units = floor(E * OR_EUNIT + 0.5);
@@ -696,17 +713,17 @@ static void run_packet(ctx_t *x, uint64_t k, uint64_t seed, uint32_t model, int 
           deposit(x, c, (uint64_t)units, &dep);
           s->Tcell[c] = cell_T(m, c, s->tally[c], x->n_total);
           double uh[3];
-          iso_dir(&r, uh);
+          iso_dir(ja[1], ja[2], uh);
           for (int d = 0; d < 3; ++d) p[d] += dmin * uh[d];
           if (o->mrw_exit_dir == 1) {
-            double mu = sqrt(U(&r));
-            double phi = 2.0 * OR_PI * U(&r);
+            double mu = sqrt(jb[0]);
+            double phi = 2.0 * OR_PI * jb[1];
             u[0] = uh[0]; u[1] = uh[1]; u[2] = uh[2];
             turn(u, mu, phi);
           } else {
-            iso_dir(&r, u);
+            iso_dir(jb[0], jb[1], u);
           }
-          double xl = U(&r);
+          double xl = ja[3];
           if (!x->gray || o->want_sed) lam = exit_bin(x, s->Tcell[c], xl);
           events++;
           s->cnt[CNT_MRW]++;
@@ -718,7 +735,7 @@ static void run_packet(ctx_t *x, uint64_t k, uint64_t seed, uint32_t model, int 
         trace(x, tp, &ntr, EV_CAPPED, c, p, lam);
         break;
       }
-      tau = -log(U(&r));
+      tau = -log(w[3]);
     } else {
       for (int d = 0; d < 3; ++d) p[d] += s_face * u[d];
       tau -= alpha * s_face;

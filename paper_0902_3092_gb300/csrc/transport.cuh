@@ -18,9 +18,11 @@
 //     spent inside comes from the inverse of Eq. 7 (table), and E_gamma c t rho kappa_bar (Eq. 9)
 //     is deposited;
 //   * leaving r_out adds the packet to the escape spectrum.
-// Random numbers: each packet owns Philox4x32-10 stream (seed; block, model, packet id); draws are
-// consumed in the same order as the FP64 CPU oracle, so gray trajectories of the FP64 build match
-// it event by event.
+// Random numbers: each packet owns a Philox4x32-10 stream (key = seed; counter = block, model, packet
+// id), and every event takes the next whole block: launch (stellar bin, direction, tau), interaction
+// (albedo test whose conditional value also draws the BW bin, direction, next tau), MRW jump (two
+// blocks: escape-time quantile, point on the sphere, exit bin; new direction). The FP64 CPU oracle
+// uses the same layout, so gray trajectories of the FP64 build match it event by event.
 #pragma once
 #include "common.cuh"
 
@@ -67,8 +69,7 @@ struct Pkt {
   R ialpha;  // 1 / alpha (0 where alpha = 0)
   int ir, it, lam, ninc;
   unsigned events, steps, xcross;  // interactions + jumps, all steps, crossings since the last interaction
-  uint32_t model, plo, phi, blk, w0, w1, w2, w3;
-  int left;
+  uint32_t model, plo, phi, blk;  // stream counter of the packet; blk: the next event's Philox block
   // gray dust: the wavelength only matters for the escape spectrum, so the bin of the last re-emission
   // is sampled at escape. 0: bin known; 1: BW bin of cell pend_cell; 2: MRW exit bin of pend_cell
   int pend_mode;
@@ -106,29 +107,20 @@ static __device__ __noinline__ uint4 philox_block(uint32_t blk, uint32_t model, 
   return make_uint4(c0, c1, c2, c3);
 }
 
-template <class R>
-__device__ __forceinline__ uint32_t next_word(Pkt<R>& s, uint32_t k0, uint32_t k1) {
-  if (s.left == 0) {
-    const uint4 w = philox_block(s.blk, s.model, s.plo, s.phi, k0, k1);
-    s.w0 = w.x; s.w1 = w.y; s.w2 = w.z; s.w3 = w.w;
-    ++s.blk;
-    s.left = 4;
-  }
-  const uint32_t w = s.w0;
-  s.w0 = s.w1; s.w1 = s.w2; s.w2 = s.w3;
-  --s.left;
-  return w;
-}
-
 // the key of every stream of a launch
 struct Key {
   uint32_t k0, k1;
 };
 
+// the four random words of the packet's next event (every event takes one whole block, so an event's
+// words depend only on how many events the packet had before it)
 template <class R>
-__device__ __forceinline__ R U(Pkt<R>& s, const Key& key) {
-  return to_uniform<R>(next_word(s, key.k0, key.k1));
+__device__ __forceinline__ uint4 next_block(Pkt<R>& s, const Key& key) {
+  return philox_block(s.blk++, s.model, s.plo, s.phi, key.k0, key.k1);
 }
+
+template <class R>
+__device__ __forceinline__ R uni(uint32_t w) { return to_uniform<R>(w); }
 
 template <class R>
 __device__ __forceinline__ R neg_log(R u);
@@ -158,11 +150,10 @@ __device__ __forceinline__ void polar_dir<double>(double mu, double u2, double& 
   z = mu;
 }
 
+// isotropic direction from two random words: cos theta = 2 u1 - 1, phi = 2 pi u2
 template <class R>
-__device__ __forceinline__ void iso_dir(Pkt<R>& s, const Key& key, R& x, R& y, R& z) {
-  const R mu = (R)2 * U(s, key) - (R)1;
-  const R u2 = U(s, key);
-  polar_dir<R>(mu, u2, x, y, z);
+__device__ __forceinline__ void iso_dir(uint32_t w1, uint32_t w2, R& x, R& y, R& z) {
+  polar_dir<R>((R)2 * uni<R>(w1) - (R)1, uni<R>(w2), x, y, z);
 }
 
 // rotate (x,y,z) by polar angle acos(mu) and azimuth 2 pi u2 about itself
@@ -359,9 +350,9 @@ __device__ __forceinline__ void launch_packet(const KParams<R>& P, const Key& ke
   s.plo = (uint32_t)k;
   s.phi = (uint32_t)(k >> 32);
   s.blk = 0;
-  s.left = 0;
-  s.lam = sample_star(M, U(s, key));
-  iso_dir(s, key, s.ux, s.uy, s.uz);
+  const uint4 w = next_block(s, key);  // stellar bin, direction, first optical depth
+  s.lam = sample_star(M, uni<R>(w.x));
+  iso_dir<R>(w.y, w.z, s.ux, s.uy, s.uz);
   s.px = s.py = s.pz = (R)0;
   s.ir = -1;
   s.it = -1;
@@ -377,7 +368,7 @@ __device__ __forceinline__ void launch_packet(const KParams<R>& P, const Key& ke
   s.ntr = 0;
   s.pend = 0;
   trace_ev<R, TRACE>(P, s, EV_LAUNCH, -1);
-  s.tau = neg_log<R>(U(s, key));
+  s.tau = neg_log<R>(uni<R>(w.w));
   acc.packets++;
 }
 
@@ -404,7 +395,9 @@ __device__ __forceinline__ void mrw_chain(const KParams<R>& P, const Key& key, c
       kb = (R)((1.f - w) * __ldg(M.kbar + k) + w * __ldg(M.kbar + k + 1));
     }
     if (!(dm * rho * chiR > P.gamma)) break;  // Eq. 11
-    const R x = mrw_x(P, U(s, key));
+    const uint4 ja = next_block(s, key);  // escape-time quantile, point on the sphere, exit bin
+    const uint4 jb = next_block(s, key);  // new direction
+    const R x = mrw_x(P, uni<R>(ja.x));
     const R tau0 = dm * rho;
     const R E = (R)3 * x * tau0 * tau0 * chiR * kb;  // Eq. 9 with c t = x R0^2 / D, D = 1/(3 rho chi_R)
     R units = floor(E * (R)kEUnit + (R)0.5);
@@ -419,19 +412,19 @@ __device__ __forceinline__ void mrw_chain(const KParams<R>& P, const Key& key, c
     else atomicAdd(M.tally + c, du);
     add_deposit(acc, du);
     R hx, hy, hz;
-    iso_dir(s, key, hx, hy, hz);
+    iso_dir<R>(ja.y, ja.z, hx, hy, hz);
     s.px += dm * hx;
     s.py += dm * hy;
     s.pz += dm * hz;
     if (P.exit_dir == 1) {
-      const R mu = sqrt(U(s, key));
-      const R u2 = U(s, key);
+      const R mu = sqrt(uni<R>(jb.x));
+      const R u2 = uni<R>(jb.y);
       s.ux = hx; s.uy = hy; s.uz = hz;
       turn<R>(s.ux, s.uy, s.uz, mu, u2);
     } else {
-      iso_dir(s, key, s.ux, s.uy, s.uz);
+      iso_dir<R>(jb.x, jb.y, s.ux, s.uy, s.uz);
     }
-    const R ul = U(s, key);
+    const R ul = uni<R>(ja.w);
     if (lam_now) {
       int k;
       float w;
@@ -553,11 +546,14 @@ template <class R, bool TRACE, bool G>
 __device__ __forceinline__ bool interact(const KParams<R>& P, const Key& key, const DevModel<R>& M, Pkt<R>& s,
                                          Acc& acc) {
   const int c = s.ir * M.nt + s.it;
+  const uint4 w = next_block(s, key);  // albedo test, new direction, next optical depth
   const R om = (G || M.gray) ? M.alb0 : M.alb[s.lam];
-  const bool sca = U(s, key) < om;
+  const R a = uni<R>(w.x);
+  const bool sca = a < om;
   const R g = sca ? ((G || M.gray) ? M.g0 : M.gq[s.lam]) : (R)0;
+  const R tau_next = neg_log<R>(uni<R>(w.w));
   if (!sca) {
-    const R ul = U(s, key);  // BW re-emission bin draw, before the new direction
+    const R ul = (a - om) / ((R)1 - om);  // the albedo uniform conditioned on absorption: the BW bin draw
     if (P.want_lam && (!(G || M.gray) || TRACE)) {
       // the old tally sets T_old / T_new of the BW re-emission
       const unsigned long long old = atomicAdd(M.tally + c, kEUnit);
@@ -585,11 +581,11 @@ __device__ __forceinline__ bool interact(const KParams<R>& P, const Key& key, co
   // new direction: Henyey-Greenstein turn for anisotropic scattering, isotropic otherwise (scattering
   // with g = 0 and re-emission share this code)
   if (g != (R)0) {
-    const R mu = hg_mu(g, U(s, key));
-    const R u2 = U(s, key);
+    const R mu = hg_mu(g, uni<R>(w.y));
+    const R u2 = uni<R>(w.z);
     turn<R>(s.ux, s.uy, s.uz, mu, u2);
   } else {
-    iso_dir(s, key, s.ux, s.uy, s.uz);
+    iso_dir<R>(w.y, w.z, s.ux, s.uy, s.uz);
   }
   trace_ev<R, TRACE>(P, s, sca ? EV_SCATTER : EV_ABSORB, c);
   s.events++;
@@ -600,7 +596,7 @@ __device__ __forceinline__ bool interact(const KParams<R>& P, const Key& key, co
     trace_ev<R, TRACE>(P, s, EV_CAPPED, c);
     return false;
   }
-  s.tau = neg_log<R>(U(s, key));
+  s.tau = tau_next;
   return true;
 }
 
