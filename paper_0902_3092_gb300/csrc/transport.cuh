@@ -112,12 +112,43 @@ struct Key {
   uint32_t k0, k1;
 };
 
-// the four random words of the packet's next event (every event takes one whole block, so an event's
-// words depend only on how many events the packet had before it)
-template <class R>
-__device__ __forceinline__ uint4 next_block(Pkt<R>& s, const Key& key) {
-  return philox_block(s.blk++, s.model, s.plo, s.phi, key.k0, key.k1);
-}
+// Sources of the packet's next event's four random words (every event takes one whole block, so an
+// event's words depend only on how many events the packet had before it).
+// SerialRng: each lane computes its packet's blocks itself.
+struct SerialRng {
+  Key key;
+  static constexpr bool coop = false;
+  template <class R>
+  __device__ __forceinline__ uint4 next(Pkt<R>& s) {
+    return philox_block(s.blk++, s.model, s.plo, s.phi, key.k0, key.k1);
+  }
+};
+
+// WarpRng: all 32 lanes of a warp carry the same packet (tail kernel); lane j holds block base + j,
+// computed by the 32 lanes at once whenever the packet has used the window, and an event's block is
+// read from its lane by shuffles. Needs a converged warp.
+struct WarpRng {
+  Key key;
+  uint32_t base;
+  uint4 mine;
+  static constexpr bool coop = true;
+  template <class R>
+  __device__ __forceinline__ uint4 next(Pkt<R>& s) {
+    if (s.blk - base >= 32u) {
+      base = s.blk;
+      mine = philox_block(base + (threadIdx.x & 31u), s.model, s.plo, s.phi, key.k0, key.k1);
+    }
+    const int j = (int)(s.blk - base);
+    ++s.blk;
+    return make_uint4(__shfl_sync(0xffffffffu, mine.x, j), __shfl_sync(0xffffffffu, mine.y, j),
+                      __shfl_sync(0xffffffffu, mine.z, j), __shfl_sync(0xffffffffu, mine.w, j));
+  }
+};
+
+// the lane that performs a packet's memory side effects (atomics): every lane, except in a warp that
+// carries one packet in all its lanes
+template <class RNG>
+__device__ __forceinline__ bool lead() { return !RNG::coop || (threadIdx.x & 31u) == 0u; }
 
 template <class R>
 __device__ __forceinline__ R uni(uint32_t w) { return to_uniform<R>(w); }
@@ -343,14 +374,14 @@ __device__ __forceinline__ void set_alpha(const DevModel<R>& M, Pkt<R>& s) {
   s.ialpha = s.alpha > (R)0 ? (R)1 / s.alpha : (R)0;
 }
 
-template <class R, bool TRACE>
-__device__ __forceinline__ void launch_packet(const KParams<R>& P, const Key& key, const DevModel<R>& M, Pkt<R>& s,
+template <class R, bool TRACE, class RNG>
+__device__ __forceinline__ void launch_packet(const KParams<R>& P, RNG& rng, const DevModel<R>& M, Pkt<R>& s,
                               unsigned long long k, int tslot, Acc& acc) {
   s.model = M.model_id;
   s.plo = (uint32_t)k;
   s.phi = (uint32_t)(k >> 32);
   s.blk = 0;
-  const uint4 w = next_block(s, key);  // stellar bin, direction, first optical depth
+  const uint4 w = rng.next(s);  // stellar bin, direction, first optical depth
   s.lam = sample_star(M, uni<R>(w.x));
   iso_dir<R>(w.y, w.z, s.ux, s.uy, s.uz);
   s.px = s.py = s.pz = (R)0;
@@ -376,8 +407,9 @@ __device__ __forceinline__ void launch_packet(const KParams<R>& P, const Key& ke
 template <class R>
 __device__ __forceinline__ R dsafe_margin() { return sizeof(R) == 4 ? (R)(1.0 - 1e-5) : (R)(1.0 - 1e-12); }
 
-template <class R, bool TRACE, bool G>
-__device__ __forceinline__ void mrw_chain(const KParams<R>& P, const Key& key, const DevModel<R>& M, Pkt<R>& s, int c, Acc& acc) {
+template <class R, bool TRACE, bool G, class RNG>
+__device__ __forceinline__ void mrw_chain(const KParams<R>& P, RNG& rng, const DevModel<R>& M, Pkt<R>& s, int c,
+                                          Acc& acc) {
   const R rho = M.rho[c];
   for (;;) {
     if (s.events >= P.max_events) break;
@@ -395,8 +427,8 @@ __device__ __forceinline__ void mrw_chain(const KParams<R>& P, const Key& key, c
       kb = (R)((1.f - w) * __ldg(M.kbar + k) + w * __ldg(M.kbar + k + 1));
     }
     if (!(dm * rho * chiR > P.gamma)) break;  // Eq. 11
-    const uint4 ja = next_block(s, key);  // escape-time quantile, point on the sphere, exit bin
-    const uint4 jb = next_block(s, key);  // new direction
+    const uint4 ja = rng.next(s);  // escape-time quantile, point on the sphere, exit bin
+    const uint4 jb = rng.next(s);  // new direction
     const R x = mrw_x(P, uni<R>(ja.x));
     const R tau0 = dm * rho;
     const R E = (R)3 * x * tau0 * tau0 * chiR * kb;  // Eq. 9 with c t = x R0^2 / D, D = 1/(3 rho chi_R)
@@ -408,8 +440,12 @@ __device__ __forceinline__ void mrw_chain(const KParams<R>& P, const Key& key, c
     const unsigned long long du = (unsigned long long)units;
     const bool lam_now = P.want_lam && (!(G || M.gray) || TRACE);  // the exit bin needs the tally now
     unsigned long long old = 0;
-    if (lam_now) old = atomicAdd(M.tally + c, du);
-    else atomicAdd(M.tally + c, du);
+    if (lam_now) {
+      if (lead<RNG>()) old = atomicAdd(M.tally + c, du);
+      if (RNG::coop) old = __shfl_sync(0xffffffffu, old, 0);
+    } else if (lead<RNG>()) {
+      atomicAdd(M.tally + c, du);
+    }
     add_deposit(acc, du);
     R hx, hy, hz;
     iso_dir<R>(ja.y, ja.z, hx, hy, hz);
@@ -446,9 +482,8 @@ __device__ __forceinline__ void mrw_chain(const KParams<R>& P, const Key& key, c
 
 // Moves a packet to its next event: enters the next cell (1), reaches an interaction point (2, the
 // interaction itself is left to interact()), or ends (0: escaped, or a step guard).
-template <class R, bool TRACE, bool G>
-__device__ __forceinline__ int advance(const KParams<R>& P, const Key& key, const DevModel<R>& M, Pkt<R>& s,
-                                       Acc& acc) {
+template <class R, bool TRACE, bool G, class RNG>
+__device__ __forceinline__ int advance(const KParams<R>& P, RNG& rng, const DevModel<R>& M, Pkt<R>& s, Acc& acc) {
   if (++s.steps > P.max_steps) {
     acc.err |= kErrStepGuard;
     acc.capped++;
@@ -467,7 +502,7 @@ __device__ __forceinline__ int advance(const KParams<R>& P, const Key& key, cons
     s.dsafe = (R)0;
     set_alpha<R, G>(M, s);
     const int c = s.it;
-    atomicAdd(M.visits + c, 1ull);
+    if (lead<RNG>()) atomicAdd(M.visits + c, 1ull);
     acc.cross++;
     trace_ev<R, TRACE>(P, s, EV_CROSS, c);
     return 1;
@@ -521,7 +556,7 @@ __device__ __forceinline__ int advance(const KParams<R>& P, const Key& key, cons
     if (P.want_lam) resolve_pending(M, s);
     int ib = (int)(fabs(s.uz) * (R)kNInc);
     ib = ib < kNInc ? ib : kNInc - 1;
-    atomicAdd(M.sed + s.lam * kNInc + ib, 1ull);
+    if (lead<RNG>()) atomicAdd(M.sed + s.lam * kNInc + ib, 1ull);
     acc.escaped++;
     trace_ev<R, TRACE>(P, s, EV_ESCAPE, -1);
     return 0;
@@ -535,18 +570,17 @@ __device__ __forceinline__ int advance(const KParams<R>& P, const Key& key, cons
   s.ninc = 0;
   set_alpha<R, G>(M, s);
   const int cn = s.ir * M.nt + s.it;
-  atomicAdd(M.visits + cn, 1ull);
+  if (lead<RNG>()) atomicAdd(M.visits + cn, 1ull);
   trace_ev<R, TRACE>(P, s, EV_CROSS, cn);
   return 1;
 }
 
 // The interaction at the packet's current point (Sect. 2.1): scattering or absorption with immediate
 // re-emission, then the MRW chain (Sect. 2.2.2) and the next optical depth. False: capped.
-template <class R, bool TRACE, bool G>
-__device__ __forceinline__ bool interact(const KParams<R>& P, const Key& key, const DevModel<R>& M, Pkt<R>& s,
-                                         Acc& acc) {
+template <class R, bool TRACE, bool G, class RNG>
+__device__ __forceinline__ bool interact(const KParams<R>& P, RNG& rng, const DevModel<R>& M, Pkt<R>& s, Acc& acc) {
   const int c = s.ir * M.nt + s.it;
-  const uint4 w = next_block(s, key);  // albedo test, new direction, next optical depth
+  const uint4 w = rng.next(s);  // albedo test, new direction, next optical depth
   const R om = (G || M.gray) ? M.alb0 : M.alb[s.lam];
   const R a = uni<R>(w.x);
   const bool sca = a < om;
@@ -556,7 +590,9 @@ __device__ __forceinline__ bool interact(const KParams<R>& P, const Key& key, co
     const R ul = (a - om) / ((R)1 - om);  // the albedo uniform conditioned on absorption: the BW bin draw
     if (P.want_lam && (!(G || M.gray) || TRACE)) {
       // the old tally sets T_old / T_new of the BW re-emission
-      const unsigned long long old = atomicAdd(M.tally + c, kEUnit);
+      unsigned long long old = 0;
+      if (lead<RNG>()) old = atomicAdd(M.tally + c, kEUnit);
+      if (RNG::coop) old = __shfl_sync(0xffffffffu, old, 0);
       int ko, kn;
       float wo, wn;
       qpos(M, old, c, ko, wo);
@@ -565,14 +601,14 @@ __device__ __forceinline__ bool interact(const KParams<R>& P, const Key& key, co
       s.pend_mode = 0;
       if (!(G || M.gray)) set_alpha<R, G>(M, s);
     } else {
-      atomicAdd(M.tally + c, kEUnit);  // nothing waits for the old value
+      if (lead<RNG>()) atomicAdd(M.tally + c, kEUnit);  // nothing waits for the old value
       if (P.want_lam) {
         s.pend_mode = 1;
         s.pend_cell = c;
         s.pend_u = (float)ul;
       }
     }
-    atomicAdd(M.nabs + c, 1ull);
+    if (lead<RNG>()) atomicAdd(M.nabs + c, 1ull);
     add_deposit(acc, kEUnit);
     acc.abs++;
   } else {
@@ -590,7 +626,7 @@ __device__ __forceinline__ bool interact(const KParams<R>& P, const Key& key, co
   trace_ev<R, TRACE>(P, s, sca ? EV_SCATTER : EV_ABSORB, c);
   s.events++;
   s.ninc++;
-  if (P.mrw && s.ninc >= P.nmin) mrw_chain<R, TRACE, G>(P, key, M, s, c, acc);
+  if (P.mrw && s.ninc >= P.nmin) mrw_chain<R, TRACE, G>(P, rng, M, s, c, acc);
   if (s.events >= P.max_events) {
     acc.capped++;
     trace_ev<R, TRACE>(P, s, EV_CAPPED, c);
@@ -601,14 +637,14 @@ __device__ __forceinline__ bool interact(const KParams<R>& P, const Key& key, co
 }
 
 // One event of a packet, an interaction run at once. False when the packet has ended.
-template <class R, bool TRACE, bool G>
-__device__ __forceinline__ bool step(const KParams<R>& P, const Key& key, const DevModel<R>& M, Pkt<R>& s, Acc& acc) {
+template <class R, bool TRACE, bool G, class RNG>
+__device__ __forceinline__ bool step(const KParams<R>& P, RNG& rng, const DevModel<R>& M, Pkt<R>& s, Acc& acc) {
   if (s.pend) {
     s.pend = 0;
-    return interact<R, TRACE, G>(P, key, M, s, acc);
+    return interact<R, TRACE, G>(P, rng, M, s, acc);
   }
-  const int r = advance<R, TRACE, G>(P, key, M, s, acc);
-  if (r == 2) return interact<R, TRACE, G>(P, key, M, s, acc);
+  const int r = advance<R, TRACE, G>(P, rng, M, s, acc);
+  if (r == 2) return interact<R, TRACE, G>(P, rng, M, s, acc);
   return r == 1;
 }
 
@@ -708,20 +744,31 @@ __device__ __forceinline__ int find_model(const KParams<R>& P, unsigned long lon
 // takes packets from the pool, those that had taken at least kTailLongSteps steps first.
 template <class R, bool TRACE, bool G>
 __global__ void __launch_bounds__(32) transport_tail_kernel(const KParams<R> P) {
-  if (threadIdx.x != 0) return;
-  const Key key{(uint32_t)P.seed, (uint32_t)(P.seed >> 32)};
+  const unsigned lane = threadIdx.x & 31u;
+  if (TRACE && lane != 0) return;  // the debug trace runs one lane per packet
   const DevModel<R>& M = P.m0;
   Acc acc = Acc{};
   const unsigned nlong = P.pool_ctr[0], nshort = P.pool_ctr[1];
   for (;;) {
-    const unsigned k = atomicAdd(P.pool_ctr + 2, 1u);
+    unsigned k = 0;
+    if (lane == 0) k = atomicAdd(P.pool_ctr + 2, 1u);
+    if (!TRACE) k = __shfl_sync(0xffffffffu, k, 0);
     if (k >= nlong + nshort) break;
     Pkt<R> s = P.pool[k < nlong ? k : P.pool_cap - 1u - (k - nlong)];
-    while (step<R, TRACE, G>(P, key, M, s, acc)) {
+    if (TRACE) {
+      SerialRng rng{{(uint32_t)P.seed, (uint32_t)(P.seed >> 32)}};
+      while (step<R, TRACE, G>(P, rng, M, s, acc)) {
+      }
+    } else {
+      // all 32 lanes carry the packet: the same arithmetic in every lane, the random blocks computed
+      // 32 at a time, side effects by lane 0
+      WarpRng rng{{(uint32_t)P.seed, (uint32_t)(P.seed >> 32)}, s.blk - 32u, make_uint4(0u, 0u, 0u, 0u)};
+      while (step<R, TRACE, G>(P, rng, M, s, acc)) {
+      }
     }
-    note_end(s, acc);
+    if (lane == 0) note_end(s, acc);
   }
-  flush(M, acc, false);
+  if (lane == 0) flush(M, acc, false);
 }
 
 // resident 256-thread blocks per SM the FP32 kernel is compiled for (register budget 65536 / (256 n))
@@ -736,7 +783,7 @@ template <class R, bool TRACE, bool BATCH, bool G>
 __global__ void __launch_bounds__(256, transport_min_blocks<R>()) transport_kernel(const KParams<R> P) {
   Pkt<R> s;
   Acc acc = Acc{};
-  const Key key{(uint32_t)P.seed, (uint32_t)(P.seed >> 32)};
+  SerialRng rng{{(uint32_t)P.seed, (uint32_t)(P.seed >> 32)}};
   bool active = false, done = false;
   int model = 0;
   const unsigned lane = threadIdx.x & 31;
@@ -764,7 +811,7 @@ __global__ void __launch_bounds__(256, transport_min_blocks<R>()) transport_kern
             const DevModel<R>& M = BATCH ? P.models[m] : P.m0;
             const unsigned long long local = q - M.q_begin;
             const int tslot = (TRACE && local < (unsigned long long)P.trace_n) ? (int)local : -1;
-            launch_packet<R, TRACE>(P, key, M, s, M.first_id + local, tslot, acc);
+            launch_packet<R, TRACE>(P, rng, M, s, M.first_id + local, tslot, acc);
             active = true;
           } else {
             done = true;
@@ -786,7 +833,7 @@ __global__ void __launch_bounds__(256, transport_min_blocks<R>()) transport_kern
         }
         const DevModel<R>& M = BATCH ? P.models[model] : P.m0;
         while (active) {
-          active = step<R, TRACE, G>(P, key, M, s, acc);
+          active = step<R, TRACE, G>(P, rng, M, s, acc);
           if (!active) note_end(s, acc);
         }
         break;
@@ -797,7 +844,7 @@ __global__ void __launch_bounds__(256, transport_min_blocks<R>()) transport_kern
     // keep crossing cells; a packet's own sequence of events and random draws is unchanged.
     const DevModel<R>& M = BATCH ? P.models[model] : P.m0;
     if (active && !s.pend) {
-      const int r = advance<R, TRACE, G>(P, key, M, s, acc);
+      const int r = advance<R, TRACE, G>(P, rng, M, s, acc);
       if (r == 0) {
         active = false;
         note_end(s, acc);
@@ -811,7 +858,7 @@ __global__ void __launch_bounds__(256, transport_min_blocks<R>()) transport_kern
       if (__popc(waiting) >= P.defer || !moving) {
         if (active && s.pend) {
           s.pend = 0;
-          if (!interact<R, TRACE, G>(P, key, M, s, acc)) {
+          if (!interact<R, TRACE, G>(P, rng, M, s, acc)) {
             active = false;
             note_end(s, acc);
           }
