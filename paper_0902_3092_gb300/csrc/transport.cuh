@@ -736,6 +736,120 @@ __device__ __forceinline__ int find_model(const KParams<R>& P, unsigned long lon
   return lo;
 }
 
+// Several interactions of one packet at once, in a warp whose 32 lanes all carry the packet (gray,
+// isotropic dust). Lane k evaluates the packet's k-th next interaction: its Philox block (the packet's
+// blocks are consumed one per interaction), the flight that leads to it (direction and optical depth
+// drawn at interaction k-1, lane 0: the packet's current ones) and, by a warp prefix sum of the flight
+// vectors, its position. The interactions are the packet's own, with its own random blocks, up to the
+// first flight that meets a cell face (the exact face distance decides, as in advance()) or the first
+// interaction after which Eq. 11 starts an MRW chain; their deposits are one atomic. Returns the number
+// of interactions done (0: the next flight crosses a face; the caller then takes a normal step), sets
+// `ended` when the MRW chain reached the event cap and `misses` when the next flight is known to meet a
+// face.
+template <class R, bool G>
+__device__ __forceinline__ int interactions_at_once(const KParams<R>& P, WarpRng& rng, const DevModel<R>& M, Pkt<R>& s,
+                                                    Acc& acc, bool& ended, bool& misses) {
+  const unsigned lane = threadIdx.x & 31u;
+  const unsigned full = 0xffffffffu;
+  const int c = s.ir * M.nt + s.it;
+  const R om = M.alb0;
+  // lane k: block of interaction k; what it draws for interaction k (albedo test) and for flight k+1
+  const uint32_t blk0 = s.blk;
+  const uint4 w = philox_block(blk0 + lane, s.model, s.plo, s.phi, rng.key.k0, rng.key.k1);
+  const R a = uni<R>(w.x);
+  R nx, ny, nz;
+  iso_dir<R>(w.y, w.z, nx, ny, nz);
+  const R tnext = neg_log<R>(uni<R>(w.w));
+  // flight k: direction and optical depth drawn at interaction k-1
+  R ux = __shfl_up_sync(full, nx, 1), uy = __shfl_up_sync(full, ny, 1), uz = __shfl_up_sync(full, nz, 1);
+  R tau = __shfl_up_sync(full, tnext, 1);
+  if (lane == 0) {
+    ux = s.ux;
+    uy = s.uy;
+    uz = s.uz;
+    tau = s.tau;
+  }
+  const R f = sizeof(R) == 8 ? tau / s.alpha : tau * s.ialpha;
+  // start of flight k (exclusive prefix sum of the flight vectors) and interaction point k (inclusive)
+  R qx = f * ux, qy = f * uy, qz = f * uz;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const R tx = __shfl_up_sync(full, qx, o), ty = __shfl_up_sync(full, qy, o), tz = __shfl_up_sync(full, qz, o);
+    if ((int)lane >= o) {
+      qx += tx;
+      qy += ty;
+      qz += tz;
+    }
+  }
+  const R px = s.px + (qx - f * ux), py = s.py + (qy - f * uy), pz = s.pz + (qz - f * uz);
+  qx += s.px;
+  qy += s.py;
+  qz += s.pz;
+  // d_min at the interaction point: the MRW test there and the safety distance of the next flight
+  const R dq = dmin_cell(M, s.ir, s.it, qx, qy, qz);
+  R dstart = __shfl_up_sync(full, dq * dsafe_margin<R>(), 1);
+  if (lane == 0) dstart = s.dsafe;
+  bool hit = f < dstart;
+  if (__ballot_sync(full, !hit)) {
+    int face;
+    const R sf = next_face(M, s.ir, s.it, px, py, pz, ux, uy, uz, face);
+    hit = hit || f < sf;
+  }
+  const unsigned miss = __ballot_sync(full, !hit);
+  const int h = miss ? __ffs(miss) - 1 : 32;  // flights 0 .. h-1 end inside the cell
+  if (h == 0) return 0;
+  const bool mrw = P.mrw && s.ninc + (int)lane + 1 >= P.nmin && dq * M.rho[c] * M.chiR0 > P.gamma;  // Eq. 11
+  const unsigned mrws = __ballot_sync(full, mrw) & (h == 32 ? full : ((1u << h) - 1u));
+  const int n = mrws ? __ffs(mrws) : h;  // interactions done; an MRW chain follows interaction n-1 if mrws
+  const unsigned done_mask = n == 32 ? full : ((1u << n) - 1u);
+  const unsigned absm = __ballot_sync(full, !(a < om)) & done_mask;
+  const int nabs = __popc(absm);
+  if (nabs) {
+    const unsigned long long dep = (unsigned long long)nabs * kEUnit;
+    if (lane == 0) {
+      atomicAdd(M.tally + c, dep);
+      atomicAdd(M.nabs + c, (unsigned long long)nabs);
+    }
+    add_deposit(acc, dep);
+    if (P.want_lam) {  // the bin of the last absorption's re-emission, drawn at escape
+      const R al = __shfl_sync(full, a, 31 - __clz(absm));
+      s.pend_mode = 1;
+      s.pend_cell = c;
+      s.pend_u = (float)((al - om) / ((R)1 - om));
+    }
+  }
+  acc.abs += nabs;
+  acc.sca += n - nabs;
+  // the packet after interaction n-1
+  const int l = n - 1;
+  s.px = __shfl_sync(full, qx, l);
+  s.py = __shfl_sync(full, qy, l);
+  s.pz = __shfl_sync(full, qz, l);
+  s.ux = __shfl_sync(full, nx, l);
+  s.uy = __shfl_sync(full, ny, l);
+  s.uz = __shfl_sync(full, nz, l);
+  const R tau_next = __shfl_sync(full, tnext, l);
+  s.dsafe = __shfl_sync(full, dq, l) * dsafe_margin<R>();
+  s.blk = blk0 + n;
+  s.events += n;
+  s.steps += n;
+  s.ninc += n;
+  s.xcross = 0;
+  rng.base = blk0;  // the lanes now hold blocks blk0 .. blk0 + 31: later events reuse them
+  rng.mine = w;
+  misses = !mrws && h < 32;
+  if (mrws) {
+    mrw_chain<R, false, G>(P, rng, M, s, c, acc);
+    if (s.events >= P.max_events) {
+      acc.capped++;
+      ended = true;
+      return n;
+    }
+  }
+  s.tau = tau_next;
+  return n;
+}
+
 // Tail of a single-disk launch. When the queue drains, the packets still in flight are mostly long
 // ones (a lane holds a long packet for long), and lanes of one warp that follow different branches
 // share its issue slots, so in the transport kernel a long packet would then advance at a fraction of
@@ -761,9 +875,19 @@ __global__ void __launch_bounds__(32) transport_tail_kernel(const KParams<R> P) 
       }
     } else {
       // all 32 lanes carry the packet: the same arithmetic in every lane, the random blocks computed
-      // 32 at a time, side effects by lane 0
+      // 32 at a time, side effects by lane 0; gray isotropic dust takes runs of interactions at once
       WarpRng rng{{(uint32_t)P.seed, (uint32_t)(P.seed >> 32)}, s.blk - 32u, make_uint4(0u, 0u, 0u, 0u)};
-      while (step<R, TRACE, G>(P, rng, M, s, acc)) {
+      bool ended = false, misses = false;
+      for (;;) {
+        // (FP32 only: the FP64 debug path keeps the oracle's order of floating-point operations)
+        if (G && sizeof(R) == 4 && !misses && !s.pend && s.ir >= 0 && s.alpha > (R)0 && M.g0 == (R)0 &&
+            s.events + 33u < P.max_events && s.steps + 33u < P.max_steps) {
+          const int n = interactions_at_once<R, G>(P, rng, M, s, acc, ended, misses);
+          if (ended) break;
+          if (n > 0) continue;
+        }
+        misses = false;
+        if (!step<R, TRACE, G>(P, rng, M, s, acc)) break;
       }
     }
     if (lane == 0) note_end(s, acc);

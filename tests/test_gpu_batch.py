@@ -33,7 +33,8 @@ def test_first_model_equals_single_disk_run(M):
     for g in (ga, gb, gc):
         t, _, _ = g.tallies()
     single = M.Disk.from_model(a)
-    single.run_photons(60_000, seed=5, mrw=True, gamma=2.0, max_events=10 ** 6)
+    # without the tail kernel: its batched interactions sum positions in another floating-point order
+    single.run_photons(60_000, seed=5, mrw=True, gamma=2.0, max_events=10 ** 6, tail_warps=-1)
     for x, y in zip(ga.tallies(), single.tallies()):
         assert np.array_equal(x, y)
     # sum of tallies equals the sum of per-packet deposits in every model

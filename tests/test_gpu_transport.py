@@ -135,15 +135,17 @@ def test_energy_identities_and_sed(M, oracle):
 
 
 def test_resume_is_bitwise(M):
+    """Gray FP32 runs without the tail kernel (whose batched interactions make a packet's floating-point
+    order depend on whether it was in flight when the queue drained) resume bit for bit."""
     d = disks.config_plain_gray(16, 16, 100.0)
     a = M.Disk.from_model(d)
-    a.run_photons(50_000, seed=3, n_total=50_000)
+    a.run_photons(50_000, seed=3, n_total=50_000, tail_warps=-1)
     b = M.Disk.from_model(d)
-    b.run_photons(20_000, seed=3, first_id=0, n_total=50_000)
+    b.run_photons(20_000, seed=3, first_id=0, n_total=50_000, tail_warps=-1)
     blob = b.checkpoint()
     c = M.Disk.from_model(d)
     c.restore(blob)
-    c.run_photons(30_000, seed=3, first_id=20_000, n_total=50_000)
+    c.run_photons(30_000, seed=3, first_id=20_000, n_total=50_000, tail_warps=-1)
     for x, y in zip(a.tallies(), c.tallies()):
         assert np.array_equal(x, y)
     # escape directions are order independent for gray dust; the BW wavelength is not (it depends on
