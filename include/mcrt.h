@@ -99,7 +99,7 @@ typedef struct {
   int refill_interval;          /* steps between refills of finished lanes; 0: tuned default */
   int want_sed;                 /* gray dust only: 0 skips the emission-bin sampling (no SED) */
   int tail_warps_per_sm;        /* single-disk runs: the packets still in flight when the packet queue
-                                   drains finish one per warp, this many warps per SM (0: 24; -1: no
+                                   drains finish one per warp, this many warps per SM (0: 20; -1: no
                                    tail kernel, they finish in the transport kernel) */
   int interact_batch;           /* a warp runs the interaction code once this many of its lanes wait at
                                    an interaction point (or none can move on); 1: no waiting; 0: 8 */

@@ -21,7 +21,7 @@ cudaError_t launch_transport<double>(const KParams<double>& P, bool trace, bool 
 template <>
 cudaError_t launch_transport_tail<double>(const KParams<double>& P, bool trace, bool gray, int sms, int warps_per_sm,
                                           cudaStream_t st) {
-  const int grid = sms * (warps_per_sm > 0 ? warps_per_sm : 24);
+  const int grid = sms * (warps_per_sm > 0 ? warps_per_sm : 20);
   if (trace) {
     if (gray) transport_tail_kernel<double, true, true><<<grid, 32, 0, st>>>(P);
     else transport_tail_kernel<double, true, false><<<grid, 32, 0, st>>>(P);

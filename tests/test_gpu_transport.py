@@ -151,3 +151,25 @@ def test_resume_is_bitwise(M):
     # escape directions are order independent for gray dust; the BW wavelength is not (it depends on
     # the tally seen at absorption time), so the spectrum is compared summed over wavelength
     assert np.allclose(a.sed().sum(0), c.sed().sum(0), rtol=1e-12, atol=0)
+
+
+def test_tail_kernel_statistically_equal(M):
+    """The tail kernel (batched interactions of the packets in flight at the drain) changes no physics:
+    two seeds without it and two with it give cell temperatures whose difference of means is as large
+    as the seed-to-seed scatter predicts, with no mean offset."""
+    d = disks.config_thick_gray(60, 40, 1e5)
+    g = M.Disk.from_model(d)
+    T, V = {}, {}
+    for tw, seed in ((-1, 11), (-1, 12), (0, 13), (0, 14)):
+        g.reset()
+        st = g.run_photons(1_000_000, seed=seed, mrw=True, gamma=2.0, max_events=10 ** 5, tail_warps=tw)
+        assert st["escaped"] + st["capped"] == 1_000_000 and st["error_flags"] == 0
+        T[seed], _, V[seed] = g.temperatures()
+    ok = np.minimum.reduce([V[s] for s in T]) > 3000
+    assert ok.sum() > 200
+    lg = {s: np.log(T[s][ok]) for s in T}
+    ab, cd = lg[11] - lg[12], lg[13] - lg[14]
+    diff = 0.5 * (lg[11] + lg[12] - lg[13] - lg[14])
+    expected = 0.5 * np.sqrt(np.mean(ab ** 2) + np.mean(cd ** 2))
+    assert np.sqrt(np.mean(diff ** 2)) < 1.5 * expected
+    assert abs(diff.mean()) < 5 * diff.std() / np.sqrt(ok.sum()) + 1e-4
