@@ -34,20 +34,21 @@ UNIT = "packets/s"
 WORKLOAD = "thick gray disk 200x120 rim-refined, tau_mid=1e6, albedo 0.5 isotropic, MRW gamma=2 + PDA"
 
 # Work per transport step (an interaction, an MRW jump or a face crossing) of one FP32 transport call on
-# this workload: ncu smsp__inst_executed.sum (warp instructions) and smsp__thread_inst_executed.sum
-# (thread instructions) of its two kernels (the persistent transport kernel and the tail kernel that
-# finishes the packets in flight when the queue drains) over a whole 1e8-packet call, divided by its
-# steps (profiles/). The kernels are bound by instruction issue (divergent, latency-bound integer/FP32
-# work, no DRAM traffic), so the roofline is issue slots: 152 SMs x 4 schedulers x 1 warp instruction
-# per clock at 2070 MHz.
-WARP_INST_PER_STEP = 59.0
-THREAD_INST_PER_STEP = 355.0
+# this workload: ncu smsp__inst_executed.sum (warp instructions) of its two kernels (the persistent
+# transport kernel, and the tail kernel that finishes the packets in flight when the queue drains) over
+# a whole 1e8-packet call, divided by its steps (profiles/); thread instructions count the transport
+# kernel's active lanes and one lane per tail warp instruction (all 32 lanes of a tail warp carry one
+# packet). The kernels are bound by instruction issue (divergent, latency-bound integer/FP32 work, no
+# DRAM traffic), so the roofline is issue slots: 152 SMs x 4 schedulers x 1 warp instruction per clock
+# at 2070 MHz.
+WARP_INST_PER_STEP = 35.2
+THREAD_INST_PER_STEP = 333.0
 ISSUE_PEAK = 152 * 4 * 2070e6           # warp instructions / s
 THREAD_ISSUE_PEAK = 32 * ISSUE_PEAK     # thread instructions / s (all lanes busy)
 # DRAM bytes of one transport call (ncu dram__bytes_read.sum + dram__bytes_write.sum of its two kernels,
 # 1e7 packets of this workload): tables and tallies stay in L2; the tail kernel reads the ~1.2e5 packet
-# states stored at the drain (14 MB). Neither grows with the packet count.
-TRANSPORT_DRAM_BYTES = 1632000 + 16640 + 15819520 + 256
+# states stored at the drain (13 MB). Neither grows with the packet count.
+TRANSPORT_DRAM_BYTES = 1546240 + 11776 + 13414144 + 256
 
 
 def parse():
