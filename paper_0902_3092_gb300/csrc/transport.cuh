@@ -518,7 +518,8 @@ __device__ __forceinline__ int advance(const KParams<R>& P, RNG& rng, const DevM
   if (s_int < s.dsafe) {
     hit = true;
   } else {
-    const R dm = dmin_cell(M, s.ir, s.it, s.px, s.py, s.pz) * dsafe_margin<R>();
+    // right after a face crossing the packet lies on a face, where d_min is 0: go to the face test
+    const R dm = s.xcross ? (R)0 : dmin_cell(M, s.ir, s.it, s.px, s.py, s.pz) * dsafe_margin<R>();
     if (s_int < dm) {
       hit = true;
       s.dsafe = dm;
