@@ -44,6 +44,7 @@ struct PdaState {
   DBuf y, r, p0, p1, Ap;              // FP32 CG vectors
   DBuf tiles;                         // int32 active tiles of the CG kernels
   std::vector<int> htiles;            // their host copy (source of the upload)
+  bool vec4 = false;                  // tiles of 128 cells for the 16-byte kernels (ntheta % 4 == 0)
   int ntiles = 0;
   DBuf sc;                            // FP64 CG scalars per iteration
   DBuf red;                           // FP64 reduction slots
@@ -402,6 +403,123 @@ __global__ void __launch_bounds__(256) k_cg_b(int n, int ntiles, const int* __re
   if (threadIdx.x == 0) atomicAdd(sc + 2 * (k + 1), (double)s);
 }
 
+// The same two kernels on 128-cell tiles, each lane taking four consecutive cells with 16-byte loads
+// and stores (used when ntheta % 4 == 0: a lane's four cells then lie in one polar row, and the rows
+// above and below start on 16-byte boundaries). The polar neighbours inside a lane are its own
+// cells; those across lanes come by shuffle, at the ends of the tile by single loads.
+__device__ __forceinline__ float4 ld4_or0(const float* __restrict__ a, int i, bool ok) {
+  return ok ? __ldg(reinterpret_cast<const float4*>(a + i)) : make_float4(0.f, 0.f, 0.f, 0.f);
+}
+
+__global__ void __launch_bounds__(256) k_cg_a4(int n, int nt, int ntiles, const int* __restrict__ tiles,
+                                               const float* __restrict__ ar, const float* __restrict__ at,
+                                               const float* __restrict__ r, const float* __restrict__ p_old,
+                                               float* __restrict__ p_new, float* __restrict__ Ap, double* sc, int k,
+                                               double tol2) {
+  __shared__ float sh[32];
+  const double rr0 = rr_of(sc, 0), rrk = rr_of(sc, k);
+  if (rrk <= tol2 * rr0 || !(rrk == rrk)) return;  // converged (or broken): no-op
+  const float beta = k == 0 ? 0.f : (float)(rrk / rr_of(sc, k - 1));
+  const int lane = threadIdx.x & 31, nw = gridDim.x * (blockDim.x >> 5);
+  const int w = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  const unsigned full = 0xffffffffu;
+  float v = 0.f;
+  for (int s0 = 0; w + (long long)s0 * nw < ntiles; s0 += 32) {
+    const long long tt = (long long)w + (long long)(s0 + lane) * nw;
+    const int base = tt < ntiles ? __ldg(tiles + tt) * 128 : -1;
+#pragma unroll 1
+    for (int u0 = 0; u0 < 32; ++u0) {
+      const int b = __shfl_sync(full, base, u0);
+      if (b < 0) break;  // warp-uniform
+      const int c = b + 4 * lane;
+      const bool in = c < n, dn = in && c >= nt, up = in && c + nt < n;
+      const float4 rc = ld4_or0(r, c, in), pc = ld4_or0(p_old, c, in);
+      const float4 arc = ld4_or0(ar, c, in), atc = ld4_or0(at, c, in);
+      const float4 ard = ld4_or0(ar, c - nt, dn);
+      const float4 rd = ld4_or0(r, c - nt, dn), pd = ld4_or0(p_old, c - nt, dn);
+      const float4 ru = ld4_or0(r, c + nt, up), pu = ld4_or0(p_old, c + nt, up);
+      float rl = __shfl_up_sync(full, rc.w, 1), pl = __shfl_up_sync(full, pc.w, 1);
+      float atl = __shfl_up_sync(full, atc.w, 1);
+      float rr = __shfl_down_sync(full, rc.x, 1), pr = __shfl_down_sync(full, pc.x, 1);
+      if (lane == 0) {
+        const bool ok = in && c > 0;
+        rl = ok ? __ldg(r + c - 1) : 0.f;
+        pl = ok ? __ldg(p_old + c - 1) : 0.f;
+        atl = ok ? __ldg(at + c - 1) : 0.f;
+      }
+      if (lane == 31) {
+        const bool ok = in && c + 4 < n;
+        rr = ok ? __ldg(r + c + 4) : 0.f;
+        pr = ok ? __ldg(p_old + c + 4) : 0.f;
+      }
+      if (!in) continue;
+      const float p0 = rc.x + beta * pc.x, p1 = rc.y + beta * pc.y, p2 = rc.z + beta * pc.z, p3 = rc.w + beta * pc.w;
+      float4 a;
+      a.x = p0 + ard.x * (rd.x + beta * pd.x) + arc.x * (ru.x + beta * pu.x) + atl * (rl + beta * pl) + atc.x * p1;
+      a.y = p1 + ard.y * (rd.y + beta * pd.y) + arc.y * (ru.y + beta * pu.y) + atc.x * p0 + atc.y * p2;
+      a.z = p2 + ard.z * (rd.z + beta * pd.z) + arc.z * (ru.z + beta * pu.z) + atc.y * p1 + atc.z * p3;
+      a.w = p3 + ard.w * (rd.w + beta * pd.w) + arc.w * (ru.w + beta * pu.w) + atc.z * p2 + atc.w * (rr + beta * pr);
+      *reinterpret_cast<float4*>(p_new + c) = make_float4(p0, p1, p2, p3);
+      *reinterpret_cast<float4*>(Ap + c) = a;
+      v += p0 * a.x + p1 * a.y + p2 * a.z + p3 * a.w;
+    }
+  }
+  const float s = block_sum_f(v, sh);
+  if (threadIdx.x == 0 && s != 0.f) atomicAdd(sc + 2 * k + 1, (double)s);
+}
+
+__global__ void __launch_bounds__(256) k_cg_b4(int n, int ntiles, const int* __restrict__ tiles,
+                                               const float* __restrict__ p_new, const float* __restrict__ Ap,
+                                               float* __restrict__ y, float* __restrict__ r, double* sc, int k,
+                                               double tol2) {
+  __shared__ float sh[32];
+  const double rr0 = rr_of(sc, 0), rrk = rr_of(sc, k);
+  if (rrk <= tol2 * rr0 || !(rrk == rrk)) return;
+  const float alpha = (float)(rrk / sc[2 * k + 1]);
+  const int lane = threadIdx.x & 31, nw = gridDim.x * (blockDim.x >> 5);
+  const int w = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  const unsigned full = 0xffffffffu;
+  float v = 0.f;
+  for (int s0 = 0; w + (long long)s0 * nw < ntiles; s0 += 32) {
+    const long long tt = (long long)w + (long long)(s0 + lane) * nw;
+    const int base = tt < ntiles ? __ldg(tiles + tt) * 128 : -1;
+#pragma unroll 1
+    for (int u0 = 0; u0 < 32; u0 += 2) {
+      const int b0 = __shfl_sync(full, base, u0), b1 = __shfl_sync(full, base, u0 + 1);
+      if (b0 < 0) break;
+      const int c0 = b0 + 4 * lane, c1 = b1 >= 0 ? b1 + 4 * lane : n;
+      const bool in0 = c0 < n, in1 = c1 < n;
+      const float4 p0 = ld4_or0(p_new, c0, in0), a0 = ld4_or0(Ap, c0, in0);
+      const float4 p1 = ld4_or0(p_new, c1, in1), a1 = ld4_or0(Ap, c1, in1);
+      float4 y0 = make_float4(0.f, 0.f, 0.f, 0.f), r0 = y0, y1 = y0, r1 = y0;
+      if (in0) {
+        y0 = *reinterpret_cast<const float4*>(y + c0);
+        r0 = *reinterpret_cast<const float4*>(r + c0);
+      }
+      if (in1) {
+        y1 = *reinterpret_cast<const float4*>(y + c1);
+        r1 = *reinterpret_cast<const float4*>(r + c1);
+      }
+      if (in0) {
+        const float4 rn = make_float4(r0.x - alpha * a0.x, r0.y - alpha * a0.y, r0.z - alpha * a0.z, r0.w - alpha * a0.w);
+        *reinterpret_cast<float4*>(y + c0) =
+            make_float4(y0.x + alpha * p0.x, y0.y + alpha * p0.y, y0.z + alpha * p0.z, y0.w + alpha * p0.w);
+        *reinterpret_cast<float4*>(r + c0) = rn;
+        v += rn.x * rn.x + rn.y * rn.y + rn.z * rn.z + rn.w * rn.w;
+      }
+      if (in1) {
+        const float4 rn = make_float4(r1.x - alpha * a1.x, r1.y - alpha * a1.y, r1.z - alpha * a1.z, r1.w - alpha * a1.w);
+        *reinterpret_cast<float4*>(y + c1) =
+            make_float4(y1.x + alpha * p1.x, y1.y + alpha * p1.y, y1.z + alpha * p1.z, y1.w + alpha * p1.w);
+        *reinterpret_cast<float4*>(r + c1) = rn;
+        v += rn.x * rn.x + rn.y * rn.y + rn.z * rn.z + rn.w * rn.w;
+      }
+    }
+  }
+  const float s = block_sum_f(v, sh);
+  if (threadIdx.x == 0) atomicAdd(sc + 2 * (k + 1), (double)s);
+}
+
 __global__ void k_update(int n, const signed char* mask, const double* dis, const float* y, double scale, double* x) {
   const int c = blockIdx.x * blockDim.x + threadIdx.x;
   if (c < n && mask[c] == 2) x[c] += scale * dis[c] * (double)y[c];
@@ -489,15 +607,15 @@ static int tgrid(K kern, int ntiles) {
   return std::max(1, std::min((ntiles + 7) / 8, sm_count() * occ));
 }
 
-// active tiles of a mask (32 consecutive cells with at least one PDA cell), in increasing order
-static std::vector<int> active_tiles(const std::vector<signed char>& mask) {
+// active tiles of a mask (`width` consecutive cells with at least one PDA cell), in increasing order
+static std::vector<int> active_tiles(const std::vector<signed char>& mask, int width) {
   const int n = (int)mask.size();
   std::vector<int> t;
-  for (int b = 0; b < n; b += 32) {
-    const int e = std::min(n, b + 32);
+  for (int b = 0; b < n; b += width) {
+    const int e = std::min(n, b + width);
     for (int c = b; c < e; ++c)
       if (mask[c] == 2) {
-        t.push_back(b / 32);
+        t.push_back(b / width);
         break;
       }
   }
@@ -605,7 +723,8 @@ static mcrt_status refine_solve(mcrt_disk* d, const mcrt_pda_opts* o, double* x,
   float* pb[2] = {P->p0.as<float>(), P->p1.as<float>()};
   const double tol2_in = o->inner_tol * o->inner_tol;
   const int* tiles = P->tiles.as<int>();
-  const int ga = tgrid(k_cg_a<kUA>, P->ntiles), gb = tgrid(k_cg_b<kUB>, P->ntiles);
+  const int ga = P->vec4 ? tgrid(k_cg_a4, P->ntiles) : tgrid(k_cg_a<kUA>, P->ntiles);
+  const int gb = P->vec4 ? tgrid(k_cg_b4, P->ntiles) : tgrid(k_cg_b<kUB>, P->ntiles);
   double norm_b = -1.0, best = INFINITY;
   int total_iters = 0, stall = 0;
   const int chunk = 32;
@@ -643,9 +762,15 @@ static mcrt_status refine_solve(mcrt_disk* d, const mcrt_pda_opts* o, double* x,
       for (; k < kend; ++k) {
         float* pnew = pb[k & 1];
         float* pold = pb[(k + 1) & 1];
-        k_cg_a<kUA><<<ga, 256, 0, st>>>(n, nt, P->ntiles, tiles, P->ar.as<float>(), P->at.as<float>(), r, pold, pnew, Ap,
-                                   sc, k, tol2_in);
-        k_cg_b<kUB><<<gb, 256, 0, st>>>(n, P->ntiles, tiles, pnew, Ap, y, r, sc, k, tol2_in);
+        if (P->vec4) {
+          k_cg_a4<<<ga, 256, 0, st>>>(n, nt, P->ntiles, tiles, P->ar.as<float>(), P->at.as<float>(), r, pold, pnew, Ap,
+                                      sc, k, tol2_in);
+          k_cg_b4<<<gb, 256, 0, st>>>(n, P->ntiles, tiles, pnew, Ap, y, r, sc, k, tol2_in);
+        } else {
+          k_cg_a<kUA><<<ga, 256, 0, st>>>(n, nt, P->ntiles, tiles, P->ar.as<float>(), P->at.as<float>(), r, pold, pnew,
+                                          Ap, sc, k, tol2_in);
+          k_cg_b<kUB><<<gb, 256, 0, st>>>(n, P->ntiles, tiles, pnew, Ap, y, r, sc, k, tol2_in);
+        }
         d->launches += 2;
       }
       std::vector<double> h(2 * (size_t)k + 2);
@@ -757,7 +882,8 @@ mcrt_status mcrt_solve_pda(mcrt_disk* d, const mcrt_pda_opts* o, int* out_n, int
   if (out_n) *out_n = P->n_pda;
   if (hred[3] > 0 || !components_ok(d, hmask))
     return set_error(d, MCRT_EINVAL, "a PDA region touches no Monte Carlo cell (singular system)");
-  P->htiles = active_tiles(hmask);
+  P->vec4 = nt % 4 == 0;  // 16-byte kernels on 128-cell tiles
+  P->htiles = active_tiles(hmask, P->vec4 ? 128 : 32);
   P->ntiles = (int)P->htiles.size();
   if (P->ntiles > 0)
     CK(cudaMemcpyAsync(P->tiles.p, P->htiles.data(), P->htiles.size() * sizeof(int), cudaMemcpyHostToDevice, st),
