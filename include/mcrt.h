@@ -203,6 +203,32 @@ mcrt_status mcrt_pda_adjoint(mcrt_disk *d, const double *w, double *grad_log_rho
 mcrt_status mcrt_pda_adjoint_dev(mcrt_disk *d, const double *w_dev, double *grad_log_rho_dev,
                                  double *grad_kappa_R_dev);
 
+/* Vertical hydrostatic structure (Sect. 3, Eq. 20): dP/dz = -rho G M_star z / R^3 with P = k_B rho T /
+ * (mu m_u), at fixed surface density, from the disk's last temperatures. Each radial shell is one
+ * column (z = r_c cos theta_c, R = r_c sin theta_c at the cell centres; trapezoid rule in z from
+ * theta = 0 to pi) and keeps its dust mass; cells without dust stay without dust. One GPU thread per
+ * shell, FP64. The paper iterates transport -> temperatures -> this density until the mean change of
+ * the temperatures between two iterations is below 3 sigma of their Monte Carlo errors. */
+typedef struct {
+  double M_star_g;              /* stellar mass (g); default 2.5 solar masses (the paper's Table 1) */
+  double mu;                    /* mean molecular weight (2.3) */
+  double T_floor_K;             /* temperatures below this (cells no packet heated) are raised to it (10 K) */
+  int which;                    /* MCRT_T_PDA (the last PDA solve, default) or MCRT_T_MC */
+  const double *shell_mass_g;   /* optional host array nr: the dust mass each radial shell keeps;
+                                   NULL: the disk's current shell masses */
+} mcrt_hydro_opts;
+
+void mcrt_default_hydro_opts(mcrt_hydro_opts *o);
+
+/* New density (g/cm^3, host array nr*ntheta, row-major [ir][itheta]) in hydrostatic equilibrium with
+ * the disk's temperatures. The disk is not changed (see mcrt_set_density). MCRT_ESTATE without
+ * temperatures (or without a PDA solution for MCRT_T_PDA); MCRT_EINVAL for bad options. */
+mcrt_status mcrt_hydrostatic_density(mcrt_disk *d, const mcrt_hydro_opts *opts, double *rho_out);
+
+/* Replaces the disk's density (host array nr*ntheta, g/cm^3, finite and >= 0) and resets its tallies;
+ * the grid, star and opacities stay. Device buffers keep their addresses. */
+mcrt_status mcrt_set_density(mcrt_disk *d, const double *rho);
+
 /* FP64 debug transport that records every event of the first n_packets packets: type (0 launch,
  * 1 cell entry, 2 scatter, 3 absorption, 4 MRW jump, 5 escape, 6 capped), cell (-1 outside the grid),
  * wavelength bin and position (cm, [packet][event][3]). Buffers hold n_packets * max_events entries;

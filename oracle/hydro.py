@@ -36,7 +36,8 @@ def cell_volumes(r_faces, theta_faces):
     """Volumes of the (r, theta) cells of an axisymmetric grid (cm^3)."""
     rf = np.asarray(r_faces, np.float64)
     tf = np.asarray(theta_faces, np.float64)
-    return (2.0 * np.pi / 3.0) * (rf[1:] ** 3 - rf[:-1] ** 3)[:, None] * (np.cos(tf[:-1]) - np.cos(tf[1:]))[None, :]
+    r1, r2 = rf[:-1], rf[1:]
+    return (2.0 * np.pi / 3.0) * (r2 * r2 * r2 - r1 * r1 * r1)[:, None] * (np.cos(tf[:-1]) - np.cos(tf[1:]))[None, :]
 
 
 def shell_masses(r_faces, theta_faces, rho):
@@ -60,7 +61,7 @@ def hydrostatic_density(r_faces, theta_faces, rho_mask, T, shell_mass, M_star=2.
         for j in range(nt):
             th = 0.5 * (tf[j] + tf[j + 1])
             z, R = rc * np.cos(th), rc * np.sin(th)
-            a = GM * z / R ** 3 * (mu * M_U / (K_B * Tc[j]))  # G M z / (R^3 c^2)
+            a = GM * z / (R * R * R) * (mu * M_U / (K_B * Tc[j]))  # G M z / (R^3 c^2)
             if j > 0:
                 phi[j] = phi[j - 1] - 0.5 * (a + a_prev) * (z - z_prev)
             a_prev, z_prev = a, z

@@ -269,9 +269,12 @@ DevModel<double> mcrt_disk::model64() const { return make_model<double>(this, tr
 // ------------------------------------------------------------------------------------------------
 template <class T>
 static cudaError_t upload(DBuf& b, const std::vector<T>& v) {
-  cudaError_t e = b.alloc(sizeof(T) * v.size());
-  if (e != cudaSuccess) return e;
-  return cudaMemcpy(b.p, v.data(), sizeof(T) * v.size(), cudaMemcpyHostToDevice);
+  const size_t bytes = sizeof(T) * v.size();
+  if (!b.p || b.n != (bytes ? bytes : 16)) {  // an allocation of the right size is kept (its address too)
+    cudaError_t e = b.alloc(bytes);
+    if (e != cudaSuccess) return e;
+  }
+  return cudaMemcpy(b.p, v.data(), bytes, cudaMemcpyHostToDevice);
 }
 
 template <class A, class B>
@@ -308,7 +311,51 @@ bool account_deposits(mcrt_disk* d, const unsigned long long* c) {
 }
 }  // namespace mcrt
 
+namespace mcrt {
+// density-dependent device arrays from d->rho: rho * l_unit (FP32, FP64), cell masses, log(1/m), rho (cgs)
+mcrt_status upload_density(mcrt_disk* d) {
+  const int nr = d->nr, nt = d->nt;
+  const size_t ncell = (size_t)nr * nt;
+  std::vector<double> rhol(ncell);
+  d->mass.resize(ncell);
+  std::vector<float> lqm(ncell);
+  for (int i = 0; i < nr; ++i)
+    for (int j = 0; j < nt; ++j) {
+      const size_t c = (size_t)i * nt + j;
+      rhol[c] = d->rho[c] * d->l_unit;
+      const double r1 = d->rf[i], r2 = d->rf[i + 1];
+      const double V = 2.0 * kPi / 3.0 * (r2 * r2 * r2 - r1 * r1 * r1) * (std::cos(d->tf[j]) - std::cos(d->tf[j + 1]));
+      d->mass[c] = d->rho[c] * V;
+      lqm[c] = d->mass[c] > 0 ? (float)(-std::log(d->mass[c])) : 0.f;
+    }
+  cudaError_t e = upload(d->rho32, cast_vec<float>(rhol));
+  if (e == cudaSuccess) e = upload(d->rho64, rhol);
+  if (e == cudaSuccess) e = upload(d->lqm, lqm);
+  if (e == cudaSuccess) e = upload(d->mass_d, d->mass);
+  if (e == cudaSuccess) e = upload(d->rho_cgs_d, d->rho);
+  if (e != cudaSuccess) return cuda_fail(d, e, "upload");
+  return MCRT_OK;
+}
+}  // namespace mcrt
+
 extern "C" {
+
+mcrt_status mcrt_set_density(mcrt_disk* d, const double* rho) {
+  if (!d) return set_error(nullptr, MCRT_EINVAL, "disk is NULL");
+  if (!rho) return set_error(d, MCRT_EINVAL, "rho is NULL");
+  const size_t n = (size_t)d->nr * d->nt;
+  for (size_t c = 0; c < n; ++c)
+    if (!(std::isfinite(rho[c]) && rho[c] >= 0)) return set_error(d, MCRT_EINVAL, "rho must be finite and >= 0");
+  CK(cudaSetDevice(d->device), "cudaSetDevice");
+  CK(cudaStreamSynchronize(d->stream), "synchronize");
+  d->rho.assign(rho, rho + n);
+  mcrt_status s = upload_density(d);
+  if (s != MCRT_OK) return s;
+  s = zero_tallies(d);
+  if (s != MCRT_OK) return s;
+  CK(cudaStreamSynchronize(d->stream), "synchronize");
+  return MCRT_OK;
+}
 
 void mcrt_default_run_opts(mcrt_run_opts* o) {
   if (!o) return;
@@ -404,18 +451,6 @@ mcrt_status mcrt_disk_create(const mcrt_grid* grid, const mcrt_star* star, int d
     else fk[j] = t < 0.5 * kPi ? 1 : -1;
   }
   const size_t ncell = (size_t)nr * nt;
-  std::vector<double> rhol(ncell);
-  d->mass.resize(ncell);
-  std::vector<float> lqm(ncell);
-  for (int i = 0; i < nr; ++i)
-    for (int j = 0; j < nt; ++j) {
-      const size_t c = (size_t)i * nt + j;
-      rhol[c] = d->rho[c] * d->l_unit;
-      const double r1 = d->rf[i], r2 = d->rf[i + 1];
-      const double V = 2.0 * kPi / 3.0 * (r2 * r2 * r2 - r1 * r1 * r1) * (std::cos(d->tf[j]) - std::cos(d->tf[j + 1]));
-      d->mass[c] = d->rho[c] * V;
-      lqm[c] = d->mass[c] > 0 ? (float)(-std::log(d->mass[c])) : 0.f;
-    }
   mcrt_status st = MCRT_OK;
 #define UP(buf, vec)                                          \
   do {                                                        \
@@ -428,19 +463,16 @@ mcrt_status mcrt_disk_create(const mcrt_grid* grid, const mcrt_star* star, int d
   UP(d->s2_32, cast_vec<float>(s2));
   UP(d->cf32, cast_vec<float>(cf));
   UP(d->sf32, cast_vec<float>(sf));
-  UP(d->rho32, cast_vec<float>(rhol));
   UP(d->rf64, rf);
   UP(d->rf2_64, rf2);
   UP(d->c2_64, c2);
   UP(d->s2_64, s2);
   UP(d->cf64, cf);
   UP(d->sf64, sf);
-  UP(d->rho64, rhol);
   UP(d->fk, fk);
-  UP(d->lqm, lqm);
-  UP(d->mass_d, d->mass);
-  UP(d->rho_cgs_d, d->rho);
 #undef UP
+  st = upload_density(d);
+  if (st != MCRT_OK) return fail(st);
   e = d->tally.alloc(ncell * 8);
   if (e == cudaSuccess) e = d->visits.alloc(ncell * 8);
   if (e == cudaSuccess) e = d->nabs.alloc(ncell * 8);

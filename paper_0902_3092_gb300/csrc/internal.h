@@ -98,6 +98,7 @@ mcrt_status cuda_fail(mcrt_disk* d, cudaError_t e, const char* what);
 const float* mrw_table(int device, cudaError_t* err);
 extern const float kMrwT0, kMrwDT;
 mcrt_status compute_temperatures(mcrt_disk* d);
+mcrt_status upload_density(mcrt_disk* d);
 // adds a run's deposit sum (counters c) to the disk's held energy; false if a tally may have wrapped
 bool account_deposits(mcrt_disk* d, const unsigned long long* c);
 void pda_free(PdaState* p);

@@ -23,7 +23,8 @@ EXPORTS = ["mcrt_disk_create", "mcrt_set_opacity", "mcrt_default_run_opts", "mcr
            "mcrt_default_pda_opts", "mcrt_solve_pda", "mcrt_pda_adjoint", "mcrt_pda_adjoint_dev",
            "mcrt_trace_packets", "mcrt_checkpoint", "mcrt_restore", "mcrt_debug_uniforms", "mcrt_debug_mrw_x",
            "mcrt_pda_solve_static", "mcrt_disk_info", "mcrt_launch_count", "mcrt_last_error",
-           "mcrt_disk_destroy", "mcrt_batch_create", "mcrt_batch_run", "mcrt_batch_config", "mcrt_batch_destroy"]
+           "mcrt_disk_destroy", "mcrt_batch_create", "mcrt_batch_run", "mcrt_batch_config", "mcrt_batch_destroy",
+           "mcrt_default_hydro_opts", "mcrt_hydrostatic_density", "mcrt_set_density"]
 
 
 class McrtError(RuntimeError):
@@ -63,6 +64,11 @@ class PdaOpts(C.Structure):
     _fields_ = [("min_visits", C.c_int), ("max_rel_err", C.c_double), ("tol", C.c_double), ("inner_tol", C.c_double),
                 ("max_outer", C.c_int), ("max_inner", C.c_int), ("min_cell_tau", C.c_double),
                 ("kappa_R", C.POINTER(C.c_double)), ("rho", C.POINTER(C.c_double))]
+
+
+class HydroOpts(C.Structure):
+    _fields_ = [("M_star_g", C.c_double), ("mu", C.c_double), ("T_floor_K", C.c_double), ("which", C.c_int),
+                ("shell_mass_g", C.POINTER(C.c_double))]
 
 
 _lib = None
@@ -110,6 +116,9 @@ def lib():
                                    C.POINTER(C.c_double)]),
         "mcrt_batch_destroy": (None, [P]),
         "mcrt_disk_destroy": (None, [P]),
+        "mcrt_default_hydro_opts": (None, [C.POINTER(HydroOpts)]),
+        "mcrt_hydrostatic_density": (st, [P, C.POINTER(HydroOpts), pd]),
+        "mcrt_set_density": (st, [P, pd]),
     }
     for name, (res, args) in sig.items():
         f = getattr(L, name)
@@ -221,6 +230,30 @@ class Disk:
 
     def reset(self):
         _check(lib().mcrt_reset(self._h), self._h)
+
+    def hydrostatic_density(self, M_star_g=None, mu=None, T_floor=None, which=T_PDA, shell_mass=None):
+        """Density in hydrostatic equilibrium with the disk's temperatures (Sect. 3, Eq. 20), nr x ntheta."""
+        o = HydroOpts()
+        lib().mcrt_default_hydro_opts(C.byref(o))
+        if M_star_g is not None:
+            o.M_star_g = M_star_g
+        if mu is not None:
+            o.mu = mu
+        if T_floor is not None:
+            o.T_floor_K = T_floor
+        o.which = which
+        sm = None
+        if shell_mass is not None:
+            sm = np.ascontiguousarray(shell_mass, np.float64)
+            o.shell_mass_g = _dp(sm)
+        out = np.zeros(self.nr * self.ntheta)
+        _check(lib().mcrt_hydrostatic_density(self._h, C.byref(o), _dp(out)), self._h)
+        return out.reshape(self.nr, self.ntheta)
+
+    def set_density(self, rho):
+        """Replaces the density (g/cm^3) and resets the tallies."""
+        r = np.ascontiguousarray(rho, np.float64).ravel()
+        _check(lib().mcrt_set_density(self._h, _dp(r)), self._h)
 
     def temperatures(self, which=T_MC):
         n = self.nr * self.ntheta

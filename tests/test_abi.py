@@ -39,14 +39,16 @@ def test_struct_layouts_match_c(L, tmp_path):
 
     from paper_0902_3092_gb300 import mcrt
     prog = tmp_path / "sz.c"
-    prog.write_text('#include "mcrt.h"\n#include <stdio.h>\n#include <stddef.h>\nint main(void){printf("%zu %zu %zu %zu %zu %zu %zu\\n",'
+    prog.write_text('#include "mcrt.h"\n#include <stdio.h>\n#include <stddef.h>\nint main(void){printf("%zu %zu %zu %zu %zu %zu %zu %zu %zu\\n",'
                     'sizeof(mcrt_grid),sizeof(mcrt_star),sizeof(mcrt_run_opts),sizeof(mcrt_run_stats),sizeof(mcrt_pda_opts),'
-                    'offsetof(mcrt_run_stats,seconds),offsetof(mcrt_pda_opts,kappa_R));return 0;}\n')
+                    'offsetof(mcrt_run_stats,seconds),offsetof(mcrt_pda_opts,kappa_R),sizeof(mcrt_hydro_opts),'
+                    'offsetof(mcrt_hydro_opts,shell_mass_g));return 0;}\n')
     exe = tmp_path / "sz"
     subprocess.check_call(["gcc", "-I", os.path.dirname(HEADER), str(prog), "-o", str(exe)])
     got = [int(x) for x in subprocess.check_output([str(exe)]).split()]
     want = [C.sizeof(mcrt.Grid), C.sizeof(mcrt.Star), C.sizeof(mcrt.RunOpts), C.sizeof(mcrt.RunStats),
-            C.sizeof(mcrt.PdaOpts), mcrt.RunStats.seconds.offset, mcrt.PdaOpts.kappa_R.offset]
+            C.sizeof(mcrt.PdaOpts), mcrt.RunStats.seconds.offset, mcrt.PdaOpts.kappa_R.offset,
+            C.sizeof(mcrt.HydroOpts), mcrt.HydroOpts.shell_mass_g.offset]
     assert got == want
 
 
@@ -60,6 +62,9 @@ def test_defaults_and_host_validation(L):
     p = mcrt.PdaOpts()
     L.mcrt_default_pda_opts(C.byref(p))
     assert p.min_visits == 30 and p.max_rel_err == 0.05
+    h = mcrt.HydroOpts()
+    L.mcrt_default_hydro_opts(C.byref(h))
+    assert h.mu == 2.3 and abs(h.M_star_g / 1.98892e33 - 2.5) < 1e-12 and h.which == mcrt.T_PDA
     # invalid input is rejected on the host before any device work
     h = C.c_void_p()
     assert L.mcrt_disk_create(None, None, 0, None, C.byref(h)) == 1

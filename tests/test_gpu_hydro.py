@@ -1,0 +1,49 @@
+"""Vertical hydrostatic structure on the GPU (Sect. 3, Eq. 20) against the FP64 oracle, and the
+iteration's 3-sigma convergence."""
+import numpy as np
+import pytest
+
+from paper_0902_3092_gb300 import disks
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def M():
+    from paper_0902_3092_gb300 import build, mcrt
+    build.build()
+    mcrt.lib()
+    return mcrt
+
+
+def test_hydrostatic_density_matches_oracle(M):
+    from oracle import hydro as H
+    d = disks.config_thick_gray(40, 30, 1e4)
+    g = M.Disk.from_model(d)
+    g.run_photons(200_000, seed=4, mrw=True, gamma=2.0, want_sed=False)
+    g.solve_pda()
+    T = g.temperatures(M.T_PDA)[0]
+    Ms = 2.5 * H.M_SUN
+    shell = H.shell_masses(d.r_faces_cm, d.theta_faces, d.rho)
+    rho_g = g.hydrostatic_density(M_star_g=Ms, mu=2.3, T_floor=10.0)
+    rho_o = H.hydrostatic_density(d.r_faces_cm, d.theta_faces, d.rho > 0, T, shell, M_star=Ms, mu=2.3, T_floor=10.0)
+    assert np.array_equal(rho_g > 0, rho_o > 0) or np.all(np.abs(rho_g - rho_o) <= 1e-200)
+    big = rho_o > 1e-200 * rho_o.max()
+    assert big.sum() > 500
+    assert np.max(np.abs(rho_g[big] / rho_o[big] - 1)) < 1e-9
+    # the new density keeps every shell's mass, and installing it keeps the shells' masses too
+    assert np.allclose(H.shell_masses(d.r_faces_cm, d.theta_faces, rho_g), shell, rtol=1e-12, atol=0)
+    g.set_density(rho_g)
+    t, v, a = g.tallies()
+    assert t.sum() == 0 and v.sum() == 0
+    rho_g2 = g.hydrostatic_density(M_star_g=Ms, which=M.T_MC, shell_mass=shell)
+    assert np.all(np.isfinite(rho_g2)) and rho_g2.max() > 0
+
+
+def test_iteration_reaches_three_sigma(M):
+    from paper_0902_3092_gb300 import hydro
+    d = disks.config_thick_gray(40, 30, 1e3)
+    _, hist = hydro.iterate(d, 300_000, max_iter=8, seed=7)
+    changes = [h["change_sigma"] for h in hist]
+    assert changes[-1] < 3.0, changes
+    assert len(hist) >= 2
