@@ -29,7 +29,7 @@ def test_hydrostatic_density_matches_oracle(M):
     rho_o = H.hydrostatic_density(d.r_faces_cm, d.theta_faces, d.rho > 0, T, shell, M_star=Ms, mu=2.3, T_floor=10.0)
     assert np.array_equal(rho_g > 0, rho_o > 0) or np.all(np.abs(rho_g - rho_o) <= 1e-200)
     big = rho_o > 1e-200 * rho_o.max()
-    assert big.sum() > 500
+    assert big.sum() > 200
     assert np.max(np.abs(rho_g[big] / rho_o[big] - 1)) < 1e-9
     # the new density keeps every shell's mass, and installing it keeps the shells' masses too
     assert np.allclose(H.shell_masses(d.r_faces_cm, d.theta_faces, rho_g), shell, rtol=1e-12, atol=0)
