@@ -41,9 +41,11 @@ def test_hydrostatic_density_matches_oracle(M):
 
 
 def test_iteration_reaches_three_sigma(M):
+    """Plain Monte Carlo (whose per-cell error is the counting error the criterion uses; MRW deposits
+    are larger than one packet energy, so there the counting error underestimates the scatter)."""
     from paper_0902_3092_gb300 import hydro
     d = disks.config_thick_gray(40, 30, 1e3)
-    _, hist = hydro.iterate(d, 300_000, max_iter=8, seed=7)
+    _, hist = hydro.iterate(d, 300_000, max_iter=8, seed=7, mrw=False)
     changes = [h["change_sigma"] for h in hist]
     assert changes[-1] < 3.0, changes
-    assert len(hist) >= 2
+    assert len(hist) >= 2 and changes[1] > changes[-1]
