@@ -67,6 +67,8 @@ def parse():
     p.add_argument("--pda-stress", type=int, default=0,
                    help="instead of the transport step: PDA solve on an N x N grid of the same disk (HBM roofline)")
     p.add_argument("--pda-iters", type=int, default=2000)
+    p.add_argument("--pda-adjoint", action="store_true",
+                   help="instead of the transport step: PDA solve and adjoint on the 400x200 non-gray disk")
     p.add_argument("--pda-min-visits", type=int, default=0,
                    help="PDA visit threshold; 0 scales the paper's 30 entries at 1e5 packets with the packet count "
                         "(Sect. 3.1 uses 30000 for its 1e8-packet runs)")
@@ -271,6 +273,37 @@ def pda_stress(args):
     print(json.dumps(line), flush=True)
 
 
+def pda_adjoint_timing(args):
+    """PDA forward solve and adjoint on the 400 x 200, tau_mid = 1e6 non-gray disk (the differentiable
+    PDA case) after a 1e7-packet MRW run; J = mean midplane temperature. Host-timed calls, 5 repeats."""
+    import torch
+    from paper_0902_3092_gb300 import disks, mcrt
+    d = disks.config_pda_adjoint(400, 200, 1e6)
+    g = mcrt.Disk.from_model(d)
+    g.run_photons(10_000_000, seed=1, mrw=True, gamma=2.0, max_events=10 ** 6, want_sed=False)
+    w = np.zeros((d.nr, d.ntheta))
+    j = d.ntheta // 2
+    w[:, j - 1:j + 1] = 1.0 / (2 * d.nr)
+    fw, bw, res = [], [], None
+    for _ in range(6):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        res = g.solve_pda(min_visits=3000)
+        t1 = time.perf_counter()
+        g.pda_adjoint(w)
+        t2 = time.perf_counter()
+        fw.append(t1 - t0)
+        bw.append(t2 - t1)
+    fw, bw = fw[1:], bw[1:]  # the first call allocates
+    line = {"metric": "PDA forward + adjoint time (400x200 non-gray disk, tau_mid=1e6)", "unit": "ms",
+            "value": 1e3 * (np.median(fw) + np.median(bw)), "higher_is_better": False, "n_gpus": 1,
+            "dtype": "f32 CG under f64 refinement", "data": "synthetic",
+            "config": {"workload": "400x200 non-gray disk, 1e7 MRW packets, PDA threshold 3000 entries",
+                       "pda_cells": res[0], "cg_iterations_forward": res[1]},
+            "forward_ms": 1e3 * float(np.median(fw)), "adjoint_ms": 1e3 * float(np.median(bw))}
+    print(json.dumps(line), flush=True)
+
+
 def main():
     args = parse()
     if args.impl == "reference":
@@ -278,6 +311,9 @@ def main():
         return
     if args.pda_stress:
         pda_stress(args)
+        return
+    if args.pda_adjoint:
+        pda_adjoint_timing(args)
         return
     import torch
     import torch.distributed as dist
