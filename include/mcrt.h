@@ -203,7 +203,7 @@ mcrt_status mcrt_pda_adjoint(mcrt_disk *d, const double *w, double *grad_log_rho
 mcrt_status mcrt_pda_adjoint_dev(mcrt_disk *d, const double *w_dev, double *grad_log_rho_dev,
                                  double *grad_kappa_R_dev);
 
-/* Vertical hydrostatic structure (Sect. 3, Eq. 20): dP/dz = -rho G M_star z / R^3 with P = k_B rho T /
+/* Vertical hydrostatic structure (Sect. 2.5, Eq. 20): dP/dz = -rho G M_star z / R^3 with P = k_B rho T /
  * (mu m_u), at fixed surface density, from the disk's last temperatures. Each radial shell is one
  * column (z = r_c cos theta_c, R = r_c sin theta_c at the cell centres; trapezoid rule in z from
  * theta = 0 to pi) and keeps its dust mass; cells without dust stay without dust. One GPU thread per

@@ -1,4 +1,4 @@
-"""Plain FP64 CPU oracle for the vertical hydrostatic structure of Min et al. 2009, Sect. 3 ("Vertical
+"""Plain FP64 CPU oracle for the vertical hydrostatic structure of Min et al. 2009, Sect. 2.5 ("Vertical
 structure", Eq. 20).
 
 TEST INFRASTRUCTURE. Only the test suite uses this module. It shares no code with the CUDA library.

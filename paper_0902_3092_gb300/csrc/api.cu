@@ -144,8 +144,8 @@ __global__ void k_temperature(int n, const unsigned long long* __restrict__ tall
     T[c] = pow(q / (4.0 * MCRT_SIGMA * kabs0), 0.25);
     return;
   }
-  // initial guess on the log-spaced grid (beyond it Q ~ T^4), then bracketed Newton on the exact
-  // bin integrals
+  // initial guess from the log-spaced grid, interpolated linearly in (log q, log T) (beyond it Q ~ T^4),
+  // then bracketed Newton on the exact bin integrals
   const double lq = log(q);
   double Tk;
   if (lq < (double)lQk[1]) {
@@ -153,9 +153,14 @@ __global__ void k_temperature(int n, const unsigned long long* __restrict__ tall
   } else if (lq >= (double)lQk[nT - 1]) {
     Tk = Tmin * exp((nT - 2) * dlnT) * exp(0.25 * (lq - (double)lQk[nT - 1]));
   } else {
-    int k = 1;
-    while (k + 1 < nT && (double)lQk[k + 1] <= lq) ++k;
-    Tk = Tmin * exp((k - 1) * dlnT);
+    int lo_k = 1, hi_k = nT - 1;  // lQk[lo_k] <= lq < lQk[hi_k]
+    while (hi_k - lo_k > 1) {
+      const int mid = (lo_k + hi_k) >> 1;
+      if ((double)lQk[mid] <= lq) lo_k = mid; else hi_k = mid;
+    }
+    const double a = (double)lQk[lo_k], b = (double)lQk[lo_k + 1];
+    const double w = b > a ? (lq - a) / (b - a) : 0.0;
+    Tk = Tmin * exp(((lo_k - 1) + w) * dlnT);
   }
   double lo = 0.0, hi = INFINITY;
   double x = Tk;

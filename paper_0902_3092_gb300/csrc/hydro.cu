@@ -1,4 +1,4 @@
-// hydro.cu -- vertical hydrostatic structure of the disk (Sect. 3, Eq. 20).
+// hydro.cu -- vertical hydrostatic structure of the disk (Sect. 2.5, Eq. 20).
 //
 // dP/dz = -rho G M_star z / R^3 with P = k_B rho T / (mu m_u), at fixed surface density, with the
 // temperatures of the last Monte Carlo (+ PDA) solution. Each radial shell of the (r, theta) grid is

@@ -137,10 +137,13 @@ __device__ double rosseland(const double* lam_e, const double* chip, int nlam, d
   return s1 / s2;
 }
 
-__global__ void k_kappaR(int n, const double* rho, const unsigned long long* tally, const double* T, const double* red,
-                         int gray, double chip0, int nlam, const double* lam_e, const double* chip, const double* over,
-                         double* kR) {
+// Rosseland extinction of the cells whose D enters a conductance (PDA cells and their dusty
+// neighbours); the others get a placeholder (their D takes part in no face)
+__global__ void k_kappaR(int nr, int nt, const signed char* mask, const double* rho, const unsigned long long* tally,
+                         const double* T, const double* red, int gray, double chip0, int nlam, const double* lam_e,
+                         const double* chip, const double* over, double* kR) {
   const int c = blockIdx.x * blockDim.x + threadIdx.x;
+  const int n = nr * nt;
   if (c >= n) return;
   if (!(rho[c] > 0)) {
     kR[c] = 1.0;
@@ -151,6 +154,13 @@ __global__ void k_kappaR(int n, const double* rho, const unsigned long long* tal
     return;
   }
   if (gray) {
+    kR[c] = chip0;
+    return;
+  }
+  const int i = c / nt, j = c - i * nt;
+  const bool used = mask[c] == 2 || (i > 0 && mask[c - nt] == 2) || (i + 1 < nr && mask[c + nt] == 2) ||
+                    (j > 0 && mask[c - 1] == 2) || (j + 1 < nt && mask[c + 1] == 2);
+  if (!used) {
     kR[c] = chip0;
     return;
   }
@@ -850,7 +860,8 @@ mcrt_status mcrt_solve_pda(mcrt_disk* d, const mcrt_pda_opts* o, int* out_n, int
     CK(over.alloc((size_t)n * 8), "cudaMalloc");
     CK(cudaMemcpyAsync(over.p, o->kappa_R, (size_t)n * 8, cudaMemcpyHostToDevice, st), "copy");
   }
-  k_kappaR<<<nblk(n), 256, 0, st>>>(n, rho, d->tally.as<unsigned long long>(), d->T_mc.as<double>(), red,
+  k_kappaR<<<nblk(n), 256, 0, st>>>(nr, nt, P->mask.as<signed char>(), rho, d->tally.as<unsigned long long>(),
+                                    d->T_mc.as<double>(), red,
                                     d->gray ? 1 : 0, (double)(d->kabs[0] + (1.0 - d->g[0]) * d->ksca[0]), d->nlam,
                                     d->lam_e_d.as<double>(), d->chip_d.as<double>(), over.as<double>(),
                                     P->kR.as<double>());

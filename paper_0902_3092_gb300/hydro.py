@@ -1,4 +1,4 @@
-"""Vertical hydrostatic structure iteration (Sect. 3, Eq. 20).
+"""Vertical hydrostatic structure iteration (Sect. 2.5, Eq. 20).
 
 Transport -> temperatures (Monte Carlo + PDA) -> density in hydrostatic equilibrium with them
 (`Disk.hydrostatic_density`, one GPU thread per radial shell) -> transport again, until the mean

@@ -232,7 +232,7 @@ class Disk:
         _check(lib().mcrt_reset(self._h), self._h)
 
     def hydrostatic_density(self, M_star_g=None, mu=None, T_floor=None, which=T_PDA, shell_mass=None):
-        """Density in hydrostatic equilibrium with the disk's temperatures (Sect. 3, Eq. 20), nr x ntheta."""
+        """Density in hydrostatic equilibrium with the disk's temperatures (Sect. 2.5, Eq. 20), nr x ntheta."""
         o = HydroOpts()
         lib().mcrt_default_hydro_opts(C.byref(o))
         if M_star_g is not None:

@@ -1,4 +1,4 @@
-"""Vertical hydrostatic structure on the GPU (Sect. 3, Eq. 20) against the FP64 oracle, and the
+"""Vertical hydrostatic structure on the GPU (Sect. 2.5, Eq. 20) against the FP64 oracle, and the
 iteration's 3-sigma convergence."""
 import numpy as np
 import pytest
@@ -45,7 +45,8 @@ def test_iteration_reaches_three_sigma(M):
     are larger than one packet energy, so there the counting error underestimates the scatter)."""
     from paper_0902_3092_gb300 import hydro
     d = disks.config_thick_gray(40, 30, 1e3)
-    _, hist = hydro.iterate(d, 300_000, max_iter=8, seed=7, mrw=False)
+    # 1e5 packets, as the case that the paper's structure iteration converges in 7 iterations (Sect. 3.4)
+    _, hist = hydro.iterate(d, 100_000, max_iter=12, seed=7, mrw=False)
     changes = [h["change_sigma"] for h in hist]
-    assert changes[-1] < 3.0, changes
+    assert changes[-1] < 3.0, changes  # the driver stops at the first iteration below 3 sigma
     assert len(hist) >= 2 and changes[1] > changes[-1]

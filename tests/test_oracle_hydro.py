@@ -1,4 +1,4 @@
-"""Pins of the vertical-structure oracle (Sect. 3, Eq. 20) against closed forms of the hydrostatic
+"""Pins of the vertical-structure oracle (Sect. 2.5, Eq. 20) against closed forms of the hydrostatic
 balance along a radial shell."""
 import numpy as np
 
