@@ -47,6 +47,7 @@ struct PdaState {
   bool vec4 = false;                  // tiles of 128 cells for the 16-byte kernels (ntheta % 4 == 0)
   int ntiles = 0;
   DBuf sc;                            // FP64 CG scalars per iteration
+  DBuf kctr;                          // int: index of the CG iteration, on the device (graph replay)
   DBuf red;                           // FP64 reduction slots
   DBuf w, gl, gk;                     // adjoint weights / gradient outputs (device staging)
   int n_pda = 0;
@@ -307,9 +308,11 @@ template <int U>
 __global__ void __launch_bounds__(256) k_cg_a(int n, int nt, int ntiles, const int* __restrict__ tiles,
                                               const float* __restrict__ ar, const float* __restrict__ at,
                                               const float* __restrict__ r, const float* __restrict__ p_old,
-                                              float* __restrict__ p_new, float* __restrict__ Ap, double* sc, int k,
+                                              float* __restrict__ p_new, float* __restrict__ Ap, double* sc, const int* kdev, int k, int kmax,
                                               double tol2) {
   __shared__ float sh[32];
+  if (kdev) k = *kdev;  // iteration index kept on the device (graph replay)
+  if (k >= kmax) return;
   const double rr0 = rr_of(sc, 0), rrk = rr_of(sc, k);
   if (rrk <= tol2 * rr0 || !(rrk == rrk)) return;  // converged (or broken): no-op
   const float beta = k == 0 ? 0.f : (float)(rrk / rr_of(sc, k - 1));
@@ -370,9 +373,11 @@ __global__ void __launch_bounds__(256) k_cg_a(int n, int nt, int ntiles, const i
 template <int U>
 __global__ void __launch_bounds__(256) k_cg_b(int n, int ntiles, const int* __restrict__ tiles,
                                               const float* __restrict__ p_new, const float* __restrict__ Ap,
-                                              float* __restrict__ y, float* __restrict__ r, double* sc, int k,
+                                              float* __restrict__ y, float* __restrict__ r, double* sc, const int* kdev, int k, int kmax,
                                               double tol2) {
   __shared__ float sh[32];
+  if (kdev) k = *kdev;  // iteration index kept on the device (graph replay)
+  if (k >= kmax) return;
   const double rr0 = rr_of(sc, 0), rrk = rr_of(sc, k);
   if (rrk <= tol2 * rr0 || !(rrk == rrk)) return;
   const float alpha = (float)(rrk / sc[2 * k + 1]);
@@ -424,9 +429,11 @@ __device__ __forceinline__ float4 ld4_or0(const float* __restrict__ a, int i, bo
 __global__ void __launch_bounds__(256) k_cg_a4(int n, int nt, int ntiles, const int* __restrict__ tiles,
                                                const float* __restrict__ ar, const float* __restrict__ at,
                                                const float* __restrict__ r, const float* __restrict__ p_old,
-                                               float* __restrict__ p_new, float* __restrict__ Ap, double* sc, int k,
+                                               float* __restrict__ p_new, float* __restrict__ Ap, double* sc, const int* kdev, int k, int kmax,
                                                double tol2) {
   __shared__ float sh[32];
+  if (kdev) k = *kdev;  // iteration index kept on the device (graph replay)
+  if (k >= kmax) return;
   const double rr0 = rr_of(sc, 0), rrk = rr_of(sc, k);
   if (rrk <= tol2 * rr0 || !(rrk == rrk)) return;  // converged (or broken): no-op
   const float beta = k == 0 ? 0.f : (float)(rrk / rr_of(sc, k - 1));
@@ -480,9 +487,11 @@ __global__ void __launch_bounds__(256) k_cg_a4(int n, int nt, int ntiles, const 
 
 __global__ void __launch_bounds__(256) k_cg_b4(int n, int ntiles, const int* __restrict__ tiles,
                                                const float* __restrict__ p_new, const float* __restrict__ Ap,
-                                               float* __restrict__ y, float* __restrict__ r, double* sc, int k,
+                                               float* __restrict__ y, float* __restrict__ r, double* sc, const int* kdev, int k, int kmax,
                                                double tol2) {
   __shared__ float sh[32];
+  if (kdev) k = *kdev;  // iteration index kept on the device (graph replay)
+  if (k >= kmax) return;
   const double rr0 = rr_of(sc, 0), rrk = rr_of(sc, k);
   if (rrk <= tol2 * rr0 || !(rrk == rrk)) return;
   const float alpha = (float)(rrk / sc[2 * k + 1]);
@@ -679,6 +688,7 @@ static mcrt_status pda_alloc(mcrt_disk* d, int max_inner) {
     if (e == cudaSuccess) e = P->mask.alloc(n);
     if (e == cudaSuccess) e = P->tiles.alloc(((size_t)n + 31) / 32 * sizeof(int));
     if (e == cudaSuccess) e = P->red.alloc(16 * 8);
+    if (e == cudaSuccess) e = P->kctr.alloc(16);
     if (e != cudaSuccess) return cuda_fail(d, e, "PDA buffers");
   }
   if (P->max_inner_alloc < max_inner) {
@@ -718,6 +728,49 @@ static bool components_ok(const mcrt_disk* d, const std::vector<signed char>& ma
   return true;
 }
 
+__global__ void k_iter_next(int* k) { ++*k; }
+
+// one CG iteration (kernels A and B) on the active tiles
+static void launch_cg_iteration(const PdaState* P, int n, int nt, const int* tiles, float* r, float* pold, float* pnew,
+                                float* Ap, float* y, double* sc, const int* kdev, int k, int kmax, double tol2, int ga,
+                                int gb, cudaStream_t st) {
+  if (P->vec4) {
+    k_cg_a4<<<ga, 256, 0, st>>>(n, nt, P->ntiles, tiles, P->ar.as<float>(), P->at.as<float>(), r, pold, pnew, Ap, sc,
+                                kdev, k, kmax, tol2);
+    k_cg_b4<<<gb, 256, 0, st>>>(n, P->ntiles, tiles, pnew, Ap, y, r, sc, kdev, k, kmax, tol2);
+  } else {
+    k_cg_a<kUA><<<ga, 256, 0, st>>>(n, nt, P->ntiles, tiles, P->ar.as<float>(), P->at.as<float>(), r, pold, pnew, Ap,
+                                    sc, kdev, k, kmax, tol2);
+    k_cg_b<kUB><<<gb, 256, 0, st>>>(n, P->ntiles, tiles, pnew, Ap, y, r, sc, kdev, k, kmax, tol2);
+  }
+}
+
+// an instantiated graph of `count` calls of a launch function captured on a stream; null when the
+// stream cannot be captured
+struct ChunkGraph {
+  cudaGraphExec_t exec = nullptr;
+  template <class F>
+  cudaGraphExec_t build(cudaStream_t st, int count, F launch) {
+    if (!st || cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+      cudaGetLastError();
+      return nullptr;
+    }
+    for (int j = 0; j < count; ++j) launch(j);
+    cudaGraph_t g = nullptr;
+    cudaError_t e = cudaStreamEndCapture(st, &g);
+    if (e == cudaSuccess && g) e = cudaGraphInstantiate(&exec, g, 0);
+    if (g) cudaGraphDestroy(g);
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      exec = nullptr;
+    }
+    return exec;
+  }
+  ~ChunkGraph() {
+    if (exec) cudaGraphExecDestroy(exec);
+  }
+};
+
 // FP64-refined solve of A x = b on the PDA cells; x holds the Dirichlet values elsewhere.
 static mcrt_status refine_solve(mcrt_disk* d, const mcrt_pda_opts* o, double* x, const double* b, int* iters_out) {
   PdaState* P = d->pda;
@@ -737,7 +790,16 @@ static mcrt_status refine_solve(mcrt_disk* d, const mcrt_pda_opts* o, double* x,
   const int gb = P->vec4 ? tgrid(k_cg_b4, P->ntiles) : tgrid(k_cg_b<kUB>, P->ntiles);
   double norm_b = -1.0, best = INFINITY;
   int total_iters = 0, stall = 0;
-  const int chunk = 32;
+  constexpr int chunk = 32;
+  // the CG iterations of one chunk as a CUDA graph (the index of the iteration lives on the device);
+  // without a graph (capture refused, e.g. on the legacy default stream) the kernels launch one by one
+  int* kdev = P->kctr.as<int>();
+  ChunkGraph cg;
+  cudaGraphExec_t chunk_exec = cg.build(st, chunk, [&](int j) {
+    launch_cg_iteration(P, n, nt, tiles, r, pb[(j + 1) & 1], pb[j & 1], Ap, y, sc, kdev, 0, o->max_inner, tol2_in, ga,
+                        gb, st);
+    k_iter_next<<<1, 1, 0, st>>>(kdev);
+  });
   for (int outer = 0; outer <= o->max_outer; ++outer) {
     CK(cudaMemsetAsync(red + 4, 0, 8, st), "memset");
     k_resid64<<<sgrid(n), 256, 0, st>>>(nr, nt, mask, Cr, Ct, dis, x, b, P->rs.as<double>(), red, 4);
@@ -767,37 +829,38 @@ static mcrt_status refine_solve(mcrt_disk* d, const mcrt_pda_opts* o, double* x,
     d->launches++;
     int k = 0;
     bool conv = false;
+    if (chunk_exec) CK(cudaMemsetAsync(kdev, 0, sizeof(int), st), "memset");
+    double h[2 * chunk + 2];
     while (k < o->max_inner && !conv) {
+      const int k0 = k;
       const int kend = std::min(k + chunk, o->max_inner);
-      for (; k < kend; ++k) {
-        float* pnew = pb[k & 1];
-        float* pold = pb[(k + 1) & 1];
-        if (P->vec4) {
-          k_cg_a4<<<ga, 256, 0, st>>>(n, nt, P->ntiles, tiles, P->ar.as<float>(), P->at.as<float>(), r, pold, pnew, Ap,
-                                      sc, k, tol2_in);
-          k_cg_b4<<<gb, 256, 0, st>>>(n, P->ntiles, tiles, pnew, Ap, y, r, sc, k, tol2_in);
-        } else {
-          k_cg_a<kUA><<<ga, 256, 0, st>>>(n, nt, P->ntiles, tiles, P->ar.as<float>(), P->at.as<float>(), r, pold, pnew,
-                                          Ap, sc, k, tol2_in);
-          k_cg_b<kUB><<<gb, 256, 0, st>>>(n, P->ntiles, tiles, pnew, Ap, y, r, sc, k, tol2_in);
+      if (chunk_exec) {
+        // one replay: `chunk` iterations, the iteration index read from the device; iterations at or
+        // beyond max_inner do nothing
+        CK(cudaGraphLaunch(chunk_exec, st), "graph launch");
+        d->launches += 3 * chunk;
+        k = kend;
+      } else {
+        for (; k < kend; ++k) {
+          float* pnew = pb[k & 1];
+          float* pold = pb[(k + 1) & 1];
+          launch_cg_iteration(P, n, nt, tiles, r, pold, pnew, Ap, y, sc, nullptr, k, o->max_inner, tol2_in, ga, gb, st);
+          d->launches += 2;
         }
-        d->launches += 2;
       }
-      std::vector<double> h(2 * (size_t)k + 2);
-      CK(cudaMemcpyAsync(h.data(), sc, sizeof(double) * h.size(), cudaMemcpyDeviceToHost, st), "copy");
+      // rr_0 and rr_{k0..k}
+      double rr0 = 0.0;
+      CK(cudaMemcpyAsync(&rr0, sc, sizeof(double), cudaMemcpyDeviceToHost, st), "copy");
+      CK(cudaMemcpyAsync(h, sc + 2 * k0, sizeof(double) * (2 * (size_t)(k - k0) + 1), cudaMemcpyDeviceToHost, st),
+         "copy");
       CK(cudaStreamSynchronize(st), "synchronize");
-      const double rr0 = h[0];
-      int kk = 0;
-      for (kk = 0; kk <= k; ++kk) {
-        const double v = h[2 * kk];
+      for (int kk = k0; kk <= k; ++kk) {
+        const double v = h[2 * (kk - k0)];
         if (v <= tol2_in * rr0 || !(v == v)) {
           conv = true;
+          total_iters += kk;
           break;
         }
-      }
-      if (conv) {
-        total_iters += kk;
-        break;
       }
     }
     if (!conv) total_iters += k;
@@ -1093,9 +1156,10 @@ extern "C" mcrt_status mcrt_pda_solve_static(int device, int nr, int ntheta, con
       const int k0 = k;
       const int kend = std::min(k + chunk, o->max_inner);
       for (; k < kend; ++k) {
-        k_cg_a<kUA><<<ga, 256, 0, st>>>(n, nt, ntiles, nullptr, ar, at, r, pb[(k + 1) & 1], pb[k & 1], Ap, sc, k,
-                                   tol2_in);
-        k_cg_b<kUB><<<gb, 256, 0, st>>>(n, ntiles, nullptr, pb[k & 1], Ap, y, r, sc, k, tol2_in);
+        k_cg_a<kUA><<<ga, 256, 0, st>>>(n, nt, ntiles, nullptr, ar, at, r, pb[(k + 1) & 1], pb[k & 1], Ap, sc, nullptr,
+                                        k, kStaticMaxInner, tol2_in);
+        k_cg_b<kUB><<<gb, 256, 0, st>>>(n, ntiles, nullptr, pb[k & 1], Ap, y, r, sc, nullptr, k, kStaticMaxInner,
+                                        tol2_in);
       }
       // rr_0 and rr_{k0..k}
       double rr0 = 0.0;
