@@ -135,3 +135,27 @@ def test_singular_region_rejected(M):
     with pytest.raises(M.McrtError) as e:
         g.solve_pda()
     assert e.value.status == 1
+
+
+@pytest.mark.parametrize("ntheta", [20, 22])
+@pytest.mark.parametrize("legacy_stream", [False, True])
+def test_pda_launch_paths(M, oracle, ntheta, legacy_stream):
+    """The 16-byte kernels (ntheta % 4 == 0) and the 4-byte ones, each with the CG iterations replayed as
+    a CUDA graph (the disk's own stream) or launched one by one (the legacy default stream, which
+    cannot be captured), solve the same system as the oracle."""
+    d = disks.config_plain_gray(24, ntheta, 1e4)
+    rc, tc = disks.cell_centres(d.r_faces_cm, d.theta_faces)
+    Tw = 400.0 * (rc[:, None] / disks.AU_CM) ** -0.5 * (1 + 0.3 * np.cos(tc)[None, :] ** 2)
+    mask = (d.rho > 0) & (np.abs(tc - math.pi / 2)[None, :] < 0.15) & (np.arange(d.nr)[:, None] > 2)
+    tally, visits = state_for(d, Tw, mask)
+    g = M.Disk.from_model(d, stream=1 if legacy_stream else None)  # 1: cudaStreamLegacy
+    g.restore(blob(d, tally, visits, 10 ** 6))
+    n_pda, iters = g.solve_pda()
+    Tg, _, _ = g.temperatures(M.T_PDA)
+    r = oracle.Run(d)
+    r.tally[:] = tally
+    r.n_total = 10 ** 6
+    To_mc, eo = r.temperatures()
+    To, mo, _, _ = oracle.solve_pda(d, To_mc, tally, visits, eo)
+    assert n_pda == int(mo.sum()) > 20 and iters > 0
+    assert np.max(np.abs(Tg[mo] / To[mo] - 1)) < 1e-6
