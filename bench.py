@@ -41,14 +41,14 @@ WORKLOAD = "thick gray disk 200x120 rim-refined, tau_mid=1e6, albedo 0.5 isotrop
 # packet). The kernels are bound by instruction issue (divergent, latency-bound integer/FP32 work, no
 # DRAM traffic), so the roofline is issue slots: 152 SMs x 4 schedulers x 1 warp instruction per clock
 # at 2070 MHz.
-WARP_INST_PER_STEP = 35.2
-THREAD_INST_PER_STEP = 333.0
+WARP_INST_PER_STEP = 35.3
+THREAD_INST_PER_STEP = 311.0
 ISSUE_PEAK = 152 * 4 * 2070e6           # warp instructions / s
 THREAD_ISSUE_PEAK = 32 * ISSUE_PEAK     # thread instructions / s (all lanes busy)
 # DRAM bytes of one transport call (ncu dram__bytes_read.sum + dram__bytes_write.sum of its two kernels,
 # 1e7 packets of this workload): tables and tallies stay in L2; the tail kernel reads the ~1.2e5 packet
 # states stored at the drain (13 MB). Neither grows with the packet count.
-TRANSPORT_DRAM_BYTES = 1546240 + 11776 + 13414144 + 256
+TRANSPORT_DRAM_BYTES = 1512704 + 20224 + 13437952 + 0
 
 
 def parse():
