@@ -67,6 +67,8 @@ def parse():
     p.add_argument("--pda-stress", type=int, default=0,
                    help="instead of the transport step: PDA solve on an N x N grid of the same disk (HBM roofline)")
     p.add_argument("--pda-iters", type=int, default=2000)
+    p.add_argument("--batch-sweep", action="store_true",
+                   help="instead of the transport step: the 64-model batched sweep (one graph replay per step)")
     p.add_argument("--pda-adjoint", action="store_true",
                    help="instead of the transport step: PDA solve and adjoint on the 400x200 non-gray disk")
     p.add_argument("--pda-min-visits", type=int, default=0,
@@ -273,6 +275,37 @@ def pda_stress(args):
     print(json.dumps(line), flush=True)
 
 
+def batch_sweep_timing(args):
+    """The batched sweep: 64 non-gray models of uneven grid, optical depth (1e2-1e6) and packet budget
+    (1e5-1e7 each) from seed 1, MRW gamma = 2, in one persistent launch replayed from a CUDA graph whose
+    launch shape the autotuner picked; packets/s over the whole batch (CUDA-event launch time)."""
+    import torch
+    from paper_0902_3092_gb300 import disks, mcrt
+    ds, npk = disks.batch_sweep(64, seed=1)
+    gs = [mcrt.Disk.from_model(d) for d in ds]
+    B = mcrt.Batch(gs, npk, mrw=True, gamma=args.gamma, max_events=int(args.max_events), want_sed=False)
+    cfg = B.config()
+    for s in range(max(1, args.warmup)):
+        B.run(seed=100 + s)
+    secs, events, capped = [], 0, 0
+    for s in range(args.steps):
+        for g in gs:
+            g.reset()
+        torch.cuda.synchronize()
+        st = B.run(seed=1 + s)
+        secs.append(max(x["seconds"] for x in st))
+        events += sum(x["events"] for x in st)
+        capped += sum(x["capped"] for x in st)
+    total = int(sum(npk))
+    line = {"metric": "photon packets/s, 64-model batched sweep (one graph launch)", "unit": "packets/s",
+            "value": total / float(np.mean(secs)), "higher_is_better": True, "n_gpus": 1, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": 1e3 * float(np.mean(secs)), "dtype": "f32", "data": "synthetic",
+            "config": {"workload": "64 non-gray disks nr 50-300 x ntheta 30-180, tau_mid 1e2-1e6, MRW gamma=2",
+                       "packets_per_step": total, "autotuned": cfg},
+            "events_per_s": events / float(np.sum(secs)), "capped_fraction": capped / (total * args.steps)}
+    print(json.dumps(line), flush=True)
+
+
 def pda_adjoint_timing(args):
     """PDA forward solve and adjoint on the 400 x 200, tau_mid = 1e6 non-gray disk (the differentiable
     PDA case) after a 1e7-packet MRW run; J = mean midplane temperature. Host-timed calls, 5 repeats."""
@@ -314,6 +347,9 @@ def main():
         return
     if args.pda_adjoint:
         pda_adjoint_timing(args)
+        return
+    if args.batch_sweep:
+        batch_sweep_timing(args)
         return
     import torch
     import torch.distributed as dist
