@@ -759,7 +759,7 @@ static mcrt_status run_impl(mcrt_disk* d, uint64_t n_packets, uint64_t seed, uin
       e = launch_transport<double>(P, trace, false, d->gray, grid, block, d->stream);
       d->launches++;
       if (e == cudaSuccess && tail) {
-        e = launch_transport_tail<double>(P, trace, d->gray, dev_sms, o->tail_warps_per_sm, d->stream);
+        e = launch_transport_tail<double>(P, trace, false, d->gray, dev_sms, o->tail_warps_per_sm, d->stream);
         d->launches++;
       }
     } else {
@@ -781,7 +781,7 @@ static mcrt_status run_impl(mcrt_disk* d, uint64_t n_packets, uint64_t seed, uin
       e = launch_transport<float>(P, false, false, d->gray, grid, block, d->stream);
       d->launches++;
       if (e == cudaSuccess && tail) {
-        e = launch_transport_tail<float>(P, false, d->gray, dev_sms, o->tail_warps_per_sm, d->stream);
+        e = launch_transport_tail<float>(P, false, false, d->gray, dev_sms, o->tail_warps_per_sm, d->stream);
         d->launches++;
       }
     }
@@ -1115,7 +1115,9 @@ struct mcrt_batch {
   double tune_seconds = 0.0;
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t exec = nullptr;
-  cudaGraphNode_t knode = nullptr;
+  std::vector<cudaGraphNode_t> knodes;  // kernel nodes (their KParams carry the seed)
+  DBuf pool, pool_ctr;                   // packets in flight at the drain, for the tail kernel
+  int tail_warps = 0, sms = 0;
   std::string err;
   ~mcrt_batch() {
     if (exec) cudaGraphExecDestroy(exec);
@@ -1133,7 +1135,13 @@ cudaError_t batch_launch(mcrt_batch* b, const KParams<float>& P, int block, int 
   }
   e = cudaMemsetAsync(b->queue.p, 0, 8, b->stream);
   if (e != cudaSuccess) return e;
-  return launch_transport<float>(P, false, true, false, grid, block, b->stream);
+  if (P.pool) {
+    e = cudaMemsetAsync(P.pool_ctr, 0, 16, b->stream);
+    if (e != cudaSuccess) return e;
+  }
+  e = launch_transport<float>(P, false, true, false, grid, block, b->stream);
+  if (e != cudaSuccess || !P.pool) return e;
+  return launch_transport_tail<float>(P, false, true, false, b->sms, b->tail_warps, b->stream);
 }
 }  // namespace
 
@@ -1260,6 +1268,19 @@ mcrt_status mcrt_batch_create(mcrt_disk* const* disks, int n, const uint64_t* n_
   }
   b->P.refill = b->refill;
   b->grid = grid_for(b->block);
+  // the tail kernel's pool: one slot per thread of the chosen launch (the autotuner ran without it)
+  b->sms = sms;
+  b->tail_warps = o->tail_warps_per_sm;
+  if (o->tail_warps_per_sm >= 0) {
+    const size_t cap = (size_t)b->grid * b->block;
+    if (b->pool.alloc(cap * sizeof(Pkt<float>)) == cudaSuccess && b->pool_ctr.alloc(16) == cudaSuccess) {
+      b->P.pool = b->pool.as<Pkt<float>>();
+      b->P.pool_ctr = b->pool_ctr.as<unsigned>();
+      b->P.pool_cap = (unsigned)cap;
+    } else {
+      cudaGetLastError();
+    }
+  }
   // capture: counter resets + the persistent launch
   e = cudaStreamSynchronize(b->stream);
   if (e == cudaSuccess) e = cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal);
@@ -1277,9 +1298,9 @@ mcrt_status mcrt_batch_create(mcrt_disk* const* disks, int n, const uint64_t* n_
     for (size_t k = 0; e == cudaSuccess && k < nn; ++k) {
       cudaGraphNodeType ty;
       cudaGraphNodeGetType(nodes[k], &ty);
-      if (ty == cudaGraphNodeTypeKernel) b->knode = nodes[k];
+      if (ty == cudaGraphNodeTypeKernel) b->knodes.push_back(nodes[k]);
     }
-    if (e == cudaSuccess && !b->knode) e = cudaErrorInvalidValue;
+    if (e == cudaSuccess && b->knodes.empty()) e = cudaErrorInvalidValue;
   }
   if (e != cudaSuccess) {
     delete b;
@@ -1295,11 +1316,13 @@ mcrt_status mcrt_batch_run(mcrt_batch* b, uint64_t seed, mcrt_run_stats* stats) 
   CK(cudaSetDevice(b->device), "cudaSetDevice");
   if (seed != b->P.seed) {
     b->P.seed = seed;
-    cudaKernelNodeParams kp;
-    CK(cudaGraphKernelNodeGetParams(b->knode, &kp), "kernel node params");
-    void* args[1] = {&b->P};
-    kp.kernelParams = args;
-    CK(cudaGraphExecKernelNodeSetParams(b->exec, b->knode, &kp), "kernel node update");
+    for (cudaGraphNode_t kn : b->knodes) {  // the transport and the tail kernel both take the KParams
+      cudaKernelNodeParams kp;
+      CK(cudaGraphKernelNodeGetParams(kn, &kp), "kernel node params");
+      void* args[1] = {&b->P};
+      kp.kernelParams = args;
+      CK(cudaGraphExecKernelNodeSetParams(b->exec, kn, &kp), "kernel node update");
+    }
   }
   cudaEvent_t e0, e1;
   CK(cudaEventCreate(&e0), "event");

@@ -45,7 +45,7 @@ template <class R>
 int transport_blocks_per_sm(bool trace, bool batch, bool gray, int block);
 // tail kernel of a single-disk launch: 32-thread blocks, warps_per_sm of them per SM (0: 20)
 template <class R>
-cudaError_t launch_transport_tail(const KParams<R>& P, bool trace, bool gray, int sms, int warps_per_sm,
+cudaError_t launch_transport_tail(const KParams<R>& P, bool trace, bool batch, bool gray, int sms, int warps_per_sm,
                                   cudaStream_t st);
 
 }  // namespace mcrt

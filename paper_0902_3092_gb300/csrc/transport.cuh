@@ -857,11 +857,10 @@ __device__ __forceinline__ int interactions_at_once(const KParams<R>& P, WarpRng
 // its speed alone. The transport kernel therefore stores them (state unchanged, so the random stream
 // and the result are the same) and this kernel runs them one per warp: lane 0 of each 32-thread block
 // takes packets from the pool, those that had taken at least kTailLongSteps steps first.
-template <class R, bool TRACE, bool G>
+template <class R, bool TRACE, bool G, bool BATCH>
 __global__ void __launch_bounds__(32) transport_tail_kernel(const KParams<R> P) {
   const unsigned lane = threadIdx.x & 31u;
   if (TRACE && lane != 0) return;  // the debug trace runs one lane per packet
-  const DevModel<R>& M = P.m0;
   Acc acc = Acc{};
   const unsigned nlong = P.pool_ctr[0], nshort = P.pool_ctr[1];
   for (;;) {
@@ -870,6 +869,7 @@ __global__ void __launch_bounds__(32) transport_tail_kernel(const KParams<R> P) 
     if (!TRACE) k = __shfl_sync(0xffffffffu, k, 0);
     if (k >= nlong + nshort) break;
     Pkt<R> s = P.pool[k < nlong ? k : P.pool_cap - 1u - (k - nlong)];
+    const DevModel<R>& M = BATCH ? P.models[s.model] : P.m0;  // batches: the packet's model index
     if (TRACE) {
       SerialRng rng{{(uint32_t)P.seed, (uint32_t)(P.seed >> 32)}};
       while (step<R, TRACE, G>(P, rng, M, s, acc)) {
@@ -881,7 +881,7 @@ __global__ void __launch_bounds__(32) transport_tail_kernel(const KParams<R> P) 
       bool ended = false, misses = false;
       for (;;) {
         // (FP32 only: the FP64 debug path keeps the oracle's order of floating-point operations)
-        if (G && sizeof(R) == 4 && !misses && !s.pend && s.ir >= 0 && s.alpha > (R)0 && M.g0 == (R)0 &&
+        if ((G || M.gray) && sizeof(R) == 4 && !misses && !s.pend && s.ir >= 0 && s.alpha > (R)0 && M.g0 == (R)0 &&
             s.events + 33u < P.max_events && s.steps + 33u < P.max_steps) {
           const int n = interactions_at_once<R, G>(P, rng, M, s, acc, ended, misses);
           if (ended) break;
@@ -891,9 +891,12 @@ __global__ void __launch_bounds__(32) transport_tail_kernel(const KParams<R> P) 
         if (!step<R, TRACE, G>(P, rng, M, s, acc)) break;
       }
     }
-    if (lane == 0) note_end(s, acc);
+    if (lane == 0) {
+      note_end(s, acc);
+      if (BATCH) flush(M, acc, false);  // counters of the packet's model
+    }
   }
-  if (lane == 0) flush(M, acc, false);
+  if (!BATCH && lane == 0) flush(P.m0, acc, false);
 }
 
 // resident 256-thread blocks per SM the FP32 kernel is compiled for (register budget 65536 / (256 n))
@@ -944,10 +947,10 @@ __global__ void __launch_bounds__(256, transport_min_blocks<R>()) transport_kern
         }
       }
       if (__all_sync(0xffffffffu, done && !active)) break;
-      // a lane that found the queue empty means it is empty for every lane: single-disk launches
-      // hand the packets still in flight to the tail kernel; batches run them to the end here
+      // a lane that found the queue empty means it is empty for every lane: the packets still in
+      // flight go to the tail kernel (or, without its pool, run to the end here)
       if (__any_sync(0xffffffffu, done)) {
-        if (!BATCH && P.pool) {
+        if (P.pool) {
           if (active) {
             const bool longp = s.steps >= kTailLongSteps;
             const unsigned k = atomicAdd(P.pool_ctr + (longp ? 0 : 1), 1u);

@@ -19,15 +19,16 @@ cudaError_t launch_transport<double>(const KParams<double>& P, bool trace, bool 
 }
 
 template <>
-cudaError_t launch_transport_tail<double>(const KParams<double>& P, bool trace, bool gray, int sms, int warps_per_sm,
-                                          cudaStream_t st) {
+cudaError_t launch_transport_tail<double>(const KParams<double>& P, bool trace, bool batch, bool gray, int sms,
+                                          int warps_per_sm, cudaStream_t st) {
+  if (batch) return cudaErrorInvalidValue;
   const int grid = sms * (warps_per_sm > 0 ? warps_per_sm : 20);
   if (trace) {
-    if (gray) transport_tail_kernel<double, true, true><<<grid, 32, 0, st>>>(P);
-    else transport_tail_kernel<double, true, false><<<grid, 32, 0, st>>>(P);
+    if (gray) transport_tail_kernel<double, true, true, false><<<grid, 32, 0, st>>>(P);
+    else transport_tail_kernel<double, true, false, false><<<grid, 32, 0, st>>>(P);
   } else {
-    if (gray) transport_tail_kernel<double, false, true><<<grid, 32, 0, st>>>(P);
-    else transport_tail_kernel<double, false, false><<<grid, 32, 0, st>>>(P);
+    if (gray) transport_tail_kernel<double, false, true, false><<<grid, 32, 0, st>>>(P);
+    else transport_tail_kernel<double, false, false, false><<<grid, 32, 0, st>>>(P);
   }
   return cudaGetLastError();
 }

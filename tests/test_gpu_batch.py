@@ -24,7 +24,8 @@ def test_first_model_equals_single_disk_run(M):
     b = disks.config_nongray(30, 24, 1e3)
     c = disks.config_thick_gray(40, 30, 1e4)
     ga, gb, gc = M.Disk.from_model(a), M.Disk.from_model(b), M.Disk.from_model(c)
-    B = M.Batch([ga, gb, gc], [60_000, 40_000, 30_000], mrw=True, gamma=2.0, max_events=10 ** 6)
+    # without the tail kernel (its batched interactions sum positions in another floating-point order)
+    B = M.Batch([ga, gb, gc], [60_000, 40_000, 30_000], mrw=True, gamma=2.0, max_events=10 ** 6, tail_warps=-1)
     cfg = B.config()
     assert cfg["block_size"] in (64, 128, 256) and cfg["refill_interval"] in (1, 4, 16)  # the tuner's candidates
     st = B.run(seed=5)
@@ -50,7 +51,7 @@ def test_replay_with_new_seed(M, oracle):
     a = disks.config_plain_gray(16, 16, 100.0)
     b = disks.config_plain_gray(16, 16, 300.0)
     ga, gb = M.Disk.from_model(a), M.Disk.from_model(b)
-    B = M.Batch([ga, gb], [200_000, 200_000], block_size=256, refill=4)
+    B = M.Batch([ga, gb], [200_000, 200_000], block_size=256, refill=4, tail_warps=-1)  # bitwise replays
     assert B.config()["block_size"] == 256
     B.run(seed=1)
     t1, _, _ = gb.tallies()
@@ -79,8 +80,13 @@ def test_sweep_of_64_models(M):
     npk = [max(1000, n // 100) for n in npk]
     gs = [M.Disk.from_model(d) for d in ds]
     B = M.Batch(gs, npk, mrw=True, gamma=2.0, max_events=10 ** 5)
-    st = B.run(seed=1)
-    for s, n in zip(st, npk):
-        assert s["packets"] == n and s["escaped"] + s["capped"] == n
-        assert s["error_flags"] == 0
+    for seed in (1, 2):  # a new seed updates both kernel nodes of the graph (transport and tail)
+        for g in gs:
+            g.reset()
+        st = B.run(seed=seed)
+        for g, s, n in zip(gs, st, npk):
+            assert s["packets"] == n and s["escaped"] + s["capped"] == n
+            assert s["error_flags"] == 0
+            t, _, _ = g.tallies()
+            assert int(t.sum(dtype=np.uint64)) == s["deposit_sum"]  # every deposit reached its model's tallies
     B.close()
