@@ -127,8 +127,9 @@ __device__ void q_sum(const double* lam_e, const double* kabs, int nlam, double 
 
 __global__ void k_temperature(int n, const unsigned long long* __restrict__ tally, const double* __restrict__ mass,
                               double lfac, int gray, double kabs0, int nlam, const double* __restrict__ lam_e,
-                              const double* __restrict__ kabs, const float* __restrict__ lQk, int nT, double Tmin,
-                              double dlnT, double* __restrict__ T, double* __restrict__ relerr) {
+                              const double* __restrict__ kabs, const double* __restrict__ lQk,
+                              const double* __restrict__ slQ, int nT, double Tmin, double dlnT,
+                              double* __restrict__ T, double* __restrict__ relerr) {
   const int c = blockIdx.x * blockDim.x + threadIdx.x;
   if (c >= n) return;
   const unsigned long long t = tally[c];
@@ -144,23 +145,30 @@ __global__ void k_temperature(int n, const unsigned long long* __restrict__ tall
     T[c] = pow(q / (4.0 * MCRT_SIGMA * kabs0), 0.25);
     return;
   }
-  // initial guess from the log-spaced grid, interpolated linearly in (log q, log T) (beyond it Q ~ T^4),
-  // then bracketed Newton on the exact bin integrals
+  // initial guess from the log-spaced grid: log T as a cubic Hermite function of log Q between the two
+  // grid temperatures that bracket q (slopes d log T / d log Q from the table; beyond the grid Q ~ T^4),
+  // then bracketed Newton on the exact bin integrals (about two evaluations from this guess)
   const double lq = log(q);
   double Tk;
-  if (lq < (double)lQk[1]) {
-    Tk = Tmin * exp(0.25 * (lq - (double)lQk[1]));
-  } else if (lq >= (double)lQk[nT - 1]) {
-    Tk = Tmin * exp((nT - 2) * dlnT) * exp(0.25 * (lq - (double)lQk[nT - 1]));
+  if (lq < lQk[1]) {
+    Tk = Tmin * exp(0.25 * (lq - lQk[1]));
+  } else if (lq >= lQk[nT - 1]) {
+    Tk = Tmin * exp((nT - 2) * dlnT) * exp(0.25 * (lq - lQk[nT - 1]));
   } else {
     int lo_k = 1, hi_k = nT - 1;  // lQk[lo_k] <= lq < lQk[hi_k]
     while (hi_k - lo_k > 1) {
       const int mid = (lo_k + hi_k) >> 1;
-      if ((double)lQk[mid] <= lq) lo_k = mid; else hi_k = mid;
+      if (lQk[mid] <= lq) lo_k = mid; else hi_k = mid;
     }
-    const double a = (double)lQk[lo_k], b = (double)lQk[lo_k + 1];
-    const double w = b > a ? (lq - a) / (b - a) : 0.0;
-    Tk = Tmin * exp(((lo_k - 1) + w) * dlnT);
+    const double x0 = lQk[lo_k], x1 = lQk[lo_k + 1], h = x1 - x0;
+    const double y0 = (lo_k - 1) * dlnT, y1 = lo_k * dlnT;
+    const double m0 = 1.0 / slQ[lo_k], m1 = 1.0 / slQ[lo_k + 1];
+    double y = y0;
+    if (h > 0) {
+      const double t = (lq - x0) / h, t2 = t * t, t3 = t2 * t;
+      y = (2 * t3 - 3 * t2 + 1) * y0 + (t3 - 2 * t2 + t) * h * m0 + (-2 * t3 + 3 * t2) * y1 + (t3 - t2) * h * m1;
+    }
+    Tk = Tmin * exp(y);
   }
   double lo = 0.0, hi = INFINITY;
   double x = Tk;
@@ -170,6 +178,13 @@ __global__ void k_temperature(int n, const unsigned long long* __restrict__ tall
     const double f = Q - q;
     if (f > 0) hi = x; else lo = x;
     double xn = x - f / dQ;
+    // Q is smooth and increasing in T, so a Newton step of relative size s leaves a relative error of
+    // order s^2: below 1e-8 the new point is the root to rounding (this also ends a guess that is the
+    // root already, where f may be 0 and the step would not lie strictly inside the bracket)
+    if (fabs(xn - x) <= 1e-8 * x) {
+      x = xn;
+      break;
+    }
     if (!(xn > lo && xn < hi)) xn = isinf(hi) ? 2.0 * x : 0.5 * (lo + hi);
     if (fabs(xn - x) <= 1e-15 * x) {
       x = xn;
@@ -186,7 +201,8 @@ mcrt_status compute_temperatures(mcrt_disk* d) {
   const double dlnT = std::log(d->Tmax / d->Tmin) / (d->nT - 2);
   k_temperature<<<(n + 255) / 256, 256, 0, d->stream>>>(
       n, d->tally.as<unsigned long long>(), d->mass_d.as<double>(), lfac, d->gray ? 1 : 0, d->kabs[0], d->nlam,
-      d->lam_e_d.as<double>(), d->kabs_d.as<double>(), d->lQk.as<float>(), d->nT, d->Tmin, dlnT,
+      d->lam_e_d.as<double>(), d->kabs_d.as<double>(), d->lQ64.as<double>(), d->slQ64.as<double>(), d->nT, d->Tmin,
+      dlnT,
       d->T_mc.as<double>(), d->relerr.as<double>());
   d->launches++;
   cudaError_t e = cudaGetLastError();
@@ -534,6 +550,7 @@ mcrt_status mcrt_set_opacity(mcrt_disk* d, int nlam, const double* lam_e, const 
   const int nT = d->nT;
   const double dlnT = std::log(d->Tmax / d->Tmin) / (nT - 2);
   std::vector<float> lQk(nT), cbw((size_t)nT * nlam, 0.f), cexit((size_t)nT * nlam), chiRk(nT), kbark(nT);
+  std::vector<double> lQ64(nT, -INFINITY), slQ64(nT, 4.0);  // FP64 log Q and d log Q / d log T (guess of T)
   lQk[0] = -INFINITY;
   for (int k = 0; k < nT; ++k) {
     const double T = (k == 0) ? d->Tmin : d->Tmin * std::exp((k - 1) * dlnT);
@@ -549,7 +566,11 @@ mcrt_status mcrt_set_opacity(mcrt_disk* d, int nlam, const double* lam_e, const 
       if (k > 0) cbw[(size_t)k * nlam + b] = (float)c1;
       cexit[(size_t)k * nlam + b] = (float)c2;
     }
-    if (k > 0) lQk[k] = (float)std::log(4.0 * kPi * q);
+    if (k > 0) {
+      lQk[k] = (float)std::log(4.0 * kPi * q);
+      lQ64[k] = std::log(4.0 * kPi * q);
+      slQ64[k] = q > 0 ? T * skdb / q : 4.0;
+    }
     chiRk[k] = (float)(sdb / sdbc);
     kbark[k] = (float)(skdb / sdb);
   }
@@ -568,6 +589,8 @@ mcrt_status mcrt_set_opacity(mcrt_disk* d, int nlam, const double* lam_e, const 
   UP(d->g64, d->g);
   UP(d->star64, star);
   UP(d->lQk, lQk);
+  UP(d->lQ64, lQ64);
+  UP(d->slQ64, slQ64);
   UP(d->cbw, cbw);
   UP(d->cexit, cexit);
   UP(d->chiRk, chiRk);

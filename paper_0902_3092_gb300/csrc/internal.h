@@ -69,6 +69,7 @@ struct mcrt_disk {
   mcrt::DBuf fk;
   mcrt::DBuf chi32, alb32, g32, star32, chi64, alb64, g64, star64;
   mcrt::DBuf lQk, cbw, cexit, chiRk, kbark, lqm;
+  mcrt::DBuf lQ64, slQ64;  // FP64 log Q(T_k) and d log Q / d log T on the T grid (temperature guesses)
   mcrt::DBuf lam_e_d, kabs_d, chip_d;  // FP64 per-bin data for exact temperatures / Rosseland means
   mcrt::DBuf mass_d, rho_cgs_d;
   // tallies

@@ -58,15 +58,16 @@ __host__ __device__ inline void g34_large(double x, double& g3, double& g4) {
   g3 = 0.0;
   g4 = 0.0;
   const double x2 = x * x, x3 = x2 * x, x4 = x3 * x;
+  const double e1 = exp(-x);
+  double e = e1;  // exp(-n x) as a running product: one exponential per call
   for (int n = 1; n < 200; ++n) {
-    const double dn = (double)n;
-    const double e = exp(-dn * x);
-    const double t3 = e * (x3 / dn + 3.0 * x2 / (dn * dn) + 6.0 * x / (dn * dn * dn) + 6.0 / (dn * dn * dn * dn));
-    const double t4 = e * (x4 + 4.0 * x3 / dn + 12.0 * x2 / (dn * dn) + 24.0 * x / (dn * dn * dn) +
-                           24.0 / (dn * dn * dn * dn));
+    const double q = 1.0 / (double)n, q2 = q * q, q3 = q2 * q, q4 = q3 * q;
+    const double t3 = e * (x3 * q + 3.0 * x2 * q2 + 6.0 * x * q3 + 6.0 * q4);
+    const double t4 = e * (x4 + 4.0 * x3 * q + 12.0 * x2 * q2 + 24.0 * x * q3 + 24.0 * q4);
     g3 += t3;
     g4 += t4;
-    if (t4 < 1e-18 * g4 && t3 < 1e-18 * g3) break;
+    if (t4 <= 1e-18 * g4 && t3 <= 1e-18 * g3) break;  // also ends at once where exp(-x) underflows to 0
+    e *= e1;
   }
 }
 
