@@ -238,7 +238,11 @@ mcrt_status mcrt_trace_packets(mcrt_disk *d, uint64_t n_packets, uint64_t seed, 
                                int32_t *lam, double *pos, int32_t *n_events);
 
 /* Checkpoint of the integer state (tallies, visits, absorptions, spectrum, packets done). buf == NULL:
- * *len receives the size needed. Restoring and continuing the packet ids reproduces a single run. */
+ * *len receives the size needed. Restoring and continuing the packet ids reproduces a single run.
+ * Layout, all uint64 in host byte order: a header of 8 words {0x4D43525443484B31, version 1, nr, ntheta,
+ * nlam, packets done, bits of the double packet count that normalises the tallies, 0}, then per cell
+ * (r-major) the tallies, the entry counts and the absorption counts, then the escaping-energy spectrum
+ * (nlam x 10 inclination bins). mcrt_restore checks the header against the disk (MCRT_EINVAL). */
 mcrt_status mcrt_checkpoint(mcrt_disk *d, void *buf, size_t *len);
 mcrt_status mcrt_restore(mcrt_disk *d, const void *buf, size_t len);
 

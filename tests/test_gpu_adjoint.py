@@ -2,15 +2,21 @@
 non-gray disk: d(mean midplane T)/d(log rho, kappa_R) against the FP64 oracle's adjoint and against
 central finite differences on 50 random cells (seed 1).
 
-The PDA threshold follows the packet count as in Sect. 3.1 (30 entries at 1e5 packets, 3000 for the
-long runs): 3000 entries for this 1e7-packet state."""
+Both sides start from one synthetic Monte Carlo state, restored into the disk: no entries in the
+~11,000 cells deeper than 100 optical depths from the nearer pole (the PDA region of a long run on
+this disk has ~12,000), and tallies for a smooth temperature field in the thick cells around them.
+The Rosseland opacity is a seeded field, log-uniform within a factor e^0.5 of 26 cm^2/g (this dust's
+Rosseland mean near 100 K), given to both sides. The PDA threshold is 3000 entries, as for the
+1e7-packet runs (Sect. 3.1)."""
 import numpy as np
 import pytest
 
+import mcstate as S
 from paper_0902_3092_gb300 import disks
 
 pytestmark = pytest.mark.gpu
 MINV = 3000
+N_TOTAL = 10_000_000
 
 
 @pytest.fixture(scope="module")
@@ -19,15 +25,16 @@ def setup(oracle):
     from paper_0902_3092_gb300 import build, mcrt
     build.build()
     d = disks.config_pda_adjoint(400, 200, 1e6)
+    t, v = S.state_for(d, S.wanted_T(d), S.deep_band(d, 100.0), N_TOTAL)
+    kR = 26.0 * np.exp(np.random.default_rng(7).uniform(-0.5, 0.5, d.rho.shape))
     g = mcrt.Disk.from_model(d)
-    g.run_photons(10_000_000, seed=1, mrw=True, gamma=2.0, max_events=10 ** 6, want_sed=False)
-    t, v, a = g.tallies()
+    g.restore(S.blob(d, t, v, N_TOTAL))
     r = oracle.Run(d)
     r.tally[:] = t
-    r.n_total = 10_000_000
+    r.n_total = N_TOTAL
     T_mc, err = r.temperatures()
-    To, mo, uo, info = oracle.solve_pda(d, T_mc, t, v, err, min_visits=MINV)
-    return torch, mcrt, d, g, (To, mo, uo, info)
+    To, mo, uo, info = oracle.solve_pda(d, T_mc, t, v, err, min_visits=MINV, kappa_R=kR)
+    return torch, mcrt, d, g, kR, (To, mo, uo, info)
 
 
 def midplane_weights(d):
@@ -38,22 +45,22 @@ def midplane_weights(d):
 
 
 def test_forward_matches_oracle(setup):
-    torch, mcrt, d, g, (To, mo, uo, info) = setup
+    torch, mcrt, d, g, kR, (To, mo, uo, info) = setup
     from paper_0902_3092_gb300.pda_torch import pda_temperature
-    assert mo.sum() > 100
+    assert mo.sum() > 10_000
     lr = torch.tensor(np.log(np.where(d.rho > 0, d.rho, 1.0)), dtype=torch.float64, device="cuda")
-    kr = torch.tensor(info["kappa_R"], dtype=torch.float64, device="cuda")
+    kr = torch.tensor(kR, dtype=torch.float64, device="cuda")
     T = pda_temperature(g, lr, kr, min_visits=MINV).cpu().numpy()
     assert np.max(np.abs(T[mo] / To[mo] - 1)) < 1e-6
 
 
 def test_gradient_matches_oracle_adjoint(setup, oracle):
-    torch, mcrt, d, g, (To, mo, uo, info) = setup
+    torch, mcrt, d, g, kR, (To, mo, uo, info) = setup
     from paper_0902_3092_gb300.pda_torch import pda_temperature
     w = midplane_weights(d)
     lr = torch.tensor(np.log(np.where(d.rho > 0, d.rho, 1.0)), dtype=torch.float64, device="cuda",
                       requires_grad=True)
-    kr = torch.tensor(info["kappa_R"], dtype=torch.float64, device="cuda", requires_grad=True)
+    kr = torch.tensor(kR, dtype=torch.float64, device="cuda", requires_grad=True)
     J = (pda_temperature(g, lr, kr, min_visits=MINV) * torch.tensor(w, device="cuda")).sum()
     J.backward()
     gl, gk = lr.grad.cpu().numpy(), kr.grad.cpu().numpy()
@@ -64,12 +71,12 @@ def test_gradient_matches_oracle_adjoint(setup, oracle):
 
 
 def test_gradient_against_finite_differences(setup):
-    torch, mcrt, d, g, (To, mo, uo, info) = setup
+    torch, mcrt, d, g, kR, (To, mo, uo, info) = setup
     from paper_0902_3092_gb300.pda_torch import pda_temperature
     w = midplane_weights(d)
     wt = torch.tensor(w, device="cuda")
     lr0 = np.log(np.where(d.rho > 0, d.rho, 1.0))
-    kr0 = info["kappa_R"].copy()
+    kr0 = kR.copy()
 
     def J(lr, kr):
         with torch.no_grad():

@@ -3,6 +3,7 @@ iteration's 3-sigma convergence."""
 import numpy as np
 import pytest
 
+import mcstate as S
 from paper_0902_3092_gb300 import disks
 
 pytestmark = pytest.mark.gpu
@@ -16,16 +17,24 @@ def M():
     return mcrt
 
 
-def test_hydrostatic_density_matches_oracle(M):
+def test_hydrostatic_density_matches_oracle(M, oracle):
+    """The same Monte Carlo state on both sides (tallies for a smooth 40-1300 K field in the dusty cells
+    heavy enough to hold one tally unit, restored into the disk; the others take T_floor) -> the same
+    Eq. 20 density to 1e-9, with the temperatures each side computes from the tallies."""
     from oracle import hydro as H
     d = disks.config_thick_gray(40, 30, 1e4)
+    n_total = 200_000
+    t, v = S.state_for(d, S.wanted_T(d), np.zeros(d.rho.shape, bool), n_total, thick_only=False)
     g = M.Disk.from_model(d)
-    g.run_photons(200_000, seed=4, mrw=True, gamma=2.0, want_sed=False)
-    g.solve_pda()
-    T = g.temperatures(M.T_PDA)[0]
+    g.restore(S.blob(d, t, v, n_total))
+    r = oracle.Run(d)
+    r.tally[:] = t
+    r.n_total = n_total
+    T, _ = r.temperatures()
+    assert (T > 0).sum() > 300
     Ms = 2.5 * H.M_SUN
     shell = H.shell_masses(d.r_faces_cm, d.theta_faces, d.rho)
-    rho_g = g.hydrostatic_density(M_star_g=Ms, mu=2.3, T_floor=10.0)
+    rho_g = g.hydrostatic_density(M_star_g=Ms, mu=2.3, T_floor=10.0, which=M.T_MC)
     rho_o = H.hydrostatic_density(d.r_faces_cm, d.theta_faces, d.rho > 0, T, shell, M_star=Ms, mu=2.3, T_floor=10.0)
     assert np.array_equal(rho_g > 0, rho_o > 0) or np.all(np.abs(rho_g - rho_o) <= 1e-200)
     big = rho_o > 1e-200 * rho_o.max()

@@ -4,6 +4,7 @@ import math
 import numpy as np
 import pytest
 
+import mcstate as S
 from paper_0902_3092_gb300 import disks
 
 pytestmark = pytest.mark.gpu
@@ -94,16 +95,21 @@ def test_fp32_temperatures_within_2_percent(M, oracle, N, min_cells):
 
 
 def test_temperature_inversion_matches_oracle(M, oracle):
-    """Same tallies -> same temperatures (FP64, gray closed form and non-gray bisected Newton)."""
-    for d in (disks.config_plain_gray(12, 12, 50.0), disks.config_nongray(12, 12, 1e3)):
+    """Same tallies -> same temperatures (FP64, gray closed form and non-gray bracketed Newton): seeded
+    tallies for cell temperatures from 3 K to 3000 K, restored into the disk, so the oracle takes
+    nothing from the GPU path."""
+    for d in (disks.config_plain_gray(12, 12, 50.0), disks.config_nongray(12, 12, 1e3),
+              disks.config_nongray(30, 24, 1e5)):
+        t, v = S.random_tallies(d, seed=d.nr, n_total=20000)
         g = M.Disk.from_model(d)
-        g.run_photons(20000, seed=5, precision=32)
+        g.restore(S.blob(d, t, v, 20000))
         T, err, vis = g.temperatures()
-        t, v, a = g.tallies()
+        assert np.array_equal(vis, v.reshape(vis.shape))
         r = oracle.Run(d)
         r.tally[:] = t
         r.n_total = 20000
         To, eo = r.temperatures()
+        assert (To > 0).sum() >= 40 and To[To > 0].max() / To[To > 0].min() > 100
         m = To > 0
         assert np.all((T > 0) == m)
         assert np.max(np.abs(T[m] / To[m] - 1)) < 1e-12

@@ -1,6 +1,6 @@
 """mcrt_pda_solve_static: the PDA solve for callers that may not allocate device memory while running
 (their device memory is owned by a pool or fixed at start-up). It must give the same temperatures as
-mcrt_solve_pda, call after call, from one fixed scratch array.
+mcrt_solve_pda, and the oracle's sparse direct solve, call after call, from one fixed scratch array.
 
 The system (PDA mask, face conductances, boundary values) is assembled here with the CPU reference's
 own assembly routines and handed over in torch device buffers; mcrt_solve_pda assembles the same
@@ -8,49 +8,29 @@ system inside the library from the same Monte Carlo state."""
 import numpy as np
 import pytest
 
+import mcstate as S
 from paper_0902_3092_gb300 import disks
 
 pytestmark = pytest.mark.gpu
-EUNIT = 65536
 
 
-def _state(d, oracle):
+def _state(d):
     """Monte Carlo state (tallies, visit counts) with a PDA band around the midplane."""
-    import math
-    rc, tc = disks.cell_centres(d.r_faces_cm, d.theta_faces)
-    T = 400.0 * (rc[:, None] / disks.AU_CM) ** -0.5 * (1 + 0.3 * np.cos(tc)[None, :] ** 2)
-    band = (d.rho > 0) & (np.abs(tc - math.pi / 2)[None, :] < 0.15) & (np.arange(d.nr)[:, None] > 2)
-    rf, tf = d.r_faces_cm, d.theta_faces
-    V = (2 * math.pi / 3) * (rf[1:] ** 3 - rf[:-1] ** 3)[:, None] * (np.cos(tf[:-1]) - np.cos(tf[1:]))[None, :]
-    q = 4 * d.opacity.kappa_abs[0] * oracle.SIGMA_SB * T ** 4
-    chi_max = float(np.max(d.opacity.kappa_abs + (1 - d.opacity.g) * d.opacity.kappa_sca))
-    thick = d.rho * chi_max * oracle.cell_extent(d) >= 1.0
     n_total = 10 ** 6
-    tally = np.where(thick, np.maximum(np.floor(q * d.rho * V * n_total * EUNIT / d.star.L) + 1, 1000 * EUNIT), 0)
-    tally = np.where(band, 0, tally).astype(np.uint64).ravel()
-    visits = np.where(band, 0, 1000).astype(np.uint64).ravel()
+    tally, visits = S.state_for(d, S.wanted_T(d), S.midplane_band(d), n_total)
     return tally, visits, n_total
-
-
-def _blob(d, tally, visits, n_total):
-    import struct
-    n = d.nr * d.ntheta
-    hdr = struct.pack("<8Q", 0x4D43525443484B31, 1, d.nr, d.ntheta, d.opacity.nlam, n_total,
-                      struct.unpack("<Q", struct.pack("<d", float(n_total)))[0], 0)
-    z = np.zeros(n, np.uint64).tobytes()
-    return hdr + tally.tobytes() + visits.tobytes() + z + np.zeros(d.opacity.nlam * 10, np.uint64).tobytes()
 
 
 def test_static_scratch_solve_matches_solve_pda(oracle):
     torch = pytest.importorskip("torch")
     from paper_0902_3092_gb300 import build, mcrt
     build.build()
-    d = disks.config_plain_gray(24, 20, 1e4)
-    tally, visits, n_total = _state(d, oracle)
+    d = disks.config_plain_gray(24, 20, 1e6)
+    tally, visits, n_total = _state(d)
 
     # existing entry point: the library assembles and solves from the Monte Carlo state
     g = mcrt.Disk.from_model(d)
-    g.restore(_blob(d, tally, visits, n_total))
+    g.restore(S.blob(d, tally, visits, n_total))
     g.solve_pda()
     T_ref, _, _ = g.temperatures(mcrt.T_PDA)
     g.close()
@@ -73,6 +53,8 @@ def test_static_scratch_solve_matches_solve_pda(oracle):
     mask = np.where(pda, 2, np.where(fixed, 1, 0)).astype(np.int8)
     u0 = np.where(fixed, T_mc ** 4, 0.0)
     assert pda.sum() > 20
+    To, mo, _, _ = oracle.solve_pda(d, T_mc, tally, visits, err)
+    assert np.array_equal(mo, pda)
 
     dev = torch.device("cuda:0")
     t_mask = torch.from_numpy(mask.ravel()).to(dev)
@@ -87,6 +69,7 @@ def test_static_scratch_solve_matches_solve_pda(oracle):
         assert it > 0
         T = np.where(pda, np.maximum(u, 0.0) ** 0.25, T_mc)
         assert np.max(np.abs(T[pda] / T_ref[pda] - 1)) < 1e-6, call
+        assert np.max(np.abs(T[pda] / To[pda] - 1)) < 1e-6, call
         assert np.array_equal(u[~pda], u0[~pda])
 
 
