@@ -240,3 +240,33 @@ def batch_sweep(n_models=64, seed=1, max_nr=300, max_ntheta=180):
         disks.append(d)
         packets.append(npk)
     return disks, packets
+
+
+@dataclasses.dataclass
+class Rays:
+    """Sky-plane sampling of an image: points (p, q) in cm along the axes of the projected disk (p along
+    its major axis) and the sky-plane area w (cm^2) each point stands for."""
+    p: np.ndarray
+    q: np.ndarray
+    w: np.ndarray
+
+    @property
+    def n(self) -> int:
+        return int(self.p.size)
+
+
+def polar_rays(r_faces_cm: np.ndarray, n_sub: int = 4, n_phi: int = 64, n_inner: int = 8) -> Rays:
+    """Rings of rays in the sky plane: n_inner rings inside the inner radius and n_sub rings across every
+    radial cell (edges equally spaced between the radial faces), n_phi rays per ring at the mid-radius
+    of the ring and equally spaced azimuths; each ray stands for its share of the ring's area."""
+    rf = np.asarray(r_faces_cm, np.float64)
+    inner = np.linspace(0.0, rf[0], n_inner + 1)
+    cells = (rf[:-1, None] + (rf[1:] - rf[:-1])[:, None] * (np.arange(n_sub) / n_sub)[None, :]).ravel()
+    edges = np.concatenate([inner[:-1], cells, rf[-1:]])
+    b = 0.5 * (edges[:-1] + edges[1:])
+    area = np.pi * (edges[1:] ** 2 - edges[:-1] ** 2) / n_phi
+    phi = (np.arange(n_phi) + 0.5) * (2.0 * np.pi / n_phi)
+    p = (b[:, None] * np.cos(phi)[None, :]).ravel()
+    q = (b[:, None] * np.sin(phi)[None, :]).ravel()
+    w = np.repeat(area, n_phi)
+    return Rays(p, q, w)
