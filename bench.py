@@ -71,6 +71,8 @@ def parse():
                    help="instead of the transport step: the 64-model batched sweep (one graph replay per step)")
     p.add_argument("--pda-adjoint", action="store_true",
                    help="instead of the transport step: PDA solve and adjoint on the 400x200 non-gray disk")
+    p.add_argument("--raytrace", action="store_true",
+                   help="instead of the transport step: ray-traced SED and image of the 200x120 disk at 45 degrees")
     p.add_argument("--pda-min-visits", type=int, default=0,
                    help="PDA visit threshold; 0 scales the paper's 30 entries at 1e5 packets with the packet count "
                         "(Sect. 3.1 uses 30000 for its 1e8-packet runs)")
@@ -337,6 +339,93 @@ def pda_adjoint_timing(args):
     print(json.dumps(line), flush=True)
 
 
+# issue-slot work of the ray-tracing kernel: warp instructions per ray segment through dust (ncu
+# smsp__inst_executed of k_raytrace<float, 4> on the 200x120 disk at 45 degrees / its segments)
+RAY_WARP_INST_PER_SEG = None
+
+
+def raytrace_timing(args):
+    """Ray-traced SED and image (Sect. 2.3, 4.1) of the 200 x 120 rim-refined tau_mid = 1e6 gray disk at 45
+    degrees and 140 pc, after a 1e7-packet MRW run (Monte Carlo temperatures): 104,448 rays (16 rings
+    inside r_in, 4 per radial cell, 128 azimuths) x 100 wavelength bins, FP32. Timed: one mcrt_raytrace
+    call (trace + star + SED) per step with CUDA events on the disk's stream, L2 flushed before each;
+    the source table is built once (the temperatures do not change between views)."""
+    import torch
+    from paper_0902_3092_gb300 import disks, mcrt
+    d = disks.config_thick_gray(200, 120, 1e6)
+    st = torch.cuda.Stream()
+    g = mcrt.Disk.from_model(d, stream=st.cuda_stream)
+    g.run_photons(10_000_000, seed=1, mrw=True, gamma=2.0, max_events=10 ** 6, want_sed=False)
+    rays = disks.polar_rays(d.r_faces_cm, n_sub=4, n_phi=128, n_inner=16)
+    incl, dist = math.pi / 4, 140 * 3.0856775814913673e18
+    g.set_rays(incl, dist, rays)
+    out = g.raytrace()  # source table and buffers
+    flush = torch.empty(256 * 2 ** 20, dtype=torch.uint8, device="cuda")
+    times = []
+    with ClockSampler(physical_gpu(0)) as clk:
+        for k in range(args.warmup + args.steps):
+            with torch.cuda.stream(st):
+                flush.zero_()
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(st)
+                out = g.raytrace()
+                e1.record(st)
+            torch.cuda.synchronize()
+            if k >= args.warmup:
+                times.append(e0.elapsed_time(e1) * 1e-3)
+    t = float(np.mean(times))
+    n_bins = d.opacity.nlam
+    seg = out["segments"]
+    # end to end through the host C ABI: rays from host memory, trace, SED back to the host
+    e2e = []
+    for k in range(3):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        g.set_rays(incl, dist, rays)
+        o2 = g.raytrace()
+        e2e.append(time.perf_counter() - t0)
+    t_e2e = float(np.median(e2e))
+    peaks = measured_peaks()
+    clocks = clk.summary()
+    mhz = clocks["sm_mhz"] or 2070.0
+    issue_peak = 152 * 4 * mhz * 1e6
+    roof = {"bound": "alu", "unit": "warp-inst/s", "kernel": "k_raytrace<float, 4> (+ k_star, k_sed_part, k_sed_final)"}
+    if RAY_WARP_INST_PER_SEG:
+        ach = RAY_WARP_INST_PER_SEG * seg / t
+        roof.update({"achieved": ach, "peak": issue_peak, "frac": ach / issue_peak, "traffic": None,
+                     "note": f"issue-slot roofline: {RAY_WARP_INST_PER_SEG} warp instructions per segment (ncu) x "
+                             f"{seg} segments / CUDA-event call time; peak = 152 SMs x 4 schedulers x SM clock"})
+    else:
+        roof.update({"achieved": None, "peak": issue_peak, "frac": None, "traffic": None})
+    # the oracle on the host cores: rays one by one for about ten seconds
+    cpu = None
+    if not args.no_cpu:
+        from oracle import oracle as O
+        from oracle import raytrace as ORT
+        O.build()
+        T, _, _ = g.temperatures()
+        S = ORT.source(d, T)
+        rng = np.random.default_rng(0)
+        t0, k = time.perf_counter(), 0
+        while time.perf_counter() - t0 < 10.0:
+            j = int(rng.integers(rays.n))
+            ORT.intensity(d, T, incl, rays.p[j], rays.q[j], S)
+            k += 1
+        cpu = {"value": k / (time.perf_counter() - t0), "unit": "rays/s", "cores": 1, "kind": "oracle",
+               "sample": f"{k} random rays of the workload, all {n_bins} bins, FP64 numpy oracle, one core "
+                         "(source table built outside the timing)"}
+    line = {"metric": "ray-traced rays/s (SED + image, all wavelength bins)", "value": rays.n / t, "unit": "rays/s",
+            "higher_is_better": True, "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1e3 * t, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": "200x120 rim-refined gray disk, tau_mid=1e6, 1e7 MRW packets; 45 deg, 140 pc",
+                       "rays": rays.n, "wavelength_bins": n_bins, "segments": seg, "l2": "flushed (256 MB write)"},
+            "e2e": {"value": rays.n / t_e2e, "unit": "rays/s", "h2d_bytes_per_step": 3 * 8 * rays.n,
+                    "d2h_bytes_per_step": 16 * n_bins},
+            "roofline": roof, "cpu_baseline": cpu, "clocks": clocks, "gpu_launches": 4,
+            "flux_total_erg_s_cm2": float(out["F"].sum())}
+    print(json.dumps(line), flush=True)
+
+
 def main():
     args = parse()
     if args.impl == "reference":
@@ -350,6 +439,9 @@ def main():
         return
     if args.batch_sweep:
         batch_sweep_timing(args)
+        return
+    if args.raytrace:
+        raytrace_timing(args)
         return
     import torch
     import torch.distributed as dist

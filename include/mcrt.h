@@ -229,6 +229,42 @@ mcrt_status mcrt_hydrostatic_density(mcrt_disk *d, const mcrt_hydro_opts *opts, 
  * the grid, star and opacities stay. Device buffers keep their addresses. */
 mcrt_status mcrt_set_density(mcrt_disk *d, const double *rho);
 
+/* ---- Ray-traced observables (Sect. 2.3: the observables come from integrating the computed source
+ * function along rays, free of Monte Carlo noise; Sect. 4.1: SED from 0.1 um to 1 cm at 45 degrees,
+ * N-band visibilities at a 100 m baseline). Readings: the source function of a cell in bin b is
+ * kappa_b Bbar_b(T) / (kappa_b + sigma_b) with the cell's Monte Carlo temperature (the PDA temperatures
+ * on request); scattering dims a ray and adds nothing to it; the star is a point source at the origin,
+ * dimmed along the radial line towards the observer, and occults no ray.
+ * Observer: direction o = (sin i, 0, cos i) for inclination i from the disk axis; sky-plane axes
+ * e1 = (0, 1, 0) (the projected major axis) and e2 = (-cos i, 0, sin i); a ray through sky point (p, q)
+ * is X(s) = p e1 + q e2 + s o. At most 256 wavelength bins. */
+
+/* Sets the rays of the observables: n sky points (p_cm, q_cm) and the sky-plane area w_cm2 (>= 0) each
+ * stands for, host arrays copied to the device and kept until the next call; incl in [0, pi],
+ * dist_cm > 0. MCRT_EINVAL for bad sizes or values (n in 1 .. 2^27), MCRT_ESTATE before
+ * mcrt_set_opacity. */
+mcrt_status mcrt_set_rays(mcrt_disk *d, double incl_rad, double dist_cm, int64_t n, const double *p_cm,
+                          const double *q_cm, const double *w_cm2);
+
+/* Traces the rays through the disk with the temperatures `which` (MCRT_T_MC, computed first if
+ * needed, or MCRT_T_PDA after a PDA solve) in FP32 (precision 0 or 32) or FP64 (64). Outputs, each
+ * optional (NULL): F_out[nlam] the flux per wavelength bin at the observer, sum_k w_k I_kb / d^2 plus
+ * the star (erg s^-1 cm^-2, integrated over the bin); F_star_out[nlam] the star's part;
+ * I_out[n * nlam] the intensity of every ray per bin (erg s^-1 cm^-2 sr^-1, ray-major);
+ * n_segments the number of ray segments through dusty cells. The image stays on the device for
+ * mcrt_visibilities. MCRT_ESTATE without rays (or PDA temperatures), MCRT_ETIMEOUT if a ray crossed
+ * more than 4 (nr + ntheta) + 64 faces. Synchronous. */
+mcrt_status mcrt_raytrace(mcrt_disk *d, int which, int precision, double *F_out, double *F_star_out,
+                          double *I_out, uint64_t *n_segments);
+
+/* Visibility amplitudes of the last traced image: for each j, bin bins[j], baseline baseline_cm[j] >= 0
+ * at position angle pa_rad[j] (from e1 towards e2), spatial frequency B (cos PA, sin PA) / lambda_b with
+ * lambda_b = sqrt(lambda_lo lambda_hi) of the bin; |V| = |sum_k w_k I_k exp(-2 pi i (u p_k + v q_k) / d)
+ * / d^2 + F*| / (sum_k w_k I_k / d^2 + F*), F* the dimmed star when with_star is nonzero, else 0.
+ * vis_out: n_vis host values. MCRT_ESTATE before mcrt_raytrace. */
+mcrt_status mcrt_visibilities(mcrt_disk *d, int n_vis, const int *bins, const double *baseline_cm,
+                              const double *pa_rad, int with_star, double *vis_out);
+
 /* FP64 debug transport that records every event of the first n_packets packets: type (0 launch,
  * 1 cell entry, 2 scatter, 3 absorption, 4 MRW jump, 5 escape, 6 capped), cell (-1 outside the grid),
  * wavelength bin and position (cm, [packet][event][3]). Buffers hold n_packets * max_events entries;

@@ -1,8 +1,9 @@
 """Builds libmcrt.so (the C ABI of include/mcrt.h) in-tree with nvcc for sm_103a.
 
-Five translation units compile in parallel; the FP64 debug transport unit and the FP64 hydrostatic
+Six translation units compile in parallel; the FP64 debug transport unit and the FP64 hydrostatic
 unit are compiled without FMA contraction so that their arithmetic follows the CPU reference operation
-by operation, the FP32 production transport unit with approximate division and square root."""
+by operation, the FP32 production transport unit and the ray-tracing unit (which marches rays with the
+transport's geometry) with approximate division and square root."""
 from __future__ import annotations
 
 import concurrent.futures as cf
@@ -21,7 +22,8 @@ COMMON = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-I", INCLUDE
 # The FP32 transport unit uses the approximate (2 ulp) division and square root: its geometry is
 # written without cancellation, so a few ulps do not change which face a ray meets.
 UNITS = [("api.cu", []), ("pda.cu", []), ("transport_f32.cu", ["-prec-div=false", "-prec-sqrt=false"]),
-         ("transport_f64.cu", ["-fmad=false"]), ("hydro.cu", ["-fmad=false"])]
+         ("transport_f64.cu", ["-fmad=false"]), ("hydro.cu", ["-fmad=false"]),
+         ("raytrace.cu", ["-prec-div=false", "-prec-sqrt=false"])]
 
 
 def nvcc() -> str:

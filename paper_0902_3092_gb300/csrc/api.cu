@@ -208,6 +208,7 @@ mcrt_status compute_temperatures(mcrt_disk* d) {
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return cuda_fail(d, e, "temperature kernel");
   d->have_T = true;
+  d->T_epoch++;
   return MCRT_OK;
 }
 
@@ -1116,6 +1117,8 @@ void mcrt_disk_destroy(mcrt_disk* d) {
   if (d->stream) cudaStreamSynchronize(d->stream);
   if (d->pda) pda_free(d->pda);
   d->pda = nullptr;
+  if (d->rays) ray_free(d->rays);
+  d->rays = nullptr;
   cudaStream_t st = d->own_stream ? d->stream : nullptr;
   delete d;  // frees the device buffers
   if (st) cudaStreamDestroy(st);

@@ -37,6 +37,7 @@ struct DBuf {
 };
 
 struct PdaState;  // pda.cu
+struct RayState;  // raytrace.cu
 
 template <class R>
 cudaError_t launch_transport(const KParams<R>& P, bool trace, bool batch, bool gray, int grid, int block,
@@ -87,6 +88,8 @@ struct mcrt_disk {
   bool tally_wrapped = false;
   float chiR0 = 0, kbar0 = 0;
   mcrt::PdaState* pda = nullptr;
+  mcrt::RayState* rays = nullptr;   // rays, source table and image of the ray-traced observables
+  unsigned long long T_epoch = 0;   // advances whenever T_mc or T_pda is recomputed
   unsigned long long launches = 0;  // kernels launched by this disk
   std::string err;
   mcrt::DevModel<float> model32() const;
@@ -103,4 +106,5 @@ mcrt_status upload_density(mcrt_disk* d);
 // adds a run's deposit sum (counters c) to the disk's held energy; false if a tally may have wrapped
 bool account_deposits(mcrt_disk* d, const unsigned long long* c);
 void pda_free(PdaState* p);
+void ray_free(RayState* r);
 }  // namespace mcrt

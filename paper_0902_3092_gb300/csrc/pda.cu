@@ -977,6 +977,7 @@ mcrt_status mcrt_solve_pda(mcrt_disk* d, const mcrt_pda_opts* o, int* out_n, int
   CK(cudaGetLastError(), "PDA kernels");
   CK(cudaStreamSynchronize(st), "synchronize");
   d->have_pda = true;
+  d->T_epoch++;
   return MCRT_OK;
 }
 

@@ -1,0 +1,501 @@
+// raytrace.cu -- ray-traced observables: images, the SED and interferometric visibilities, by integrating
+// the source function along straight rays through the (r, theta) grid with the Monte Carlo temperatures
+// (Sect. 2.3: observables from the computed source function, free of Monte Carlo noise; Sect. 4.1: SED at
+// 45 degrees, N-band visibilities at a 100 m baseline).
+//
+// Readings: the source function of a cell in bin b is S_b = kappa_b Bbar_b(T) / chi_b with chi = kappa +
+// sigma (thermal emission over the total extinction; scattering takes light out of a ray and adds none);
+// S and the extinction are constant in a cell, so a segment of optical depth dtau updates the intensity
+// carried towards the observer exactly: I <- S + (I - S) exp(-dtau). The star is a point source at the
+// origin, dimmed along the radial line towards the observer, and occults no ray.
+//
+// Layout: one warp per ray, the 32 lanes over the wavelength bins (nlam <= 256: up to 8 bins per lane,
+// intensities in registers); every lane marches the same cells, so the march costs one warp instruction
+// stream per ray and the per-bin work runs on all lanes. The source table S[cell][bin] is read one row
+// (nlam contiguous values) per segment.
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstring>
+
+#include "internal.h"
+#include "planck.cuh"
+
+namespace mcrt {
+
+struct RayState {
+  DBuf p, q, w;   // rays: sky-plane coordinates (cm) and areas (cm^2), FP64
+  long long n = 0;
+  double incl = 0, dist = 0;
+  DBuf S;         // cells x nlam source table of the last trace (float or double)
+  int S_prec = 0, S_which = -1;
+  unsigned long long S_epoch = ~0ull;
+  DBuf img;       // n x nlam image of the last trace
+  int img_prec = 0;
+  bool have_img = false;
+  DBuf part, F, Fs, cnt;  // SED partial sums, disk + star flux, star flux, counters
+  DBuf vis_par;           // per visibility: bin, fu, fv
+  DBuf vis_out;
+};
+
+void ray_free(RayState* r) { delete r; }
+
+namespace {
+
+constexpr int kRayBlock = 256;
+constexpr int kSedBlock = 128;
+
+// S[c][b] = kappa_b Bbar_b(T_c) / chi_b, FP64 bin integrals; one warp per cell, lanes over bins.
+template <class R>
+__global__ void k_source(int nc, int nlam, const double* __restrict__ T, const double* __restrict__ lam_e,
+                         const double* __restrict__ kabs, const double* __restrict__ chi, R* __restrict__ S) {
+  const int lane = threadIdx.x & 31;
+  const int nw = (gridDim.x * blockDim.x) >> 5;
+  const double k4 = kKB * kKB * kKB * kKB;
+  for (int c = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; c < nc; c += nw) {
+    const double t = T[c];
+    const double pref3 = 2.0 * k4 * t * t * t * t / (kH * kH * kH * kC * kC);
+    for (int b = lane; b < nlam; b += 32) {
+      double v = 0.0;
+      if (t > 0.0) {
+        // bin b spans lam_e[b] .. lam_e[b+1]; G3 at the short edge is 0 for the first bin (lambda -> 0),
+        // at the long edge G3(0) for the last one (lambda -> infinity)
+        double g_short = 0.0, g_long, g4;
+        if (b > 0) tails(kH * kC / (lam_e[b] * 1e-4 * kKB * t), g_short, g4);
+        if (b + 1 == nlam) tails(0.0, g_long, g4);
+        else tails(kH * kC / (lam_e[b + 1] * 1e-4 * kKB * t), g_long, g4);
+        v = pref3 * (g_long - g_short) * kabs[b] / chi[b];
+      }
+      S[(size_t)c * nlam + b] = (R)v;
+    }
+  }
+}
+
+template <class R>
+__device__ __forceinline__ R exp_neg(R x);
+template <>
+__device__ __forceinline__ float exp_neg<float>(float x) { return __expf(-x); }
+template <>
+__device__ __forceinline__ double exp_neg<double>(double x) { return exp(-x); }
+
+// One warp per ray (grid-stride over rays). Rays enter at the outer sphere on the far side and run
+// towards the observer along o = (sin i, 0, cos i); the cell march is the transport's (next_face), with
+// the cavity inside r_in crossed in one step. cnt[0] += segments with dust, cnt[1] |= 1 when a ray
+// crossed more faces than the bound.
+template <class R, int NPL>
+__global__ void __launch_bounds__(kRayBlock) k_raytrace(const DevModel<R> M, const R* __restrict__ chi,
+                                                        const R* __restrict__ S, long long n,
+                                                        const double* __restrict__ p, const double* __restrict__ q,
+                                                        double inv_l, R ox, R oz, R e2x, R e2z, int max_cross,
+                                                        R* __restrict__ img, unsigned long long* __restrict__ cnt) {
+  const int lane = threadIdx.x & 31;
+  const long long nw = ((long long)gridDim.x * blockDim.x) >> 5;
+  const int nlam = M.nlam, nt = M.nt, nr = M.nr;
+  R ch[NPL];
+#pragma unroll
+  for (int k = 0; k < NPL; ++k) {
+    const int b = lane + 32 * k;
+    ch[k] = b < nlam ? chi[b] : (R)0;
+  }
+  unsigned long long segs = 0;
+  bool err = false;
+  const R rout2 = M.rf2[nr];
+  for (long long ray = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5; ray < n; ray += nw) {
+    R I[NPL];
+#pragma unroll
+    for (int k = 0; k < NPL; ++k) I[k] = (R)0;
+    const R pp = (R)(p[ray] * inv_l), qq = (R)(q[ray] * inv_l);
+    const R b2 = pp * pp + qq * qq;
+    if (b2 < rout2) {
+      const R s0 = -sqrt(rout2 - b2);
+      R px = qq * e2x + s0 * ox, py = pp, pz = qq * e2z + s0 * oz;
+      const R ux = ox, uy = (R)0, uz = oz;
+      int ir = nr - 1, it = theta_cell(M, px, py, pz);
+      for (int nc = 0;; ++nc) {
+        if (nc > max_cross) {
+          err = true;
+          break;
+        }
+        if (ir < 0) {  // inner cavity: straight to the far side of r_in
+          const R bb = px * ux + py * uy + pz * uz;
+          const R r2 = px * px + py * py + pz * pz;
+          const R sf = sphere_far(bb, r2 - M.rf2[0]);
+          px += sf * ux;
+          py += sf * uy;
+          pz += sf * uz;
+          ir = 0;
+          it = theta_cell(M, px, py, pz);
+          continue;
+        }
+        int face;
+        const R L = next_face(M, ir, it, px, py, pz, ux, uy, uz, face);
+        const int c = ir * nt + it;
+        const R a = M.rho[c] * L;  // optical depth per unit chi (rho is stored per internal length)
+        if (a > (R)0) {
+          const R* Sc = S + (size_t)c * nlam;
+#pragma unroll
+          for (int k = 0; k < NPL; ++k) {
+            const int b = lane + 32 * k;
+            if (b < nlam) {
+              const R s = Sc[b];
+              I[k] = s + (I[k] - s) * exp_neg<R>(a * ch[k]);
+            }
+          }
+          ++segs;
+        }
+        px += L * ux;
+        py += L * uy;
+        pz += L * uz;
+        if (face == 1) ++ir;
+        else if (face == 0) --ir;
+        else if (face == 2) --it;
+        else ++it;
+        if (ir >= nr) break;
+      }
+    }
+    R* o = img + (size_t)ray * nlam;
+#pragma unroll
+    for (int k = 0; k < NPL; ++k) {
+      const int b = lane + 32 * k;
+      if (b < nlam) o[b] = I[k];
+    }
+  }
+  if (lane == 0) {
+    if (segs) atomicAdd(cnt, segs);
+    if (err) atomicOr(cnt + 1, 1ull);
+  }
+}
+
+// Flux of the star per bin at distance d: pi R*^2 Bbar_b(T*) / d^2, dimmed by chi_b times the column
+// sum rho dr of polar row `it` (the row that holds the line of sight).
+__global__ void k_star(int nr, int nt, int it, int nlam, const double* __restrict__ rho_l,
+                       const double* __restrict__ rf_l, const double* __restrict__ lam_e,
+                       const double* __restrict__ chi, double Tstar, double Rstar, double dist,
+                       double* __restrict__ Fs) {
+  const int b = blockIdx.x * blockDim.x + threadIdx.x;
+  if (b >= nlam) return;
+  double col = 0.0;
+  for (int ir = 0; ir < nr; ++ir) col += rho_l[ir * nt + it] * (rf_l[ir + 1] - rf_l[ir]);
+  const double k4 = kKB * kKB * kKB * kKB;
+  const double pref3 = 2.0 * k4 * Tstar * Tstar * Tstar * Tstar / (kH * kH * kH * kC * kC);
+  double g_short = 0.0, g_long, g4;
+  if (b > 0) tails(kH * kC / (lam_e[b] * 1e-4 * kKB * Tstar), g_short, g4);
+  if (b + 1 == nlam) tails(0.0, g_long, g4);
+  else tails(kH * kC / (lam_e[b + 1] * 1e-4 * kKB * Tstar), g_long, g4);
+  const double B = pref3 * (g_long - g_short);
+  Fs[b] = 3.14159265358979323846 * Rstar * Rstar * B / (dist * dist) * exp(-col * chi[b]);
+}
+
+// Weighted image sums per bin over a contiguous range of rays (one block per range, threads over bins,
+// so each ray's row is read contiguously).
+template <class R>
+__global__ void k_sed_part(long long n, int nlam, long long per_blk, const R* __restrict__ img,
+                           const double* __restrict__ w, double* __restrict__ part) {
+  const long long r0 = (long long)blockIdx.x * per_blk;
+  const long long r1 = r0 + per_blk < n ? r0 + per_blk : n;
+  for (int b = threadIdx.x; b < nlam; b += blockDim.x) {
+    double s = 0.0;
+    for (long long r = r0; r < r1; ++r) s += w[r] * (double)img[r * nlam + b];
+    part[(size_t)blockIdx.x * nlam + b] = s;
+  }
+}
+
+// F_b = sum of the partial sums (fixed order) / d^2 + star.
+__global__ void k_sed_final(int nblk, int nlam, const double* __restrict__ part, double inv_d2,
+                            const double* __restrict__ Fs, double* __restrict__ F) {
+  const int b = blockIdx.x * blockDim.x + threadIdx.x;
+  if (b >= nlam) return;
+  double s = 0.0;
+  for (int j = 0; j < nblk; ++j) s += part[(size_t)j * nlam + b];
+  F[b] = s * inv_d2 + Fs[b];
+}
+
+// One block per visibility: sums over the rays of w I exp(-2 pi i t), t = fu p + fv q in turns (fu, fv:
+// spatial frequency over distance, cycles per cm at the source), reduced to its fractional part in FP64
+// before the sine and cosine.
+template <class R>
+__global__ void k_vis(long long n, int nlam, const R* __restrict__ img, const double* __restrict__ p,
+                      const double* __restrict__ q, const double* __restrict__ w, const double* __restrict__ par,
+                      const double* __restrict__ Fs, int with_star, double inv_d2, double* __restrict__ out) {
+  const int j = blockIdx.x;
+  const int b = (int)par[3 * j];
+  const double fu = par[3 * j + 1], fv = par[3 * j + 2];
+  double re = 0.0, im = 0.0, tot = 0.0;
+  for (long long r = threadIdx.x; r < n; r += blockDim.x) {
+    const double f = w[r] * (double)img[r * nlam + b];
+    double t = fu * p[r] + fv * q[r];
+    t -= rint(t);
+    double sn, cs;
+    if (sizeof(R) == 8) {
+      sincospi(2.0 * t, &sn, &cs);
+    } else {
+      float s32, c32;
+      sincospif(2.0f * (float)t, &s32, &c32);
+      sn = s32;
+      cs = c32;
+    }
+    re += f * cs;
+    im -= f * sn;
+    tot += f;
+  }
+  __shared__ double sh[3][32];
+  for (int o = 16; o > 0; o >>= 1) {
+    re += __shfl_down_sync(0xffffffffu, re, o);
+    im += __shfl_down_sync(0xffffffffu, im, o);
+    tot += __shfl_down_sync(0xffffffffu, tot, o);
+  }
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  if (lane == 0) {
+    sh[0][wid] = re;
+    sh[1][wid] = im;
+    sh[2][wid] = tot;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double a = 0.0, c = 0.0, t = 0.0;
+    for (int k = 0; k < (int)(blockDim.x >> 5); ++k) {
+      a += sh[0][k];
+      c += sh[1][k];
+      t += sh[2][k];
+    }
+    const double fs = with_star ? Fs[b] : 0.0;
+    a = a * inv_d2 + fs;
+    c = c * inv_d2;
+    t = t * inv_d2 + fs;
+    out[j] = t > 0.0 ? sqrt(a * a + c * c) / t : 0.0;
+  }
+}
+
+int sm_count(int device) {
+  int v = 0;
+  cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, device);
+  return v > 0 ? v : 1;
+}
+
+template <class R>
+cudaError_t launch_trace(mcrt_disk* d, RayState* rs, const DevModel<R>& M, const R* chi, int grid) {
+  const double si = std::sin(rs->incl), ci = std::cos(rs->incl);
+  const int max_cross = 4 * (d->nr + d->nt) + 64;
+  const R ox = (R)si, oz = (R)ci, e2x = (R)(-ci), e2z = (R)si;
+  const double inv_l = 1.0 / d->l_unit;
+  const R* S = rs->S.as<R>();
+  R* img = rs->img.as<R>();
+  auto* cnt = rs->cnt.as<unsigned long long>();
+  const double* p = rs->p.as<double>();
+  const double* q = rs->q.as<double>();
+  const int npl = (d->nlam + 31) / 32;
+#define MCRT_TRACE_CASE(K)                                                                                 \
+  case K:                                                                                                  \
+    k_raytrace<R, K><<<grid, kRayBlock, 0, d->stream>>>(M, chi, S, rs->n, p, q, inv_l, ox, oz, e2x, e2z,    \
+                                                        max_cross, img, cnt);                              \
+    break;
+  switch (npl) {
+    MCRT_TRACE_CASE(1)
+    MCRT_TRACE_CASE(2)
+    MCRT_TRACE_CASE(3)
+    MCRT_TRACE_CASE(4)
+    MCRT_TRACE_CASE(5)
+    MCRT_TRACE_CASE(6)
+    MCRT_TRACE_CASE(7)
+    MCRT_TRACE_CASE(8)
+    default:
+      return cudaErrorInvalidValue;
+  }
+#undef MCRT_TRACE_CASE
+  return cudaGetLastError();
+}
+
+template <class R>
+int trace_blocks_per_sm() {
+  int v = 0;
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&v, k_raytrace<R, 4>, kRayBlock, 0);
+  return v > 0 ? v : 1;
+}
+
+}  // namespace
+}  // namespace mcrt
+
+using namespace mcrt;
+
+#define CK(call, what)                                    \
+  do {                                                    \
+    cudaError_t e_ = (call);                              \
+    if (e_ != cudaSuccess) return cuda_fail(d, e_, what); \
+  } while (0)
+
+namespace {
+
+template <class R>
+DevModel<R> model_of(const mcrt_disk* d);
+template <>
+DevModel<float> model_of<float>(const mcrt_disk* d) { return d->model32(); }
+template <>
+DevModel<double> model_of<double>(const mcrt_disk* d) { return d->model64(); }
+template <class R>
+const R* chi_of(const mcrt_disk* d) { return static_cast<const R*>(sizeof(R) == 8 ? d->chi64.p : d->chi32.p); }
+
+template <class R>
+mcrt_status trace_impl(mcrt_disk* d, int which) {
+  RayState* rs = d->rays;
+  const size_t nc = (size_t)d->nr * d->nt;
+  const int nlam = d->nlam;
+  const double* T = which == MCRT_T_PDA ? d->T_pda.as<double>() : d->T_mc.as<double>();
+  const int prec = sizeof(R) == 8 ? 64 : 32;
+  if (rs->S_epoch != d->T_epoch || rs->S_which != which || rs->S_prec != prec || !rs->S.p) {
+    if (rs->S.n < nc * nlam * sizeof(R)) CK(rs->S.alloc(nc * nlam * sizeof(R)), "cudaMalloc");
+    const int blocks = (int)((nc * 32 + 255) / 256);
+    k_source<R><<<blocks, 256, 0, d->stream>>>((int)nc, nlam, T, d->lam_e_d.as<double>(), d->kabs_d.as<double>(),
+                                               d->chi64.as<double>(), rs->S.as<R>());
+    d->launches++;
+    CK(cudaGetLastError(), "source kernel");
+    rs->S_epoch = d->T_epoch;
+    rs->S_which = which;
+    rs->S_prec = prec;
+  }
+  const size_t img_bytes = (size_t)rs->n * nlam * sizeof(R);
+  if (rs->img.n < img_bytes) CK(rs->img.alloc(img_bytes), "cudaMalloc");
+  CK(cudaMemsetAsync(rs->cnt.p, 0, 2 * sizeof(unsigned long long), d->stream), "memset");
+  const int sms = sm_count(d->device);
+  const long long warps_needed = rs->n;
+  long long grid = (long long)sms * trace_blocks_per_sm<R>();
+  const long long need = (warps_needed * 32 + kRayBlock - 1) / kRayBlock;
+  if (grid > need) grid = need;
+  if (grid < 1) grid = 1;
+  CK(launch_trace<R>(d, rs, model_of<R>(d), chi_of<R>(d), (int)grid), "ray-trace kernel");
+  d->launches++;
+  rs->img_prec = prec;
+  rs->have_img = true;
+  // star, then the SED from the image
+  int it = 0;
+  while (it + 1 < d->nt && d->tf[it + 1] <= rs->incl) ++it;
+  k_star<<<(nlam + 127) / 128, 128, 0, d->stream>>>(d->nr, d->nt, it, nlam, d->rho64.as<double>(), d->rf64.as<double>(),
+                                                    d->lam_e_d.as<double>(), d->chi64.as<double>(), d->Tstar, d->Rstar,
+                                                    rs->dist, rs->Fs.as<double>());
+  d->launches++;
+  const int nblk = (int)std::min<long long>(rs->n, (long long)sms * 4);
+  const long long per_blk = (rs->n + nblk - 1) / nblk;
+  if (rs->part.n < (size_t)nblk * nlam * 8) CK(rs->part.alloc((size_t)nblk * nlam * 8), "cudaMalloc");
+  k_sed_part<R><<<nblk, kSedBlock, 0, d->stream>>>(rs->n, nlam, per_blk, rs->img.as<R>(), rs->w.as<double>(),
+                                                  rs->part.as<double>());
+  k_sed_final<<<(nlam + 127) / 128, 128, 0, d->stream>>>(nblk, nlam, rs->part.as<double>(), 1.0 / (rs->dist * rs->dist),
+                                                         rs->Fs.as<double>(), rs->F.as<double>());
+  d->launches += 2;
+  CK(cudaGetLastError(), "SED kernels");
+  return MCRT_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+mcrt_status mcrt_set_rays(mcrt_disk* d, double incl_rad, double dist_cm, int64_t n, const double* p_cm,
+                          const double* q_cm, const double* w_cm2) {
+  if (!d) return set_error(nullptr, MCRT_EINVAL, "disk is NULL");
+  if (!d->has_opacity) return set_error(d, MCRT_ESTATE, "mcrt_set_opacity must come first");
+  if (!(incl_rad >= 0.0 && incl_rad <= 3.14159265358979323846))
+    return set_error(d, MCRT_EINVAL, "inclination must lie in [0, pi]");
+  if (!(dist_cm > 0.0) || !std::isfinite(dist_cm)) return set_error(d, MCRT_EINVAL, "distance must be > 0");
+  if (n < 1 || n > (int64_t)1 << 27) return set_error(d, MCRT_EINVAL, "rays: 1 .. 2^27");
+  if (!p_cm || !q_cm || !w_cm2) return set_error(d, MCRT_EINVAL, "p, q, w must not be NULL");
+  if (d->nlam > 256) return set_error(d, MCRT_EINVAL, "ray tracing takes at most 256 wavelength bins");
+  for (int64_t k = 0; k < n; ++k)
+    if (!std::isfinite(p_cm[k]) || !std::isfinite(q_cm[k]) || !(w_cm2[k] >= 0.0) || !std::isfinite(w_cm2[k]))
+      return set_error(d, MCRT_EINVAL, "rays: p, q finite and w >= 0");
+  CK(cudaSetDevice(d->device), "cudaSetDevice");
+  if (!d->rays) d->rays = new RayState();
+  RayState* rs = d->rays;
+  const size_t bytes = (size_t)n * 8;
+  if (rs->p.n < bytes) CK(rs->p.alloc(bytes), "cudaMalloc");
+  if (rs->q.n < bytes) CK(rs->q.alloc(bytes), "cudaMalloc");
+  if (rs->w.n < bytes) CK(rs->w.alloc(bytes), "cudaMalloc");
+  if (!rs->F.p) CK(rs->F.alloc(256 * 8), "cudaMalloc");
+  if (!rs->Fs.p) CK(rs->Fs.alloc(256 * 8), "cudaMalloc");
+  if (!rs->cnt.p) CK(rs->cnt.alloc(2 * 8), "cudaMalloc");
+  CK(cudaMemcpyAsync(rs->p.p, p_cm, bytes, cudaMemcpyHostToDevice, d->stream), "copy");
+  CK(cudaMemcpyAsync(rs->q.p, q_cm, bytes, cudaMemcpyHostToDevice, d->stream), "copy");
+  CK(cudaMemcpyAsync(rs->w.p, w_cm2, bytes, cudaMemcpyHostToDevice, d->stream), "copy");
+  CK(cudaStreamSynchronize(d->stream), "synchronize");
+  rs->n = n;
+  rs->incl = incl_rad;
+  rs->dist = dist_cm;
+  rs->have_img = false;
+  return MCRT_OK;
+}
+
+mcrt_status mcrt_raytrace(mcrt_disk* d, int which, int precision, double* F_out, double* F_star_out, double* I_out,
+                          uint64_t* n_segments) {
+  if (!d) return set_error(nullptr, MCRT_EINVAL, "disk is NULL");
+  if (!d->rays || d->rays->n < 1) return set_error(d, MCRT_ESTATE, "mcrt_set_rays must come first");
+  if (which != MCRT_T_MC && which != MCRT_T_PDA) return set_error(d, MCRT_EINVAL, "which");
+  if (precision != 0 && precision != 32 && precision != 64) return set_error(d, MCRT_EINVAL, "precision: 32 or 64");
+  if (which == MCRT_T_PDA && !d->have_pda) return set_error(d, MCRT_ESTATE, "no PDA solution");
+  if (d->nlam > 256) return set_error(d, MCRT_EINVAL, "ray tracing takes at most 256 wavelength bins");
+  CK(cudaSetDevice(d->device), "cudaSetDevice");
+  if (!d->have_T) {
+    mcrt_status s = compute_temperatures(d);
+    if (s != MCRT_OK) return s;
+  }
+  RayState* rs = d->rays;
+  mcrt_status s = precision == 64 ? trace_impl<double>(d, which) : trace_impl<float>(d, which);
+  if (s != MCRT_OK) return s;
+  unsigned long long c[2];
+  CK(cudaMemcpyAsync(c, rs->cnt.p, sizeof(c), cudaMemcpyDeviceToHost, d->stream), "copy");
+  if (F_out) CK(cudaMemcpyAsync(F_out, rs->F.p, (size_t)d->nlam * 8, cudaMemcpyDeviceToHost, d->stream), "copy");
+  if (F_star_out)
+    CK(cudaMemcpyAsync(F_star_out, rs->Fs.p, (size_t)d->nlam * 8, cudaMemcpyDeviceToHost, d->stream), "copy");
+  CK(cudaStreamSynchronize(d->stream), "synchronize");
+  if (I_out) {
+    const size_t m = (size_t)rs->n * d->nlam;
+    if (rs->img_prec == 64) {
+      CK(cudaMemcpy(I_out, rs->img.p, m * 8, cudaMemcpyDeviceToHost), "copy");
+    } else {
+      std::vector<float> tmp(m);
+      CK(cudaMemcpy(tmp.data(), rs->img.p, m * 4, cudaMemcpyDeviceToHost), "copy");
+      for (size_t k = 0; k < m; ++k) I_out[k] = tmp[k];
+    }
+  }
+  if (n_segments) *n_segments = c[0];
+  if (c[1]) return set_error(d, MCRT_ETIMEOUT, "a ray crossed more cell faces than 4 (nr + ntheta) + 64");
+  return MCRT_OK;
+}
+
+mcrt_status mcrt_visibilities(mcrt_disk* d, int n_vis, const int* bins, const double* baseline_cm,
+                              const double* pa_rad, int with_star, double* vis_out) {
+  if (!d) return set_error(nullptr, MCRT_EINVAL, "disk is NULL");
+  if (!d->rays || !d->rays->have_img) return set_error(d, MCRT_ESTATE, "mcrt_raytrace must come first");
+  if (n_vis < 1 || n_vis > (1 << 20) || !bins || !baseline_cm || !pa_rad || !vis_out)
+    return set_error(d, MCRT_EINVAL, "bad arguments");
+  RayState* rs = d->rays;
+  std::vector<double> par((size_t)3 * n_vis);
+  for (int j = 0; j < n_vis; ++j) {
+    if (bins[j] < 0 || bins[j] >= d->nlam) return set_error(d, MCRT_EINVAL, "bin out of range");
+    if (!(baseline_cm[j] >= 0.0) || !std::isfinite(baseline_cm[j]) || !std::isfinite(pa_rad[j]))
+      return set_error(d, MCRT_EINVAL, "baselines: finite, >= 0");
+    // bin centre lambda = sqrt(lambda_lo lambda_hi); frequency over distance in cycles per cm at the source
+    const double lam_cm = std::sqrt(d->lam_e[bins[j]] * d->lam_e[bins[j] + 1]) * 1e-4;
+    const double f = baseline_cm[j] / (lam_cm * rs->dist);
+    par[3 * j] = bins[j];
+    par[3 * j + 1] = f * std::cos(pa_rad[j]);
+    par[3 * j + 2] = f * std::sin(pa_rad[j]);
+  }
+  CK(cudaSetDevice(d->device), "cudaSetDevice");
+  if (rs->vis_par.n < par.size() * 8) CK(rs->vis_par.alloc(par.size() * 8), "cudaMalloc");
+  if (rs->vis_out.n < (size_t)n_vis * 8) CK(rs->vis_out.alloc((size_t)n_vis * 8), "cudaMalloc");
+  CK(cudaMemcpyAsync(rs->vis_par.p, par.data(), par.size() * 8, cudaMemcpyHostToDevice, d->stream), "copy");
+  const double inv_d2 = 1.0 / (rs->dist * rs->dist);
+  if (rs->img_prec == 64)
+    k_vis<double><<<n_vis, 256, 0, d->stream>>>(rs->n, d->nlam, rs->img.as<double>(), rs->p.as<double>(),
+                                                rs->q.as<double>(), rs->w.as<double>(), rs->vis_par.as<double>(),
+                                                rs->Fs.as<double>(), with_star, inv_d2, rs->vis_out.as<double>());
+  else
+    k_vis<float><<<n_vis, 256, 0, d->stream>>>(rs->n, d->nlam, rs->img.as<float>(), rs->p.as<double>(),
+                                               rs->q.as<double>(), rs->w.as<double>(), rs->vis_par.as<double>(),
+                                               rs->Fs.as<double>(), with_star, inv_d2, rs->vis_out.as<double>());
+  d->launches++;
+  CK(cudaGetLastError(), "visibility kernel");
+  CK(cudaMemcpyAsync(vis_out, rs->vis_out.p, (size_t)n_vis * 8, cudaMemcpyDeviceToHost, d->stream), "copy");
+  CK(cudaStreamSynchronize(d->stream), "synchronize");
+  return MCRT_OK;
+}
+
+}  // extern "C"

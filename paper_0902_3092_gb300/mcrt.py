@@ -24,7 +24,8 @@ EXPORTS = ["mcrt_disk_create", "mcrt_set_opacity", "mcrt_default_run_opts", "mcr
            "mcrt_trace_packets", "mcrt_checkpoint", "mcrt_restore", "mcrt_debug_uniforms", "mcrt_debug_mrw_x",
            "mcrt_pda_solve_static", "mcrt_disk_info", "mcrt_launch_count", "mcrt_last_error",
            "mcrt_disk_destroy", "mcrt_batch_create", "mcrt_batch_run", "mcrt_batch_config", "mcrt_batch_destroy",
-           "mcrt_default_hydro_opts", "mcrt_hydrostatic_density", "mcrt_set_density"]
+           "mcrt_default_hydro_opts", "mcrt_hydrostatic_density", "mcrt_set_density", "mcrt_set_rays",
+           "mcrt_raytrace", "mcrt_visibilities"]
 
 
 class McrtError(RuntimeError):
@@ -119,6 +120,9 @@ def lib():
         "mcrt_default_hydro_opts": (None, [C.POINTER(HydroOpts)]),
         "mcrt_hydrostatic_density": (st, [P, C.POINTER(HydroOpts), pd]),
         "mcrt_set_density": (st, [P, pd]),
+        "mcrt_set_rays": (st, [P, C.c_double, C.c_double, C.c_int64, pd, pd, pd]),
+        "mcrt_raytrace": (st, [P, C.c_int, C.c_int, pd, pd, pd, pu]),
+        "mcrt_visibilities": (st, [P, C.c_int, pi, pd, pd, C.c_int, pd]),
     }
     for name, (res, args) in sig.items():
         f = getattr(L, name)
@@ -313,6 +317,39 @@ class Disk:
         n = C.c_uint64()
         _check(lib().mcrt_launch_count(self._h, C.byref(n)), self._h)
         return n.value
+
+    def set_rays(self, incl, dist_cm, rays):
+        """Sky-plane rays of the observables (paper_0902_3092_gb300.disks.Rays, cm) for an observer at
+        inclination incl (rad) and distance dist_cm."""
+        self._rays = tuple(np.ascontiguousarray(x, np.float64) for x in (rays.p, rays.q, rays.w))
+        p, q, w = self._rays
+        _check(lib().mcrt_set_rays(self._h, float(incl), float(dist_cm), len(p), _dp(p), _dp(q), _dp(w)), self._h)
+
+    def raytrace(self, which=T_MC, precision=32, want_image=False):
+        """Ray-traced SED of the current rays: dict with F (disk + star, erg/s/cm^2 per wavelength bin),
+        F_star, segments (ray segments through dust) and, with want_image, I (rays x bins intensities,
+        erg/s/cm^2/sr per bin)."""
+        F, Fs = np.zeros(self.nlam), np.zeros(self.nlam)
+        n = len(self._rays[0])
+        I = np.zeros(n * self.nlam) if want_image else None
+        seg = np.zeros(1, np.uint64)
+        _check(lib().mcrt_raytrace(self._h, int(which), int(precision), _dp(F), _dp(Fs),
+                                   None if I is None else _dp(I), _up(seg)), self._h)
+        out = {"F": F, "F_star": Fs, "segments": int(seg[0])}
+        if I is not None:
+            out["I"] = I.reshape(n, self.nlam)
+        return out
+
+    def visibilities(self, bins, baseline_cm, pa_rad, with_star=True):
+        """|V| of the last ray-traced image at wavelength bins `bins`, baselines (cm) and position angles
+        (rad, from the projected major axis), the star included as an unresolved source."""
+        b = np.ascontiguousarray(bins, np.int32).ravel()
+        B = np.ascontiguousarray(np.broadcast_to(baseline_cm, b.shape), np.float64)
+        pa = np.ascontiguousarray(np.broadcast_to(pa_rad, b.shape), np.float64)
+        out = np.zeros(b.size)
+        _check(lib().mcrt_visibilities(self._h, b.size, _ip(b), _dp(B), _dp(pa), int(bool(with_star)), _dp(out)),
+               self._h)
+        return out
 
     def checkpoint(self) -> bytes:
         n = C.c_size_t()

@@ -69,6 +69,9 @@ def test_defaults_and_host_validation(L):
     h = C.c_void_p()
     assert L.mcrt_disk_create(None, None, 0, None, C.byref(h)) == 1
     assert b"NULL" in L.mcrt_last_error(None)
+    assert L.mcrt_set_rays(None, 0.5, 1e20, 1, None, None, None) == 1
+    assert L.mcrt_raytrace(None, 0, 32, None, None, None, None) == 1
+    assert L.mcrt_visibilities(None, 1, None, None, None, 1, None) == 1
     L.mcrt_disk_destroy(None)
 
 
