@@ -10,9 +10,10 @@
 // origin, dimmed along the radial line towards the observer, and occults no ray.
 //
 // Layout: one warp per ray, the 32 lanes over the wavelength bins (nlam <= 256: up to 8 bins per lane,
-// intensities in registers); every lane marches the same cells, so the march costs one warp instruction
-// stream per ray and the per-bin work runs on all lanes. The source table S[cell][bin] is read one row
-// (nlam contiguous values) per segment.
+// intensities in registers); every lane marches the same cells (raymarch.cuh: closed-form crossings, one
+// square root and at most one quadratic per cell), so the march costs one warp instruction stream per
+// ray and the per-bin work runs on all lanes. The source table S[cell][bin] is read one row (nlam
+// contiguous values) per segment.
 #include <cuda_runtime.h>
 
 #include <cmath>
@@ -20,6 +21,7 @@
 
 #include "internal.h"
 #include "planck.cuh"
+#include "raymarch.cuh"
 
 namespace mcrt {
 
@@ -71,26 +73,43 @@ __global__ void k_source(int nc, int nlam, const double* __restrict__ T, const d
   }
 }
 
+// One segment of optical depth x through a cell of source function s: I <- I e^-x + s (1 - e^-x).
+// 1 - e^-x is not formed as a difference where x is small (optically thin segments, where the FP32
+// exponential's absolute error of ~2e-7 would be a large part of it): below 0.1 it is the series
+// x (1 - x/2 + x^2/6 - x^3/24), whose truncation is below 1e-6 of it; in FP64, expm1.
 template <class R>
-__device__ __forceinline__ R exp_neg(R x);
+__device__ __forceinline__ R segment(R I, R s, R x);
 template <>
-__device__ __forceinline__ float exp_neg<float>(float x) { return __expf(-x); }
+__device__ __forceinline__ float segment<float>(float I, float s, float x) {
+  const float e = __expf(-x);
+  const float ser = x * (1.f - x * (0.5f - x * (1.f / 6.f - x * (1.f / 24.f))));
+  const bool small = x < 0.1f;
+  const float om = small ? ser : 1.f - e;
+  return (small ? 1.f - ser : e) * I + om * s;
+}
 template <>
-__device__ __forceinline__ double exp_neg<double>(double x) { return exp(-x); }
+__device__ __forceinline__ double segment<double>(double I, double s, double x) {
+  return exp(-x) * I - expm1(-x) * s;
+}
 
-// One warp per ray (grid-stride over rays). Rays enter at the outer sphere on the far side and run
-// towards the observer along o = (sin i, 0, cos i); the cell march is the transport's (next_face), with
-// the cavity inside r_in crossed in one step. cnt[0] += segments with dust, cnt[1] |= 1 when a ray
-// crossed more faces than the bound.
+// One warp per ray (grid-stride over rays). The cells and path lengths come from march_ray (closed-form
+// crossings of the straight ray with the spheres and cones); every lane marches the same ray and applies
+// the segment to its own wavelength bins. cnt[0] += segments with dust, cnt[1] |= 1 when a ray took more
+// events than the bound.
 template <class R, int NPL>
 __global__ void __launch_bounds__(kRayBlock) k_raytrace(const DevModel<R> M, const R* __restrict__ chi,
                                                         const R* __restrict__ S, long long n,
                                                         const double* __restrict__ p, const double* __restrict__ q,
-                                                        double inv_l, R ox, R oz, R e2x, R e2z, int max_cross,
+                                                        double inv_l, R si, R ci, int max_events,
                                                         R* __restrict__ img, unsigned long long* __restrict__ cnt) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  FaceCoef<R>* face = reinterpret_cast<FaceCoef<R>*>(smem_raw);  // nt+1 entries for this inclination
+  for (int j = threadIdx.x; j <= M.nt; j += blockDim.x) face[j] = face_coef<R>(M.c2[j], M.s2[j], M.fk[j], si, ci);
+  __syncthreads();
   const int lane = threadIdx.x & 31;
   const long long nw = ((long long)gridDim.x * blockDim.x) >> 5;
-  const int nlam = M.nlam, nt = M.nt, nr = M.nr;
+  const int nlam = M.nlam, nt = M.nt;
+  const RayGrid<R> G{M.nr, M.nt, M.rf2, M.cf, face};
   R ch[NPL];
 #pragma unroll
   for (int k = 0; k < NPL; ++k) {
@@ -99,60 +118,25 @@ __global__ void __launch_bounds__(kRayBlock) k_raytrace(const DevModel<R> M, con
   }
   unsigned long long segs = 0;
   bool err = false;
-  const R rout2 = M.rf2[nr];
   for (long long ray = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5; ray < n; ray += nw) {
     R I[NPL];
 #pragma unroll
     for (int k = 0; k < NPL; ++k) I[k] = (R)0;
-    const R pp = (R)(p[ray] * inv_l), qq = (R)(q[ray] * inv_l);
-    const R b2 = pp * pp + qq * qq;
-    if (b2 < rout2) {
-      const R s0 = -sqrt(rout2 - b2);
-      R px = qq * e2x + s0 * ox, py = pp, pz = qq * e2z + s0 * oz;
-      const R ux = ox, uy = (R)0, uz = oz;
-      int ir = nr - 1, it = theta_cell(M, px, py, pz);
-      for (int nc = 0;; ++nc) {
-        if (nc > max_cross) {
-          err = true;
-          break;
-        }
-        if (ir < 0) {  // inner cavity: straight to the far side of r_in
-          const R bb = px * ux + py * uy + pz * uz;
-          const R r2 = px * px + py * py + pz * pz;
-          const R sf = sphere_far(bb, r2 - M.rf2[0]);
-          px += sf * ux;
-          py += sf * uy;
-          pz += sf * uz;
-          ir = 0;
-          it = theta_cell(M, px, py, pz);
-          continue;
-        }
-        int face;
-        const R L = next_face(M, ir, it, px, py, pz, ux, uy, uz, face);
-        const int c = ir * nt + it;
-        const R a = M.rho[c] * L;  // optical depth per unit chi (rho is stored per internal length)
-        if (a > (R)0) {
-          const R* Sc = S + (size_t)c * nlam;
+    const int rc = march_ray(G, (R)(p[ray] * inv_l), (R)(q[ray] * inv_l), si, ci, max_events,
+                             [&](int ir, int it, R L) {
+                               const int c = ir * nt + it;
+                               const R a = M.rho[c] * L;  // optical depth per unit chi
+                               if (a > (R)0) {
+                                 const R* Sc = S + (size_t)c * nlam;
 #pragma unroll
-          for (int k = 0; k < NPL; ++k) {
-            const int b = lane + 32 * k;
-            if (b < nlam) {
-              const R s = Sc[b];
-              I[k] = s + (I[k] - s) * exp_neg<R>(a * ch[k]);
-            }
-          }
-          ++segs;
-        }
-        px += L * ux;
-        py += L * uy;
-        pz += L * uz;
-        if (face == 1) ++ir;
-        else if (face == 0) --ir;
-        else if (face == 2) --it;
-        else ++it;
-        if (ir >= nr) break;
-      }
-    }
+                                 for (int k = 0; k < NPL; ++k) {
+                                   const int b = lane + 32 * k;
+                                   if (b < nlam) I[k] = segment<R>(I[k], Sc[b], a * ch[k]);
+                                 }
+                                 ++segs;
+                               }
+                             });
+    if (rc < 0) err = true;
     R* o = img + (size_t)ray * nlam;
 #pragma unroll
     for (int k = 0; k < NPL; ++k) {
@@ -274,9 +258,8 @@ int sm_count(int device) {
 
 template <class R>
 cudaError_t launch_trace(mcrt_disk* d, RayState* rs, const DevModel<R>& M, const R* chi, int grid) {
-  const double si = std::sin(rs->incl), ci = std::cos(rs->incl);
-  const int max_cross = 4 * (d->nr + d->nt) + 64;
-  const R ox = (R)si, oz = (R)ci, e2x = (R)(-ci), e2z = (R)si;
+  const R si = (R)std::sin(rs->incl), ci = (R)std::cos(rs->incl);
+  const int max_events = 4 * (d->nr + d->nt) + 64;
   const double inv_l = 1.0 / d->l_unit;
   const R* S = rs->S.as<R>();
   R* img = rs->img.as<R>();
@@ -284,10 +267,16 @@ cudaError_t launch_trace(mcrt_disk* d, RayState* rs, const DevModel<R>& M, const
   const double* p = rs->p.as<double>();
   const double* q = rs->q.as<double>();
   const int npl = (d->nlam + 31) / 32;
+  const size_t smem = (size_t)(d->nt + 1) * sizeof(FaceCoef<R>);
 #define MCRT_TRACE_CASE(K)                                                                                 \
   case K:                                                                                                  \
-    k_raytrace<R, K><<<grid, kRayBlock, 0, d->stream>>>(M, chi, S, rs->n, p, q, inv_l, ox, oz, e2x, e2z,    \
-                                                        max_cross, img, cnt);                              \
+    if (smem > 48 * 1024) {                                                                                \
+      cudaError_t e = cudaFuncSetAttribute(k_raytrace<R, K>, cudaFuncAttributeMaxDynamicSharedMemorySize,  \
+                                           (int)smem);                                                     \
+      if (e != cudaSuccess) return e;                                                                      \
+    }                                                                                                      \
+    k_raytrace<R, K><<<grid, kRayBlock, smem, d->stream>>>(M, chi, S, rs->n, p, q, inv_l, si, ci, max_events, \
+                                                        img, cnt);                                         \
     break;
   switch (npl) {
     MCRT_TRACE_CASE(1)
@@ -306,9 +295,9 @@ cudaError_t launch_trace(mcrt_disk* d, RayState* rs, const DevModel<R>& M, const
 }
 
 template <class R>
-int trace_blocks_per_sm() {
+int trace_blocks_per_sm(size_t smem) {
   int v = 0;
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&v, k_raytrace<R, 4>, kRayBlock, 0);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&v, k_raytrace<R, 4>, kRayBlock, smem);
   return v > 0 ? v : 1;
 }
 
@@ -357,7 +346,9 @@ mcrt_status trace_impl(mcrt_disk* d, int which) {
   CK(cudaMemsetAsync(rs->cnt.p, 0, 2 * sizeof(unsigned long long), d->stream), "memset");
   const int sms = sm_count(d->device);
   const long long warps_needed = rs->n;
-  long long grid = (long long)sms * trace_blocks_per_sm<R>();
+  const size_t smem = (size_t)(d->nt + 1) * sizeof(FaceCoef<R>);
+  if (smem > 200 * 1024) return set_error(d, MCRT_EINVAL, "too many polar cells for the ray-tracing face table");
+  long long grid = (long long)sms * trace_blocks_per_sm<R>(smem);
   const long long need = (warps_needed * 32 + kRayBlock - 1) / kRayBlock;
   if (grid > need) grid = need;
   if (grid < 1) grid = 1;
@@ -455,7 +446,7 @@ mcrt_status mcrt_raytrace(mcrt_disk* d, int which, int precision, double* F_out,
     }
   }
   if (n_segments) *n_segments = c[0];
-  if (c[1]) return set_error(d, MCRT_ETIMEOUT, "a ray crossed more cell faces than 4 (nr + ntheta) + 64");
+  if (c[1]) return set_error(d, MCRT_ETIMEOUT, "a ray took more than 4 (nr + ntheta) + 64 events");
   return MCRT_OK;
 }
 
