@@ -28,6 +28,15 @@
  *                interaction's MRW chain
  *   MRW jump:    two blocks: w0 escape-time quantile P, (w1, w2) point on the
  *                sphere, w3 exit bin; then (w0, w1) new direction, w2 and w3 unused
+ *   source:      only when the model has internal sources (viscous heating, Sect. 5):
+ *                a block before the launch, w0 and w1 one uniform of 46 bits
+ *                u = (w0 - 2^-24) + w1 2^-23 that picks the star (u L_tot < L_star)
+ *                or the cell (the first c whose cumulative source luminosity passes
+ *                u L_tot - L_star), w2 the radius (uniform in r^3 across the cell),
+ *                w3 the polar position (uniform in cos theta); the star's packets
+ *                then take the launch block, a cell's packet is released at that
+ *                point by an absorption with omega = 0 (the interaction block: w0
+ *                the BW bin, (w1, w2) direction, w3 tau)
  */
 #include <math.h>
 #include <stdint.h>
@@ -211,6 +220,7 @@ typedef struct {
   const double *lam_e;/* nlam+1 (micron) */
   const double *kabs, *ksca, *g; /* nlam */
   double Tstar, Rstar;
+  const double *Lsrc; /* nr*nt internal source luminosity (erg/s) or NULL */
 } oracle_model;
 
 typedef struct {
@@ -289,20 +299,34 @@ double oracle_T_of_q(const oracle_model *m, double q) {
   return T;
 }
 
-/* Temperature of cell c from its fixed-point tally; L_abs = tally/EUNIT * Lstar/N. */
-static double cell_T(const oracle_model *m, int c, uint64_t tally, double n_total) {
+static double star_lum(const oracle_model *m) {
+  return 4.0 * OR_PI * m->Rstar * m->Rstar * OR_SIGMA * pow(m->Tstar, 4);
+}
+
+/* Luminosity the packets carry: the star plus every internal source. */
+double oracle_packet_lum(const oracle_model *m) {
+  double L = 0.0;
+  if (m->Lsrc)
+    for (int c = 0; c < m->nr * m->nt; ++c) L += m->Lsrc[c];
+  return star_lum(m) + L;
+}
+
+/* Temperature of cell c from its fixed-point tally; L_abs = tally/EUNIT * Lpkt/N (Lpkt: the
+ * luminosity the packets carry). A cell's own source releases count as absorbed energy, so the
+ * balance is emission = absorption + heating. */
+static double cell_T(const oracle_model *m, int c, uint64_t tally, double n_total, double Lpkt) {
   if (tally == 0) return 0.0;
   int ir = c / m->nt, it = c % m->nt;
   double mass = m->rho[c] * cell_volume(m, ir, it);
-  double Lstar = 4.0 * OR_PI * m->Rstar * m->Rstar * OR_SIGMA * pow(m->Tstar, 4);
-  double Labs = ((double)tally / OR_EUNIT) * Lstar / n_total;
+  double Labs = ((double)tally / OR_EUNIT) * Lpkt / n_total;
   return oracle_T_of_q(m, Labs / mass);
 }
 
 /* Per-cell temperature and statistical error 1/(4 sqrt(N_abs,eq)). */
 void oracle_temperatures(const oracle_model *m, const uint64_t *tally, double n_total, double *T, double *relerr) {
+  const double Lpkt = oracle_packet_lum(m);
   for (int c = 0; c < m->nr * m->nt; ++c) {
-    T[c] = (m->rho[c] > 0.0) ? cell_T(m, c, tally[c], n_total) : 0.0;
+    T[c] = (m->rho[c] > 0.0) ? cell_T(m, c, tally[c], n_total, Lpkt) : 0.0;
     if (relerr) {
       double n = (double)tally[c] / OR_EUNIT;
       relerr[c] = n > 0 ? 0.25 / sqrt(n) : INFINITY;
@@ -571,8 +595,10 @@ typedef struct {
   oracle_state *st;
   int gray;
   double n_total;
+  double Lpkt;    /* luminosity the packets carry */
   double *w, *w2; /* nlam scratch */
   double *star_w;
+  double *src_cum; /* nr*nt+1 cumulative source luminosity, or NULL */
 } ctx_t;
 
 static void trace(ctx_t *x, int tp, int *ntr, int type, int cell, const double p[3], int lam) {
@@ -623,6 +649,50 @@ static void deposit(ctx_t *x, int c, uint64_t units, uint64_t *pkt_dep) {
   *pkt_dep += units;
 }
 
+/* The chain of MRW jumps from the packet's point in cell (ir, it) while Eq. 11 holds (Sect. 2.2.2). */
+static void mrw_walk(ctx_t *x, or_rng *r, double p[3], double u[3], int *lam, int ir, int it, uint64_t *events,
+                     int tp, int *ntr, uint64_t *dep) {
+  const oracle_model *m = x->m;
+  const oracle_opts *o = x->o;
+  oracle_state *s = x->st;
+  const int c = ir * m->nt + it;
+  for (;;) {
+    if (*events >= o->max_events) break;
+    double dmin = oracle_dmin(m, p, ir, it);
+    double T = fmax(s->Tcell[c], 1.0);
+    double D, kbar;
+    oracle_diffusion(m, T, m->rho[c], &D, &kbar);
+    /* Eq. 11 with rho chi_R = 1/(3 D) */
+    if (!(dmin > o->gamma * 3.0 * D)) break;
+    double ja[4], jb[4];
+    U4(r, ja);
+    U4(r, jb);
+    double x0 = oracle_mrw_x(ja[0]);
+    double ct = x0 * dmin * dmin / D;           /* path length c t */
+    double E = ct * m->rho[c] * kbar;             /* Eq. 9, in packet energies */
+    double units = floor(E * OR_EUNIT + 0.5);
+    if (units >= 1.8e19) { s->cnt[CNT_ERR] |= 2u; units = 1.8e19; }
+    deposit(x, c, (uint64_t)units, dep);
+    s->Tcell[c] = cell_T(m, c, s->tally[c], x->n_total, x->Lpkt);
+    double uh[3];
+    iso_dir(ja[1], ja[2], uh);
+    for (int d = 0; d < 3; ++d) p[d] += dmin * uh[d];
+    if (o->mrw_exit_dir == 1) {
+      double mu = sqrt(jb[0]);
+      double phi = 2.0 * OR_PI * jb[1];
+      u[0] = uh[0]; u[1] = uh[1]; u[2] = uh[2];
+      turn(u, mu, phi);
+    } else {
+      iso_dir(jb[0], jb[1], u);
+    }
+    double xl = ja[3];
+    if (!x->gray || o->want_sed) *lam = exit_bin(x, s->Tcell[c], xl);
+    (*events)++;
+    s->cnt[CNT_MRW]++;
+    trace(x, tp, ntr, EV_MRW, c, p, *lam);
+  }
+}
+
 static void run_packet(ctx_t *x, uint64_t k, uint64_t seed, uint32_t model, int tp) {
   const oracle_model *m = x->m;
   const oracle_opts *o = x->o;
@@ -633,13 +703,68 @@ static void run_packet(ctx_t *x, uint64_t k, uint64_t seed, uint32_t model, int 
   int ntr = 0;
   uint64_t dep = 0, events = 0, crossings = 0;
   double p[3] = {0, 0, 0}, u[3], w[4];
-  U4(&r, w);
-  int lam = sample_bins(x->star_w, m->nlam, w[0]);
-  iso_dir(w[1], w[2], u);
-  int ir = -1, it = -1, ninc = 0;
-  trace(x, tp, &ntr, EV_LAUNCH, -1, p, lam);
-  double tau = -log(w[3]);
-  s->cnt[CNT_PACKETS]++;
+  int ir = -1, it = -1, ninc = 0, lam = 0;
+  double tau = 0.0;
+  int released = 0;
+  if (x->src_cum) {
+    /* internal sources: the star or a cell, chosen in proportion to their luminosities */
+    const int n = m->nr * nt;
+    const double Lstar = star_lum(m);
+    const double Ltot = Lstar + x->src_cum[n];
+    U4(&r, w);
+    const double us = (w[0] - 0.5 / 8388608.0) + w[1] * (1.0 / 8388608.0);
+    const double t = us * Ltot;
+    if (t >= Lstar) {
+      const double tt = t - Lstar;
+      int c = 0;
+      while (c < n - 1 && !(x->src_cum[c + 1] > tt)) ++c;
+      while (c > 0 && !(x->src_cum[c + 1] > x->src_cum[c])) --c; /* rounding past the end: the last source */
+      ir = c / nt;
+      it = c % nt;
+      /* a point uniform in the cell's volume (at azimuth 0: the grid is axisymmetric) */
+      const double r1 = m->rf[ir], r2 = m->rf[ir + 1];
+      const double rr = cbrt(r1 * r1 * r1 + w[2] * (r2 * r2 * r2 - r1 * r1 * r1));
+      const double c1 = cos(m->tf[it]), c2 = cos(m->tf[it + 1]);
+      const double mu = c1 + w[3] * (c2 - c1);
+      p[0] = rr * sqrt(1.0 - mu * mu);
+      p[1] = 0.0;
+      p[2] = rr * mu;
+      s->visits[c]++;
+      trace(x, tp, &ntr, EV_LAUNCH, c, p, lam);
+      s->cnt[CNT_PACKETS]++;
+      /* the release: an absorption with omega = 0 at that point */
+      U4(&r, w);
+      deposit(x, c, (uint64_t)OR_EUNIT, &dep);
+      s->nabs[c]++;
+      double Told = s->Tcell[c];
+      double Tnew = cell_T(m, c, s->tally[c], x->n_total, x->Lpkt);
+      s->Tcell[c] = Tnew;
+      if (!x->gray || o->want_sed) lam = bw_bin(x, Told, Tnew, w[0]);
+      iso_dir(w[1], w[2], u);
+      s->cnt[CNT_ABS]++;
+      trace(x, tp, &ntr, EV_ABSORB, c, p, lam);
+      events++;
+      ninc++;
+      if (o->mrw && ninc >= o->nmin) mrw_walk(x, &r, p, u, &lam, ir, it, &events, tp, &ntr, &dep);
+      released = 1;
+      if (events >= o->max_events) {
+        s->cnt[CNT_CAPPED]++;
+        trace(x, tp, &ntr, EV_CAPPED, c, p, lam);
+        s->cnt[CNT_EVENTS] += events;
+        s->cnt[CNT_DEPSUM] += dep;
+        return;
+      }
+      tau = -log(w[3]);
+    }
+  }
+  if (!released) {
+    U4(&r, w);
+    lam = sample_bins(x->star_w, m->nlam, w[0]);
+    iso_dir(w[1], w[2], u);
+    trace(x, tp, &ntr, EV_LAUNCH, -1, p, lam);
+    tau = -log(w[3]);
+    s->cnt[CNT_PACKETS]++;
+  }
   for (;;) {
     if (++crossings > 4000000000ull) { s->cnt[CNT_ERR] |= 4u; s->cnt[CNT_CAPPED]++; break; }
     if (ir < 0) {
@@ -681,7 +806,7 @@ static void run_packet(ctx_t *x, uint64_t k, uint64_t seed, uint32_t model, int 
         deposit(x, c, (uint64_t)OR_EUNIT, &dep);
         s->nabs[c]++;
         double Told = s->Tcell[c];
-        double Tnew = cell_T(m, c, s->tally[c], x->n_total);
+        double Tnew = cell_T(m, c, s->tally[c], x->n_total, x->Lpkt);
         (void)before;
         s->Tcell[c] = Tnew;
         double xl = (w[0] - omega) / (1.0 - omega);
@@ -693,43 +818,7 @@ static void run_packet(ctx_t *x, uint64_t k, uint64_t seed, uint32_t model, int 
       events++;
       ninc++;
       /* modified random walk, Sect. 2.2.2 */
-      if (o->mrw && ninc >= o->nmin) {
-        for (;;) {
-          if (events >= o->max_events) break;
-          double dmin = oracle_dmin(m, p, ir, it);
-          double T = fmax(s->Tcell[c], 1.0);
-          double D, kbar;
-          oracle_diffusion(m, T, m->rho[c], &D, &kbar);
-          /* Eq. 11 with rho chi_R = 1/(3 D) */
-          if (!(dmin > o->gamma * 3.0 * D)) break;
-          double ja[4], jb[4];
-          U4(&r, ja);
-          U4(&r, jb);
-          double x0 = oracle_mrw_x(ja[0]);
-          double ct = x0 * dmin * dmin / D;           /* path length c t */
-          double E = ct * m->rho[c] * kbar;             /* Eq. 9, in packet energies */
-          double units = floor(E * OR_EUNIT + 0.5);
-          if (units >= 1.8e19) { s->cnt[CNT_ERR] |= 2u; units = 1.8e19; }
-          deposit(x, c, (uint64_t)units, &dep);
-          s->Tcell[c] = cell_T(m, c, s->tally[c], x->n_total);
-          double uh[3];
-          iso_dir(ja[1], ja[2], uh);
-          for (int d = 0; d < 3; ++d) p[d] += dmin * uh[d];
-          if (o->mrw_exit_dir == 1) {
-            double mu = sqrt(jb[0]);
-            double phi = 2.0 * OR_PI * jb[1];
-            u[0] = uh[0]; u[1] = uh[1]; u[2] = uh[2];
-            turn(u, mu, phi);
-          } else {
-            iso_dir(jb[0], jb[1], u);
-          }
-          double xl = ja[3];
-          if (!x->gray || o->want_sed) lam = exit_bin(x, s->Tcell[c], xl);
-          events++;
-          s->cnt[CNT_MRW]++;
-          trace(x, tp, &ntr, EV_MRW, c, p, lam);
-        }
-      }
+      if (o->mrw && ninc >= o->nmin) mrw_walk(x, &r, p, u, &lam, ir, it, &events, tp, &ntr, &dep);
       if (events >= o->max_events) {
         s->cnt[CNT_CAPPED]++;
         trace(x, tp, &ntr, EV_CAPPED, c, p, lam);
@@ -777,6 +866,18 @@ int oracle_run(const oracle_model *m, const oracle_opts *o, oracle_state *s, uin
   x.st = s;
   x.gray = is_gray(m);
   x.n_total = (double)n_total;
+  x.Lpkt = oracle_packet_lum(m);
+  x.src_cum = NULL;
+  if (m->Lsrc) {
+    const int n = m->nr * m->nt;
+    x.src_cum = (double *)malloc(sizeof(double) * (n + 1));
+    x.src_cum[0] = 0.0;
+    for (int c = 0; c < n; ++c) x.src_cum[c + 1] = x.src_cum[c] + m->Lsrc[c];
+    if (!(x.src_cum[n] > 0.0)) {
+      free(x.src_cum);
+      x.src_cum = NULL;
+    }
+  }
   x.w = (double *)malloc(sizeof(double) * m->nlam);
   x.w2 = (double *)malloc(sizeof(double) * m->nlam);
   x.star_w = (double *)malloc(sizeof(double) * m->nlam);
@@ -788,6 +889,7 @@ int oracle_run(const oracle_model *m, const oracle_opts *o, oracle_state *s, uin
   free(x.w);
   free(x.w2);
   free(x.star_w);
+  free(x.src_cum);
   return 0;
 }
 

@@ -59,7 +59,7 @@ class _Model(C.Structure):
                 ("rf", C.POINTER(C.c_double)), ("tf", C.POINTER(C.c_double)), ("rho", C.POINTER(C.c_double)),
                 ("lam_e", C.POINTER(C.c_double)), ("kabs", C.POINTER(C.c_double)),
                 ("ksca", C.POINTER(C.c_double)), ("g", C.POINTER(C.c_double)),
-                ("Tstar", C.c_double), ("Rstar", C.c_double)]
+                ("Tstar", C.c_double), ("Rstar", C.c_double), ("Lsrc", C.POINTER(C.c_double))]
 
 
 class _Opts(C.Structure):
@@ -100,6 +100,7 @@ def lib():
         L.oracle_run.argtypes = [C.POINTER(_Model), C.POINTER(_Opts), C.POINTER(_State), C.c_uint64, C.c_uint64,
                                  C.c_uint64, C.c_uint64, C.c_uint32]
         L.oracle_star_bin.restype = C.c_int; L.oracle_star_bin.argtypes = [C.POINTER(_Model), d]
+        L.oracle_packet_lum.restype = d; L.oracle_packet_lum.argtypes = [C.POINTER(_Model)]
         for f in ("oracle_cone_exit",):
             getattr(L, f).restype = d
             getattr(L, f).argtypes = [pd, pd, d, C.c_int]
@@ -128,7 +129,7 @@ def _ip(a):
 class Model:
     """Holds the arrays of a disk (keeps them alive for the C side)."""
 
-    def __init__(self, disk):
+    def __init__(self, disk, sources=None):
         self.disk = disk
         self.rf = np.ascontiguousarray(disk.r_faces_cm, np.float64)
         self.tf = np.ascontiguousarray(disk.theta_faces, np.float64)
@@ -139,8 +140,11 @@ class Model:
         self.ksca = np.ascontiguousarray(op.kappa_sca, np.float64)
         self.g = np.ascontiguousarray(op.g, np.float64)
         self.nr, self.nt, self.nlam = disk.nr, disk.ntheta, op.nlam
+        # internal source luminosity per cell (erg/s; viscous heating), or none
+        self.Lsrc = None if sources is None else np.ascontiguousarray(sources, np.float64).ravel()
         self.c = _Model(self.nr, self.nt, self.nlam, _dp(self.rf), _dp(self.tf), _dp(self.rho), _dp(self.lam_e),
-                        _dp(self.kabs), _dp(self.ksca), _dp(self.g), disk.star.T_K, disk.star.R_cm)
+                        _dp(self.kabs), _dp(self.ksca), _dp(self.g), disk.star.T_K, disk.star.R_cm,
+                        None if self.Lsrc is None else _dp(self.Lsrc))
 
     @property
     def ptr(self):
@@ -148,10 +152,11 @@ class Model:
 
 
 class Run:
-    """Tallies of an oracle Monte Carlo run (may be continued: resume)."""
+    """Tallies of an oracle Monte Carlo run (may be continued: resume). sources: luminosity (erg/s) of
+    internal sources per cell (viscous heating), released by absorption-like events (see mcrt_oracle.c)."""
 
-    def __init__(self, disk):
-        self.model = Model(disk)
+    def __init__(self, disk, sources=None):
+        self.model = Model(disk, sources)
         n = self.model.nr * self.model.nt
         self.tally = np.zeros(n, np.uint64)
         self.visits = np.zeros(n, np.uint64)
@@ -202,10 +207,14 @@ class Run:
         L.oracle_temperatures(self.model.ptr, _up(self.tally), float(self.n_total), _dp(T), _dp(e))
         return T.reshape(self.model.nr, self.model.nt), e.reshape(self.model.nr, self.model.nt)
 
+    @property
+    def packet_lum(self):
+        """Luminosity the packets carry (erg/s): the star plus the internal sources."""
+        return float(lib().oracle_packet_lum(self.model.ptr))
+
     def sed_lum(self):
         """Escaped luminosity per (wavelength bin, inclination bin), erg/s."""
-        Lstar = self.model.disk.star.L
-        return self.sed.reshape(self.model.nlam, NINC).astype(np.float64) * Lstar / self.n_total
+        return self.sed.reshape(self.model.nlam, NINC).astype(np.float64) * self.packet_lum / self.n_total
 
 
 # ----------------------------------------------------------------------------- small helpers

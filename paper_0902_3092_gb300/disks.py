@@ -270,3 +270,29 @@ def polar_rays(r_faces_cm: np.ndarray, n_sub: int = 4, n_phi: int = 64, n_inner:
     q = (b[:, None] * np.sin(phi)[None, :]).ravel()
     w = np.repeat(area, n_phi)
     return Rays(p, q, w)
+
+
+G_CGS = 6.67430e-8        # cm^3 g^-1 s^-2
+MSUN_G = 1.98892e33
+YEAR_S = 3.15576e7
+
+
+def viscous_sources(d: Disk, mdot_msun_yr: float = 1e-8, M_star_msun: float = 2.5) -> np.ndarray:
+    """Internal source luminosity per cell (erg/s, nr x ntheta) for viscous heating, which the paper
+    leaves to future work (Sect. 5). Reading: the steady accretion-disk dissipation, 3 G M Mdot /
+    (8 pi R^3) (1 - sqrt(R_in / R)) per unit area of each face, released in proportion to the dust
+    mass of the column, so a cell at cylindrical radius R releases m_cell Q(R) / Sigma(R) with Q twice
+    the one-face rate and Sigma(R) = sqrt(pi) h1 rho0 AU / (R / AU) the surface density of Eq. 17."""
+    prm = d.params
+    R_in = prm["R_in_au"] * AU_CM
+    rc, tc = cell_centres(d.r_faces_cm, d.theta_faces)
+    R = rc[:, None] * np.sin(tc)[None, :]
+    rf, tf = d.r_faces_cm, d.theta_faces
+    V = (2 * math.pi / 3) * (rf[1:] ** 3 - rf[:-1] ** 3)[:, None] * (np.cos(tf[:-1]) - np.cos(tf[1:]))[None, :]
+    mdot = mdot_msun_yr * MSUN_G / YEAR_S
+    GM = G_CGS * M_star_msun * MSUN_G
+    with np.errstate(divide="ignore", invalid="ignore"):
+        F = np.where(R > R_in, 3 * GM * mdot / (8 * math.pi * R ** 3) * (1 - np.sqrt(R_in / R)), 0.0)
+        sigma = math.sqrt(math.pi) * prm["h1_au"] * AU_CM * prm["rho0"] / (R / AU_CM)
+        L = np.where((d.rho > 0) & (sigma > 0), d.rho * V * 2 * F / sigma, 0.0)
+    return np.ascontiguousarray(L)
