@@ -73,6 +73,8 @@ def parse():
                    help="instead of the transport step: PDA solve and adjoint on the 400x200 non-gray disk")
     p.add_argument("--raytrace", action="store_true",
                    help="instead of the transport step: ray-traced SED and image of the 200x120 disk at 45 degrees")
+    p.add_argument("--viscous", action="store_true",
+                   help="instead of the transport step: packets released by viscous heating in the 200x120 disk")
     p.add_argument("--pda-min-visits", type=int, default=0,
                    help="PDA visit threshold; 0 scales the paper's 30 entries at 1e5 packets with the packet count "
                         "(Sect. 3.1 uses 30000 for its 1e8-packet runs)")
@@ -428,6 +430,57 @@ def raytrace_timing(args):
     print(json.dumps(line), flush=True)
 
 
+def viscous_timing(args):
+    """Viscous heating (Sect. 5): packets released inside the 200 x 120 rim-refined tau_mid = 1e6 gray
+    disk by the steady accretion dissipation of disks.viscous_sources (scaled to 1e4 L* so that the
+    star's packets are 1e-4 of all), transported with MRW (gamma = 1, the paper's setting) and, for
+    comparison, without it under a 1e6-event cap. Timed: reset + transport of 1e6 packets per step with
+    CUDA events on the disk's stream."""
+    import torch
+    from paper_0902_3092_gb300 import disks, mcrt
+    d = disks.config_thick_gray(200, 120, 1e6)
+    L = disks.viscous_sources(d)
+    L *= 1e4 * d.star.L / L.sum()
+    st = torch.cuda.Stream()
+    g = mcrt.Disk.from_model(d, stream=st.cuda_stream)
+    g.set_sources(L)
+    n = 1_000_000
+    cap = 10 ** 6
+    g.run_photons(100_000, seed=99, mrw=True, gamma=1.0, max_events=cap, want_sed=False)
+    times, stats = [], None
+    with ClockSampler(physical_gpu(0)) as clk:
+        for k in range(args.warmup + args.steps):
+            with torch.cuda.stream(st):
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(st)
+                g.reset()
+                stats = g.run_photons(n, seed=1 + k, mrw=True, gamma=1.0, max_events=cap, want_sed=False)
+                e1.record(st)
+            torch.cuda.synchronize()
+            if k >= args.warmup:
+                times.append(e0.elapsed_time(e1) * 1e-3)
+    t = float(np.mean(times))
+    # plain Monte Carlo (no MRW) on the same sources
+    n_plain = 20_000
+    g.reset()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    sp = g.run_photons(n_plain, seed=7, mrw=False, max_events=cap, want_sed=False)
+    tp = time.perf_counter() - t0
+    line = {"metric": "viscous-heating packets/s (released in the disk, MRW gamma=1)", "value": n / t,
+            "unit": "packets/s", "higher_is_better": True, "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1e3 * t, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": "200x120 rim-refined gray disk, tau_mid=1e6, steady accretion dissipation "
+                                   "(scaled to 1e4 L*), MRW gamma=1", "packets_per_step": n,
+                       "max_events_per_packet": cap},
+            "events_per_packet": stats["events"] / n, "mrw_jumps_per_packet": stats["mrw_jumps"] / n,
+            "capped_fraction": stats["capped"] / n, "us_per_packet": 1e6 * t / n,
+            "plain_mc": {"packets": n_plain, "packets_per_s": n_plain / tp, "us_per_packet": 1e6 * tp / n_plain,
+                         "capped_fraction": sp["capped"] / n_plain, "events_per_packet": sp["events"] / n_plain},
+            "clocks": clk.summary()}
+    print(json.dumps(line), flush=True)
+
+
 def main():
     args = parse()
     if args.impl == "reference":
@@ -444,6 +497,9 @@ def main():
         return
     if args.raytrace:
         raytrace_timing(args)
+        return
+    if args.viscous:
+        viscous_timing(args)
         return
     import torch
     import torch.distributed as dist

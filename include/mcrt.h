@@ -229,6 +229,17 @@ mcrt_status mcrt_hydrostatic_density(mcrt_disk *d, const mcrt_hydro_opts *opts, 
  * the grid, star and opacities stay. Device buffers keep their addresses. */
 mcrt_status mcrt_set_density(mcrt_disk *d, const double *rho);
 
+/* Internal sources (Sect. 5: viscous heating, whose energy the MRW carries out of the midplane):
+ * luminosity per cell (host array nr*ntheta, erg/s, finite, >= 0, zero in dust-free cells; NULL or
+ * all zero: none). Packets then start from the star or a cell in proportion to the luminosities and
+ * carry (L_star + sum L) / N each; a cell's packet starts at a point uniform in the cell's volume and
+ * is released there by an absorption with omega = 0, so its energy enters the cell's tally (the
+ * temperatures then balance emission against absorption plus heating) and leaves with the
+ * Bjorkman-Wood spectrum. Random draws: one extra block before each packet's launch (see
+ * mcrt_run_photons). Resets the tallies; checkpoints do not hold the sources. MCRT_EINVAL for bad
+ * values. */
+mcrt_status mcrt_set_sources(mcrt_disk *d, const double *L_cell_erg_s);
+
 /* ---- Ray-traced observables (Sect. 2.3: the observables come from integrating the computed source
  * function along rays, free of Monte Carlo noise; Sect. 4.1: SED from 0.1 um to 1 cm at 45 degrees,
  * N-band visibilities at a 100 m baseline). Readings: the source function of a cell in bin b is

@@ -197,7 +197,7 @@ __global__ void k_temperature(int n, const unsigned long long* __restrict__ tall
 
 mcrt_status compute_temperatures(mcrt_disk* d) {
   const int n = d->nr * d->nt;
-  const double lfac = d->Lstar / (d->n_total > 0 ? d->n_total : 1.0);
+  const double lfac = d->Lpkt() / (d->n_total > 0 ? d->n_total : 1.0);
   const double dlnT = std::log(d->Tmax / d->Tmin) / (d->nT - 2);
   k_temperature<<<(n + 255) / 256, 256, 0, d->stream>>>(
       n, d->tally.as<unsigned long long>(), d->mass_d.as<double>(), lfac, d->gray ? 1 : 0, d->kabs[0], d->nlam,
@@ -274,7 +274,11 @@ static DevModel<R> make_model(const mcrt_disk* d, bool f64) {
   m.chiR = d->chiRk.as<float>();
   m.kbar = d->kbark.as<float>();
   m.lqm = d->lqm.as<float>();
-  m.lq_run = (float)std::log(d->Lstar / ((d->n_total > 0 ? d->n_total : 1.0) * (double)kEUnit));
+  m.lq_run = (float)std::log(d->Lpkt() / ((d->n_total > 0 ? d->n_total : 1.0) * (double)kEUnit));
+  m.src_cum = d->n_src ? d->src_cum.as<double>() : nullptr;
+  m.src_Lstar = d->Lstar;
+  m.src_Ltot = d->Lpkt();
+  m.n_src = d->n_src;
   m.tally = d->tally.as<unsigned long long>();
   m.visits = d->visits.as<unsigned long long>();
   m.nabs = d->nabs.as<unsigned long long>();
@@ -374,6 +378,34 @@ mcrt_status mcrt_set_density(mcrt_disk* d, const double* rho) {
   mcrt_status s = upload_density(d);
   if (s != MCRT_OK) return s;
   s = zero_tallies(d);
+  if (s != MCRT_OK) return s;
+  CK(cudaStreamSynchronize(d->stream), "synchronize");
+  return MCRT_OK;
+}
+
+mcrt_status mcrt_set_sources(mcrt_disk* d, const double* L) {
+  if (!d) return set_error(nullptr, MCRT_EINVAL, "disk is NULL");
+  const size_t n = (size_t)d->nr * d->nt;
+  std::vector<double> cum(n + 1, 0.0);
+  if (L) {
+    for (size_t c = 0; c < n; ++c) {
+      if (!(std::isfinite(L[c]) && L[c] >= 0)) return set_error(d, MCRT_EINVAL, "source luminosities: finite, >= 0");
+      if (L[c] > 0 && !(d->rho[c] > 0)) return set_error(d, MCRT_EINVAL, "a source in a cell without dust");
+      cum[c + 1] = cum[c] + L[c];  // in cell order, as the sources are drawn
+    }
+  }
+  CK(cudaSetDevice(d->device), "cudaSetDevice");
+  CK(cudaStreamSynchronize(d->stream), "synchronize");
+  if (cum[n] > 0) {
+    cudaError_t e = upload(d->src_cum, cum);
+    if (e != cudaSuccess) return cuda_fail(d, e, "upload");
+    d->n_src = (int)n;
+    d->Lsrc_total = cum[n];
+  } else {
+    d->n_src = 0;
+    d->Lsrc_total = 0;
+  }
+  mcrt_status s = zero_tallies(d);  // the packet energy changed
   if (s != MCRT_OK) return s;
   CK(cudaStreamSynchronize(d->stream), "synchronize");
   return MCRT_OK;
@@ -1000,7 +1032,7 @@ mcrt_status mcrt_sed(mcrt_disk* d, int n_incl, double* L) {
   std::vector<unsigned long long> c((size_t)d->nlam * kNInc);
   CK(cudaMemcpyAsync(c.data(), d->sed.p, c.size() * 8, cudaMemcpyDeviceToHost, d->stream), "copy");
   CK(cudaStreamSynchronize(d->stream), "synchronize");
-  const double e = d->Lstar / (d->n_total > 0 ? d->n_total : 1.0);
+  const double e = d->Lpkt() / (d->n_total > 0 ? d->n_total : 1.0);
   const int grp = kNInc / n_incl;
   for (int b = 0; b < d->nlam; ++b)
     for (int i = 0; i < n_incl; ++i) {

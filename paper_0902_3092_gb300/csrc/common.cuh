@@ -110,7 +110,12 @@ struct DevModel {
   const float* chiR;      // nT: Rosseland mean of chi' (cm^2/g)
   const float* kbar;      // nT: kappa_bar of Eq. 10
   const float* lqm;       // nr*nt: log(1 / m_cell) (1/g)
-  float lq_run;           // log(L_star / (N EUNIT)): log q = log(tally) + lqm[c] + lq_run
+  float lq_run;           // log(L_pkt / (N EUNIT)): log q = log(tally) + lqm[c] + lq_run
+  // internal sources (viscous heating): cumulative luminosity over the cells (n_src + 1 entries, FP64),
+  // the star's luminosity and the total the packets carry; n_src = 0 without sources
+  const double* src_cum;
+  double src_Lstar, src_Ltot;
+  int n_src;
   // tallies
   unsigned long long* tally;   // nr*nt fixed-point absorbed energy
   unsigned long long* visits;  // nr*nt packet entries

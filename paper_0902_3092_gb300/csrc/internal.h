@@ -59,6 +59,11 @@ struct mcrt_disk {
   bool gray = false, has_opacity = false;
   double l_unit = 1.0;  // cm per internal length unit (= r_faces[0])
   double Tstar = 0, Rstar = 0, Lstar = 0;
+  // internal sources (viscous heating): cumulative luminosity over the cells on the device, their total
+  double Lsrc_total = 0;
+  mcrt::DBuf src_cum;
+  int n_src = 0;
+  double Lpkt() const { return Lstar + Lsrc_total; }  // luminosity the packets carry
   std::vector<double> rf, tf, rho, mass;
   std::vector<double> lam_e, kabs, ksca, g;
   // temperature grid

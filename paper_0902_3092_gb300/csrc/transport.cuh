@@ -76,7 +76,8 @@ struct Pkt {
   int pend_cell;
   float pend_u;
   int tslot, ntr;
-  int pend;  // 1: moved to an interaction point whose interaction has not run yet
+  int pend;  // 1: moved to an interaction point whose interaction has not run yet; 2: an internal
+            // source's packet waiting for its release
 };
 
 // packets that had taken this many steps when the queue drained go first in the tail kernel
@@ -374,13 +375,60 @@ __device__ __forceinline__ void set_alpha(const DevModel<R>& M, Pkt<R>& s) {
   s.ialpha = s.alpha > (R)0 ? (R)1 / s.alpha : (R)0;
 }
 
-template <class R, bool TRACE, class RNG>
+template <class R, bool TRACE, bool G, class RNG>
 __device__ __forceinline__ void launch_packet(const KParams<R>& P, RNG& rng, const DevModel<R>& M, Pkt<R>& s,
                               unsigned long long k, int tslot, Acc& acc) {
   s.model = M.model_id;
   s.plo = (uint32_t)k;
   s.phi = (uint32_t)(k >> 32);
   s.blk = 0;
+  if (M.n_src) {
+    // internal sources (viscous heating, Sect. 5): a first block picks the star or a cell in proportion
+    // to the luminosities (one 46-bit uniform from two words) and the point in the cell
+    const uint4 v = rng.next(s);
+    const double us = (to_uniform<double>(v.x) - 0x1p-24) + to_uniform<double>(v.y) * 0x1p-23;
+    const double t = us * M.src_Ltot;
+    if (t >= M.src_Lstar) {
+      const double tt = t - M.src_Lstar;
+      int lo = 0, hi = M.n_src - 1;  // the first cell whose cumulative luminosity passes tt
+      while (lo < hi) {
+        const int mid = (lo + hi) >> 1;
+        if (M.src_cum[mid + 1] > tt) hi = mid; else lo = mid + 1;
+      }
+      int c = lo;
+      while (c > 0 && !(M.src_cum[c + 1] > M.src_cum[c])) --c;  // rounding past the end: the last source
+      const int ir = c / M.nt, it = c - ir * M.nt;
+      // uniform in the cell's volume: r^3 and cos(theta) uniform across the cell, azimuth 0
+      const R r1 = M.rf[ir], r2 = M.rf[ir + 1];
+      const R rr = cbrt(r1 * r1 * r1 + uni<R>(v.z) * (r2 * r2 * r2 - r1 * r1 * r1));
+      const R c1 = M.cf[it], c2 = M.cf[it + 1];
+      const R mu = c1 + uni<R>(v.w) * (c2 - c1);
+      s.px = rr * sqrt((R)1 - mu * mu);
+      s.py = (R)0;
+      s.pz = rr * mu;
+      s.ux = (R)0;
+      s.uy = (R)0;
+      s.uz = (R)1;
+      s.ir = ir;
+      s.it = it;
+      s.lam = 0;
+      s.ninc = 0;
+      s.events = 0;
+      s.steps = 0;
+      s.xcross = 0;
+      s.dsafe = (R)0;
+      set_alpha<R, G>(M, s);
+      s.pend_mode = 0;
+      s.tslot = tslot;
+      s.ntr = 0;
+      s.tau = (R)0;
+      s.pend = 2;  // the next event releases the packet: an absorption with omega = 0 at this point
+      if (lead<RNG>()) atomicAdd(M.visits + c, 1ull);
+      trace_ev<R, TRACE>(P, s, EV_LAUNCH, c);
+      acc.packets++;
+      return;
+    }
+  }
   const uint4 w = rng.next(s);  // stellar bin, direction, first optical depth
   s.lam = sample_star(M, uni<R>(w.x));
   iso_dir<R>(w.y, w.z, s.ux, s.uy, s.uz);
@@ -577,12 +625,14 @@ __device__ __forceinline__ int advance(const KParams<R>& P, RNG& rng, const DevM
 }
 
 // The interaction at the packet's current point (Sect. 2.1): scattering or absorption with immediate
-// re-emission, then the MRW chain (Sect. 2.2.2) and the next optical depth. False: capped.
+// re-emission, then the MRW chain (Sect. 2.2.2) and the next optical depth. A release (the first event
+// of an internal source's packet) is an absorption with omega = 0. False: capped.
 template <class R, bool TRACE, bool G, class RNG>
-__device__ __forceinline__ bool interact(const KParams<R>& P, RNG& rng, const DevModel<R>& M, Pkt<R>& s, Acc& acc) {
+__device__ __forceinline__ bool interact(const KParams<R>& P, RNG& rng, const DevModel<R>& M, Pkt<R>& s, Acc& acc,
+                                         bool release = false) {
   const int c = s.ir * M.nt + s.it;
   const uint4 w = rng.next(s);  // albedo test, new direction, next optical depth
-  const R om = (G || M.gray) ? M.alb0 : M.alb[s.lam];
+  const R om = release ? (R)0 : ((G || M.gray) ? M.alb0 : M.alb[s.lam]);
   const R a = uni<R>(w.x);
   const bool sca = a < om;
   const R g = sca ? ((G || M.gray) ? M.g0 : M.gq[s.lam]) : (R)0;
@@ -641,8 +691,9 @@ __device__ __forceinline__ bool interact(const KParams<R>& P, RNG& rng, const De
 template <class R, bool TRACE, bool G, class RNG>
 __device__ __forceinline__ bool step(const KParams<R>& P, RNG& rng, const DevModel<R>& M, Pkt<R>& s, Acc& acc) {
   if (s.pend) {
+    const bool release = s.pend == 2;
     s.pend = 0;
-    return interact<R, TRACE, G>(P, rng, M, s, acc);
+    return interact<R, TRACE, G>(P, rng, M, s, acc, release);
   }
   const int r = advance<R, TRACE, G>(P, rng, M, s, acc);
   if (r == 2) return interact<R, TRACE, G>(P, rng, M, s, acc);
@@ -939,7 +990,7 @@ __global__ void __launch_bounds__(256, transport_min_blocks<R>()) transport_kern
             const DevModel<R>& M = BATCH ? P.models[m] : P.m0;
             const unsigned long long local = q - M.q_begin;
             const int tslot = (TRACE && local < (unsigned long long)P.trace_n) ? (int)local : -1;
-            launch_packet<R, TRACE>(P, rng, M, s, M.first_id + local, tslot, acc);
+            launch_packet<R, TRACE, G>(P, rng, M, s, M.first_id + local, tslot, acc);
             active = true;
           } else {
             done = true;
@@ -985,8 +1036,9 @@ __global__ void __launch_bounds__(256, transport_min_blocks<R>()) transport_kern
       const unsigned moving = __ballot_sync(0xffffffffu, active && !s.pend);
       if (__popc(waiting) >= P.defer || !moving) {
         if (active && s.pend) {
+          const bool release = s.pend == 2;
           s.pend = 0;
-          if (!interact<R, TRACE, G>(P, rng, M, s, acc)) {
+          if (!interact<R, TRACE, G>(P, rng, M, s, acc, release)) {
             active = false;
             note_end(s, acc);
           }

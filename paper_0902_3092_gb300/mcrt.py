@@ -25,7 +25,7 @@ EXPORTS = ["mcrt_disk_create", "mcrt_set_opacity", "mcrt_default_run_opts", "mcr
            "mcrt_pda_solve_static", "mcrt_disk_info", "mcrt_launch_count", "mcrt_last_error",
            "mcrt_disk_destroy", "mcrt_batch_create", "mcrt_batch_run", "mcrt_batch_config", "mcrt_batch_destroy",
            "mcrt_default_hydro_opts", "mcrt_hydrostatic_density", "mcrt_set_density", "mcrt_set_rays",
-           "mcrt_raytrace", "mcrt_visibilities"]
+           "mcrt_raytrace", "mcrt_visibilities", "mcrt_set_sources"]
 
 
 class McrtError(RuntimeError):
@@ -121,6 +121,7 @@ def lib():
         "mcrt_hydrostatic_density": (st, [P, C.POINTER(HydroOpts), pd]),
         "mcrt_set_density": (st, [P, pd]),
         "mcrt_set_rays": (st, [P, C.c_double, C.c_double, C.c_int64, pd, pd, pd]),
+        "mcrt_set_sources": (st, [P, pd]),
         "mcrt_raytrace": (st, [P, C.c_int, C.c_int, pd, pd, pd, pu]),
         "mcrt_visibilities": (st, [P, C.c_int, pi, pd, pd, C.c_int, pd]),
     }
@@ -254,6 +255,17 @@ class Disk:
         _check(lib().mcrt_hydrostatic_density(self._h, C.byref(o), _dp(out)), self._h)
         return out.reshape(self.nr, self.ntheta)
 
+    def set_sources(self, L_cell=None):
+        """Internal source luminosity per cell (erg/s, nr x ntheta; None: none), e.g. viscous heating
+        from disks.viscous_sources; resets the tallies."""
+        if L_cell is None:
+            _check(lib().mcrt_set_sources(self._h, None), self._h)
+            self.L_src = 0.0
+            return
+        L = np.ascontiguousarray(L_cell, np.float64).ravel()
+        _check(lib().mcrt_set_sources(self._h, _dp(L)), self._h)
+        self.L_src = float(L.sum())
+
     def set_density(self, rho):
         """Replaces the density (g/cm^3) and resets the tallies."""
         r = np.ascontiguousarray(rho, np.float64).ravel()
@@ -330,7 +342,8 @@ class Disk:
         F_star, segments (ray segments through dust) and, with want_image, I (rays x bins intensities,
         erg/s/cm^2/sr per bin)."""
         F, Fs = np.zeros(self.nlam), np.zeros(self.nlam)
-        n = len(self._rays[0])
+        rays = getattr(self, "_rays", None)
+        n = len(rays[0]) if rays is not None else 0
         I = np.zeros(n * self.nlam) if want_image else None
         seg = np.zeros(1, np.uint64)
         _check(lib().mcrt_raytrace(self._h, int(which), int(precision), _dp(F), _dp(Fs),
