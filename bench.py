@@ -434,7 +434,7 @@ def viscous_timing(args):
     """Viscous heating (Sect. 5): packets released inside the 200 x 120 rim-refined tau_mid = 1e6 gray
     disk by the steady accretion dissipation of disks.viscous_sources (scaled to 1e4 L* so that the
     star's packets are 1e-4 of all), transported with MRW (gamma = 1, the paper's setting) and, for
-    comparison, without it under a 1e6-event cap. Timed: reset + transport of 1e6 packets per step with
+    comparison, without it under a 1e6-event cap. Timed: reset + transport of 2e5 packets per step with
     CUDA events on the disk's stream."""
     import torch
     from paper_0902_3092_gb300 import disks, mcrt
@@ -444,9 +444,9 @@ def viscous_timing(args):
     st = torch.cuda.Stream()
     g = mcrt.Disk.from_model(d, stream=st.cuda_stream)
     g.set_sources(L)
-    n = 1_000_000
+    n = 200_000
     cap = 10 ** 6
-    g.run_photons(100_000, seed=99, mrw=True, gamma=1.0, max_events=cap, want_sed=False)
+    g.run_photons(20_000, seed=99, mrw=True, gamma=1.0, max_events=cap, want_sed=False)
     times, stats = [], None
     with ClockSampler(physical_gpu(0)) as clk:
         for k in range(args.warmup + args.steps):
