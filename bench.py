@@ -342,10 +342,12 @@ def pda_adjoint_timing(args):
 
 
 # issue-slot work of the ray-tracing kernel: warp instructions per ray segment through dust (ncu
-# smsp__inst_executed of k_raytrace<float, 4> on the 200x120 disk at 45 degrees, 4.577e9, over its
-# 17,980,808 segments; the count includes the crossings of dust-free cells, 40 % of all crossings)
-RAY_WARP_INST_PER_SEG = 254.6
-RAY_DRAM_BYTES = 7541504 + 35840  # dram__bytes_read.sum + dram__bytes_write.sum of the same launch
+# smsp__inst_executed of k_raytrace<float, 25> on the 200x120 disk at 45 degrees, 2.765e9, over its
+# 17,980,808 segments; the count includes the crossings of dust-free cells, 40 % of all crossings, and
+# the four marches of each ray, one per chunk of 25 wavelength bins)
+RAY_WARP_INST_PER_SEG = 153.8
+RAY_THREAD_INST_PER_SEG = 2835.5  # smsp__thread_inst_executed (5.098e10) over the same segments
+RAY_DRAM_BYTES = 14522624 + 6551040  # dram__bytes_read.sum + dram__bytes_write.sum of the same launch
 
 
 def raytrace_timing(args):
@@ -393,12 +395,14 @@ def raytrace_timing(args):
     clocks = clk.summary()
     mhz = clocks["sm_mhz"] or 2070.0
     issue_peak = 152 * 4 * mhz * 1e6
-    roof = {"bound": "alu", "unit": "warp-inst/s", "kernel": "k_raytrace<float, 4> (+ k_star, k_sed_part, k_sed_final)"}
+    roof = {"bound": "alu", "unit": "warp-inst/s", "kernel": "k_raytrace<float, 25> (+ k_star, k_sed_part, k_sed_final)"}
     if RAY_WARP_INST_PER_SEG:
         ach = RAY_WARP_INST_PER_SEG * seg / t
         roof.update({"achieved": ach, "peak": issue_peak, "frac": ach / issue_peak, "traffic": RAY_DRAM_BYTES,
+                     "thread_inst_frac": RAY_THREAD_INST_PER_SEG * seg / t / (32 * issue_peak),
                      "note": f"issue-slot roofline: {RAY_WARP_INST_PER_SEG} warp instructions per segment (ncu) x "
-                             f"{seg} segments / CUDA-event call time; peak = 152 SMs x 4 schedulers x SM clock"})
+                             f"{seg} segments / CUDA-event call time; peak = 152 SMs x 4 schedulers x SM clock; "
+                             "thread_inst_frac counts active lanes"})
     else:
         roof.update({"achieved": None, "peak": issue_peak, "frac": None, "traffic": None})
     # the oracle on the host cores: rays one by one for about ten seconds

@@ -9,15 +9,18 @@
 // carried towards the observer exactly: I <- S + (I - S) exp(-dtau). The star is a point source at the
 // origin, dimmed along the radial line towards the observer, and occults no ray.
 //
-// Layout: one warp per ray, the 32 lanes over the wavelength bins (nlam <= 256: up to 8 bins per lane,
-// intensities in registers); every lane marches the same cells (raymarch.cuh: closed-form crossings, one
-// square root and at most one quadratic per cell), so the march costs one warp instruction stream per
-// ray and the per-bin work runs on all lanes. The source table S[cell][bin] is read one row (nlam
-// contiguous values) per segment.
+// Layout: one thread per ray and chunk of up to 25 wavelength bins (intensities and extinctions in
+// registers); the thread marches its ray (raymarch.cuh: closed-form crossings, one square root or one
+// quadratic per cell) and reads CH contiguous values of the source table row S[cell][bin] per segment.
+// Consecutive threads take neighbouring rays of one ring, whose paths are alike.
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cmath>
+#include <cstdlib>
 #include <cstring>
+#include <utility>
+#include <vector>
 
 #include "internal.h"
 #include "planck.cuh"
@@ -27,6 +30,7 @@ namespace mcrt {
 
 struct RayState {
   DBuf p, q, w;   // rays: sky-plane coordinates (cm) and areas (cm^2), FP64
+  DBuf order;     // the rays in Morton order of their sky positions (int32): neighbours share warps
   long long n = 0;
   double incl = 0, dist = 0;
   DBuf S;         // cells x nlam source table of the last trace (float or double)
@@ -92,62 +96,87 @@ __device__ __forceinline__ double segment<double>(double I, double s, double x) 
   return exp(-x) * I - expm1(-x) * s;
 }
 
-// One warp per ray (grid-stride over rays). The cells and path lengths come from march_ray (closed-form
-// crossings of the straight ray with the spheres and cones); every lane marches the same ray and applies
-// the segment to its own wavelength bins. cnt[0] += segments with dust, cnt[1] |= 1 when a ray took more
-// events than the bound.
-template <class R, int NPL>
+// One thread per (ray, chunk of CH wavelength bins), grid-stride over the items, consecutive threads on
+// consecutive rays of the same chunk. Each thread marches its ray (march_ray: closed-form crossings of
+// the straight ray with the spheres and cones) and applies every segment to its CH bins, whose
+// intensities and extinctions stay in registers; a ray with nlam bins is marched ceil(nlam / CH) times.
+// Per bin the sequence of segment updates is the same for any chunking. cnt[0] += segments with dust
+// (counted by chunk 0), cnt[1] |= 1 when a ray took more events than the bound.
+template <class R, int CH>
 __global__ void __launch_bounds__(kRayBlock) k_raytrace(const DevModel<R> M, const R* __restrict__ chi,
-                                                        const R* __restrict__ S, long long n,
+                                                        const R* __restrict__ S, long long n, int nchunk,
+                                                        const int* __restrict__ order,
                                                         const double* __restrict__ p, const double* __restrict__ q,
                                                         double inv_l, R si, R ci, int max_events,
                                                         R* __restrict__ img, unsigned long long* __restrict__ cnt) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   FaceCoef<R>* face = reinterpret_cast<FaceCoef<R>*>(smem_raw);  // nt+1 entries for this inclination
+  R* chs = reinterpret_cast<R*>(smem_raw + (size_t)(M.nt + 1) * sizeof(FaceCoef<R>));  // nlam extinctions
   for (int j = threadIdx.x; j <= M.nt; j += blockDim.x) face[j] = face_coef<R>(M.c2[j], M.s2[j], M.fk[j], si, ci);
+  for (int b = threadIdx.x; b < M.nlam; b += blockDim.x) chs[b] = chi[b];
   __syncthreads();
-  const int lane = threadIdx.x & 31;
-  const long long nw = ((long long)gridDim.x * blockDim.x) >> 5;
   const int nlam = M.nlam, nt = M.nt;
   const RayGrid<R> G{M.nr, M.nt, M.rf2, M.cf, face};
-  R ch[NPL];
-#pragma unroll
-  for (int k = 0; k < NPL; ++k) {
-    const int b = lane + 32 * k;
-    ch[k] = b < nlam ? chi[b] : (R)0;
-  }
+  const long long items = n * nchunk;
   unsigned long long segs = 0;
   bool err = false;
-  for (long long ray = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5; ray < n; ray += nw) {
-    R I[NPL];
+  for (long long w = (long long)blockIdx.x * blockDim.x + threadIdx.x; w < items;
+       w += (long long)gridDim.x * blockDim.x) {
+    const int chunk = (int)(w / n);
+    const long long ray = order[w - (long long)chunk * n];
+    const int b0 = chunk * CH;
+    R I[CH], ch[CH];
 #pragma unroll
-    for (int k = 0; k < NPL; ++k) I[k] = (R)0;
+    for (int k = 0; k < CH; ++k) {
+      I[k] = (R)0;
+      ch[k] = b0 + k < nlam ? chs[b0 + k] : (R)0;
+    }
     const int rc = march_ray(G, (R)(p[ray] * inv_l), (R)(q[ray] * inv_l), si, ci, max_events,
                              [&](int ir, int it, R L) {
                                const int c = ir * nt + it;
                                const R a = M.rho[c] * L;  // optical depth per unit chi
                                if (a > (R)0) {
-                                 const R* Sc = S + (size_t)c * nlam;
+                                 const R* Sc = S + (size_t)c * nlam + b0;
 #pragma unroll
-                                 for (int k = 0; k < NPL; ++k) {
-                                   const int b = lane + 32 * k;
-                                   if (b < nlam) I[k] = segment<R>(I[k], Sc[b], a * ch[k]);
-                                 }
-                                 ++segs;
+                                 for (int k = 0; k < CH; ++k)
+                                   if (b0 + k < nlam) I[k] = segment<R>(I[k], Sc[k], a * ch[k]);
+                                 segs += chunk == 0;
                                }
                              });
     if (rc < 0) err = true;
-    R* o = img + (size_t)ray * nlam;
+    R* o = img + (size_t)ray * nlam + b0;
 #pragma unroll
-    for (int k = 0; k < NPL; ++k) {
-      const int b = lane + 32 * k;
-      if (b < nlam) o[b] = I[k];
+    for (int k = 0; k < CH; ++k)
+      if (b0 + k < nlam) o[k] = I[k];
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) segs += __shfl_xor_sync(0xffffffffu, segs, o);
+  const bool any_err = __any_sync(0xffffffffu, err);
+  if ((threadIdx.x & 31) == 0) {
+    if (segs) atomicAdd(cnt, segs);
+    if (any_err) atomicOr(cnt + 1, 1ull);
+  }
+}
+
+// bins per thread for nlam bins: the candidate that minimises chunks x (bins + a march's worth of work);
+// the environment variable MCRT_RAY_CHUNK (4, 8, 16, 20 or 25) overrides the choice, for tuning
+inline int ray_chunk(int nlam) {
+  const int cand[5] = {4, 8, 16, 20, 25};
+  if (const char* env = std::getenv("MCRT_RAY_CHUNK")) {
+    const int v = std::atoi(env);
+    for (int c : cand)
+      if (v == c) return c;
+  }
+  int best = 25;
+  long long cost = -1;
+  for (int c : cand) {
+    const long long k = ((long long)nlam + c - 1) / c * (c + 6);
+    if (cost < 0 || k < cost) {
+      cost = k;
+      best = c;
     }
   }
-  if (lane == 0) {
-    if (segs) atomicAdd(cnt, segs);
-    if (err) atomicOr(cnt + 1, 1ull);
-  }
+  return best;
 }
 
 // Flux of the star per bin at distance d: pi R*^2 Bbar_b(T*) / d^2, dimmed by chi_b times the column
@@ -256,49 +285,39 @@ int sm_count(int device) {
   return v > 0 ? v : 1;
 }
 
-template <class R>
-cudaError_t launch_trace(mcrt_disk* d, RayState* rs, const DevModel<R>& M, const R* chi, int grid) {
+template <class R, int CH>
+cudaError_t launch_trace_ch(mcrt_disk* d, RayState* rs, const DevModel<R>& M, const R* chi, int sms) {
   const R si = (R)std::sin(rs->incl), ci = (R)std::cos(rs->incl);
   const int max_events = 4 * (d->nr + d->nt) + 64;
   const double inv_l = 1.0 / d->l_unit;
-  const R* S = rs->S.as<R>();
-  R* img = rs->img.as<R>();
-  auto* cnt = rs->cnt.as<unsigned long long>();
-  const double* p = rs->p.as<double>();
-  const double* q = rs->q.as<double>();
-  const int npl = (d->nlam + 31) / 32;
-  const size_t smem = (size_t)(d->nt + 1) * sizeof(FaceCoef<R>);
-#define MCRT_TRACE_CASE(K)                                                                                 \
-  case K:                                                                                                  \
-    if (smem > 48 * 1024) {                                                                                \
-      cudaError_t e = cudaFuncSetAttribute(k_raytrace<R, K>, cudaFuncAttributeMaxDynamicSharedMemorySize,  \
-                                           (int)smem);                                                     \
-      if (e != cudaSuccess) return e;                                                                      \
-    }                                                                                                      \
-    k_raytrace<R, K><<<grid, kRayBlock, smem, d->stream>>>(M, chi, S, rs->n, p, q, inv_l, si, ci, max_events, \
-                                                        img, cnt);                                         \
-    break;
-  switch (npl) {
-    MCRT_TRACE_CASE(1)
-    MCRT_TRACE_CASE(2)
-    MCRT_TRACE_CASE(3)
-    MCRT_TRACE_CASE(4)
-    MCRT_TRACE_CASE(5)
-    MCRT_TRACE_CASE(6)
-    MCRT_TRACE_CASE(7)
-    MCRT_TRACE_CASE(8)
-    default:
-      return cudaErrorInvalidValue;
+  const int nchunk = (d->nlam + CH - 1) / CH;
+  const size_t smem = (size_t)(d->nt + 1) * sizeof(FaceCoef<R>) + (size_t)d->nlam * sizeof(R);
+  if (smem > 48 * 1024) {
+    cudaError_t e = cudaFuncSetAttribute(k_raytrace<R, CH>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
   }
-#undef MCRT_TRACE_CASE
+  int per_sm = 0;
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_raytrace<R, CH>, kRayBlock, smem);
+  long long grid = (long long)sms * (per_sm > 0 ? per_sm : 1);
+  const long long need = (rs->n * nchunk + kRayBlock - 1) / kRayBlock;
+  if (grid > need) grid = need;
+  if (grid < 1) grid = 1;
+  k_raytrace<R, CH><<<(int)grid, kRayBlock, smem, d->stream>>>(M, chi, rs->S.as<R>(), rs->n, nchunk,
+                                                               rs->order.as<int>(), rs->p.as<double>(), rs->q.as<double>(), inv_l, si, ci,
+                                                               max_events, rs->img.as<R>(),
+                                                               rs->cnt.as<unsigned long long>());
   return cudaGetLastError();
 }
 
 template <class R>
-int trace_blocks_per_sm(size_t smem) {
-  int v = 0;
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&v, k_raytrace<R, 4>, kRayBlock, smem);
-  return v > 0 ? v : 1;
+cudaError_t launch_trace(mcrt_disk* d, RayState* rs, const DevModel<R>& M, const R* chi, int sms) {
+  switch (ray_chunk(d->nlam)) {
+    case 4: return launch_trace_ch<R, 4>(d, rs, M, chi, sms);
+    case 8: return launch_trace_ch<R, 8>(d, rs, M, chi, sms);
+    case 16: return launch_trace_ch<R, 16>(d, rs, M, chi, sms);
+    case 20: return launch_trace_ch<R, 20>(d, rs, M, chi, sms);
+    default: return launch_trace_ch<R, 25>(d, rs, M, chi, sms);
+  }
 }
 
 }  // namespace
@@ -345,14 +364,9 @@ mcrt_status trace_impl(mcrt_disk* d, int which) {
   if (rs->img.n < img_bytes) CK(rs->img.alloc(img_bytes), "cudaMalloc");
   CK(cudaMemsetAsync(rs->cnt.p, 0, 2 * sizeof(unsigned long long), d->stream), "memset");
   const int sms = sm_count(d->device);
-  const long long warps_needed = rs->n;
-  const size_t smem = (size_t)(d->nt + 1) * sizeof(FaceCoef<R>);
+  const size_t smem = (size_t)(d->nt + 1) * sizeof(FaceCoef<R>) + (size_t)nlam * sizeof(R);
   if (smem > 200 * 1024) return set_error(d, MCRT_EINVAL, "too many polar cells for the ray-tracing face table");
-  long long grid = (long long)sms * trace_blocks_per_sm<R>(smem);
-  const long long need = (warps_needed * 32 + kRayBlock - 1) / kRayBlock;
-  if (grid > need) grid = need;
-  if (grid < 1) grid = 1;
-  CK(launch_trace<R>(d, rs, model_of<R>(d), chi_of<R>(d), (int)grid), "ray-trace kernel");
+  CK(launch_trace<R>(d, rs, model_of<R>(d), chi_of<R>(d), sms), "ray-trace kernel");
   d->launches++;
   rs->img_prec = prec;
   rs->have_img = true;
@@ -402,6 +416,24 @@ mcrt_status mcrt_set_rays(mcrt_disk* d, double incl_rad, double dist_cm, int64_t
   if (!rs->F.p) CK(rs->F.alloc(256 * 8), "cudaMalloc");
   if (!rs->Fs.p) CK(rs->Fs.alloc(256 * 8), "cudaMalloc");
   if (!rs->cnt.p) CK(rs->cnt.alloc(2 * 8), "cudaMalloc");
+  // Morton order of the sky positions (16 bits per axis over the square of side 2 r_out): consecutive
+  // threads take neighbouring rays, whose paths cross the same cells
+  std::vector<std::pair<uint32_t, int>> key((size_t)n);
+  const double rmax = d->rf[d->nr];
+  for (int64_t k = 0; k < n; ++k) {
+    auto quant = [&](double x) {
+      const double t = std::min(std::max((x / rmax + 1.0) * 0.5, 0.0), 1.0);
+      return (uint32_t)std::min(65535.0, std::floor(t * 65536.0));
+    };
+    uint32_t x = quant(p_cm[k]), y = quant(q_cm[k]), m = 0;
+    for (int bit = 0; bit < 16; ++bit) m |= ((x >> bit) & 1u) << (2 * bit) | ((y >> bit) & 1u) << (2 * bit + 1);
+    key[(size_t)k] = {m, (int)k};
+  }
+  std::stable_sort(key.begin(), key.end(), [](const auto& u, const auto& v) { return u.first < v.first; });
+  std::vector<int> order((size_t)n);
+  for (int64_t k = 0; k < n; ++k) order[(size_t)k] = key[(size_t)k].second;
+  if (rs->order.n < (size_t)n * 4) CK(rs->order.alloc((size_t)n * 4), "cudaMalloc");
+  CK(cudaMemcpyAsync(rs->order.p, order.data(), (size_t)n * 4, cudaMemcpyHostToDevice, d->stream), "copy");
   CK(cudaMemcpyAsync(rs->p.p, p_cm, bytes, cudaMemcpyHostToDevice, d->stream), "copy");
   CK(cudaMemcpyAsync(rs->q.p, q_cm, bytes, cudaMemcpyHostToDevice, d->stream), "copy");
   CK(cudaMemcpyAsync(rs->w.p, w_cm2, bytes, cudaMemcpyHostToDevice, d->stream), "copy");
