@@ -12,7 +12,8 @@
 // Layout: one thread per ray and chunk of up to 25 wavelength bins (intensities and extinctions in
 // registers); the thread marches its ray (raymarch.cuh: closed-form crossings, one square root or one
 // quadratic per cell) and reads CH contiguous values of the source table row S[cell][bin] per segment.
-// Consecutive threads take neighbouring rays of one ring, whose paths are alike.
+// Consecutive threads take rays that are neighbours on the sky (Morton order of the sky positions, built
+// by mcrt_set_rays), whose paths cross the same cells.
 #include <cuda_runtime.h>
 
 #include <algorithm>
