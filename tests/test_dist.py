@@ -16,7 +16,13 @@ def _free_port():
     return p
 
 
-def _rank(rank, world, port, out):
+def _sources(d):
+    from paper_0902_3092_gb300 import disks
+    L = disks.viscous_sources(d)
+    return L * (2.0 * d.star.L / L.sum())
+
+
+def _rank(rank, world, port, out, with_sources=False):
     import torch.distributed as dist
 
     from oracle import oracle as O
@@ -28,7 +34,8 @@ def _rank(rank, world, port, out):
     d = disks.config_plain_gray(12, 12, 50.0)
     per = 1500
     first, n = D.packet_range(rank, world, per)
-    r = O.Run(d).run(n, seed=3, first_id=first, n_total=per * world, want_sed=True)
+    src = _sources(d) if with_sources else None
+    r = O.Run(d, sources=src).run(n, seed=3, first_id=first, n_total=per * world, want_sed=True)
     blob = D.make_blob(d.nr, d.ntheta, d.opacity.nlam, r.tally, r.visits, r.nabs, r.sed, n, per * world)
     red = D.allreduce_blob(blob)
     if rank == 0:
@@ -37,7 +44,10 @@ def _rank(rank, world, port, out):
     dist.destroy_process_group()
 
 
-def test_two_rank_tally_allreduce_is_exact():
+@pytest.mark.parametrize("with_sources", [False, True])
+def test_two_rank_tally_allreduce_is_exact(with_sources):
+    """Also with internal sources (viscous heating): the source choices come from each packet's own
+    counter-based stream, so sharding by packet id changes nothing."""
     from oracle import oracle as O
     from paper_0902_3092_gb300 import disks
     from paper_0902_3092_gb300 import dist as D
@@ -45,7 +55,7 @@ def test_two_rank_tally_allreduce_is_exact():
     ctx = mp.get_context("spawn")
     q = ctx.Queue()
     port = _free_port()
-    ps = [ctx.Process(target=_rank, args=(r, 2, port, q)) for r in range(2)]
+    ps = [ctx.Process(target=_rank, args=(r, 2, port, q, with_sources)) for r in range(2)]
     for p in ps:
         p.start()
     red = q.get(timeout=120)
@@ -54,7 +64,8 @@ def test_two_rank_tally_allreduce_is_exact():
         assert p.exitcode == 0
     hdr, body = D.split_blob(red)
     d = disks.config_plain_gray(12, 12, 50.0)
-    ref = O.Run(d).run(3000, seed=3, first_id=0, n_total=3000, want_sed=True)
+    ref = O.Run(d, sources=_sources(d) if with_sources else None).run(3000, seed=3, first_id=0, n_total=3000,
+                                                                         want_sed=True)
     n = d.nr * d.ntheta
     assert int(hdr[5]) == 3000
     assert np.array_equal(body[:n], ref.tally)

@@ -90,3 +90,25 @@ def test_sweep_of_64_models(M):
             t, _, _ = g.tallies()
             assert int(t.sum(dtype=np.uint64)) == s["deposit_sum"]  # every deposit reached its model's tallies
     B.close()
+
+
+def test_batch_model_with_sources_equals_single_disk_run(M):
+    """A batched model that carries internal sources (viscous heating) draws its source choices from
+    the same Philox counters as a single-disk run: bitwise equal gray tallies (without the tail kernel)."""
+    a = disks.config_plain_gray(20, 20, 100.0)
+    L = disks.viscous_sources(a)
+    L *= 3.0 * a.star.L / L.sum()
+    ga = M.Disk.from_model(a)
+    ga.set_sources(L)
+    gb = M.Disk.from_model(disks.config_nongray(30, 24, 1e3))
+    B = M.Batch([ga, gb], [50_000, 30_000], mrw=True, gamma=2.0, max_events=10 ** 6, tail_warps=-1)
+    st = B.run(seed=5)
+    assert st[0]["packets"] == 50_000 and st[0]["escaped"] + st[0]["capped"] == 50_000
+    single = M.Disk.from_model(a)
+    single.set_sources(L)
+    single.run_photons(50_000, seed=5, mrw=True, gamma=2.0, max_events=10 ** 6, tail_warps=-1)
+    for x, y in zip(ga.tallies(), single.tallies()):
+        assert np.array_equal(x, y)
+    t, _, _ = ga.tallies()
+    assert int(t.sum()) == st[0]["deposit_sum"]
+    B.close()
