@@ -28,6 +28,11 @@
  *                interaction's MRW chain
  *   MRW jump:    two blocks: w0 escape-time quantile P, (w1, w2) point on the
  *                sphere, w3 exit bin; then (w0, w1) new direction, w2 and w3 unused
+ *   polarization: with a Mueller matrix (Sect. 2.3), a scattering takes w1 for the
+ *                scattering angle (inverse CDF of S11 sin theta on the table) and w2
+ *                for the azimuth of the scattering plane (inverse CDF of
+ *                1 + (S12/S11)(q cos 2phi + u sin 2phi)), in place of the direction
+ *                pair of the unpolarized case
  *   source:      only when the model has internal sources (viscous heating, Sect. 5):
  *                a block before the launch, w0 and w1 one uniform of 46 bits
  *                u = (w0 - 2^-24) + w1 2^-23 that picks the star (u L_tot < L_star)
@@ -221,6 +226,10 @@ typedef struct {
   const double *kabs, *ksca, *g; /* nlam */
   double Tstar, Rstar;
   const double *Lsrc; /* nr*nt internal source luminosity (erg/s) or NULL */
+  /* Mueller matrix per bin for polarized transport, or NULL: [nlam][4][nmu] = S11, S12, S33, S34 at the
+   * scattering angles theta_k = k pi / (nmu - 1); S22 = S11, S44 = S33 (Sect. 2.3) */
+  const double *mueller;
+  int nmu;
 } oracle_model;
 
 typedef struct {
@@ -237,6 +246,8 @@ typedef struct {
   uint64_t *visits; /* nr*nt packet entries */
   uint64_t *nabs;   /* nr*nt absorption events */
   uint64_t *sed;    /* nlam*NINC escaped packets [lam*NINC + incl] */
+  int64_t *sed_q, *sed_u; /* with a Mueller matrix: Stokes Q/I and U/I of the escaped packets in the sky
+                             frame (reference: the projected disk axis), 2^20 per packet, or NULL */
   double *Tcell;    /* nr*nt current temperature (K) */
   uint64_t cnt[10]; /* packets, events, absorptions, scatterings, crossings, mrw_jumps, capped, escaped,
                        deposit_sum_lo32-free (sum of per-packet deposits), error flags */
@@ -572,6 +583,132 @@ static double hg_mu(double g, double xi) {
   return fmin(1.0, fmax(-1.0, mu));
 }
 
+/* ------------------------------------------------------------------------- */
+/* Polarization: Stokes (q, u, v) = (Q, U, V) / I of a packet relative to a  */
+/* reference unit vector e perpendicular to its direction (Q > 0: E along e) */
+/* ------------------------------------------------------------------------- */
+#define OR_QUNIT 1048576.0 /* fixed-point Stokes tallies: 2^20 per packet */
+
+/* the reference of an unpolarized packet: the horizontal direction z x u (x - (x.u) u near the axis) */
+static void ref_perp(const double u[3], double e[3]) {
+  if (fabs(u[2]) < 0.999999) {
+    e[0] = -u[1];
+    e[1] = u[0];
+    e[2] = 0.0;
+  } else {
+    e[0] = 1.0 - u[0] * u[0];
+    e[1] = -u[0] * u[1];
+    e[2] = -u[0] * u[2];
+  }
+  double n = sqrt(e[0] * e[0] + e[1] * e[1] + e[2] * e[2]);
+  e[0] /= n; e[1] /= n; e[2] /= n;
+}
+
+/* Stokes in the frame whose reference is e turned by psi about u (e' = e cos psi + (u x e) sin psi). */
+static void rotate_stokes(double st[3], double psi) {
+  double c = cos(2.0 * psi), s = sin(2.0 * psi);
+  double q = st[0] * c + st[1] * s;
+  double uu = -st[0] * s + st[1] * c;
+  st[0] = q;
+  st[1] = uu;
+}
+
+/* Element k (0: S11, 1: S12, 2: S33, 3: S34) of bin table t at scattering angle th, linear in theta. */
+static double mueller_at(const double *t, int nmu, int k, double th) {
+  double x = th / OR_PI * (nmu - 1);
+  int j = (int)floor(x);
+  if (j < 0) j = 0;
+  if (j > nmu - 2) j = nmu - 2;
+  double f = x - j;
+  return (1.0 - f) * t[k * nmu + j] + f * t[k * nmu + j + 1];
+}
+
+/* Scattering angle from S11 sin(theta): cumulative by the trapezoid rule on the table's grid, inverted
+ * linearly in theta within the bracketing interval. */
+double oracle_pol_sample_theta(const double *S11, int nmu, double xi) {
+  double *c = (double *)malloc(sizeof(double) * nmu);
+  double h = OR_PI / (nmu - 1);
+  c[0] = 0.0;
+  for (int k = 1; k < nmu; ++k)
+    c[k] = c[k - 1] + 0.5 * h * (S11[k - 1] * sin((k - 1) * h) + S11[k] * sin(k * h));
+  double target = xi * c[nmu - 1], th = OR_PI;
+  for (int k = 1; k < nmu; ++k) {
+    if (c[k] >= target && c[k] > c[k - 1]) {
+      th = (k - 1) * h + (target - c[k - 1]) / (c[k] - c[k - 1]) * h;
+      break;
+    }
+  }
+  free(c);
+  return th;
+}
+
+/* Azimuth of the scattering plane from p(phi) = (1 + a (q cos 2phi + u sin 2phi)) / (2 pi): the root of
+ * F(phi) = phi / (2 pi) + a (q sin 2phi + u (1 - cos 2phi)) / (4 pi) = xi by Newton steps kept inside a
+ * bisection bracket (F rises monotonically from 0 to 1 on [0, 2 pi]). */
+double oracle_pol_sample_phi(double a, double q, double u, double xi) {
+  double lo = 0.0, hi = 2.0 * OR_PI, phi = 2.0 * OR_PI * xi;
+  for (int it = 0; it < 200; ++it) {
+    double F = phi / (2.0 * OR_PI) + a * (q * sin(2.0 * phi) + u * (1.0 - cos(2.0 * phi))) / (4.0 * OR_PI) - xi;
+    if (F > 0) hi = phi; else lo = phi;
+    double dF = (1.0 + a * (q * cos(2.0 * phi) + u * sin(2.0 * phi))) / (2.0 * OR_PI);
+    double nx = dF > 0 ? phi - F / dF : 0.5 * (lo + hi);
+    if (!(nx > lo && nx < hi)) nx = 0.5 * (lo + hi);
+    if (fabs(nx - phi) < 1e-13) { phi = nx; break; }
+    phi = nx;
+  }
+  return phi;
+}
+
+/* One scattering with bin table t: angle from w1, plane azimuth (measured from e about u) from w2; the
+ * Stokes vector is turned into the scattering plane, multiplied by the Mueller matrix and renormalised,
+ * and the new reference is the in-plane direction perpendicular to the new direction. */
+void oracle_pol_scatter(const double *t, int nmu, double u[3], double e[3], double st[3], double w1, double w2) {
+  double th = oracle_pol_sample_theta(t, nmu, w1);
+  double s11 = mueller_at(t, nmu, 0, th), s12 = mueller_at(t, nmu, 1, th);
+  double s33 = mueller_at(t, nmu, 2, th), s34 = mueller_at(t, nmu, 3, th);
+  double a = s11 > 0 ? s12 / s11 : 0.0;
+  double phi = oracle_pol_sample_phi(a, st[0], st[1], w2);
+  rotate_stokes(st, phi);
+  double cp = cos(phi), sp = sin(phi), ct = cos(th), sn = sin(th);
+  double uxe[3] = {u[1] * e[2] - u[2] * e[1], u[2] * e[0] - u[0] * e[2], u[0] * e[1] - u[1] * e[0]};
+  double ep[3], un[3], en[3];
+  for (int d = 0; d < 3; ++d) ep[d] = e[d] * cp + uxe[d] * sp;
+  for (int d = 0; d < 3; ++d) un[d] = u[d] * ct + ep[d] * sn;
+  for (int d = 0; d < 3; ++d) en[d] = ep[d] * ct - u[d] * sn;
+  double nu = sqrt(un[0] * un[0] + un[1] * un[1] + un[2] * un[2]);
+  for (int d = 0; d < 3; ++d) un[d] /= nu;
+  double dot = en[0] * un[0] + en[1] * un[1] + en[2] * un[2];
+  for (int d = 0; d < 3; ++d) en[d] -= dot * un[d];
+  double ne = sqrt(en[0] * en[0] + en[1] * en[1] + en[2] * en[2]);
+  for (int d = 0; d < 3; ++d) { u[d] = un[d]; e[d] = en[d] / ne; }
+  double I = s11 + s12 * st[0];
+  double Q = s12 + s11 * st[0];
+  double U = s33 * st[1] + s34 * st[2];
+  double V = -s34 * st[1] + s33 * st[2];
+  if (I > 0) {
+    st[0] = Q / I; st[1] = U / I; st[2] = V / I;
+  } else {
+    st[0] = st[1] = st[2] = 0.0;
+  }
+}
+
+/* Stokes q, u of a packet in the sky frame of an observer along its direction u: the reference turned
+ * from e to the disk axis projected on the sky (north); unchanged along the axis itself. */
+void oracle_pol_observer(const double u[3], const double e[3], const double st[3], double *q, double *uu) {
+  double n[3] = {-u[2] * u[0], -u[2] * u[1], 1.0 - u[2] * u[2]};
+  double nn = sqrt(n[0] * n[0] + n[1] * n[1] + n[2] * n[2]);
+  double s[3] = {st[0], st[1], st[2]};
+  if (nn > 1e-12) {
+    for (int d = 0; d < 3; ++d) n[d] /= nn;
+    double uxe[3] = {u[1] * e[2] - u[2] * e[1], u[2] * e[0] - u[0] * e[2], u[0] * e[1] - u[1] * e[0]};
+    double c = e[0] * n[0] + e[1] * n[1] + e[2] * n[2];
+    double sn = uxe[0] * n[0] + uxe[1] * n[1] + uxe[2] * n[2];
+    rotate_stokes(s, atan2(sn, c));
+  }
+  *q = s[0];
+  *uu = s[1];
+}
+
 /* smallest b with cumulative(w) >= xi * total */
 static int sample_bins(const double *w, int n, double xi) {
   double tot = 0.0;
@@ -599,6 +736,7 @@ typedef struct {
   double *w, *w2; /* nlam scratch */
   double *star_w;
   double *src_cum; /* nr*nt+1 cumulative source luminosity, or NULL */
+  int pol;         /* Mueller matrix given: packets carry Stokes q, u, v and a reference vector */
 } ctx_t;
 
 static void trace(ctx_t *x, int tp, int *ntr, int type, int cell, const double p[3], int lam) {
@@ -650,8 +788,8 @@ static void deposit(ctx_t *x, int c, uint64_t units, uint64_t *pkt_dep) {
 }
 
 /* The chain of MRW jumps from the packet's point in cell (ir, it) while Eq. 11 holds (Sect. 2.2.2). */
-static void mrw_walk(ctx_t *x, or_rng *r, double p[3], double u[3], int *lam, int ir, int it, uint64_t *events,
-                     int tp, int *ntr, uint64_t *dep) {
+static void mrw_walk(ctx_t *x, or_rng *r, double p[3], double u[3], double e[3], double st[3], int *lam, int ir,
+                     int it, uint64_t *events, int tp, int *ntr, uint64_t *dep) {
   const oracle_model *m = x->m;
   const oracle_opts *o = x->o;
   oracle_state *s = x->st;
@@ -687,6 +825,10 @@ static void mrw_walk(ctx_t *x, or_rng *r, double p[3], double u[3], int *lam, in
     }
     double xl = ja[3];
     if (!x->gray || o->want_sed) *lam = exit_bin(x, s->Tcell[c], xl);
+    if (x->pol) { /* a diffusing packet leaves the sphere unpolarized */
+      st[0] = st[1] = st[2] = 0.0;
+      ref_perp(u, e);
+    }
     (*events)++;
     s->cnt[CNT_MRW]++;
     trace(x, tp, ntr, EV_MRW, c, p, *lam);
@@ -703,6 +845,7 @@ static void run_packet(ctx_t *x, uint64_t k, uint64_t seed, uint32_t model, int 
   int ntr = 0;
   uint64_t dep = 0, events = 0, crossings = 0;
   double p[3] = {0, 0, 0}, u[3], w[4];
+  double e[3] = {1, 0, 0}, st[3] = {0, 0, 0}; /* polarization: reference vector and Stokes q, u, v */
   int ir = -1, it = -1, ninc = 0, lam = 0;
   double tau = 0.0;
   int released = 0;
@@ -741,11 +884,12 @@ static void run_packet(ctx_t *x, uint64_t k, uint64_t seed, uint32_t model, int 
       s->Tcell[c] = Tnew;
       if (!x->gray || o->want_sed) lam = bw_bin(x, Told, Tnew, w[0]);
       iso_dir(w[1], w[2], u);
+      if (x->pol) ref_perp(u, e);
       s->cnt[CNT_ABS]++;
       trace(x, tp, &ntr, EV_ABSORB, c, p, lam);
       events++;
       ninc++;
-      if (o->mrw && ninc >= o->nmin) mrw_walk(x, &r, p, u, &lam, ir, it, &events, tp, &ntr, &dep);
+      if (o->mrw && ninc >= o->nmin) mrw_walk(x, &r, p, u, e, st, &lam, ir, it, &events, tp, &ntr, &dep);
       released = 1;
       if (events >= o->max_events) {
         s->cnt[CNT_CAPPED]++;
@@ -761,6 +905,7 @@ static void run_packet(ctx_t *x, uint64_t k, uint64_t seed, uint32_t model, int 
     U4(&r, w);
     lam = sample_bins(x->star_w, m->nlam, w[0]);
     iso_dir(w[1], w[2], u);
+    if (x->pol) ref_perp(u, e);
     trace(x, tp, &ntr, EV_LAUNCH, -1, p, lam);
     tau = -log(w[3]);
     s->cnt[CNT_PACKETS]++;
@@ -790,7 +935,11 @@ static void run_packet(ctx_t *x, uint64_t k, uint64_t seed, uint32_t model, int 
       /* interaction */
       double omega = m->ksca[lam] / chi;
       U4(&r, w);
-      if (w[0] < omega) {
+      if (w[0] < omega && x->pol) {
+        oracle_pol_scatter(m->mueller + (size_t)lam * 4 * m->nmu, m->nmu, u, e, st, w[1], w[2]);
+        s->cnt[CNT_SCA]++;
+        trace(x, tp, &ntr, EV_SCATTER, c, p, lam);
+      } else if (w[0] < omega) {
         double g = m->g[lam];
         if (g != 0.0) {
           double mu = hg_mu(g, w[1]);
@@ -812,13 +961,17 @@ static void run_packet(ctx_t *x, uint64_t k, uint64_t seed, uint32_t model, int 
         double xl = (w[0] - omega) / (1.0 - omega);
         if (!x->gray || o->want_sed) lam = bw_bin(x, Told, Tnew, xl);
         iso_dir(w[1], w[2], u);
+        if (x->pol) { /* re-emission is unpolarized */
+          st[0] = st[1] = st[2] = 0.0;
+          ref_perp(u, e);
+        }
         s->cnt[CNT_ABS]++;
         trace(x, tp, &ntr, EV_ABSORB, c, p, lam);
       }
       events++;
       ninc++;
       /* modified random walk, Sect. 2.2.2 */
-      if (o->mrw && ninc >= o->nmin) mrw_walk(x, &r, p, u, &lam, ir, it, &events, tp, &ntr, &dep);
+      if (o->mrw && ninc >= o->nmin) mrw_walk(x, &r, p, u, e, st, &lam, ir, it, &events, tp, &ntr, &dep);
       if (events >= o->max_events) {
         s->cnt[CNT_CAPPED]++;
         trace(x, tp, &ntr, EV_CAPPED, c, p, lam);
@@ -839,6 +992,12 @@ static void run_packet(ctx_t *x, uint64_t k, uint64_t seed, uint32_t model, int 
         int ib = (int)(az * OR_NINC);
         if (ib >= OR_NINC) ib = OR_NINC - 1;
         s->sed[lam * OR_NINC + ib]++;
+        if (x->pol) {
+          double qo, uo;
+          oracle_pol_observer(u, e, st, &qo, &uo);
+          s->sed_q[lam * OR_NINC + ib] += (int64_t)floor(qo * OR_QUNIT + 0.5);
+          s->sed_u[lam * OR_NINC + ib] += (int64_t)floor(uo * OR_QUNIT + 0.5);
+        }
         s->cnt[CNT_ESCAPED]++;
         trace(x, tp, &ntr, EV_ESCAPE, -1, p, lam);
         break;
@@ -867,6 +1026,7 @@ int oracle_run(const oracle_model *m, const oracle_opts *o, oracle_state *s, uin
   x.gray = is_gray(m);
   x.n_total = (double)n_total;
   x.Lpkt = oracle_packet_lum(m);
+  x.pol = m->mueller != NULL && m->nmu >= 2 && s->sed_q != NULL && s->sed_u != NULL;
   x.src_cum = NULL;
   if (m->Lsrc) {
     const int n = m->nr * m->nt;

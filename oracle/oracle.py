@@ -22,6 +22,9 @@ Sections, equations and the readings taken where the paper is silent:
 * Adjoint of the PDA solve: derivative of J = sum_i w_i T_i with respect to
   log rho_i and kappa_R,i (the Rosseland mean entering D), with the Monte Carlo
   boundary temperatures held fixed.
+* Internal sources (viscous heating, Sect. 5) and polarized transport with a full
+  Mueller matrix per scattering (Sect. 2.3): see mcrt_oracle.c; ray-traced
+  observables: raytrace.py; vertical structure: hydro.py.
 """
 from __future__ import annotations
 
@@ -59,7 +62,8 @@ class _Model(C.Structure):
                 ("rf", C.POINTER(C.c_double)), ("tf", C.POINTER(C.c_double)), ("rho", C.POINTER(C.c_double)),
                 ("lam_e", C.POINTER(C.c_double)), ("kabs", C.POINTER(C.c_double)),
                 ("ksca", C.POINTER(C.c_double)), ("g", C.POINTER(C.c_double)),
-                ("Tstar", C.c_double), ("Rstar", C.c_double), ("Lsrc", C.POINTER(C.c_double))]
+                ("Tstar", C.c_double), ("Rstar", C.c_double), ("Lsrc", C.POINTER(C.c_double)),
+                ("mueller", C.POINTER(C.c_double)), ("nmu", C.c_int)]
 
 
 class _Opts(C.Structure):
@@ -70,6 +74,7 @@ class _Opts(C.Structure):
 class _State(C.Structure):
     _fields_ = [("tally", C.POINTER(C.c_uint64)), ("visits", C.POINTER(C.c_uint64)),
                 ("nabs", C.POINTER(C.c_uint64)), ("sed", C.POINTER(C.c_uint64)),
+                ("sed_q", C.POINTER(C.c_int64)), ("sed_u", C.POINTER(C.c_int64)),
                 ("Tcell", C.POINTER(C.c_double)), ("cnt", C.c_uint64 * 10),
                 ("trace_packets", C.c_int), ("trace_max", C.c_int),
                 ("tr_type", C.POINTER(C.c_int32)), ("tr_cell", C.POINTER(C.c_int32)),
@@ -101,6 +106,10 @@ def lib():
                                  C.c_uint64, C.c_uint64, C.c_uint32]
         L.oracle_star_bin.restype = C.c_int; L.oracle_star_bin.argtypes = [C.POINTER(_Model), d]
         L.oracle_packet_lum.restype = d; L.oracle_packet_lum.argtypes = [C.POINTER(_Model)]
+        L.oracle_pol_sample_theta.restype = d; L.oracle_pol_sample_theta.argtypes = [pd, C.c_int, d]
+        L.oracle_pol_sample_phi.restype = d; L.oracle_pol_sample_phi.argtypes = [d, d, d, d]
+        L.oracle_pol_scatter.argtypes = [pd, C.c_int, pd, pd, pd, d, d]
+        L.oracle_pol_observer.argtypes = [pd, pd, pd, pd, pd]
         for f in ("oracle_cone_exit",):
             getattr(L, f).restype = d
             getattr(L, f).argtypes = [pd, pd, d, C.c_int]
@@ -129,7 +138,7 @@ def _ip(a):
 class Model:
     """Holds the arrays of a disk (keeps them alive for the C side)."""
 
-    def __init__(self, disk, sources=None):
+    def __init__(self, disk, sources=None, mueller=None):
         self.disk = disk
         self.rf = np.ascontiguousarray(disk.r_faces_cm, np.float64)
         self.tf = np.ascontiguousarray(disk.theta_faces, np.float64)
@@ -142,9 +151,14 @@ class Model:
         self.nr, self.nt, self.nlam = disk.nr, disk.ntheta, op.nlam
         # internal source luminosity per cell (erg/s; viscous heating), or none
         self.Lsrc = None if sources is None else np.ascontiguousarray(sources, np.float64).ravel()
+        # Mueller matrix per bin for polarized transport: (nlam, 4, nmu) = S11, S12, S33, S34 on
+        # theta_k = k pi / (nmu - 1), or none
+        self.mueller = None if mueller is None else np.ascontiguousarray(mueller, np.float64)
+        nmu = 0 if self.mueller is None else self.mueller.shape[-1]
         self.c = _Model(self.nr, self.nt, self.nlam, _dp(self.rf), _dp(self.tf), _dp(self.rho), _dp(self.lam_e),
                         _dp(self.kabs), _dp(self.ksca), _dp(self.g), disk.star.T_K, disk.star.R_cm,
-                        None if self.Lsrc is None else _dp(self.Lsrc))
+                        None if self.Lsrc is None else _dp(self.Lsrc),
+                        None if self.mueller is None else _dp(self.mueller), nmu)
 
     @property
     def ptr(self):
@@ -155,13 +169,15 @@ class Run:
     """Tallies of an oracle Monte Carlo run (may be continued: resume). sources: luminosity (erg/s) of
     internal sources per cell (viscous heating), released by absorption-like events (see mcrt_oracle.c)."""
 
-    def __init__(self, disk, sources=None):
-        self.model = Model(disk, sources)
+    def __init__(self, disk, sources=None, mueller=None):
+        self.model = Model(disk, sources, mueller)
         n = self.model.nr * self.model.nt
         self.tally = np.zeros(n, np.uint64)
         self.visits = np.zeros(n, np.uint64)
         self.nabs = np.zeros(n, np.uint64)
         self.sed = np.zeros(self.model.nlam * NINC, np.uint64)
+        self.sed_q = np.zeros(self.model.nlam * NINC, np.int64)
+        self.sed_u = np.zeros(self.model.nlam * NINC, np.int64)
         self.Tcell = np.zeros(n, np.float64)
         self.counters = np.zeros(10, np.uint64)
         self.trace = None
@@ -172,6 +188,8 @@ class Run:
         opts = _Opts(int(mrw), float(gamma), int(nmin), int(max_events), int(want_sed), int(mrw_exit_dir))
         st = _State()
         st.tally, st.visits, st.nabs, st.sed = _up(self.tally), _up(self.visits), _up(self.nabs), _up(self.sed)
+        st.sed_q = self.sed_q.ctypes.data_as(C.POINTER(C.c_int64))
+        st.sed_u = self.sed_u.ctypes.data_as(C.POINTER(C.c_int64))
         st.Tcell = _dp(self.Tcell)
         for i in range(10):
             st.cnt[i] = int(self.counters[i])
@@ -212,6 +230,14 @@ class Run:
         """Luminosity the packets carry (erg/s): the star plus the internal sources."""
         return float(lib().oracle_packet_lum(self.model.ptr))
 
+    def sed_stokes(self):
+        """Escaped luminosity per (wavelength bin, inclination bin) as Stokes I, Q, U (erg/s) in the sky
+        frame whose reference is the projected disk axis (Q > 0: polarized along it)."""
+        e = self.packet_lum / self.n_total
+        sh = (self.model.nlam, NINC)
+        return (self.sed.reshape(sh).astype(np.float64) * e, self.sed_q.reshape(sh) / 1048576.0 * e,
+                self.sed_u.reshape(sh) / 1048576.0 * e)
+
     def sed_lum(self):
         """Escaped luminosity per (wavelength bin, inclination bin), erg/s."""
         return self.sed.reshape(self.model.nlam, NINC).astype(np.float64) * self.packet_lum / self.n_total
@@ -232,6 +258,30 @@ def uniforms(seed, model, packet, n):
     out = np.zeros(n)
     lib().oracle_uniforms(seed, model, packet, n, _dp(out))
     return out
+
+
+def pol_sample_theta(S11, xi):
+    S11 = np.ascontiguousarray(S11, np.float64)
+    return float(lib().oracle_pol_sample_theta(_dp(S11), len(S11), float(xi)))
+
+
+def pol_sample_phi(a, q, u, xi):
+    return float(lib().oracle_pol_sample_phi(float(a), float(q), float(u), float(xi)))
+
+
+def pol_scatter(table, u, e, st, w1, w2):
+    """One polarized scattering (table: (4, nmu) Mueller elements of a bin); returns (u, e, st)."""
+    t = np.ascontiguousarray(table, np.float64)
+    u, e, st = (np.array(x, np.float64) for x in (u, e, st))
+    lib().oracle_pol_scatter(_dp(t), t.shape[-1], _dp(u), _dp(e), _dp(st), float(w1), float(w2))
+    return u, e, st
+
+
+def pol_observer(u, e, st):
+    u, e, st = (np.ascontiguousarray(x, np.float64) for x in (u, e, st))
+    q, uu = C.c_double(), C.c_double()
+    lib().oracle_pol_observer(_dp(u), _dp(e), _dp(st), C.byref(q), C.byref(uu))
+    return q.value, uu.value
 
 
 def planck_bins(lam_e, T):

@@ -296,3 +296,26 @@ def viscous_sources(d: Disk, mdot_msun_yr: float = 1e-8, M_star_msun: float = 2.
         sigma = math.sqrt(math.pi) * prm["h1_au"] * AU_CM * prm["rho0"] / (R / AU_CM)
         L = np.where((d.rho > 0) & (sigma > 0), d.rho * V * 2 * F / sigma, 0.0)
     return np.ascontiguousarray(L)
+
+
+def rayleigh_mueller(nlam: int = 100, nmu: int = 181) -> np.ndarray:
+    """Mueller matrix of small (Rayleigh) particles on theta_k = k pi / (nmu - 1), every bin alike:
+    (nlam, 4, nmu) = S11, S12, S33, S34 with S11 = (3/4)(1 + mu^2), S12 = (3/4)(mu^2 - 1),
+    S33 = (3/2) mu, S34 = 0 (mu = cos theta; normalised so S11 averages to 1 over the sphere)."""
+    mu = np.cos(np.linspace(0.0, math.pi, nmu))
+    t = np.stack([0.75 * (1 + mu ** 2), 0.75 * (mu ** 2 - 1), 1.5 * mu, np.zeros(nmu)])
+    return np.ascontiguousarray(np.broadcast_to(t, (nlam, 4, nmu)))
+
+
+def hg_polarized_mueller(g: np.ndarray, p_lin: np.ndarray, nmu: int = 181) -> np.ndarray:
+    """Synthetic Mueller matrix per bin in the form White (1979, ApJ 229, 954) gives for dust: a
+    Henyey-Greenstein S11 of asymmetry g, S12 = -p_lin S11 (1 - mu^2) / (1 + mu^2) and
+    S33 = S11 2 mu / (1 + mu^2), no circular term (S34 = 0). g = 0 and p_lin = 1 give the Rayleigh
+    polarization with an isotropic S11. (nlam, 4, nmu) on theta_k = k pi / (nmu - 1)."""
+    g = np.atleast_1d(np.asarray(g, np.float64))[:, None]
+    p = np.atleast_1d(np.asarray(p_lin, np.float64))[:, None]
+    mu = np.cos(np.linspace(0.0, math.pi, nmu))[None, :]
+    s11 = (1 - g ** 2) / (1 + g ** 2 - 2 * g * mu) ** 1.5
+    out = np.stack([s11, -p * s11 * (1 - mu ** 2) / (1 + mu ** 2), s11 * 2 * mu / (1 + mu ** 2),
+                    np.zeros_like(s11)], axis=1)
+    return np.ascontiguousarray(out)
