@@ -240,6 +240,23 @@ mcrt_status mcrt_set_density(mcrt_disk *d, const double *rho);
  * values. */
 mcrt_status mcrt_set_sources(mcrt_disk *d, const double *L_cell_erg_s);
 
+/* Polarized transport (Sect. 2.3: the full angle-dependent Mueller matrix of each scattering). table:
+ * host array [nlam][4][nmu] of S11, S12, S33, S34 at the scattering angles theta_k = k pi / (nmu - 1)
+ * (S22 = S11, S44 = S33), linear in theta between them; finite, S11 >= 0 and not all zero; nmu in
+ * 2 .. 4097; NULL turns polarization off. Packets then carry Stokes (Q, U, V) / I relative to a reference
+ * vector: a scattering draws its angle from S11 sin(theta) and the azimuth of its plane from
+ * 1 + (S12/S11)(q cos 2phi + u sin 2phi) with the two direction uniforms of its random block, and
+ * applies the matrix; re-emitted packets and packets leaving an MRW sphere are unpolarized; escaping
+ * packets add Q/I and U/I, in the frame of the disk axis projected on the sky, to fixed-point tallies
+ * (2^20 per packet; read with mcrt_sed_stokes). Single disks only (batches and event traces refuse
+ * polarized disks, MCRT_EINVAL); resets the tallies. */
+mcrt_status mcrt_set_mueller(mcrt_disk *d, int nmu, const double *table);
+
+/* Escaped luminosity per (wavelength bin, inclination group) as Stokes I, Q, U (erg/s, each
+ * nlam * n_incl host values, n_incl dividing MCRT_NINC), Q > 0 for light polarized along the projected
+ * disk axis. MCRT_ESTATE without a Mueller matrix. */
+mcrt_status mcrt_sed_stokes(mcrt_disk *d, int n_incl, double *L_I, double *L_Q, double *L_U);
+
 /* ---- Ray-traced observables (Sect. 2.3: the observables come from integrating the computed source
  * function along rays, free of Monte Carlo noise; Sect. 4.1: SED from 0.1 um to 1 cm at 45 degrees,
  * N-band visibilities at a 100 m baseline). Readings: the source function of a cell in bin b is

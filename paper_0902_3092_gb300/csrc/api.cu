@@ -279,6 +279,11 @@ static DevModel<R> make_model(const mcrt_disk* d, bool f64) {
   m.src_Lstar = d->Lstar;
   m.src_Ltot = d->Lpkt();
   m.n_src = d->n_src;
+  m.mtab = (const R*)(f64 ? d->mtab64.p : d->mtab32.p);
+  m.mcdf = (const R*)(f64 ? d->mcdf64.p : d->mcdf32.p);
+  m.nmu = d->pol ? d->nmu : 0;
+  m.sed_q = d->sed_q.as<unsigned long long>();
+  m.sed_u = d->sed_u.as<unsigned long long>();
   m.tally = d->tally.as<unsigned long long>();
   m.visits = d->visits.as<unsigned long long>();
   m.nabs = d->nabs.as<unsigned long long>();
@@ -320,6 +325,8 @@ static mcrt_status zero_tallies(mcrt_disk* d) {
   CK(cudaMemsetAsync(d->visits.p, 0, n * 8, d->stream), "memset");
   CK(cudaMemsetAsync(d->nabs.p, 0, n * 8, d->stream), "memset");
   if (d->sed.p) CK(cudaMemsetAsync(d->sed.p, 0, d->sed.n, d->stream), "memset");
+  if (d->sed_q.p) CK(cudaMemsetAsync(d->sed_q.p, 0, d->sed_q.n, d->stream), "memset");
+  if (d->sed_u.p) CK(cudaMemsetAsync(d->sed_u.p, 0, d->sed_u.n, d->stream), "memset");
   d->have_T = false;
   d->have_pda = false;
   d->packets_done = 0;
@@ -765,6 +772,8 @@ static mcrt_status run_impl(mcrt_disk* d, uint64_t n_packets, uint64_t seed, uin
   d->n_total = (double)(o->n_total_packets ? o->n_total_packets : n_packets);
   const bool trace = trace_max > 0;
   const bool f64 = trace || o->precision == 64;
+  const bool pol = d->pol;
+  if (pol && trace) return set_error(d, MCRT_EINVAL, "polarized transport has no event trace");
   CK(cudaMemsetAsync(d->cnt.p, 0, C_NCNT * 8, d->stream), "memset");
   CK(cudaMemsetAsync(d->queue.p, 0, 8, d->stream), "memset");
   DBuf ttype, tcell, tlam, tpos, tn;
@@ -808,14 +817,17 @@ static mcrt_status run_impl(mcrt_disk* d, uint64_t n_packets, uint64_t seed, uin
         P.tr_n = tn.as<int32_t>();
         P.l_unit = d->l_unit;
       }
-      const int bps = transport_blocks_per_sm<double>(trace, false, d->gray, block);
+      const int bps = pol ? transport_blocks_per_sm_pol<double>(d->gray, block)
+                          : transport_blocks_per_sm<double>(trace, false, d->gray, block);
       const long long want = (long long)((n_packets + block - 1) / block);
       const int grid = (int)std::max(1ll, std::min<long long>(want, (long long)dev_sms * std::max(1, bps)));
       const bool tail = setup_pool(d, P, (unsigned)grid * block, o->tail_warps_per_sm);
-      e = launch_transport<double>(P, trace, false, d->gray, grid, block, d->stream);
+      e = pol ? launch_transport_pol<double>(P, d->gray, grid, block, d->stream)
+              : launch_transport<double>(P, trace, false, d->gray, grid, block, d->stream);
       d->launches++;
       if (e == cudaSuccess && tail) {
-        e = launch_transport_tail<double>(P, trace, false, d->gray, dev_sms, o->tail_warps_per_sm, d->stream);
+        e = pol ? launch_transport_tail_pol<double>(P, d->gray, dev_sms, o->tail_warps_per_sm, d->stream)
+                : launch_transport_tail<double>(P, trace, false, d->gray, dev_sms, o->tail_warps_per_sm, d->stream);
         d->launches++;
       }
     } else {
@@ -830,14 +842,17 @@ static mcrt_status run_impl(mcrt_disk* d, uint64_t n_packets, uint64_t seed, uin
       P.total = n_packets;
       P.queue = d->queue.as<unsigned long long>();
       P.want_lam = (!d->gray || o->want_sed) ? 1 : 0;
-      const int bps = transport_blocks_per_sm<float>(false, false, d->gray, block);
+      const int bps = pol ? transport_blocks_per_sm_pol<float>(d->gray, block)
+                          : transport_blocks_per_sm<float>(false, false, d->gray, block);
       const long long want = (long long)((n_packets + block - 1) / block);
       const int grid = (int)std::max(1ll, std::min<long long>(want, (long long)dev_sms * std::max(1, bps)));
       const bool tail = setup_pool(d, P, (unsigned)grid * block, o->tail_warps_per_sm);
-      e = launch_transport<float>(P, false, false, d->gray, grid, block, d->stream);
+      e = pol ? launch_transport_pol<float>(P, d->gray, grid, block, d->stream)
+              : launch_transport<float>(P, false, false, d->gray, grid, block, d->stream);
       d->launches++;
       if (e == cudaSuccess && tail) {
-        e = launch_transport_tail<float>(P, false, false, d->gray, dev_sms, o->tail_warps_per_sm, d->stream);
+        e = pol ? launch_transport_tail_pol<float>(P, d->gray, dev_sms, o->tail_warps_per_sm, d->stream)
+                : launch_transport_tail<float>(P, false, false, d->gray, dev_sms, o->tail_warps_per_sm, d->stream);
         d->launches++;
       }
     }
@@ -897,6 +912,7 @@ mcrt_status mcrt_run_batch(mcrt_disk* const* disks, int n, const uint64_t* n_pac
   for (int i = 0; i < n; ++i) {
     if (!disks[i]) return set_error(nullptr, MCRT_EINVAL, "NULL disk in batch");
     if (!disks[i]->has_opacity) return set_error(disks[i], MCRT_ESTATE, "mcrt_set_opacity must come first");
+    if (disks[i]->pol) return set_error(disks[i], MCRT_EINVAL, "batches do not take polarized disks");
     if (disks[i]->device != d0->device) return set_error(disks[i], MCRT_EINVAL, "batch disks on different devices");
   }
   mcrt_disk* d = d0;
@@ -1045,6 +1061,77 @@ mcrt_status mcrt_sed(mcrt_disk* d, int n_incl, double* L) {
 
 // checkpoint layout: 8 x uint64 header (magic, version, nr, nt, nlam, packets_done, n_total bits, 0),
 // then tally, visits, nabs (nr*nt each) and sed (nlam*10), all uint64.
+mcrt_status mcrt_set_mueller(mcrt_disk* d, int nmu, const double* table) {
+  if (!d) return set_error(nullptr, MCRT_EINVAL, "disk is NULL");
+  if (!d->has_opacity) return set_error(d, MCRT_ESTATE, "mcrt_set_opacity must come first");
+  CK(cudaSetDevice(d->device), "cudaSetDevice");
+  CK(cudaStreamSynchronize(d->stream), "synchronize");
+  if (!table) {
+    d->pol = false;
+    d->nmu = 0;
+    return MCRT_OK;
+  }
+  if (nmu < 2 || nmu > 4097) return set_error(d, MCRT_EINVAL, "nmu: 2 .. 4097 scattering angles");
+  const size_t nl = (size_t)d->nlam, m = (size_t)nmu;
+  std::vector<double> cdf(nl * m);
+  const double h = kPi / (nmu - 1);
+  for (size_t b = 0; b < nl; ++b) {
+    const double* t = table + b * 4 * m;
+    for (size_t k = 0; k < 4 * m; ++k)
+      if (!std::isfinite(t[k])) return set_error(d, MCRT_EINVAL, "Mueller matrix: finite values");
+    for (size_t k = 0; k < m; ++k)
+      if (t[k] < 0) return set_error(d, MCRT_EINVAL, "Mueller matrix: S11 >= 0");
+    // cumulative S11 sin(theta) by the trapezoid rule, normalised to 1
+    double* c = cdf.data() + b * m;
+    c[0] = 0.0;
+    for (size_t k = 1; k < m; ++k)
+      c[k] = c[k - 1] + 0.5 * h * (t[k - 1] * std::sin((double)(k - 1) * h) + t[k] * std::sin((double)k * h));
+    if (!(c[m - 1] > 0)) return set_error(d, MCRT_EINVAL, "Mueller matrix: S11 vanishes");
+    const double tot = c[m - 1];
+    for (size_t k = 0; k < m; ++k) c[k] /= tot;
+  }
+  std::vector<double> tab(table, table + nl * 4 * m);
+  cudaError_t e = upload(d->mtab64, tab);
+  if (e == cudaSuccess) e = upload(d->mtab32, cast_vec<float>(tab));
+  if (e == cudaSuccess) e = upload(d->mcdf64, cdf);
+  if (e == cudaSuccess) e = upload(d->mcdf32, cast_vec<float>(cdf));
+  if (e == cudaSuccess && d->sed_q.n < nl * kNInc * 8) e = d->sed_q.alloc(nl * kNInc * 8);
+  if (e == cudaSuccess && d->sed_u.n < nl * kNInc * 8) e = d->sed_u.alloc(nl * kNInc * 8);
+  if (e != cudaSuccess) return cuda_fail(d, e, "upload");
+  d->nmu = nmu;
+  d->pol = true;
+  mcrt_status s = zero_tallies(d);
+  if (s != MCRT_OK) return s;
+  CK(cudaStreamSynchronize(d->stream), "synchronize");
+  return MCRT_OK;
+}
+
+mcrt_status mcrt_sed_stokes(mcrt_disk* d, int n_incl, double* L_I, double* L_Q, double* L_U) {
+  if (!d) return set_error(nullptr, MCRT_EINVAL, "disk is NULL");
+  if (!L_I || !L_Q || !L_U || n_incl <= 0 || kNInc % n_incl) return set_error(d, MCRT_EINVAL, "n_incl must divide 10");
+  if (!d->pol) return set_error(d, MCRT_ESTATE, "mcrt_set_mueller must come first");
+  mcrt_status s = mcrt_sed(d, n_incl, L_I);
+  if (s != MCRT_OK) return s;
+  const size_t nc = (size_t)d->nlam * kNInc;
+  std::vector<unsigned long long> q(nc), u(nc);
+  CK(cudaMemcpyAsync(q.data(), d->sed_q.p, nc * 8, cudaMemcpyDeviceToHost, d->stream), "copy");
+  CK(cudaMemcpyAsync(u.data(), d->sed_u.p, nc * 8, cudaMemcpyDeviceToHost, d->stream), "copy");
+  CK(cudaStreamSynchronize(d->stream), "synchronize");
+  const double e = d->Lpkt() / (d->n_total > 0 ? d->n_total : 1.0) / 1048576.0;
+  const int grp = kNInc / n_incl;
+  for (int b = 0; b < d->nlam; ++b)
+    for (int i = 0; i < n_incl; ++i) {
+      long long sq = 0, su = 0;
+      for (int j = 0; j < grp; ++j) {
+        sq += (long long)q[(size_t)b * kNInc + i * grp + j];
+        su += (long long)u[(size_t)b * kNInc + i * grp + j];
+      }
+      L_Q[(size_t)b * n_incl + i] = (double)sq * e;
+      L_U[(size_t)b * n_incl + i] = (double)su * e;
+    }
+  return MCRT_OK;
+}
+
 mcrt_status mcrt_checkpoint(mcrt_disk* d, void* buf, size_t* len) {
   if (!d || !len) return set_error(d, MCRT_EINVAL, "bad arguments");
   const size_t n = (size_t)d->nr * d->nt;
@@ -1213,6 +1300,7 @@ mcrt_status mcrt_batch_create(mcrt_disk* const* disks, int n, const uint64_t* n_
   for (int i = 0; i < n; ++i) {
     if (!disks[i]) return set_error(nullptr, MCRT_EINVAL, "NULL disk in batch");
     if (!disks[i]->has_opacity) return set_error(disks[i], MCRT_ESTATE, "mcrt_set_opacity must come first");
+    if (disks[i]->pol) return set_error(disks[i], MCRT_EINVAL, "batches do not take polarized disks");
     if (disks[i]->device != disks[0]->device) return set_error(nullptr, MCRT_EINVAL, "disks on different devices");
   }
   mcrt_disk* d = disks[0];

@@ -116,6 +116,14 @@ struct DevModel {
   const double* src_cum;
   double src_Lstar, src_Ltot;
   int n_src;
+  // polarization (Sect. 2.3): Mueller matrix per bin [nlam][4][nmu] (S11, S12, S33, S34 at theta_k =
+  // k pi / (nmu - 1)), the normalised cumulative S11 sin(theta) per bin [nlam][nmu], and the escaping
+  // Stokes Q/I, U/I per [lam][incl] in fixed point (2^20 per packet, two's complement)
+  const R* mtab;
+  const R* mcdf;
+  int nmu;
+  unsigned long long* sed_q;
+  unsigned long long* sed_u;
   // tallies
   unsigned long long* tally;   // nr*nt fixed-point absorbed energy
   unsigned long long* visits;  // nr*nt packet entries

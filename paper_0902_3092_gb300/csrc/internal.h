@@ -48,6 +48,13 @@ int transport_blocks_per_sm(bool trace, bool batch, bool gray, int block);
 template <class R>
 cudaError_t launch_transport_tail(const KParams<R>& P, bool trace, bool batch, bool gray, int sms, int warps_per_sm,
                                   cudaStream_t st);
+// polarized transport (single disk, no event trace)
+template <class R>
+cudaError_t launch_transport_pol(const KParams<R>& P, bool gray, int grid, int block, cudaStream_t st);
+template <class R>
+cudaError_t launch_transport_tail_pol(const KParams<R>& P, bool gray, int sms, int warps_per_sm, cudaStream_t st);
+template <class R>
+int transport_blocks_per_sm_pol(bool gray, int block);
 
 }  // namespace mcrt
 
@@ -64,6 +71,11 @@ struct mcrt_disk {
   mcrt::DBuf src_cum;
   int n_src = 0;
   double Lpkt() const { return Lstar + Lsrc_total; }  // luminosity the packets carry
+  // polarized transport: Mueller matrix per bin and its cumulative S11 sin(theta) (FP32 and FP64
+  // copies), escaping Stokes Q/I and U/I (fixed point, 2^20 per packet)
+  bool pol = false;
+  int nmu = 0;
+  mcrt::DBuf mtab32, mtab64, mcdf32, mcdf64, sed_q, sed_u;
   std::vector<double> rf, tf, rho, mass;
   std::vector<double> lam_e, kabs, ksca, g;
   // temperature grid

@@ -78,6 +78,9 @@ struct Pkt {
   int tslot, ntr;
   int pend;  // 1: moved to an interaction point whose interaction has not run yet; 2: an internal
             // source's packet waiting for its release
+  // polarized transport only: Stokes (Q, U, V) / I relative to the reference vector (ex, ey, ez),
+  // perpendicular to the direction (Q > 0: electric field along it)
+  R sq, su, sv, ex, ey, ez;
 };
 
 // packets that had taken this many steps when the queue drained go first in the tail kernel
@@ -206,6 +209,147 @@ __device__ __forceinline__ void turn(R& x, R& y, R& z, R mu, R u2) {
   }
   const R n = rsqrt_<R>(x * x + y * y + z * z);
   x *= n; y *= n; z *= n;
+}
+
+// ------------------------------------------------------------------------------------------------
+// Polarization (Sect. 2.3: the full Mueller matrix of each scattering)
+// ------------------------------------------------------------------------------------------------
+// the reference of an unpolarized packet: the horizontal direction z x u (x - (x.u) u near the axis)
+template <class R>
+__device__ __forceinline__ void pol_reset(Pkt<R>& s) {
+  R ex, ey, ez;
+  if (fabs(s.uz) < (R)0.999999) {
+    ex = -s.uy;
+    ey = s.ux;
+    ez = (R)0;
+  } else {
+    ex = (R)1 - s.ux * s.ux;
+    ey = -s.ux * s.uy;
+    ez = -s.ux * s.uz;
+  }
+  const R n = sqrt(ex * ex + ey * ey + ez * ez);
+  s.ex = ex / n;
+  s.ey = ey / n;
+  s.ez = ez / n;
+  s.sq = s.su = s.sv = (R)0;
+}
+
+// Stokes q, u in the frame whose reference is turned by psi about the direction
+template <class R>
+__device__ __forceinline__ void pol_rotate(R& q, R& u, R psi) {
+  const R c = cos((R)2 * psi), sn = sin((R)2 * psi);
+  const R qn = q * c + u * sn;
+  u = -q * sn + u * c;
+  q = qn;
+}
+
+// scattering angle from the normalised cumulative S11 sin(theta) of bin lam (linear in theta between
+// the grid's angles)
+template <class R>
+__device__ __forceinline__ R pol_theta(const DevModel<R>& M, int lam, R xi) {
+  const R* c = M.mcdf + (size_t)lam * M.nmu;
+  int lo = 1, hi = M.nmu - 1;  // the first k >= 1 with c[k] >= xi
+  while (lo < hi) {
+    const int mid = (lo + hi) >> 1;
+    if (c[mid] >= xi) hi = mid; else lo = mid + 1;
+  }
+  const R h = (R)3.14159265358979323846 / (R)(M.nmu - 1);
+  const R d = c[lo] - c[lo - 1];
+  return (R)(lo - 1) * h + (d > (R)0 ? (xi - c[lo - 1]) / d : (R)0) * h;
+}
+
+template <class R>
+__device__ __forceinline__ R mueller_at(const DevModel<R>& M, int lam, int k, R th) {
+  const R* t = M.mtab + ((size_t)lam * 4 + k) * M.nmu;
+  R x = th / (R)3.14159265358979323846 * (R)(M.nmu - 1);
+  int j = (int)floor(x);
+  j = j < 0 ? 0 : (j > M.nmu - 2 ? M.nmu - 2 : j);
+  const R f = x - (R)j;
+  return ((R)1 - f) * t[j] + f * t[j + 1];
+}
+
+// azimuth of the scattering plane: the root of F(phi) = phi / 2pi + a (q sin 2phi + u (1 - cos 2phi)) / 4pi
+// = xi by Newton steps kept inside a bisection bracket
+template <class R>
+__device__ __forceinline__ R pol_phi(R a, R q, R u, R xi) {
+  const R tp = (R)6.283185307179586476925;
+  R lo = (R)0, hi = tp, phi = tp * xi;
+  for (int it = 0; it < 200; ++it) {
+    const R s2 = sin((R)2 * phi), c2 = cos((R)2 * phi);
+    const R F = phi / tp + a * (q * s2 + u * ((R)1 - c2)) / ((R)2 * tp) - xi;
+    if (F > (R)0) hi = phi; else lo = phi;
+    const R dF = ((R)1 + a * (q * c2 + u * s2)) / tp;
+    R nx = dF > (R)0 ? phi - F / dF : (R)0.5 * (lo + hi);
+    if (!(nx > lo && nx < hi)) nx = (R)0.5 * (lo + hi);
+    if (fabs(nx - phi) < (sizeof(R) == 8 ? (R)1e-13 : (R)1e-6)) {
+      phi = nx;
+      break;
+    }
+    phi = nx;
+  }
+  return phi;
+}
+
+// one polarized scattering of bin lam with uniforms (w1, w2): angle, plane, Stokes update, new direction
+// and reference (the in-plane direction perpendicular to the new direction)
+template <class R>
+__device__ __forceinline__ void pol_scatter(const DevModel<R>& M, Pkt<R>& s, R w1, R w2) {
+  const R th = pol_theta(M, s.lam, w1);
+  const R s11 = mueller_at(M, s.lam, 0, th), s12 = mueller_at(M, s.lam, 1, th);
+  const R s33 = mueller_at(M, s.lam, 2, th), s34 = mueller_at(M, s.lam, 3, th);
+  const R a = s11 > (R)0 ? s12 / s11 : (R)0;
+  const R phi = pol_phi(a, s.sq, s.su, w2);
+  R q = s.sq, u = s.su;
+  pol_rotate(q, u, phi);
+  const R cp = cos(phi), sp = sin(phi), ct = cos(th), st = sin(th);
+  const R cx = s.uy * s.ez - s.uz * s.ey, cy = s.uz * s.ex - s.ux * s.ez, cz = s.ux * s.ey - s.uy * s.ex;
+  const R px = s.ex * cp + cx * sp, py = s.ey * cp + cy * sp, pz = s.ez * cp + cz * sp;
+  R nx = s.ux * ct + px * st, ny = s.uy * ct + py * st, nz = s.uz * ct + pz * st;
+  R ex = px * ct - s.ux * st, ey = py * ct - s.uy * st, ez = pz * ct - s.uz * st;
+  const R nn = sqrt(nx * nx + ny * ny + nz * nz);
+  nx /= nn;
+  ny /= nn;
+  nz /= nn;
+  const R dot = ex * nx + ey * ny + ez * nz;
+  ex -= dot * nx;
+  ey -= dot * ny;
+  ez -= dot * nz;
+  const R ne = sqrt(ex * ex + ey * ey + ez * ez);
+  s.ux = nx;
+  s.uy = ny;
+  s.uz = nz;
+  s.ex = ex / ne;
+  s.ey = ey / ne;
+  s.ez = ez / ne;
+  const R I = s11 + s12 * q;
+  const R Q = s12 + s11 * q;
+  const R U = s33 * u + s34 * s.sv;
+  const R V = -s34 * u + s33 * s.sv;
+  if (I > (R)0) {
+    s.sq = Q / I;
+    s.su = U / I;
+    s.sv = V / I;
+  } else {
+    s.sq = s.su = s.sv = (R)0;
+  }
+}
+
+// Stokes q, u of an escaping packet in the sky frame (reference: the disk axis projected on the sky)
+template <class R>
+__device__ __forceinline__ void pol_observer(const Pkt<R>& s, R& q, R& u) {
+  q = s.sq;
+  u = s.su;
+  R nx = -s.uz * s.ux, ny = -s.uz * s.uy, nz = (R)1 - s.uz * s.uz;
+  const R nn = sqrt(nx * nx + ny * ny + nz * nz);
+  if (nn > (R)1e-12) {
+    nx /= nn;
+    ny /= nn;
+    nz /= nn;
+    const R cx = s.uy * s.ez - s.uz * s.ey, cy = s.uz * s.ex - s.ux * s.ez, cz = s.ux * s.ey - s.uy * s.ex;
+    const R c = s.ex * nx + s.ey * ny + s.ez * nz;
+    const R sn = cx * nx + cy * ny + cz * nz;
+    pol_rotate(q, u, atan2(sn, c));
+  }
 }
 
 template <class R>
@@ -375,7 +519,7 @@ __device__ __forceinline__ void set_alpha(const DevModel<R>& M, Pkt<R>& s) {
   s.ialpha = s.alpha > (R)0 ? (R)1 / s.alpha : (R)0;
 }
 
-template <class R, bool TRACE, bool G, class RNG>
+template <class R, bool TRACE, bool G, bool POL = false, class RNG>
 __device__ __forceinline__ void launch_packet(const KParams<R>& P, RNG& rng, const DevModel<R>& M, Pkt<R>& s,
                               unsigned long long k, int tslot, Acc& acc) {
   s.model = M.model_id;
@@ -446,6 +590,7 @@ __device__ __forceinline__ void launch_packet(const KParams<R>& P, RNG& rng, con
   s.tslot = tslot;
   s.ntr = 0;
   s.pend = 0;
+  if (POL) pol_reset(s);
   trace_ev<R, TRACE>(P, s, EV_LAUNCH, -1);
   s.tau = neg_log<R>(uni<R>(w.w));
   acc.packets++;
@@ -455,7 +600,7 @@ __device__ __forceinline__ void launch_packet(const KParams<R>& P, RNG& rng, con
 template <class R>
 __device__ __forceinline__ R dsafe_margin() { return sizeof(R) == 4 ? (R)(1.0 - 1e-5) : (R)(1.0 - 1e-12); }
 
-template <class R, bool TRACE, bool G, class RNG>
+template <class R, bool TRACE, bool G, bool POL = false, class RNG>
 __device__ __forceinline__ void mrw_chain(const KParams<R>& P, RNG& rng, const DevModel<R>& M, Pkt<R>& s, int c,
                                           Acc& acc) {
   const R rho = M.rho[c];
@@ -508,6 +653,7 @@ __device__ __forceinline__ void mrw_chain(const KParams<R>& P, RNG& rng, const D
     } else {
       iso_dir<R>(jb.x, jb.y, s.ux, s.uy, s.uz);
     }
+    if (POL) pol_reset(s);  // a packet leaves the diffusion sphere unpolarized
     const R ul = uni<R>(ja.w);
     if (lam_now) {
       int k;
@@ -530,7 +676,7 @@ __device__ __forceinline__ void mrw_chain(const KParams<R>& P, RNG& rng, const D
 
 // Moves a packet to its next event: enters the next cell (1), reaches an interaction point (2, the
 // interaction itself is left to interact()), or ends (0: escaped, or a step guard).
-template <class R, bool TRACE, bool G, class RNG>
+template <class R, bool TRACE, bool G, bool POL = false, class RNG>
 __device__ __forceinline__ int advance(const KParams<R>& P, RNG& rng, const DevModel<R>& M, Pkt<R>& s, Acc& acc) {
   if (++s.steps > P.max_steps) {
     acc.err |= kErrStepGuard;
@@ -606,6 +752,15 @@ __device__ __forceinline__ int advance(const KParams<R>& P, RNG& rng, const DevM
     int ib = (int)(fabs(s.uz) * (R)kNInc);
     ib = ib < kNInc ? ib : kNInc - 1;
     if (lead<RNG>()) atomicAdd(M.sed + s.lam * kNInc + ib, 1ull);
+    if (POL) {
+      R q, u;
+      pol_observer(s, q, u);
+      const long long iq = (long long)floor(q * (R)1048576 + (R)0.5), iu = (long long)floor(u * (R)1048576 + (R)0.5);
+      if (lead<RNG>()) {
+        atomicAdd(M.sed_q + s.lam * kNInc + ib, (unsigned long long)iq);
+        atomicAdd(M.sed_u + s.lam * kNInc + ib, (unsigned long long)iu);
+      }
+    }
     acc.escaped++;
     trace_ev<R, TRACE>(P, s, EV_ESCAPE, -1);
     return 0;
@@ -627,7 +782,7 @@ __device__ __forceinline__ int advance(const KParams<R>& P, RNG& rng, const DevM
 // The interaction at the packet's current point (Sect. 2.1): scattering or absorption with immediate
 // re-emission, then the MRW chain (Sect. 2.2.2) and the next optical depth. A release (the first event
 // of an internal source's packet) is an absorption with omega = 0. False: capped.
-template <class R, bool TRACE, bool G, class RNG>
+template <class R, bool TRACE, bool G, bool POL = false, class RNG>
 __device__ __forceinline__ bool interact(const KParams<R>& P, RNG& rng, const DevModel<R>& M, Pkt<R>& s, Acc& acc,
                                          bool release = false) {
   const int c = s.ir * M.nt + s.it;
@@ -667,17 +822,20 @@ __device__ __forceinline__ bool interact(const KParams<R>& P, RNG& rng, const De
   }
   // new direction: Henyey-Greenstein turn for anisotropic scattering, isotropic otherwise (scattering
   // with g = 0 and re-emission share this code)
-  if (g != (R)0) {
+  if (POL && sca) {
+    pol_scatter(M, s, uni<R>(w.y), uni<R>(w.z));  // the Mueller matrix of bin lam (Sect. 2.3)
+  } else if (g != (R)0) {
     const R mu = hg_mu(g, uni<R>(w.y));
     const R u2 = uni<R>(w.z);
     turn<R>(s.ux, s.uy, s.uz, mu, u2);
   } else {
     iso_dir<R>(w.y, w.z, s.ux, s.uy, s.uz);
   }
+  if (POL && !sca) pol_reset(s);  // re-emission is unpolarized
   trace_ev<R, TRACE>(P, s, sca ? EV_SCATTER : EV_ABSORB, c);
   s.events++;
   s.ninc++;
-  if (P.mrw && s.ninc >= P.nmin) mrw_chain<R, TRACE, G>(P, rng, M, s, c, acc);
+  if (P.mrw && s.ninc >= P.nmin) mrw_chain<R, TRACE, G, POL>(P, rng, M, s, c, acc);
   if (s.events >= P.max_events) {
     acc.capped++;
     trace_ev<R, TRACE>(P, s, EV_CAPPED, c);
@@ -688,15 +846,15 @@ __device__ __forceinline__ bool interact(const KParams<R>& P, RNG& rng, const De
 }
 
 // One event of a packet, an interaction run at once. False when the packet has ended.
-template <class R, bool TRACE, bool G, class RNG>
+template <class R, bool TRACE, bool G, bool POL = false, class RNG>
 __device__ __forceinline__ bool step(const KParams<R>& P, RNG& rng, const DevModel<R>& M, Pkt<R>& s, Acc& acc) {
   if (s.pend) {
     const bool release = s.pend == 2;
     s.pend = 0;
-    return interact<R, TRACE, G>(P, rng, M, s, acc, release);
+    return interact<R, TRACE, G, POL>(P, rng, M, s, acc, release);
   }
-  const int r = advance<R, TRACE, G>(P, rng, M, s, acc);
-  if (r == 2) return interact<R, TRACE, G>(P, rng, M, s, acc);
+  const int r = advance<R, TRACE, G, POL>(P, rng, M, s, acc);
+  if (r == 2) return interact<R, TRACE, G, POL>(P, rng, M, s, acc);
   return r == 1;
 }
 
@@ -908,7 +1066,7 @@ __device__ __forceinline__ int interactions_at_once(const KParams<R>& P, WarpRng
 // its speed alone. The transport kernel therefore stores them (state unchanged, so the random stream
 // and the result are the same) and this kernel runs them one per warp: lane 0 of each 32-thread block
 // takes packets from the pool, those that had taken at least kTailLongSteps steps first.
-template <class R, bool TRACE, bool G, bool BATCH>
+template <class R, bool TRACE, bool G, bool BATCH, bool POL = false>
 __global__ void __launch_bounds__(32) transport_tail_kernel(const KParams<R> P) {
   const unsigned lane = threadIdx.x & 31u;
   if (TRACE && lane != 0) return;  // the debug trace runs one lane per packet
@@ -923,7 +1081,7 @@ __global__ void __launch_bounds__(32) transport_tail_kernel(const KParams<R> P) 
     const DevModel<R>& M = BATCH ? P.models[s.model] : P.m0;  // batches: the packet's model index
     if (TRACE) {
       SerialRng rng{{(uint32_t)P.seed, (uint32_t)(P.seed >> 32)}};
-      while (step<R, TRACE, G>(P, rng, M, s, acc)) {
+      while (step<R, TRACE, G, POL>(P, rng, M, s, acc)) {
       }
     } else {
       // all 32 lanes carry the packet: the same arithmetic in every lane, the random blocks computed
@@ -932,14 +1090,14 @@ __global__ void __launch_bounds__(32) transport_tail_kernel(const KParams<R> P) 
       bool ended = false, misses = false;
       for (;;) {
         // (FP32 only: the FP64 debug path keeps the oracle's order of floating-point operations)
-        if ((G || M.gray) && sizeof(R) == 4 && !misses && !s.pend && s.ir >= 0 && s.alpha > (R)0 && M.g0 == (R)0 &&
+        if (!POL && (G || M.gray) && sizeof(R) == 4 && !misses && !s.pend && s.ir >= 0 && s.alpha > (R)0 && M.g0 == (R)0 &&
             s.events + 33u < P.max_events && s.steps + 33u < P.max_steps) {
           const int n = interactions_at_once<R, G>(P, rng, M, s, acc, ended, misses);
           if (ended) break;
           if (n > 0) continue;
         }
         misses = false;
-        if (!step<R, TRACE, G>(P, rng, M, s, acc)) break;
+        if (!step<R, TRACE, G, POL>(P, rng, M, s, acc)) break;
       }
     }
     if (lane == 0) {
@@ -958,7 +1116,7 @@ template <class R>
 constexpr int transport_min_blocks() { return sizeof(R) == 4 ? MCRT_TRANSPORT_MIN_BLOCKS : 1; }
 
 // G: gray dust known at compile time (single-disk gray runs); otherwise M.gray is read at run time.
-template <class R, bool TRACE, bool BATCH, bool G>
+template <class R, bool TRACE, bool BATCH, bool G, bool POL = false>
 __global__ void __launch_bounds__(256, transport_min_blocks<R>()) transport_kernel(const KParams<R> P) {
   Pkt<R> s;
   Acc acc = Acc{};
@@ -990,7 +1148,7 @@ __global__ void __launch_bounds__(256, transport_min_blocks<R>()) transport_kern
             const DevModel<R>& M = BATCH ? P.models[m] : P.m0;
             const unsigned long long local = q - M.q_begin;
             const int tslot = (TRACE && local < (unsigned long long)P.trace_n) ? (int)local : -1;
-            launch_packet<R, TRACE, G>(P, rng, M, s, M.first_id + local, tslot, acc);
+            launch_packet<R, TRACE, G, POL>(P, rng, M, s, M.first_id + local, tslot, acc);
             active = true;
           } else {
             done = true;
@@ -1012,7 +1170,7 @@ __global__ void __launch_bounds__(256, transport_min_blocks<R>()) transport_kern
         }
         const DevModel<R>& M = BATCH ? P.models[model] : P.m0;
         while (active) {
-          active = step<R, TRACE, G>(P, rng, M, s, acc);
+          active = step<R, TRACE, G, POL>(P, rng, M, s, acc);
           if (!active) note_end(s, acc);
         }
         break;
@@ -1023,7 +1181,7 @@ __global__ void __launch_bounds__(256, transport_min_blocks<R>()) transport_kern
     // keep crossing cells; a packet's own sequence of events and random draws is unchanged.
     const DevModel<R>& M = BATCH ? P.models[model] : P.m0;
     if (active && !s.pend) {
-      const int r = advance<R, TRACE, G>(P, rng, M, s, acc);
+      const int r = advance<R, TRACE, G, POL>(P, rng, M, s, acc);
       if (r == 0) {
         active = false;
         note_end(s, acc);
@@ -1038,7 +1196,7 @@ __global__ void __launch_bounds__(256, transport_min_blocks<R>()) transport_kern
         if (active && s.pend) {
           const bool release = s.pend == 2;
           s.pend = 0;
-          if (!interact<R, TRACE, G>(P, rng, M, s, acc, release)) {
+          if (!interact<R, TRACE, G, POL>(P, rng, M, s, acc, release)) {
             active = false;
             note_end(s, acc);
           }

@@ -25,7 +25,7 @@ EXPORTS = ["mcrt_disk_create", "mcrt_set_opacity", "mcrt_default_run_opts", "mcr
            "mcrt_pda_solve_static", "mcrt_disk_info", "mcrt_launch_count", "mcrt_last_error",
            "mcrt_disk_destroy", "mcrt_batch_create", "mcrt_batch_run", "mcrt_batch_config", "mcrt_batch_destroy",
            "mcrt_default_hydro_opts", "mcrt_hydrostatic_density", "mcrt_set_density", "mcrt_set_rays",
-           "mcrt_raytrace", "mcrt_visibilities", "mcrt_set_sources"]
+           "mcrt_raytrace", "mcrt_visibilities", "mcrt_set_sources", "mcrt_set_mueller", "mcrt_sed_stokes"]
 
 
 class McrtError(RuntimeError):
@@ -122,6 +122,8 @@ def lib():
         "mcrt_set_density": (st, [P, pd]),
         "mcrt_set_rays": (st, [P, C.c_double, C.c_double, C.c_int64, pd, pd, pd]),
         "mcrt_set_sources": (st, [P, pd]),
+        "mcrt_set_mueller": (st, [P, C.c_int, pd]),
+        "mcrt_sed_stokes": (st, [P, C.c_int, pd, pd, pd]),
         "mcrt_raytrace": (st, [P, C.c_int, C.c_int, pd, pd, pd, pu]),
         "mcrt_visibilities": (st, [P, C.c_int, pi, pd, pd, C.c_int, pd]),
     }
@@ -265,6 +267,24 @@ class Disk:
         L = np.ascontiguousarray(L_cell, np.float64).ravel()
         _check(lib().mcrt_set_sources(self._h, _dp(L)), self._h)
         self.L_src = float(L.sum())
+
+    def set_mueller(self, table=None):
+        """Polarized transport with a Mueller matrix per wavelength bin (nlam x 4 x nmu: S11, S12, S33,
+        S34 on theta_k = k pi / (nmu - 1), e.g. disks.rayleigh_mueller); None turns it off. Resets the
+        tallies."""
+        if table is None:
+            _check(lib().mcrt_set_mueller(self._h, 0, None), self._h)
+            return
+        t = np.ascontiguousarray(table, np.float64)
+        _check(lib().mcrt_set_mueller(self._h, int(t.shape[-1]), _dp(t)), self._h)
+
+    def sed_stokes(self, n_incl=NINC):
+        """Escaped luminosity per (wavelength bin, inclination group) as Stokes I, Q, U (erg/s); Q > 0
+        for light polarized along the projected disk axis."""
+        I, Q, U = (np.zeros(self.nlam * n_incl) for _ in range(3))
+        _check(lib().mcrt_sed_stokes(self._h, int(n_incl), _dp(I), _dp(Q), _dp(U)), self._h)
+        sh = (self.nlam, n_incl)
+        return I.reshape(sh), Q.reshape(sh), U.reshape(sh)
 
     def set_density(self, rho):
         """Replaces the density (g/cm^3) and resets the tallies."""

@@ -73,6 +73,8 @@ def test_defaults_and_host_validation(L):
     assert L.mcrt_raytrace(None, 0, 32, None, None, None, None) == 1
     assert L.mcrt_visibilities(None, 1, None, None, None, 1, None) == 1
     assert L.mcrt_set_sources(None, None) == 1
+    assert L.mcrt_set_mueller(None, 181, None) == 1
+    assert L.mcrt_sed_stokes(None, 10, None, None, None) == 1
     L.mcrt_disk_destroy(None)
 
 
