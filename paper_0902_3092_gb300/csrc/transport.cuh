@@ -212,11 +212,12 @@ __device__ __forceinline__ void turn(R& x, R& y, R& z, R mu, R u2) {
 }
 
 // ------------------------------------------------------------------------------------------------
-// Polarization (Sect. 2.3: the full Mueller matrix of each scattering)
+// Polarization (Sect. 2.3: the full Mueller matrix of each scattering); host and device, so that the
+// same code can be checked against the oracle on the CPU
 // ------------------------------------------------------------------------------------------------
 // the reference of an unpolarized packet: the horizontal direction z x u (x - (x.u) u near the axis)
 template <class R>
-__device__ __forceinline__ void pol_reset(Pkt<R>& s) {
+__host__ __device__ __forceinline__ void pol_reset(Pkt<R>& s) {
   R ex, ey, ez;
   if (fabs(s.uz) < (R)0.999999) {
     ex = -s.uy;
@@ -236,7 +237,7 @@ __device__ __forceinline__ void pol_reset(Pkt<R>& s) {
 
 // Stokes q, u in the frame whose reference is turned by psi about the direction
 template <class R>
-__device__ __forceinline__ void pol_rotate(R& q, R& u, R psi) {
+__host__ __device__ __forceinline__ void pol_rotate(R& q, R& u, R psi) {
   const R c = cos((R)2 * psi), sn = sin((R)2 * psi);
   const R qn = q * c + u * sn;
   u = -q * sn + u * c;
@@ -246,7 +247,7 @@ __device__ __forceinline__ void pol_rotate(R& q, R& u, R psi) {
 // scattering angle from the normalised cumulative S11 sin(theta) of bin lam (linear in theta between
 // the grid's angles)
 template <class R>
-__device__ __forceinline__ R pol_theta(const DevModel<R>& M, int lam, R xi) {
+__host__ __device__ __forceinline__ R pol_theta(const DevModel<R>& M, int lam, R xi) {
   const R* c = M.mcdf + (size_t)lam * M.nmu;
   int lo = 1, hi = M.nmu - 1;  // the first k >= 1 with c[k] >= xi
   while (lo < hi) {
@@ -259,7 +260,7 @@ __device__ __forceinline__ R pol_theta(const DevModel<R>& M, int lam, R xi) {
 }
 
 template <class R>
-__device__ __forceinline__ R mueller_at(const DevModel<R>& M, int lam, int k, R th) {
+__host__ __device__ __forceinline__ R mueller_at(const DevModel<R>& M, int lam, int k, R th) {
   const R* t = M.mtab + ((size_t)lam * 4 + k) * M.nmu;
   R x = th / (R)3.14159265358979323846 * (R)(M.nmu - 1);
   int j = (int)floor(x);
@@ -271,7 +272,7 @@ __device__ __forceinline__ R mueller_at(const DevModel<R>& M, int lam, int k, R 
 // azimuth of the scattering plane: the root of F(phi) = phi / 2pi + a (q sin 2phi + u (1 - cos 2phi)) / 4pi
 // = xi by Newton steps kept inside a bisection bracket
 template <class R>
-__device__ __forceinline__ R pol_phi(R a, R q, R u, R xi) {
+__host__ __device__ __forceinline__ R pol_phi(R a, R q, R u, R xi) {
   const R tp = (R)6.283185307179586476925;
   R lo = (R)0, hi = tp, phi = tp * xi;
   for (int it = 0; it < 200; ++it) {
@@ -293,7 +294,7 @@ __device__ __forceinline__ R pol_phi(R a, R q, R u, R xi) {
 // one polarized scattering of bin lam with uniforms (w1, w2): angle, plane, Stokes update, new direction
 // and reference (the in-plane direction perpendicular to the new direction)
 template <class R>
-__device__ __forceinline__ void pol_scatter(const DevModel<R>& M, Pkt<R>& s, R w1, R w2) {
+__host__ __device__ __forceinline__ void pol_scatter(const DevModel<R>& M, Pkt<R>& s, R w1, R w2) {
   const R th = pol_theta(M, s.lam, w1);
   const R s11 = mueller_at(M, s.lam, 0, th), s12 = mueller_at(M, s.lam, 1, th);
   const R s33 = mueller_at(M, s.lam, 2, th), s34 = mueller_at(M, s.lam, 3, th);
@@ -336,7 +337,7 @@ __device__ __forceinline__ void pol_scatter(const DevModel<R>& M, Pkt<R>& s, R w
 
 // Stokes q, u of an escaping packet in the sky frame (reference: the disk axis projected on the sky)
 template <class R>
-__device__ __forceinline__ void pol_observer(const Pkt<R>& s, R& q, R& u) {
+__host__ __device__ __forceinline__ void pol_observer(const Pkt<R>& s, R& q, R& u) {
   q = s.sq;
   u = s.su;
   R nx = -s.uz * s.ux, ny = -s.uz * s.uy, nz = (R)1 - s.uz * s.uz;
