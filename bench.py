@@ -75,6 +75,8 @@ def parse():
                    help="instead of the transport step: ray-traced SED and image of the 200x120 disk at 45 degrees")
     p.add_argument("--viscous", action="store_true",
                    help="instead of the transport step: packets released by viscous heating in the 200x120 disk")
+    p.add_argument("--polarized", action="store_true",
+                   help="instead of the transport step: polarized transport (Rayleigh Mueller matrix) vs unpolarized")
     p.add_argument("--pda-min-visits", type=int, default=0,
                    help="PDA visit threshold; 0 scales the paper's 30 entries at 1e5 packets with the packet count "
                         "(Sect. 3.1 uses 30000 for its 1e8-packet runs)")
@@ -485,6 +487,49 @@ def viscous_timing(args):
     print(json.dumps(line), flush=True)
 
 
+def polarized_timing(args):
+    """Polarized transport (Sect. 2.3): the 200 x 120 rim-refined tau_mid = 1e6 gray disk with the exact
+    Rayleigh Mueller matrix in every bin, MRW (gamma = 2), 1e7 packets per step, FP32; timed with CUDA
+    events on the disk's stream (reset + transport), against the same run without polarization."""
+    import torch
+    from paper_0902_3092_gb300 import disks, mcrt
+    d = disks.config_thick_gray(200, 120, 1e6)
+    st = torch.cuda.Stream()
+    g = mcrt.Disk.from_model(d, stream=st.cuda_stream)
+    n = 10_000_000
+
+    def timed(pol):
+        g.set_mueller(disks.rayleigh_mueller(d.opacity.nlam, 181) if pol else None)
+        g.run_photons(n // 10, seed=99, mrw=True, gamma=2.0, max_events=10 ** 6)
+        ts, stats = [], None
+        for k in range(args.warmup + args.steps):
+            with torch.cuda.stream(st):
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(st)
+                g.reset()
+                stats = g.run_photons(n, seed=1 + k, mrw=True, gamma=2.0, max_events=10 ** 6)
+                e1.record(st)
+            torch.cuda.synchronize()
+            if k >= args.warmup:
+                ts.append(e0.elapsed_time(e1) * 1e-3)
+        return float(np.mean(ts)), stats
+
+    with ClockSampler(physical_gpu(0)) as clk:
+        t_pol, s_pol = timed(True)
+        t_unp, _ = timed(False)
+    g.set_mueller(disks.rayleigh_mueller(d.opacity.nlam, 181))
+    g.run_photons(n, seed=1, mrw=True, gamma=2.0, max_events=10 ** 6)
+    I, Q, U = (x.sum(axis=0) for x in g.sed_stokes())
+    line = {"metric": "polarized packets/s (Rayleigh Mueller matrix, MRW gamma=2)", "value": n / t_pol,
+            "unit": "packets/s", "higher_is_better": True, "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1e3 * t_pol, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": "200x120 rim-refined gray disk, tau_mid=1e6, albedo 0.5, Rayleigh Mueller matrix",
+                       "packets_per_step": n},
+            "unpolarized_packets_per_s": n / t_unp, "scatterings_per_packet": s_pol["scatterings"] / n,
+            "Q_over_I_by_inclination": [float(x) for x in Q / I], "clocks": clk.summary()}
+    print(json.dumps(line), flush=True)
+
+
 def main():
     args = parse()
     if args.impl == "reference":
@@ -504,6 +549,9 @@ def main():
         return
     if args.viscous:
         viscous_timing(args)
+        return
+    if args.polarized:
+        polarized_timing(args)
         return
     import torch
     import torch.distributed as dist
