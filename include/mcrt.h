@@ -11,7 +11,11 @@
  *   3. the partial diffusion approximation (PDA), div(D grad T^4) = 0 in the cells that few
  *      packets reached, Monte Carlo temperatures as boundary values (Sect. 2.2.1, Eq. 4)
  *                                                                              -> mcrt_solve_pda
- * plus the escaping-packet spectrum (mcrt_sed) and the adjoint of the PDA solve (mcrt_pda_adjoint).
+ * plus the escaping-packet spectrum (mcrt_sed) and the adjoint of the PDA solve (mcrt_pda_adjoint);
+ * batches of disks in one launch (mcrt_batch_*), the vertical hydrostatic structure (Sect. 2.5, Eq. 20:
+ * mcrt_hydrostatic_density), internal sources such as viscous heating (Sect. 5: mcrt_set_sources),
+ * polarized transport with a Mueller matrix (Sect. 2.3: mcrt_set_mueller, mcrt_sed_stokes) and
+ * ray-traced observables (Sect. 2.3, 4.1: mcrt_set_rays, mcrt_raytrace, mcrt_visibilities).
  *
  * Conventions
  *  - Units are cgs at this boundary: cm, g cm^-3, cm^2 g^-1, K, erg s^-1; wavelengths in micron.
@@ -249,7 +253,8 @@ mcrt_status mcrt_set_sources(mcrt_disk *d, const double *L_cell_erg_s);
  * applies the matrix; re-emitted packets and packets leaving an MRW sphere are unpolarized; escaping
  * packets add Q/I and U/I, in the frame of the disk axis projected on the sky, to fixed-point tallies
  * (2^20 per packet; read with mcrt_sed_stokes). Single disks only (batches and event traces refuse
- * polarized disks, MCRT_EINVAL); resets the tallies. */
+ * polarized disks, MCRT_EINVAL); resets the tallies; checkpoints hold neither the matrix nor the Stokes
+ * tallies. */
 mcrt_status mcrt_set_mueller(mcrt_disk *d, int nmu, const double *table);
 
 /* Escaped luminosity per (wavelength bin, inclination group) as Stokes I, Q, U (erg/s, each
