@@ -53,7 +53,8 @@ typedef enum {
   MCRT_ESTATE = 7     /* call order: e.g. transport before mcrt_set_opacity */
 } mcrt_status;
 
-/* Fixed-point energy unit: one packet energy L_star/N is 2^16 counts in the 64-bit tallies. */
+/* Fixed-point energy unit: one packet energy (L_star plus any internal sources) / N is 2^16 counts in
+ * the 64-bit tallies. */
 #define MCRT_EUNIT 65536
 /* Inclination bins of the escape spectrum, uniform in |cos i| over [0, 1]. */
 #define MCRT_NINC 10
@@ -96,7 +97,8 @@ typedef struct {
   int mrw_exit_dir;             /* direction after a jump: 0 isotropic, 1 cosine-weighted outward */
   uint64_t max_events_per_packet; /* a packet that exceeds this is dropped and counted as capped
                                      (values above 2^31 are taken as 2^31) */
-  uint64_t n_total_packets;     /* packets of the whole run (energy per packet L_star / n_total);
+  uint64_t n_total_packets;     /* packets of the whole run (energy per packet (L_star + internal
+                                   sources) / n_total);
                                    0 means the n_packets of this call */
   int block_size;               /* threads per block of the transport kernel (multiple of 32, <= 256);
                                    0: tuned default */
