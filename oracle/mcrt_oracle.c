@@ -256,6 +256,12 @@ typedef struct {
   int trace_max;         /* events per traced packet */
   int32_t *tr_type, *tr_cell, *tr_lam, *tr_n;
   double *tr_pos;        /* [packet][event][3] */
+  /* optional path-length estimator of the mean intensity: path length (cm) per [cell][bin] of all
+   * flights, J = E_pkt * jtally / (4 pi V) per bin (Lucy 1999); NULL: not kept */
+  double *jtally;
+  /* optional escape spectrum of the packets that scattered at least once, [lam*NINC + incl]; NULL: not
+   * kept */
+  uint64_t *sed_sca;
 } oracle_state;
 
 enum { EV_LAUNCH = 0, EV_CROSS = 1, EV_SCATTER = 2, EV_ABSORB = 3, EV_MRW = 4, EV_ESCAPE = 5, EV_CAPPED = 6 };
@@ -807,6 +813,18 @@ static void mrw_walk(ctx_t *x, or_rng *r, double p[3], double u[3], double e[3],
     U4(r, jb);
     double x0 = oracle_mrw_x(ja[0]);
     double ct = x0 * dmin * dmin / D;           /* path length c t */
+    if (s->jtally) {
+      /* the diffusing radiation has the spectrum of the diffusion flux, dBbar/dT / chi' (the MRW exit
+       * spectrum): the jump's path length counts in J with those weights */
+      oracle_dplanck_bins(m->lam_e, m->nlam, fmax(s->Tcell[c], 1.0), x->w);
+      double tot = 0.0;
+      for (int b = 0; b < m->nlam; ++b) {
+        x->w[b] /= chi_prime(m, b);
+        tot += x->w[b];
+      }
+      if (tot > 0)
+        for (int b = 0; b < m->nlam; ++b) s->jtally[(size_t)c * m->nlam + b] += ct * x->w[b] / tot;
+    }
     double E = ct * m->rho[c] * kbar;             /* Eq. 9, in packet energies */
     double units = floor(E * OR_EUNIT + 0.5);
     if (units >= 1.8e19) { s->cnt[CNT_ERR] |= 2u; units = 1.8e19; }
@@ -846,7 +864,7 @@ static void run_packet(ctx_t *x, uint64_t k, uint64_t seed, uint32_t model, int 
   uint64_t dep = 0, events = 0, crossings = 0;
   double p[3] = {0, 0, 0}, u[3], w[4];
   double e[3] = {1, 0, 0}, st[3] = {0, 0, 0}; /* polarization: reference vector and Stokes q, u, v */
-  int ir = -1, it = -1, ninc = 0, lam = 0;
+  int ir = -1, it = -1, ninc = 0, lam = 0, scattered = 0;
   double tau = 0.0;
   int released = 0;
   if (x->src_cum) {
@@ -932,15 +950,18 @@ static void run_packet(ctx_t *x, uint64_t k, uint64_t seed, uint32_t model, int 
     double s_int = alpha > 0 ? tau / alpha : INFINITY;
     if (s_int < s_face) {
       for (int d = 0; d < 3; ++d) p[d] += s_int * u[d];
+      if (s->jtally) s->jtally[(size_t)c * m->nlam + lam] += s_int;
       /* interaction */
       double omega = m->ksca[lam] / chi;
       U4(&r, w);
       if (w[0] < omega && x->pol) {
         oracle_pol_scatter(m->mueller + (size_t)lam * 4 * m->nmu, m->nmu, u, e, st, w[1], w[2]);
+        scattered = 1;
         s->cnt[CNT_SCA]++;
         trace(x, tp, &ntr, EV_SCATTER, c, p, lam);
       } else if (w[0] < omega) {
         double g = m->g[lam];
+        scattered = 1;
         if (g != 0.0) {
           double mu = hg_mu(g, w[1]);
           double phi = 2.0 * OR_PI * w[2];
@@ -980,6 +1001,7 @@ static void run_packet(ctx_t *x, uint64_t k, uint64_t seed, uint32_t model, int 
       tau = -log(w[3]);
     } else {
       for (int d = 0; d < 3; ++d) p[d] += s_face * u[d];
+      if (s->jtally && alpha > 0) s->jtally[(size_t)c * m->nlam + lam] += s_face;
       tau -= alpha * s_face;
       if (tau < 0) tau = 0;
       s->cnt[CNT_CROSS]++;
@@ -992,6 +1014,7 @@ static void run_packet(ctx_t *x, uint64_t k, uint64_t seed, uint32_t model, int 
         int ib = (int)(az * OR_NINC);
         if (ib >= OR_NINC) ib = OR_NINC - 1;
         s->sed[lam * OR_NINC + ib]++;
+        if (s->sed_sca && scattered) s->sed_sca[lam * OR_NINC + ib]++;
         if (x->pol) {
           double qo, uo;
           oracle_pol_observer(u, e, st, &qo, &uo);

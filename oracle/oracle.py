@@ -79,7 +79,8 @@ class _State(C.Structure):
                 ("trace_packets", C.c_int), ("trace_max", C.c_int),
                 ("tr_type", C.POINTER(C.c_int32)), ("tr_cell", C.POINTER(C.c_int32)),
                 ("tr_lam", C.POINTER(C.c_int32)), ("tr_n", C.POINTER(C.c_int32)),
-                ("tr_pos", C.POINTER(C.c_double))]
+                ("tr_pos", C.POINTER(C.c_double)), ("jtally", C.POINTER(C.c_double)),
+                ("sed_sca", C.POINTER(C.c_uint64))]
 
 
 def lib():
@@ -176,6 +177,8 @@ class Run:
         self.visits = np.zeros(n, np.uint64)
         self.nabs = np.zeros(n, np.uint64)
         self.sed = np.zeros(self.model.nlam * NINC, np.uint64)
+        self.jtally = None
+        self.sed_sca = np.zeros(self.model.nlam * NINC, np.uint64)
         self.sed_q = np.zeros(self.model.nlam * NINC, np.int64)
         self.sed_u = np.zeros(self.model.nlam * NINC, np.int64)
         self.Tcell = np.zeros(n, np.float64)
@@ -183,7 +186,9 @@ class Run:
         self.trace = None
 
     def run(self, n_packets, seed=1, first_id=0, n_total=None, mrw=False, gamma=2.0, nmin=20,
-            max_events=10 ** 9, want_sed=True, mrw_exit_dir=0, model_id=0, trace_packets=0, trace_max=0):
+            max_events=10 ** 9, want_sed=True, mrw_exit_dir=0, model_id=0, trace_packets=0, trace_max=0,
+            want_j=False):
+        """want_j: keep the path-length estimator of the mean intensity (see mean_intensity)."""
         L = lib()
         opts = _Opts(int(mrw), float(gamma), int(nmin), int(max_events), int(want_sed), int(mrw_exit_dir))
         st = _State()
@@ -191,6 +196,11 @@ class Run:
         st.sed_q = self.sed_q.ctypes.data_as(C.POINTER(C.c_int64))
         st.sed_u = self.sed_u.ctypes.data_as(C.POINTER(C.c_int64))
         st.Tcell = _dp(self.Tcell)
+        if want_j and self.jtally is None:
+            self.jtally = np.zeros(self.model.nr * self.model.nt * self.model.nlam)
+        if self.jtally is not None:
+            st.jtally = _dp(self.jtally)
+        st.sed_sca = _up(self.sed_sca)
         for i in range(10):
             st.cnt[i] = int(self.counters[i])
         tr = None
@@ -225,6 +235,17 @@ class Run:
         L.oracle_temperatures(self.model.ptr, _up(self.tally), float(self.n_total), _dp(T), _dp(e))
         return T.reshape(self.model.nr, self.model.nt), e.reshape(self.model.nr, self.model.nt)
 
+    def mean_intensity(self):
+        """Mean intensity per cell and bin (erg s^-1 cm^-2 sr^-1, integrated over the bin), shape
+        (nr, ntheta, nlam): J = E_pkt sum(path length) / (4 pi V), the path-length estimator."""
+        if self.jtally is None:
+            raise ValueError("run with want_j=True")
+        rf, tf = self.model.rf, self.model.tf
+        V = (2 * np.pi / 3) * (rf[1:] ** 3 - rf[:-1] ** 3)[:, None] * (np.cos(tf[:-1]) - np.cos(tf[1:]))[None, :]
+        e = self.packet_lum / self.n_total
+        jt = self.jtally.reshape(self.model.nr, self.model.nt, self.model.nlam)
+        return e * jt / (4 * np.pi * V[:, :, None])
+
     @property
     def packet_lum(self):
         """Luminosity the packets carry (erg/s): the star plus the internal sources."""
@@ -237,6 +258,10 @@ class Run:
         sh = (self.model.nlam, NINC)
         return (self.sed.reshape(sh).astype(np.float64) * e, self.sed_q.reshape(sh) / 1048576.0 * e,
                 self.sed_u.reshape(sh) / 1048576.0 * e)
+
+    def sed_scattered_lum(self):
+        """Escaped luminosity of the packets that scattered at least once, per (bin, inclination), erg/s."""
+        return self.sed_sca.reshape(self.model.nlam, NINC).astype(np.float64) * self.packet_lum / self.n_total
 
     def sed_lum(self):
         """Escaped luminosity per (wavelength bin, inclination bin), erg/s."""

@@ -12,8 +12,9 @@ Readings (the paper states what is computed, not how):
   Sect. 4.1); the caller passes T.
 * Source function per cell and wavelength bin: thermal emission over the total extinction,
   S_b = kappa_b Bbar_b(T) / (kappa_b + sigma_b), with Bbar_b the Planck function integrated over the
-  bin. Scattering removes light from a ray and adds none (the paper uses the scattered Monte Carlo field
-  as well; that field is not kept here).
+  bin; with the mean intensity J_b of a Monte Carlo run (path-length estimator) the scattered light
+  sigma_b J_b / (kappa_b + sigma_b) is added (isotropic scattering). Without J, scattering removes light
+  from a ray and adds none.
 * Within a cell S and the extinction are constant, so the integral along a segment of optical depth
   dtau is exact: a segment adds S (1 - exp(-dtau)), dimmed by exp(-tau) of everything between it and
   the observer.
@@ -106,8 +107,10 @@ def segments(disk, incl, p, q):
     return (ir * disk.ntheta + it)[ok], L[ok]
 
 
-def source(disk, T):
-    """S[c, b] = kappa_b Bbar_b(T_c) / chi_b (erg s^-1 cm^-2 sr^-1 per bin), cells r-major."""
+def source(disk, T, J=None):
+    """S[c, b] = kappa_b Bbar_b(T_c) / chi_b (erg s^-1 cm^-2 sr^-1 per bin), cells r-major; with the mean
+    intensity J (nr, ntheta, nlam) of a Monte Carlo run, the isotropic scattering term sigma_b J_b / chi_b
+    is added (the scattered light; exact for isotropic scattering)."""
     op = disk.opacity
     chi = op.kappa_abs + op.kappa_sca
     T = np.asarray(T, np.float64).ravel()
@@ -115,6 +118,8 @@ def source(disk, T):
     for c, t in enumerate(T):
         if t > 0:
             S[c] = op.kappa_abs * O.planck_bins(op.lam_edges_um, t) / chi
+    if J is not None:
+        S += np.asarray(J, np.float64).reshape(T.size, op.nlam) * (op.kappa_sca / chi)[None, :]
     return S
 
 
@@ -134,8 +139,8 @@ def intensity(disk, T, incl, p, q, S=None):
     return (S[cells] * (1.0 - np.exp(-dtau)) * np.exp(-front)).sum(axis=0)
 
 
-def image(disk, T, incl, p, q):
-    S = source(disk, T)
+def image(disk, T, incl, p, q, J=None):
+    S = source(disk, T, J)
     return np.array([intensity(disk, T, incl, pk, qk, S) for pk, qk in zip(p, q)])
 
 
@@ -155,10 +160,10 @@ def star_flux(disk, incl, dist):
     return math.pi * disk.star.R_cm ** 2 * Bs / dist ** 2 * np.exp(-star_tau(disk, incl))
 
 
-def sed(disk, T, incl, dist, p, q, w):
+def sed(disk, T, incl, dist, p, q, w, J=None):
     """Flux per bin (erg s^-1 cm^-2): sum_k w_k I_k / d^2 over the rays (w_k their sky-plane areas in
-    cm^2) plus the star. Returns (total, disk part)."""
-    I = image(disk, T, incl, p, q)
+    cm^2) plus the star. Returns (total, disk part). J: add the scattered light (see source)."""
+    I = image(disk, T, incl, p, q, J)
     Fd = (np.asarray(w)[:, None] * I).sum(axis=0) / dist ** 2
     return Fd + star_flux(disk, incl, dist), Fd
 
