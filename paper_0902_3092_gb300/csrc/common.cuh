@@ -146,7 +146,8 @@ enum CntIdx {
 };
 
 // ------------------------------------------------------------------------------------------------
-// Geometry helpers (templated on the floating type)
+// Geometry helpers (templated on the floating type; host and device, so that the same code can be
+// checked against the oracle on the CPU)
 // ------------------------------------------------------------------------------------------------
 template <class R>
 __device__ __forceinline__ R rsqrt_(R x);
@@ -156,12 +157,12 @@ template <>
 __device__ __forceinline__ double rsqrt_(double x) { return rsqrt(x); }
 
 template <class R>
-__device__ __forceinline__ R inf_() { return (R)INFINITY; }
+__host__ __device__ __forceinline__ R inf_() { return (R)INFINITY; }
 
 // Larger root of s^2 + 2 b s + c = 0 (leaving the sphere |x|^2 = R^2), from q = -(b + sign(b) sqrt(disc))
 // and c/q; the sign bit of b (not b >= 0) picks the branch, so b = -0 is handled like copysign does.
 template <class R>
-__device__ __forceinline__ R sphere_far(R b, R c) {
+__host__ __device__ __forceinline__ R sphere_far(R b, R c) {
   R disc = b * b - c;
   disc = disc > (R)0 ? disc : (R)0;
   const R q = -(b + copysign(sqrt(disc), b));
@@ -172,7 +173,7 @@ __device__ __forceinline__ R sphere_far(R b, R c) {
 
 // Smaller root when the sphere is hit from outside (b < 0), else infinity.
 template <class R>
-__device__ __forceinline__ R sphere_near(R b, R c) {
+__host__ __device__ __forceinline__ R sphere_near(R b, R c) {
   if (!(b < (R)0)) return inf_<R>();
   const R disc = b * b - c;
   if (disc < (R)0) return inf_<R>();
@@ -186,7 +187,7 @@ __device__ __forceinline__ R sphere_near(R b, R c) {
 // is >= 0 exactly where theta >= theta_f on the face's own nappe; the exit is where G changes sign
 // in the leaving direction, on that nappe.
 template <class R>
-__device__ __forceinline__ R cone_exit(const DevModel<R>& M, int f, R px, R py, R pz, R ux, R uy, R uz,
+__host__ __device__ __forceinline__ R cone_exit(const DevModel<R>& M, int f, R px, R py, R pz, R ux, R uy, R uz,
                                        bool leaving_down) {
   const int kind = M.fk[f];
   if (kind == 2) return inf_<R>();
@@ -224,7 +225,7 @@ __device__ __forceinline__ R cone_exit(const DevModel<R>& M, int f, R px, R py, 
 // Distance to the boundary of cell (ir, it) along the ray, and which face: 0 inner sphere,
 // 1 outer sphere, 2 lower polar face, 3 upper polar face.
 template <class R>
-__device__ __forceinline__ R next_face(const DevModel<R>& M, int ir, int it, R px, R py, R pz, R ux, R uy, R uz,
+__host__ __device__ __forceinline__ R next_face(const DevModel<R>& M, int ir, int it, R px, R py, R pz, R ux, R uy, R uz,
                                        int& face) {
   const R b = px * ux + py * uy + pz * uz;
   const R r2 = px * px + py * py + pz * pz;
@@ -246,7 +247,7 @@ __device__ __forceinline__ R next_face(const DevModel<R>& M, int ir, int it, R p
 // Smallest distance from p to the faces of cell (ir, it): d_min of Eq. 11. Also a lower bound on the
 // distance to the cell boundary along any direction.
 template <class R>
-__device__ __forceinline__ R dmin_cell(const DevModel<R>& M, int ir, int it, R px, R py, R pz) {
+__host__ __device__ __forceinline__ R dmin_cell(const DevModel<R>& M, int ir, int it, R px, R py, R pz) {
   const R rc2 = px * px + py * py;
   const R r = sqrt(rc2 + pz * pz);
   const R rc = sqrt(rc2);
@@ -260,7 +261,7 @@ __device__ __forceinline__ R dmin_cell(const DevModel<R>& M, int ir, int it, R p
 // and the valid one selected, so the dependency chains of the four faces overlap (a packet that
 // runs alone on its SM is latency bound). They return what the generic versions return.
 template <>
-__device__ __forceinline__ float sphere_far<float>(float b, float c) {
+__host__ __device__ __forceinline__ float sphere_far<float>(float b, float c) {
   const float disc = fmaxf(b * b - c, 0.f);
   const float q = -(b + copysignf(sqrtf(disc), b));
   const float s = fmaxf(q, c / q);
@@ -268,7 +269,7 @@ __device__ __forceinline__ float sphere_far<float>(float b, float c) {
 }
 
 template <>
-__device__ __forceinline__ float sphere_near<float>(float b, float c) {
+__host__ __device__ __forceinline__ float sphere_near<float>(float b, float c) {
   const float disc = b * b - c;
   const float q = -b + sqrtf(fmaxf(disc, 0.f));
   const float s = fmaxf(c / q, 0.f);
@@ -276,7 +277,7 @@ __device__ __forceinline__ float sphere_near<float>(float b, float c) {
 }
 
 template <>
-__device__ __forceinline__ float cone_exit<float>(const DevModel<float>& M, int f, float px, float py, float pz, float ux,
+__host__ __device__ __forceinline__ float cone_exit<float>(const DevModel<float>& M, int f, float px, float py, float pz, float ux,
                                                   float uy, float uz, bool leaving_down) {
   const int kind = M.fk[f];
   const float sig = (float)kind, cc = M.c2[f], ss = M.s2[f];
@@ -300,7 +301,7 @@ __device__ __forceinline__ float cone_exit<float>(const DevModel<float>& M, int 
 }
 
 template <>
-__device__ __forceinline__ float next_face<float>(const DevModel<float>& M, int ir, int it, float px, float py, float pz,
+__host__ __device__ __forceinline__ float next_face<float>(const DevModel<float>& M, int ir, int it, float px, float py, float pz,
                                                   float ux, float uy, float uz, int& face) {
   const float b = px * ux + py * uy + pz * uz;
   const float r2 = px * px + py * py + pz * pz;
@@ -318,7 +319,7 @@ __device__ __forceinline__ float next_face<float>(const DevModel<float>& M, int 
 }
 
 template <>
-__device__ __forceinline__ float dmin_cell<float>(const DevModel<float>& M, int ir, int it, float px, float py, float pz) {
+__host__ __device__ __forceinline__ float dmin_cell<float>(const DevModel<float>& M, int ir, int it, float px, float py, float pz) {
   const float rc2 = px * px + py * py;
   const float r = sqrtf(rc2 + pz * pz);
   const float rc = sqrtf(rc2);
@@ -330,7 +331,7 @@ __device__ __forceinline__ float dmin_cell<float>(const DevModel<float>& M, int 
 
 // Polar cell containing the direction of p: the last face k in 1..nt-1 with cos theta_k >= z/r.
 template <class R>
-__device__ __forceinline__ int theta_cell(const DevModel<R>& M, R px, R py, R pz) {
+__host__ __device__ __forceinline__ int theta_cell(const DevModel<R>& M, R px, R py, R pz) {
   const R mu = pz / sqrt(px * px + py * py + pz * pz);
   int lo = 0, hi = M.nt;  // invariant: answer in [lo, hi)
   while (hi - lo > 1) {
