@@ -257,7 +257,7 @@ typedef struct {
   int32_t *tr_type, *tr_cell, *tr_lam, *tr_n;
   double *tr_pos;        /* [packet][event][3] */
   /* optional path-length estimator of the mean intensity: path length (cm) per [cell][bin] of all
-   * flights, J = E_pkt * jtally / (4 pi V) per bin (Lucy 1999); NULL: not kept */
+   * flights and MRW jumps, J = E_pkt * jtally / (4 pi V) per bin (Lucy 1999); NULL: not kept */
   double *jtally;
   /* optional escape spectrum of the packets that scattered at least once, [lam*NINC + incl]; NULL: not
    * kept */
@@ -814,16 +814,21 @@ static void mrw_walk(ctx_t *x, or_rng *r, double p[3], double u[3], double e[3],
     double x0 = oracle_mrw_x(ja[0]);
     double ct = x0 * dmin * dmin / D;           /* path length c t */
     if (s->jtally) {
-      /* the diffusing radiation has the spectrum of the diffusion flux, dBbar/dT / chi' (the MRW exit
-       * spectrum): the jump's path length counts in J with those weights */
-      oracle_dplanck_bins(m->lam_e, m->nlam, fmax(s->Tcell[c], 1.0), x->w);
+      /* the walk's path length counts in J spread over the bins as Eq. 10 spreads it, by the distance
+       * travelled at each frequency, eta_b / chi'_b (eta: the fixed point of Eq. 13 at the cell's
+       * temperature), so that sum_b kappa_b J_b gives back the absorption of Eq. 9 */
+      oracle_eta_iterate(m, T, 500, x->w);
       double tot = 0.0;
       for (int b = 0; b < m->nlam; ++b) {
         x->w[b] /= chi_prime(m, b);
         tot += x->w[b];
       }
-      if (tot > 0)
-        for (int b = 0; b < m->nlam; ++b) s->jtally[(size_t)c * m->nlam + b] += ct * x->w[b] / tot;
+      if (!(tot > 0)) { /* no absorption: the closed-form fixed point, eta / chi' ~ dB/dT */
+        oracle_dplanck_bins(m->lam_e, m->nlam, T, x->w);
+        tot = 0.0;
+        for (int b = 0; b < m->nlam; ++b) tot += x->w[b];
+      }
+      for (int b = 0; b < m->nlam; ++b) s->jtally[(size_t)c * m->nlam + b] += ct * x->w[b] / tot;
     }
     double E = ct * m->rho[c] * kbar;             /* Eq. 9, in packet energies */
     double units = floor(E * OR_EUNIT + 0.5);

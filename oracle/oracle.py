@@ -237,7 +237,9 @@ class Run:
 
     def mean_intensity(self):
         """Mean intensity per cell and bin (erg s^-1 cm^-2 sr^-1, integrated over the bin), shape
-        (nr, ntheta, nlam): J = E_pkt sum(path length) / (4 pi V), the path-length estimator."""
+        (nr, ntheta, nlam): J = E_pkt (sum of path lengths) / (4 pi V), the path-length estimator;
+        flights count in the packet's bin, an MRW walk's c t over the bins with the weights of Eq. 10
+        (see mcrt_oracle.c)."""
         if self.jtally is None:
             raise ValueError("run with want_j=True")
         rf, tf = self.model.rf, self.model.tf

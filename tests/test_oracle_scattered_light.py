@@ -1,11 +1,12 @@
 """Pins of the oracle's mean-intensity estimator and of the scattered-light source function of its ray
 tracer (Sect. 2.3: the observables come from the computed source function, scattering included): the
-path-length estimator against the closed form of an optically thin absorbing shell, and the
-ray-traced scattered flux of a purely scattering disk against the Monte Carlo escape spectrum of the
+path-length estimator against the closed form of an optically thin absorbing shell and, with MRW
+walks, against radiative equilibrium, and the ray-traced scattered flux of a purely scattering disk against the Monte Carlo escape spectrum of the
 packets that scattered."""
 import math
 
 import numpy as np
+import pytest
 
 from paper_0902_3092_gb300 import disks
 
@@ -40,6 +41,31 @@ def test_mean_intensity_of_thin_absorbing_shell(oracle):
         t1, t2 = a * (rf[i] - rf[0]), a * (rf[i + 1] - rf[0])
         ref = Lb / (16 * math.pi ** 2) * (math.exp(-t1) - math.exp(-t2)) / a * 3 / (rf[i + 1] ** 3 - rf[i] ** 3)
         assert np.all(np.abs(Js[sel] / ref[sel] - 1) < 4 / np.sqrt(n_b[sel]) + 2e-3), (i, Js[sel] / ref[sel])
+
+
+@pytest.mark.parametrize("kind,n", [("gray", 20_000), ("nongray", 8_000)])
+def test_mean_intensity_balances_absorption_with_mrw(oracle, kind, n):
+    """Radiative equilibrium: a cell's absorbed energy, which sets its temperature, equals
+    4 pi m sum_b kappa_b J_b, the absorption the path-length J implies; with MRW walks (Eq. 9-10) the
+    walk's c t must count in J with the weights of Eq. 10, else the MRW cells break the balance (the
+    diffusion-flux spectrum dB/dT / chi' instead would put this dust's kappa_bar 27 % low, spreading at
+    the end-of-run temperature 10 % high). Every cell with 100 or more packet energies, within four
+    counting errors sqrt(n_abs) / (absorbed packet energies) plus 1e-3; cells where the walks deposit
+    over 40 % take part."""
+    d = disks.config_plain_gray(16, 16, 1e4) if kind == "gray" else disks.config_nongray(16, 16, 1e4)
+    r = oracle.Run(d).run(n, seed=5, mrw=True, gamma=2.0, nmin=5, want_j=True)
+    J = r.mean_intensity()
+    T, _ = r.temperatures()
+    op = d.opacity
+    units = r.tally.reshape(d.nr, d.ntheta) / 65536.0
+    nabs = r.nabs.reshape(d.nr, d.ntheta).astype(float)
+    n_mrw_cells = 0
+    for i, j in zip(*np.nonzero(units >= 100)):
+        absorbed = (op.kappa_abs * J[i, j]).sum()
+        emitted = (op.kappa_abs * oracle.planck_bins(op.lam_edges_um, T[i, j])).sum()
+        assert abs(absorbed / emitted - 1) < 4 * math.sqrt(nabs[i, j]) / units[i, j] + 1e-3, (i, j)
+        n_mrw_cells += nabs[i, j] < 0.6 * units[i, j]
+    assert r.stats["mrw_jumps"] > 300 and n_mrw_cells >= 2
 
 
 def test_ray_traced_scattered_light_matches_monte_carlo(oracle):
