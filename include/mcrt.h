@@ -15,7 +15,8 @@
  * batches of disks in one launch (mcrt_batch_*), the vertical hydrostatic structure (Sect. 2.5, Eq. 20:
  * mcrt_hydrostatic_density), internal sources such as viscous heating (Sect. 5: mcrt_set_sources),
  * polarized transport with a Mueller matrix (Sect. 2.3: mcrt_set_mueller, mcrt_sed_stokes) and
- * ray-traced observables (Sect. 2.3, 4.1: mcrt_set_rays, mcrt_raytrace, mcrt_visibilities).
+ * ray-traced observables (Sect. 2.3, 4.1: mcrt_set_rays, mcrt_raytrace, mcrt_visibilities) with the
+ * scattered light of a mean-intensity tally (mcrt_keep_mean_intensity, mcrt_mean_intensity).
  *
  * Conventions
  *  - Units are cgs at this boundary: cm, g cm^-3, cm^2 g^-1, K, erg s^-1; wavelengths in micron.
@@ -159,6 +160,8 @@ void mcrt_batch_destroy(mcrt_batch *b);
 mcrt_status mcrt_reset(mcrt_disk *d);
 
 enum { MCRT_T_MC = 0, MCRT_T_PDA = 1 };
+/* Flag for mcrt_raytrace's `which`: add the scattered light of the mean-intensity tally. */
+enum { MCRT_WITH_SCATTERING = 4 };
 
 /* Radiative-equilibrium temperature per cell (Sect. 2.1): solves 4 pi m kappa_P(T) B(T) = L_abs with
  * L_abs = tally / EUNIT * L_star / n_total. which = MCRT_T_MC: Monte Carlo temperatures; MCRT_T_PDA:
@@ -268,8 +271,9 @@ mcrt_status mcrt_sed_stokes(mcrt_disk *d, int n_incl, double *L_I, double *L_Q, 
  * function along rays, free of Monte Carlo noise; Sect. 4.1: SED from 0.1 um to 1 cm at 45 degrees,
  * N-band visibilities at a 100 m baseline). Readings: the source function of a cell in bin b is
  * kappa_b Bbar_b(T) / (kappa_b + sigma_b) with the cell's Monte Carlo temperature (the PDA temperatures
- * on request); scattering dims a ray and adds nothing to it; the star is a point source at the origin,
- * dimmed along the radial line towards the observer, and occults no ray.
+ * on request); scattering dims a ray, and adds the scattered light with MCRT_WITH_SCATTERING (below);
+ * the star is a point source at the origin, dimmed along the radial line towards the observer, and
+ * occults no ray.
  * Observer: direction o = (sin i, 0, cos i) for inclination i from the disk axis; sky-plane axes
  * e1 = (0, 1, 0) (the projected major axis) and e2 = (-cos i, 0, sin i); a ray through sky point (p, q)
  * is X(s) = p e1 + q e2 + s o. At most 256 wavelength bins. */
@@ -281,8 +285,27 @@ mcrt_status mcrt_sed_stokes(mcrt_disk *d, int n_incl, double *L_I, double *L_Q, 
 mcrt_status mcrt_set_rays(mcrt_disk *d, double incl_rad, double dist_cm, int64_t n, const double *p_cm,
                           const double *q_cm, const double *w_cm2);
 
+/* Mean intensity from the path lengths of the packets (Sect. 2.3: the scattering field of the observables;
+ * the path-length estimator, Lucy 1999). keep = 1: the following runs add the length of every flight to
+ * a tally per cell and wavelength bin (the bin the packet has in flight), and the path length c t of every
+ * MRW walk (Eq. 9, c t = x R0^2 / D) spread over the bins with the weights of Eq. 10, eta_b / chi'_b
+ * (dBbar_b/dT normalised, the fixed point of Eq. 13) at the cell's temperature when the walk starts,
+ * so that 4 pi m sum_b kappa_b J_b gives back the absorption. keep = 0: no tally (the production
+ * kernels). Single disks without polarization or event trace (those refuse it, MCRT_EINVAL); gray dust
+ * with want_sed = 0 keeps every flight in its launch bin. Resets the tallies; checkpoints do not hold it.
+ * Device memory: nr * ntheta * nlam doubles. MCRT_ESTATE before mcrt_set_opacity. */
+mcrt_status mcrt_keep_mean_intensity(mcrt_disk *d, int keep);
+
+/* J_out: host array nr * ntheta * nlam (cell-major, bins fastest), the mean intensity integrated over
+ * each bin, J = E_pkt (sum of path lengths) / (4 pi V) in erg s^-1 cm^-2 sr^-1, E_pkt the packet
+ * energy of the runs (zero before any run). MCRT_ESTATE without mcrt_keep_mean_intensity. */
+mcrt_status mcrt_mean_intensity(mcrt_disk *d, double *J_out);
+
 /* Traces the rays through the disk with the temperatures `which` (MCRT_T_MC, computed first if
- * needed, or MCRT_T_PDA after a PDA solve) in FP32 (precision 0 or 32) or FP64 (64). Outputs, each
+ * needed, or MCRT_T_PDA after a PDA solve) in FP32 (precision 0 or 32) or FP64 (64). With
+ * MCRT_WITH_SCATTERING or'ed into `which`, the source function adds the scattered light
+ * (sigma_b / chi_b) J_b of the mean-intensity tally (isotropic scattering; MCRT_ESTATE without
+ * mcrt_keep_mean_intensity). Outputs, each
  * optional (NULL): F_out[nlam] the flux per wavelength bin at the observer, sum_k w_k I_kb / d^2 plus
  * the star (erg s^-1 cm^-2, integrated over the bin); F_star_out[nlam] the star's part;
  * I_out[n * nlam] the intensity of every ray per bin (erg s^-1 cm^-2 sr^-1, ray-major);

@@ -23,7 +23,8 @@ COMMON = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-I", INCLUDE
 # written without cancellation, so a few ulps do not change which face a ray meets.
 UNITS = [("api.cu", []), ("pda.cu", []), ("transport_f32.cu", ["-prec-div=false", "-prec-sqrt=false"]),
          ("transport_f64.cu", ["-fmad=false"]), ("hydro.cu", ["-fmad=false"]),
-         ("raytrace.cu", ["-prec-div=false", "-prec-sqrt=false"])]
+         ("raytrace.cu", ["-prec-div=false", "-prec-sqrt=false"]),
+         ("transport_x32.cu", ["-prec-div=false", "-prec-sqrt=false"]), ("transport_x64.cu", ["-fmad=false"])]
 
 
 def nvcc() -> str:

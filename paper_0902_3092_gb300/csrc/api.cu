@@ -284,6 +284,8 @@ static DevModel<R> make_model(const mcrt_disk* d, bool f64) {
   m.nmu = d->pol ? d->nmu : 0;
   m.sed_q = d->sed_q.as<unsigned long long>();
   m.sed_u = d->sed_u.as<unsigned long long>();
+  m.jlen = d->keep_j ? d->jlen.as<double>() : nullptr;
+  m.jw = d->jw.as<float>();
   m.tally = d->tally.as<unsigned long long>();
   m.visits = d->visits.as<unsigned long long>();
   m.nabs = d->nabs.as<unsigned long long>();
@@ -327,6 +329,7 @@ static mcrt_status zero_tallies(mcrt_disk* d) {
   if (d->sed.p) CK(cudaMemsetAsync(d->sed.p, 0, d->sed.n, d->stream), "memset");
   if (d->sed_q.p) CK(cudaMemsetAsync(d->sed_q.p, 0, d->sed_q.n, d->stream), "memset");
   if (d->sed_u.p) CK(cudaMemsetAsync(d->sed_u.p, 0, d->sed_u.n, d->stream), "memset");
+  if (d->keep_j && d->jlen.p) CK(cudaMemsetAsync(d->jlen.p, 0, d->jlen.n, d->stream), "memset");
   d->have_T = false;
   d->have_pda = false;
   d->packets_done = 0;
@@ -590,6 +593,7 @@ mcrt_status mcrt_set_opacity(mcrt_disk* d, int nlam, const double* lam_e, const 
   const int nT = d->nT;
   const double dlnT = std::log(d->Tmax / d->Tmin) / (nT - 2);
   std::vector<float> lQk(nT), cbw((size_t)nT * nlam, 0.f), cexit((size_t)nT * nlam), chiRk(nT), kbark(nT);
+  std::vector<float> jw((size_t)nT * nlam, 0.f);  // Eq. 10 weights of the J tally: dBbar_b/dT normalised
   std::vector<double> lQ64(nT, -INFINITY), slQ64(nT, 4.0);  // FP64 log Q and d log Q / d log T (guess of T)
   lQk[0] = -INFINITY;
   for (int k = 0; k < nT; ++k) {
@@ -613,6 +617,8 @@ mcrt_status mcrt_set_opacity(mcrt_disk* d, int nlam, const double* lam_e, const 
     }
     chiRk[k] = (float)(sdb / sdbc);
     kbark[k] = (float)(skdb / sdb);
+    if (sdb > 0)
+      for (int b = 0; b < nlam; ++b) jw[(size_t)k * nlam + b] = (float)(dB[b] / sdb);
   }
   cudaError_t e;
 #define UP(buf, vec)                                   \
@@ -635,6 +641,7 @@ mcrt_status mcrt_set_opacity(mcrt_disk* d, int nlam, const double* lam_e, const 
   UP(d->cexit, cexit);
   UP(d->chiRk, chiRk);
   UP(d->kbark, kbark);
+  UP(d->jw, jw);
   UP(d->lam_e_d, d->lam_e);
   UP(d->kabs_d, d->kabs);
   UP(d->chip_d, chip);
@@ -643,6 +650,10 @@ mcrt_status mcrt_set_opacity(mcrt_disk* d, int nlam, const double* lam_e, const 
   d->kbar0 = (float)d->kabs[0];
   e = d->sed.alloc((size_t)nlam * kNInc * 8);
   if (e != cudaSuccess) return cuda_fail(d, e, "cudaMalloc");
+  if (d->keep_j) {  // the J tally follows the number of bins
+    e = d->jlen.alloc((size_t)d->nr * d->nt * nlam * 8);
+    if (e != cudaSuccess) return cuda_fail(d, e, "cudaMalloc");
+  }
   d->has_opacity = true;
   mcrt_status st = zero_tallies(d);
   if (st != MCRT_OK) return st;
@@ -772,8 +783,10 @@ static mcrt_status run_impl(mcrt_disk* d, uint64_t n_packets, uint64_t seed, uin
   d->n_total = (double)(o->n_total_packets ? o->n_total_packets : n_packets);
   const bool trace = trace_max > 0;
   const bool f64 = trace || o->precision == 64;
-  const bool pol = d->pol;
+  const bool pol = d->pol, jt = d->keep_j;
   if (pol && trace) return set_error(d, MCRT_EINVAL, "polarized transport has no event trace");
+  if (jt && trace) return set_error(d, MCRT_EINVAL, "the mean-intensity tally has no event trace");
+  if (jt && pol) return set_error(d, MCRT_EINVAL, "polarized transport does not keep the mean intensity");
   CK(cudaMemsetAsync(d->cnt.p, 0, C_NCNT * 8, d->stream), "memset");
   CK(cudaMemsetAsync(d->queue.p, 0, 8, d->stream), "memset");
   DBuf ttype, tcell, tlam, tpos, tn;
@@ -817,17 +830,20 @@ static mcrt_status run_impl(mcrt_disk* d, uint64_t n_packets, uint64_t seed, uin
         P.tr_n = tn.as<int32_t>();
         P.l_unit = d->l_unit;
       }
-      const int bps = pol ? transport_blocks_per_sm_pol<double>(d->gray, block)
-                          : transport_blocks_per_sm<double>(trace, false, d->gray, block);
+      const int bps = pol  ? transport_blocks_per_sm_pol<double>(d->gray, block)
+                      : jt ? transport_blocks_per_sm_j<double>(d->gray, block)
+                           : transport_blocks_per_sm<double>(trace, false, d->gray, block);
       const long long want = (long long)((n_packets + block - 1) / block);
       const int grid = (int)std::max(1ll, std::min<long long>(want, (long long)dev_sms * std::max(1, bps)));
       const bool tail = setup_pool(d, P, (unsigned)grid * block, o->tail_warps_per_sm);
-      e = pol ? launch_transport_pol<double>(P, d->gray, grid, block, d->stream)
-              : launch_transport<double>(P, trace, false, d->gray, grid, block, d->stream);
+      e = pol  ? launch_transport_pol<double>(P, d->gray, grid, block, d->stream)
+          : jt ? launch_transport_j<double>(P, d->gray, grid, block, d->stream)
+               : launch_transport<double>(P, trace, false, d->gray, grid, block, d->stream);
       d->launches++;
       if (e == cudaSuccess && tail) {
-        e = pol ? launch_transport_tail_pol<double>(P, d->gray, dev_sms, o->tail_warps_per_sm, d->stream)
-                : launch_transport_tail<double>(P, trace, false, d->gray, dev_sms, o->tail_warps_per_sm, d->stream);
+        e = pol  ? launch_transport_tail_pol<double>(P, d->gray, dev_sms, o->tail_warps_per_sm, d->stream)
+            : jt ? launch_transport_tail_j<double>(P, d->gray, dev_sms, o->tail_warps_per_sm, d->stream)
+                 : launch_transport_tail<double>(P, trace, false, d->gray, dev_sms, o->tail_warps_per_sm, d->stream);
         d->launches++;
       }
     } else {
@@ -842,17 +858,20 @@ static mcrt_status run_impl(mcrt_disk* d, uint64_t n_packets, uint64_t seed, uin
       P.total = n_packets;
       P.queue = d->queue.as<unsigned long long>();
       P.want_lam = (!d->gray || o->want_sed) ? 1 : 0;
-      const int bps = pol ? transport_blocks_per_sm_pol<float>(d->gray, block)
-                          : transport_blocks_per_sm<float>(false, false, d->gray, block);
+      const int bps = pol  ? transport_blocks_per_sm_pol<float>(d->gray, block)
+                      : jt ? transport_blocks_per_sm_j<float>(d->gray, block)
+                           : transport_blocks_per_sm<float>(false, false, d->gray, block);
       const long long want = (long long)((n_packets + block - 1) / block);
       const int grid = (int)std::max(1ll, std::min<long long>(want, (long long)dev_sms * std::max(1, bps)));
       const bool tail = setup_pool(d, P, (unsigned)grid * block, o->tail_warps_per_sm);
-      e = pol ? launch_transport_pol<float>(P, d->gray, grid, block, d->stream)
-              : launch_transport<float>(P, false, false, d->gray, grid, block, d->stream);
+      e = pol  ? launch_transport_pol<float>(P, d->gray, grid, block, d->stream)
+          : jt ? launch_transport_j<float>(P, d->gray, grid, block, d->stream)
+               : launch_transport<float>(P, false, false, d->gray, grid, block, d->stream);
       d->launches++;
       if (e == cudaSuccess && tail) {
-        e = pol ? launch_transport_tail_pol<float>(P, d->gray, dev_sms, o->tail_warps_per_sm, d->stream)
-                : launch_transport_tail<float>(P, false, false, d->gray, dev_sms, o->tail_warps_per_sm, d->stream);
+        e = pol  ? launch_transport_tail_pol<float>(P, d->gray, dev_sms, o->tail_warps_per_sm, d->stream)
+            : jt ? launch_transport_tail_j<float>(P, d->gray, dev_sms, o->tail_warps_per_sm, d->stream)
+                 : launch_transport_tail<float>(P, false, false, d->gray, dev_sms, o->tail_warps_per_sm, d->stream);
         d->launches++;
       }
     }
@@ -913,6 +932,7 @@ mcrt_status mcrt_run_batch(mcrt_disk* const* disks, int n, const uint64_t* n_pac
     if (!disks[i]) return set_error(nullptr, MCRT_EINVAL, "NULL disk in batch");
     if (!disks[i]->has_opacity) return set_error(disks[i], MCRT_ESTATE, "mcrt_set_opacity must come first");
     if (disks[i]->pol) return set_error(disks[i], MCRT_EINVAL, "batches do not take polarized disks");
+    if (disks[i]->keep_j) return set_error(disks[i], MCRT_EINVAL, "batches do not keep the mean intensity");
     if (disks[i]->device != d0->device) return set_error(disks[i], MCRT_EINVAL, "batch disks on different devices");
   }
   mcrt_disk* d = d0;
@@ -1061,6 +1081,23 @@ mcrt_status mcrt_sed(mcrt_disk* d, int n_incl, double* L) {
 
 // checkpoint layout: 8 x uint64 header (magic, version, nr, nt, nlam, packets_done, n_total bits, 0),
 // then tally, visits, nabs (nr*nt each) and sed (nlam*10), all uint64.
+mcrt_status mcrt_keep_mean_intensity(mcrt_disk* d, int keep) {
+  if (!d) return set_error(nullptr, MCRT_EINVAL, "disk is NULL");
+  if (!d->has_opacity) return set_error(d, MCRT_ESTATE, "mcrt_set_opacity must come first");
+  CK(cudaSetDevice(d->device), "cudaSetDevice");
+  const size_t bytes = (size_t)d->nr * d->nt * d->nlam * 8;
+  if (keep && d->jlen.n != bytes) {
+    cudaError_t e = d->jlen.alloc(bytes);
+    if (e != cudaSuccess) return cuda_fail(d, e, "cudaMalloc");
+  }
+  if (!keep) d->jlen.release();
+  d->keep_j = keep != 0;
+  mcrt_status s = zero_tallies(d);
+  if (s != MCRT_OK) return s;
+  CK(cudaStreamSynchronize(d->stream), "synchronize");
+  return MCRT_OK;
+}
+
 mcrt_status mcrt_set_mueller(mcrt_disk* d, int nmu, const double* table) {
   if (!d) return set_error(nullptr, MCRT_EINVAL, "disk is NULL");
   if (!d->has_opacity) return set_error(d, MCRT_ESTATE, "mcrt_set_opacity must come first");
@@ -1301,6 +1338,7 @@ mcrt_status mcrt_batch_create(mcrt_disk* const* disks, int n, const uint64_t* n_
     if (!disks[i]) return set_error(nullptr, MCRT_EINVAL, "NULL disk in batch");
     if (!disks[i]->has_opacity) return set_error(disks[i], MCRT_ESTATE, "mcrt_set_opacity must come first");
     if (disks[i]->pol) return set_error(disks[i], MCRT_EINVAL, "batches do not take polarized disks");
+    if (disks[i]->keep_j) return set_error(disks[i], MCRT_EINVAL, "batches do not keep the mean intensity");
     if (disks[i]->device != disks[0]->device) return set_error(nullptr, MCRT_EINVAL, "disks on different devices");
   }
   mcrt_disk* d = disks[0];

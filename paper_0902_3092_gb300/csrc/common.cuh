@@ -124,6 +124,11 @@ struct DevModel {
   int nmu;
   unsigned long long* sed_q;
   unsigned long long* sed_u;
+  // path-length estimator of the mean intensity: path length (internal units) of flights and MRW walks
+  // per [cell][bin], NULL when not kept; the weights of Eq. 10 that spread a walk over the bins, per
+  // [T_k][bin] (dBbar_b/dT normalised: eta_b / chi'_b at the fixed point of Eq. 13)
+  double* jlen;
+  const float* jw;
   // tallies
   unsigned long long* tally;   // nr*nt fixed-point absorbed energy
   unsigned long long* visits;  // nr*nt packet entries

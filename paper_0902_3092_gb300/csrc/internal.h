@@ -55,6 +55,13 @@ template <class R>
 cudaError_t launch_transport_tail_pol(const KParams<R>& P, bool gray, int sms, int warps_per_sm, cudaStream_t st);
 template <class R>
 int transport_blocks_per_sm_pol(bool gray, int block);
+// transport that keeps the path-length estimator of the mean intensity (single disk, no event trace)
+template <class R>
+cudaError_t launch_transport_j(const KParams<R>& P, bool gray, int grid, int block, cudaStream_t st);
+template <class R>
+cudaError_t launch_transport_tail_j(const KParams<R>& P, bool gray, int sms, int warps_per_sm, cudaStream_t st);
+template <class R>
+int transport_blocks_per_sm_j(bool gray, int block);
 
 }  // namespace mcrt
 
@@ -76,6 +83,10 @@ struct mcrt_disk {
   bool pol = false;
   int nmu = 0;
   mcrt::DBuf mtab32, mtab64, mcdf32, mcdf64, sed_q, sed_u;
+  // path-length estimator of the mean intensity (kept on request): path length per [cell][bin], and the
+  // Eq. 10 weights per [T_k][bin] that spread an MRW walk over the bins
+  bool keep_j = false;
+  mcrt::DBuf jlen, jw;
   std::vector<double> rf, tf, rho, mass;
   std::vector<double> lam_e, kabs, ksca, g;
   // temperature grid

@@ -52,10 +52,32 @@ namespace {
 constexpr int kRayBlock = 256;
 constexpr int kSedBlock = 128;
 
-// S[c][b] = kappa_b Bbar_b(T_c) / chi_b, FP64 bin integrals; one warp per cell, lanes over bins.
+// Volume of cell c (internal units): (2 pi / 3) (r1^3 - r0^3) (cos theta0 - cos theta1).
+__device__ __forceinline__ double cell_volume(const double* rf, const double* cf, int nt, int c) {
+  const int i = c / nt, j = c - i * nt;
+  const double r0 = rf[i], r1 = rf[i + 1];
+  return (2.0 * kPi / 3.0) * (r1 * r1 * r1 - r0 * r0 * r0) * (cf[j] - cf[j + 1]);
+}
+
+// The mean intensity of the path-length estimator, J[c][b] = jfac jlen[c][b] / V_c with
+// jfac = E_pkt / (4 pi l^2) (erg s^-1 cm^-2 sr^-1, integrated over the bin; jlen and V in internal units).
+__global__ void k_mean_intensity(int nc, int nt, int nlam, const double* __restrict__ rf, const double* __restrict__ cf,
+                                 const double* __restrict__ jlen, double jfac, double* __restrict__ J) {
+  const size_t n = (size_t)nc * nlam;
+  for (size_t k = blockIdx.x * (size_t)blockDim.x + threadIdx.x; k < n; k += (size_t)gridDim.x * blockDim.x) {
+    const int c = (int)(k / nlam);
+    J[k] = jfac * jlen[k] / cell_volume(rf, cf, nt, c);
+  }
+}
+
+// Source function per cell and bin: S[c][b] = kappa_b Bbar_b(T_c) / chi_b (FP64 bin integrals), plus
+// the scattered light (sigma_b / chi_b) J_b of the mean-intensity tally when jlen is given (isotropic
+// scattering); one warp per cell, lanes over bins.
 template <class R>
 __global__ void k_source(int nc, int nlam, const double* __restrict__ T, const double* __restrict__ lam_e,
-                         const double* __restrict__ kabs, const double* __restrict__ chi, R* __restrict__ S) {
+                         const double* __restrict__ kabs, const double* __restrict__ chi, R* __restrict__ S,
+                         const double* __restrict__ jlen, double jfac, const double* __restrict__ alb,
+                         const double* __restrict__ rf, const double* __restrict__ cf, int nt) {
   const int lane = threadIdx.x & 31;
   const int nw = (gridDim.x * blockDim.x) >> 5;
   const double k4 = kKB * kKB * kKB * kKB;
@@ -73,6 +95,7 @@ __global__ void k_source(int nc, int nlam, const double* __restrict__ T, const d
         else tails(kH * kC / (lam_e[b + 1] * 1e-4 * kKB * t), g_long, g4);
         v = pref3 * (g_long - g_short) * kabs[b] / chi[b];
       }
+      if (jlen) v += alb[b] * (jfac * jlen[(size_t)c * nlam + b] / cell_volume(rf, cf, nt, c));
       S[(size_t)c * nlam + b] = (R)v;
     }
   }
@@ -343,18 +366,28 @@ DevModel<double> model_of<double>(const mcrt_disk* d) { return d->model64(); }
 template <class R>
 const R* chi_of(const mcrt_disk* d) { return static_cast<const R*>(sizeof(R) == 8 ? d->chi64.p : d->chi32.p); }
 
+// E_pkt / (4 pi l^2): turns path length per internal volume into the mean intensity; 0 before any run
+static double j_factor(const mcrt_disk* d) {
+  if (!d->packets_done || !(d->n_total > 0)) return 0.0;
+  return d->Lpkt() / d->n_total / (4.0 * kPi * d->l_unit * d->l_unit);
+}
+
 template <class R>
 mcrt_status trace_impl(mcrt_disk* d, int which) {
   RayState* rs = d->rays;
   const size_t nc = (size_t)d->nr * d->nt;
   const int nlam = d->nlam;
-  const double* T = which == MCRT_T_PDA ? d->T_pda.as<double>() : d->T_mc.as<double>();
+  const bool scat = (which & MCRT_WITH_SCATTERING) != 0;
+  const double* T = (which & ~MCRT_WITH_SCATTERING) == MCRT_T_PDA ? d->T_pda.as<double>() : d->T_mc.as<double>();
   const int prec = sizeof(R) == 8 ? 64 : 32;
   if (rs->S_epoch != d->T_epoch || rs->S_which != which || rs->S_prec != prec || !rs->S.p) {
     if (rs->S.n < nc * nlam * sizeof(R)) CK(rs->S.alloc(nc * nlam * sizeof(R)), "cudaMalloc");
     const int blocks = (int)((nc * 32 + 255) / 256);
     k_source<R><<<blocks, 256, 0, d->stream>>>((int)nc, nlam, T, d->lam_e_d.as<double>(), d->kabs_d.as<double>(),
-                                               d->chi64.as<double>(), rs->S.as<R>());
+                                               d->chi64.as<double>(), rs->S.as<R>(),
+                                               scat ? d->jlen.as<double>() : nullptr, j_factor(d),
+                                               d->alb64.as<double>(), d->rf64.as<double>(), d->cf64.as<double>(),
+                                               d->nt);
     d->launches++;
     CK(cudaGetLastError(), "source kernel");
     rs->S_epoch = d->T_epoch;
@@ -446,13 +479,34 @@ mcrt_status mcrt_set_rays(mcrt_disk* d, double incl_rad, double dist_cm, int64_t
   return MCRT_OK;
 }
 
+mcrt_status mcrt_mean_intensity(mcrt_disk* d, double* J_out) {
+  if (!d) return set_error(nullptr, MCRT_EINVAL, "disk is NULL");
+  if (!J_out) return set_error(d, MCRT_EINVAL, "J_out must not be NULL");
+  if (!d->keep_j) return set_error(d, MCRT_ESTATE, "mcrt_keep_mean_intensity must come first");
+  CK(cudaSetDevice(d->device), "cudaSetDevice");
+  const size_t nc = (size_t)d->nr * d->nt, n = nc * d->nlam;
+  DBuf J;
+  CK(J.alloc(n * 8), "cudaMalloc");
+  const int blocks = (int)std::min<size_t>((n + 255) / 256, (size_t)sm_count(d->device) * 8);
+  k_mean_intensity<<<blocks, 256, 0, d->stream>>>((int)nc, d->nt, d->nlam, d->rf64.as<double>(), d->cf64.as<double>(),
+                                                  d->jlen.as<double>(), j_factor(d), J.as<double>());
+  d->launches++;
+  CK(cudaGetLastError(), "mean-intensity kernel");
+  CK(cudaMemcpyAsync(J_out, J.p, n * 8, cudaMemcpyDeviceToHost, d->stream), "copy");
+  CK(cudaStreamSynchronize(d->stream), "synchronize");
+  return MCRT_OK;
+}
+
 mcrt_status mcrt_raytrace(mcrt_disk* d, int which, int precision, double* F_out, double* F_star_out, double* I_out,
                           uint64_t* n_segments) {
   if (!d) return set_error(nullptr, MCRT_EINVAL, "disk is NULL");
   if (!d->rays || d->rays->n < 1) return set_error(d, MCRT_ESTATE, "mcrt_set_rays must come first");
-  if (which != MCRT_T_MC && which != MCRT_T_PDA) return set_error(d, MCRT_EINVAL, "which");
+  const int base = which & ~MCRT_WITH_SCATTERING;
+  if (base != MCRT_T_MC && base != MCRT_T_PDA) return set_error(d, MCRT_EINVAL, "which");
   if (precision != 0 && precision != 32 && precision != 64) return set_error(d, MCRT_EINVAL, "precision: 32 or 64");
-  if (which == MCRT_T_PDA && !d->have_pda) return set_error(d, MCRT_ESTATE, "no PDA solution");
+  if (base == MCRT_T_PDA && !d->have_pda) return set_error(d, MCRT_ESTATE, "no PDA solution");
+  if ((which & MCRT_WITH_SCATTERING) && !d->keep_j)
+    return set_error(d, MCRT_ESTATE, "scattered light needs the mean-intensity tally (mcrt_keep_mean_intensity)");
   if (d->nlam > 256) return set_error(d, MCRT_EINVAL, "ray tracing takes at most 256 wavelength bins");
   CK(cudaSetDevice(d->device), "cudaSetDevice");
   if (!d->have_T) {

@@ -520,7 +520,7 @@ __device__ __forceinline__ void set_alpha(const DevModel<R>& M, Pkt<R>& s) {
   s.ialpha = s.alpha > (R)0 ? (R)1 / s.alpha : (R)0;
 }
 
-template <class R, bool TRACE, bool G, bool POL = false, class RNG>
+template <class R, bool TRACE, bool G, bool POL = false, bool JT = false, class RNG>
 __device__ __forceinline__ void launch_packet(const KParams<R>& P, RNG& rng, const DevModel<R>& M, Pkt<R>& s,
                               unsigned long long k, int tslot, Acc& acc) {
   s.model = M.model_id;
@@ -601,7 +601,30 @@ __device__ __forceinline__ void launch_packet(const KParams<R>& P, RNG& rng, con
 template <class R>
 __device__ __forceinline__ R dsafe_margin() { return sizeof(R) == 4 ? (R)(1.0 - 1e-5) : (R)(1.0 - 1e-12); }
 
-template <class R, bool TRACE, bool G, bool POL = false, class RNG>
+// Path-length estimator of the mean intensity (the scattering field of the observables, Sect. 2.3):
+// every flight adds its length to the tally of its cell and bin.
+template <class R, class RNG>
+__device__ __forceinline__ void j_flight(const DevModel<R>& M, int c, int lam, R len) {
+  if (lead<RNG>()) atomicAdd(M.jlen + (size_t)c * M.nlam + lam, (double)len);
+}
+
+// An MRW walk of path length ct in cell c adds it spread over the bins with the weights of Eq. 10 (the
+// distance travelled at each frequency, eta_b / chi'_b), interpolated at the cell's T-grid position
+// (k, w); the lanes of a warp that carries one packet share the bins.
+template <class R, class RNG>
+__device__ __forceinline__ void j_walk(const DevModel<R>& M, int c, R ct, int k, float w) {
+  const float* w0 = M.jw + (size_t)k * M.nlam;
+  const float* w1 = w0 + M.nlam;
+  double* dst = M.jlen + (size_t)c * M.nlam;
+  const int first = RNG::coop ? (int)(threadIdx.x & 31u) : 0;
+  const int stride = RNG::coop ? 32 : 1;
+  for (int b = first; b < M.nlam; b += stride) {
+    const float wb = (1.f - w) * __ldg(w0 + b) + w * __ldg(w1 + b);
+    if (wb > 0.f) atomicAdd(dst + b, (double)ct * (double)wb);
+  }
+}
+
+template <class R, bool TRACE, bool G, bool POL = false, bool JT = false, class RNG>
 __device__ __forceinline__ void mrw_chain(const KParams<R>& P, RNG& rng, const DevModel<R>& M, Pkt<R>& s, int c,
                                           Acc& acc) {
   const R rho = M.rho[c];
@@ -610,15 +633,16 @@ __device__ __forceinline__ void mrw_chain(const KParams<R>& P, RNG& rng, const D
     const R dm = dmin_cell(M, s.ir, s.it, s.px, s.py, s.pz);
     s.dsafe = dm * dsafe_margin<R>();  // d_min at the current position bounds the next flight's face test
     R chiR, kb;
+    int kq = 0;  // the cell's position on the T grid (non-gray dust, or the J weights)
+    float wq = 0.f;
     if (G || M.gray) {
       chiR = M.chiR0;
       kb = M.kbar0;
+      if (JT) qpos(M, *(volatile unsigned long long*)(M.tally + c), c, kq, wq);
     } else {
-      int k;
-      float w;
-      qpos(M, *(volatile unsigned long long*)(M.tally + c), c, k, w);
-      chiR = (R)((1.f - w) * __ldg(M.chiR + k) + w * __ldg(M.chiR + k + 1));
-      kb = (R)((1.f - w) * __ldg(M.kbar + k) + w * __ldg(M.kbar + k + 1));
+      qpos(M, *(volatile unsigned long long*)(M.tally + c), c, kq, wq);
+      chiR = (R)((1.f - wq) * __ldg(M.chiR + kq) + wq * __ldg(M.chiR + kq + 1));
+      kb = (R)((1.f - wq) * __ldg(M.kbar + kq) + wq * __ldg(M.kbar + kq + 1));
     }
     if (!(dm * rho * chiR > P.gamma)) break;  // Eq. 11
     const uint4 ja = rng.next(s);  // escape-time quantile, point on the sphere, exit bin
@@ -626,13 +650,15 @@ __device__ __forceinline__ void mrw_chain(const KParams<R>& P, RNG& rng, const D
     const R x = mrw_x(P, uni<R>(ja.x));
     const R tau0 = dm * rho;
     const R E = (R)3 * x * tau0 * tau0 * chiR * kb;  // Eq. 9 with c t = x R0^2 / D, D = 1/(3 rho chi_R)
+    if (JT) j_walk<R, RNG>(M, c, (R)3 * x * dm * dm * rho * chiR, kq, wq);
     R units = floor(E * (R)kEUnit + (R)0.5);
     if (!(units < (R)1.8e19)) {
       units = (R)1.8e19;
       acc.err |= kErrMrwClip;
     }
     const unsigned long long du = (unsigned long long)units;
-    const bool lam_now = P.want_lam && (!(G || M.gray) || TRACE);  // the exit bin needs the tally now
+    // the exit bin needs the tally now (the J tally needs the bin of every flight)
+    const bool lam_now = P.want_lam && (!(G || M.gray) || TRACE || JT);
     unsigned long long old = 0;
     if (lam_now) {
       if (lead<RNG>()) old = atomicAdd(M.tally + c, du);
@@ -677,7 +703,7 @@ __device__ __forceinline__ void mrw_chain(const KParams<R>& P, RNG& rng, const D
 
 // Moves a packet to its next event: enters the next cell (1), reaches an interaction point (2, the
 // interaction itself is left to interact()), or ends (0: escaped, or a step guard).
-template <class R, bool TRACE, bool G, bool POL = false, class RNG>
+template <class R, bool TRACE, bool G, bool POL = false, bool JT = false, class RNG>
 __device__ __forceinline__ int advance(const KParams<R>& P, RNG& rng, const DevModel<R>& M, Pkt<R>& s, Acc& acc) {
   if (++s.steps > P.max_steps) {
     acc.err |= kErrStepGuard;
@@ -725,6 +751,7 @@ __device__ __forceinline__ int advance(const KParams<R>& P, RNG& rng, const DevM
     }
   }
   if (hit) {
+    if (JT) j_flight<R, RNG>(M, s.ir * M.nt + s.it, s.lam, s_int);
     s.xcross = 0;
     s.px += s_int * s.ux;
     s.py += s_int * s.uy;
@@ -738,6 +765,7 @@ __device__ __forceinline__ int advance(const KParams<R>& P, RNG& rng, const DevM
     acc.capped++;
     return 0;
   }
+  if (JT && alpha > (R)0) j_flight<R, RNG>(M, s.ir * M.nt + s.it, s.lam, s_face);
   s.px += s_face * s.ux;
   s.py += s_face * s.uy;
   s.pz += s_face * s.uz;
@@ -783,7 +811,7 @@ __device__ __forceinline__ int advance(const KParams<R>& P, RNG& rng, const DevM
 // The interaction at the packet's current point (Sect. 2.1): scattering or absorption with immediate
 // re-emission, then the MRW chain (Sect. 2.2.2) and the next optical depth. A release (the first event
 // of an internal source's packet) is an absorption with omega = 0. False: capped.
-template <class R, bool TRACE, bool G, bool POL = false, class RNG>
+template <class R, bool TRACE, bool G, bool POL = false, bool JT = false, class RNG>
 __device__ __forceinline__ bool interact(const KParams<R>& P, RNG& rng, const DevModel<R>& M, Pkt<R>& s, Acc& acc,
                                          bool release = false) {
   const int c = s.ir * M.nt + s.it;
@@ -795,7 +823,7 @@ __device__ __forceinline__ bool interact(const KParams<R>& P, RNG& rng, const De
   const R tau_next = neg_log<R>(uni<R>(w.w));
   if (!sca) {
     const R ul = (a - om) / ((R)1 - om);  // the albedo uniform conditioned on absorption: the BW bin draw
-    if (P.want_lam && (!(G || M.gray) || TRACE)) {
+    if (P.want_lam && (!(G || M.gray) || TRACE || JT)) {
       // the old tally sets T_old / T_new of the BW re-emission
       unsigned long long old = 0;
       if (lead<RNG>()) old = atomicAdd(M.tally + c, kEUnit);
@@ -836,7 +864,7 @@ __device__ __forceinline__ bool interact(const KParams<R>& P, RNG& rng, const De
   trace_ev<R, TRACE>(P, s, sca ? EV_SCATTER : EV_ABSORB, c);
   s.events++;
   s.ninc++;
-  if (P.mrw && s.ninc >= P.nmin) mrw_chain<R, TRACE, G, POL>(P, rng, M, s, c, acc);
+  if (P.mrw && s.ninc >= P.nmin) mrw_chain<R, TRACE, G, POL, JT>(P, rng, M, s, c, acc);
   if (s.events >= P.max_events) {
     acc.capped++;
     trace_ev<R, TRACE>(P, s, EV_CAPPED, c);
@@ -847,15 +875,15 @@ __device__ __forceinline__ bool interact(const KParams<R>& P, RNG& rng, const De
 }
 
 // One event of a packet, an interaction run at once. False when the packet has ended.
-template <class R, bool TRACE, bool G, bool POL = false, class RNG>
+template <class R, bool TRACE, bool G, bool POL = false, bool JT = false, class RNG>
 __device__ __forceinline__ bool step(const KParams<R>& P, RNG& rng, const DevModel<R>& M, Pkt<R>& s, Acc& acc) {
   if (s.pend) {
     const bool release = s.pend == 2;
     s.pend = 0;
-    return interact<R, TRACE, G, POL>(P, rng, M, s, acc, release);
+    return interact<R, TRACE, G, POL, JT>(P, rng, M, s, acc, release);
   }
-  const int r = advance<R, TRACE, G, POL>(P, rng, M, s, acc);
-  if (r == 2) return interact<R, TRACE, G, POL>(P, rng, M, s, acc);
+  const int r = advance<R, TRACE, G, POL, JT>(P, rng, M, s, acc);
+  if (r == 2) return interact<R, TRACE, G, POL, JT>(P, rng, M, s, acc);
   return r == 1;
 }
 
@@ -1067,7 +1095,7 @@ __device__ __forceinline__ int interactions_at_once(const KParams<R>& P, WarpRng
 // its speed alone. The transport kernel therefore stores them (state unchanged, so the random stream
 // and the result are the same) and this kernel runs them one per warp: lane 0 of each 32-thread block
 // takes packets from the pool, those that had taken at least kTailLongSteps steps first.
-template <class R, bool TRACE, bool G, bool BATCH, bool POL = false>
+template <class R, bool TRACE, bool G, bool BATCH, bool POL = false, bool JT = false>
 __global__ void __launch_bounds__(32) transport_tail_kernel(const KParams<R> P) {
   const unsigned lane = threadIdx.x & 31u;
   if (TRACE && lane != 0) return;  // the debug trace runs one lane per packet
@@ -1082,7 +1110,7 @@ __global__ void __launch_bounds__(32) transport_tail_kernel(const KParams<R> P) 
     const DevModel<R>& M = BATCH ? P.models[s.model] : P.m0;  // batches: the packet's model index
     if (TRACE) {
       SerialRng rng{{(uint32_t)P.seed, (uint32_t)(P.seed >> 32)}};
-      while (step<R, TRACE, G, POL>(P, rng, M, s, acc)) {
+      while (step<R, TRACE, G, POL, JT>(P, rng, M, s, acc)) {
       }
     } else {
       // all 32 lanes carry the packet: the same arithmetic in every lane, the random blocks computed
@@ -1091,14 +1119,14 @@ __global__ void __launch_bounds__(32) transport_tail_kernel(const KParams<R> P) 
       bool ended = false, misses = false;
       for (;;) {
         // (FP32 only: the FP64 debug path keeps the oracle's order of floating-point operations)
-        if (!POL && (G || M.gray) && sizeof(R) == 4 && !misses && !s.pend && s.ir >= 0 && s.alpha > (R)0 && M.g0 == (R)0 &&
+        if (!POL && !JT && (G || M.gray) && sizeof(R) == 4 && !misses && !s.pend && s.ir >= 0 && s.alpha > (R)0 && M.g0 == (R)0 &&
             s.events + 33u < P.max_events && s.steps + 33u < P.max_steps) {
           const int n = interactions_at_once<R, G>(P, rng, M, s, acc, ended, misses);
           if (ended) break;
           if (n > 0) continue;
         }
         misses = false;
-        if (!step<R, TRACE, G, POL>(P, rng, M, s, acc)) break;
+        if (!step<R, TRACE, G, POL, JT>(P, rng, M, s, acc)) break;
       }
     }
     if (lane == 0) {
@@ -1117,7 +1145,7 @@ template <class R>
 constexpr int transport_min_blocks() { return sizeof(R) == 4 ? MCRT_TRANSPORT_MIN_BLOCKS : 1; }
 
 // G: gray dust known at compile time (single-disk gray runs); otherwise M.gray is read at run time.
-template <class R, bool TRACE, bool BATCH, bool G, bool POL = false>
+template <class R, bool TRACE, bool BATCH, bool G, bool POL = false, bool JT = false>
 __global__ void __launch_bounds__(256, transport_min_blocks<R>()) transport_kernel(const KParams<R> P) {
   Pkt<R> s;
   Acc acc = Acc{};
@@ -1149,7 +1177,7 @@ __global__ void __launch_bounds__(256, transport_min_blocks<R>()) transport_kern
             const DevModel<R>& M = BATCH ? P.models[m] : P.m0;
             const unsigned long long local = q - M.q_begin;
             const int tslot = (TRACE && local < (unsigned long long)P.trace_n) ? (int)local : -1;
-            launch_packet<R, TRACE, G, POL>(P, rng, M, s, M.first_id + local, tslot, acc);
+            launch_packet<R, TRACE, G, POL, JT>(P, rng, M, s, M.first_id + local, tslot, acc);
             active = true;
           } else {
             done = true;
@@ -1171,7 +1199,7 @@ __global__ void __launch_bounds__(256, transport_min_blocks<R>()) transport_kern
         }
         const DevModel<R>& M = BATCH ? P.models[model] : P.m0;
         while (active) {
-          active = step<R, TRACE, G, POL>(P, rng, M, s, acc);
+          active = step<R, TRACE, G, POL, JT>(P, rng, M, s, acc);
           if (!active) note_end(s, acc);
         }
         break;
@@ -1182,7 +1210,7 @@ __global__ void __launch_bounds__(256, transport_min_blocks<R>()) transport_kern
     // keep crossing cells; a packet's own sequence of events and random draws is unchanged.
     const DevModel<R>& M = BATCH ? P.models[model] : P.m0;
     if (active && !s.pend) {
-      const int r = advance<R, TRACE, G, POL>(P, rng, M, s, acc);
+      const int r = advance<R, TRACE, G, POL, JT>(P, rng, M, s, acc);
       if (r == 0) {
         active = false;
         note_end(s, acc);
@@ -1197,7 +1225,7 @@ __global__ void __launch_bounds__(256, transport_min_blocks<R>()) transport_kern
         if (active && s.pend) {
           const bool release = s.pend == 2;
           s.pend = 0;
-          if (!interact<R, TRACE, G, POL>(P, rng, M, s, acc, release)) {
+          if (!interact<R, TRACE, G, POL, JT>(P, rng, M, s, acc, release)) {
             active = false;
             note_end(s, acc);
           }

@@ -35,29 +35,4 @@ int transport_blocks_per_sm<float>(bool trace, bool batch, bool gray, int block)
   return n;
 }
 
-// polarized transport (Mueller matrix, Sect. 2.3): single disk, no event trace
-template <>
-cudaError_t launch_transport_pol<float>(const KParams<float>& P, bool gray, int grid, int block, cudaStream_t st) {
-  if (gray) transport_kernel<float, false, false, true, true><<<grid, block, 0, st>>>(P);
-  else transport_kernel<float, false, false, false, true><<<grid, block, 0, st>>>(P);
-  return cudaGetLastError();
-}
-
-template <>
-cudaError_t launch_transport_tail_pol<float>(const KParams<float>& P, bool gray, int sms, int warps_per_sm,
-                                          cudaStream_t st) {
-  const int grid = sms * (warps_per_sm > 0 ? warps_per_sm : 20);
-  if (gray) transport_tail_kernel<float, false, true, false, true><<<grid, 32, 0, st>>>(P);
-  else transport_tail_kernel<float, false, false, false, true><<<grid, 32, 0, st>>>(P);
-  return cudaGetLastError();
-}
-
-template <>
-int transport_blocks_per_sm_pol<float>(bool gray, int block) {
-  int n = 0;
-  if (gray) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, transport_kernel<float, false, false, true, true>, block, 0);
-  else cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, transport_kernel<float, false, false, false, true>, block, 0);
-  return n;
-}
-
 }  // namespace mcrt

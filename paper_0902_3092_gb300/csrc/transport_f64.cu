@@ -47,29 +47,4 @@ int transport_blocks_per_sm<double>(bool trace, bool batch, bool gray, int block
   return n;
 }
 
-// polarized transport (Mueller matrix, Sect. 2.3): single disk, no event trace
-template <>
-cudaError_t launch_transport_pol<double>(const KParams<double>& P, bool gray, int grid, int block, cudaStream_t st) {
-  if (gray) transport_kernel<double, false, false, true, true><<<grid, block, 0, st>>>(P);
-  else transport_kernel<double, false, false, false, true><<<grid, block, 0, st>>>(P);
-  return cudaGetLastError();
-}
-
-template <>
-cudaError_t launch_transport_tail_pol<double>(const KParams<double>& P, bool gray, int sms, int warps_per_sm,
-                                          cudaStream_t st) {
-  const int grid = sms * (warps_per_sm > 0 ? warps_per_sm : 20);
-  if (gray) transport_tail_kernel<double, false, true, false, true><<<grid, 32, 0, st>>>(P);
-  else transport_tail_kernel<double, false, false, false, true><<<grid, 32, 0, st>>>(P);
-  return cudaGetLastError();
-}
-
-template <>
-int transport_blocks_per_sm_pol<double>(bool gray, int block) {
-  int n = 0;
-  if (gray) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, transport_kernel<double, false, false, true, true>, block, 0);
-  else cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, transport_kernel<double, false, false, false, true>, block, 0);
-  return n;
-}
-
 }  // namespace mcrt

@@ -17,6 +17,7 @@ LIB_PATH = os.path.join(HERE, "libmcrt.so")
 EUNIT = 65536
 NINC = 10
 T_MC, T_PDA = 0, 1
+WITH_SCATTERING = 4
 STATUS = {0: "OK", 1: "EINVAL", 2: "ENOMEM", 3: "ECUDA", 4: "ENOTCONV", 5: "ETIMEOUT", 6: "EOVERFLOW", 7: "ESTATE"}
 EXPORTS = ["mcrt_disk_create", "mcrt_set_opacity", "mcrt_default_run_opts", "mcrt_run_photons", "mcrt_run_batch",
            "mcrt_reset", "mcrt_temperatures", "mcrt_temperatures_dev", "mcrt_get_tallies", "mcrt_sed",
@@ -25,7 +26,8 @@ EXPORTS = ["mcrt_disk_create", "mcrt_set_opacity", "mcrt_default_run_opts", "mcr
            "mcrt_pda_solve_static", "mcrt_disk_info", "mcrt_launch_count", "mcrt_last_error",
            "mcrt_disk_destroy", "mcrt_batch_create", "mcrt_batch_run", "mcrt_batch_config", "mcrt_batch_destroy",
            "mcrt_default_hydro_opts", "mcrt_hydrostatic_density", "mcrt_set_density", "mcrt_set_rays",
-           "mcrt_raytrace", "mcrt_visibilities", "mcrt_set_sources", "mcrt_set_mueller", "mcrt_sed_stokes"]
+           "mcrt_raytrace", "mcrt_visibilities", "mcrt_set_sources", "mcrt_set_mueller", "mcrt_sed_stokes",
+           "mcrt_keep_mean_intensity", "mcrt_mean_intensity"]
 
 
 class McrtError(RuntimeError):
@@ -124,6 +126,8 @@ def lib():
         "mcrt_set_sources": (st, [P, pd]),
         "mcrt_set_mueller": (st, [P, C.c_int, pd]),
         "mcrt_sed_stokes": (st, [P, C.c_int, pd, pd, pd]),
+        "mcrt_keep_mean_intensity": (st, [P, C.c_int]),
+        "mcrt_mean_intensity": (st, [P, pd]),
         "mcrt_raytrace": (st, [P, C.c_int, C.c_int, pd, pd, pd, pu]),
         "mcrt_visibilities": (st, [P, C.c_int, pi, pd, pd, C.c_int, pd]),
     }
@@ -286,6 +290,18 @@ class Disk:
         sh = (self.nlam, n_incl)
         return I.reshape(sh), Q.reshape(sh), U.reshape(sh)
 
+    def keep_mean_intensity(self, keep=True):
+        """Path-length estimator of the mean intensity in the following runs (flights in their bin, MRW
+        walks spread with the weights of Eq. 10); resets the tallies."""
+        _check(lib().mcrt_keep_mean_intensity(self._h, int(bool(keep))), self._h)
+
+    def mean_intensity(self):
+        """Mean intensity per cell and bin, (nr, ntheta, nlam), erg s^-1 cm^-2 sr^-1 integrated over the
+        bin."""
+        J = np.zeros(self.nr * self.ntheta * self.nlam)
+        _check(lib().mcrt_mean_intensity(self._h, _dp(J)), self._h)
+        return J.reshape(self.nr, self.ntheta, self.nlam)
+
     def set_density(self, rho):
         """Replaces the density (g/cm^3) and resets the tallies."""
         r = np.ascontiguousarray(rho, np.float64).ravel()
@@ -357,16 +373,17 @@ class Disk:
         p, q, w = self._rays
         _check(lib().mcrt_set_rays(self._h, float(incl), float(dist_cm), len(p), _dp(p), _dp(q), _dp(w)), self._h)
 
-    def raytrace(self, which=T_MC, precision=32, want_image=False):
+    def raytrace(self, which=T_MC, precision=32, want_image=False, scattering=False):
         """Ray-traced SED of the current rays: dict with F (disk + star, erg/s/cm^2 per wavelength bin),
         F_star, segments (ray segments through dust) and, with want_image, I (rays x bins intensities,
-        erg/s/cm^2/sr per bin)."""
+        erg/s/cm^2/sr per bin). scattering: add the scattered light of the mean-intensity tally."""
         F, Fs = np.zeros(self.nlam), np.zeros(self.nlam)
         rays = getattr(self, "_rays", None)
         n = len(rays[0]) if rays is not None else 0
         I = np.zeros(n * self.nlam) if want_image else None
         seg = np.zeros(1, np.uint64)
-        _check(lib().mcrt_raytrace(self._h, int(which), int(precision), _dp(F), _dp(Fs),
+        w = int(which) | (WITH_SCATTERING if scattering else 0)
+        _check(lib().mcrt_raytrace(self._h, w, int(precision), _dp(F), _dp(Fs),
                                    None if I is None else _dp(I), _up(seg)), self._h)
         out = {"F": F, "F_star": Fs, "segments": int(seg[0])}
         if I is not None:

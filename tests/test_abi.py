@@ -75,6 +75,8 @@ def test_defaults_and_host_validation(L):
     assert L.mcrt_set_sources(None, None) == 1
     assert L.mcrt_set_mueller(None, 181, None) == 1
     assert L.mcrt_sed_stokes(None, 10, None, None, None) == 1
+    assert L.mcrt_keep_mean_intensity(None, 1) == 1
+    assert L.mcrt_mean_intensity(None, None) == 1
     L.mcrt_disk_destroy(None)
 
 
