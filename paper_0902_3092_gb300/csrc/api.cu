@@ -12,6 +12,7 @@
 
 #include "internal.h"
 #include "planck.cuh"
+#include "tables.h"
 
 using mcrt::DBuf;
 
@@ -589,37 +590,9 @@ mcrt_status mcrt_set_opacity(mcrt_disk* d, int nlam, const double* lam_e, const 
     acc += B[b];
     star[b] = acc;
   }
-  // temperature grid: T_0 = 0, T_k = Tmin (Tmax/Tmin)^((k-1)/(nT-2))
   const int nT = d->nT;
-  const double dlnT = std::log(d->Tmax / d->Tmin) / (nT - 2);
-  std::vector<float> lQk(nT), cbw((size_t)nT * nlam, 0.f), cexit((size_t)nT * nlam), chiRk(nT), kbark(nT);
-  std::vector<float> jw((size_t)nT * nlam, 0.f);  // Eq. 10 weights of the J tally: dBbar_b/dT normalised
-  std::vector<double> lQ64(nT, -INFINITY), slQ64(nT, 4.0);  // FP64 log Q and d log Q / d log T (guess of T)
-  lQk[0] = -INFINITY;
-  for (int k = 0; k < nT; ++k) {
-    const double T = (k == 0) ? d->Tmin : d->Tmin * std::exp((k - 1) * dlnT);
-    planck_bins(d->lam_e.data(), nlam, T, B.data(), dB.data());
-    double q = 0, c1 = 0, c2 = 0, sdb = 0, sdbc = 0, skdb = 0;
-    for (int b = 0; b < nlam; ++b) {
-      q += d->kabs[b] * B[b];
-      c1 += d->kabs[b] * B[b];
-      c2 += dB[b] / chip[b];
-      sdb += dB[b];
-      sdbc += dB[b] / chip[b];
-      skdb += d->kabs[b] * dB[b];
-      if (k > 0) cbw[(size_t)k * nlam + b] = (float)c1;
-      cexit[(size_t)k * nlam + b] = (float)c2;
-    }
-    if (k > 0) {
-      lQk[k] = (float)std::log(4.0 * kPi * q);
-      lQ64[k] = std::log(4.0 * kPi * q);
-      slQ64[k] = q > 0 ? T * skdb / q : 4.0;
-    }
-    chiRk[k] = (float)(sdb / sdbc);
-    kbark[k] = (float)(skdb / sdb);
-    if (sdb > 0)
-      for (int b = 0; b < nlam; ++b) jw[(size_t)k * nlam + b] = (float)(dB[b] / sdb);
-  }
+  TGridTables tt;
+  build_T_tables(nlam, d->lam_e.data(), d->kabs.data(), chip.data(), nT, d->Tmin, d->Tmax, tt);
   cudaError_t e;
 #define UP(buf, vec)                                   \
   do {                                                 \
@@ -634,14 +607,14 @@ mcrt_status mcrt_set_opacity(mcrt_disk* d, int nlam, const double* lam_e, const 
   UP(d->alb64, alb);
   UP(d->g64, d->g);
   UP(d->star64, star);
-  UP(d->lQk, lQk);
-  UP(d->lQ64, lQ64);
-  UP(d->slQ64, slQ64);
-  UP(d->cbw, cbw);
-  UP(d->cexit, cexit);
-  UP(d->chiRk, chiRk);
-  UP(d->kbark, kbark);
-  UP(d->jw, jw);
+  UP(d->lQk, tt.lQk);
+  UP(d->lQ64, tt.lQ64);
+  UP(d->slQ64, tt.slQ64);
+  UP(d->cbw, tt.cbw);
+  UP(d->cexit, tt.cexit);
+  UP(d->chiRk, tt.chiRk);
+  UP(d->kbark, tt.kbark);
+  UP(d->jw, tt.jw);
   UP(d->lam_e_d, d->lam_e);
   UP(d->kabs_d, d->kabs);
   UP(d->chip_d, chip);

@@ -1,0 +1,78 @@
+"""The library's dust tables on its temperature grid (tables.h, host code run when the opacities are
+set; the transport and temperature kernels read them), compiled for the host and compared with the
+oracle's exact quantities at grid temperatures from 1 K to 1e4 K: Q(T) = 4 pi sum_b kappa_b Bbar_b(T) and
+its logarithmic slope; the cumulative re-emission spectrum kappa_b Bbar_b(T) (Bjorkman & Wood, Sect. 2.1)
+and MRW exit spectrum dBbar_b/dT / chi'_b; chi_R = 1 / (3 rho D) with D of Eq. 12-15 and kappa_bar of
+Eq. 10, both at the oracle's iterated fixed point of Eq. 13; the J weights eta_b / chi'_b normalised.
+FP32 entries to 1e-6 relative (their rounding; the cumulative spectra to 1e-6 of their total, which
+is what sampling from them sees), FP64 ones to 1e-12."""
+import ctypes as C
+import math
+import os
+import shutil
+import subprocess
+
+import numpy as np
+import pytest
+
+from paper_0902_3092_gb300 import disks
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+NT, TMIN, TMAX = 1024, 1.0, 1.0e4
+
+
+@pytest.fixture(scope="module")
+def shim(tmp_path_factory):
+    nvcc = shutil.which("nvcc") or "/usr/local/cuda/bin/nvcc"
+    if not os.path.exists(nvcc):
+        pytest.skip("nvcc not found")
+    out = tmp_path_factory.mktemp("tables") / "libtables.so"
+    subprocess.check_call([nvcc, "-O2", "-std=c++17", "-Xcompiler", "-fPIC", "-shared",
+                           "-I", os.path.join(ROOT, "include"), "-I", os.path.join(ROOT, "paper_0902_3092_gb300", "csrc"),
+                           os.path.join(ROOT, "tests", "hostshim", "tables_shim.cu"), "-o", str(out)])
+    return C.CDLL(str(out))
+
+
+def tables(shim, op):
+    nlam = op.nlam
+    chip = np.ascontiguousarray(op.kappa_abs + (1 - op.g) * op.kappa_sca)
+    f = lambda n: np.zeros(n, np.float32)
+    out = dict(lQk=f(NT), cbw=f(NT * nlam), cexit=f(NT * nlam), chiR=f(NT), kbar=f(NT), jw=f(NT * nlam),
+               lQ64=np.zeros(NT), slQ64=np.zeros(NT))
+    P = lambda a: np.ascontiguousarray(a).ctypes.data_as(C.c_void_p)
+    shim.tables_host(C.c_int(nlam), P(op.lam_edges_um), P(op.kappa_abs), P(chip), C.c_int(NT), C.c_double(TMIN),
+                     C.c_double(TMAX), *(P(out[k]) for k in ("lQk", "cbw", "cexit", "chiR", "kbar", "jw", "lQ64", "slQ64")))
+    for k in ("cbw", "cexit", "jw"):
+        out[k] = out[k].reshape(NT, nlam)
+    return out, chip
+
+
+@pytest.mark.parametrize("kind", ["nongray", "gray_hg"])
+def test_tables_match_oracle(shim, oracle, kind):
+    if kind == "nongray":
+        d = disks.config_nongray(8, 8, 100.0)
+    else:
+        d = disks.config_plain_gray(8, 8, 100.0)
+        d.opacity = disks.gray_opacity(nlam=60, albedo=0.6, g=0.5)
+    op = d.opacity
+    t, chip = tables(shim, op)
+    dln = math.log(TMAX / TMIN) / (NT - 2)
+    for k in list(range(1, NT, 37)) + [NT - 1]:
+        T = TMIN * math.exp((k - 1) * dln)
+        B, dB = oracle.planck_bins(op.lam_edges_um, T), oracle.dplanck_bins(op.lam_edges_um, T)
+        q = 4 * math.pi * (op.kappa_abs * B).sum()
+        assert abs(t["lQ64"][k] - math.log(q)) < 1e-12 * abs(math.log(q)) + 1e-13
+        assert abs(t["lQk"][k] - math.log(q)) < 2e-6 * abs(math.log(q)) + 1e-6
+        h = 1e-4
+        slope = (math.log((op.kappa_abs * oracle.planck_bins(op.lam_edges_um, T * math.exp(h))).sum())
+                 - math.log((op.kappa_abs * oracle.planck_bins(op.lam_edges_um, T * math.exp(-h))).sum())) / (2 * h)
+        assert abs(t["slQ64"][k] / slope - 1) < 1e-6
+        for tab, ref in (("cbw", np.cumsum(op.kappa_abs * B)), ("cexit", np.cumsum(dB / chip))):
+            assert np.all(np.abs(t[tab][k] - ref) <= 1e-6 * ref[-1]), (tab, k)  # of the CDF's total
+        D, kb = oracle.diffusion(d, T, 1.0)
+        assert abs(t["chiR"][k] * 3 * D - 1) < 1e-6 and abs(t["kbar"][k] / kb - 1) < 1e-6, k
+        w = oracle.eta_iterate(d, T) / chip
+        w /= w.sum()
+        assert np.max(np.abs(t["jw"][k] - w)) < 1e-7, k
+        assert abs(float(t["jw"][k].astype(np.float64).sum()) - 1) < 1e-5
+    assert np.isneginf(t["lQk"][0]) and not t["cbw"][0].any()
