@@ -35,46 +35,10 @@ mcrt_status cuda_fail(mcrt_disk* d, cudaError_t e, const char* what) {
 }
 
 // ------------------------------------------------------------------------------------------------
-// MRW inverse escape-time tables (Eq. 7-8), built once per process on the host, uploaded per device.
-// P(x) = 2 sum (-1)^{n+1} exp(-n^2 pi^2 x) for x >= 0.1; for smaller x its Jacobi-theta transform
-// 1 - P = (2/sqrt(pi x)) sum_{n>=0} exp(-(n+1/2)^2/x) converges in a few terms.
+// MRW inverse escape-time tables (Eq. 7-8; built by tables.h), once per process, uploaded per device.
 // ------------------------------------------------------------------------------------------------
-static double survival(double x) {
-  if (x <= 0) return 1.0;
-  if (x >= 0.1) {
-    double s = 0.0;
-    for (int n = 1; n < 64; ++n) {
-      const double t = std::exp(-(double)n * n * kPi * kPi * x);
-      s += (n & 1) ? t : -t;
-      if (t < 1e-20) break;
-    }
-    return 2.0 * s;
-  }
-  double s = 0.0;
-  for (int n = 0; n < 16; ++n) {
-    const double a = n + 0.5;
-    const double t = std::exp(-a * a / x);
-    s += t;
-    if (t < 1e-20 * s) break;
-  }
-  return 1.0 - 2.0 / std::sqrt(kPi * x) * s;
-}
-
-static double survival_inverse(double P0, bool complement, double Q0) {
-  // complement: solve 1 - P(x) = Q0 (accurate when P0 is close to 1)
-  double lo = 1e-5, hi = 64.0;
-  for (int it = 0; it < 200; ++it) {
-    const double mid = std::sqrt(lo * hi);
-    const double v = survival(mid);
-    const bool above = complement ? (1.0 - v < Q0) : (v > P0);  // still inside: move right
-    if (above) lo = mid; else hi = mid;
-    if (hi / lo - 1.0 < 1e-15) break;
-  }
-  return std::sqrt(lo * hi);
-}
-
-const float kMrwT0 = (float)(-24.0 * 0.69314718055994530942);  // ln 2^-24
-const float kMrwDT = (float)((-0.69314718055994530942 + 24.0 * 0.69314718055994530942) / (kMrwTab - 1));
+const float kMrwT0 = mrw_table_t0();
+const float kMrwDT = mrw_table_dt();
 
 const float* mrw_table(int device, cudaError_t* err) {
   static std::mutex mu;
@@ -86,12 +50,7 @@ const float* mrw_table(int device, cudaError_t* err) {
     if (pr.first == device) return pr.second;
   if (host.empty()) {
     host.resize(2 * kMrwTab);
-    for (int i = 0; i < kMrwTab; ++i) {
-      const double t = (double)kMrwT0 + (double)i * (double)kMrwDT;
-      const double u = std::exp(t);
-      host[i] = (float)survival_inverse(u, false, 0.0);                     // P(x) = u, u <= 1/2
-      host[kMrwTab + i] = (float)(1.0 / survival_inverse(1.0 - u, true, u));  // P(x) = 1-u
-    }
+    build_mrw_table(host.data());
   }
   float* p = nullptr;
   cudaError_t e = cudaMalloc(&p, sizeof(float) * host.size());

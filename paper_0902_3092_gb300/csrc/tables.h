@@ -1,5 +1,6 @@
-// tables.h -- the dust tables on the temperature grid that the transport and temperature kernels read
-// (built on the host when the opacities are set; host code, compiled for the host in the tests too).
+// tables.h -- the tables the transport and temperature kernels read: the dust tables on the temperature
+// grid (built when the opacities are set) and the inverse MRW escape-time table (built once per
+// process). Host code, compiled for the host in the tests too.
 #pragma once
 #include <cmath>
 #include <vector>
@@ -60,6 +61,62 @@ inline void build_T_tables(int nlam, const double* lam_e, const double* kabs, co
     t.kbark[k] = (float)(skdb / sdb);
     if (sdb > 0)
       for (int b = 0; b < nlam; ++b) t.jw[(size_t)k * nlam + b] = (float)(dB[b] / sdb);
+  }
+}
+
+// MRW escape-time law (Eq. 7-8): P(x) = 2 sum (-1)^{n+1} exp(-n^2 pi^2 x), the probability that a walker
+// started at the centre of a sphere is still inside at x = D c t / R0^2. For x < 0.1 the series is
+// slow; there its Jacobi-theta transform 1 - P = (2 / sqrt(pi x)) sum_{n>=0} exp(-(n + 1/2)^2 / x)
+// converges in a few terms.
+inline double mrw_survival(double x) {
+  if (x <= 0) return 1.0;
+  if (x >= 0.1) {
+    double s = 0.0;
+    for (int n = 1; n < 64; ++n) {
+      const double t = std::exp(-(double)n * n * kPi * kPi * x);
+      s += (n & 1) ? t : -t;
+      if (t < 1e-20) break;
+    }
+    return 2.0 * s;
+  }
+  double s = 0.0;
+  for (int n = 0; n < 16; ++n) {
+    const double a = n + 0.5;
+    const double t = std::exp(-a * a / x);
+    s += t;
+    if (t < 1e-20 * s) break;
+  }
+  return 1.0 - 2.0 / std::sqrt(kPi * x) * s;
+}
+
+// x with P(x) = P0 by bisection in log x; complement: solve 1 - P(x) = Q0 instead (accurate when P0
+// is close to 1)
+inline double mrw_survival_inverse(double P0, bool complement, double Q0) {
+  double lo = 1e-5, hi = 64.0;
+  for (int it = 0; it < 200; ++it) {
+    const double mid = std::sqrt(lo * hi);
+    const double v = mrw_survival(mid);
+    const bool above = complement ? (1.0 - v < Q0) : (v > P0);  // still inside: move right
+    if (above) lo = mid; else hi = mid;
+    if (hi / lo - 1.0 < 1e-15) break;
+  }
+  return std::sqrt(lo * hi);
+}
+
+// The inverse tables read by the transport kernels: node i at u = exp(t0 + i dt), u from 2^-24 to 1/2;
+// tab[i] = x with P(x) = u, tab[kMrwTab + i] = 1 / x with P(x) = 1 - u (the kernel interpolates linearly
+// in log u and takes the second table for u > 1/2).
+inline float mrw_table_t0() { return (float)(-24.0 * 0.69314718055994530942); }  // ln 2^-24
+inline float mrw_table_dt() {
+  return (float)((-0.69314718055994530942 + 24.0 * 0.69314718055994530942) / (kMrwTab - 1));
+}
+inline void build_mrw_table(float* tab) {
+  const float t0 = mrw_table_t0(), dt = mrw_table_dt();
+  for (int i = 0; i < kMrwTab; ++i) {
+    const double t = (double)t0 + (double)i * (double)dt;
+    const double u = std::exp(t);
+    tab[i] = (float)mrw_survival_inverse(u, false, 0.0);                     // P(x) = u, u <= 1/2
+    tab[kMrwTab + i] = (float)(1.0 / mrw_survival_inverse(1.0 - u, true, u));  // P(x) = 1-u
   }
 }
 

@@ -18,3 +18,10 @@ extern "C" void tables_host(int nlam, const double* lam_e, const double* kabs, c
   std::memcpy(lQ64, t.lQ64.data(), nT * sizeof(double));
   std::memcpy(slQ64, t.slQ64.data(), nT * sizeof(double));
 }
+
+extern "C" int mrw_table_host(float* tab, float* t0, float* dt) {
+  mcrt::build_mrw_table(tab);
+  *t0 = mcrt::mrw_table_t0();
+  *dt = mcrt::mrw_table_dt();
+  return mcrt::kMrwTab;
+}

@@ -1,6 +1,6 @@
-"""The library's dust tables on its temperature grid (tables.h, host code run when the opacities are
-set; the transport and temperature kernels read them), compiled for the host and compared with the
-oracle's exact quantities at grid temperatures from 1 K to 1e4 K: Q(T) = 4 pi sum_b kappa_b Bbar_b(T) and
+"""The tables the library's kernels read (tables.h, host code), compiled for the host and compared with
+the oracle: the MRW escape-time inverse, and the dust tables on the temperature grid (built when the
+opacities are set), against the oracle's exact quantities at grid temperatures from 1 K to 1e4 K: Q(T) = 4 pi sum_b kappa_b Bbar_b(T) and
 its logarithmic slope; the cumulative re-emission spectrum kappa_b Bbar_b(T) (Bjorkman & Wood, Sect. 2.1)
 and MRW exit spectrum dBbar_b/dT / chi'_b; chi_R = 1 / (3 rho D) with D of Eq. 12-15 and kappa_bar of
 Eq. 10, both at the oracle's iterated fixed point of Eq. 13; the J weights eta_b / chi'_b normalised.
@@ -76,3 +76,24 @@ def test_tables_match_oracle(shim, oracle, kind):
         assert np.max(np.abs(t["jw"][k] - w)) < 1e-7, k
         assert abs(float(t["jw"][k].astype(np.float64).sum()) - 1) < 1e-5
     assert np.isneginf(t["lQk"][0]) and not t["cbw"][0].any()
+
+
+def test_mrw_escape_time_table_matches_oracle(shim, oracle):
+    """The inverse of the MRW escape-time law P(x) (Eq. 7-8) that the kernels interpolate: nodes
+    u = 2^-24 .. 1/2 evenly in log u, x with P(x) = u and 1/x with P(x) = 1 - u, against the oracle's
+    bisection of the series: the nodes to their FP32 rounding (1e-7), and halfway between nodes the
+    kernels' linear interpolation in log u within 3e-6 of the exact inverse."""
+    n = 2048
+    tab = np.zeros(2 * n, np.float32)
+    t0, dt = C.c_float(), C.c_float()
+    assert shim.mrw_table_host(tab.ctypes.data_as(C.c_void_p), C.byref(t0), C.byref(dt)) == n
+    t0, dt = np.float64(t0.value), np.float64(dt.value)
+    assert abs(t0 - math.log(2.0 ** -24)) < 1e-6 and abs(t0 + (n - 1) * dt - math.log(0.5)) < 1e-4
+    lo, hi = tab[:n].astype(np.float64), tab[n:].astype(np.float64)
+    for frac, tol in ((0.0, 1e-7), (0.5, 3e-6)):
+        i = np.arange(0, n - 1, 7)
+        u = np.exp(t0 + (i + frac) * dt)
+        xl = (1 - frac) * lo[i] + frac * lo[i + 1]
+        xh = 1.0 / ((1 - frac) * hi[i] + frac * hi[i + 1])
+        assert np.max(np.abs(xl / [oracle.mrw_x(x) for x in u] - 1)) < tol, frac
+        assert np.max(np.abs(xh / [oracle.mrw_x(1 - x) for x in u] - 1)) < tol, frac
