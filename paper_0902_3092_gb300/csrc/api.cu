@@ -1043,21 +1043,13 @@ mcrt_status mcrt_set_mueller(mcrt_disk* d, int nmu, const double* table) {
   if (nmu < 2 || nmu > 4097) return set_error(d, MCRT_EINVAL, "nmu: 2 .. 4097 scattering angles");
   const size_t nl = (size_t)d->nlam, m = (size_t)nmu;
   std::vector<double> cdf(nl * m);
-  const double h = kPi / (nmu - 1);
   for (size_t b = 0; b < nl; ++b) {
     const double* t = table + b * 4 * m;
     for (size_t k = 0; k < 4 * m; ++k)
       if (!std::isfinite(t[k])) return set_error(d, MCRT_EINVAL, "Mueller matrix: finite values");
     for (size_t k = 0; k < m; ++k)
       if (t[k] < 0) return set_error(d, MCRT_EINVAL, "Mueller matrix: S11 >= 0");
-    // cumulative S11 sin(theta) by the trapezoid rule, normalised to 1
-    double* c = cdf.data() + b * m;
-    c[0] = 0.0;
-    for (size_t k = 1; k < m; ++k)
-      c[k] = c[k - 1] + 0.5 * h * (t[k - 1] * std::sin((double)(k - 1) * h) + t[k] * std::sin((double)k * h));
-    if (!(c[m - 1] > 0)) return set_error(d, MCRT_EINVAL, "Mueller matrix: S11 vanishes");
-    const double tot = c[m - 1];
-    for (size_t k = 0; k < m; ++k) c[k] /= tot;
+    if (!mueller_cdf(t, nmu, cdf.data() + b * m)) return set_error(d, MCRT_EINVAL, "Mueller matrix: S11 vanishes");
   }
   std::vector<double> tab(table, table + nl * 4 * m);
   cudaError_t e = upload(d->mtab64, tab);

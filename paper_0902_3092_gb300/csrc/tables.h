@@ -120,4 +120,18 @@ inline void build_mrw_table(float* tab) {
   }
 }
 
+// Sampling table of the scattering angle of a Mueller matrix (Sect. 2.3): the cumulative S11 sin(theta)
+// on theta_k = k pi / (nmu - 1) by the trapezoid rule, normalised to 1 (the kernels interpolate S11
+// linearly, so theta follows from a quadratic within an interval). False when S11 sin(theta) vanishes.
+inline bool mueller_cdf(const double* S11, int nmu, double* c) {
+  const double h = kPi / (nmu - 1);
+  c[0] = 0.0;
+  for (int k = 1; k < nmu; ++k)
+    c[k] = c[k - 1] + 0.5 * h * (S11[k - 1] * std::sin((double)(k - 1) * h) + S11[k] * std::sin((double)k * h));
+  if (!(c[nmu - 1] > 0)) return false;
+  const double tot = c[nmu - 1];
+  for (int k = 0; k < nmu; ++k) c[k] /= tot;
+  return true;
+}
+
 }  // namespace mcrt

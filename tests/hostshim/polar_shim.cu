@@ -1,16 +1,19 @@
-// Host build of the polarization functions of the CUDA library (transport.cuh), for a CPU test
-// against the oracle: one scattering and the sky-frame Stokes of a packet, in FP32 and FP64.
+// Host build of the polarization functions of the CUDA library (transport.cuh) and of its sampling
+// table of the scattering angle (tables.h, as mcrt_set_mueller builds it), for a CPU test against the
+// oracle: one scattering and the sky-frame Stokes of a packet, in FP32 and FP64.
 #include <cmath>
 #include <cstring>
 #include <vector>
 
+#include "tables.h"
 #include "transport.cuh"
 
 using namespace mcrt;
 
 template <class R>
-static void scatter(int nmu, const double* table, const double* cdf, double* u, double* e, double* st, double w1,
-                    double w2) {
+static void scatter(int nmu, const double* table, double* u, double* e, double* st, double w1, double w2) {
+  std::vector<double> cdf((size_t)nmu);
+  mueller_cdf(table, nmu, cdf.data());
   std::vector<R> t(4 * (size_t)nmu), c((size_t)nmu);
   for (size_t k = 0; k < t.size(); ++k) t[k] = (R)table[k];
   for (int k = 0; k < nmu; ++k) c[k] = (R)cdf[k];
@@ -44,13 +47,11 @@ static void observer(const double* u, const double* e, const double* st, double*
   *uu = b;
 }
 
-extern "C" void pol_scatter_f(int nmu, const double* t, const double* c, double* u, double* e, double* st, double w1,
-                              double w2) {
-  scatter<float>(nmu, t, c, u, e, st, w1, w2);
+extern "C" void pol_scatter_f(int nmu, const double* t, double* u, double* e, double* st, double w1, double w2) {
+  scatter<float>(nmu, t, u, e, st, w1, w2);
 }
-extern "C" void pol_scatter_d(int nmu, const double* t, const double* c, double* u, double* e, double* st, double w1,
-                              double w2) {
-  scatter<double>(nmu, t, c, u, e, st, w1, w2);
+extern "C" void pol_scatter_d(int nmu, const double* t, double* u, double* e, double* st, double w1, double w2) {
+  scatter<double>(nmu, t, u, e, st, w1, w2);
 }
 extern "C" void pol_observer_f(const double* u, const double* e, const double* st, double* q, double* uu) {
   observer<float>(u, e, st, q, uu);

@@ -1,5 +1,6 @@
 """The polarization functions of the transport kernels (transport.cuh: pol_scatter, pol_observer; host
-and device code) compiled for the host with nvcc and compared with the oracle's on random packets, for
+and device code), with the sampling table of the scattering angle that mcrt_set_mueller builds
+(tables.h), compiled for the host with nvcc and compared with the oracle's on random packets, for
 the exact Rayleigh matrix and a polarized Henyey-Greenstein matrix: FP64 to 1e-11, FP32 to 2e-5 (float
 rounding of the geometry and of the table interpolation, ~1e-6, and the FP32 Newton tolerance of the
 plane azimuth, 1e-6, which moves the direction and the Stokes vector by a few 1e-6)."""
@@ -29,21 +30,10 @@ def shim(tmp_path_factory):
     return C.CDLL(str(out))
 
 
-def _cdf(S11):
-    """Normalised cumulative S11 sin(theta) by the trapezoid rule, as mcrt_set_mueller builds it."""
-    n = len(S11)
-    h = math.pi / (n - 1)
-    c = np.zeros(n)
-    for k in range(1, n):
-        c[k] = c[k - 1] + 0.5 * h * (S11[k - 1] * math.sin((k - 1) * h) + S11[k] * math.sin(k * h))
-    return c / c[-1]
-
-
 @pytest.mark.parametrize("which", ["rayleigh", "hg"])
 def test_kernel_polarization_functions_match_oracle(shim, oracle, which):
     tab = disks.rayleigh_mueller(1, 181)[0] if which == "rayleigh" else disks.hg_polarized_mueller([0.5], [0.6], 181)[0]
     t = np.ascontiguousarray(tab)
-    c = _cdf(t[0])
     P = lambda a: a.ctypes.data_as(C.c_void_p)
     rng = np.random.default_rng(1)
     for k in range(500):
@@ -58,7 +48,7 @@ def test_kernel_polarization_functions_match_oracle(shim, oracle, which):
         qo, uuo = oracle.pol_observer(uo, eo, so)
         for f, g, tol in ((shim.pol_scatter_d, shim.pol_observer_d, 1e-11), (shim.pol_scatter_f, shim.pol_observer_f, 2e-5)):
             uu, ee, ss = u.copy(), e.copy(), st.copy()
-            f(C.c_int(181), P(t), P(c), P(uu), P(ee), P(ss), C.c_double(w1), C.c_double(w2))
+            f(C.c_int(181), P(t), P(uu), P(ee), P(ss), C.c_double(w1), C.c_double(w2))
             assert np.abs(uu - uo).max() < tol and np.abs(ee - eo).max() < tol and np.abs(ss - so).max() < tol, (k, tol)
             q, qu = C.c_double(), C.c_double()
             g(P(uo), P(eo), P(so), C.byref(q), C.byref(qu))
