@@ -14,6 +14,24 @@ constexpr double kPi = 3.14159265358979323846;
 // error flag bits (mcrt_run_stats.error_flags)
 constexpr unsigned kErrOverflow = 1u, kErrMrwClip = 2u, kErrStepGuard = 4u;
 
+// Read-only load through the non-coherent cache on the device, a plain load on the host; the fast
+// logarithm intrinsic on the device, logf on the host. They let table lookups be compiled for the host.
+template <class T>
+__host__ __device__ __forceinline__ T ldg(const T* p) {
+#ifdef __CUDA_ARCH__
+  return __ldg(p);
+#else
+  return *p;
+#endif
+}
+__host__ __device__ __forceinline__ float fast_logf(float x) {
+#ifdef __CUDA_ARCH__
+  return __logf(x);
+#else
+  return logf(x);
+#endif
+}
+
 // event types of the debug trace
 enum EventType { EV_LAUNCH = 0, EV_CROSS = 1, EV_SCATTER = 2, EV_ABSORB = 3, EV_MRW = 4, EV_ESCAPE = 5, EV_CAPPED = 6 };
 

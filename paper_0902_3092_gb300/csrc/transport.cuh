@@ -379,14 +379,14 @@ __device__ __forceinline__ R mrw_x(const KParams<R>& P, R u) {
 // position on the temperature grid of the absorbed energy `tally` of cell c: interval k and weight
 // w, linear in log q. tally = 0 (or below the first grid temperature) gives k = 0, w = 0.
 template <class R>
-__device__ __forceinline__ void qpos(const DevModel<R>& M, unsigned long long tally, int c, int& k, float& w) {
+__host__ __device__ __forceinline__ void qpos(const DevModel<R>& M, unsigned long long tally, int c, int& k, float& w) {
   k = 0;
   w = 0.f;
   if (tally == 0ull) return;
-  const float lq = (sizeof(R) == 4 ? __logf((float)tally) : logf((float)tally)) + __ldg(M.lqm + c) + M.lq_run;
-  if (!(lq >= __ldg(M.lQk + 1))) return;
+  const float lq = (sizeof(R) == 4 ? fast_logf((float)tally) : logf((float)tally)) + ldg(M.lqm + c) + M.lq_run;
+  if (!(lq >= ldg(M.lQk + 1))) return;
   const int nT = M.nT;
-  if (lq >= __ldg(M.lQk + nT - 1)) {
+  if (lq >= ldg(M.lQk + nT - 1)) {
     k = nT - 2;
     w = 1.f;
     return;
@@ -394,10 +394,10 @@ __device__ __forceinline__ void qpos(const DevModel<R>& M, unsigned long long ta
   int lo = 1, hi = nT - 1;  // lQk[lo] <= lq < lQk[hi]
   while (hi - lo > 1) {
     const int mid = (lo + hi) >> 1;
-    if (__ldg(M.lQk + mid) <= lq) lo = mid; else hi = mid;
+    if (ldg(M.lQk + mid) <= lq) lo = mid; else hi = mid;
   }
   k = lo;
-  const float a = __ldg(M.lQk + lo), b = __ldg(M.lQk + lo + 1);
+  const float a = ldg(M.lQk + lo), b = ldg(M.lQk + lo + 1);
   w = (lq - a) / (b - a);
 }
 
@@ -408,22 +408,22 @@ __device__ __forceinline__ void qpos(const DevModel<R>& M, unsigned long long ta
 //   adjacent intervals:       D = (1 - w_old)(C[k_old+1] - C[k_old]) + w_new (C[k_new+1] - C[k_new])
 //   further apart:            D = C(T_new) - C(T_old), both interpolated
 // Below the first grid temperature (k = 0) the spectrum is the one of the first interval.
-static __device__ __noinline__ int sample_bw_rows(const float* __restrict__ C, int nl, int ko, float wo, int kn, float wn,
+static __host__ __device__ __noinline__ int sample_bw_rows(const float* __restrict__ C, int nl, int ko, float wo, int kn, float wn,
                                           float u) {
   int mode = kn <= ko ? 0 : (kn == ko + 1 ? 1 : 2);
   auto D = [&](int b) -> float {
     if (mode == 0) {
       const float* r = C + (size_t)kn * nl;
-      return __ldg(r + nl + b) - __ldg(r + b);
+      return ldg(r + nl + b) - ldg(r + b);
     }
     if (mode == 1) {
       const float* ro = C + (size_t)ko * nl;
-      const float c0 = __ldg(ro + b), c1 = __ldg(ro + nl + b), c2 = __ldg(ro + 2 * nl + b);
+      const float c0 = ldg(ro + b), c1 = ldg(ro + nl + b), c2 = ldg(ro + 2 * nl + b);
       return (1.f - wo) * (c1 - c0) + wn * (c2 - c1);
     }
     const float* ro = C + (size_t)ko * nl;
     const float* rn = C + (size_t)kn * nl;
-    return ((1.f - wn) * __ldg(rn + b) + wn * __ldg(rn + nl + b)) - ((1.f - wo) * __ldg(ro + b) + wo * __ldg(ro + nl + b));
+    return ((1.f - wn) * ldg(rn + b) + wn * ldg(rn + nl + b)) - ((1.f - wo) * ldg(ro + b) + wo * ldg(ro + nl + b));
   };
   float tot = D(nl - 1);
   if (!(tot > 0.f)) {
@@ -440,9 +440,9 @@ static __device__ __noinline__ int sample_bw_rows(const float* __restrict__ C, i
 }
 
 // MRW exit bin from the cumulative dBbar/dT / chi' row at (k, w)
-static __device__ __noinline__ int sample_exit_rows(const float* __restrict__ cexit, int nl, int k, float w, float u) {
+static __host__ __device__ __noinline__ int sample_exit_rows(const float* __restrict__ cexit, int nl, int k, float w, float u) {
   const float* X = cexit + (size_t)k * nl;
-  auto cum = [&](int b) { return (1.f - w) * __ldg(X + b) + w * __ldg(X + nl + b); };
+  auto cum = [&](int b) { return (1.f - w) * ldg(X + b) + w * ldg(X + nl + b); };
   const float target = u * cum(nl - 1);
   int lo = -1, hi = nl - 1;
   while (hi - lo > 1) {
@@ -453,17 +453,17 @@ static __device__ __noinline__ int sample_exit_rows(const float* __restrict__ ce
 }
 
 template <class R>
-__device__ __forceinline__ int sample_bw(const DevModel<R>& M, int ko, float wo, int kn, float wn, float u) {
+__host__ __device__ __forceinline__ int sample_bw(const DevModel<R>& M, int ko, float wo, int kn, float wn, float u) {
   return sample_bw_rows(M.cbw, M.nlam, ko, wo, kn, wn, u);
 }
 
 template <class R>
-__device__ __forceinline__ int sample_exit(const DevModel<R>& M, int k, float w, float u) {
+__host__ __device__ __forceinline__ int sample_exit(const DevModel<R>& M, int k, float w, float u) {
   return sample_exit_rows(M.cexit, M.nlam, k, w, u);
 }
 
 template <class R>
-__device__ __forceinline__ int sample_star(const DevModel<R>& M, R u) {
+__host__ __device__ __forceinline__ int sample_star(const DevModel<R>& M, R u) {
   const int nl = M.nlam;
   const R target = u * M.star_cum[nl - 1];
   int lo = -1, hi = nl - 1;
