@@ -86,3 +86,40 @@ def test_binding_fails_loudly_without_library(monkeypatch):
     monkeypatch.setattr(mcrt, "LIB_PATH", "/nonexistent/libmcrt.so")
     with pytest.raises(RuntimeError):
         mcrt.lib()
+
+
+def test_disk_create_validates_on_the_host(L):
+    """mcrt_disk_create checks the grid and star before it touches a device: each bad input gives
+    MCRT_EINVAL and a message naming it; a valid one gets past the checks (here MCRT_ECUDA without a
+    device, or a disk on a GPU machine)."""
+    import ctypes as C
+    import math
+
+    import numpy as np
+
+    from paper_0902_3092_gb300 import mcrt
+    rf0 = np.array([1e13, 2e13, 4e13])
+    tf0 = np.array([0.0, math.pi / 2, math.pi])
+    rho0 = np.full(4, 1e-15)
+
+    def create(rf=rf0, tf=tf0, rho=rho0, T=5000.0, R=1e11, nr=2, nt=2):
+        rf, tf, rho = (np.ascontiguousarray(x, np.float64) for x in (rf, tf, rho))
+        p = lambda a: a.ctypes.data_as(C.POINTER(C.c_double))
+        g = mcrt.Grid(nr, nt, p(rf), p(tf), p(rho))
+        s = mcrt.Star(T, R)
+        h = C.c_void_p()
+        st = L.mcrt_disk_create(C.byref(g), C.byref(s), 0, None, C.byref(h))
+        if st == 0:
+            L.mcrt_disk_destroy(h)
+        return st, (L.mcrt_last_error(None) or b"").decode()
+
+    st, _ = create()
+    assert st in (0, 3)
+    bad = [(dict(rf=[1e13, 1e13, 4e13]), "r_faces"), (dict(rf=[-1.0, 2e13, 4e13]), "r_faces"),
+           (dict(rf=[1e13, math.nan, 4e13]), "r_faces"), (dict(tf=[0.1, math.pi / 2, math.pi]), "0 to pi"),
+           (dict(tf=[0.0, math.pi / 2, 3.0]), "0 to pi"), (dict(tf=[0.0, 0.0, math.pi]), "theta_faces"),
+           (dict(rho=[1e-15, -1.0, 0.0, 0.0]), "rho"), (dict(rho=[1e-15, math.inf, 0.0, 0.0]), "rho"),
+           (dict(T=0.0), "star"), (dict(R=math.inf), "star"), (dict(nr=0), "grid sizes")]
+    for kw, word in bad:
+        st, msg = create(**kw)
+        assert st == 1 and word in msg, (kw, st, msg)
