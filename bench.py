@@ -73,6 +73,9 @@ def parse():
                    help="instead of the transport step: PDA solve and adjoint on the 400x200 non-gray disk")
     p.add_argument("--raytrace", action="store_true",
                    help="instead of the transport step: ray-traced SED and image of the 200x120 disk at 45 degrees")
+    p.add_argument("--scattering", action="store_true",
+                   help="with --raytrace: keep the mean-intensity tally in the transport run (timed with and "
+                        "without it) and add the scattered light to the source function")
     p.add_argument("--viscous", action="store_true",
                    help="instead of the transport step: packets released by viscous heating in the 200x120 disk")
     p.add_argument("--polarized", action="store_true",
@@ -357,17 +360,24 @@ def raytrace_timing(args):
     degrees and 140 pc, after a 1e7-packet MRW run (Monte Carlo temperatures): 104,448 rays (16 rings
     inside r_in, 4 per radial cell, 128 azimuths) x 100 wavelength bins, FP32. Timed: one mcrt_raytrace
     call (trace + star + SED) per step with CUDA events on the disk's stream, L2 flushed before each;
-    the source table is built once (the temperatures do not change between views)."""
+    the source table is built once (the temperatures do not change between views). --scattering: the
+    transport run keeps the mean-intensity tally (its device time reported beside the same run without
+    it) and the source function adds the scattered light sigma J / chi."""
     import torch
     from paper_0902_3092_gb300 import disks, mcrt
     d = disks.config_thick_gray(200, 120, 1e6)
     st = torch.cuda.Stream()
     g = mcrt.Disk.from_model(d, stream=st.cuda_stream)
-    g.run_photons(10_000_000, seed=1, mrw=True, gamma=2.0, max_events=10 ** 6, want_sed=False)
+    scat = bool(args.scattering)
+    transport_s = {}
+    for keep in ((False, True) if scat else (False,)):
+        g.keep_mean_intensity(keep)  # resets the tallies
+        s = g.run_photons(10_000_000, seed=1, mrw=True, gamma=2.0, max_events=10 ** 6, want_sed=scat)
+        transport_s["with_j_tally" if keep else "plain"] = s["seconds"]
     rays = disks.polar_rays(d.r_faces_cm, n_sub=4, n_phi=128, n_inner=16)
     incl, dist = math.pi / 4, 140 * 3.0856775814913673e18
     g.set_rays(incl, dist, rays)
-    out = g.raytrace()  # source table and buffers
+    out = g.raytrace(scattering=scat)  # source table and buffers
     flush = torch.empty(256 * 2 ** 20, dtype=torch.uint8, device="cuda")
     times = []
     with ClockSampler(physical_gpu(0)) as clk:
@@ -376,7 +386,7 @@ def raytrace_timing(args):
                 flush.zero_()
                 e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
                 e0.record(st)
-                out = g.raytrace()
+                out = g.raytrace(scattering=scat)
                 e1.record(st)
             torch.cuda.synchronize()
             if k >= args.warmup:
@@ -390,7 +400,7 @@ def raytrace_timing(args):
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         g.set_rays(incl, dist, rays)
-        o2 = g.raytrace()
+        o2 = g.raytrace(scattering=scat)
         e2e.append(time.perf_counter() - t0)
     t_e2e = float(np.median(e2e))
     peaks = measured_peaks()
@@ -433,6 +443,9 @@ def raytrace_timing(args):
                     "d2h_bytes_per_step": 16 * n_bins},
             "roofline": roof, "cpu_baseline": cpu, "clocks": clocks, "gpu_launches": 4,
             "flux_total_erg_s_cm2": float(out["F"].sum())}
+    if scat:
+        line["config"]["scattering"] = "mean-intensity tally, sigma J / chi in the source function"
+        line["transport_seconds"] = transport_s
     print(json.dumps(line), flush=True)
 
 
