@@ -336,7 +336,8 @@ mcrt_status mcrt_trace_packets(mcrt_disk *d, uint64_t n_packets, uint64_t seed, 
  * Layout, all uint64 in host byte order: a header of 8 words {0x4D43525443484B31, version 1, nr, ntheta,
  * nlam, packets done, bits of the double packet count that normalises the tallies, 0}, then per cell
  * (r-major) the tallies, the entry counts and the absorption counts, then the escaping-energy spectrum
- * (nlam x 10 inclination bins). mcrt_restore checks the header against the disk (MCRT_EINVAL). */
+ * (nlam x 10 inclination bins). mcrt_restore checks the header against the disk (MCRT_EINVAL) and
+ * zeroes the tallies a checkpoint does not hold (polarization Stokes, mean-intensity path lengths). */
 mcrt_status mcrt_checkpoint(mcrt_disk *d, void *buf, size_t *len);
 mcrt_status mcrt_restore(mcrt_disk *d, const void *buf, size_t len);
 

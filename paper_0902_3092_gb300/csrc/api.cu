@@ -1134,6 +1134,10 @@ mcrt_status mcrt_restore(mcrt_disk* d, const void* buf, size_t len) {
   CK(cudaMemcpyAsync(d->visits.p, h + 8 + n, n * 8, cudaMemcpyHostToDevice, d->stream), "copy");
   CK(cudaMemcpyAsync(d->nabs.p, h + 8 + 2 * n, n * 8, cudaMemcpyHostToDevice, d->stream), "copy");
   if (nsed) CK(cudaMemcpyAsync(d->sed.p, h + 8 + 3 * n, nsed * 8, cudaMemcpyHostToDevice, d->stream), "copy");
+  // the tallies a checkpoint does not hold (Stokes Q/U, mean-intensity path lengths) start from zero
+  if (d->sed_q.p) CK(cudaMemsetAsync(d->sed_q.p, 0, d->sed_q.n, d->stream), "memset");
+  if (d->sed_u.p) CK(cudaMemsetAsync(d->sed_u.p, 0, d->sed_u.n, d->stream), "memset");
+  if (d->keep_j && d->jlen.p) CK(cudaMemsetAsync(d->jlen.p, 0, d->jlen.n, d->stream), "memset");
   CK(cudaStreamSynchronize(d->stream), "synchronize");
   d->packets_done = h[5];
   std::memcpy(&d->n_total, &h[6], 8);

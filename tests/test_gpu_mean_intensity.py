@@ -146,3 +146,20 @@ def test_tally_leaves_transport_unchanged_and_refusals(M):
     assert e.value.status == 7
     a.close()
     b.close()
+
+
+def test_restore_zeroes_the_tallies_a_checkpoint_does_not_hold(M):
+    """A checkpoint holds the integer tallies, not the path lengths: restoring one zeroes J (and the
+    restored tallies are the checkpoint's)."""
+    d = disks.config_plain_gray(10, 10, 30.0)
+    g = M.Disk.from_model(d)
+    g.keep_mean_intensity()
+    g.run_photons(2000, seed=1, precision=64)
+    blob = g.checkpoint()
+    saved = g.tallies()
+    g.run_photons(2000, seed=1, first_id=2000, precision=64)
+    assert g.mean_intensity().any()
+    g.restore(blob)
+    assert not g.mean_intensity().any()
+    assert all(np.array_equal(x, y) for x, y in zip(g.tallies(), saved))
+    g.close()
