@@ -363,16 +363,16 @@ __device__ __forceinline__ R hg_mu(R g, R xi) {
 
 // inverse of the MRW survival law P(x) = u (Eq. 7-8) from the two tables
 template <class R>
-__device__ __forceinline__ R mrw_x(const KParams<R>& P, R u) {
+__host__ __device__ __forceinline__ R mrw_x(const KParams<R>& P, R u) {
   const bool lower = u <= (R)0.5;
   const float a = lower ? (float)u : (float)((R)1 - u);
-  const float t = sizeof(R) == 4 ? __logf(a) : logf(a);
+  const float t = sizeof(R) == 4 ? fast_logf(a) : logf(a);
   float f = (t - P.mrw_t0) / P.mrw_dt;
   f = fminf(fmaxf(f, 0.f), (float)(kMrwTab - 1) - 1e-3f);
   const int i = (int)f;
   const float w = f - (float)i;
   const float* T = P.mrw_tab + (lower ? 0 : kMrwTab);
-  const float v = __ldg(T + i) * (1.f - w) + __ldg(T + i + 1) * w;
+  const float v = ldg(T + i) * (1.f - w) + ldg(T + i + 1) * w;
   return lower ? (R)v : (R)1 / (R)v;
 }
 

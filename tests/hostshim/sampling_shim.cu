@@ -1,6 +1,6 @@
-// Host build of the wavelength sampling of the transport kernels (transport.cuh: qpos, sample_bw,
-// sample_exit, sample_star) over the library's own temperature-grid tables (tables.h), for a CPU test
-// against the exact spectra of the oracle. One cell, log(1/m) = 0: log q = log(tally) + lq_run.
+// Host build of the wavelength sampling and the MRW escape-time lookup of the transport kernels
+// (transport.cuh: qpos, sample_bw, sample_exit, sample_star, mrw_x) over the library's own tables
+// (tables.h), for CPU tests against the oracle. One cell, log(1/m) = 0: log q = log(tally) + lq_run.
 #include <cstring>
 #include <vector>
 
@@ -55,3 +55,26 @@ extern "C" int exit_bin_host(unsigned long long tally, float u) {
 }
 
 extern "C" int star_bin_host(double u) { return sample_star(H->M, u); }
+
+// MRW escape time x with P(x) = u (Eq. 7-8) as the kernels look it up, FP32 (prec 32) or FP64
+extern "C" double mrw_x_host(double u, int prec) {
+  static std::vector<float> tab;
+  if (tab.empty()) {
+    tab.resize(2 * kMrwTab);
+    build_mrw_table(tab.data());
+  }
+  if (prec == 32) {
+    KParams<float> P;
+    std::memset(&P, 0, sizeof(P));
+    P.mrw_tab = tab.data();
+    P.mrw_t0 = mrw_table_t0();
+    P.mrw_dt = mrw_table_dt();
+    return mrw_x(P, (float)u);
+  }
+  KParams<double> P;
+  std::memset(&P, 0, sizeof(P));
+  P.mrw_tab = tab.data();
+  P.mrw_t0 = mrw_table_t0();
+  P.mrw_dt = mrw_table_dt();
+  return mrw_x(P, u);
+}

@@ -68,3 +68,20 @@ def test_sampled_bins_follow_exact_spectra(lib, oracle):
         F = np.cumsum(p) / p.sum()
         dev = np.max(np.abs(_cdf(nl, lambda u: lib.bw_bin_host(tally(T_old), tally(T_new), u)) - F))
         assert dev < tol, (T_old, ratio, dev)
+
+
+def test_kernel_mrw_escape_time_matches_oracle(lib, oracle):
+    """The kernels' MRW escape-time lookup (mrw_x over the library's table, Eq. 7-8), FP32 and FP64, at
+    uniforms on the kernels' 2^-23 grid (where 1 - u is exact): within 1e-5 of the oracle's inverse of
+    P(x), including both tails, the switch of tables at u = 1/2 and the grid's end points (measured
+    5.9e-6, at u = 1/2, where the index clamp keeps 1e-3 of an interval)."""
+    lib.mrw_x_host.restype = C.c_double
+    lib.mrw_x_host.argtypes = [C.c_double, C.c_int]
+    rng = np.random.default_rng(2)
+    k = np.concatenate([rng.integers(0, 2 ** 23, 400), np.arange(0, 30), 2 ** 23 - 1 - np.arange(0, 30),
+                        [2 ** 22 - 1, 2 ** 22]])
+    u = (k + 0.5) / 2 ** 23
+    ref = np.array([oracle.mrw_x(x) for x in u])
+    for prec in (32, 64):
+        x = np.array([lib.mrw_x_host(float(v), prec) for v in u])
+        assert np.max(np.abs(x / ref - 1)) < 1e-5, prec
