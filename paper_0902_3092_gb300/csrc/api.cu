@@ -310,23 +310,12 @@ bool account_deposits(mcrt_disk* d, const unsigned long long* c) {
 namespace mcrt {
 // density-dependent device arrays from d->rho: rho * l_unit (FP32, FP64), cell masses, log(1/m), rho (cgs)
 mcrt_status upload_density(mcrt_disk* d) {
-  const int nr = d->nr, nt = d->nt;
-  const size_t ncell = (size_t)nr * nt;
-  std::vector<double> rhol(ncell);
-  d->mass.resize(ncell);
-  std::vector<float> lqm(ncell);
-  for (int i = 0; i < nr; ++i)
-    for (int j = 0; j < nt; ++j) {
-      const size_t c = (size_t)i * nt + j;
-      rhol[c] = d->rho[c] * d->l_unit;
-      const double r1 = d->rf[i], r2 = d->rf[i + 1];
-      const double V = 2.0 * kPi / 3.0 * (r2 * r2 * r2 - r1 * r1 * r1) * (std::cos(d->tf[j]) - std::cos(d->tf[j + 1]));
-      d->mass[c] = d->rho[c] * V;
-      lqm[c] = d->mass[c] > 0 ? (float)(-std::log(d->mass[c])) : 0.f;
-    }
-  cudaError_t e = upload(d->rho32, cast_vec<float>(rhol));
-  if (e == cudaSuccess) e = upload(d->rho64, rhol);
-  if (e == cudaSuccess) e = upload(d->lqm, lqm);
+  DensityArrays da;
+  density_arrays(d->nr, d->nt, d->rf.data(), d->tf.data(), d->rho.data(), da);
+  d->mass = da.mass;
+  cudaError_t e = upload(d->rho32, cast_vec<float>(da.rhol));
+  if (e == cudaSuccess) e = upload(d->rho64, da.rhol);
+  if (e == cudaSuccess) e = upload(d->lqm, da.lqm);
   if (e == cudaSuccess) e = upload(d->mass_d, d->mass);
   if (e == cudaSuccess) e = upload(d->rho_cgs_d, d->rho);
   if (e != cudaSuccess) return cuda_fail(d, e, "upload");
@@ -458,22 +447,8 @@ mcrt_status mcrt_disk_create(const mcrt_grid* grid, const mcrt_star* star, int d
   d->Tmax = std::max(1e4, 2.0 * d->Tstar);
 
   // geometry in units of r_faces[0]
-  std::vector<double> rf(nr + 1), rf2(nr + 1), c2(nt + 1), s2(nt + 1), cf(nt + 1), sf(nt + 1);
-  std::vector<signed char> fk(nt + 1);
-  for (int i = 0; i <= nr; ++i) {
-    rf[i] = d->rf[i] / d->l_unit;
-    rf2[i] = rf[i] * rf[i];
-  }
-  for (int j = 0; j <= nt; ++j) {
-    const double t = d->tf[j];
-    cf[j] = std::cos(t);
-    sf[j] = std::sin(t);
-    c2[j] = cf[j] * cf[j];
-    s2[j] = sf[j] * sf[j];
-    if (j == 0 || j == nt) fk[j] = 2;
-    else if (std::fabs(t - 0.5 * kPi) < 1e-12) fk[j] = 0;
-    else fk[j] = t < 0.5 * kPi ? 1 : -1;
-  }
+  GeomArrays geo;
+  geometry_arrays(nr, nt, d->rf.data(), d->tf.data(), geo);
   const size_t ncell = (size_t)nr * nt;
   mcrt_status st = MCRT_OK;
 #define UP(buf, vec)                                          \
@@ -481,19 +456,19 @@ mcrt_status mcrt_disk_create(const mcrt_grid* grid, const mcrt_star* star, int d
     cudaError_t e2 = upload(buf, vec);                        \
     if (e2 != cudaSuccess) return fail(cuda_fail(d, e2, "upload")); \
   } while (0)
-  UP(d->rf32, cast_vec<float>(rf));
-  UP(d->rf2_32, cast_vec<float>(rf2));
-  UP(d->c2_32, cast_vec<float>(c2));
-  UP(d->s2_32, cast_vec<float>(s2));
-  UP(d->cf32, cast_vec<float>(cf));
-  UP(d->sf32, cast_vec<float>(sf));
-  UP(d->rf64, rf);
-  UP(d->rf2_64, rf2);
-  UP(d->c2_64, c2);
-  UP(d->s2_64, s2);
-  UP(d->cf64, cf);
-  UP(d->sf64, sf);
-  UP(d->fk, fk);
+  UP(d->rf32, cast_vec<float>(geo.rf));
+  UP(d->rf2_32, cast_vec<float>(geo.rf2));
+  UP(d->c2_32, cast_vec<float>(geo.c2));
+  UP(d->s2_32, cast_vec<float>(geo.s2));
+  UP(d->cf32, cast_vec<float>(geo.cf));
+  UP(d->sf32, cast_vec<float>(geo.sf));
+  UP(d->rf64, geo.rf);
+  UP(d->rf2_64, geo.rf2);
+  UP(d->c2_64, geo.c2);
+  UP(d->s2_64, geo.s2);
+  UP(d->cf64, geo.cf);
+  UP(d->sf64, geo.sf);
+  UP(d->fk, geo.fk);
 #undef UP
   st = upload_density(d);
   if (st != MCRT_OK) return fail(st);
@@ -537,18 +512,9 @@ mcrt_status mcrt_set_opacity(mcrt_disk* d, int nlam, const double* lam_e, const 
   for (int b = 1; b < nlam; ++b)
     if (d->kabs[b] != d->kabs[0] || d->ksca[b] != d->ksca[0] || d->g[b] != d->g[0]) d->gray = false;
 
-  std::vector<double> chi(nlam), alb(nlam), chip(nlam), star(nlam), B(nlam), dB(nlam);
-  for (int b = 0; b < nlam; ++b) {
-    chi[b] = d->kabs[b] + d->ksca[b];
-    alb[b] = d->ksca[b] / chi[b];
-    chip[b] = d->kabs[b] + (1.0 - d->g[b]) * d->ksca[b];
-  }
-  planck_bins(d->lam_e.data(), nlam, d->Tstar, B.data(), nullptr);
-  double acc = 0.0;
-  for (int b = 0; b < nlam; ++b) {
-    acc += B[b];
-    star[b] = acc;
-  }
+  DustArrays dust;
+  dust_arrays(nlam, d->lam_e.data(), d->kabs.data(), d->ksca.data(), d->g.data(), d->Tstar, dust);
+  const std::vector<double>&chi = dust.chi, &alb = dust.alb, &chip = dust.chip, &star = dust.star;
   const int nT = d->nT;
   TGridTables tt;
   build_T_tables(nlam, d->lam_e.data(), d->kabs.data(), chip.data(), nT, d->Tmin, d->Tmax, tt);

@@ -1,6 +1,7 @@
-// tables.h -- the tables the transport and temperature kernels read: the dust tables on the temperature
-// grid (built when the opacities are set) and the inverse MRW escape-time table (built once per
-// process). Host code, compiled for the host in the tests too.
+// tables.h -- the arrays and tables the kernels read, built on the host: the grid geometry, the density
+// arrays, the dust per wavelength bin and its tables on the temperature grid, the inverse MRW
+// escape-time table, and the sampling table of a Mueller matrix. Host code, compiled for the host in the
+// tests too.
 #pragma once
 #include <cmath>
 #include <vector>
@@ -61,6 +62,85 @@ inline void build_T_tables(int nlam, const double* lam_e, const double* kabs, co
     t.kbark[k] = (float)(skdb / sdb);
     if (sdb > 0)
       for (int b = 0; b < nlam; ++b) t.jw[(size_t)k * nlam + b] = (float)(dB[b] / sdb);
+  }
+}
+
+// Geometry of the grid in units of r_faces[0] (FP64; the FP32 copies are cast from these): radial faces
+// and their squares, per polar face cos, sin, their squares and its kind (2 the axis, 0 the midplane
+// plane, +1 / -1 a cone opening up / down).
+struct GeomArrays {
+  std::vector<double> rf, rf2, c2, s2, cf, sf;
+  std::vector<signed char> fk;
+};
+inline void geometry_arrays(int nr, int nt, const double* rf_cm, const double* tf, GeomArrays& g) {
+  const double l = rf_cm[0];
+  g.rf.resize(nr + 1);
+  g.rf2.resize(nr + 1);
+  g.c2.resize(nt + 1);
+  g.s2.resize(nt + 1);
+  g.cf.resize(nt + 1);
+  g.sf.resize(nt + 1);
+  g.fk.resize(nt + 1);
+  for (int i = 0; i <= nr; ++i) {
+    g.rf[i] = rf_cm[i] / l;
+    g.rf2[i] = g.rf[i] * g.rf[i];
+  }
+  for (int j = 0; j <= nt; ++j) {
+    const double t = tf[j];
+    g.cf[j] = std::cos(t);
+    g.sf[j] = std::sin(t);
+    g.c2[j] = g.cf[j] * g.cf[j];
+    g.s2[j] = g.sf[j] * g.sf[j];
+    if (j == 0 || j == nt) g.fk[j] = 2;
+    else if (std::fabs(t - 0.5 * kPi) < 1e-12) g.fk[j] = 0;
+    else g.fk[j] = t < 0.5 * kPi ? 1 : -1;
+  }
+}
+
+// Density-dependent arrays: rho * l_unit (extinction per internal length unit per cm^2/g), the cell
+// masses (g) and log(1 / m) (FP32, 0 for empty cells).
+struct DensityArrays {
+  std::vector<double> rhol, mass;
+  std::vector<float> lqm;
+};
+inline void density_arrays(int nr, int nt, const double* rf_cm, const double* tf, const double* rho, DensityArrays& d) {
+  const size_t ncell = (size_t)nr * nt;
+  d.rhol.resize(ncell);
+  d.mass.resize(ncell);
+  d.lqm.resize(ncell);
+  for (int i = 0; i < nr; ++i)
+    for (int j = 0; j < nt; ++j) {
+      const size_t c = (size_t)i * nt + j;
+      d.rhol[c] = rho[c] * rf_cm[0];
+      const double r1 = rf_cm[i], r2 = rf_cm[i + 1];
+      const double V = 2.0 * kPi / 3.0 * (r2 * r2 * r2 - r1 * r1 * r1) * (std::cos(tf[j]) - std::cos(tf[j + 1]));
+      d.mass[c] = rho[c] * V;
+      d.lqm[c] = d.mass[c] > 0 ? (float)(-std::log(d.mass[c])) : 0.f;
+    }
+}
+
+// Dust per wavelength bin: extinction chi = kappa + sigma, albedo sigma / chi, chi' = kappa + (1 - g) sigma,
+// and the cumulative stellar spectrum (unnormalised Bbar_b(T_star)).
+struct DustArrays {
+  std::vector<double> chi, alb, chip, star;
+};
+inline void dust_arrays(int nlam, const double* lam_e, const double* kabs, const double* ksca, const double* g,
+                        double Tstar, DustArrays& o) {
+  o.chi.resize(nlam);
+  o.alb.resize(nlam);
+  o.chip.resize(nlam);
+  o.star.resize(nlam);
+  for (int b = 0; b < nlam; ++b) {
+    o.chi[b] = kabs[b] + ksca[b];
+    o.alb[b] = ksca[b] / o.chi[b];
+    o.chip[b] = kabs[b] + (1.0 - g[b]) * ksca[b];
+  }
+  std::vector<double> B(nlam);
+  planck_bins(lam_e, nlam, Tstar, B.data(), nullptr);
+  double acc = 0.0;
+  for (int b = 0; b < nlam; ++b) {
+    acc += B[b];
+    o.star[b] = acc;
   }
 }
 

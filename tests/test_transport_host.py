@@ -1,0 +1,108 @@
+"""The transport kernels' per-packet code (transport.cuh: launch_packet, step, advance, interact, the MRW
+chain and the mean-intensity tally) compiled for the host in FP64 over a model built by the library's own
+host builders (tables.h), packets run one after another as one lane of the FP64 kernels runs them, and
+compared with the oracle on the CPU.
+
+Gray dust with MRW: the same events as the oracle (every counter, entry and absorption count equal);
+energy tallies within 1e-5 (the tabulated MRW escape time, within 6e-6 of the exact inverse); the
+mean intensity per cell within 1e-5, per bin within 5e-3 of itself plus 1e-5 of the cell's (the walks'
+spectrum from the FP32 weight table). The J tally changes nothing else (the same run without
+it: identical tallies and counters). Non-gray dust, where the tabulated re-emission sampling lets the
+packets' histories part from the oracle's: radiative equilibrium on the run's own J and temperatures,
+sum_b kappa_b J_b = sum_b kappa_b Bbar_b(T), in every cell with 100 packet energies, within four counting
+errors plus 2e-3."""
+import ctypes as C
+import math
+import os
+import shutil
+import subprocess
+
+import numpy as np
+import pytest
+
+from paper_0902_3092_gb300 import disks
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+CUDA_INC = "/usr/local/cuda/include"
+
+
+@pytest.fixture(scope="module")
+def lib(tmp_path_factory):
+    if not shutil.which("g++") or not os.path.exists(os.path.join(CUDA_INC, "cuda_runtime.h")):
+        pytest.skip("g++ or the CUDA headers not found")
+    out = tmp_path_factory.mktemp("transport") / "libhosttransport.so"
+    subprocess.check_call(["g++", "-O2", "-std=c++17", "-ffp-contract=off", "-fPIC", "-shared", "-I", CUDA_INC,
+                           "-I", os.path.join(ROOT, "include"), "-I", os.path.join(ROOT, "paper_0902_3092_gb300", "csrc"),
+                           os.path.join(ROOT, "tests", "hostshim", "transport_shim.cpp"), "-o", str(out)])
+    return C.CDLL(str(out))
+
+
+def run(lib, d, n, seed, mrw, gamma, nmin, want_sed, keep_j):
+    op = d.opacity
+    nc = d.nr * d.ntheta
+    t, v, a = (np.zeros(nc, np.uint64) for _ in range(3))
+    sed = np.zeros(op.nlam * 10, np.uint64)
+    j = np.zeros(nc * op.nlam) if keep_j else None
+    cnt = np.zeros(8, np.uint64)
+    arrs = [np.ascontiguousarray(x, np.float64) for x in
+            (d.r_faces_cm, d.theta_faces, d.rho.ravel(), op.lam_edges_um, op.kappa_abs, op.kappa_sca, op.g)]
+    P = lambda x: None if x is None else x.ctypes.data_as(C.c_void_p)
+    lib.host_transport(C.c_int(d.nr), C.c_int(d.ntheta), P(arrs[0]), P(arrs[1]), P(arrs[2]), C.c_int(op.nlam),
+                       P(arrs[3]), P(arrs[4]), P(arrs[5]), P(arrs[6]), C.c_double(d.star.T_K), C.c_double(d.star.R_cm),
+                       C.c_uint64(n), C.c_uint64(seed), C.c_int(mrw), C.c_double(gamma), C.c_int(nmin),
+                       C.c_int(want_sed), P(t), P(v), P(a), P(sed), P(j), P(cnt))
+    out = dict(tally=t, visits=v, nabs=a, sed=sed, counters=cnt)
+    if keep_j:  # path lengths (internal units, l = r_in) -> J = E_pkt * length / (4 pi V)
+        rf, tf = d.r_faces_cm, d.theta_faces
+        V = (2 * np.pi / 3) * np.diff(rf ** 3)[:, None] * (np.cos(tf[:-1]) - np.cos(tf[1:]))[None, :]
+        out["J"] = (d.star.L / n) * j.reshape(d.nr, d.ntheta, op.nlam) * rf[0] / (4 * np.pi * V[:, :, None])
+        out["V"] = V
+    return out
+
+
+def test_gray_mrw_transport_and_mean_intensity_match_oracle(lib, oracle):
+    d = disks.config_thick_gray(30, 20, 1e4)
+    n = 2000
+    h = run(lib, d, n, seed=3, mrw=1, gamma=2.0, nmin=20, want_sed=0, keep_j=1)
+    ref = oracle.Run(d).run(n, seed=3, mrw=True, gamma=2.0, want_sed=False, want_j=True)
+    st = ref.stats
+    want = [st[k] for k in ("packets", "absorptions", "scatterings", "crossings", "mrw_jumps", "capped", "escaped",
+                            "error_flags")]
+    assert [int(x) for x in h["counters"]] == want and st["mrw_jumps"] > 1000
+    assert np.array_equal(h["visits"], ref.visits) and np.array_equal(h["nabs"], ref.nabs)
+    m = ref.tally > 0
+    assert np.array_equal(h["tally"] > 0, m)
+    assert np.max(np.abs(h["tally"][m].astype(float) / ref.tally[m].astype(float) - 1)) < 1e-5
+    J, Jo = h["J"], ref.mean_intensity()
+    tot, toto = J.sum(axis=2), Jo.sum(axis=2)
+    assert np.array_equal(tot > 0, toto > 0)
+    pos = toto > 0
+    assert np.max(np.abs(tot[pos] / toto[pos] - 1)) < 1e-5
+    # per bin: the walks' spectrum comes from the FP32 weight table (within 3.4e-3 of the exact weights
+    # where they exceed 1e-6 of the total, zero where the exact ones fall below ~1e-45)
+    assert np.all(np.abs(J - Jo) <= 5e-3 * Jo + 1e-5 * toto[:, :, None])
+    # without the tally: the same transport
+    h2 = run(lib, d, n, seed=3, mrw=1, gamma=2.0, nmin=20, want_sed=0, keep_j=0)
+    for k in ("tally", "visits", "nabs", "sed", "counters"):
+        assert np.array_equal(h[k], h2[k]), k
+
+
+def test_nongray_mean_intensity_balances_absorption(lib, oracle):
+    d = disks.config_nongray(16, 16, 1e4)
+    n = 300_000
+    h = run(lib, d, n, seed=8, mrw=1, gamma=2.0, nmin=5, want_sed=1, keep_j=1)
+    assert int(h["counters"][4]) > 10_000 and int(h["counters"][7]) == 0
+    r = oracle.Run(d)
+    r.tally[:] = h["tally"]
+    r.n_total = n
+    T, _ = r.temperatures()
+    op = d.opacity
+    units = h["tally"].reshape(d.nr, d.ntheta) / 65536.0
+    nabs = h["nabs"].reshape(d.nr, d.ntheta).astype(float)
+    n_mrw_cells = 0
+    for i, j in zip(*np.nonzero(units >= 100)):
+        absorbed = (op.kappa_abs * h["J"][i, j]).sum()
+        emitted = (op.kappa_abs * oracle.planck_bins(op.lam_edges_um, T[i, j])).sum()
+        assert abs(absorbed / emitted - 1) < 4 * math.sqrt(nabs[i, j]) / units[i, j] + 2e-3, (i, j)
+        n_mrw_cells += nabs[i, j] < 0.6 * units[i, j]
+    assert n_mrw_cells >= 2
