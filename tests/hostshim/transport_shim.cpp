@@ -1,8 +1,9 @@
 // Host build of the transport kernels' per-packet code (transport.cuh: launch_packet, step and what they
-// call) in FP64, for a CPU test against the oracle: packets run one after another, as one lane of the FP64
-// kernels runs them, over a model built by the library's own host builders (tables.h). Compiled by the host
-// compiler with single-lane stand-ins for the CUDA builtins the header names (one lane: warp operations
-// return their own lane's value; atomics are plain read-modify-writes).
+// call) in FP32 or FP64, for CPU tests against the oracle: packets run one after another, as one lane of a
+// single-disk kernel runs them, over a model built by the library's own host builders (tables.h).
+// Compiled by the host compiler with single-lane stand-ins for the CUDA builtins the header names (one
+// lane: warp operations return their own lane's value; atomics are plain read-modify-writes; the fast
+// FP32 intrinsics are the host's correctly rounded functions).
 #include <cmath>
 #include <cstdint>
 #include <cstring>
@@ -22,8 +23,22 @@ static HostIdx host_threadIdx{0, 0, 0}, host_blockIdx{0, 0, 0}, host_blockDim{1,
 #define __noinline__ __attribute__((noinline))
 #endif
 #define __launch_bounds__(...)
+// float overloads of the math functions, as CUDA provides them for device code
+using std::acos;
+using std::atan2;
+using std::cbrt;
+using std::cos;
+using std::exp;
+using std::fabs;
+using std::floor;
+using std::fmax;
+using std::fmin;
 using std::isfinite;
+using std::log;
+using std::pow;
 using std::signbit;
+using std::sin;
+using std::sqrt;
 template <class T>
 inline T __ldg(const T* p) { return *p; }
 inline float __logf(float x) { return std::log(x); }
@@ -72,101 +87,128 @@ using namespace mcrt;
 
 namespace {
 
-template <bool G, bool JT>
-void run_packets(const KParams<double>& P, const DevModel<double>& M, uint64_t n, Acc& acc) {
+template <class R, bool G, bool POL, bool JT>
+void run_packets(const KParams<R>& P, const DevModel<R>& M, uint64_t n, Acc& acc) {
   for (uint64_t k = 0; k < n; ++k) {
-    Pkt<double> s;
+    Pkt<R> s;
     std::memset(&s, 0, sizeof(s));
     SerialRng rng{{(uint32_t)P.seed, (uint32_t)(P.seed >> 32)}};
-    launch_packet<double, false, G, false, JT>(P, rng, M, s, k, -1, acc);
-    while (step<double, false, G, false, JT>(P, rng, M, s, acc)) {
+    launch_packet<R, false, G, POL, JT>(P, rng, M, s, k, -1, acc);
+    while (step<R, false, G, POL, JT>(P, rng, M, s, acc)) {
     }
   }
 }
 
-}  // namespace
+template <class R>
+std::vector<R> cast(const std::vector<double>& v) {
+  return std::vector<R>(v.begin(), v.end());
+}
 
-// Transports packets 0 .. n-1 with Philox key `seed` through the disk (cgs inputs, as mcrt_disk_create and
-// mcrt_set_opacity take them) and returns the tallies (nr*nt: fixed-point energy, entries, absorptions),
-// the escape counts (nlam * 10), the mean-intensity path lengths (nr*nt*nlam, internal length units;
-// NULL: not kept) and the counters {packets, absorptions, scatterings, crossings, MRW jumps, capped,
-// escaped, error flags}.
-extern "C" void host_transport(int nr, int nt, const double* rf_cm, const double* tf, const double* rho, int nlam,
-                               const double* lam_e, const double* kabs, const double* ksca, const double* g,
-                               double Tstar, double Rstar, uint64_t n, uint64_t seed, int mrw, double gamma, int nmin,
-                               int want_sed, uint64_t* tally, uint64_t* visits, uint64_t* nabs, uint64_t* sed,
-                               double* jlen, uint64_t* counters) {
+struct Inputs {
+  int nr, nt, nlam;
+  const double *rf_cm, *tf, *rho, *lam_e, *kabs, *ksca, *g;
+  double Tstar, Rstar;
+  uint64_t n, seed;
+  int mrw, nmin, want_sed, nmu;
+  double gamma;
+  const double* mueller;  // [nlam][4][nmu] or NULL
+};
+
+struct Outputs {
+  uint64_t *tally, *visits, *nabs, *sed, *sed_q, *sed_u, *counters;
+  double* jlen;
+};
+
+// the model as the library builds it (make_model, fill_params), in precision R
+template <class R>
+void run(const Inputs& in, const Outputs& out) {
+  const int nr = in.nr, nt = in.nt, nlam = in.nlam;
   GeomArrays geo;
-  geometry_arrays(nr, nt, rf_cm, tf, geo);
+  geometry_arrays(nr, nt, in.rf_cm, in.tf, geo);
   DensityArrays den;
-  density_arrays(nr, nt, rf_cm, tf, rho, den);
+  density_arrays(nr, nt, in.rf_cm, in.tf, in.rho, den);
   DustArrays dust;
-  dust_arrays(nlam, lam_e, kabs, ksca, g, Tstar, dust);
+  dust_arrays(nlam, in.lam_e, in.kabs, in.ksca, in.g, in.Tstar, dust);
   const int nT = 1024;
   TGridTables tt;
-  build_T_tables(nlam, lam_e, kabs, dust.chip.data(), nT, 1.0, std::max(1e4, 2.0 * Tstar), tt);
+  build_T_tables(nlam, in.lam_e, in.kabs, dust.chip.data(), nT, 1.0, std::max(1e4, 2.0 * in.Tstar), tt);
   std::vector<float> mtab(2 * kMrwTab);
   build_mrw_table(mtab.data());
-  std::vector<double> gq(g, g + nlam);
+  std::vector<double> gq(in.g, in.g + nlam), mt, mc;
+  if (in.mueller) {
+    mt.assign(in.mueller, in.mueller + (size_t)nlam * 4 * in.nmu);
+    mc.resize((size_t)nlam * in.nmu);
+    for (int b = 0; b < nlam; ++b) mueller_cdf(in.mueller + (size_t)b * 4 * in.nmu, in.nmu, mc.data() + (size_t)b * in.nmu);
+  }
   bool gray = true;
   for (int b = 1; b < nlam; ++b)
-    if (kabs[b] != kabs[0] || ksca[b] != ksca[0] || g[b] != g[0]) gray = false;
+    if (in.kabs[b] != in.kabs[0] || in.ksca[b] != in.ksca[0] || in.g[b] != in.g[0]) gray = false;
   std::vector<unsigned long long> cnt(C_NCNT, 0ull);
+  const std::vector<R> rf = cast<R>(geo.rf), rf2 = cast<R>(geo.rf2), c2 = cast<R>(geo.c2), s2 = cast<R>(geo.s2),
+                       cf = cast<R>(geo.cf), sf = cast<R>(geo.sf), rho = cast<R>(den.rhol), chi = cast<R>(dust.chi),
+                       alb = cast<R>(dust.alb), g = cast<R>(gq), star = cast<R>(dust.star), mtr = cast<R>(mt),
+                       mcr = cast<R>(mc);
 
-  DevModel<double> M;
+  DevModel<R> M;
   std::memset(&M, 0, sizeof(M));
   M.nr = nr;
   M.nt = nt;
   M.nlam = nlam;
   M.nT = nT;
   M.gray = gray ? 1 : 0;
-  M.rf = geo.rf.data();
-  M.rf2 = geo.rf2.data();
-  M.c2 = geo.c2.data();
-  M.s2 = geo.s2.data();
-  M.cf = geo.cf.data();
-  M.sf = geo.sf.data();
+  M.rf = rf.data();
+  M.rf2 = rf2.data();
+  M.c2 = c2.data();
+  M.s2 = s2.data();
+  M.cf = cf.data();
+  M.sf = sf.data();
   M.fk = geo.fk.data();
-  M.rho = den.rhol.data();
-  M.chi = dust.chi.data();
-  M.alb = dust.alb.data();
-  M.gq = gq.data();
-  M.star_cum = dust.star.data();
-  M.chi0 = kabs[0] + ksca[0];
-  M.alb0 = ksca[0] / M.chi0;
-  M.g0 = g[0];
-  M.chiR0 = kabs[0] + (1.0 - g[0]) * ksca[0];
-  M.kbar0 = kabs[0];
+  M.rho = rho.data();
+  M.chi = chi.data();
+  M.alb = alb.data();
+  M.gq = g.data();
+  M.star_cum = star.data();
+  const double chi0 = in.kabs[0] + in.ksca[0];
+  M.chi0 = (R)chi0;
+  M.alb0 = (R)(in.ksca[0] / chi0);
+  M.g0 = (R)in.g[0];
+  M.chiR0 = (R)(in.kabs[0] + (1.0 - in.g[0]) * in.ksca[0]);
+  M.kbar0 = (R)in.kabs[0];
   M.lQk = tt.lQk.data();
   M.cbw = tt.cbw.data();
   M.cexit = tt.cexit.data();
   M.chiR = tt.chiRk.data();
   M.kbar = tt.kbark.data();
   M.lqm = den.lqm.data();
-  const double Lstar = 4.0 * kPi * Rstar * Rstar * MCRT_SIGMA * std::pow(Tstar, 4);
-  M.lq_run = (float)std::log(Lstar / ((double)n * (double)kEUnit));
+  const double Lstar = 4.0 * kPi * in.Rstar * in.Rstar * MCRT_SIGMA * std::pow(in.Tstar, 4);
+  M.lq_run = (float)std::log(Lstar / ((double)in.n * (double)kEUnit));
   M.src_Lstar = Lstar;
   M.src_Ltot = Lstar;
-  M.jlen = jlen;
+  M.mtab = in.mueller ? mtr.data() : nullptr;
+  M.mcdf = in.mueller ? mcr.data() : nullptr;
+  M.nmu = in.mueller ? in.nmu : 0;
+  M.sed_q = (unsigned long long*)out.sed_q;
+  M.sed_u = (unsigned long long*)out.sed_u;
+  M.jlen = out.jlen;
   M.jw = tt.jw.data();
-  M.tally = (unsigned long long*)tally;
-  M.visits = (unsigned long long*)visits;
-  M.nabs = (unsigned long long*)nabs;
-  M.sed = (unsigned long long*)sed;
+  M.tally = (unsigned long long*)out.tally;
+  M.visits = (unsigned long long*)out.visits;
+  M.nabs = (unsigned long long*)out.nabs;
+  M.sed = (unsigned long long*)out.sed;
   M.cnt = cnt.data();
-  M.n_packets = n;
+  M.n_packets = in.n;
 
-  KParams<double> P;
+  KParams<R> P;
   std::memset(&P, 0, sizeof(P));
   P.m0 = M;
-  P.mrw = mrw ? 1 : 0;
-  P.nmin = nmin;
+  P.mrw = in.mrw ? 1 : 0;
+  P.nmin = in.nmin;
   P.exit_dir = 0;
-  P.want_lam = (!gray || want_sed) ? 1 : 0;
+  P.want_lam = (!gray || in.want_sed) ? 1 : 0;
   P.refill = 4;
   P.defer = 8;
-  P.gamma = gamma;
-  P.seed = seed;
+  P.gamma = (R)in.gamma;
+  P.seed = in.seed;
   P.max_events = 1ull << 31;
   P.max_steps = 4000000000ull;
   P.mrw_tab = mtab.data();
@@ -176,10 +218,38 @@ extern "C" void host_transport(int nr, int nt, const double* rf_cm, const double
 
   Acc acc;
   std::memset(&acc, 0, sizeof(acc));
-  if (gray && jlen) run_packets<true, true>(P, M, n, acc);
-  else if (gray) run_packets<true, false>(P, M, n, acc);
-  else if (jlen) run_packets<false, true>(P, M, n, acc);
-  else run_packets<false, false>(P, M, n, acc);
+  const bool pol = in.mueller != nullptr, jt = out.jlen != nullptr;
+  if (pol) {
+    if (gray) run_packets<R, true, true, false>(P, M, in.n, acc);
+    else run_packets<R, false, true, false>(P, M, in.n, acc);
+  } else if (jt) {
+    if (gray) run_packets<R, true, false, true>(P, M, in.n, acc);
+    else run_packets<R, false, false, true>(P, M, in.n, acc);
+  } else {
+    if (gray) run_packets<R, true, false, false>(P, M, in.n, acc);
+    else run_packets<R, false, false, false>(P, M, in.n, acc);
+  }
   const unsigned long long c[8] = {acc.packets, acc.abs, acc.sca, acc.cross, acc.mrw, acc.capped, acc.escaped, acc.err};
-  for (int i = 0; i < 8; ++i) counters[i] = c[i];
+  for (int i = 0; i < 8; ++i) out.counters[i] = c[i];
+}
+
+}  // namespace
+
+// Transports packets 0 .. n-1 with Philox key `seed` through the disk (cgs inputs, as mcrt_disk_create and
+// mcrt_set_opacity take them), in FP32 (prec 32) or FP64, polarized with a Mueller matrix [nlam][4][nmu]
+// (NULL: unpolarized), keeping the mean-intensity path lengths when jlen is given (nr*nt*nlam, internal
+// length units; not with a Mueller matrix). Returns the tallies (nr*nt: fixed-point energy, entries,
+// absorptions), the escape counts and Stokes Q/I, U/I tallies (nlam * 10) and the counters {packets,
+// absorptions, scatterings, crossings, MRW jumps, capped, escaped, error flags}.
+extern "C" void host_transport(int nr, int nt, const double* rf_cm, const double* tf, const double* rho, int nlam,
+                               const double* lam_e, const double* kabs, const double* ksca, const double* g,
+                               double Tstar, double Rstar, uint64_t n, uint64_t seed, int mrw, double gamma, int nmin,
+                               int want_sed, int prec, int nmu, const double* mueller, uint64_t* tally,
+                               uint64_t* visits, uint64_t* nabs, uint64_t* sed, uint64_t* sed_q, uint64_t* sed_u,
+                               double* jlen, uint64_t* counters) {
+  const Inputs in{nr, nt, nlam, rf_cm, tf, rho, lam_e, kabs, ksca, g, Tstar, Rstar, n, seed, mrw, nmin, want_sed, nmu,
+                  gamma, mueller};
+  const Outputs out{tally, visits, nabs, sed, sed_q, sed_u, counters, jlen};
+  if (prec == 32) run<float>(in, out);
+  else run<double>(in, out);
 }

@@ -1,7 +1,7 @@
 """The transport kernels' per-packet code (transport.cuh: launch_packet, step, advance, interact, the MRW
-chain and the mean-intensity tally) compiled for the host in FP64 over a model built by the library's own
-host builders (tables.h), packets run one after another as one lane of the FP64 kernels runs them, and
-compared with the oracle on the CPU.
+chain, the mean-intensity tally and the polarization) compiled for the host, FP64 and FP32, over a model
+built by the library's own host builders (tables.h), packets run one after another as one lane of a
+single-disk kernel runs them, and compared with the oracle on the CPU.
 
 Gray dust with MRW: the same events as the oracle (every counter, entry and absorption count equal);
 energy tallies within 1e-5 (the tabulated MRW escape time, within 6e-6 of the exact inverse); the
@@ -10,7 +10,8 @@ spectrum from the FP32 weight table). The J tally changes nothing else (the same
 it: identical tallies and counters). Non-gray dust, where the tabulated re-emission sampling lets the
 packets' histories part from the oracle's: radiative equilibrium on the run's own J and temperatures,
 sum_b kappa_b J_b = sum_b kappa_b Bbar_b(T), in every cell with 100 packet energies, within four counting
-errors plus 2e-3."""
+errors plus 2e-3. Polarized transport: FP64 equal to the oracle's events, tallies and (within three
+fixed-point units) Stokes sums; FP32 Q/I of a thin scattering disk within Monte Carlo errors."""
 import ctypes as C
 import math
 import os
@@ -37,27 +38,39 @@ def lib(tmp_path_factory):
     return C.CDLL(str(out))
 
 
-def run(lib, d, n, seed, mrw, gamma, nmin, want_sed, keep_j):
+def run(lib, d, n, seed, mrw, gamma, nmin, want_sed, keep_j, prec=64, mueller=None):
     op = d.opacity
     nc = d.nr * d.ntheta
     t, v, a = (np.zeros(nc, np.uint64) for _ in range(3))
-    sed = np.zeros(op.nlam * 10, np.uint64)
+    sed, q, u = (np.zeros(op.nlam * 10, np.uint64) for _ in range(3))
     j = np.zeros(nc * op.nlam) if keep_j else None
     cnt = np.zeros(8, np.uint64)
     arrs = [np.ascontiguousarray(x, np.float64) for x in
             (d.r_faces_cm, d.theta_faces, d.rho.ravel(), op.lam_edges_um, op.kappa_abs, op.kappa_sca, op.g)]
+    mu = None if mueller is None else np.ascontiguousarray(mueller, np.float64)
     P = lambda x: None if x is None else x.ctypes.data_as(C.c_void_p)
     lib.host_transport(C.c_int(d.nr), C.c_int(d.ntheta), P(arrs[0]), P(arrs[1]), P(arrs[2]), C.c_int(op.nlam),
                        P(arrs[3]), P(arrs[4]), P(arrs[5]), P(arrs[6]), C.c_double(d.star.T_K), C.c_double(d.star.R_cm),
                        C.c_uint64(n), C.c_uint64(seed), C.c_int(mrw), C.c_double(gamma), C.c_int(nmin),
-                       C.c_int(want_sed), P(t), P(v), P(a), P(sed), P(j), P(cnt))
-    out = dict(tally=t, visits=v, nabs=a, sed=sed, counters=cnt)
+                       C.c_int(want_sed), C.c_int(prec), C.c_int(0 if mu is None else mu.shape[-1]), P(mu),
+                       P(t), P(v), P(a), P(sed), P(q), P(u), P(j), P(cnt))
+    out = dict(tally=t, visits=v, nabs=a, sed=sed, counters=cnt, sed_q=q.view(np.int64), sed_u=u.view(np.int64))
     if keep_j:  # path lengths (internal units, l = r_in) -> J = E_pkt * length / (4 pi V)
         rf, tf = d.r_faces_cm, d.theta_faces
         V = (2 * np.pi / 3) * np.diff(rf ** 3)[:, None] * (np.cos(tf[:-1]) - np.cos(tf[1:]))[None, :]
         out["J"] = (d.star.L / n) * j.reshape(d.nr, d.ntheta, op.nlam) * rf[0] / (4 * np.pi * V[:, :, None])
-        out["V"] = V
     return out
+
+
+def counters_of(stats):
+    return [stats[k] for k in ("packets", "absorptions", "scatterings", "crossings", "mrw_jumps", "capped", "escaped",
+                               "error_flags")]
+
+
+def _scatter_disk(tau, albedo, nlam=4):
+    op = disks.gray_opacity(nlam=nlam, albedo=albedo)
+    return disks.make_disk(disks.log_r_faces(0.1, 100.0, 16), disks.midplane_refined_theta_faces(16),
+                           disks.paper_star(), op, tau, h1_au=0.2, p=1.0, name="scatter")
 
 
 def test_gray_mrw_transport_and_mean_intensity_match_oracle(lib, oracle):
@@ -65,10 +78,7 @@ def test_gray_mrw_transport_and_mean_intensity_match_oracle(lib, oracle):
     n = 2000
     h = run(lib, d, n, seed=3, mrw=1, gamma=2.0, nmin=20, want_sed=0, keep_j=1)
     ref = oracle.Run(d).run(n, seed=3, mrw=True, gamma=2.0, want_sed=False, want_j=True)
-    st = ref.stats
-    want = [st[k] for k in ("packets", "absorptions", "scatterings", "crossings", "mrw_jumps", "capped", "escaped",
-                            "error_flags")]
-    assert [int(x) for x in h["counters"]] == want and st["mrw_jumps"] > 1000
+    assert [int(x) for x in h["counters"]] == counters_of(ref.stats) and ref.stats["mrw_jumps"] > 1000
     assert np.array_equal(h["visits"], ref.visits) and np.array_equal(h["nabs"], ref.nabs)
     m = ref.tally > 0
     assert np.array_equal(h["tally"] > 0, m)
@@ -106,3 +116,38 @@ def test_nongray_mean_intensity_balances_absorption(lib, oracle):
         assert abs(absorbed / emitted - 1) < 4 * math.sqrt(nabs[i, j]) / units[i, j] + 2e-3, (i, j)
         n_mrw_cells += nabs[i, j] < 0.6 * units[i, j]
     assert n_mrw_cells >= 2
+
+
+def test_fp64_polarized_transport_matches_oracle(lib, oracle):
+    """tau_mid = 3 gray disk, albedo 0.7, Rayleigh matrix, MRW: the oracle's events and integer tallies
+    exactly; Stokes Q and U per inclination bin (summed over wavelength) within three fixed-point units."""
+    d = _scatter_disk(3.0, 0.7)
+    mu = disks.rayleigh_mueller(4, 181)
+    n = 20_000
+    h = run(lib, d, n, seed=3, mrw=1, gamma=2.0, nmin=5, want_sed=1, keep_j=0, mueller=mu)
+    ref = oracle.Run(d, mueller=mu).run(n, seed=3, mrw=True, gamma=2.0, nmin=5)
+    assert [int(x) for x in h["counters"]] == counters_of(ref.stats) and ref.stats["scatterings"] > 2000
+    for k in ("tally", "visits", "nabs"):
+        assert np.array_equal(h[k], getattr(ref, k)), k
+    Q, U = (h[k].reshape(4, 10).sum(axis=0) for k in ("sed_q", "sed_u"))
+    Qo, Uo = (getattr(ref, k).reshape(4, 10).sum(axis=0) for k in ("sed_q", "sed_u"))
+    assert np.all(np.abs(Q - Qo) <= 3) and np.all(np.abs(U - Uo) <= 3) and np.abs(Qo).max() > 1000
+
+
+def test_fp32_thin_disk_polarization_matches_oracle(lib, oracle):
+    """FP32 polarized transport of the optically thin Rayleigh-scattering disk (albedo 0.9999, h/r = 0.2,
+    midplane optical depth 0.05): Q/I per inclination bin within four Monte Carlo errors of the oracle's
+    (independent seeds), U/I consistent with zero, Q/I positive and largest edge-on."""
+    d = _scatter_disk(0.05, 0.9999)
+    mu = disks.rayleigh_mueller(4, 181)
+    n = 1_000_000
+    h = run(lib, d, n, seed=12, mrw=0, gamma=2.0, nmin=20, want_sed=1, keep_j=0, prec=32, mueller=mu)
+    assert int(h["counters"][6]) == n and int(h["counters"][7]) == 0
+    ref = oracle.Run(d, mueller=mu).run(n, seed=11)
+    I, Q, U = (h[k].reshape(4, 10).sum(axis=0).astype(float) for k in ("sed", "sed_q", "sed_u"))
+    Q, U = Q / 2 ** 20, U / 2 ** 20
+    Io, Qo = ref.sed.reshape(4, 10).sum(axis=0).astype(float), ref.sed_q.reshape(4, 10).sum(axis=0) / 2 ** 20
+    sig = math.sqrt(2 * 0.5 * ref.stats["scatterings"] / 10) / (n / 10)  # two runs, per bin
+    assert np.all(np.abs(Q / I - Qo / Io) < 4 * sig), (Q / I, Qo / Io, sig)
+    assert np.all(np.abs(U / I) < 4 * sig)
+    assert Q[0] > 0 and Q[0] / I[0] > Q[9] / I[9]
