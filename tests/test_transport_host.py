@@ -97,10 +97,11 @@ def test_gray_mrw_transport_and_mean_intensity_match_oracle(lib, oracle):
         assert np.array_equal(h[k], h2[k]), k
 
 
-def test_nongray_mean_intensity_balances_absorption(lib, oracle):
+@pytest.mark.parametrize("prec", [64, 32])
+def test_nongray_mean_intensity_balances_absorption(lib, oracle, prec):
     d = disks.config_nongray(16, 16, 1e4)
     n = 300_000
-    h = run(lib, d, n, seed=8, mrw=1, gamma=2.0, nmin=5, want_sed=1, keep_j=1)
+    h = run(lib, d, n, seed=8, mrw=1, gamma=2.0, nmin=5, want_sed=1, keep_j=1, prec=prec)
     assert int(h["counters"][4]) > 10_000 and int(h["counters"][7]) == 0
     r = oracle.Run(d)
     r.tally[:] = h["tally"]
