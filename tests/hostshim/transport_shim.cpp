@@ -112,6 +112,7 @@ struct Inputs {
   int mrw, nmin, want_sed, nmu;
   double gamma;
   const double* mueller;  // [nlam][4][nmu] or NULL
+  const double* Lsrc;     // internal sources: luminosity per cell (erg/s), or NULL
 };
 
 struct Outputs {
@@ -144,6 +145,12 @@ void run(const Inputs& in, const Outputs& out) {
   for (int b = 1; b < nlam; ++b)
     if (in.kabs[b] != in.kabs[0] || in.ksca[b] != in.ksca[0] || in.g[b] != in.g[0]) gray = false;
   std::vector<unsigned long long> cnt(C_NCNT, 0ull);
+  // internal sources as mcrt_set_sources keeps them: cumulative luminosity in cell order
+  const size_t ncell = (size_t)nr * nt;
+  std::vector<double> src_cum(ncell + 1, 0.0);
+  if (in.Lsrc)
+    for (size_t c = 0; c < ncell; ++c) src_cum[c + 1] = src_cum[c] + in.Lsrc[c];
+  const double Lsrc = src_cum[ncell];
   const std::vector<R> rf = cast<R>(geo.rf), rf2 = cast<R>(geo.rf2), c2 = cast<R>(geo.c2), s2 = cast<R>(geo.s2),
                        cf = cast<R>(geo.cf), sf = cast<R>(geo.sf), rho = cast<R>(den.rhol), chi = cast<R>(dust.chi),
                        alb = cast<R>(dust.alb), g = cast<R>(gq), star = cast<R>(dust.star), mtr = cast<R>(mt),
@@ -181,9 +188,11 @@ void run(const Inputs& in, const Outputs& out) {
   M.kbar = tt.kbark.data();
   M.lqm = den.lqm.data();
   const double Lstar = 4.0 * kPi * in.Rstar * in.Rstar * MCRT_SIGMA * std::pow(in.Tstar, 4);
-  M.lq_run = (float)std::log(Lstar / ((double)in.n * (double)kEUnit));
+  M.lq_run = (float)std::log((Lstar + Lsrc) / ((double)in.n * (double)kEUnit));
+  M.src_cum = Lsrc > 0 ? src_cum.data() : nullptr;
   M.src_Lstar = Lstar;
-  M.src_Ltot = Lstar;
+  M.src_Ltot = Lstar + Lsrc;
+  M.n_src = Lsrc > 0 ? (int)ncell : 0;
   M.mtab = in.mueller ? mtr.data() : nullptr;
   M.mcdf = in.mueller ? mcr.data() : nullptr;
   M.nmu = in.mueller ? in.nmu : 0;
@@ -237,18 +246,19 @@ void run(const Inputs& in, const Outputs& out) {
 
 // Transports packets 0 .. n-1 with Philox key `seed` through the disk (cgs inputs, as mcrt_disk_create and
 // mcrt_set_opacity take them), in FP32 (prec 32) or FP64, polarized with a Mueller matrix [nlam][4][nmu]
-// (NULL: unpolarized), keeping the mean-intensity path lengths when jlen is given (nr*nt*nlam, internal
+// (NULL: unpolarized), with internal sources Lsrc per cell (erg/s; NULL: none), keeping the mean-intensity path lengths when jlen is given (nr*nt*nlam, internal
 // length units; not with a Mueller matrix). Returns the tallies (nr*nt: fixed-point energy, entries,
 // absorptions), the escape counts and Stokes Q/I, U/I tallies (nlam * 10) and the counters {packets,
 // absorptions, scatterings, crossings, MRW jumps, capped, escaped, error flags}.
 extern "C" void host_transport(int nr, int nt, const double* rf_cm, const double* tf, const double* rho, int nlam,
                                const double* lam_e, const double* kabs, const double* ksca, const double* g,
                                double Tstar, double Rstar, uint64_t n, uint64_t seed, int mrw, double gamma, int nmin,
-                               int want_sed, int prec, int nmu, const double* mueller, uint64_t* tally,
+                               int want_sed, int prec, int nmu, const double* mueller, const double* Lsrc,
+                               uint64_t* tally,
                                uint64_t* visits, uint64_t* nabs, uint64_t* sed, uint64_t* sed_q, uint64_t* sed_u,
                                double* jlen, uint64_t* counters) {
   const Inputs in{nr, nt, nlam, rf_cm, tf, rho, lam_e, kabs, ksca, g, Tstar, Rstar, n, seed, mrw, nmin, want_sed, nmu,
-                  gamma, mueller};
+                  gamma, mueller, Lsrc};
   const Outputs out{tally, visits, nabs, sed, sed_q, sed_u, counters, jlen};
   if (prec == 32) run<float>(in, out);
   else run<double>(in, out);
