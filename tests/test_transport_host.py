@@ -180,3 +180,15 @@ def test_internal_sources_with_mean_intensity_match_oracle(lib, oracle):
     tot, toto = h["J"].sum(axis=2), ref.mean_intensity().sum(axis=2)
     assert np.array_equal(tot > 0, toto > 0)
     assert np.max(np.abs(tot[toto > 0] / toto[toto > 0] - 1)) < 1e-5
+
+
+@pytest.mark.parametrize("prec", [64, 32])
+def test_j_tally_leaves_transport_unchanged_with_sed(lib, prec):
+    """With the escape spectrum wanted, the J tally makes gray packets draw their bin at every event
+    instead of once at escape; the transport itself (tallies, entries, absorptions, counters) is the same."""
+    d = disks.config_thick_gray(30, 20, 1e4)
+    a = run(lib, d, 1000, seed=4, mrw=1, gamma=2.0, nmin=20, want_sed=1, keep_j=0, prec=prec)
+    b = run(lib, d, 1000, seed=4, mrw=1, gamma=2.0, nmin=20, want_sed=1, keep_j=1, prec=prec)
+    assert int(a["counters"][4]) > 500
+    for k in ("tally", "visits", "nabs", "counters"):
+        assert np.array_equal(a[k], b[k]), k
