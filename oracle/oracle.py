@@ -453,7 +453,7 @@ def conductances(disk, D, part=None):
     zero where either cell does not take part (no dust, or `part` False)."""
     hr_in, hr_out, ht_lo, ht_hi = half_resistances(disk.r_faces_cm, disk.theta_faces)
     dust = (disk.rho > 0) if part is None else part
-    with np.errstate(divide="ignore", invalid="ignore"):
+    with np.errstate(divide="ignore", invalid="ignore", over="ignore"):  # D -> 0: no conductance
         Cr = 1.0 / (hr_out[:-1] / D[:-1] + hr_in[1:] / D[1:])
         Ct = 1.0 / (ht_hi[:, :-1] / D[:, :-1] + ht_lo[:, 1:] / D[:, 1:])
     Cr = np.where(dust[:-1] & dust[1:], Cr, 0.0)
