@@ -13,14 +13,13 @@
 #include <cmath>
 #include <vector>
 
+#include "hydro.cuh"
 #include "internal.h"
 
 namespace mcrt {
 namespace {
 
-constexpr double kG = 6.67430e-8;          // cm^3 g^-1 s^-2
-constexpr double kKB = 1.380649e-16;       // erg / K
-constexpr double kMU = 1.66053906660e-24;  // g
+constexpr double kG = 6.67430e-8;  // cm^3 g^-1 s^-2
 
 __global__ void k_hydro(int nr, int nt, const double* __restrict__ rf, const double* __restrict__ tf,
                         const double* __restrict__ T, const double* __restrict__ rho_cur,
@@ -28,43 +27,7 @@ __global__ void k_hydro(int nr, int nt, const double* __restrict__ rf, const dou
                         double* __restrict__ rho_out) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= nr) return;
-  const double rc = 0.5 * (rf[i] + rf[i + 1]);
-  const size_t row = (size_t)i * nt;
-  double phi = 0.0, a_prev = 0.0, z_prev = 0.0, lgmax = -INFINITY;
-  bool any = false;
-  for (int j = 0; j < nt; ++j) {
-    const double th = 0.5 * (tf[j] + tf[j + 1]);
-    const double z = rc * cos(th), R = rc * sin(th);
-    const double Tc = fmax(T[row + j], T_floor);
-    const double a = GM * z / (R * R * R) * (mu * kMU / (kKB * Tc));  // G M z / (R^3 c^2)
-    if (j > 0) phi = phi - 0.5 * (a + a_prev) * (z - z_prev);
-    a_prev = a;
-    z_prev = z;
-    const double lg = phi - log(Tc);
-    rho_out[row + j] = lg;
-    if (rho_cur[row + j] > 0.0) {
-      any = true;
-      lgmax = fmax(lgmax, lg);
-    }
-  }
-  const double M = shell_mass[i];
-  if (!any || !(M > 0.0)) {
-    for (int j = 0; j < nt; ++j) rho_out[row + j] = 0.0;
-    return;
-  }
-  const double r1 = rf[i], r2 = rf[i + 1];
-  const double sh = 2.0 * kPi / 3.0 * (r2 * r2 * r2 - r1 * r1 * r1);
-  double sum = 0.0;
-  for (int j = 0; j < nt; ++j) {
-    double p = 0.0;
-    if (rho_cur[row + j] > 0.0) {
-      p = exp(rho_out[row + j] - lgmax);
-      sum += p * (sh * (cos(tf[j]) - cos(tf[j + 1])));
-    }
-    rho_out[row + j] = p;
-  }
-  const double s = M / sum;
-  for (int j = 0; j < nt; ++j) rho_out[row + j] *= s;
+  hydro_shell(i, nt, rf, tf, T, rho_cur, shell_mass, GM, mu, T_floor, rho_out);
 }
 
 }  // namespace

@@ -1,0 +1,52 @@
+"""The hydrostatic kernel's column sweep (hydro.cuh: hydro_shell, Sect. 2.5, Eq. 20; host and device code)
+compiled for the host and compared with the oracle's hydrostatic density on a seeded temperature field
+with cells below the floor and dust-free cells: the same density to 1e-12 (relative, where it is above
+1e-200 of the maximum), dust-free cells empty, every shell's mass kept."""
+import ctypes as C
+import os
+import shutil
+import subprocess
+
+import numpy as np
+import pytest
+
+from paper_0902_3092_gb300 import disks
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+G_CGS = 6.67430e-8
+
+
+@pytest.fixture(scope="module")
+def lib(tmp_path_factory):
+    nvcc = shutil.which("nvcc") or "/usr/local/cuda/bin/nvcc"
+    if not os.path.exists(nvcc):
+        pytest.skip("nvcc not found")
+    out = tmp_path_factory.mktemp("hydro") / "libhydro.so"
+    subprocess.check_call([nvcc, "-O2", "-std=c++17", "-Xcompiler", "-fPIC", "-shared",
+                           "-I", os.path.join(ROOT, "include"), "-I", os.path.join(ROOT, "paper_0902_3092_gb300", "csrc"),
+                           os.path.join(ROOT, "tests", "hostshim", "hydro_shim.cu"), "-o", str(out)])
+    return C.CDLL(str(out))
+
+
+def test_hydro_shell_matches_oracle(lib):
+    from oracle import hydro as H
+    d = disks.config_thick_gray(40, 30, 1e4)
+    rho = d.rho.copy()
+    rho[5, :4] = 0.0  # dust-free cells inside a shell
+    rng = np.random.default_rng(3)
+    rc = 0.5 * (d.r_faces_cm[1:] + d.r_faces_cm[:-1])
+    T = 300.0 * (rc[:, None] / disks.AU_CM) ** -0.5 * np.exp(0.3 * rng.standard_normal(rho.shape))
+    T[rng.random(rho.shape) < 0.1] = 0.0  # no packet: raised to the floor
+    shell = H.shell_masses(d.r_faces_cm, d.theta_faces, rho)
+    Ms = 2.5 * H.M_SUN
+    want = H.hydrostatic_density(d.r_faces_cm, d.theta_faces, rho > 0, T, shell, M_star=Ms, mu=2.3, T_floor=10.0)
+    P = lambda a: np.ascontiguousarray(a, np.float64).ctypes.data_as(C.c_void_p)
+    got = np.zeros(rho.size)
+    lib.host_hydro(d.nr, d.ntheta, P(d.r_faces_cm), P(d.theta_faces), P(T.ravel()), P(rho.ravel()), P(shell),
+                   C.c_double(G_CGS * Ms), C.c_double(2.3), C.c_double(10.0), P(got))
+    got = got.reshape(rho.shape)
+    assert np.all(got[rho == 0] == 0)
+    big = want > 1e-200 * want.max()
+    assert big.sum() > 500
+    assert np.max(np.abs(got[big] / want[big] - 1)) < 1e-12
+    assert np.allclose(H.shell_masses(d.r_faces_cm, d.theta_faces, got), shell, rtol=1e-12, atol=0)
