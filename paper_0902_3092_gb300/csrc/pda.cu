@@ -123,21 +123,6 @@ __global__ void k_bnd_mean(int nr, int nt, const signed char* mask, const double
   }
 }
 
-// Rosseland mean of chi' = kappa + (1-g) sigma at T (Eq. 3 with Eq. 16), exact bin integrals
-__device__ double rosseland(const double* lam_e, const double* chip, int nlam, double T) {
-  double g4p = 0.0, s1 = 0.0, s2 = 0.0;
-  for (int b = 0; b < nlam; ++b) {
-    double g3, g4;
-    if (b + 1 == nlam) tails(0.0, g3, g4);
-    else tails(kH * kC / (lam_e[b + 1] * 1e-4 * kKB * T), g3, g4);
-    const double db = g4 - g4p;
-    s1 += db;
-    s2 += db / chip[b];
-    g4p = g4;
-  }
-  return s1 / s2;
-}
-
 // Rosseland extinction of the cells whose D enters a conductance (PDA cells and their dusty
 // neighbours); the others get a placeholder (their D takes part in no face)
 __global__ void k_kappaR(int nr, int nt, const signed char* mask, const double* rho, const unsigned long long* tally,

@@ -118,4 +118,19 @@ __host__ __device__ inline void planck_bins(const double* lam_e, int nlam, doubl
   }
 }
 
+// Rosseland mean of chi' = kappa + (1-g) sigma at T (Eq. 3 with Eq. 16), exact bin integrals
+__host__ __device__ inline double rosseland(const double* lam_e, const double* chip, int nlam, double T) {
+  double g4p = 0.0, s1 = 0.0, s2 = 0.0;
+  for (int b = 0; b < nlam; ++b) {
+    double g3, g4;
+    if (b + 1 == nlam) tails(0.0, g3, g4);
+    else tails(kH * kC / (lam_e[b + 1] * 1e-4 * kKB * T), g3, g4);
+    const double db = g4 - g4p;
+    s1 += db;
+    s2 += db / chip[b];
+    g4p = g4;
+  }
+  return s1 / s2;
+}
+
 }  // namespace mcrt

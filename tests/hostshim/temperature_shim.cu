@@ -1,5 +1,6 @@
 // Host build of the temperature kernel's per-cell solve (temperature.cuh: q_sum, cell_temperature) over
-// the library's temperature-grid tables (tables.h), for a CPU test against the oracle.
+// the library's temperature-grid tables (tables.h), and the Rosseland mean the PDA kernels read
+// (planck.cuh: rosseland), for CPU tests against the oracle.
 #include <algorithm>
 #include <vector>
 
@@ -22,4 +23,9 @@ extern "C" void host_temperatures(int nlam, const double* lam_e, const double* k
   for (int i = 0; i < n; ++i)
     T[i] = mcrt::cell_temperature(q[i], gray ? 1 : 0, kabs[0], nlam, lam_e, kabs, tt.lQ64.data(), tt.slQ64.data(), nT,
                                   Tmin, dlnT);
+}
+
+// Rosseland mean of chi' at each of the n temperatures (planck.cuh: rosseland, read by the PDA kernels)
+extern "C" void host_rosseland(int nlam, const double* lam_e, const double* chip, int n, const double* T, double* out) {
+  for (int i = 0; i < n; ++i) out[i] = mcrt::rosseland(lam_e, chip, nlam, T[i]);
 }

@@ -43,3 +43,18 @@ def test_cell_temperature_inverts_Q(lib, oracle, kind):
     assert np.max(np.abs(T / T_true - 1)) < 1e-10
     To = np.array([oracle.T_of_q(d, x) for x in q[::10]])
     assert np.max(np.abs(T[::10] / To - 1)) < 1e-10
+
+
+def test_rosseland_mean_matches_oracle(lib, oracle):
+    """The Rosseland mean of chi' that the PDA kernels compute per cell (planck.cuh: rosseland, Eq. 3 with
+    Eq. 16) against the oracle's, non-gray dust with anisotropic scattering, 1 K - 3e4 K: 1e-12."""
+    d = disks.config_nongray(8, 8, 100.0)
+    op = d.opacity
+    chip = np.ascontiguousarray(op.kappa_abs + (1.0 - op.g) * op.kappa_sca)
+    T = np.exp(np.linspace(0.0, math.log(3e4), 60))
+    P = lambda a: np.ascontiguousarray(a, np.float64).ctypes.data_as(C.c_void_p)
+    out = np.zeros(len(T))
+    lib.host_rosseland(op.nlam, P(op.lam_edges_um), P(chip), len(T), P(T), P(out))
+    ref = np.array([oracle.rosseland_chi(d, t) for t in T])
+    assert np.max(np.abs(out / ref - 1)) < 1e-12
+    assert not np.allclose(ref, ref[0])  # the mean does depend on T for this dust
