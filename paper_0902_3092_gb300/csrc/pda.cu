@@ -25,6 +25,7 @@
 #include <vector>
 
 #include "internal.h"
+#include "tables.h"
 #include "planck.cuh"
 
 namespace mcrt {
@@ -639,21 +640,9 @@ static mcrt_status pda_alloc(mcrt_disk* d, int max_inner) {
     P->nt = nt;
     P->n = n;
     // geometric half-cell resistances
-    std::vector<double> hi_(n), ho(n), tl(n), th(n), el(n);
-    for (int i = 0; i < nr; ++i) {
-      const double r1 = d->rf[i], r2 = d->rf[i + 1], rc = 0.5 * (r1 + r2);
-      for (int j = 0; j < nt; ++j) {
-        const double t1 = d->tf[j], t2 = d->tf[j + 1], tc = 0.5 * (t1 + t2);
-        const double om = 2.0 * kPi * (std::cos(t1) - std::cos(t2));
-        const size_t c = (size_t)i * nt + j;
-        hi_[c] = (1.0 / r1 - 1.0 / rc) / om;
-        ho[c] = (1.0 / rc - 1.0 / r2) / om;
-        const double ltc = std::log(std::tan(0.5 * tc));
-        tl[c] = (t1 > 0 ? ltc - std::log(std::tan(0.5 * t1)) : INFINITY) / (2.0 * kPi * (r2 - r1));
-        th[c] = (t2 < kPi ? std::log(std::tan(0.5 * t2)) - ltc : INFINITY) / (2.0 * kPi * (r2 - r1));
-        el[c] = std::min(r2 - r1, rc * (t2 - t1));
-      }
-    }
+    HalfResistances hr;
+    half_resistances(nr, nt, d->rf.data(), d->tf.data(), hr);
+    const std::vector<double>&hi_ = hr.hr_in, &ho = hr.hr_out, &tl = hr.ht_lo, &th = hr.ht_hi, &el = hr.ell;
     cudaError_t e = P->hr_in.alloc((size_t)n * 8);
     if (e == cudaSuccess) e = cudaMemcpy(P->hr_in.p, hi_.data(), (size_t)n * 8, cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = P->hr_out.alloc((size_t)n * 8);

@@ -3,6 +3,7 @@
 // escape-time table, and the sampling table of a Mueller matrix. Host code, compiled for the host in the
 // tests too.
 #pragma once
+#include <algorithm>
 #include <cmath>
 #include <vector>
 
@@ -141,6 +142,36 @@ inline void dust_arrays(int nlam, const double* lam_e, const double* kabs, const
   for (int b = 0; b < nlam; ++b) {
     acc += B[b];
     o.star[b] = acc;
+  }
+}
+
+// Geometric half-cell resistances of the PDA (Sect. 2.2.1; multiply by 1/D), per cell (cgs faces): from the
+// cell's centre to its inner / outer radial face, (1/a - 1/b) / Omega over the radial half [a, b] of solid
+// angle Omega, and to its lower / upper polar face, (ln tan(t2/2) - ln tan(t1/2)) / (2 pi (r2 - r1)) over
+// the polar half [t1, t2] (infinite towards the axis); ell: the cell's smallest extent, min(dr, r_c dtheta).
+struct HalfResistances {
+  std::vector<double> hr_in, hr_out, ht_lo, ht_hi, ell;
+};
+inline void half_resistances(int nr, int nt, const double* rf, const double* tf, HalfResistances& h) {
+  const size_t n = (size_t)nr * nt;
+  h.hr_in.resize(n);
+  h.hr_out.resize(n);
+  h.ht_lo.resize(n);
+  h.ht_hi.resize(n);
+  h.ell.resize(n);
+  for (int i = 0; i < nr; ++i) {
+    const double r1 = rf[i], r2 = rf[i + 1], rc = 0.5 * (r1 + r2);
+    for (int j = 0; j < nt; ++j) {
+      const double t1 = tf[j], t2 = tf[j + 1], tc = 0.5 * (t1 + t2);
+      const double om = 2.0 * kPi * (std::cos(t1) - std::cos(t2));
+      const size_t c = (size_t)i * nt + j;
+      h.hr_in[c] = (1.0 / r1 - 1.0 / rc) / om;
+      h.hr_out[c] = (1.0 / rc - 1.0 / r2) / om;
+      const double ltc = std::log(std::tan(0.5 * tc));
+      h.ht_lo[c] = (t1 > 0 ? ltc - std::log(std::tan(0.5 * t1)) : INFINITY) / (2.0 * kPi * (r2 - r1));
+      h.ht_hi[c] = (t2 < kPi ? std::log(std::tan(0.5 * t2)) - ltc : INFINITY) / (2.0 * kPi * (r2 - r1));
+      h.ell[c] = std::min(r2 - r1, rc * (t2 - t1));
+    }
   }
 }
 

@@ -25,3 +25,16 @@ extern "C" int mrw_table_host(float* tab, float* t0, float* dt) {
   *dt = mcrt::mrw_table_dt();
   return mcrt::kMrwTab;
 }
+
+// PDA half-cell resistances and cell extents (nr*nt each), as the PDA set-up builds them
+extern "C" void half_resistances_host(int nr, int nt, const double* rf, const double* tf, double* hr_in, double* hr_out,
+                                      double* ht_lo, double* ht_hi, double* ell) {
+  mcrt::HalfResistances h;
+  mcrt::half_resistances(nr, nt, rf, tf, h);
+  const size_t n = (size_t)nr * nt * sizeof(double);
+  std::memcpy(hr_in, h.hr_in.data(), n);
+  std::memcpy(hr_out, h.hr_out.data(), n);
+  std::memcpy(ht_lo, h.ht_lo.data(), n);
+  std::memcpy(ht_hi, h.ht_hi.data(), n);
+  std::memcpy(ell, h.ell.data(), n);
+}

@@ -97,3 +97,21 @@ def test_mrw_escape_time_table_matches_oracle(shim, oracle):
         xh = 1.0 / ((1 - frac) * hi[i] + frac * hi[i + 1])
         assert np.max(np.abs(xl / [oracle.mrw_x(x) for x in u] - 1)) < tol, frac
         assert np.max(np.abs(xh / [oracle.mrw_x(1 - x) for x in u] - 1)) < tol, frac
+
+
+def test_pda_half_resistances_match_oracle(shim, oracle):
+    """The PDA's geometric half-cell resistances (Sect. 2.2.1, exact for constant D) and cell extents on
+    the rim-refined 200 x 120 grid against the oracle's: 1e-12, except the faces on the polar axis, which
+    carry no flux (infinite in the library)."""
+    d = disks.config_thick_gray(200, 120, 1e6)
+    nr, nt = d.nr, d.ntheta
+    out = [np.zeros(nr * nt) for _ in range(5)]
+    P = lambda a: np.ascontiguousarray(a, np.float64).ctypes.data_as(C.c_void_p)
+    shim.half_resistances_host(nr, nt, P(d.r_faces_cm), P(d.theta_faces), *(P(x) for x in out))
+    hi, ho, tl, th, el = (x.reshape(nr, nt) for x in out)
+    ri, ro, rl, rh = oracle.half_resistances(d.r_faces_cm, d.theta_faces)
+    for got, want in ((hi, ri), (ho, ro), (tl[:, 1:], rl[:, 1:]), (th[:, :-1], rh[:, :-1])):
+        assert np.max(np.abs(got / want - 1)) < 1e-12
+    assert np.all(np.isinf(tl[:, 0])) and np.all(np.isinf(th[:, -1]))
+    ext = oracle.cell_extent(d)
+    assert np.max(np.abs(el / ext - 1)) < 1e-12
