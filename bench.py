@@ -592,11 +592,22 @@ def main():
         # the exchange of the Monte Carlo step: integer tallies summed over ranks (exact in int64)
         g.restore(D.allreduce_blob(g.checkpoint()))
 
+    guard_records = []
+
     def step(i):
         g.reset()
         first, _ = D.packet_range(rank, world, Np, i)
-        st = g.run_photons(Np, seed=1, first_id=first, n_total=Np * world, mrw=True,
-                           gamma=args.gamma, want_sed=True, max_events=int(args.max_events))
+        try:
+            st = g.run_photons(Np, seed=1, first_id=first, n_total=Np * world, mrw=True,
+                               gamma=args.gamma, want_sed=True, max_events=int(args.max_events))
+        except mcrt.McrtError as e:
+            # a step guard dropped packets: the call still completed (the dropped packets count as capped);
+            # keep its statistics and report the record of the first dropped packet
+            if e.status != 5 or not getattr(e, "stats", None):
+                raise
+            st = e.stats
+            guard_records.append({k: st[k] for k in ("guarded", "guard_packet", "guard_kind", "guard_in_tail",
+                                                      "guard_cell", "guard_pos_cm", "guard_dir")})
         combine()
         n_pda, iters = g.solve_pda(min_visits=min_visits)
         return st, n_pda, iters
@@ -697,7 +708,9 @@ def main():
                 "transport": {"kernel_ms_per_step": 1e3 * float(np.mean(tr_s)), "events": s0["events"],
                               "crossings": s0["crossings"], "mrw_jumps": s0["mrw_jumps"], "capped": s0["capped"],
                               "capped_fraction": s0["capped"] / Np, "max_packet_steps": s0["max_packet_steps"],
-                              "events_per_s": s0["events"] / s0["seconds"], "error_flags": s0["error_flags"]},
+                              "events_per_s": s0["events"] / s0["seconds"], "error_flags": s0["error_flags"],
+                              "guarded_packets": int(sum(s[0]["guarded"] for s in stats)),
+                              "guard_records": guard_records[:3]},
                 "pda": {"ms_per_step": float(np.mean(pda_ms)), "cells": stats[-1][1], "cg_iterations": stats[-1][2]},
                 "plain_mc": plain, "peaks_file": bool(peaks)}
         print(json.dumps(line), flush=True)

@@ -122,6 +122,17 @@ typedef struct {
   double seconds;       /* device time of the transport kernel(s) */
   uint64_t max_packet_steps;  /* interactions + jumps + face crossings of the longest packet */
   uint64_t longest_packet;    /* its packet id modulo 2^24 */
+  /* Step guards: a packet that takes more than 4 max_events_per_packet + 1e7 steps, or crosses 1e5
+   * faces without an interaction, is dropped (counted in `capped` and `guarded`, error_flags bit 2).
+   * The first one is recorded (single-disk runs) so that it can be replayed: */
+  uint64_t guarded;           /* packets dropped by a step guard */
+  uint64_t guard_packet;      /* full id of the first of them */
+  int32_t guard_kind;         /* 0 none, 1 step limit, 2 face crossings without an interaction */
+  int32_t guard_in_tail;      /* 1 if the tail kernel carried it */
+  int32_t guard_cell[2];      /* its cell (ir, itheta) when the guard fired; ir = -1: inner cavity */
+  uint64_t guard_events, guard_steps;  /* its interactions + jumps and its steps then */
+  double guard_pos_cm[3];     /* its position (cm) and direction then */
+  double guard_dir[3];
 } mcrt_run_stats;
 
 /* Transports packets first_packet_id .. first_packet_id+n_packets-1 (Sect. 2.1, 2.2.2): launch from

@@ -5,6 +5,7 @@
 #include <algorithm>
 #include <chrono>
 #include <cmath>
+#include <cstdio>
 #include <cstring>
 #include <mutex>
 #include <string>
@@ -407,7 +408,7 @@ mcrt_status mcrt_disk_create(const mcrt_grid* grid, const mcrt_star* star, int d
   e = d->tally.alloc(ncell * 8);
   if (e == cudaSuccess) e = d->visits.alloc(ncell * 8);
   if (e == cudaSuccess) e = d->nabs.alloc(ncell * 8);
-  if (e == cudaSuccess) e = d->cnt.alloc(C_NCNT * 8);
+  if (e == cudaSuccess) e = d->cnt.alloc((C_NCNT + kTripWords) * 8);  // run counters, then the guard record
   if (e == cudaSuccess) e = d->queue.alloc(8);
   if (e == cudaSuccess) e = d->T_mc.alloc(ncell * 8);
   if (e == cudaSuccess) e = d->relerr.alloc(ncell * 8);
@@ -555,6 +556,7 @@ static void fill_params(KParams<R>& P, const mcrt_run_opts* o, uint64_t seed, co
   P.tr_pos = nullptr;
   P.models = nullptr;
   P.nmodels = 1;
+  P.trip = nullptr;
 }
 
 static void stats_from(const unsigned long long* c, mcrt_run_stats* s, double secs) {
@@ -571,6 +573,31 @@ static void stats_from(const unsigned long long* c, mcrt_run_stats* s, double se
   s->seconds = secs;
   s->max_packet_steps = c[C_MAXSTEPS];
   s->longest_packet = c[C_LONGEST] & 0xffffffull;
+  s->guarded = c[C_GUARDS];
+  s->guard_packet = 0;
+  s->guard_kind = 0;
+  s->guard_in_tail = 0;
+  s->guard_cell[0] = s->guard_cell[1] = -1;
+  for (int i = 0; i < 3; ++i) s->guard_pos_cm[i] = s->guard_dir[i] = 0.0;
+  s->guard_events = s->guard_steps = 0;
+}
+
+// the record of the first packet dropped by a step guard (words of note_trip) into the run statistics
+static void trip_from(const unsigned long long* t, double l_unit, mcrt_run_stats* s) {
+  if (t[0] == 0) return;
+  double v[8];
+  std::memcpy(v, t + 8, sizeof(v));
+  s->guard_packet = t[1];
+  s->guard_kind = (int32_t)(t[2] & 255u);
+  s->guard_in_tail = (t[2] & 256u) ? 1 : 0;
+  s->guard_cell[0] = (int32_t)(long long)t[3];
+  s->guard_cell[1] = (int32_t)(long long)t[4];
+  s->guard_events = t[5];
+  s->guard_steps = t[6];
+  for (int i = 0; i < 3; ++i) {
+    s->guard_pos_cm[i] = v[i] * l_unit;
+    s->guard_dir[i] = v[3 + i];
+  }
 }
 
 // events = scatterings + absorptions + MRW jumps (the kernel counts the three separately)
@@ -617,7 +644,7 @@ static mcrt_status run_impl(mcrt_disk* d, uint64_t n_packets, uint64_t seed, uin
   if (pol && trace) return set_error(d, MCRT_EINVAL, "polarized transport has no event trace");
   if (jt && trace) return set_error(d, MCRT_EINVAL, "the mean-intensity tally has no event trace");
   if (jt && pol) return set_error(d, MCRT_EINVAL, "polarized transport does not keep the mean intensity");
-  CK(cudaMemsetAsync(d->cnt.p, 0, C_NCNT * 8, d->stream), "memset");
+  CK(cudaMemsetAsync(d->cnt.p, 0, (C_NCNT + kTripWords) * 8, d->stream), "memset");
   CK(cudaMemsetAsync(d->queue.p, 0, 8, d->stream), "memset");
   DBuf ttype, tcell, tlam, tpos, tn;
   if (trace) {
@@ -649,6 +676,7 @@ static mcrt_status run_impl(mcrt_disk* d, uint64_t n_packets, uint64_t seed, uin
       P.m0.model_id = 0;
       P.total = n_packets;
       P.queue = d->queue.as<unsigned long long>();
+      P.trip = d->cnt.as<unsigned long long>() + C_NCNT;
       P.want_lam = (!d->gray || o->want_sed) ? 1 : 0;
       if (trace) {
         P.trace_n = (int)n_packets;
@@ -687,6 +715,7 @@ static mcrt_status run_impl(mcrt_disk* d, uint64_t n_packets, uint64_t seed, uin
       P.m0.model_id = 0;
       P.total = n_packets;
       P.queue = d->queue.as<unsigned long long>();
+      P.trip = d->cnt.as<unsigned long long>() + C_NCNT;
       P.want_lam = (!d->gray || o->want_sed) ? 1 : 0;
       const int bps = pol  ? transport_blocks_per_sm_pol<float>(d->gray, block)
                       : jt ? transport_blocks_per_sm_j<float>(d->gray, block)
@@ -712,7 +741,7 @@ static mcrt_status run_impl(mcrt_disk* d, uint64_t n_packets, uint64_t seed, uin
     }
   }
   CK(cudaEventRecord(ev1, d->stream), "event");
-  unsigned long long c[C_NCNT];
+  unsigned long long c[C_NCNT + kTripWords];
   CK(cudaMemcpyAsync(c, d->cnt.p, sizeof(c), cudaMemcpyDeviceToHost, d->stream), "copy counters");
   if (trace) {
     const size_t m = (size_t)n_packets * trace_max;
@@ -732,9 +761,17 @@ static mcrt_status run_impl(mcrt_disk* d, uint64_t n_packets, uint64_t seed, uin
   d->packets_done += n_packets;
   d->have_T = false;
   d->have_pda = false;
-  if (stats) stats_from(c, stats, ms * 1e-3);
+  if (stats) {
+    stats_from(c, stats, ms * 1e-3);
+    trip_from(c + C_NCNT, d->l_unit, stats);
+  }
   if (!account_deposits(d, c)) return set_error(d, MCRT_EOVERFLOW, "fixed-point tally overflow");
-  if (c[C_ERR] & kErrStepGuard) return set_error(d, MCRT_ETIMEOUT, "packet step guard reached");
+  if (c[C_ERR] & kErrStepGuard) {
+    char msg[160];
+    std::snprintf(msg, sizeof msg, "packet step guard reached: %llu packet(s) dropped, the first packet id %llu",
+                  c[C_GUARDS], c[C_NCNT] ? c[C_NCNT + 1] : 0ull);
+    return set_error(d, MCRT_ETIMEOUT, msg);
+  }
   return MCRT_OK;
 }
 

@@ -165,6 +165,7 @@ enum CntIdx {
   C_PACKETS = 0, C_EVENTS, C_ABS, C_SCA, C_CROSS, C_MRW, C_CAPPED, C_ESCAPED, C_DEPSUM, C_ERR,
   C_MAXSTEPS,  // steps (interactions + jumps + crossings) of the longest packet
   C_LONGEST,   // (steps << 24) | (packet id & 0xffffff) of the longest packet
+  C_GUARDS,    // packets dropped by a step guard (also counted as capped)
   C_NCNT = 16
 };
 

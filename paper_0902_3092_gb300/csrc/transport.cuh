@@ -54,6 +54,8 @@ struct KParams {
   Pkt<R>* pool;                // one slot per thread of the launch: long packets from the front,
   unsigned* pool_ctr;          // the others from the back; [0] long, [1] others, [2] taken by the tail
   unsigned pool_cap;
+  // the first packet that a step guard drops (kTripWords words, word 0 claims it; NULL: not kept)
+  unsigned long long* trip;
   // debug trace (TRACE builds)
   int trace_n, trace_max;
   int32_t *tr_type, *tr_cell, *tr_lam, *tr_n;
@@ -153,6 +155,30 @@ struct WarpRng {
 // carries one packet in all its lanes
 template <class RNG>
 __device__ __forceinline__ bool lead() { return !RNG::coop || (threadIdx.x & 31u) == 0u; }
+
+// Record of the first packet dropped by a step guard: its full id, which guard, where it was and how it
+// was moving, so that the packet can be replayed. Words: 0 claim, 1 packet id, 2 guard (1: step limit,
+// 2: face crossings without an interaction) | 256 in the tail kernel, 3 ir, 4 itheta, 5 events, 6 steps,
+// 7 crossings since the last interaction, 8-13 position and direction (FP64 bits, internal units),
+// 14 optical depth left, 15 safety distance.
+constexpr int kTripWords = 16;
+template <class R, class RNG>
+__device__ __noinline__ void note_trip(const KParams<R>& P, const DevModel<R>& M, const Pkt<R>& s, unsigned kind) {
+  if (!lead<RNG>()) return;
+  atomicAdd(M.cnt + C_GUARDS, 1ull);
+  unsigned long long* t = P.trip;
+  if (!t || atomicCAS(t, 0ull, 1ull) != 0ull) return;
+  t[1] = ((unsigned long long)s.phi << 32) | s.plo;
+  t[2] = kind | (RNG::coop ? 256u : 0u);
+  t[3] = (unsigned long long)(long long)s.ir;
+  t[4] = (unsigned long long)(long long)s.it;
+  t[5] = s.events;
+  t[6] = s.steps;
+  t[7] = s.xcross;
+  const double v[8] = {(double)s.px, (double)s.py, (double)s.pz, (double)s.ux, (double)s.uy, (double)s.uz,
+                       (double)s.tau, (double)s.dsafe};
+  for (int i = 0; i < 8; ++i) t[8 + i] = (unsigned long long)__double_as_longlong(v[i]);
+}
 
 template <class R>
 __device__ __forceinline__ R uni(uint32_t w) { return to_uniform<R>(w); }
@@ -708,6 +734,7 @@ __device__ __forceinline__ int advance(const KParams<R>& P, RNG& rng, const DevM
   if (++s.steps > P.max_steps) {
     acc.err |= kErrStepGuard;
     acc.capped++;
+    note_trip<R, RNG>(P, M, s, 1u);
     return 0;
   }
   if (s.ir < 0) {  // inner cavity: straight to r_in
@@ -746,6 +773,14 @@ __device__ __forceinline__ int advance(const KParams<R>& P, RNG& rng, const DevM
       s.dsafe = dm;
     } else {
       s_face = next_face(M, s.ir, s.it, s.px, s.py, s.pz, s.ux, s.uy, s.uz, face);
+      if (sizeof(R) == 4 && s.xcross) {
+        // FP32: a crossing that follows another one moves at least 1e-6 of the radius (about 16 ulps of
+        // the position). A ray that grazes a face can otherwise step back and forth across it without
+        // moving: at a sphere the rounded p.u says "inward" while |p| rounds onto the face, so the face
+        // is met at distance 0 and the chord back out (2|p.u|) is below the position's resolution.
+        const R mv = (R)1e-6 * (fabs(s.px) + fabs(s.py) + fabs(s.pz));
+        s_face = s_face > mv ? s_face : mv;
+      }
       hit = s_int < s_face;
       s.dsafe = (R)0;
     }
@@ -763,6 +798,7 @@ __device__ __forceinline__ int advance(const KParams<R>& P, RNG& rng, const DevM
   if (++s.xcross > 100000u) {
     acc.err |= kErrStepGuard;
     acc.capped++;
+    note_trip<R, RNG>(P, M, s, 2u);
     return 0;
   }
   if (JT && alpha > (R)0) j_flight<R, RNG>(M, s.ir * M.nt + s.it, s.lam, s_face);

@@ -57,10 +57,17 @@ class RunStats(C.Structure):
                 ("scatterings", C.c_uint64), ("crossings", C.c_uint64), ("mrw_jumps", C.c_uint64),
                 ("capped", C.c_uint64), ("escaped", C.c_uint64), ("deposit_sum", C.c_uint64),
                 ("error_flags", C.c_uint32), ("seconds", C.c_double), ("max_packet_steps", C.c_uint64),
-                ("longest_packet", C.c_uint64)]
+                ("longest_packet", C.c_uint64), ("guarded", C.c_uint64), ("guard_packet", C.c_uint64),
+                ("guard_kind", C.c_int32), ("guard_in_tail", C.c_int32), ("guard_cell", C.c_int32 * 2),
+                ("guard_events", C.c_uint64), ("guard_steps", C.c_uint64), ("guard_pos_cm", C.c_double * 3),
+                ("guard_dir", C.c_double * 3)]
 
     def as_dict(self):
-        return {k: getattr(self, k) for k, _ in self._fields_}
+        out = {}
+        for k, _ in self._fields_:
+            v = getattr(self, k)
+            out[k] = list(v) if isinstance(v, C.Array) else v
+        return out
 
 
 class PdaOpts(C.Structure):
@@ -222,8 +229,12 @@ class Disk:
     def run_photons(self, n_packets, seed=1, first_id=0, **kw):
         o = run_opts(**kw)
         s = RunStats()
-        _check(lib().mcrt_run_photons(self._h, int(n_packets), int(seed), int(first_id), C.byref(o), C.byref(s)),
-               self._h)
+        try:
+            _check(lib().mcrt_run_photons(self._h, int(n_packets), int(seed), int(first_id), C.byref(o),
+                                          C.byref(s)), self._h)
+        except McrtError as e:
+            e.stats = s.as_dict()  # filled when the run completed (a step guard dropped packets)
+            raise
         return s.as_dict()
 
     def trace(self, n_packets, seed=1, first_id=0, max_events=1000, **kw):

@@ -66,6 +66,16 @@ inline unsigned long long atomicMax(unsigned long long* p, unsigned long long v)
   if (v > o) *p = v;
   return o;
 }
+inline unsigned long long atomicCAS(unsigned long long* p, unsigned long long cmp, unsigned long long v) {
+  const unsigned long long o = *p;
+  if (o == cmp) *p = v;
+  return o;
+}
+inline long long __double_as_longlong(double x) {
+  long long v;
+  std::memcpy(&v, &x, sizeof v);
+  return v;
+}
 template <class T>
 inline T __shfl_sync(unsigned, T v, int, int = 32) { return v; }
 template <class T>

@@ -36,12 +36,53 @@ struct Inputs {
   double gamma;
   const double* mueller;  // [nlam][4][nmu] or NULL
   const double* Lsrc;     // internal sources: luminosity per cell (erg/s), or NULL
+  // replay instead of packets: {ir, itheta, px, py, pz, ux, uy, uz, tau, xcross, max_calls} (positions in
+  // units of the inner radius; the values of the recorded state), or NULL
+  const double* replay;
 };
 
 struct Outputs {
   uint64_t *tally, *visits, *nabs, *sed, *sed_q, *sed_u, *counters;
   double* jlen;
+  int64_t* replay_out;  // {advance calls, face crossings, last result, error flags, ir, itheta}
 };
+
+// Moves one gray packet from a given state with advance() alone (no interaction is run): until it reaches
+// an interaction point, ends, or max_calls calls. This replays the geometry of a recorded state.
+template <class R, bool G>
+void replay_advance(const KParams<R>& P, const DevModel<R>& M, const double* st, int64_t* out) {
+  Pkt<R> s;
+  std::memset(&s, 0, sizeof(s));
+  s.ir = (int)st[0];
+  s.it = (int)st[1];
+  s.px = (R)st[2];
+  s.py = (R)st[3];
+  s.pz = (R)st[4];
+  s.ux = (R)st[5];
+  s.uy = (R)st[6];
+  s.uz = (R)st[7];
+  s.tau = (R)st[8];
+  s.xcross = (unsigned)st[9];
+  s.plo = 1u;
+  if (s.ir >= 0) set_alpha<R, G>(M, s);
+  SerialRng rng{{(uint32_t)P.seed, (uint32_t)(P.seed >> 32)}};
+  Acc acc;
+  std::memset(&acc, 0, sizeof(acc));
+  const int64_t max_calls = (int64_t)st[10];
+  int64_t calls = 0;
+  int r = 1;
+  while (calls < max_calls) {
+    r = advance<R, false, G, false, false>(P, rng, M, s, acc);
+    ++calls;
+    if (r != 1) break;
+  }
+  out[0] = calls;
+  out[1] = acc.cross;
+  out[2] = r;
+  out[3] = acc.err;
+  out[4] = s.ir;
+  out[5] = s.it;
+}
 
 // the model as the library builds it (make_model, fill_params), in precision R
 template <class R>
@@ -148,6 +189,11 @@ void run(const Inputs& in, const Outputs& out) {
   P.mrw_dt = mrw_table_dt();
   P.nmodels = 1;
 
+  if (in.replay) {
+    if (gray) replay_advance<R, true>(P, M, in.replay, out.replay_out);
+    else replay_advance<R, false>(P, M, in.replay, out.replay_out);
+    return;
+  }
   Acc acc;
   std::memset(&acc, 0, sizeof(acc));
   const bool pol = in.mueller != nullptr, jt = out.jlen != nullptr;
@@ -181,8 +227,24 @@ extern "C" void host_transport(int nr, int nt, const double* rf_cm, const double
                                uint64_t* visits, uint64_t* nabs, uint64_t* sed, uint64_t* sed_q, uint64_t* sed_u,
                                double* jlen, uint64_t* counters) {
   const Inputs in{nr, nt, nlam, rf_cm, tf, rho, lam_e, kabs, ksca, g, Tstar, Rstar, n, seed, mrw, nmin, want_sed, nmu,
-                  gamma, mueller, Lsrc};
-  const Outputs out{tally, visits, nabs, sed, sed_q, sed_u, counters, jlen};
+                  gamma, mueller, Lsrc, nullptr};
+  const Outputs out{tally, visits, nabs, sed, sed_q, sed_u, counters, jlen, nullptr};
   if (prec == 32) run<float>(in, out);
   else run<double>(in, out);
+}
+
+// Replays the geometry of one packet from a recorded state (see replay_advance) on the disk, FP32 (prec 32)
+// or FP64, with the kernels' step guards (1e5 crossings without an interaction). state: {ir, itheta, px, py,
+// pz, ux, uy, uz, tau, xcross, max_calls}; out: {advance calls, face crossings, last result (0 ended,
+// 1 crossed, 2 interaction point), error flags, ir, itheta}.
+extern "C" void host_replay(int nr, int nt, const double* rf_cm, const double* tf, const double* rho, int nlam,
+                            const double* lam_e, const double* kabs, const double* ksca, const double* g, double Tstar,
+                            double Rstar, int prec, const double* state, int64_t* out) {
+  const Inputs in{nr, nt, nlam, rf_cm, tf, rho, lam_e, kabs, ksca, g, Tstar, Rstar, 1, 1, 0, 20, 0, 0,
+                  2.0, nullptr, nullptr, state};
+  std::vector<uint64_t> t((size_t)nr * nt), v((size_t)nr * nt), a((size_t)nr * nt), sed((size_t)nlam * kNInc),
+      cnt(8);
+  const Outputs o{t.data(), v.data(), a.data(), sed.data(), nullptr, nullptr, cnt.data(), nullptr, out};
+  if (prec == 32) run<float>(in, o);
+  else run<double>(in, o);
 }

@@ -39,16 +39,18 @@ def test_struct_layouts_match_c(L, tmp_path):
 
     from paper_0902_3092_gb300 import mcrt
     prog = tmp_path / "sz.c"
-    prog.write_text('#include "mcrt.h"\n#include <stdio.h>\n#include <stddef.h>\nint main(void){printf("%zu %zu %zu %zu %zu %zu %zu %zu %zu\\n",'
+    prog.write_text('#include "mcrt.h"\n#include <stdio.h>\n#include <stddef.h>\nint main(void){printf("%zu %zu %zu %zu %zu %zu %zu %zu %zu %zu %zu\\n",'
                     'sizeof(mcrt_grid),sizeof(mcrt_star),sizeof(mcrt_run_opts),sizeof(mcrt_run_stats),sizeof(mcrt_pda_opts),'
                     'offsetof(mcrt_run_stats,seconds),offsetof(mcrt_pda_opts,kappa_R),sizeof(mcrt_hydro_opts),'
-                    'offsetof(mcrt_hydro_opts,shell_mass_g));return 0;}\n')
+                    'offsetof(mcrt_hydro_opts,shell_mass_g),offsetof(mcrt_run_stats,guard_cell),'
+                    'offsetof(mcrt_run_stats,guard_dir));return 0;}\n')
     exe = tmp_path / "sz"
     subprocess.check_call(["gcc", "-I", os.path.dirname(HEADER), str(prog), "-o", str(exe)])
     got = [int(x) for x in subprocess.check_output([str(exe)]).split()]
     want = [C.sizeof(mcrt.Grid), C.sizeof(mcrt.Star), C.sizeof(mcrt.RunOpts), C.sizeof(mcrt.RunStats),
             C.sizeof(mcrt.PdaOpts), mcrt.RunStats.seconds.offset, mcrt.PdaOpts.kappa_R.offset,
-            C.sizeof(mcrt.HydroOpts), mcrt.HydroOpts.shell_mass_g.offset]
+            C.sizeof(mcrt.HydroOpts), mcrt.HydroOpts.shell_mass_g.offset, mcrt.RunStats.guard_cell.offset,
+            mcrt.RunStats.guard_dir.offset]
     assert got == want
 
 

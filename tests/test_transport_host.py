@@ -13,6 +13,7 @@ sum_b kappa_b J_b = sum_b kappa_b Bbar_b(T), in every cell with 100 packet energ
 errors plus 2e-3. Polarized transport: FP64 equal to the oracle's events, tallies and (within three
 fixed-point units) Stokes sums; FP32 Q/I of a thin scattering disk within Monte Carlo errors."""
 import ctypes as C
+import dataclasses
 import math
 import os
 import shutil
@@ -192,3 +193,84 @@ def test_j_tally_leaves_transport_unchanged_with_sed(lib, prec):
     assert int(a["counters"][4]) > 500
     for k in ("tally", "visits", "nabs", "counters"):
         assert np.array_equal(a[k], b[k]), k
+
+
+# A packet of the 200x120 tau_mid = 1e6 benchmark disk (packet 1306294732 of the FP32 MRW run, seed 1) that
+# the GPU's step guard dropped after 1e5 face crossings without an interaction: recorded position (units of
+# the inner radius) and direction, FP32 values, in cell (0, 54). It lies on the inner sphere and moves along
+# it (p.u / r = +6e-9 exactly), but in FP32 p.u rounds to -2.4e-9 and |p|^2 to 1.
+TANGENT_STATE = dict(ir=0, it=54, p=(-0.874395668506622314453125, -0.4849975109100341796875, 0.01447851955890655517578125),
+                     u=(0.48418593406677246, -0.8740962147712708, -0.03898179531097412))
+
+
+def replay(lib, d, prec, state, tau=1.0, xcross=0, max_calls=300000):
+    op = d.opacity
+    arrs = [np.ascontiguousarray(x, np.float64) for x in
+            (d.r_faces_cm, d.theta_faces, d.rho.ravel(), op.lam_edges_um, op.kappa_abs, op.kappa_sca, op.g)]
+    st = np.array([state["ir"], state["it"], *state["p"], *state["u"], tau, xcross, max_calls], np.float64)
+    out = np.zeros(6, np.int64)
+    P = lambda x: x.ctypes.data_as(C.c_void_p)
+    lib.host_replay(C.c_int(d.nr), C.c_int(d.ntheta), P(arrs[0]), P(arrs[1]), P(arrs[2]), C.c_int(op.nlam),
+                    P(arrs[3]), P(arrs[4]), P(arrs[5]), P(arrs[6]), C.c_double(d.star.T_K), C.c_double(d.star.R_cm),
+                    C.c_int(prec), P(st), P(out))
+    return dict(calls=int(out[0]), crossings=int(out[1]), result=int(out[2]), err=int(out[3]), ir=int(out[4]),
+                it=int(out[5]))
+
+
+def test_tangent_packet_at_the_inner_radius_moves_on(lib):
+    """The recorded state of the dropped packet, replayed by the FP32 per-packet code: the rounded p.u and
+    |p| put the inner sphere at distance 0 and the chord through the cavity (2|p.u|) below the position's
+    resolution, so without a minimum move after a crossing the packet steps between cell 0 and the cavity
+    until the guard drops it. It must instead leave the face within a few crossings and reach its
+    interaction point in the dense rim cell, without a guard flag."""
+    f32 = lambda v: tuple(float(np.float32(x)) for x in v)
+    st = dict(TANGENT_STATE, p=f32(TANGENT_STATE["p"]), u=f32(TANGENT_STATE["u"]))
+    p, u = np.array(st["p"], np.float32), np.array(st["u"], np.float32)
+    b = np.float32(np.float32(p[0] * u[0] + p[1] * u[1]) + p[2] * u[2])
+    r2 = np.float32(np.float32(p[0] * p[0] + p[1] * p[1]) + p[2] * p[2])
+    assert b < 0 and r2 == np.float32(1.0)  # the rounding that the state was recorded with
+    d = disks.config_thick_gray(200, 120, 1e6)
+    r = replay(lib, d, 32, st)
+    assert r["err"] == 0 and r["crossings"] < 10 and r["result"] == 2, r
+    # the same ray with a little optical depth left: it ends in cell 0 or 1 next to the face, not in the cavity
+    assert r["ir"] in (0, 1), r
+
+
+def test_grazing_rays_at_spheres_and_cones_make_progress(lib):
+    """Rays started exactly on a face of the 200x120 disk and tangent to it (spheres at the rim, cones near the
+    midplane), FP32 per-packet code with no optical depth used up (tau = 1e30 in a dust-free disk): each must
+    leave the grid (a straight line meets each face at most twice), never stepping back and forth across the
+    face it grazes. (The FP64 debug path keeps the oracle's geometry operation by operation, and both accept
+    a root up to 1e-9 of the radius behind the packet as on the face, so an exactly tangent ray steps back
+    and forth there until the crossing guard drops it.)"""
+    prec = 32
+    d = disks.config_thick_gray(200, 120, 1e6)
+    d = dataclasses.replace(d, rho=np.zeros_like(d.rho))
+    rng = np.random.default_rng(5)
+    rf = d.r_faces_cm / d.r_faces_cm[0]
+    tf = d.theta_faces
+    bad = []
+    for k in range(400):
+        kind = k % 2
+        if kind == 0:  # on sphere ir (the inner face of cell ir), tangent
+            ir = int(rng.integers(0, 25))
+            it = int(rng.integers(40, 80))
+            th = tf[it] + rng.random() * (tf[it + 1] - tf[it])
+            ph = rng.random() * 2 * np.pi
+            n = np.array([np.sin(th) * np.cos(ph), np.sin(th) * np.sin(ph), np.cos(th)])
+            p = rf[ir] * n
+            t = np.cross(n, rng.normal(size=3))
+        else:  # on cone it (the lower face of cell it), tangent to the cone along its generator's normal
+            ir = int(rng.integers(0, 40))
+            it = int(rng.integers(50, 70))
+            r = rf[ir] + rng.random() * (rf[ir + 1] - rf[ir])
+            th, ph = tf[it], rng.random() * 2 * np.pi
+            p = r * np.array([np.sin(th) * np.cos(ph), np.sin(th) * np.sin(ph), np.cos(th)])
+            t = np.array([-np.sin(ph), np.cos(ph), 0.0])  # azimuthal: tangent to the cone
+            t = t + 0.01 * rng.normal() * p / np.linalg.norm(p)
+        t /= np.linalg.norm(t)
+        st = dict(ir=ir, it=it, p=tuple(p), u=tuple(t))
+        res = replay(lib, d, prec, st, tau=1e30, xcross=1, max_calls=5000)
+        if res["err"] or res["calls"] >= 5000 or res["result"] != 0:
+            bad.append((k, res))
+    assert not bad, bad[:5]
