@@ -44,6 +44,7 @@
  *                the BW bin, (w1, w2) direction, w3 tau)
  */
 #include <math.h>
+#include <pthread.h>
 #include <stdint.h>
 #include <stdlib.h>
 #include <string.h>
@@ -743,6 +744,7 @@ typedef struct {
   double *star_w;
   double *src_cum; /* nr*nt+1 cumulative source luminosity, or NULL */
   int pol;         /* Mueller matrix given: packets carry Stokes q, u, v and a reference vector */
+  int par;         /* packet-parallel run: other threads deposit into the same tallies */
 } ctx_t;
 
 static void trace(ctx_t *x, int tp, int *ntr, int type, int cell, const double p[3], int lam) {
@@ -785,12 +787,42 @@ static int exit_bin(ctx_t *x, double T, double xi) {
   return sample_bins(x->w, m->nlam, xi);
 }
 
-static void deposit(ctx_t *x, int c, uint64_t units, uint64_t *pkt_dep) {
+/* Adds `units` to the tally of cell c and returns the tally before it (in a packet-parallel run the
+ * addition is atomic, so the returned value is the one this deposit followed). */
+static uint64_t deposit(ctx_t *x, int c, uint64_t units, uint64_t *pkt_dep) {
   oracle_state *s = x->st;
-  uint64_t old = s->tally[c];
-  s->tally[c] = old + units;
-  if (s->tally[c] < old) s->cnt[CNT_ERR] |= 1u; /* overflow */
+  uint64_t old;
+  if (x->par) {
+    old = __atomic_fetch_add(&s->tally[c], units, __ATOMIC_RELAXED);
+  } else {
+    old = s->tally[c];
+    s->tally[c] = old + units;
+  }
+  if (old + units < old) s->cnt[CNT_ERR] |= 1u; /* overflow */
   *pkt_dep += units;
+  return old;
+}
+
+/* Temperatures of cell c before and after a deposit of `units` onto the tally value `before`: the cell's
+ * temperature follows its absorbed energy (Sect. 2.1). A serial run keeps the current temperature of every
+ * cell in Tcell; in a packet-parallel run the other threads move the tallies, so both are inverted from
+ * the tally values of this deposit. */
+static void cell_T_step(ctx_t *x, int c, uint64_t before, uint64_t units, double *Told, double *Tnew) {
+  oracle_state *s = x->st;
+  if (x->par) {
+    *Told = cell_T(x->m, c, before, x->n_total, x->Lpkt);
+    *Tnew = cell_T(x->m, c, before + units, x->n_total, x->Lpkt);
+  } else {
+    *Told = s->Tcell[c];
+    *Tnew = cell_T(x->m, c, s->tally[c], x->n_total, x->Lpkt);
+    s->Tcell[c] = *Tnew;
+  }
+}
+
+/* the current temperature of cell c */
+static double cell_T_now(ctx_t *x, int c) {
+  if (x->par) return cell_T(x->m, c, __atomic_load_n(&x->st->tally[c], __ATOMIC_RELAXED), x->n_total, x->Lpkt);
+  return x->st->Tcell[c];
 }
 
 /* The chain of MRW jumps from the packet's point in cell (ir, it) while Eq. 11 holds (Sect. 2.2.2). */
@@ -803,7 +835,7 @@ static void mrw_walk(ctx_t *x, or_rng *r, double p[3], double u[3], double e[3],
   for (;;) {
     if (*events >= o->max_events) break;
     double dmin = oracle_dmin(m, p, ir, it);
-    double T = fmax(s->Tcell[c], 1.0);
+    double T = fmax(cell_T_now(x, c), 1.0);
     double D, kbar;
     oracle_diffusion(m, T, m->rho[c], &D, &kbar);
     /* Eq. 11 with rho chi_R = 1/(3 D) */
@@ -833,8 +865,9 @@ static void mrw_walk(ctx_t *x, or_rng *r, double p[3], double u[3], double e[3],
     double E = ct * m->rho[c] * kbar;             /* Eq. 9, in packet energies */
     double units = floor(E * OR_EUNIT + 0.5);
     if (units >= 1.8e19) { s->cnt[CNT_ERR] |= 2u; units = 1.8e19; }
-    deposit(x, c, (uint64_t)units, dep);
-    s->Tcell[c] = cell_T(m, c, s->tally[c], x->n_total, x->Lpkt);
+    const uint64_t before = deposit(x, c, (uint64_t)units, dep);
+    double Tb, Ta; /* before and after the deposit */
+    cell_T_step(x, c, before, (uint64_t)units, &Tb, &Ta);
     double uh[3];
     iso_dir(ja[1], ja[2], uh);
     for (int d = 0; d < 3; ++d) p[d] += dmin * uh[d];
@@ -847,7 +880,7 @@ static void mrw_walk(ctx_t *x, or_rng *r, double p[3], double u[3], double e[3],
       iso_dir(jb[0], jb[1], u);
     }
     double xl = ja[3];
-    if (!x->gray || o->want_sed) *lam = exit_bin(x, s->Tcell[c], xl);
+    if (!x->gray || o->want_sed) *lam = exit_bin(x, Ta, xl);
     if (x->pol) { /* a diffusing packet leaves the sphere unpolarized */
       st[0] = st[1] = st[2] = 0.0;
       ref_perp(u, e);
@@ -900,11 +933,10 @@ static void run_packet(ctx_t *x, uint64_t k, uint64_t seed, uint32_t model, int 
       s->cnt[CNT_PACKETS]++;
       /* the release: an absorption with omega = 0 at that point */
       U4(&r, w);
-      deposit(x, c, (uint64_t)OR_EUNIT, &dep);
+      const uint64_t before = deposit(x, c, (uint64_t)OR_EUNIT, &dep);
       s->nabs[c]++;
-      double Told = s->Tcell[c];
-      double Tnew = cell_T(m, c, s->tally[c], x->n_total, x->Lpkt);
-      s->Tcell[c] = Tnew;
+      double Told, Tnew;
+      cell_T_step(x, c, before, (uint64_t)OR_EUNIT, &Told, &Tnew);
       if (!x->gray || o->want_sed) lam = bw_bin(x, Told, Tnew, w[0]);
       iso_dir(w[1], w[2], u);
       if (x->pol) ref_perp(u, e);
@@ -977,13 +1009,10 @@ static void run_packet(ctx_t *x, uint64_t k, uint64_t seed, uint32_t model, int 
         s->cnt[CNT_SCA]++;
         trace(x, tp, &ntr, EV_SCATTER, c, p, lam);
       } else {
-        uint64_t before = s->tally[c];
-        deposit(x, c, (uint64_t)OR_EUNIT, &dep);
+        const uint64_t before = deposit(x, c, (uint64_t)OR_EUNIT, &dep);
         s->nabs[c]++;
-        double Told = s->Tcell[c];
-        double Tnew = cell_T(m, c, s->tally[c], x->n_total, x->Lpkt);
-        (void)before;
-        s->Tcell[c] = Tnew;
+        double Told, Tnew;
+        cell_T_step(x, c, before, (uint64_t)OR_EUNIT, &Told, &Tnew);
         double xl = (w[0] - omega) / (1.0 - omega);
         if (!x->gray || o->want_sed) lam = bw_bin(x, Told, Tnew, xl);
         iso_dir(w[1], w[2], u);
@@ -1045,39 +1074,152 @@ static void run_packet(ctx_t *x, uint64_t k, uint64_t seed, uint32_t model, int 
 
 /* Run packets first_id .. first_id+n-1. n_total sets the packet energy Lstar/n_total.
  * The tallies and Tcell carry over between calls (resume). Returns 0. */
+static void ctx_init(ctx_t *x, const oracle_model *m, const oracle_opts *o, oracle_state *s, uint64_t n_total,
+                     int par) {
+  x->m = m;
+  x->o = o;
+  x->st = s;
+  x->gray = is_gray(m);
+  x->n_total = (double)n_total;
+  x->Lpkt = oracle_packet_lum(m);
+  x->pol = m->mueller != NULL && m->nmu >= 2 && s->sed_q != NULL && s->sed_u != NULL;
+  x->par = par;
+  x->src_cum = NULL;
+  if (m->Lsrc) {
+    const int n = m->nr * m->nt;
+    x->src_cum = (double *)malloc(sizeof(double) * (n + 1));
+    x->src_cum[0] = 0.0;
+    for (int c = 0; c < n; ++c) x->src_cum[c + 1] = x->src_cum[c] + m->Lsrc[c];
+    if (!(x->src_cum[n] > 0.0)) {
+      free(x->src_cum);
+      x->src_cum = NULL;
+    }
+  }
+  x->w = (double *)malloc(sizeof(double) * m->nlam);
+  x->w2 = (double *)malloc(sizeof(double) * m->nlam);
+  x->star_w = (double *)malloc(sizeof(double) * m->nlam);
+  oracle_planck_bins(m->lam_e, m->nlam, m->Tstar, x->star_w);
+}
+
+static void ctx_free(ctx_t *x) {
+  free(x->w);
+  free(x->w2);
+  free(x->star_w);
+  free(x->src_cum);
+}
+
 int oracle_run(const oracle_model *m, const oracle_opts *o, oracle_state *s, uint64_t n, uint64_t first_id,
                uint64_t n_total, uint64_t seed, uint32_t model) {
   ctx_t x;
-  x.m = m;
-  x.o = o;
-  x.st = s;
-  x.gray = is_gray(m);
-  x.n_total = (double)n_total;
-  x.Lpkt = oracle_packet_lum(m);
-  x.pol = m->mueller != NULL && m->nmu >= 2 && s->sed_q != NULL && s->sed_u != NULL;
-  x.src_cum = NULL;
-  if (m->Lsrc) {
-    const int n = m->nr * m->nt;
-    x.src_cum = (double *)malloc(sizeof(double) * (n + 1));
-    x.src_cum[0] = 0.0;
-    for (int c = 0; c < n; ++c) x.src_cum[c + 1] = x.src_cum[c] + m->Lsrc[c];
-    if (!(x.src_cum[n] > 0.0)) {
-      free(x.src_cum);
-      x.src_cum = NULL;
-    }
-  }
-  x.w = (double *)malloc(sizeof(double) * m->nlam);
-  x.w2 = (double *)malloc(sizeof(double) * m->nlam);
-  x.star_w = (double *)malloc(sizeof(double) * m->nlam);
-  oracle_planck_bins(m->lam_e, m->nlam, m->Tstar, x.star_w);
+  ctx_init(&x, m, o, s, n_total, 0);
   for (uint64_t i = 0; i < n; ++i) {
     int tp = (i < (uint64_t)s->trace_packets) ? (int)i : -1;
     run_packet(&x, first_id + i, seed, model, tp);
   }
-  free(x.w);
-  free(x.w2);
-  free(x.star_w);
-  free(x.src_cum);
+  ctx_free(&x);
+  return 0;
+}
+
+/* ------------------------------------------------------------------------- */
+/* Packet-parallel runs: the same packets on several host threads, for the    */
+/* CPU baseline's timing and for runs too long for one core. The threads take */
+/* chunks of packet ids from a shared counter; the energy tallies are shared  */
+/* and added to atomically (integers, so the sums do not depend on the order), */
+/* every other count is kept per thread and summed at the end. For gray dust  */
+/* the trajectories do not depend on the temperatures, so the tallies, counts */
+/* and escapes per inclination equal the serial run's bit for bit (only the   */
+/* wavelength bins drawn at re-emission follow the order of the deposits);    */
+/* for non-gray dust each re-emission sees the tally that its own deposit     */
+/* followed, which another thread may have moved since the serial order would */
+/* have it.                                                                   */
+/* ------------------------------------------------------------------------- */
+typedef struct {
+  const oracle_model *m;
+  const oracle_opts *o;
+  oracle_state st; /* this thread's counts; the tally pointer is the shared one */
+  uint64_t n, first_id, n_total, seed;
+  uint32_t model;
+  uint64_t *next;  /* shared: the next packet index to hand out */
+} par_job;
+
+#define OR_PAR_CHUNK 16
+
+static void *par_worker(void *arg) {
+  par_job *j = (par_job *)arg;
+  ctx_t x;
+  ctx_init(&x, j->m, j->o, &j->st, j->n_total, 1);
+  for (;;) {
+    const uint64_t i0 = __atomic_fetch_add(j->next, (uint64_t)OR_PAR_CHUNK, __ATOMIC_RELAXED);
+    if (i0 >= j->n) break;
+    const uint64_t i1 = i0 + OR_PAR_CHUNK < j->n ? i0 + OR_PAR_CHUNK : j->n;
+    for (uint64_t i = i0; i < i1; ++i) run_packet(&x, j->first_id + i, j->seed, j->model, -1);
+  }
+  ctx_free(&x);
+  return NULL;
+}
+
+/* oracle_run on `threads` host threads. No event trace or mean-intensity tally (returns -1 if asked). The
+ * cell temperatures Tcell are set from the final tallies, so that a serial run may continue. */
+int oracle_run_par(const oracle_model *m, const oracle_opts *o, oracle_state *s, uint64_t n, uint64_t first_id,
+                   uint64_t n_total, uint64_t seed, uint32_t model, int threads) {
+  if (threads < 1 || s->trace_packets > 0 || s->jtally) return -1;
+  const size_t nc = (size_t)m->nr * m->nt, ns = (size_t)m->nlam * OR_NINC;
+  par_job *jobs = (par_job *)calloc((size_t)threads, sizeof(par_job));
+  pthread_t *tid = (pthread_t *)calloc((size_t)threads, sizeof(pthread_t));
+  uint64_t next = 0;
+  for (int t = 0; t < threads; ++t) {
+    par_job *j = &jobs[t];
+    j->m = m;
+    j->o = o;
+    j->n = n;
+    j->first_id = first_id;
+    j->n_total = n_total;
+    j->seed = seed;
+    j->model = model;
+    j->next = &next;
+    j->st.tally = s->tally;
+    j->st.visits = (uint64_t *)calloc(nc, sizeof(uint64_t));
+    j->st.nabs = (uint64_t *)calloc(nc, sizeof(uint64_t));
+    j->st.sed = (uint64_t *)calloc(ns, sizeof(uint64_t));
+    j->st.sed_sca = s->sed_sca ? (uint64_t *)calloc(ns, sizeof(uint64_t)) : NULL;
+    j->st.sed_q = s->sed_q ? (int64_t *)calloc(ns, sizeof(int64_t)) : NULL;
+    j->st.sed_u = s->sed_u ? (int64_t *)calloc(ns, sizeof(int64_t)) : NULL;
+    j->st.Tcell = NULL;
+  }
+  int started = 0;
+  for (int t = 0; t < threads; ++t) {
+    if (pthread_create(&tid[t], NULL, par_worker, &jobs[t]) != 0) break;
+    ++started;
+  }
+  if (started == 0) par_worker(&jobs[0]); /* no thread could be started: run them here */
+  for (int t = 0; t < started; ++t) pthread_join(tid[t], NULL);
+  for (int t = 0; t < threads; ++t) {
+    par_job *j = &jobs[t];
+    for (size_t c = 0; c < nc; ++c) {
+      s->visits[c] += j->st.visits[c];
+      s->nabs[c] += j->st.nabs[c];
+    }
+    for (size_t k = 0; k < ns; ++k) {
+      s->sed[k] += j->st.sed[k];
+      if (s->sed_sca) s->sed_sca[k] += j->st.sed_sca[k];
+      if (s->sed_q) s->sed_q[k] += j->st.sed_q[k];
+      if (s->sed_u) s->sed_u[k] += j->st.sed_u[k];
+    }
+    for (int k = 0; k < 10; ++k) {
+      if (k == CNT_ERR) s->cnt[k] |= j->st.cnt[k];
+      else s->cnt[k] += j->st.cnt[k];
+    }
+    free(j->st.visits);
+    free(j->st.nabs);
+    free(j->st.sed);
+    free(j->st.sed_sca);
+    free(j->st.sed_q);
+    free(j->st.sed_u);
+  }
+  free(jobs);
+  free(tid);
+  const double Lpkt = oracle_packet_lum(m);
+  for (size_t c = 0; c < nc; ++c) s->Tcell[c] = cell_T(m, (int)c, s->tally[c], (double)n_total, Lpkt);
   return 0;
 }
 

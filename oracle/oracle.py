@@ -48,7 +48,7 @@ EV_NAMES = ["launch", "cross", "scatter", "absorb", "mrw", "escape", "capped"]
 def build(force: bool = False) -> str:
     """Compile the C oracle (plain gcc, no FP contraction so x86 and Arm agree)."""
     if force or not os.path.exists(LIB) or os.path.getmtime(LIB) < os.path.getmtime(SRC):
-        cmd = ["gcc", "-O2", "-std=c11", "-ffp-contract=off", "-fno-fast-math", "-fPIC", "-shared",
+        cmd = ["gcc", "-O2", "-std=c11", "-ffp-contract=off", "-fno-fast-math", "-fPIC", "-shared", "-pthread",
                "-o", LIB, SRC, "-lm"]
         subprocess.check_call(cmd)
     return LIB
@@ -105,6 +105,9 @@ def lib():
         L.oracle_run.restype = C.c_int
         L.oracle_run.argtypes = [C.POINTER(_Model), C.POINTER(_Opts), C.POINTER(_State), C.c_uint64, C.c_uint64,
                                  C.c_uint64, C.c_uint64, C.c_uint32]
+        L.oracle_run_par.restype = C.c_int
+        L.oracle_run_par.argtypes = [C.POINTER(_Model), C.POINTER(_Opts), C.POINTER(_State), C.c_uint64, C.c_uint64,
+                                     C.c_uint64, C.c_uint64, C.c_uint32, C.c_int]
         L.oracle_star_bin.restype = C.c_int; L.oracle_star_bin.argtypes = [C.POINTER(_Model), d]
         L.oracle_packet_lum.restype = d; L.oracle_packet_lum.argtypes = [C.POINTER(_Model)]
         L.oracle_pol_sample_theta.restype = d; L.oracle_pol_sample_theta.argtypes = [pd, C.c_int, d]
@@ -187,8 +190,11 @@ class Run:
 
     def run(self, n_packets, seed=1, first_id=0, n_total=None, mrw=False, gamma=2.0, nmin=20,
             max_events=10 ** 9, want_sed=True, mrw_exit_dir=0, model_id=0, trace_packets=0, trace_max=0,
-            want_j=False):
-        """want_j: keep the path-length estimator of the mean intensity (see mean_intensity)."""
+            want_j=False, threads=1):
+        """want_j: keep the path-length estimator of the mean intensity (see mean_intensity). threads > 1:
+        the packets on that many host threads (shared atomic energy tallies; no trace or J tally; gray
+        runs give the serial tallies, counts and escapes per inclination bit for bit, non-gray runs the
+        same method with the re-emission temperatures of each deposit's own tally value)."""
         L = lib()
         opts = _Opts(int(mrw), float(gamma), int(nmin), int(max_events), int(want_sed), int(mrw_exit_dir))
         st = _State()
@@ -214,8 +220,16 @@ class Run:
             st.tr_type, st.tr_cell, st.tr_lam = _ip(tr["type"]), _ip(tr["cell"]), _ip(tr["lam"])
             st.tr_n, st.tr_pos = _ip(tr["n"]), _dp(tr["pos"])
         n_total = n_packets if n_total is None else n_total
-        L.oracle_run(self.model.ptr, C.byref(opts), C.byref(st), int(n_packets), int(first_id), int(n_total),
-                     int(seed), int(model_id))
+        if threads > 1:
+            if trace_packets or self.jtally is not None:
+                raise ValueError("a packet-parallel run keeps no trace and no mean-intensity tally")
+            rc = L.oracle_run_par(self.model.ptr, C.byref(opts), C.byref(st), int(n_packets), int(first_id),
+                                  int(n_total), int(seed), int(model_id), int(threads))
+            if rc != 0:
+                raise RuntimeError("oracle_run_par failed")
+        else:
+            L.oracle_run(self.model.ptr, C.byref(opts), C.byref(st), int(n_packets), int(first_id), int(n_total),
+                         int(seed), int(model_id))
         self.counters = np.array([st.cnt[i] for i in range(10)], np.uint64)
         self.trace = tr
         self.n_total = n_total
