@@ -34,21 +34,70 @@ UNIT = "packets/s"
 WORKLOAD = "thick gray disk 200x120 rim-refined, tau_mid=1e6, albedo 0.5 isotropic, MRW gamma=2 + PDA"
 
 # Work per transport step (an interaction, an MRW jump or a face crossing) of one FP32 transport call on
-# this workload: ncu smsp__inst_executed.sum (warp instructions) of its two kernels (the persistent
-# transport kernel, and the tail kernel that finishes the packets in flight when the queue drains) over
-# a whole 1e8-packet call, divided by its steps (profiles/); thread instructions count the transport
-# kernel's active lanes and one lane per tail warp instruction (all 32 lanes of a tail warp carry one
-# packet). The kernels are bound by instruction issue (divergent, latency-bound integer/FP32 work, no
-# DRAM traffic), so the roofline is issue slots: 152 SMs x 4 schedulers x 1 warp instruction per clock
-# at 2070 MHz.
-WARP_INST_PER_STEP = 35.3
-THREAD_INST_PER_STEP = 311.0
-ISSUE_PEAK = 152 * 4 * 2070e6           # warp instructions / s
-THREAD_ISSUE_PEAK = 32 * ISSUE_PEAK     # thread instructions / s (all lanes busy)
-# DRAM bytes of one transport call (ncu dram__bytes_read.sum + dram__bytes_write.sum of its two kernels,
-# 1e7 packets of this workload): tables and tallies stay in L2; the tail kernel reads the ~1.2e5 packet
-# states stored at the drain (13 MB). Neither grows with the packet count.
-TRANSPORT_DRAM_BYTES = 1512704 + 20224 + 13437952 + 0
+# this workload, from the ncu counts of its two kernels (the persistent transport kernel, and the tail
+# kernel that finishes the packets in flight when the queue drains) on a 1e7-packet call: warp and thread
+# instructions (smsp__inst_executed.sum, smsp__thread_inst_executed.sum) and DRAM bytes per step. The
+# kernels are bound by instruction issue (divergent, latency-bound integer/FP32 work; tallies and tables
+# stay in L2), so the roofline is issue slots: 152 SMs x 4 schedulers x 1 warp instruction per clock. The
+# counts live in the profile summary written from that capture, so a kernel change without a new capture
+# leaves the roofline figures null.
+COUNTS_FILE = os.path.join(ROOT, "profiles", "transport_counts_thickgray_200x120.md")
+N_SMS, SCHEDULERS = 152, 4
+
+
+def transport_counts():
+    """Per-step counts of the profile summary: the indented `key: value` lines."""
+    out = {}
+    try:
+        with open(COUNTS_FILE) as f:
+            for ln in f:
+                if ln.startswith("    ") and ":" in ln:
+                    k, v = ln.strip().split(":", 1)
+                    try:
+                        out[k.strip()] = float(v)
+                    except ValueError:
+                        out[k.strip()] = v.strip()
+    except OSError:
+        pass
+    return out
+
+
+def transport_source_hash():
+    """Hash of the transport kernels' sources: counts taken from another version are not used."""
+    import hashlib
+    h = hashlib.sha256()
+    for f in ("common.cuh", "transport.cuh", "transport_f32.cu"):
+        with open(os.path.join(ROOT, "paper_0902_3092_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def transport_roofline(steps_per_launch, t_launch, clocks, peaks):
+    """Issue-slot roofline of one transport call (its two kernels): warp instructions per step from the
+    ncu counts x steps per launch / the launch's CUDA-event time, against 152 SMs x 4 schedulers x the
+    maximum SM clock; beside it the active-lane figure (thread instructions against 32 lanes per slot)."""
+    c = transport_counts()
+    mhz = clocks.get("sm_max_mhz") or peaks.get("sm_max_mhz") or 2070.0
+    peak = N_SMS * SCHEDULERS * mhz * 1e6
+    roof = {"bound": "alu", "unit": "warp-inst/s", "peak": peak, "achieved": None, "frac": None, "traffic": None,
+            "thread_inst_frac": None,
+            "kernel": "transport_kernel<float> + transport_tail_kernel<float> (one 1e8-packet transport call)",
+            "counts_file": os.path.relpath(COUNTS_FILE, ROOT)}
+    fresh = c.get("source_sha16") == transport_source_hash()
+    if not c or not fresh:
+        roof["note"] = "no ncu counts for the current transport kernels (their sources changed since the capture)"
+        return roof
+    wps, tps = c["warp_inst_per_step"], c["thread_inst_per_step"]
+    ach = wps * steps_per_launch / t_launch
+    roof.update({"achieved": ach, "frac": ach / peak,
+                 "thread_inst_frac": tps * steps_per_launch / t_launch / (32 * peak),
+                 "traffic": c.get("dram_bytes_per_launch"),
+                 "note": f"issue slots: {wps:.2f} warp instructions per transport step (ncu, both kernels, "
+                         f"{c.get('profiled_packets', '?')}-packet call) x {steps_per_launch:.4g} steps per launch / "
+                         f"{t_launch:.4g} s CUDA-event launch time; peak = 152 SMs x 4 schedulers x {mhz:g} MHz; "
+                         f"thread_inst_frac = {tps:.1f} thread instructions per step against 32 lanes per slot "
+                         "(the share of lanes doing work); traffic = DRAM bytes of one 1e8-packet call (ncu)"})
+    return roof
 
 
 def parse():
@@ -80,6 +129,11 @@ def parse():
                    help="instead of the transport step: packets released by viscous heating in the 200x120 disk")
     p.add_argument("--polarized", action="store_true",
                    help="instead of the transport step: polarized transport (Rayleigh Mueller matrix) vs unpolarized")
+    p.add_argument("--profile-transport", action="store_true",
+                   help="instead of the step: one transport call of --packets packets on the workload, its "
+                        "statistics as JSON (the program the ncu captures of the transport kernels run)")
+    p.add_argument("--no-accuracy", action="store_true", help="skip the equal-accuracy study")
+    p.add_argument("--cpu-threads", type=int, default=0, help="oracle threads (0: every host core)")
     p.add_argument("--pda-min-visits", type=int, default=0,
                    help="PDA visit threshold; 0 scales the paper's 30 entries at 1e5 packets with the packet count "
                         "(Sect. 3.1 uses 30000 for its 1e8-packet runs)")
@@ -162,17 +216,22 @@ def measured_peaks():
         return {}
 
 
-def cpu_baseline(d, gamma, budget_s, max_events):
-    """The FP64 oracle as it stands, one host core: MRW transport of a bounded packet sample of the same
-    disk, then its PDA solve; value = sample packets / transport seconds."""
+def host_threads(args):
+    return args.cpu_threads or os.cpu_count() or 1
+
+
+def cpu_baseline(d, gamma, budget_s, max_events, threads):
+    """The FP64 oracle as it stands, on `threads` host threads (its packet-parallel mode): MRW transport of
+    a bounded packet sample of the same disk for about `budget_s` seconds, then its PDA solve on those
+    tallies; value = sample packets / transport seconds."""
     from oracle import oracle as O
     O.build()
     run = O.Run(d)
     t0 = time.perf_counter()
-    n, chunk = 0, 50
+    n, chunk = 0, 400 * threads
     while time.perf_counter() - t0 < budget_s:
         run.run(chunk, seed=1, first_id=n, n_total=10 ** 8, mrw=True, gamma=gamma, want_sed=False,
-                max_events=max_events)
+                max_events=max_events, threads=threads)
         n += chunk
     t_tr = time.perf_counter() - t0
     T, err = run.temperatures()
@@ -182,9 +241,10 @@ def cpu_baseline(d, gamma, budget_s, max_events):
         pda_ms = (time.perf_counter() - t1) * 1e3
     except ValueError:
         pda_ms = None
-    return {"value": n / t_tr, "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": f"{n} packets of the workload disk (MRW gamma={gamma}) in {t_tr:.1f} s on one core; "
-                      f"oracle PDA (scipy sparse direct) on those tallies {pda_ms if pda_ms is None else round(pda_ms, 1)} ms",
+    return {"value": n / t_tr, "unit": UNIT, "cores": threads, "kind": "oracle",
+            "sample": f"{n} packets of the workload disk (MRW gamma={gamma}) in {t_tr:.1f} s on {threads} host "
+                      f"threads (oracle packet-parallel mode); oracle PDA (scipy sparse direct) on those tallies "
+                      f"{pda_ms if pda_ms is None else round(pda_ms, 1)} ms",
             "pda_ms": pda_ms}
 
 
@@ -195,14 +255,15 @@ def run_reference(args):
     from oracle import oracle as O
     O.build()
     d = workload()
-    per_step = 200
-    # warm-up then timed steps: each step is a bounded sample of the workload (transport + PDA)
+    threads = host_threads(args)
+    per_step = 5000 * threads
+    # warm-up then timed steps: each step is a bounded sample of the workload (transport + temperatures + PDA)
     times = []
     for s in range(args.warmup + args.steps):
         run = O.Run(d)
         t0 = time.perf_counter()
-        run.run(per_step, seed=1, first_id=s * per_step, n_total=10 ** 8, mrw=True, gamma=args.gamma, want_sed=False,
-                max_events=int(args.max_events))
+        run.run(per_step, seed=1, first_id=s * per_step, n_total=10 ** 8, mrw=True, gamma=args.gamma,
+                want_sed=False, max_events=int(args.max_events), threads=threads)
         T, err = run.temperatures()
         try:
             O.solve_pda(d, T, run.tally, run.visits, err)
@@ -216,10 +277,105 @@ def run_reference(args):
             "warmup": args.warmup, "ms_per_step": 1e3 * t / args.steps, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",
             "config": {"workload": WORKLOAD, "packets_per_step": per_step},
-            "cpu_baseline": {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
-                             "sample": f"{per_step} packets + temperatures + PDA per step, FP64 oracle, one core"},
+            "cpu_baseline": {"value": v, "unit": UNIT, "cores": threads, "kind": "oracle",
+                             "sample": f"{per_step} packets + temperatures + PDA per step, FP64 oracle, "
+                                       f"{threads} host threads (packet-parallel mode)"},
             "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
+
+
+def profile_transport(args):
+    """One FP32 MRW transport call of the workload (the program the ncu captures of the transport kernels
+    run); prints its statistics, whose steps (events + crossings) turn the captured counts into per-step
+    figures."""
+    from paper_0902_3092_gb300 import build, mcrt
+    build.build()
+    d = workload()
+    g = mcrt.Disk.from_model(d, device=0)
+    n = int(args.packets)
+    st = g.run_photons(n, seed=1, first_id=0, n_total=n, mrw=True, gamma=args.gamma, want_sed=True,
+                       max_events=int(args.max_events))
+    st = {k: v for k, v in st.items() if not k.startswith("guard_")}
+    st["steps"] = st["events"] + st["crossings"]
+    print(json.dumps({"profile_transport": {"workload": WORKLOAD, "packets": n, **st}}), flush=True)
+
+
+def midplane_errors(T, T_ref, rows, sel):
+    """RMS and maximum relative error of the midplane temperatures (the two polar rows next to theta =
+    pi/2) over the cells `sel` (Sect. 3.1-3.2 compare temperatures this way)."""
+    t, r = T[:, rows], T_ref[:, rows]
+    ok = sel & (r > 0)
+    rel = np.abs(t[ok] / r[ok] - 1.0)
+    return float(np.sqrt(np.mean(rel ** 2))), float(rel.max()), int(ok.sum())
+
+
+def equal_accuracy(g, d, args):
+    """The speed-up of MRW + PDA over plain Monte Carlo at equal midplane-temperature accuracy (Sect. 3.1,
+    3.2), on this GPU. Reference: plain Monte Carlo, two independent halves of `ref` packets each, whose
+    midplane cells are used where the halves agree within 2 % (elsewhere the reference itself is not
+    converged). Both methods are swept over packet counts (other seeds); each point's time is the transport
+    kernels' device time plus the PDA call. The accuracy level is the lowest RMS error both methods reach;
+    each method's time is that of its cheapest sweep point at or below the level, and the ratio is plain MC's
+    time over MRW + PDA's. Every run keeps the benchmark's per-packet event cap."""
+    from paper_0902_3092_gb300 import mcrt
+    cap = int(args.max_events)
+    j = d.ntheta // 2
+    rows = [j - 1, j]
+    ref_n = 10 ** 8
+    halves, t_ref = [], 0.0
+    for h in range(2):
+        g.reset()
+        st = g.run_photons(ref_n, seed=1000 + h, mrw=False, max_events=cap, want_sed=False)
+        t_ref += st["seconds"]
+        halves.append((np.frombuffer(g.checkpoint(), np.uint64).copy(), g.temperatures()[0]))
+    comb = halves[0][0].copy()
+    comb[8:] = halves[0][0][8:] + halves[1][0][8:]
+    comb[5] = 2 * ref_n
+    comb[6] = np.frombuffer(np.array([float(2 * ref_n)]).tobytes(), np.uint64)[0]
+    g.restore(comb.tobytes())
+    T_ref = g.temperatures()[0]
+    h0, h1 = halves[0][1][:, rows], halves[1][1][:, rows]
+    with np.errstate(divide="ignore", invalid="ignore"):
+        conv = (h0 > 0) & (h1 > 0) & (np.abs(h0 / h1 - 1) <= 0.02)
+    sweeps = {"plain MC": (False, False, [10 ** 6, 3 * 10 ** 6, 10 ** 7, 3 * 10 ** 7, 10 ** 8]),
+              "MRW+PDA": (True, True, [10 ** 5, 3 * 10 ** 5, 10 ** 6, 3 * 10 ** 6, 10 ** 7, 3 * 10 ** 7, 10 ** 8])}
+    pts = {}
+    for name, (mrw, pda, ns) in sweeps.items():
+        pts[name] = []
+        for n in ns:
+            g.reset()
+            st = g.run_photons(n, seed=77, mrw=mrw, gamma=args.gamma, max_events=cap, want_sed=False)
+            t = st["seconds"]
+            if pda:
+                t0 = time.perf_counter()
+                g.solve_pda(min_visits=max(30, int(round(30 * n / 1e5))))
+                t += time.perf_counter() - t0
+                T = g.temperatures(mcrt.T_PDA)[0]
+            else:
+                T = g.temperatures()[0]
+            rms, mx, cells = midplane_errors(T, T_ref, rows, conv)
+            pts[name].append({"packets": n, "seconds": t, "rms": rms, "max": mx})
+    level = max(min(p["rms"] for p in pts[k]) for k in pts)
+    reach = {}
+    for k in pts:
+        seq = pts[k]
+        i = next(i for i, p in enumerate(seq) if p["rms"] <= level * (1 + 1e-12))
+        t, n = seq[i]["seconds"], float(seq[i]["packets"])
+        if i > 0 and seq[i - 1]["rms"] > level and seq[i]["rms"] < level:
+            # between two sweep points: log time and log packets linear in log error
+            a, b = seq[i - 1], seq[i]
+            f = math.log(a["rms"] / level) / math.log(a["rms"] / b["rms"])
+            t = math.exp(math.log(a["seconds"]) + f * math.log(b["seconds"] / a["seconds"]))
+            n = math.exp(math.log(a["packets"]) + f * math.log(b["packets"] / a["packets"]))
+        reach[k] = {"seconds": t, "packets": n, "sweep_point": seq[i]}
+    return {"level_rms": level, "cells": int(conv.sum()), "midplane_cells": int(2 * d.nr),
+            "reference": {"method": "plain MC, two halves", "packets": 2 * ref_n, "kernel_s": t_ref,
+                          "cells_converged": "midplane cells whose halves agree within 2 %"},
+            "plain_mc": reach["plain MC"], "mrw_pda": reach["MRW+PDA"],
+            "speedup": reach["plain MC"]["seconds"] / reach["MRW+PDA"]["seconds"],
+            "sweeps": pts, "event_cap": cap,
+            "note": "time to reach the lowest midplane RMS error both methods reach (interpolated in log-log "
+                    "between sweep points); transport device time + PDA call"}
 
 
 # algorithmic bytes per PDA cell and FP32 CG iteration: kernel A reads r, p_old and the two couplings and
@@ -548,6 +704,9 @@ def main():
     if args.impl == "reference":
         run_reference(args)
         return
+    if args.profile_transport:
+        profile_transport(args)
+        return
     if args.pda_stress:
         pda_stress(args)
         return
@@ -677,21 +836,16 @@ def main():
                "d2h_bytes_per_step": int(d2h)}
 
     peaks = measured_peaks()
-    steps_per_launch = float(np.mean(ev_steps))
-    achieved = WARP_INST_PER_STEP * steps_per_launch / float(np.mean(tr_s))
-    thread_achieved = THREAD_INST_PER_STEP * steps_per_launch / float(np.mean(tr_s))
-    roofline = {"bound": "alu", "achieved": achieved, "peak": ISSUE_PEAK, "unit": "warp-inst/s",
-                "frac": achieved / ISSUE_PEAK, "traffic": TRANSPORT_DRAM_BYTES,
-                "kernel": "transport_kernel<float> + transport_tail_kernel<float> (one transport call, gray)",
-                "thread_inst_frac": thread_achieved / THREAD_ISSUE_PEAK,
-                "note": f"issue-slot roofline: {WARP_INST_PER_STEP:g} warp instructions per transport step "
-                        f"(ncu count on this workload) x {steps_per_launch:.3e} steps per launch / CUDA-event launch "
-                        "time; peak = 152 SMs x 4 schedulers x 2070 MHz (no DRAM bound: tallies and tables are "
-                        f"L2-resident); thread_inst_frac counts active lanes ({THREAD_INST_PER_STEP:g} per step)"}
+    clocks = clk.summary()
+    roofline = transport_roofline(float(np.mean(ev_steps)), float(np.mean(tr_s)), clocks, peaks)
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:
-        cpu = cpu_baseline(d, args.gamma, args.cpu_seconds, int(args.max_events))
+        cpu = cpu_baseline(d, args.gamma, args.cpu_seconds, int(args.max_events), host_threads(args))
+
+    acc = None
+    if rank == 0 and world == 1 and not args.no_accuracy:
+        acc = equal_accuracy(g, d, args)
 
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -704,7 +858,7 @@ def main():
                            "l2": "flushed between timed steps (512 MiB write outside the timed region)",
                            "parallelism": f"packet ranges per rank, int64 tally all-reduce" if world > 1 else "1 GPU"},
                 "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": int(launches),
-                "clocks": clk.summary(),
+                "clocks": clocks, "equal_accuracy": acc,
                 "transport": {"kernel_ms_per_step": 1e3 * float(np.mean(tr_s)), "events": s0["events"],
                               "crossings": s0["crossings"], "mrw_jumps": s0["mrw_jumps"], "capped": s0["capped"],
                               "capped_fraction": s0["capped"] / Np, "max_packet_steps": s0["max_packet_steps"],
