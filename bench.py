@@ -757,7 +757,9 @@ def main():
         g.reset()
         first, _ = D.packet_range(rank, world, Np, i)
         try:
-            st = g.run_photons(Np, seed=1, first_id=first, n_total=Np * world, mrw=True,
+            # the rank's share is a run of its own (n_total = its packets); the exchange reads the summed
+            # tallies with the total packet count
+            st = g.run_photons(Np, seed=1, first_id=first, n_total=Np, mrw=True,
                                gamma=args.gamma, want_sed=True, max_events=int(args.max_events))
         except mcrt.McrtError as e:
             # a step guard dropped packets: the call still completed (the dropped packets count as capped);

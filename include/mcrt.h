@@ -363,14 +363,17 @@ mcrt_status mcrt_debug_mrw_x(int device, int n, const double *P0, double *x_out)
  * start-up -- and mcrt_solve_pda allocates its working vectors on first use. This entry point takes the
  * assembled system in the caller's device buffers and keeps its working vectors in one file-scope
  * device array of fixed size; it never calls cudaMalloc or cudaFree.
- *   device:     CUDA device whose copy of the array is used (made current by the call).
+ *   device:     CUDA device whose copy of the array is used (current during the call; the caller's
+ *               current device is restored before it returns).
  *   nr, ntheta: grid; nr * ntheta <= 131072, or MCRT_EINVAL.
  *   mask_dev:   int8 per cell: 2 unknown (PDA) cell, 1 cell with a fixed value, 0 no flux.
  *   Cr_dev:     conductance of the face between (ir, it) and (ir+1, it), per cell (last row unused).
  *   Ct_dev:     conductance of the face between (ir, it) and (ir, it+1), per cell (last column unused).
  *   u_dev:      T^4 per cell: fixed values on mask-1 cells (read), the solution on mask-2 cells
  *               (written; their input values are the starting guess, normally 0).
- *   opts:       tol, inner_tol, max_outer, max_inner (<= 20000); the other fields are not used.
+ *   opts:       tol, inner_tol, max_outer, max_inner (<= 20000); the other fields are not used. tol is
+ *               relative to |S b|, the scaled right-hand side (the residual with the unknowns at 0), as
+ *               in mcrt_solve_pda, whatever the starting guess.
  *   cuda_stream: stream to run on (NULL: the legacy default stream). The call returns when the solve
  *               has finished on that stream.
  * The first call on a device looks up the device address of the array (cudaGetSymbolAddress) with that

@@ -1045,7 +1045,42 @@ __global__ void k_static_dis(int nr, int nt, const signed char* mask, const doub
     atomicAdd(red + 3, 1.0);
   }
 }
+// |S b|^2 of the system: the scaled residual with every unknown (mask 2) cell at 0, so that only the fixed
+// (mask 1) neighbours contribute; the solve's tolerance is relative to it, as in mcrt_solve_pda
+__global__ void k_static_bnorm(int nr, int nt, const signed char* mask, const double* Cr, const double* Ct,
+                               const double* dis, const double* u, double* red) {
+  __shared__ double sh[32];
+  double acc = 0.0;
+  for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < nr * nt; c += gridDim.x * blockDim.x) {
+    if (mask[c] != 2) continue;
+    const int i = c / nt, j = c - i * nt;
+    double r = 0.0;
+    if (i > 0 && mask[c - nt] == 1) r += Cr[c - nt] * u[c - nt];
+    if (i + 1 < nr && mask[c + nt] == 1) r += Cr[c] * u[c + nt];
+    if (j > 0 && mask[c - 1] == 1) r += Ct[c - 1] * u[c - 1];
+    if (j + 1 < nt && mask[c + 1] == 1) r += Ct[c] * u[c + 1];
+    const double v = dis[c] * r;
+    acc += v * v;
+  }
+  const double s = block_sum_d(acc, sh);
+  if (threadIdx.x == 0 && s != 0.0) atomicAdd(red + 5, s);
+}
 }  // namespace mcrt
+
+namespace {
+// makes a device current for the lifetime of the object and restores the caller's current device after
+struct CurrentDevice {
+  int prev = -1;
+  cudaError_t err = cudaSuccess;
+  explicit CurrentDevice(int dev) {
+    if (cudaGetDevice(&prev) != cudaSuccess) prev = -1;
+    err = cudaSetDevice(dev);
+  }
+  ~CurrentDevice() {
+    if (prev >= 0) cudaSetDevice(prev);
+  }
+};
+}  // namespace
 
 extern "C" mcrt_status mcrt_pda_solve_static(int device, int nr, int ntheta, const signed char* mask_dev,
                                              const double* Cr_dev, const double* Ct_dev, double* u_dev,
@@ -1060,7 +1095,8 @@ extern "C" mcrt_status mcrt_pda_solve_static(int device, int nr, int ntheta, con
   if (o->max_inner > kStaticMaxInner)
     return set_error(nullptr, MCRT_EINVAL, "max_inner must be <= 20000 for mcrt_pda_solve_static");
   if (device < 0 || device >= 64) return set_error(nullptr, MCRT_EINVAL, "device index out of range");
-  CK(cudaSetDevice(device), "cudaSetDevice");
+  const CurrentDevice cur(device);  // the caller's current device is restored on every return
+  CK(cur.err, "cudaSetDevice");
   unsigned char* base = nullptr;
   {
     std::lock_guard<std::mutex> lock(g_static_mu);
@@ -1090,15 +1126,17 @@ extern "C" mcrt_status mcrt_pda_solve_static(int device, int nr, int ntheta, con
   CK(cudaMemsetAsync(red, 0, 16 * sizeof(double), st), "memset");
   k_static_dis<<<nblk(n), 256, 0, st>>>(nr, nt, mask_dev, Cr_dev, Ct_dev, dis, red);
   k_scaled<<<nblk(n), 256, 0, st>>>(nr, nt, mask_dev, Cr_dev, Ct_dev, dis, ar, at);
-  double singular = 0.0;
-  CK(cudaMemcpyAsync(&singular, red + 3, sizeof(double), cudaMemcpyDeviceToHost, st), "copy");
+  k_static_bnorm<<<sgrid(n), 256, 0, st>>>(nr, nt, mask_dev, Cr_dev, Ct_dev, dis, u_dev, red);
+  double red_h[6] = {0, 0, 0, 0, 0, 0};
+  CK(cudaMemcpyAsync(red_h, red, sizeof(red_h), cudaMemcpyDeviceToHost, st), "copy");
   CK(cudaStreamSynchronize(st), "synchronize");
   CK(cudaGetLastError(), "PDA kernels");
-  if (singular > 0) return set_error(nullptr, MCRT_EINVAL, "a PDA cell has no conducting face (singular system)");
+  if (red_h[3] > 0) return set_error(nullptr, MCRT_EINVAL, "a PDA cell has no conducting face (singular system)");
+  const double norm_b = std::sqrt(red_h[5]);  // |S b|: the tolerance does not depend on the starting guess
   const double tol2_in = o->inner_tol * o->inner_tol;
   const int ntiles = (n + 31) / 32;  // every tile of the grid
   const int ga = tgrid(k_cg_a<kUA>, ntiles), gb = tgrid(k_cg_b<kUB>, ntiles);
-  double norm_b = -1.0, best = INFINITY;
+  double best = INFINITY;
   int total_iters = 0, stall = 0;
   const int chunk = 32;
   double h[2 * chunk + 2];
@@ -1109,7 +1147,6 @@ extern "C" mcrt_status mcrt_pda_solve_static(int device, int nr, int ntheta, con
     CK(cudaMemcpyAsync(&rn2, red + 4, sizeof(double), cudaMemcpyDeviceToHost, st), "copy");
     CK(cudaStreamSynchronize(st), "synchronize");
     const double rn = std::sqrt(rn2);
-    if (norm_b < 0) norm_b = rn;
     if (!(rn == rn)) return set_error(nullptr, MCRT_ENOTCONV, "PDA residual is not finite");
     if (rn <= o->tol * norm_b || rn == 0.0) {
       if (out_iters) *out_iters = total_iters;

@@ -5,6 +5,13 @@ absorption counts and escape spectrum over the ranks, before temperatures and th
 The tallies travel as checkpoint blobs (the layout of mcrt_checkpoint: 8 uint64 header words, then
 tally, visits, absorptions per cell and the spectrum counts), so the exchange is independent of where
 the tallies live; with gray dust the summed state is bitwise that of a single run over all packets.
+
+Each rank transports its share as a run of its own: n_total = its own packet count. The tallies count
+packet energies, so that choice only sets the temperatures seen during the rank's run -- those of its own
+tallies, which decide the Bjorkman-Wood re-emission spectra and the MRW coefficients of non-gray dust. A
+rank whose share were weighed as 1/k of the whole run would see temperatures low by k^(1/4) and re-emit
+at the wrong temperature. The exchange then rewrites the header to the total packet count, so the summed
+state is k independent BW runs added together, read with the packet energy of the whole run.
 """
 from __future__ import annotations
 
@@ -35,6 +42,18 @@ def split_blob(blob: bytes):
     if int(hdr[0]) != MAGIC:
         raise ValueError("not a checkpoint blob")
     return hdr.copy(), a[HEADER_WORDS:].copy()
+
+
+def combine_blobs(blobs) -> bytes:
+    """The exchange without a process group: the integer states of several ranks' blobs summed, the header
+    carrying the total packet count (what allreduce_blob leaves on every rank)."""
+    hdrs, bodies = zip(*(split_blob(b) for b in blobs))
+    hdr = hdrs[0].copy()
+    body = np.sum(np.stack(bodies), axis=0, dtype=np.uint64)
+    n = int(sum(int(h[5]) for h in hdrs))
+    hdr[5] = n
+    hdr[6] = _n_total_word(float(n))
+    return hdr.tobytes() + body.tobytes()
 
 
 def allreduce_blob(blob: bytes, group=None) -> bytes:

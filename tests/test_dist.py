@@ -85,3 +85,87 @@ def test_packet_ranges_partition():
             assert not (ids & seen)
             seen |= ids
     assert seen == set(range(1200))
+
+
+def _rank_nongray(rank, world, port, out, per):
+    import torch.distributed as dist
+
+    from oracle import oracle as O
+    from paper_0902_3092_gb300 import dist as D
+    os.environ["MASTER_ADDR"] = "127.0.0.1"
+    os.environ["MASTER_PORT"] = str(port)
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    d = _nongray_disk()
+    first, n = D.packet_range(rank, world, per)
+    # the rank's share is a run of its own: n_total = its packets (the temperatures it sees are its own)
+    r = O.Run(d).run(n, seed=5, first_id=first, n_total=n, want_sed=True, threads=2)
+    blob = D.make_blob(d.nr, d.ntheta, d.opacity.nlam, r.tally, r.visits, r.nabs, r.sed, n, n)
+    T_own, e_own = r.temperatures()
+    red = D.allreduce_blob(blob)
+    out.put((rank, red, T_own, e_own, r.nabs.copy()))
+    dist.barrier()
+    dist.destroy_process_group()
+
+
+def _nongray_disk():
+    from paper_0902_3092_gb300 import disks
+    return disks.make_disk(disks.log_r_faces(0.1, 100.0, 12), disks.midplane_refined_theta_faces(10),
+                           disks.paper_star(), disks.powerlaw_opacity(nlam=16), 3e3)
+
+
+def test_two_rank_nongray_run_matches_a_single_run():
+    """Non-gray dust (Bjorkman-Wood re-emission at the temperatures seen during the run): each rank runs its
+    share with its own packet count, so its own temperatures are those of a full run (not low by 2^(1/4)),
+    and the all-reduced state, read with the total packet count, agrees with runs of all the packets on one
+    process. A cell's scatter is measured from six such runs (in optically thick cells a packet is absorbed
+    many times before it leaves, so 1/(4 sqrt N) would understate it)."""
+    from oracle import oracle as O
+    from paper_0902_3092_gb300 import dist as D
+    O.build()
+    per = 20000
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    port = _free_port()
+    ps = [ctx.Process(target=_rank_nongray, args=(r, 2, port, q, per)) for r in range(2)]
+    for p in ps:
+        p.start()
+    res = sorted([q.get(timeout=300) for _ in range(2)], key=lambda x: x[0])
+    for p in ps:
+        p.join(timeout=120)
+        assert p.exitcode == 0
+    d = _nongray_disk()
+    red = res[0][1]
+    assert red == res[1][1]
+    hdr, body = D.split_blob(red)
+    assert int(hdr[5]) == 2 * per
+    n = d.nr * d.ntheta
+    comb = O.Run(d)
+    comb.tally[:] = body[:n]
+    comb.n_total = 2 * per
+    Tc, _ = comb.temperatures()
+    fulls = [O.Run(d).run(2 * per, seed=20 + k, want_sed=True, threads=4) for k in range(6)]
+    Tf = np.array([f.temperatures()[0] for f in fulls])
+    mean, sd = Tf.mean(0), Tf.std(0, ddof=1)
+    sel = (body[2 * n:3 * n].reshape(mean.shape) >= 300) & (sd > 0)
+    assert sel.sum() >= 6
+    z = np.abs(Tc[sel] - mean[sel]) / (sd[sel] * np.sqrt(1 + 1 / len(Tf)))
+    assert z.max() < 5.0, np.sort(z)[-3:]
+    for rank, _, T_own, _, _ in res:
+        lr = np.log(T_own[sel] / mean[sel])
+        # a half-size run scatters sqrt(2) more; low by 2^(1/4) would be log 0.84 = -0.173
+        tol = 4 * np.sqrt(2 * np.mean((sd[sel] / mean[sel]) ** 2) / sel.sum())
+        assert abs(lr.mean()) < tol < 0.1, (rank, lr.mean(), tol)
+
+
+def test_combine_blobs_sums_states_and_packet_counts():
+    from paper_0902_3092_gb300 import dist as D
+    rng = np.random.default_rng(3)
+    blobs = []
+    for k in range(3):
+        st = [rng.integers(0, 2 ** 40, size=s, dtype=np.uint64) for s in (20, 20, 20, 30)]
+        blobs.append(D.make_blob(4, 5, 3, *st, packets_done=100 * (k + 1), n_total=100 * (k + 1)))
+    hdr, body = D.split_blob(D.combine_blobs(blobs))
+    assert int(hdr[5]) == 600
+    assert np.frombuffer(np.array([600.0]).tobytes(), np.uint64)[0] == hdr[6]
+    want = sum(D.split_blob(b)[1] for b in blobs)
+    assert np.array_equal(body, want)

@@ -1,0 +1,93 @@
+"""Non-gray FP32 production transport against the oracle: Bjorkman-Wood re-emission from the tabulated
+temperature rows (Sect. 2.1), Henyey-Greenstein scattering with g = 0.6 (Eq. 16's anisotropic dust), the
+MRW with gamma = 2 and its exit spectrum (Sect. 2.2.2), on a 40 x 30 disk of midplane optical depth 1e5
+with the power-law dust of the non-gray benchmark configuration (absorption ~1/lambda beyond 1 micron,
+albedo falling from 0.5 to 0 at 100 micron) in 24 wavelength bins.
+
+The two sides share no floating-point path (the oracle integrates the Planck function exactly at every
+re-emission; the kernels interpolate FP32 tables), so their histories are independent samples of the same
+method. The oracle runs 2e5 packets on every host core (its packet-parallel mode); the GPU runs 16 seeds of
+the same packet count. One MRW jump deposits many packet energies, so the counting error 1/(4 sqrt N) of a
+cell understates its scatter: the bar therefore applies where the measured single-run spread of the GPU
+temperature at that packet count (an estimate of the oracle run's own error) is at most 0.5 %, in cells
+with at least 3000 absorptions; there the 16-run GPU mean must agree with the oracle within 2 % (about four
+combined standard deviations). The escape spectrum per wavelength bin must agree within 4.5 Poisson
+standard deviations in every bin with at least 100 oracle escapes."""
+import os
+
+import numpy as np
+import pytest
+
+from paper_0902_3092_gb300 import disks
+
+pytestmark = pytest.mark.gpu
+
+N = 200_000
+SEEDS = 16
+
+
+@pytest.fixture(scope="module")
+def M():
+    from paper_0902_3092_gb300 import build, mcrt
+    build.build()
+    mcrt.lib()
+    return mcrt
+
+
+@pytest.fixture(scope="module")
+def disk():
+    return disks.make_disk(disks.log_r_faces(0.1, 100.0, 40), disks.midplane_refined_theta_faces(30),
+                           disks.paper_star(), disks.powerlaw_opacity(nlam=24, g=0.6), 1e5,
+                           name="nongray40x30_tau1e5_24bins")
+
+
+def _escapes(g, d):
+    blob = np.frombuffer(g.checkpoint(), np.uint64)  # header, tally, visits, absorptions, escape counts
+    nc = d.nr * d.ntheta
+    return blob[8 + 3 * nc:8 + 3 * nc + d.opacity.nlam * 10].reshape(d.opacity.nlam, 10).sum(1).astype(float)
+
+
+@pytest.fixture(scope="module")
+def runs(M, disk, oracle):
+    g = M.Disk.from_model(disk)
+    Ts, seds = [], []
+    for k in range(SEEDS):
+        g.reset()
+        st = g.run_photons(N, seed=100 + k, mrw=True, gamma=2.0, want_sed=True)
+        assert st["error_flags"] == 0 and st["escaped"] + st["capped"] == N and st["mrw_jumps"] > 0
+        Ts.append(g.temperatures()[0])
+        seds.append(_escapes(g, disk))
+    g.close()
+    ref = oracle.Run(disk).run(N, seed=7, mrw=True, gamma=2.0, want_sed=True, threads=os.cpu_count() or 1)
+    return np.array(Ts), np.array(seds), ref
+
+
+def test_fp32_nongray_temperatures_match_oracle(runs, disk):
+    Ts, _, ref = runs
+    To, _ = ref.temperatures()
+    nabs = ref.nabs.reshape(To.shape)
+    Tm = Ts.mean(0)
+    with np.errstate(invalid="ignore", divide="ignore"):
+        spread = Ts.std(0, ddof=1) / Tm  # one run's relative error at N packets
+    sel = (nabs >= 3000) & (spread <= 0.005) & (To > 0) & (Tm > 0)
+    assert sel.sum() >= 10, int(sel.sum())
+    dev = np.abs(Tm[sel] / To[sel] - 1)
+    assert dev.max() <= 0.02, np.sort(dev)[-5:]
+    # no systematic offset of the FP32 re-emission tables: the mean log ratio within four of its errors
+    lr = np.log(Tm[sel] / To[sel])
+    err = np.sqrt(np.sum(spread[sel] ** 2 * (1 + 1 / len(Ts)))) / sel.sum()
+    assert abs(lr.mean()) <= 4 * err + 1e-3, (lr.mean(), err)
+
+
+def test_fp32_nongray_escape_spectrum_matches_oracle(runs, disk):
+    _, seds, ref = runs
+    so = ref.sed.reshape(disk.opacity.nlam, 10).sum(1).astype(float)
+    sg = seds.sum(0)
+    no, ng = so.sum(), sg.sum()
+    assert no == ref.stats["escaped"] and no > 0.99 * N and ng > 0.99 * SEEDS * N
+    fo, fg = so / no, sg / ng
+    sig = np.sqrt(fo * (1 - fo) / no + fo * (1 - fo) / ng)
+    m = so >= 100
+    assert m.sum() >= 10
+    z = np.abs(fg[m] - fo[m]) / sig[m]
+    assert z.max() <= 4.5, np.sort(z)[-4:]

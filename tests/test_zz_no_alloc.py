@@ -71,6 +71,17 @@ def test_static_scratch_solve_matches_solve_pda(oracle):
         assert np.max(np.abs(T[pda] / T_ref[pda] - 1)) < 1e-6, call
         assert np.max(np.abs(T[pda] / To[pda] - 1)) < 1e-6, call
         assert np.array_equal(u[~pda], u0[~pda])
+    # a third call from a starting guess far from the solution: the tolerance is relative to the
+    # right-hand side, not to the first residual, so it lands on the same solution
+    guess = np.where(pda, 3.0 * u, u0)
+    t_u = torch.from_numpy(guess.ravel().copy()).to(dev)
+    torch.cuda.synchronize()
+    mcrt.pda_solve_static(d.nr, d.ntheta, t_mask.data_ptr(), t_cr.data_ptr(), t_ct.data_ptr(), t_u.data_ptr(),
+                          device=0)
+    u3 = t_u.cpu().numpy().reshape(d.rho.shape)
+    T3 = np.where(pda, np.maximum(u3, 0.0) ** 0.25, T_mc)
+    assert np.max(np.abs(T3[pda] / To[pda] - 1)) < 1e-6
+    assert torch.cuda.current_device() == 0
 
 
 def test_static_scratch_size_limit():
