@@ -18,6 +18,7 @@ import argparse
 import json
 import math
 import os
+import re
 import subprocess
 import sys
 import threading
@@ -51,12 +52,12 @@ def transport_counts():
     try:
         with open(COUNTS_FILE) as f:
             for ln in f:
-                if ln.startswith("    ") and ":" in ln:
-                    k, v = ln.strip().split(":", 1)
+                m = re.match(r"^    ([a-z0-9_]+): (\S+)\s*$", ln)
+                if m:
                     try:
-                        out[k.strip()] = float(v)
+                        out[m.group(1)] = float(m.group(2))
                     except ValueError:
-                        out[k.strip()] = v.strip()
+                        out[m.group(1)] = m.group(2)
     except OSError:
         pass
     return out
@@ -93,7 +94,7 @@ def transport_roofline(steps_per_launch, t_launch, clocks, peaks):
                  "thread_inst_frac": tps * steps_per_launch / t_launch / (32 * peak),
                  "traffic": c.get("dram_bytes_per_launch"),
                  "note": f"issue slots: {wps:.2f} warp instructions per transport step (ncu, both kernels, "
-                         f"{c.get('profiled_packets', '?')}-packet call) x {steps_per_launch:.4g} steps per launch / "
+                         f"{c.get('profiled_packets', 0):.0e}-packet call) x {steps_per_launch:.4g} steps per launch / "
                          f"{t_launch:.4g} s CUDA-event launch time; peak = 152 SMs x 4 schedulers x {mhz:g} MHz; "
                          f"thread_inst_frac = {tps:.1f} thread instructions per step against 32 lanes per slot "
                          "(the share of lanes doing work); traffic = DRAM bytes of one 1e8-packet call (ncu)"})
@@ -227,12 +228,18 @@ def cpu_baseline(d, gamma, budget_s, max_events, threads):
     from oracle import oracle as O
     O.build()
     run = O.Run(d)
+    # a short call sets the rate, then one call of the rest of the budget: each call waits for its longest
+    # packet, so one long call keeps every thread busy
     t0 = time.perf_counter()
-    n, chunk = 0, 400 * threads
-    while time.perf_counter() - t0 < budget_s:
-        run.run(chunk, seed=1, first_id=n, n_total=10 ** 8, mrw=True, gamma=gamma, want_sed=False,
-                max_events=max_events, threads=threads)
-        n += chunk
+    n = 500 * threads
+    run.run(n, seed=1, first_id=0, n_total=10 ** 8, mrw=True, gamma=gamma, want_sed=False, max_events=max_events,
+            threads=threads)
+    rate = n / (time.perf_counter() - t0)
+    m = int(max(0.0, budget_s - (time.perf_counter() - t0)) * rate)
+    if m > 0:
+        run.run(m, seed=1, first_id=n, n_total=10 ** 8, mrw=True, gamma=gamma, want_sed=False, max_events=max_events,
+                threads=threads)
+        n += m
     t_tr = time.perf_counter() - t0
     T, err = run.temperatures()
     t1 = time.perf_counter()

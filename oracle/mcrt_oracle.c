@@ -1140,6 +1140,7 @@ typedef struct {
   uint64_t n, first_id, n_total, seed;
   uint32_t model;
   uint64_t *next;  /* shared: the next packet index to hand out */
+  char pad[256];   /* keeps the counters of neighbouring threads off each other's cache lines */
 } par_job;
 
 #define OR_PAR_CHUNK 16
@@ -1164,9 +1165,14 @@ int oracle_run_par(const oracle_model *m, const oracle_opts *o, oracle_state *s,
                    uint64_t n_total, uint64_t seed, uint32_t model, int threads) {
   if (threads < 1 || s->trace_packets > 0 || s->jtally) return -1;
   const size_t nc = (size_t)m->nr * m->nt, ns = (size_t)m->nlam * OR_NINC;
-  par_job *jobs = (par_job *)calloc((size_t)threads, sizeof(par_job));
+  par_job *jobs = (par_job *)aligned_alloc(256, ((sizeof(par_job) * (size_t)threads + 255) / 256) * 256);
+  memset(jobs, 0, sizeof(par_job) * (size_t)threads);
   pthread_t *tid = (pthread_t *)calloc((size_t)threads, sizeof(pthread_t));
   uint64_t next = 0;
+  /* gray dust without an escape spectrum: no temperature steers a packet (D and kappa_bar are constants,
+   * no re-emission bin is drawn), so every thread deposits into a tally of its own, added at the end,
+   * instead of contending for the shared one */
+  const int own_tally = is_gray(m) && !o->want_sed;
   for (int t = 0; t < threads; ++t) {
     par_job *j = &jobs[t];
     j->m = m;
@@ -1177,7 +1183,7 @@ int oracle_run_par(const oracle_model *m, const oracle_opts *o, oracle_state *s,
     j->seed = seed;
     j->model = model;
     j->next = &next;
-    j->st.tally = s->tally;
+    j->st.tally = own_tally ? (uint64_t *)calloc(nc, sizeof(uint64_t)) : s->tally;
     j->st.visits = (uint64_t *)calloc(nc, sizeof(uint64_t));
     j->st.nabs = (uint64_t *)calloc(nc, sizeof(uint64_t));
     j->st.sed = (uint64_t *)calloc(ns, sizeof(uint64_t));
@@ -1196,9 +1202,15 @@ int oracle_run_par(const oracle_model *m, const oracle_opts *o, oracle_state *s,
   for (int t = 0; t < threads; ++t) {
     par_job *j = &jobs[t];
     for (size_t c = 0; c < nc; ++c) {
+      if (own_tally) {
+        const uint64_t old = s->tally[c];
+        s->tally[c] = old + j->st.tally[c];
+        if (s->tally[c] < old) s->cnt[CNT_ERR] |= 1u; /* overflow */
+      }
       s->visits[c] += j->st.visits[c];
       s->nabs[c] += j->st.nabs[c];
     }
+    if (own_tally) free(j->st.tally);
     for (size_t k = 0; k < ns; ++k) {
       s->sed[k] += j->st.sed[k];
       if (s->sed_sca) s->sed_sca[k] += j->st.sed_sca[k];

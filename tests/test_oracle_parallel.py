@@ -27,8 +27,10 @@ def _same(a, b):
     assert a.stats == b.stats
 
 
-@pytest.mark.parametrize("mrw,sources", [(False, False), (True, False), (True, True)])
-def test_gray_parallel_run_equals_serial_run(mrw, sources):
+@pytest.mark.parametrize("mrw,sources,want_sed", [(False, False, True), (True, False, True), (True, True, True),
+                                                  (True, False, False)])
+def test_gray_parallel_run_equals_serial_run(mrw, sources, want_sed):
+    """(Without the escape spectrum each thread keeps a tally of its own, added at the end.)"""
     d = disks.make_disk(disks.rim_refined_r_faces(0.1, 100.0, 24), disks.midplane_refined_theta_faces(16),
                         disks.paper_star(), disks.gray_opacity(nlam=20), 3e3)
     L = None
@@ -36,8 +38,9 @@ def test_gray_parallel_run_equals_serial_run(mrw, sources):
         L = disks.viscous_sources(d)
         L *= 0.5 * d.star.L / L.sum()
     n = 4000
-    ser = oracle.Run(d, sources=L).run(n, seed=5, mrw=mrw, gamma=2.0, want_sed=True, max_events=10 ** 5)
-    par = oracle.Run(d, sources=L).run(n, seed=5, mrw=mrw, gamma=2.0, want_sed=True, max_events=10 ** 5, threads=4)
+    ser = oracle.Run(d, sources=L).run(n, seed=5, mrw=mrw, gamma=2.0, want_sed=want_sed, max_events=10 ** 5)
+    par = oracle.Run(d, sources=L).run(n, seed=5, mrw=mrw, gamma=2.0, want_sed=want_sed, max_events=10 ** 5,
+                                       threads=4)
     _same(ser, par)
     assert ser.stats["escaped"] + ser.stats["capped"] == n
     if mrw:
