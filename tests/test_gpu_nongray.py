@@ -6,7 +6,7 @@ albedo falling from 0.5 to 0 at 100 micron) in 24 wavelength bins.
 
 The two sides share no floating-point path (the oracle integrates the Planck function exactly at every
 re-emission; the kernels interpolate FP32 tables), so their histories are independent samples of the same
-method. The oracle runs 2e5 packets on every host core (its packet-parallel mode); the GPU runs 16 seeds of
+method. The oracle runs 1e6 packets on every host core (its packet-parallel mode); the GPU runs 16 seeds of
 the same packet count. One MRW jump deposits many packet energies, so the counting error 1/(4 sqrt N) of a
 cell understates its scatter: the bar therefore applies where the measured single-run spread of the GPU
 temperature at that packet count (an estimate of the oracle run's own error) is at most 0.5 %, in cells
@@ -22,7 +22,7 @@ from paper_0902_3092_gb300 import disks
 
 pytestmark = pytest.mark.gpu
 
-N = 200_000
+N = 1_000_000
 SEEDS = 16
 
 
