@@ -381,8 +381,13 @@ def equal_accuracy(g, d, args):
             f = math.log(a["rms"] / level) / math.log(a["rms"] / b["rms"])
             t = math.exp(math.log(a["seconds"]) + f * math.log(b["seconds"] / a["seconds"]))
             n = math.exp(math.log(a["packets"]) + f * math.log(b["packets"] / a["packets"]))
-        reach[k] = {"seconds": t, "packets": n, "sweep_point": seq[i]}
+        # the first sweep point already below the level: the time there bounds the time to reach it
+        reach[k] = {"seconds": t, "packets": n, "sweep_point": seq[i], "upper_bound": i == 0 and seq[0]["rms"] < level}
+    best = min(pts["MRW+PDA"], key=lambda p: p["rms"])
     return {"level_rms": level, "cells": int(conv.sum()), "midplane_cells": int(2 * d.nr),
+            "plain_mc_floor_rms": min(p["rms"] for p in pts["plain MC"]),
+            "mrw_pda_best": {"rms": best["rms"], "packets": best["packets"], "seconds": best["seconds"]},
+            "speedup_is_lower_bound": bool(reach["MRW+PDA"]["upper_bound"]),
             "reference": {"method": "MRW gamma=2, two independent halves", "packets": 2 * ref_n, "kernel_s": t_ref,
                           "cells": "midplane cells whose halves agree within 2 %",
                           "validation": "MRW vs plain MC without an event cap on the tau_mid=1e4 and 1e5 disks: "

@@ -236,6 +236,9 @@ typedef struct {
   int which;                    /* MCRT_T_PDA (the last PDA solve, default) or MCRT_T_MC */
   const double *shell_mass_g;   /* optional host array nr: the dust mass each radial shell keeps;
                                    NULL: the disk's current shell masses */
+  const double *relax;          /* optional host array nr, each in (0, 2]: a damped step per shell,
+                                   log rho_new = (1 - a) log rho_cur + a log rho_Eq20 in the dusty cells,
+                                   rescaled to the shell's mass (the paper iterates undamped); NULL: a = 1 */
 } mcrt_hydro_opts;
 
 void mcrt_default_hydro_opts(mcrt_hydro_opts *o);

@@ -37,7 +37,7 @@ def cell_volumes(r_faces, theta_faces):
     rf = np.asarray(r_faces, np.float64)
     tf = np.asarray(theta_faces, np.float64)
     r1, r2 = rf[:-1], rf[1:]
-    return (2.0 * np.pi / 3.0) * (r2 * r2 * r2 - r1 * r1 * r1)[:, None] * (np.cos(tf[:-1]) - np.cos(tf[1:]))[None, :]
+    return (2.0 * np.pi / 3.0) * (r2 ** 3 - r1 ** 3)[:, None] * (np.cos(tf[:-1]) - np.cos(tf[1:]))[None, :]
 
 
 def shell_masses(r_faces, theta_faces, rho):
@@ -61,7 +61,7 @@ def hydrostatic_density(r_faces, theta_faces, rho_mask, T, shell_mass, M_star=2.
         for j in range(nt):
             th = 0.5 * (tf[j] + tf[j + 1])
             z, R = rc * np.cos(th), rc * np.sin(th)
-            a = GM * z / (R * R * R) * (mu * M_U / (K_B * Tc[j]))  # G M z / (R^3 c^2)
+            a = GM * z / R ** 3 * (mu * M_U / (K_B * Tc[j]))  # G M z / (R^3 c^2)
             if j > 0:
                 phi[j] = phi[j - 1] - 0.5 * (a + a_prev) * (z - z_prev)
             a_prev, z_prev = a, z
@@ -72,6 +72,24 @@ def hydrostatic_density(r_faces, theta_faces, rho_mask, T, shell_mass, M_star=2.
         prof = np.where(m, np.exp(lg - lg[m].max()), 0.0)
         rho[i] = prof * (shell_mass[i] / (prof * V[i]).sum())
     return rho
+
+
+def relaxed_density(r_faces, theta_faces, rho_cur, rho_h, a, shell_mass):
+    """A damped step of the structure iteration (a reading: the paper iterates without damping): per radial
+    shell i, log rho = (1 - a_i) log rho_cur + a_i log rho_h in the cells where both are positive (zero
+    elsewhere), rescaled so that the shell keeps its mass. a_i = 1 returns rho_h."""
+    V = cell_volumes(r_faces, theta_faces)
+    rho_cur, rho_h = np.asarray(rho_cur, np.float64), np.asarray(rho_h, np.float64)
+    out = np.array(rho_h, copy=True)
+    for i, ai in enumerate(np.asarray(a, np.float64)):
+        if ai == 1.0:
+            continue
+        ok = (rho_cur[i] > 0) & (rho_h[i] > 0)
+        v = np.zeros_like(rho_h[i])
+        v[ok] = np.exp((1.0 - ai) * np.log(rho_cur[i][ok]) + ai * np.log(rho_h[i][ok]))
+        tot = (v * V[i]).sum()
+        out[i] = v * (shell_mass[i] / tot) if tot > 0 else 0.0
+    return out
 
 
 def isothermal_shell_density(r_faces, theta_faces, i, T, M_star=2.5 * M_SUN, mu=2.3):

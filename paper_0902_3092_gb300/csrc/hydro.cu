@@ -24,10 +24,11 @@ constexpr double kG = 6.67430e-8;  // cm^3 g^-1 s^-2
 __global__ void k_hydro(int nr, int nt, const double* __restrict__ rf, const double* __restrict__ tf,
                         const double* __restrict__ T, const double* __restrict__ rho_cur,
                         const double* __restrict__ shell_mass, double GM, double mu, double T_floor,
-                        double* __restrict__ rho_out) {
+                        const double* __restrict__ relax, double* __restrict__ rho_out) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= nr) return;
   hydro_shell(i, nt, rf, tf, T, rho_cur, shell_mass, GM, mu, T_floor, rho_out);
+  if (relax) hydro_relax(i, nt, rf, tf, rho_cur, relax[i], shell_mass, rho_out);
 }
 
 }  // namespace
@@ -50,6 +51,7 @@ void mcrt_default_hydro_opts(mcrt_hydro_opts* o) {
   o->T_floor_K = 10.0;
   o->which = MCRT_T_PDA;
   o->shell_mass_g = nullptr;
+  o->relax = nullptr;
 }
 
 mcrt_status mcrt_hydrostatic_density(mcrt_disk* d, const mcrt_hydro_opts* o, double* rho_out) {
@@ -74,12 +76,19 @@ mcrt_status mcrt_hydrostatic_density(mcrt_disk* d, const mcrt_hydro_opts* o, dou
     for (int i = 0; i < nr; ++i)
       for (int j = 0; j < nt; ++j) M[i] += d->mass[(size_t)i * nt + j];
   }
+  if (o->relax)
+    for (int i = 0; i < nr; ++i)
+      if (!(o->relax[i] > 0.0 && o->relax[i] <= 2.0)) return set_error(d, MCRT_EINVAL, "relax must be in (0, 2]");
   CK(cudaSetDevice(d->device), "cudaSetDevice");
   if (!d->have_T) {
     mcrt_status s = compute_temperatures(d);
     if (s != MCRT_OK) return s;
   }
-  DBuf rf, tf, Md, out;
+  DBuf rf, tf, Md, out, rl;
+  if (o->relax) {
+    CK(rl.alloc(nr * 8), "cudaMalloc");
+    CK(cudaMemcpyAsync(rl.p, o->relax, nr * 8, cudaMemcpyHostToDevice, d->stream), "copy");
+  }
   CK(rf.alloc((nr + 1) * 8), "cudaMalloc");
   CK(tf.alloc((nt + 1) * 8), "cudaMalloc");
   CK(Md.alloc(nr * 8), "cudaMalloc");
@@ -91,7 +100,7 @@ mcrt_status mcrt_hydrostatic_density(mcrt_disk* d, const mcrt_hydro_opts* o, dou
   const double* T = (o->which == MCRT_T_PDA ? d->T_pda : d->T_mc).as<double>();
   k_hydro<<<(nr + 127) / 128, 128, 0, st>>>(nr, nt, rf.as<double>(), tf.as<double>(), T, d->rho_cgs_d.as<double>(),
                                             Md.as<double>(), kG * o->M_star_g, o->mu, o->T_floor_K,
-                                            out.as<double>());
+                                            o->relax ? rl.as<double>() : nullptr, out.as<double>());
   d->launches++;
   CK(cudaGetLastError(), "hydrostatic kernel");
   CK(cudaMemcpyAsync(rho_out, out.p, n * 8, cudaMemcpyDeviceToHost, st), "copy");

@@ -55,4 +55,25 @@ __host__ __device__ inline void hydro_shell(int i, int nt, const double* rf, con
   for (int j = 0; j < nt; ++j) rho_out[row + j] *= s;
 }
 
+// Relaxed update of shell i: log rho_new = (1 - a) log rho_cur + a log rho_h in the cells with dust, then
+// the shell rescaled to its mass (a damped step of the structure iteration; a = 1 leaves rho_h as it is).
+// rho_h: in the Eq. 20 density of the shell (hydro_shell), out the relaxed one.
+__host__ __device__ inline void hydro_relax(int i, int nt, const double* rf, const double* tf, const double* rho_cur,
+                                            double a, const double* shell_mass, double* rho_h) {
+  if (a == 1.0) return;
+  const size_t row = (size_t)i * nt;
+  const double r1 = rf[i], r2 = rf[i + 1];
+  const double sh = 2.0 * kPi / 3.0 * (r2 * r2 * r2 - r1 * r1 * r1);
+  double sum = 0.0;
+  for (int j = 0; j < nt; ++j) {
+    const double c = rho_cur[row + j], h = rho_h[row + j];
+    const double v = (c > 0.0 && h > 0.0) ? exp((1.0 - a) * log(c) + a * log(h)) : 0.0;
+    rho_h[row + j] = v;
+    sum += v * (sh * (cos(tf[j]) - cos(tf[j + 1])));
+  }
+  const double M = shell_mass[i];
+  const double s = sum > 0.0 ? M / sum : 0.0;
+  for (int j = 0; j < nt; ++j) rho_h[row + j] *= s;
+}
+
 }  // namespace mcrt

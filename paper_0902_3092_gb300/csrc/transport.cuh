@@ -87,6 +87,8 @@ struct Pkt {
 
 // packets that had taken this many steps when the queue drained go first in the tail kernel
 constexpr unsigned kTailLongSteps = 20000u;
+// 32-thread blocks of the tail kernel resident per SM by default (its register budget: 65536 / (32 x 20))
+constexpr int kTailBlocksPerSm = 20;
 
 // Per-lane run counters, flushed once per launch (32-bit: a lane's share of a launch stays far below 2^32)
 struct Acc {
@@ -163,7 +165,7 @@ __device__ __forceinline__ bool lead() { return !RNG::coop || (threadIdx.x & 31u
 // 14 optical depth left, 15 safety distance.
 constexpr int kTripWords = 16;
 template <class R, class RNG>
-__device__ __noinline__ void note_trip(const KParams<R>& P, const DevModel<R>& M, const Pkt<R>& s, unsigned kind) {
+__device__ __forceinline__ void note_trip(const KParams<R>& P, const DevModel<R>& M, const Pkt<R>& s, unsigned kind) {
   if (!lead<RNG>()) return;
   atomicAdd(M.cnt + C_GUARDS, 1ull);
   unsigned long long* t = P.trip;
@@ -650,9 +652,113 @@ __device__ __forceinline__ void j_walk(const DevModel<R>& M, int c, R ct, int k,
   }
 }
 
+// The faces of one cell as d_min needs them, loaded once for a chain of jumps inside the cell.
+struct CellFaces {
+  float rlo, rhi, cl, sl, cu, su;
+  bool hasl, hasu;
+};
+
+__device__ __forceinline__ CellFaces cell_faces(const DevModel<float>& M, int ir, int it) {
+  CellFaces f;
+  f.rlo = M.rf[ir];
+  f.rhi = M.rf[ir + 1];
+  f.cl = M.cf[it];
+  f.sl = M.sf[it];
+  f.cu = M.cf[it + 1];
+  f.su = M.sf[it + 1];
+  f.hasl = M.fk[it] != 2;
+  f.hasu = M.fk[it + 1] != 2;
+  return f;
+}
+
+// dmin_cell<float> with the cell's faces in registers (the same arithmetic)
+__device__ __forceinline__ float dmin_faces(const CellFaces& f, float px, float py, float pz) {
+  const float rc2 = px * px + py * py;
+  const float r = sqrtf(rc2 + pz * pz);
+  const float rc = sqrtf(rc2);
+  const float d0 = fminf(r - f.rlo, f.rhi - r);
+  const float dl = f.hasl ? fabsf(rc * f.cl - pz * f.sl) : inf_<float>();
+  const float du = f.hasu ? fabsf(rc * f.cu - pz * f.su) : inf_<float>();
+  return fmaxf(fminf(d0, fminf(dl, du)), 0.f);
+}
+
+// The MRW chain of a packet that all 32 lanes of a warp carry (tail kernel; gray dust, FP32, isotropic
+// direction after a jump). What a jump draws -- its escape-time quantile, the point on the sphere, the exit
+// bin's uniform and the new direction -- does not depend on where the packet is, so the lanes evaluate the
+// next 16 jumps at once (lane 2k the first of jump k's two blocks, lane 2k+1 the second); only
+// p <- p + d_min(p) h_k, with the Eq. 11 test at every point, runs jump after jump. The draws and the
+// arithmetic of each jump are mrw_chain's; the deposits of the jumps of one cell are one atomic.
+__device__ __forceinline__ void mrw_chain_warp(const KParams<float>& P, WarpRng& rng, const DevModel<float>& M,
+                                               Pkt<float>& s, int c, Acc& acc) {
+  const unsigned lane = threadIdx.x & 31u;
+  const unsigned full = 0xffffffffu;
+  const float rho = M.rho[c];
+  const float chiR = M.chiR0, kb = M.kbar0;
+  const CellFaces f = cell_faces(M, s.ir, s.it);
+  bool more = true;
+  while (more) {
+    const uint32_t blk0 = s.blk;
+    const uint4 w = philox_block(blk0 + lane, s.model, s.plo, s.phi, rng.key.k0, rng.key.k1);
+    rng.base = blk0;  // the lanes now hold blocks blk0 .. blk0 + 31: later events reuse them
+    rng.mine = w;
+    // even lanes: jump k's first block (quantile, point on the sphere, exit-bin uniform); odd lanes: its
+    // second block (new direction). Every lane evaluates both forms; each keeps the one it serves.
+    const float x = mrw_x(P, uni<float>(w.x));
+    float hx, hy, hz, nx, ny, nz;
+    iso_dir<float>(w.y, w.z, hx, hy, hz);
+    iso_dir<float>(w.x, w.y, nx, ny, nz);
+    const float ul = uni<float>(w.w);
+    unsigned long long dep = 0ull;
+    int k = 0;
+    more = false;
+    for (; k < 16; ++k) {
+      if (s.events >= P.max_events) break;
+      const float dm = dmin_faces(f, s.px, s.py, s.pz);
+      s.dsafe = dm * dsafe_margin<float>();
+      if (!(dm * rho * chiR > P.gamma)) break;  // Eq. 11
+      const float xk = __shfl_sync(full, x, 2 * k);
+      const float tau0 = dm * rho;
+      const float E = 3.f * xk * tau0 * tau0 * chiR * kb;  // Eq. 9, as mrw_chain
+      float units = floorf(E * (float)kEUnit + 0.5f);
+      if (!(units < 1.8e19f)) {
+        units = 1.8e19f;
+        acc.err |= kErrMrwClip;
+      }
+      dep += (unsigned long long)units;
+      s.px += dm * __shfl_sync(full, hx, 2 * k);
+      s.py += dm * __shfl_sync(full, hy, 2 * k);
+      s.pz += dm * __shfl_sync(full, hz, 2 * k);
+      s.events++;
+      acc.mrw++;
+      s.dsafe = 0.f;
+      more = k == 15;
+    }
+    if (k > 0) {
+      if (lane == 0) atomicAdd(M.tally + c, dep);
+      add_deposit(acc, dep);
+      const int last = 2 * (k - 1);
+      s.ux = __shfl_sync(full, nx, last + 1);
+      s.uy = __shfl_sync(full, ny, last + 1);
+      s.uz = __shfl_sync(full, nz, last + 1);
+      if (P.want_lam) {  // the exit bin of the last jump, drawn at escape
+        s.pend_mode = 2;
+        s.pend_cell = c;
+        s.pend_u = __shfl_sync(full, ul, last);
+      }
+      s.blk = blk0 + 2u * (unsigned)k;
+    }
+  }
+}
+
 template <class R, bool TRACE, bool G, bool POL = false, bool JT = false, class RNG>
 __device__ __forceinline__ void mrw_chain(const KParams<R>& P, RNG& rng, const DevModel<R>& M, Pkt<R>& s, int c,
                                           Acc& acc) {
+  if constexpr (RNG::coop && sizeof(R) == 4 && !TRACE && !POL && !JT) {
+    if ((G || M.gray) && P.exit_dir == 0) {
+      mrw_chain_warp(P, rng, M, s, c, acc);
+      return;
+    }
+  }
   const R rho = M.rho[c];
   for (;;) {
     if (s.events >= P.max_events) break;
@@ -1132,7 +1238,7 @@ __device__ __forceinline__ int interactions_at_once(const KParams<R>& P, WarpRng
 // and the result are the same) and this kernel runs them one per warp: lane 0 of each 32-thread block
 // takes packets from the pool, those that had taken at least kTailLongSteps steps first.
 template <class R, bool TRACE, bool G, bool BATCH, bool POL = false, bool JT = false>
-__global__ void __launch_bounds__(32) transport_tail_kernel(const KParams<R> P) {
+__global__ void __launch_bounds__(32, kTailBlocksPerSm) transport_tail_kernel(const KParams<R> P) {
   const unsigned lane = threadIdx.x & 31u;
   if (TRACE && lane != 0) return;  // the debug trace runs one lane per packet
   Acc acc = Acc{};

@@ -18,7 +18,7 @@ template <>
 cudaError_t launch_transport_tail<float>(const KParams<float>& P, bool trace, bool batch, bool gray, int sms,
                                          int warps_per_sm, cudaStream_t st) {
   if (trace) return cudaErrorInvalidValue;
-  const int grid = sms * (warps_per_sm > 0 ? warps_per_sm : 20);
+  const int grid = sms * (warps_per_sm > 0 ? warps_per_sm : kTailBlocksPerSm);
   if (batch) transport_tail_kernel<float, false, false, true><<<grid, 32, 0, st>>>(P);
   else if (gray) transport_tail_kernel<float, false, true, false><<<grid, 32, 0, st>>>(P);
   else transport_tail_kernel<float, false, false, false><<<grid, 32, 0, st>>>(P);

@@ -22,7 +22,7 @@ template <>
 cudaError_t launch_transport_tail<double>(const KParams<double>& P, bool trace, bool batch, bool gray, int sms,
                                           int warps_per_sm, cudaStream_t st) {
   if (batch) return cudaErrorInvalidValue;
-  const int grid = sms * (warps_per_sm > 0 ? warps_per_sm : 20);
+  const int grid = sms * (warps_per_sm > 0 ? warps_per_sm : kTailBlocksPerSm);
   if (trace) {
     if (gray) transport_tail_kernel<double, true, true, false><<<grid, 32, 0, st>>>(P);
     else transport_tail_kernel<double, true, false, false><<<grid, 32, 0, st>>>(P);

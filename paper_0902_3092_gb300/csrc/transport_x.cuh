@@ -16,7 +16,7 @@ cudaError_t launch_x(const KParams<R>& P, bool gray, int grid, int block, cudaSt
 
 template <class R, bool POL, bool JT>
 cudaError_t launch_tail_x(const KParams<R>& P, bool gray, int sms, int warps_per_sm, cudaStream_t st) {
-  const int grid = sms * (warps_per_sm > 0 ? warps_per_sm : 20);
+  const int grid = sms * (warps_per_sm > 0 ? warps_per_sm : kTailBlocksPerSm);
   if (gray) transport_tail_kernel<R, false, true, false, POL, JT><<<grid, 32, 0, st>>>(P);
   else transport_tail_kernel<R, false, false, false, POL, JT><<<grid, 32, 0, st>>>(P);
   return cudaGetLastError();

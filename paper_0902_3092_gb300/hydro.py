@@ -3,9 +3,19 @@
 Transport -> temperatures (Monte Carlo + PDA) -> density in hydrostatic equilibrium with them
 (`Disk.hydrostatic_density`, one GPU thread per radial shell) -> transport again, until the mean
 change of the temperatures between two iterations is below `tol_sigma` (3) of their Monte Carlo
-errors, as the paper's convergence criterion states. Each radial shell keeps its dust mass.
+errors, as the paper's convergence criterion states (the statistic, a driver-side reading, is
+`temperature_change`). Each radial shell keeps its dust mass.
 
-    python -m paper_0902_3092_gb300.hydro [--packets 1e7] [--iterations 8]
+Two schemes. "picard", the paper's: the next density is the Eq. 20 density of the last temperatures.
+"adjoint": a damped step per radial shell, log rho <- log rho + a_i (log rho_Eq20 - log rho), with
+a_i = min(1, 1/k) / (1 - g_i) at update k. g_i is the shell's loop gain, the response of its midplane
+temperature to itself through one update: the PDA adjoint (Sect. 2.2.1; d T_mid / d log rho of every
+cell, the Monte Carlo boundary held) times the response of the Eq. 20 density to a uniform scaling of
+the shell's temperatures at fixed mass. 1/(1 - g_i) is the Newton step of that linear map, and the 1/k
+factor (a Robbins-Monro schedule) averages the Monte Carlo noise of the successive temperature fields
+instead of letting the density follow it.
+
+    python -m paper_0902_3092_gb300.hydro [--packets 1e7] [--iterations 8] [--scheme adjoint]
 """
 from __future__ import annotations
 
@@ -21,19 +31,66 @@ from . import disks, mcrt
 
 def temperature_change(T_old, err_old, T_new, err_new):
     """Mean |T_new - T_old| / sqrt(sigma_old^2 + sigma_new^2), sigma = T * relative error, over the cells
-    that have a Monte Carlo error estimate in both iterations."""
-    s_old, s_new = T_old * err_old, T_new * err_new
-    ok = (T_old > 0) & (T_new > 0) & np.isfinite(s_old) & np.isfinite(s_new) & (s_old > 0) & (s_new > 0)
+    that have a Monte Carlo error estimate in both iterations (a reading of the paper's 3-sigma criterion:
+    the relative error is the counting error 1/(4 sqrt N) of each cell)."""
+    ok = (T_old > 0) & (T_new > 0) & np.isfinite(err_old) & np.isfinite(err_new) & (err_old > 0) & (err_new > 0)
     if not ok.any():
         return float("inf")
-    return float(np.mean(np.abs(T_new[ok] - T_old[ok]) / np.hypot(s_old[ok], s_new[ok])))
+    s_old, s_new = T_old[ok] * err_old[ok], T_new[ok] * err_new[ok]
+    return float(np.mean(np.abs(T_new[ok] - T_old[ok]) / np.hypot(s_old, s_new)))
+
+
+def midplane_rows(ntheta):
+    j = ntheta // 2
+    return [j - 1, j]
+
+
+def shell_gains(g, T, rho_h, T_floor=10.0):
+    """Loop gain g_i of each radial shell: sum_j (d log T_mid,i / d log rho_ij) delta_ij.
+
+    d log T_mid,i / d log rho_ij: the PDA adjoint of J_i = the shell's mean midplane temperature (the two
+    polar rows next to theta = pi/2), divided by J_i; zero where the midplane has no PDA cell (the Monte
+    Carlo temperatures are held). delta_ij = d log rho_ij / d log T of the Eq. 20 density rho_h for a
+    uniform scaling of the shell's temperatures at fixed mass: rho_j is proportional to exp(Phi_j) / T_j
+    with Phi inversely proportional to T, so delta_j = -(Phi_j - <Phi>), <.> weighted by cell mass, and
+    Phi_j = log(rho_j T_j) up to a constant of the shell."""
+    nr, nt = T.shape
+    rows = midplane_rows(nt)
+    Tc = np.maximum(T, T_floor)
+    V = g_cell_volumes(g)
+    gains = np.zeros(nr)
+    for i in range(nr):
+        J = float(np.mean(T[i, rows]))
+        m = rho_h[i] > 0
+        if not (J > 0) or not m.any():
+            continue
+        w = np.zeros((nr, nt))
+        w[i, rows] = 1.0 / len(rows)
+        dlr, _ = g.pda_adjoint(w)
+        phi = np.log(rho_h[i][m] * Tc[i][m])
+        wm = rho_h[i][m] * V[i][m]
+        delta = -(phi - np.sum(wm * phi) / np.sum(wm))
+        gains[i] = float(np.sum(dlr[i][m] * delta)) / J
+    return gains
+
+
+def g_cell_volumes(g):
+    rf, tf = g._rf, g._tf
+    return (2.0 * np.pi / 3.0) * (rf[1:] ** 3 - rf[:-1] ** 3)[:, None] * (np.cos(tf[:-1]) - np.cos(tf[1:]))[None, :]
 
 
 def iterate(model, packets, max_iter=8, seed=1, mrw=True, gamma=2.0, max_events=1e6, pda=True, min_visits=30,
-            M_star_g=None, tol_sigma=3.0, disk=None):
-    """Runs the iteration on `model` (a disks.Disk); returns the mcrt.Disk and one record per iteration."""
+            M_star_g=None, tol_sigma=3.0, disk=None, scheme="picard", on_update=None):
+    """Runs the iteration on `model` (a disks.Disk); returns the mcrt.Disk and one record per iteration.
+    scheme: "picard" or "adjoint" (see the module docstring; "adjoint" needs the PDA). on_update(rho_cur,
+    relax, rho_new): called with each update's current density, step factors (None for Picard) and new
+    density, e.g. to check them."""
+    if scheme not in ("picard", "adjoint"):
+        raise ValueError("scheme must be picard or adjoint")
+    if scheme == "adjoint" and not pda:
+        raise ValueError("the adjoint scheme needs the PDA")
     g = disk if disk is not None else mcrt.Disk.from_model(model)
-    hist, prev = [], None
+    hist, prev, k = [], None, 0
     for it in range(max_iter):
         t0 = time.perf_counter()
         g.reset()
@@ -53,7 +110,19 @@ def iterate(model, packets, max_iter=8, seed=1, mrw=True, gamma=2.0, max_events=
             rec["wall_s"] = time.perf_counter() - t0
             hist.append(rec)
             break
-        rho = g.hydrostatic_density(M_star_g=M_star_g, which=mcrt.T_PDA if pda else mcrt.T_MC)
+        which = mcrt.T_PDA if pda else mcrt.T_MC
+        rho_cur = g.density() if on_update is not None or scheme == "adjoint" else None
+        relax = None
+        if scheme == "adjoint":
+            k += 1
+            rho_h = g.hydrostatic_density(M_star_g=M_star_g, which=which)
+            gains = shell_gains(g, T, rho_h)
+            relax = np.clip(min(1.0, 1.0 / k) / (1.0 - gains), 0.05, 2.0)
+            rec["gain_range"] = [float(gains.min()), float(gains.max())]
+            rec["relax_mean"] = float(relax.mean())
+        rho = g.hydrostatic_density(M_star_g=M_star_g, which=which, relax=relax)
+        if on_update is not None:
+            on_update(rho_cur, relax, rho)
         g.set_density(rho)
         rec["wall_s"] = time.perf_counter() - t0
         hist.append(rec)
@@ -67,10 +136,11 @@ def main(argv=None):
     p.add_argument("--nr", type=int, default=200)
     p.add_argument("--ntheta", type=int, default=120)
     p.add_argument("--tau", type=float, default=1e6)
+    p.add_argument("--scheme", default="picard", choices=["picard", "adjoint"])
     a = p.parse_args(argv)
     d = disks.config_thick_gray(a.nr, a.ntheta, a.tau)
     _, hist = iterate(d, int(a.packets), max_iter=a.iterations,
-                      min_visits=max(30, int(30 * a.packets / 1e5)))
+                      min_visits=max(30, int(30 * a.packets / 1e5)), scheme=a.scheme)
     for h in hist:
         print(json.dumps(h), flush=True)
 

@@ -78,7 +78,7 @@ class PdaOpts(C.Structure):
 
 class HydroOpts(C.Structure):
     _fields_ = [("M_star_g", C.c_double), ("mu", C.c_double), ("T_floor_K", C.c_double), ("which", C.c_int),
-                ("shell_mass_g", C.POINTER(C.c_double))]
+                ("shell_mass_g", C.POINTER(C.c_double)), ("relax", C.POINTER(C.c_double))]
 
 
 _lib = None
@@ -253,8 +253,9 @@ class Disk:
     def reset(self):
         _check(lib().mcrt_reset(self._h), self._h)
 
-    def hydrostatic_density(self, M_star_g=None, mu=None, T_floor=None, which=T_PDA, shell_mass=None):
-        """Density in hydrostatic equilibrium with the disk's temperatures (Sect. 2.5, Eq. 20), nr x ntheta."""
+    def hydrostatic_density(self, M_star_g=None, mu=None, T_floor=None, which=T_PDA, shell_mass=None, relax=None):
+        """Density in hydrostatic equilibrium with the disk's temperatures (Sect. 2.5, Eq. 20), nr x ntheta;
+        relax (nr factors): a damped step per shell from the disk's current density (see mcrt.h)."""
         o = HydroOpts()
         lib().mcrt_default_hydro_opts(C.byref(o))
         if M_star_g is not None:
@@ -268,6 +269,12 @@ class Disk:
         if shell_mass is not None:
             sm = np.ascontiguousarray(shell_mass, np.float64)
             o.shell_mass_g = _dp(sm)
+        rl = None
+        if relax is not None:
+            rl = np.ascontiguousarray(relax, np.float64)
+            if rl.shape != (self.nr,):
+                raise ValueError("relax needs one factor per radial shell")
+            o.relax = _dp(rl)
         out = np.zeros(self.nr * self.ntheta)
         _check(lib().mcrt_hydrostatic_density(self._h, C.byref(o), _dp(out)), self._h)
         return out.reshape(self.nr, self.ntheta)
@@ -315,8 +322,13 @@ class Disk:
 
     def set_density(self, rho):
         """Replaces the density (g/cm^3) and resets the tallies."""
-        r = np.ascontiguousarray(rho, np.float64).ravel()
+        r = np.ascontiguousarray(rho, np.float64).ravel().copy()
         _check(lib().mcrt_set_density(self._h, _dp(r)), self._h)
+        self._rho = r
+
+    def density(self):
+        """The density the disk holds (g/cm^3, nr x ntheta): the one it was created or last set with."""
+        return self._rho.reshape(self.nr, self.ntheta).copy()
 
     def temperatures(self, which=T_MC):
         n = self.nr * self.ntheta

@@ -50,3 +50,31 @@ def test_hydro_shell_matches_oracle(lib):
     assert big.sum() > 500
     assert np.max(np.abs(got[big] / want[big] - 1)) < 1e-12
     assert np.allclose(H.shell_masses(d.r_faces_cm, d.theta_faces, got), shell, rtol=1e-12, atol=0)
+
+
+def test_hydro_relax_matches_oracle(lib):
+    """The damped step of the structure iteration (hydro.cuh: hydro_relax) against the oracle's
+    relaxed_density: the same density to 1e-12 for factors 0.3, 1 and 1.7 across the shells, the shells'
+    masses kept, dust-free cells empty."""
+    from oracle import hydro as H
+    d = disks.config_thick_gray(40, 30, 1e4)
+    rho = d.rho.copy()
+    rho[5, :4] = 0.0
+    rng = np.random.default_rng(4)
+    rc = 0.5 * (d.r_faces_cm[1:] + d.r_faces_cm[:-1])
+    T = 300.0 * (rc[:, None] / disks.AU_CM) ** -0.5 * np.exp(0.2 * rng.standard_normal(rho.shape))
+    shell = H.shell_masses(d.r_faces_cm, d.theta_faces, rho)
+    Ms = 2.5 * H.M_SUN
+    rho_h = H.hydrostatic_density(d.r_faces_cm, d.theta_faces, rho > 0, T, shell, M_star=Ms, mu=2.3, T_floor=10.0)
+    a = np.array([(0.3, 1.0, 1.7)[i % 3] for i in range(d.nr)])
+    want = H.relaxed_density(d.r_faces_cm, d.theta_faces, rho, rho_h, a, shell)
+    P = lambda x: np.ascontiguousarray(x, np.float64).ctypes.data_as(C.c_void_p)
+    got = np.ascontiguousarray(rho_h, np.float64).ravel().copy()
+    lib.host_hydro_relax(d.nr, d.ntheta, P(d.r_faces_cm), P(d.theta_faces), P(rho.ravel()), P(a), P(shell),
+                         got.ctypes.data_as(C.c_void_p))
+    got = got.reshape(rho.shape)
+    assert np.all(got[rho == 0] == 0)
+    big = want > 1e-200 * want.max()
+    assert big.sum() > 500
+    assert np.max(np.abs(got[big] / want[big] - 1)) < 1e-12
+    assert np.allclose(H.shell_masses(d.r_faces_cm, d.theta_faces, got), shell, rtol=1e-12, atol=0)

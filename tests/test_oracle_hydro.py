@@ -2,6 +2,8 @@
 balance along a radial shell."""
 import numpy as np
 
+from paper_0902_3092_gb300 import disks
+
 from oracle import hydro as H
 
 AU = 1.495978707e13
@@ -77,3 +79,28 @@ def test_convergence_statistic():
     f = 1 + 0.03
     T2 = T * f  # |dT| = 0.03 T against sigma = 0.01 T sqrt(1 + f^2)
     assert abs(H.convergence(T, e, T2, e) - 3.0 / np.sqrt(1 + f * f)) < 1e-12
+
+
+def test_relaxed_density_limits_and_mass():
+    """The damped step: a = 1 gives the Eq. 20 density, a = 0 the current density (both already at the
+    shell's mass), a = 1/2 the normalised geometric mean; every shell keeps its mass."""
+    from oracle import hydro as H
+    d = disks.config_thick_gray(20, 16, 1e4)
+    rng = np.random.default_rng(9)
+    shell = H.shell_masses(d.r_faces_cm, d.theta_faces, d.rho)
+    rc = 0.5 * (d.r_faces_cm[1:] + d.r_faces_cm[:-1])
+    T = 200.0 * (rc[:, None] / disks.AU_CM) ** -0.5 * np.exp(0.2 * rng.standard_normal(d.rho.shape))
+    rho_h = H.hydrostatic_density(d.r_faces_cm, d.theta_faces, d.rho > 0, T, shell)
+    one = H.relaxed_density(d.r_faces_cm, d.theta_faces, d.rho, rho_h, np.ones(d.nr), shell)
+    assert np.array_equal(one, rho_h)
+    zero = H.relaxed_density(d.r_faces_cm, d.theta_faces, d.rho, rho_h, np.zeros(d.nr), shell)
+    ok = (d.rho > 0) & (rho_h > 0)
+    assert np.allclose(zero[ok], d.rho[ok], rtol=1e-12, atol=0)
+    half = H.relaxed_density(d.r_faces_cm, d.theta_faces, d.rho, rho_h, np.full(d.nr, 0.5), shell)
+    with np.errstate(divide="ignore"):
+        gm = np.where(ok, np.exp(0.5 * np.log(d.rho) + 0.5 * np.log(rho_h)), 0.0)  # sqrt(rho rho_h) without underflow
+    V = H.cell_volumes(d.r_faces_cm, d.theta_faces)
+    gm *= (shell / (gm * V).sum(1))[:, None]
+    assert np.allclose(half, gm, rtol=1e-12, atol=0)
+    for x in (one, zero, half):
+        assert np.allclose(H.shell_masses(d.r_faces_cm, d.theta_faces, x), shell, rtol=1e-12, atol=0)
