@@ -89,6 +89,19 @@ mcrt_status mcrt_disk_create(const mcrt_grid *grid, const mcrt_star *star, int d
 mcrt_status mcrt_set_opacity(mcrt_disk *d, int nlam, const double *lam_edges_um, const double *kappa_abs,
                              const double *kappa_sca, const double *g);
 
+/* Packets in flight with non-gray dust. The Bjorkman-Wood re-emission (Sect. 2.1) draws a packet's new
+ * wavelength from the temperatures of the moment, and with non-gray dust the wavelength steers the packet.
+ * The temperatures then telescope exactly to the final spectrum in every cell, but in a very thick cell
+ * whether a re-emitted packet is absorbed there again depends on where in the cell it is, and that
+ * correlation depends on the order of the events. A run with many of its packets in flight at once
+ * (one per GPU thread) is therefore not the one-packet-after-another run of the method: with 12 % of a
+ * 1e6-packet run in flight, the inner-rim midplane of a tau_mid = 1e5 disk came out 17 % too hot and
+ * escape-spectrum bins shifted by up to 20 %; the shift fell to noise level as the share in flight
+ * went to 0.1 %. So with non-gray dust and max_in_flight = 0, at most n_total / MCRT_NONGRAY_IN_FLIGHT
+ * packets are in flight (at least one warp); gray dust, whose trajectories no temperature changes, uses
+ * the whole device. Batches interleave their models' packets so that each model keeps this share. */
+#define MCRT_NONGRAY_IN_FLIGHT 1000
+
 typedef struct {
   int precision;                /* 32: production path; 64: debug path whose gray trajectories match
                                    the FP64 oracle event by event */
@@ -110,6 +123,10 @@ typedef struct {
                                    tail kernel, they finish in the transport kernel) */
   int interact_batch;           /* a warp runs the interaction code once this many of its lanes wait at
                                    an interaction point (or none can move on); 1: no waiting; 0: 8 */
+  uint64_t max_in_flight;       /* at most this many packets in flight at once (the transport launch's
+                                   threads, rounded up to whole blocks); 0: one per thread the device
+                                   holds for gray dust, n_total / MCRT_NONGRAY_IN_FLIGHT for non-gray
+                                   dust (see there) */
 } mcrt_run_opts;
 
 void mcrt_default_run_opts(mcrt_run_opts *o);

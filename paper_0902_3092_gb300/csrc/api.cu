@@ -8,6 +8,7 @@
 #include <cstdio>
 #include <cstring>
 #include <mutex>
+#include <queue>
 #include <string>
 #include <vector>
 
@@ -317,6 +318,7 @@ void mcrt_default_run_opts(mcrt_run_opts* o) {
   o->refill_interval = 0;
   o->tail_warps_per_sm = 0;
   o->interact_batch = 0;
+  o->max_in_flight = 0;
   o->want_sed = 1;
 }
 
@@ -626,6 +628,44 @@ static bool setup_pool(mcrt_disk* d, KParams<R>& P, unsigned cap, int tail_warps
   return true;
 }
 
+// blocks of a single-disk transport launch: one packet per thread, at most the device's resident blocks,
+// and at most max_in_flight threads (whole blocks) when given
+static int transport_grid(uint64_t n_packets, int block, int sms, int bps, uint64_t max_in_flight) {
+  long long g = (long long)((n_packets + block - 1) / block);
+  g = std::min<long long>(g, (long long)sms * std::max(1, bps));
+  if (max_in_flight) g = std::min<long long>(g, (long long)((max_in_flight + block - 1) / block));
+  return (int)std::max(1ll, g);
+}
+
+// packets in flight of a run: the caller's cap, else all threads for gray dust and n_total /
+// MCRT_NONGRAY_IN_FLIGHT (at least one warp) for non-gray dust (see mcrt.h)
+static uint64_t in_flight_cap(bool gray, double n_total, uint64_t requested) {
+  if (requested || gray) return requested;
+  return std::max<uint64_t>(32, (uint64_t)(n_total / MCRT_NONGRAY_IN_FLIGHT));
+}
+
+// Queue of a batch with non-gray dust: chunks of 32 slots of one model, ordered so that every model moves
+// through its packets at the same pace (chunk k of model m at (k + 1/2) / chunks_m, ties by model), so that
+// each model has the launch's share of its packets in flight (see MCRT_NONGRAY_IN_FLIGHT in mcrt.h).
+// Entry: model << 48 | the model's first packet of the chunk.
+static std::vector<unsigned long long> interleaved_queue(const uint64_t* n, int models) {
+  std::vector<unsigned long long> out;
+  using Item = std::pair<double, int>;
+  std::priority_queue<Item, std::vector<Item>, std::greater<Item>> next;
+  std::vector<uint64_t> chunks(models), k(models, 0);
+  for (int i = 0; i < models; ++i) {
+    chunks[i] = (n[i] + 31) / 32;
+    if (chunks[i]) next.push({0.5 / (double)chunks[i], i});
+  }
+  while (!next.empty()) {
+    const int i = next.top().second;
+    next.pop();
+    out.push_back(((unsigned long long)i << 48) | (k[i] * 32));
+    if (++k[i] < chunks[i]) next.push({((double)k[i] + 0.5) / (double)chunks[i], i});
+  }
+  return out;
+}
+
 static mcrt_status run_impl(mcrt_disk* d, uint64_t n_packets, uint64_t seed, uint64_t first_id,
                             const mcrt_run_opts* o, mcrt_run_stats* stats, int trace_max, int32_t* tr_type,
                             int32_t* tr_cell, int32_t* tr_lam, double* tr_pos, int32_t* tr_n) {
@@ -691,8 +731,7 @@ static mcrt_status run_impl(mcrt_disk* d, uint64_t n_packets, uint64_t seed, uin
       const int bps = pol  ? transport_blocks_per_sm_pol<double>(d->gray, block)
                       : jt ? transport_blocks_per_sm_j<double>(d->gray, block)
                            : transport_blocks_per_sm<double>(trace, false, d->gray, block);
-      const long long want = (long long)((n_packets + block - 1) / block);
-      const int grid = (int)std::max(1ll, std::min<long long>(want, (long long)dev_sms * std::max(1, bps)));
+      const int grid = transport_grid(n_packets, block, dev_sms, bps, in_flight_cap(d->gray, d->n_total, o->max_in_flight));
       const bool tail = setup_pool(d, P, (unsigned)grid * block, o->tail_warps_per_sm);
       e = pol  ? launch_transport_pol<double>(P, d->gray, grid, block, d->stream)
           : jt ? launch_transport_j<double>(P, d->gray, grid, block, d->stream)
@@ -720,8 +759,7 @@ static mcrt_status run_impl(mcrt_disk* d, uint64_t n_packets, uint64_t seed, uin
       const int bps = pol  ? transport_blocks_per_sm_pol<float>(d->gray, block)
                       : jt ? transport_blocks_per_sm_j<float>(d->gray, block)
                            : transport_blocks_per_sm<float>(false, false, d->gray, block);
-      const long long want = (long long)((n_packets + block - 1) / block);
-      const int grid = (int)std::max(1ll, std::min<long long>(want, (long long)dev_sms * std::max(1, bps)));
+      const int grid = transport_grid(n_packets, block, dev_sms, bps, in_flight_cap(d->gray, d->n_total, o->max_in_flight));
       const bool tail = setup_pool(d, P, (unsigned)grid * block, o->tail_warps_per_sm);
       e = pol  ? launch_transport_pol<float>(P, d->gray, grid, block, d->stream)
           : jt ? launch_transport_j<float>(P, d->gray, grid, block, d->stream)
@@ -841,11 +879,20 @@ mcrt_status mcrt_run_batch(mcrt_disk* const* disks, int n, const uint64_t* n_pac
   bool any_nongray = false;
   for (int i = 0; i < n; ++i) any_nongray |= !disks[i]->gray;
   P.want_lam = (any_nongray || o->want_sed) ? 1 : 0;
+  DBuf qmap;
+  if (any_nongray) {  // the models' packets interleaved, each model with the launch's share in flight
+    if (n > 65535) return set_error(d, MCRT_EINVAL, "a non-gray batch takes at most 65535 disks");
+    const std::vector<unsigned long long> qm = interleaved_queue(n_packets, n);
+    CK(qmap.alloc(qm.size() * 8), "cudaMalloc");
+    CK(cudaMemcpyAsync(qmap.p, qm.data(), qm.size() * 8, cudaMemcpyHostToDevice, d->stream), "copy");
+    P.qmap = qmap.as<unsigned long long>();
+    P.total = 32ull * qm.size();
+  }
   int dev_sms = 0;
   CK(cudaDeviceGetAttribute(&dev_sms, cudaDevAttrMultiProcessorCount, d->device), "attribute");
   const int block = o->block_size ? o->block_size : 128;
   const int bps = transport_blocks_per_sm<float>(false, true, false, block);
-  const int grid = dev_sms * std::max(1, bps);
+  const int grid = transport_grid(P.total, block, dev_sms, bps, in_flight_cap(!any_nongray, (double)q, o->max_in_flight));
   cudaEvent_t ev0, ev1;
   CK(cudaEventCreate(&ev0), "event");
   CK(cudaEventCreate(&ev1), "event");
@@ -1154,7 +1201,7 @@ struct mcrt_batch {
   std::vector<mcrt_disk*> disks;
   std::vector<uint64_t> npk;
   unsigned long long total = 0;
-  DBuf models, queue;
+  DBuf models, queue, qmap;  // qmap: the interleaved queue of a non-gray batch
   KParams<float> P;
   int block = 256, refill = 1, grid = 0;
   double tune_seconds = 0.0;
@@ -1247,10 +1294,26 @@ mcrt_status mcrt_batch_create(mcrt_disk* const* disks, int n, const uint64_t* n_
   b->P.total = b->total;
   b->P.queue = b->queue.as<unsigned long long>();
   b->P.want_lam = (any_nongray || o->want_sed) ? 1 : 0;
+  if (any_nongray) {  // the models' packets interleaved, each model with the launch's share in flight
+    if (n > 65535) {
+      delete b;
+      return set_error(d, MCRT_EINVAL, "a non-gray batch takes at most 65535 disks");
+    }
+    const std::vector<unsigned long long> qm = interleaved_queue(n_packets, n);
+    e = b->qmap.alloc(qm.size() * 8);
+    if (e == cudaSuccess) e = cudaMemcpy(b->qmap.p, qm.data(), qm.size() * 8, cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) {
+      delete b;
+      return cuda_fail(d, e, "batch queue");
+    }
+    b->P.qmap = b->qmap.as<unsigned long long>();
+    b->P.total = 32ull * qm.size();
+  }
+  const uint64_t cap = in_flight_cap(!any_nongray, (double)b->total, o->max_in_flight);
   int sms = 0;
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, d->device);
   auto grid_for = [&](int block) {
-    return sms * std::max(1, transport_blocks_per_sm<float>(false, true, false, block));
+    return transport_grid(b->P.total, block, sms, transport_blocks_per_sm<float>(false, true, false, block), cap);
   };
   if (o->block_size) {
     b->block = o->block_size;
@@ -1275,6 +1338,7 @@ mcrt_status mcrt_batch_create(mcrt_disk* const* disks, int n, const uint64_t* n_
     KParams<float> T = b->P;
     T.models = tm.as<DevModel<float>>();
     T.total = tq;
+    T.qmap = nullptr;  // the tuning run takes each model's packets in one range
     cudaEvent_t e0, e1;
     cudaEventCreate(&e0);
     cudaEventCreate(&e1);

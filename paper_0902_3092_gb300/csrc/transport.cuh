@@ -45,6 +45,10 @@ struct KParams {
   R gamma;
   unsigned long long total;    // packets in the queue
   unsigned long long* queue;   // queue head (global counter)
+  // batch launches whose models' packets are interleaved: per chunk of 32 queue slots, model << 48 | the
+  // model's first packet of the chunk (slots past a model's last packet are padding); NULL: each model's
+  // packets one range of the queue (q_begin)
+  const unsigned long long* qmap;
   uint64_t seed;
   unsigned long long max_events;
   unsigned long long max_steps;  // loop guard per packet
@@ -1309,18 +1313,27 @@ __global__ void __launch_bounds__(256, transport_min_blocks<R>()) transport_kern
           const unsigned long long q = base + __popc(need & ((1u << lane) - 1u));
           if (q < P.total) {
             int m = 0;
+            unsigned long long local = q;
             if (BATCH) {
-              m = find_model(P, q);
+              if (P.qmap) {
+                const unsigned long long e = __ldg(P.qmap + (q >> 5));
+                m = (int)(e >> 48);
+                local = (e & 0xffffffffffffull) + (q & 31ull);
+              } else {
+                m = find_model(P, q);
+                local = q - P.models[m].q_begin;
+              }
               if (m != model) {
                 flush(P.models[model], acc, false);
                 model = m;
               }
             }
             const DevModel<R>& M = BATCH ? P.models[m] : P.m0;
-            const unsigned long long local = q - M.q_begin;
-            const int tslot = (TRACE && local < (unsigned long long)P.trace_n) ? (int)local : -1;
-            launch_packet<R, TRACE, G, POL, JT>(P, rng, M, s, M.first_id + local, tslot, acc);
-            active = true;
+            if (local < M.n_packets) {  // (a padding slot of an interleaved queue launches nothing)
+              const int tslot = (TRACE && local < (unsigned long long)P.trace_n) ? (int)local : -1;
+              launch_packet<R, TRACE, G, POL, JT>(P, rng, M, s, M.first_id + local, tslot, acc);
+              active = true;
+            }
           } else {
             done = true;
           }

@@ -82,9 +82,9 @@ def g_cell_volumes(g):
 def iterate(model, packets, max_iter=8, seed=1, mrw=True, gamma=2.0, max_events=1e6, pda=True, min_visits=30,
             M_star_g=None, tol_sigma=3.0, disk=None, scheme="picard", on_update=None):
     """Runs the iteration on `model` (a disks.Disk); returns the mcrt.Disk and one record per iteration.
-    scheme: "picard" or "adjoint" (see the module docstring; "adjoint" needs the PDA). on_update(rho_cur,
-    relax, rho_new): called with each update's current density, step factors (None for Picard) and new
-    density, e.g. to check them."""
+    scheme: "picard" or "adjoint" (see the module docstring; "adjoint" needs the PDA). on_update(g, rho_cur,
+    relax, rho_new): called with the disk, each update's current density, step factors (None for Picard)
+    and new density, before the new density is installed, e.g. to check them."""
     if scheme not in ("picard", "adjoint"):
         raise ValueError("scheme must be picard or adjoint")
     if scheme == "adjoint" and not pda:
@@ -122,7 +122,7 @@ def iterate(model, packets, max_iter=8, seed=1, mrw=True, gamma=2.0, max_events=
             rec["relax_mean"] = float(relax.mean())
         rho = g.hydrostatic_density(M_star_g=M_star_g, which=which, relax=relax)
         if on_update is not None:
-            on_update(rho_cur, relax, rho)
+            on_update(g, rho_cur, relax, rho)
         g.set_density(rho)
         rec["wall_s"] = time.perf_counter() - t0
         hist.append(rec)

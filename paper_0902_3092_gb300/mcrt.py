@@ -49,7 +49,7 @@ class RunOpts(C.Structure):
     _fields_ = [("precision", C.c_int), ("mrw", C.c_int), ("gamma", C.c_double), ("mrw_min_interactions", C.c_int),
                 ("mrw_exit_dir", C.c_int), ("max_events_per_packet", C.c_uint64), ("n_total_packets", C.c_uint64),
                 ("block_size", C.c_int), ("refill_interval", C.c_int), ("want_sed", C.c_int),
-                ("tail_warps_per_sm", C.c_int), ("interact_batch", C.c_int)]
+                ("tail_warps_per_sm", C.c_int), ("interact_batch", C.c_int), ("max_in_flight", C.c_uint64)]
 
 
 class RunStats(C.Structure):
@@ -165,7 +165,7 @@ def _check(status, handle=None):
 
 
 def run_opts(precision=32, mrw=False, gamma=2.0, nmin=20, exit_dir=0, max_events=100_000_000, n_total=0,
-             block_size=0, refill=0, want_sed=True, tail_warps=0, interact_batch=0):
+             block_size=0, refill=0, want_sed=True, tail_warps=0, interact_batch=0, max_in_flight=0):
     o = RunOpts()
     lib().mcrt_default_run_opts(C.byref(o))
     o.precision, o.mrw, o.gamma, o.mrw_min_interactions, o.mrw_exit_dir = precision, int(mrw), gamma, nmin, exit_dir
@@ -173,6 +173,7 @@ def run_opts(precision=32, mrw=False, gamma=2.0, nmin=20, exit_dir=0, max_events
     o.block_size, o.refill_interval, o.want_sed = block_size, refill, int(want_sed)
     o.tail_warps_per_sm = tail_warps
     o.interact_batch = interact_batch
+    o.max_in_flight = int(max_in_flight)
     return o
 
 

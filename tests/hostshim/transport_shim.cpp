@@ -22,6 +22,37 @@ void run_packets(const KParams<R>& P, const DevModel<R>& M, uint64_t n, Acc& acc
   }
 }
 
+// Packets 0 .. n-1 with up to `lanes` of them in flight at once: one step of every packet in flight per
+// round, a finished packet's slot refilled with the next id -- the order in which a persistent kernel's
+// lanes interleave their packets' events, here one after another on one thread.
+template <class R, bool G>
+void run_interleaved(const KParams<R>& P, const DevModel<R>& M, uint64_t n, uint64_t lanes, Acc& acc) {
+  std::vector<Pkt<R>> st(lanes);
+  std::vector<char> act(lanes, 0);
+  SerialRng rng{{(uint32_t)P.seed, (uint32_t)(P.seed >> 32)}};
+  uint64_t next = 0, live = 0;
+  for (uint64_t l = 0; l < lanes && next < n; ++l) {
+    std::memset(&st[l], 0, sizeof(Pkt<R>));
+    launch_packet<R, false, G>(P, rng, M, st[l], next++, -1, acc);
+    act[l] = 1;
+    ++live;
+  }
+  while (live) {
+    for (uint64_t l = 0; l < lanes; ++l) {
+      if (!act[l]) continue;
+      if (!step<R, false, G>(P, rng, M, st[l], acc)) {
+        if (next < n) {
+          std::memset(&st[l], 0, sizeof(Pkt<R>));
+          launch_packet<R, false, G>(P, rng, M, st[l], next++, -1, acc);
+        } else {
+          act[l] = 0;
+          --live;
+        }
+      }
+    }
+  }
+}
+
 template <class R>
 std::vector<R> cast(const std::vector<double>& v) {
   return std::vector<R>(v.begin(), v.end());
@@ -36,6 +67,7 @@ struct Inputs {
   double gamma;
   const double* mueller;  // [nlam][4][nmu] or NULL
   const double* Lsrc;     // internal sources: luminosity per cell (erg/s), or NULL
+  uint64_t lanes;         // > 0: packets in flight at once (run_interleaved), 0: one after another
   // replay instead of packets: {ir, itheta, px, py, pz, ux, uy, uz, tau, xcross, max_calls} (positions in
   // units of the inner radius; the values of the recorded state), or NULL
   const double* replay;
@@ -203,6 +235,9 @@ void run(const Inputs& in, const Outputs& out) {
   } else if (jt) {
     if (gray) run_packets<R, true, false, true>(P, M, in.n, acc);
     else run_packets<R, false, false, true>(P, M, in.n, acc);
+  } else if (in.lanes) {
+    if (gray) run_interleaved<R, true>(P, M, in.n, in.lanes, acc);
+    else run_interleaved<R, false>(P, M, in.n, in.lanes, acc);
   } else {
     if (gray) run_packets<R, true, false, false>(P, M, in.n, acc);
     else run_packets<R, false, false, false>(P, M, in.n, acc);
@@ -227,7 +262,7 @@ extern "C" void host_transport(int nr, int nt, const double* rf_cm, const double
                                uint64_t* visits, uint64_t* nabs, uint64_t* sed, uint64_t* sed_q, uint64_t* sed_u,
                                double* jlen, uint64_t* counters) {
   const Inputs in{nr, nt, nlam, rf_cm, tf, rho, lam_e, kabs, ksca, g, Tstar, Rstar, n, seed, mrw, nmin, want_sed, nmu,
-                  gamma, mueller, Lsrc, nullptr};
+                  gamma, mueller, Lsrc, 0, nullptr};
   const Outputs out{tally, visits, nabs, sed, sed_q, sed_u, counters, jlen, nullptr};
   if (prec == 32) run<float>(in, out);
   else run<double>(in, out);
@@ -241,10 +276,25 @@ extern "C" void host_replay(int nr, int nt, const double* rf_cm, const double* t
                             const double* lam_e, const double* kabs, const double* ksca, const double* g, double Tstar,
                             double Rstar, int prec, const double* state, int64_t* out) {
   const Inputs in{nr, nt, nlam, rf_cm, tf, rho, lam_e, kabs, ksca, g, Tstar, Rstar, 1, 1, 0, 20, 0, 0,
-                  2.0, nullptr, nullptr, state};
+                  2.0, nullptr, nullptr, 0, state};
   std::vector<uint64_t> t((size_t)nr * nt), v((size_t)nr * nt), a((size_t)nr * nt), sed((size_t)nlam * kNInc),
       cnt(8);
   const Outputs o{t.data(), v.data(), a.data(), sed.data(), nullptr, nullptr, cnt.data(), nullptr, out};
   if (prec == 32) run<float>(in, o);
   else run<double>(in, o);
+}
+
+// host_transport with `lanes` packets in flight at once (run_interleaved; unpolarized, no J tally)
+extern "C" void host_transport_interleaved(int nr, int nt, const double* rf_cm, const double* tf, const double* rho,
+                                           int nlam, const double* lam_e, const double* kabs, const double* ksca,
+                                           const double* g, double Tstar, double Rstar, uint64_t n, uint64_t seed,
+                                           int mrw, double gamma, int nmin, int want_sed, int prec, uint64_t lanes,
+                                           uint64_t* tally, uint64_t* visits, uint64_t* nabs, uint64_t* sed,
+                                           uint64_t* counters) {
+  const Inputs in{nr, nt, nlam, rf_cm, tf, rho, lam_e, kabs, ksca, g, Tstar, Rstar, n, seed, mrw, nmin, want_sed, 0,
+                  gamma, nullptr, nullptr, lanes, nullptr};
+  std::vector<uint64_t> q((size_t)nlam * kNInc), u((size_t)nlam * kNInc);
+  const Outputs out{tally, visits, nabs, sed, q.data(), u.data(), counters, nullptr, nullptr};
+  if (prec == 32) run<float>(in, out);
+  else run<double>(in, out);
 }

@@ -61,3 +61,40 @@ def test_iteration_settles(M):
     assert len(hist) >= 2 and changes[-1] < 8.0, changes
     assert len(hist) < 12  # stopped by the criterion
     assert all(h["transport_s"] > 0 for h in hist)
+
+
+def test_adjoint_scheme_reaches_the_3_sigma_criterion_before_picard(M, oracle):
+    """Sect. 2.5's criterion (mean temperature change below 3 sigma of the Monte Carlo errors) on the 40x30
+    disk of midplane optical depth 1e3 with plain Monte Carlo, 1e5 packets per iteration. Picard (the paper's
+    iteration) lets the density follow each run's noise and plateaus above 3 sigma; the adjoint scheme
+    (hydro.py: a per-shell step 1/(1 - g_i) from the PDA adjoint's loop gain, times a Robbins-Monro 1/k)
+    averages the noise and meets the criterion within 8 iterations, before Picard does. At every update
+    the library's (relaxed) density equals the oracle's Eq. 20 density relaxed the same way from the same
+    temperatures, to 1e-9."""
+    from oracle import hydro as H
+    from paper_0902_3092_gb300 import hydro
+    d = disks.config_thick_gray(40, 30, 1e3)
+    checked = []
+
+    def check(g, rho_cur, relax, rho_new):
+        T = g.temperatures(M.T_PDA)[0]
+        shell = H.shell_masses(d.r_faces_cm, d.theta_faces, rho_cur)
+        rho_h = H.hydrostatic_density(d.r_faces_cm, d.theta_faces, rho_cur > 0, T, shell, M_star=2.5 * H.M_SUN,
+                                      mu=2.3, T_floor=10.0)
+        want = rho_h if relax is None else H.relaxed_density(d.r_faces_cm, d.theta_faces, rho_cur, rho_h, relax,
+                                                             shell)
+        big = want > 1e-200 * want.max()
+        assert np.array_equal(rho_new > 0, want > 0) or np.all(np.abs(rho_new - want)[~big] <= 1e-200)
+        assert np.max(np.abs(rho_new[big] / want[big] - 1)) < 1e-9
+        checked.append(relax is not None)
+
+    _, ha = hydro.iterate(d, 100_000, max_iter=8, seed=7, mrw=False, tol_sigma=3.0, scheme="adjoint", on_update=check)
+    _, hp = hydro.iterate(d, 100_000, max_iter=8, seed=7, mrw=False, tol_sigma=3.0, scheme="picard", on_update=check)
+    ca = [h["change_sigma"] for h in ha]
+    cp = [h["change_sigma"] for h in hp]
+    assert ca[-1] < 3.0 and len(ha) < 8, ca       # the adjoint scheme met the criterion
+    first_p = next((i for i, c in enumerate(cp) if c < 3.0), None)
+    assert first_p is None or first_p > len(ha) - 1, (ca, cp)
+    assert np.mean(cp[2:]) > 3.0, cp              # Picard's plateau
+    assert any(checked) and not all(checked)
+    assert all(h["gain_range"][1] < 1.0 for h in ha if "gain_range" in h)

@@ -169,3 +169,40 @@ def test_singular_region_is_rejected(oracle):
     d = custom_disk(rf, tf, np.full((6, 6), 1e-10))
     with pytest.raises(ValueError):
         run_pda(oracle, d, np.ones((6, 6), bool), np.full((6, 6), 100.0))
+
+
+def test_thickness_threshold_of_the_pda_region(oracle):
+    """Reading of Sect. 2.2.1 ("regions of high optical depth"): an unvisited cell joins the PDA region only
+    if it is optically thick across its smallest extent at the most opaque wavelength, rho * max_b chi'_b *
+    min(dr, r dtheta) >= 1. Cells built on both sides of the threshold: one thick radially (3) but thin
+    polarly (0.5) stays out (a test of dr alone would take it in); a non-gray cell thick only at its most
+    opaque wavelength (1.5 there, 0.2 at the least) comes in (a test of the smallest chi' would leave it
+    out); lowering the threshold to 0.25 lets the polarly thin cell in, which is what the reading decides."""
+    rf = np.array([1.0, 1.3, 1.6]) * disks.AU_CM
+    tf = np.array([0.0, 1.0, 1.05, np.pi / 2, np.pi - 1.05, np.pi - 1.0, np.pi])
+    nr, nt = 2, 6
+    rc = 0.5 * (rf[:-1] + rf[1:])
+    dr = rf[1:] - rf[:-1]
+    dth = tf[1:] - tf[:-1]
+    op = disks.powerlaw_opacity(nlam=8, g=0.0)
+    chip = op.kappa_abs + op.kappa_sca
+    cmax, cmin = float(chip.max()), float(chip.min())
+    rho = np.full((nr, nt), 1e-30)
+    # (0, 1): polar extent rc dth = 0.05 rc, radial 0.3 AU: their ratio sets the two optical depths
+    ext = min(dr[0], rc[0] * dth[1])
+    assert ext == rc[0] * dth[1] < dr[0]
+    rho[0, 1] = 0.5 / (cmax * ext)            # 0.5 across the smallest extent, 0.5 dr/ext > 1 radially
+    assert rho[0, 1] * cmax * dr[0] > 1.0
+    ext2 = min(dr[1], rc[1] * dth[1])
+    rho[1, 1] = 1.5 / (cmax * ext2)           # 1.5 at the most opaque bin
+    assert rho[1, 1] * cmin * ext2 < 1.0      # thin at the least opaque one
+    d = custom_disk(rf, tf, rho, op)
+    visits = np.zeros((nr, nt))
+    relerr = np.full((nr, nt), np.inf)
+    m = oracle.pda_mask(d, visits, relerr)
+    assert not m[0, 1] and m[1, 1]
+    m2 = oracle.pda_mask(d, visits, relerr, min_cell_tau=0.25)
+    assert m2[0, 1] and m2[1, 1]
+    # a visited cell with a small error never joins, however thick
+    visits[1, 1], relerr[1, 1] = 1000, 0.01
+    assert not oracle.pda_mask(d, visits, relerr)[1, 1]
