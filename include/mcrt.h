@@ -96,11 +96,12 @@ mcrt_status mcrt_set_opacity(mcrt_disk *d, int nlam, const double *lam_edges_um,
  * correlation depends on the order of the events. A run with many of its packets in flight at once
  * (one per GPU thread) is therefore not the one-packet-after-another run of the method: with 12 % of a
  * 1e6-packet run in flight, the inner-rim midplane of a tau_mid = 1e5 disk came out 17 % too hot and
- * escape-spectrum bins shifted by up to 20 %; the shift fell to noise level as the share in flight
- * went to 0.1 %. So with non-gray dust and max_in_flight = 0, at most n_total / MCRT_NONGRAY_IN_FLIGHT
- * packets are in flight (at least one warp); gray dust, whose trajectories no temperature changes, uses
- * the whole device. Batches interleave their models' packets so that each model keeps this share. */
-#define MCRT_NONGRAY_IN_FLIGHT 1000
+ * escape-spectrum bins shifted by up to 20 %; with 0.03 % in flight the largest shift was 1.6 %, within
+ * the noise of its reference. So with non-gray dust and max_in_flight = 0, at most
+ * n_total / MCRT_NONGRAY_IN_FLIGHT packets are in flight (at least one warp); gray dust, whose
+ * trajectories no temperature changes, uses the whole device. Batches interleave their models' packets
+ * so that each model keeps this share. */
+#define MCRT_NONGRAY_IN_FLIGHT 3000
 
 typedef struct {
   int precision;                /* 32: production path; 64: debug path whose gray trajectories match
