@@ -434,19 +434,35 @@ __host__ __device__ __forceinline__ void qpos(const DevModel<R>& M, unsigned lon
 }
 
 // BW re-emission bin: smallest b with D(b) >= u D(last), D the cumulative difference spectrum
-// kappa [Bbar(T_new) - Bbar(T_old)] from the tabulated rows C[k] = cumulative kappa Bbar(T_k),
+// kappa [Bbar(T_new) - Bbar(T_old)] from the tabulated rows C[k] = cumulative kappa Bbar(T_k) (nT rows),
 // arranged so that nearby temperatures do not cancel in FP32:
-//   both in interval k:       D = shape of C[k+1] - C[k] (the interval's derivative spectrum)
+//   both in interval k:       D = the derivative spectrum at the pair's position w in the interval,
+//                             linear between the derivative spectra C[j+1] - C[j] of interval k and of
+//                             its neighbour on w's side (each taken at its interval's middle): second
+//                             order in the grid spacing; the interval's own alone next to the grid's ends
 //   adjacent intervals:       D = (1 - w_old)(C[k_old+1] - C[k_old]) + w_new (C[k_new+1] - C[k_new])
 //   further apart:            D = C(T_new) - C(T_old), both interpolated
 // Below the first grid temperature (k = 0) the spectrum is the one of the first interval.
-static __host__ __device__ __noinline__ int sample_bw_rows(const float* __restrict__ C, int nl, int ko, float wo, int kn, float wn,
-                                          float u) {
+static __host__ __device__ __noinline__ int sample_bw_rows(const float* __restrict__ C, int nl, int nT, int ko, float wo,
+                                                           int kn, float wn, float u) {
   int mode = kn <= ko ? 0 : (kn == ko + 1 ? 1 : 2);
+  // mode 0: interval j2 weighs a2 against interval kn (j2 = kn and a2 = 0 at the grid's ends, where the
+  // first interval, from 0 K, is no derivative)
+  const float w = kn == ko ? 0.5f * (wo + wn) : wn;
+  int j2 = kn;
+  float a2 = 0.f;
+  if (w >= 0.5f && kn + 2 <= nT - 1) {
+    j2 = kn + 1;
+    a2 = w - 0.5f;
+  } else if (w < 0.5f && kn >= 2) {
+    j2 = kn - 1;
+    a2 = 0.5f - w;
+  }
   auto D = [&](int b) -> float {
     if (mode == 0) {
       const float* r = C + (size_t)kn * nl;
-      return ldg(r + nl + b) - ldg(r + b);
+      const float* r2 = C + (size_t)j2 * nl;
+      return (1.f - a2) * (ldg(r + nl + b) - ldg(r + b)) + a2 * (ldg(r2 + nl + b) - ldg(r2 + b));
     }
     if (mode == 1) {
       const float* ro = C + (size_t)ko * nl;
@@ -486,7 +502,7 @@ static __host__ __device__ __noinline__ int sample_exit_rows(const float* __rest
 
 template <class R>
 __host__ __device__ __forceinline__ int sample_bw(const DevModel<R>& M, int ko, float wo, int kn, float wn, float u) {
-  return sample_bw_rows(M.cbw, M.nlam, ko, wo, kn, wn, u);
+  return sample_bw_rows(M.cbw, M.nlam, M.nT, ko, wo, kn, wn, u);
 }
 
 template <class R>

@@ -274,3 +274,43 @@ def test_grazing_rays_at_spheres_and_cones_make_progress(lib):
         if res["err"] or res["calls"] >= 5000 or res["result"] != 0:
             bad.append((k, res))
     assert not bad, bad[:5]
+
+
+def _run_interleaved(lib, d, n, lanes, seed):
+    op = d.opacity
+    arrs = [np.ascontiguousarray(x, np.float64) for x in
+            (d.r_faces_cm, d.theta_faces, d.rho.ravel(), op.lam_edges_um, op.kappa_abs, op.kappa_sca, op.g)]
+    t, v, a = (np.zeros(d.nr * d.ntheta, np.uint64) for _ in range(3))
+    sed = np.zeros(op.nlam * 10, np.uint64)
+    cnt = np.zeros(8, np.uint64)
+    P = lambda x: x.ctypes.data_as(C.c_void_p)
+    lib.host_transport_interleaved(C.c_int(d.nr), C.c_int(d.ntheta), P(arrs[0]), P(arrs[1]), P(arrs[2]),
+                                   C.c_int(op.nlam), P(arrs[3]), P(arrs[4]), P(arrs[5]), P(arrs[6]),
+                                   C.c_double(d.star.T_K), C.c_double(d.star.R_cm), C.c_uint64(n), C.c_uint64(seed),
+                                   C.c_int(0), C.c_double(2.0), C.c_int(20), C.c_int(1), C.c_int(32),
+                                   C.c_uint64(lanes), P(t), P(v), P(a), P(sed), P(cnt))
+    assert int(cnt[5] + cnt[6]) == n  # capped + escaped
+    return t.reshape(d.nr, d.ntheta)
+
+
+def test_bjorkman_wood_depends_on_how_many_packets_are_in_flight(lib):
+    """Why non-gray runs cap the packets in flight (MCRT_NONGRAY_IN_FLIGHT): the FP32 per-packet code on a
+    12x10 non-gray disk of midplane optical depth 1e5 (5e4 packets, 16 seeds each), run one packet after
+    another as Sect. 2.1's Bjorkman-Wood transport is, and with many packets in flight at once, each
+    taking one step per round as a persistent kernel's lanes do. With a tenth of the packets in flight the
+    inner-rim midplane absorbs far more energy (each re-emission's wavelength comes from temperatures the
+    other packets move, and in these thick cells the wavelength decides how long a packet stays); with
+    n / 3000 in flight, the library's default, it agrees with the one-at-a-time run."""
+    d = disks.make_disk(disks.log_r_faces(0.1, 100.0, 12), disks.midplane_refined_theta_faces(10),
+                        disks.paper_star(), disks.powerlaw_opacity(nlam=12, g=0.6), 1e5)
+    n, j = 50_000, d.ntheta // 2
+
+    def rim(lanes):
+        x = np.array([float(_run_interleaved(lib, d, n, lanes, 100 + s)[0, j - 1:j + 1].sum()) for s in range(16)])
+        return x.mean(), x.std(ddof=1) / np.sqrt(len(x))
+
+    one, e1 = rim(1)
+    many, em = rim(n // 10)
+    few, ef = rim(max(1, n // 3000))
+    assert (many - one) / np.hypot(e1, em) > 4.0, (one, many)
+    assert abs(few - one) / np.hypot(e1, ef) < 3.0, (one, few)
