@@ -155,6 +155,22 @@ struct WarpRng {
     return make_uint4(__shfl_sync(0xffffffffu, mine.x, j), __shfl_sync(0xffffffffu, mine.y, j),
                       __shfl_sync(0xffffffffu, mine.z, j), __shfl_sync(0xffffffffu, mine.w, j));
   }
+  // The packet's next blocks side by side, lane j holding block s.blk + j for j < count: the window the
+  // lanes already hold, shifted down, while at least `need` of its blocks are unused; 32 new blocks
+  // otherwise. Does not advance s.blk.
+  template <class R>
+  __device__ __forceinline__ uint4 window(const Pkt<R>& s, unsigned need, unsigned& count) {
+    const unsigned off = s.blk - base;  // (wraps to a large value when the lanes hold no block of s)
+    if (off > 32u - need) {
+      base = s.blk;
+      mine = philox_block(base + (threadIdx.x & 31u), s.model, s.plo, s.phi, key.k0, key.k1);
+      count = 32u;
+      return mine;
+    }
+    count = 32u - off;
+    return make_uint4(__shfl_down_sync(0xffffffffu, mine.x, off), __shfl_down_sync(0xffffffffu, mine.y, off),
+                      __shfl_down_sync(0xffffffffu, mine.z, off), __shfl_down_sync(0xffffffffu, mine.w, off));
+  }
 };
 
 // the lane that performs a packet's memory side effects (atomics): every lane, except in a warp that
@@ -705,9 +721,10 @@ __device__ __forceinline__ float dmin_faces(const CellFaces& f, float px, float 
 // The MRW chain of a packet that all 32 lanes of a warp carry (tail kernel; gray dust, FP32, isotropic
 // direction after a jump). What a jump draws -- its escape-time quantile, the point on the sphere, the exit
 // bin's uniform and the new direction -- does not depend on where the packet is, so the lanes evaluate the
-// next 16 jumps at once (lane 2k the first of jump k's two blocks, lane 2k+1 the second); only
-// p <- p + d_min(p) h_k, with the Eq. 11 test at every point, runs jump after jump. The draws and the
-// arithmetic of each jump are mrw_chain's; the deposits of the jumps of one cell are one atomic.
+// next jumps at once (lane 2k the first of jump k's two blocks, lane 2k+1 the second; up to 16 jumps
+// from the blocks the lanes hold); only p <- p + d_min(p) h_k, with the Eq. 11 test at every point, runs
+// jump after jump. The draws and the arithmetic of each jump are mrw_chain's; the deposits of the jumps
+// of one window are one atomic.
 __device__ __forceinline__ void mrw_chain_warp(const KParams<float>& P, WarpRng& rng, const DevModel<float>& M,
                                                Pkt<float>& s, int c, Acc& acc) {
   const unsigned lane = threadIdx.x & 31u;
@@ -718,9 +735,9 @@ __device__ __forceinline__ void mrw_chain_warp(const KParams<float>& P, WarpRng&
   bool more = true;
   while (more) {
     const uint32_t blk0 = s.blk;
-    const uint4 w = philox_block(blk0 + lane, s.model, s.plo, s.phi, rng.key.k0, rng.key.k1);
-    rng.base = blk0;  // the lanes now hold blocks blk0 .. blk0 + 31: later events reuse them
-    rng.mine = w;
+    unsigned m;
+    const uint4 w = rng.window(s, 4u, m);
+    const int kmax = (int)(m >> 1);
     // even lanes: jump k's first block (quantile, point on the sphere, exit-bin uniform); odd lanes: its
     // second block (new direction). Every lane evaluates both forms; each keeps the one it serves.
     const float x = mrw_x(P, uni<float>(w.x));
@@ -731,7 +748,7 @@ __device__ __forceinline__ void mrw_chain_warp(const KParams<float>& P, WarpRng&
     unsigned long long dep = 0ull;
     int k = 0;
     more = false;
-    for (; k < 16; ++k) {
+    for (; k < kmax; ++k) {
       if (s.events >= P.max_events) break;
       const float dm = dmin_faces(f, s.px, s.py, s.pz);
       s.dsafe = dm * dsafe_margin<float>();
@@ -751,7 +768,7 @@ __device__ __forceinline__ void mrw_chain_warp(const KParams<float>& P, WarpRng&
       s.events++;
       acc.mrw++;
       s.dsafe = 0.f;
-      more = k == 15;
+      more = k == kmax - 1;
     }
     if (k > 0) {
       if (lane == 0) atomicAdd(M.tally + c, dep);
@@ -1147,6 +1164,9 @@ __device__ __forceinline__ int find_model(const KParams<R>& P, unsigned long lon
 // of interactions done (0: the next flight crosses a face; the caller then takes a normal step), sets
 // `ended` when the MRW chain reached the event cap and `misses` when the next flight is known to meet a
 // face.
+// fewest blocks a run of interactions starts from before the lanes compute a new window of 32
+constexpr unsigned kMinRun = 16u;
+
 template <class R, bool G>
 __device__ __forceinline__ int interactions_at_once(const KParams<R>& P, WarpRng& rng, const DevModel<R>& M, Pkt<R>& s,
                                                     Acc& acc, bool& ended, bool& misses) {
@@ -1154,9 +1174,12 @@ __device__ __forceinline__ int interactions_at_once(const KParams<R>& P, WarpRng
   const unsigned full = 0xffffffffu;
   const int c = s.ir * M.nt + s.it;
   const R om = M.alb0;
-  // lane k: block of interaction k; what it draws for interaction k (albedo test) and for flight k+1
+  // lane k: block of interaction k; what it draws for interaction k (albedo test) and for flight k+1.
+  // Lanes from m on hold no block of this packet's run: the run stops at interaction m - 1 at the latest.
   const uint32_t blk0 = s.blk;
-  const uint4 w = philox_block(blk0 + lane, s.model, s.plo, s.phi, rng.key.k0, rng.key.k1);
+  unsigned m;
+  const uint4 w = rng.window(s, kMinRun, m);
+  const unsigned win = m == 32u ? full : ((1u << m) - 1u);
   const R a = uni<R>(w.x);
   R nx, ny, nz;
   iso_dir<R>(w.y, w.z, nx, ny, nz);
@@ -1191,13 +1214,13 @@ __device__ __forceinline__ int interactions_at_once(const KParams<R>& P, WarpRng
   R dstart = __shfl_up_sync(full, dq * dsafe_margin<R>(), 1);
   if (lane == 0) dstart = s.dsafe;
   bool hit = f < dstart;
-  if (__ballot_sync(full, !hit)) {
+  if (__ballot_sync(full, !hit) & win) {
     int face;
     const R sf = next_face(M, s.ir, s.it, px, py, pz, ux, uy, uz, face);
     hit = hit || f < sf;
   }
-  const unsigned miss = __ballot_sync(full, !hit);
-  const int h = miss ? __ffs(miss) - 1 : 32;  // flights 0 .. h-1 end inside the cell
+  const unsigned miss = __ballot_sync(full, !hit) & win;
+  const int h = miss ? __ffs(miss) - 1 : (int)m;  // flights 0 .. h-1 end inside the cell
   if (h == 0) return 0;
   const bool mrw = P.mrw && s.ninc + (int)lane + 1 >= P.nmin && dq * M.rho[c] * M.chiR0 > P.gamma;  // Eq. 11
   const unsigned mrws = __ballot_sync(full, mrw) & (h == 32 ? full : ((1u << h) - 1u));
@@ -1236,9 +1259,7 @@ __device__ __forceinline__ int interactions_at_once(const KParams<R>& P, WarpRng
   s.steps += n;
   s.ninc += n;
   s.xcross = 0;
-  rng.base = blk0;  // the lanes now hold blocks blk0 .. blk0 + 31: later events reuse them
-  rng.mine = w;
-  misses = !mrws && h < 32;
+  misses = !mrws && h < (int)m;  // flight h leaves the cell (h = m: the window ended, not the run)
   if (mrws) {
     mrw_chain<R, false, G>(P, rng, M, s, c, acc);
     if (s.events >= P.max_events) {

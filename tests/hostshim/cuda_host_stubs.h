@@ -81,6 +81,8 @@ inline T __shfl_sync(unsigned, T v, int, int = 32) { return v; }
 template <class T>
 inline T __shfl_up_sync(unsigned, T v, unsigned, int = 32) { return v; }
 template <class T>
+inline T __shfl_down_sync(unsigned, T v, unsigned, int = 32) { return v; }
+template <class T>
 inline T __shfl_xor_sync(unsigned, T v, int, int = 32) { return v; }
 inline unsigned __ballot_sync(unsigned, int p) { return p ? 1u : 0u; }
 inline int __any_sync(unsigned, int p) { return p; }
