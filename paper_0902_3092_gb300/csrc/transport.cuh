@@ -870,6 +870,53 @@ __device__ __forceinline__ void mrw_chain(const KParams<R>& P, RNG& rng, const D
   }
 }
 
+// Crosses face `face` of the packet's cell at distance s_face along its direction (alpha: the extinction
+// of the cell it leaves): the packet enters the next cell (1), or leaves the grid (0, escaped).
+template <class R, bool TRACE, bool G, bool POL = false, class RNG>
+__device__ __forceinline__ int cross_face(const KParams<R>& P, const DevModel<R>& M, Pkt<R>& s, Acc& acc, R s_face,
+                                          int face, R alpha) {
+  s.px += s_face * s.ux;
+  s.py += s_face * s.uy;
+  s.pz += s_face * s.uz;
+  s.tau -= alpha * s_face;
+  if (s.tau < (R)0) s.tau = (R)0;
+  acc.cross++;
+  if (face == 1) s.ir++;
+  else if (face == 0) s.ir--;
+  else if (face == 2) s.it--;
+  else s.it++;
+  if (s.ir >= M.nr) {
+    if (P.want_lam) resolve_pending(M, s);
+    int ib = (int)(fabs(s.uz) * (R)kNInc);
+    ib = ib < kNInc ? ib : kNInc - 1;
+    if (lead<RNG>()) atomicAdd(M.sed + s.lam * kNInc + ib, 1ull);
+    if (POL) {
+      R q, u;
+      pol_observer(s, q, u);
+      const long long iq = (long long)floor(q * (R)1048576 + (R)0.5), iu = (long long)floor(u * (R)1048576 + (R)0.5);
+      if (lead<RNG>()) {
+        atomicAdd(M.sed_q + s.lam * kNInc + ib, (unsigned long long)iq);
+        atomicAdd(M.sed_u + s.lam * kNInc + ib, (unsigned long long)iu);
+      }
+    }
+    acc.escaped++;
+    trace_ev<R, TRACE>(P, s, EV_ESCAPE, -1);
+    return 0;
+  }
+  if (s.ir < 0) {
+    s.alpha = (R)0;
+    s.ialpha = (R)0;
+    trace_ev<R, TRACE>(P, s, EV_CROSS, -1);
+    return 1;
+  }
+  s.ninc = 0;
+  set_alpha<R, G>(M, s);
+  const int cn = s.ir * M.nt + s.it;
+  if (lead<RNG>()) atomicAdd(M.visits + cn, 1ull);
+  trace_ev<R, TRACE>(P, s, EV_CROSS, cn);
+  return 1;
+}
+
 // Moves a packet to its next event: enters the next cell (1), reaches an interaction point (2, the
 // interaction itself is left to interact()), or ends (0: escaped, or a step guard).
 template <class R, bool TRACE, bool G, bool POL = false, bool JT = false, class RNG>
@@ -945,46 +992,7 @@ __device__ __forceinline__ int advance(const KParams<R>& P, RNG& rng, const DevM
     return 0;
   }
   if (JT && alpha > (R)0) j_flight<R, RNG>(M, s.ir * M.nt + s.it, s.lam, s_face);
-  s.px += s_face * s.ux;
-  s.py += s_face * s.uy;
-  s.pz += s_face * s.uz;
-  s.tau -= alpha * s_face;
-  if (s.tau < (R)0) s.tau = (R)0;
-  acc.cross++;
-  if (face == 1) s.ir++;
-  else if (face == 0) s.ir--;
-  else if (face == 2) s.it--;
-  else s.it++;
-  if (s.ir >= M.nr) {
-    if (P.want_lam) resolve_pending(M, s);
-    int ib = (int)(fabs(s.uz) * (R)kNInc);
-    ib = ib < kNInc ? ib : kNInc - 1;
-    if (lead<RNG>()) atomicAdd(M.sed + s.lam * kNInc + ib, 1ull);
-    if (POL) {
-      R q, u;
-      pol_observer(s, q, u);
-      const long long iq = (long long)floor(q * (R)1048576 + (R)0.5), iu = (long long)floor(u * (R)1048576 + (R)0.5);
-      if (lead<RNG>()) {
-        atomicAdd(M.sed_q + s.lam * kNInc + ib, (unsigned long long)iq);
-        atomicAdd(M.sed_u + s.lam * kNInc + ib, (unsigned long long)iu);
-      }
-    }
-    acc.escaped++;
-    trace_ev<R, TRACE>(P, s, EV_ESCAPE, -1);
-    return 0;
-  }
-  if (s.ir < 0) {
-    s.alpha = (R)0;
-    s.ialpha = (R)0;
-    trace_ev<R, TRACE>(P, s, EV_CROSS, -1);
-    return 1;
-  }
-  s.ninc = 0;
-  set_alpha<R, G>(M, s);
-  const int cn = s.ir * M.nt + s.it;
-  if (lead<RNG>()) atomicAdd(M.visits + cn, 1ull);
-  trace_ev<R, TRACE>(P, s, EV_CROSS, cn);
-  return 1;
+  return cross_face<R, TRACE, G, POL, RNG>(P, M, s, acc, s_face, face, alpha);
 }
 
 // The interaction at the packet's current point (Sect. 2.1): scattering or absorption with immediate
@@ -1160,16 +1168,16 @@ __device__ __forceinline__ int find_model(const KParams<R>& P, unsigned long lon
 // drawn at interaction k-1, lane 0: the packet's current ones) and, by a warp prefix sum of the flight
 // vectors, its position. The interactions are the packet's own, with its own random blocks, up to the
 // first flight that meets a cell face (the exact face distance decides, as in advance()) or the first
-// interaction after which Eq. 11 starts an MRW chain; their deposits are one atomic. Returns the number
-// of interactions done (0: the next flight crosses a face; the caller then takes a normal step), sets
-// `ended` when the MRW chain reached the event cap and `misses` when the next flight is known to meet a
-// face.
+// interaction after which Eq. 11 starts an MRW chain; their deposits are one atomic. A run that ends at
+// a face ends with that crossing, as advance() makes it. Returns the number of interactions done (0: the
+// packet's next flight crosses a face; the caller then takes a normal step); sets `ended` when the packet
+// ended (its MRW chain reached the event cap, or the crossing left the grid).
 // fewest blocks a run of interactions starts from before the lanes compute a new window of 32
 constexpr unsigned kMinRun = 16u;
 
 template <class R, bool G>
 __device__ __forceinline__ int interactions_at_once(const KParams<R>& P, WarpRng& rng, const DevModel<R>& M, Pkt<R>& s,
-                                                    Acc& acc, bool& ended, bool& misses) {
+                                                    Acc& acc, bool& ended) {
   const unsigned lane = threadIdx.x & 31u;
   const unsigned full = 0xffffffffu;
   const int c = s.ir * M.nt + s.it;
@@ -1205,18 +1213,26 @@ __device__ __forceinline__ int interactions_at_once(const KParams<R>& P, WarpRng
       qz += tz;
     }
   }
-  const R px = s.px + (qx - f * ux), py = s.py + (qy - f * uy), pz = s.pz + (qz - f * uz);
   qx += s.px;
   qy += s.py;
   qz += s.pz;
+  // start of flight k: interaction point k - 1 as lane k - 1 holds it (the packet's position after the
+  // run), so that the face distance of a flight that leaves the cell is the one advance() would find
+  R px = __shfl_up_sync(full, qx, 1), py = __shfl_up_sync(full, qy, 1), pz = __shfl_up_sync(full, qz, 1);
+  if (lane == 0) {
+    px = s.px;
+    py = s.py;
+    pz = s.pz;
+  }
   // d_min at the interaction point: the MRW test there and the safety distance of the next flight
   const R dq = dmin_cell(M, s.ir, s.it, qx, qy, qz);
   R dstart = __shfl_up_sync(full, dq * dsafe_margin<R>(), 1);
   if (lane == 0) dstart = s.dsafe;
   bool hit = f < dstart;
+  R sf = inf_<R>();
+  int face = 1;
   if (__ballot_sync(full, !hit) & win) {
-    int face;
-    const R sf = next_face(M, s.ir, s.it, px, py, pz, ux, uy, uz, face);
+    sf = next_face(M, s.ir, s.it, px, py, pz, ux, uy, uz, face);
     hit = hit || f < sf;
   }
   const unsigned miss = __ballot_sync(full, !hit) & win;
@@ -1259,7 +1275,19 @@ __device__ __forceinline__ int interactions_at_once(const KParams<R>& P, WarpRng
   s.steps += n;
   s.ninc += n;
   s.xcross = 0;
-  misses = !mrws && h < (int)m;  // flight h leaves the cell (h = m: the window ended, not the run)
+  if (!mrws && h < (int)m) {
+    // flight h leaves the cell (h = m: the window ended, not the run): the crossing advance() would make
+    // next (no interaction before the face; d_min at the start of the flight is the safety distance the
+    // run's last interaction left, and the face distance is lane h's)
+    const R s_face = __shfl_sync(full, sf, h);
+    const int fc = __shfl_sync(full, face, h);
+    s.tau = tau_next;
+    s.steps++;
+    s.xcross = 1;
+    s.dsafe = (R)0;
+    if (!cross_face<R, false, G, false, WarpRng>(P, M, s, acc, s_face, fc, s.alpha)) ended = true;
+    return n;
+  }
   if (mrws) {
     mrw_chain<R, false, G>(P, rng, M, s, c, acc);
     if (s.events >= P.max_events) {
@@ -1299,16 +1327,15 @@ __global__ void __launch_bounds__(32, kTailBlocksPerSm) transport_tail_kernel(co
       // all 32 lanes carry the packet: the same arithmetic in every lane, the random blocks computed
       // 32 at a time, side effects by lane 0; gray isotropic dust takes runs of interactions at once
       WarpRng rng{{(uint32_t)P.seed, (uint32_t)(P.seed >> 32)}, s.blk - 32u, make_uint4(0u, 0u, 0u, 0u)};
-      bool ended = false, misses = false;
+      bool ended = false;
       for (;;) {
         // (FP32 only: the FP64 debug path keeps the oracle's order of floating-point operations)
-        if (!POL && !JT && (G || M.gray) && sizeof(R) == 4 && !misses && !s.pend && s.ir >= 0 && s.alpha > (R)0 && M.g0 == (R)0 &&
+        if (!POL && !JT && (G || M.gray) && sizeof(R) == 4 && !s.pend && s.ir >= 0 && s.alpha > (R)0 && M.g0 == (R)0 &&
             s.events + 33u < P.max_events && s.steps + 33u < P.max_steps) {
-          const int n = interactions_at_once<R, G>(P, rng, M, s, acc, ended, misses);
+          const int n = interactions_at_once<R, G>(P, rng, M, s, acc, ended);
           if (ended) break;
           if (n > 0) continue;
         }
-        misses = false;
         if (!step<R, TRACE, G, POL, JT>(P, rng, M, s, acc)) break;
       }
     }
