@@ -870,6 +870,122 @@ __device__ __forceinline__ void mrw_chain(const KParams<R>& P, RNG& rng, const D
   }
 }
 
+// position of the (i+1)-th set bit of m (0 <= i < popc(m))
+__device__ __forceinline__ int nth_set_bit(unsigned m, int i) {
+  int pos = 0;
+#pragma unroll
+  for (int b = 16; b > 0; b >>= 1) {
+    const int c = __popc(m & ((1u << b) - 1u));
+    if (c <= i) {
+      i -= c;
+      m >>= b;
+      pos += b;
+    }
+  }
+  return pos;
+}
+
+// The MRW chains of the lanes in `want` (one packet per lane; transport kernel, single gray FP32 disk,
+// isotropic direction after a jump), made together by the whole warp: the Eq. 11 test at each chain's
+// point, then the 32 lanes compute the next random blocks of every chain that goes on (up to 16 chains,
+// 2 to 32 blocks each: lane j a block of chain j / per) and each chain lane makes its jumps from them, one
+// after another, with the blocks read from the lanes that hold them. The draws and the arithmetic of
+// every jump are mrw_chain's; a chain's deposits of one pass are one atomic. Needs a converged warp.
+__device__ __forceinline__ void mrw_chains_lanes(const KParams<float>& P, const Key& key, const DevModel<float>& M,
+                                                 Pkt<float>& s, Acc& acc, bool want) {
+  const unsigned lane = threadIdx.x & 31u;
+  const unsigned full = 0xffffffffu;
+  const int c = s.ir * M.nt + s.it;
+  const float rho = want ? M.rho[c] : 0.f;
+  const float chiR = M.chiR0, kb = M.kbar0;
+  for (;;) {
+    // the test that opens each pass of mrw_chain's loop: event cap, d_min (the safety distance), Eq. 11
+    float dm = 0.f;
+    if (want) {
+      if (s.events >= P.max_events) {
+        want = false;
+      } else {
+        dm = dmin_cell(M, s.ir, s.it, s.px, s.py, s.pz);
+        s.dsafe = dm * dsafe_margin<float>();
+        want = dm * rho * chiR > P.gamma;
+      }
+    }
+    const unsigned gm = __ballot_sync(full, want);
+    if (!gm) break;
+    const int k = __popc(gm);
+    const int served = k < 16 ? k : 16;  // the others wait for the next pass (their test stands)
+    const int per = k > 16 ? 2 : (int)((32u / (unsigned)k) & ~1u);
+    const int rank = __popc(gm & ((1u << lane) - 1u));
+    const int ci = (int)lane / per, co = (int)lane - ci * per;
+    const int src = ci < served ? nth_set_bit(gm, ci) : (int)lane;
+    const uint32_t plo = __shfl_sync(full, s.plo, src), phi = __shfl_sync(full, s.phi, src);
+    const uint32_t mdl = __shfl_sync(full, s.model, src), blk = __shfl_sync(full, s.blk, src);
+    const uint4 w = philox_block(blk + (uint32_t)co, mdl, plo, phi, key.k0, key.k1);
+    // even slots: a jump's first block (quantile, point on the sphere, exit-bin uniform); odd: its second
+    // (new direction). Every lane evaluates both forms.
+    const float x = mrw_x(P, uni<float>(w.x));
+    float hx, hy, hz, nx, ny, nz;
+    iso_dir<float>(w.y, w.z, hx, hy, hz);
+    iso_dir<float>(w.x, w.y, nx, ny, nz);
+    const float ul = uni<float>(w.w);
+    const int base = rank * per;
+    bool go = want && rank < served;
+    unsigned long long dep = 0ull;
+    int kk = 0;
+    for (int j = 0; j < per / 2; ++j) {
+      if (go && j > 0) {
+        if (s.events >= P.max_events) {
+          go = false;
+        } else {
+          dm = dmin_cell(M, s.ir, s.it, s.px, s.py, s.pz);
+          s.dsafe = dm * dsafe_margin<float>();
+          go = dm * rho * chiR > P.gamma;
+        }
+      }
+      const int sl = go ? base + 2 * j : (int)lane;
+      const float xk = __shfl_sync(full, x, sl);
+      const float jx = __shfl_sync(full, hx, sl), jy = __shfl_sync(full, hy, sl), jz = __shfl_sync(full, hz, sl);
+      if (go) {
+        const float tau0 = dm * rho;
+        const float E = 3.f * xk * tau0 * tau0 * chiR * kb;  // Eq. 9, as mrw_chain
+        float units = floorf(E * (float)kEUnit + 0.5f);
+        if (!(units < 1.8e19f)) {
+          units = 1.8e19f;
+          acc.err |= kErrMrwClip;
+        }
+        dep += (unsigned long long)units;
+        s.px += dm * jx;
+        s.py += dm * jy;
+        s.pz += dm * jz;
+        s.events++;
+        acc.mrw++;
+        s.dsafe = 0.f;
+        kk = j + 1;
+      }
+      if (!__any_sync(full, go)) break;
+    }
+    const int l1 = kk > 0 ? base + 2 * kk - 2 : (int)lane;
+    const int l2 = kk > 0 ? l1 + 1 : (int)lane;
+    const float ex = __shfl_sync(full, nx, l2), ey = __shfl_sync(full, ny, l2), ez = __shfl_sync(full, nz, l2);
+    const float eu = __shfl_sync(full, ul, l1);
+    if (kk > 0) {
+      atomicAdd(M.tally + c, dep);
+      add_deposit(acc, dep);
+      s.ux = ex;
+      s.uy = ey;
+      s.uz = ez;
+      if (P.want_lam) {  // the exit bin of the last jump, drawn at escape
+        s.pend_mode = 2;
+        s.pend_cell = c;
+        s.pend_u = eu;
+      }
+      s.blk += 2u * (unsigned)kk;
+    }
+    // a served chain goes on only after jumps in all its slots (its next test opens the next pass)
+    want = want && (rank >= served || go);
+  }
+}
+
 // Crosses face `face` of the packet's cell at distance s_face along its direction (alpha: the extinction
 // of the cell it leaves): the packet enters the next cell (1), or leaves the grid (0, escaped).
 template <class R, bool TRACE, bool G, bool POL = false, class RNG>
@@ -997,10 +1113,12 @@ __device__ __forceinline__ int advance(const KParams<R>& P, RNG& rng, const DevM
 
 // The interaction at the packet's current point (Sect. 2.1): scattering or absorption with immediate
 // re-emission, then the MRW chain (Sect. 2.2.2) and the next optical depth. A release (the first event
-// of an internal source's packet) is an absorption with omega = 0. False: capped.
+// of an internal source's packet) is an absorption with omega = 0. False: capped. With tau_out, the
+// interaction stops after the scattering or re-emission: the caller runs the MRW chain, the cap test and
+// sets the next optical depth (*tau_out).
 template <class R, bool TRACE, bool G, bool POL = false, bool JT = false, class RNG>
 __device__ __forceinline__ bool interact(const KParams<R>& P, RNG& rng, const DevModel<R>& M, Pkt<R>& s, Acc& acc,
-                                         bool release = false) {
+                                         bool release = false, R* tau_out = nullptr) {
   const int c = s.ir * M.nt + s.it;
   const uint4 w = rng.next(s);  // albedo test, new direction, next optical depth
   const R om = release ? (R)0 : ((G || M.gray) ? M.alb0 : M.alb[s.lam]);
@@ -1051,6 +1169,10 @@ __device__ __forceinline__ bool interact(const KParams<R>& P, RNG& rng, const De
   trace_ev<R, TRACE>(P, s, sca ? EV_SCATTER : EV_ABSORB, c);
   s.events++;
   s.ninc++;
+  if (tau_out) {
+    *tau_out = tau_next;
+    return true;
+  }
   if (P.mrw && s.ninc >= P.nmin) mrw_chain<R, TRACE, G, POL, JT>(P, rng, M, s, c, acc);
   if (s.events >= P.max_events) {
     acc.capped++;
@@ -1354,6 +1476,10 @@ __global__ void __launch_bounds__(32, kTailBlocksPerSm) transport_tail_kernel(co
 template <class R>
 constexpr int transport_min_blocks() { return sizeof(R) == 4 ? MCRT_TRANSPORT_MIN_BLOCKS : 1; }
 
+// transport kernels whose MRW chains run warp-wide (mrw_chains_lanes): single gray FP32 disk
+template <class R, bool TRACE, bool BATCH, bool G, bool POL, bool JT>
+__host__ __device__ constexpr bool kLaneChains() { return sizeof(R) == 4 && !TRACE && !BATCH && G && !POL && !JT; }
+
 // G: gray dust known at compile time (single-disk gray runs); otherwise M.gray is read at run time.
 template <class R, bool TRACE, bool BATCH, bool G, bool POL = false, bool JT = false>
 __global__ void __launch_bounds__(256, transport_min_blocks<R>()) transport_kernel(const KParams<R> P) {
@@ -1440,7 +1566,33 @@ __global__ void __launch_bounds__(256, transport_min_blocks<R>()) transport_kern
     const unsigned waiting = __ballot_sync(0xffffffffu, active && s.pend);
     if (waiting) {
       const unsigned moving = __ballot_sync(0xffffffffu, active && !s.pend);
-      if (__popc(waiting) >= P.defer || !moving) {
+      bool batch_now = __popc(waiting) >= P.defer || !moving;
+      if constexpr (kLaneChains<R, TRACE, BATCH, G, POL, JT>()) {
+        if (batch_now && P.exit_dir == 0) {
+          // the MRW chains that follow the interactions run warp-wide
+          batch_now = false;
+          const bool inter = active && s.pend;
+          bool chain = false;
+          R tau_next = (R)0;
+          if (inter) {
+            const bool release = s.pend == 2;
+            s.pend = 0;
+            interact<R, TRACE, G, POL, JT>(P, rng, M, s, acc, release, &tau_next);
+            chain = P.mrw && s.ninc >= P.nmin;
+          }
+          if (__any_sync(0xffffffffu, chain)) mrw_chains_lanes(P, rng.key, M, s, acc, chain);
+          if (inter) {
+            if (s.events >= P.max_events) {
+              acc.capped++;
+              active = false;
+              note_end(s, acc);
+            } else {
+              s.tau = tau_next;
+            }
+          }
+        }
+      }
+      if (batch_now) {
         if (active && s.pend) {
           const bool release = s.pend == 2;
           s.pend = 0;
