@@ -1291,14 +1291,15 @@ __device__ __forceinline__ int find_model(const KParams<R>& P, unsigned long lon
 // vectors, its position. The interactions are the packet's own, with its own random blocks, up to the
 // first flight that meets a cell face (the exact face distance decides, as in advance()) or the first
 // interaction after which Eq. 11 starts an MRW chain; their deposits are one atomic. A run that ends at
-// a face ends with that crossing, as advance() makes it. Returns the number of interactions done (0: the
-// packet's next flight crosses a face; the caller then takes a normal step); sets `ended` when the packet
-// ended (its MRW chain reached the event cap, or the crossing left the grid).
+// a face ends with that crossing, as advance() makes it, and so does a call whose first flight leaves the
+// cell. False when the call did nothing (advance()'s guard on crossings is due; the caller then takes a
+// normal step); sets `ended` when the packet ended (its MRW chain reached the event cap, or the crossing
+// left the grid).
 // fewest blocks a run of interactions starts from before the lanes compute a new window of 32
 constexpr unsigned kMinRun = 16u;
 
 template <class R, bool G>
-__device__ __forceinline__ int interactions_at_once(const KParams<R>& P, WarpRng& rng, const DevModel<R>& M, Pkt<R>& s,
+__device__ __forceinline__ bool interactions_at_once(const KParams<R>& P, WarpRng& rng, const DevModel<R>& M, Pkt<R>& s,
                                                     Acc& acc, bool& ended) {
   const unsigned lane = threadIdx.x & 31u;
   const unsigned full = 0xffffffffu;
@@ -1355,11 +1356,27 @@ __device__ __forceinline__ int interactions_at_once(const KParams<R>& P, WarpRng
   int face = 1;
   if (__ballot_sync(full, !hit) & win) {
     sf = next_face(M, s.ir, s.it, px, py, pz, ux, uy, uz, face);
+    if (sizeof(R) == 4 && lane == 0 && s.xcross) {
+      // flight 0 after a crossing: advance()'s minimum move
+      const R mv = (R)1e-6 * (fabs(s.px) + fabs(s.py) + fabs(s.pz));
+      sf = sf > mv ? sf : mv;
+    }
     hit = hit || f < sf;
   }
   const unsigned miss = __ballot_sync(full, !hit) & win;
   const int h = miss ? __ffs(miss) - 1 : (int)m;  // flights 0 .. h-1 end inside the cell
-  if (h == 0) return 0;
+  if (h == 0) {
+    // the packet's flight leaves the cell: the crossing advance() would make (its face distance is lane
+    // 0's), unless advance()'s guard on crossings without an interaction is due
+    if (s.xcross >= 100000u) return false;
+    const R s_face = __shfl_sync(full, sf, 0);
+    const int fc = __shfl_sync(full, face, 0);
+    s.steps++;
+    s.xcross++;
+    s.dsafe = (R)0;
+    if (!cross_face<R, false, G, false, WarpRng>(P, M, s, acc, s_face, fc, s.alpha)) ended = true;
+    return true;
+  }
   const bool mrw = P.mrw && s.ninc + (int)lane + 1 >= P.nmin && dq * M.rho[c] * M.chiR0 > P.gamma;  // Eq. 11
   const unsigned mrws = __ballot_sync(full, mrw) & (h == 32 ? full : ((1u << h) - 1u));
   const int n = mrws ? __ffs(mrws) : h;  // interactions done; an MRW chain follows interaction n-1 if mrws
@@ -1408,18 +1425,18 @@ __device__ __forceinline__ int interactions_at_once(const KParams<R>& P, WarpRng
     s.xcross = 1;
     s.dsafe = (R)0;
     if (!cross_face<R, false, G, false, WarpRng>(P, M, s, acc, s_face, fc, s.alpha)) ended = true;
-    return n;
+    return true;
   }
   if (mrws) {
     mrw_chain<R, false, G>(P, rng, M, s, c, acc);
     if (s.events >= P.max_events) {
       acc.capped++;
       ended = true;
-      return n;
+      return true;
     }
   }
   s.tau = tau_next;
-  return n;
+  return true;
 }
 
 // Tail of a single-disk launch. When the queue drains, the packets still in flight are mostly long
@@ -1454,9 +1471,9 @@ __global__ void __launch_bounds__(32, kTailBlocksPerSm) transport_tail_kernel(co
         // (FP32 only: the FP64 debug path keeps the oracle's order of floating-point operations)
         if (!POL && !JT && (G || M.gray) && sizeof(R) == 4 && !s.pend && s.ir >= 0 && s.alpha > (R)0 && M.g0 == (R)0 &&
             s.events + 33u < P.max_events && s.steps + 33u < P.max_steps) {
-          const int n = interactions_at_once<R, G>(P, rng, M, s, acc, ended);
+          const bool moved = interactions_at_once<R, G>(P, rng, M, s, acc, ended);
           if (ended) break;
-          if (n > 0) continue;
+          if (moved) continue;
         }
         if (!step<R, TRACE, G, POL, JT>(P, rng, M, s, acc)) break;
       }
