@@ -1296,7 +1296,7 @@ __device__ __forceinline__ int find_model(const KParams<R>& P, unsigned long lon
 // normal step); sets `ended` when the packet ended (its MRW chain reached the event cap, or the crossing
 // left the grid).
 // fewest blocks a run of interactions starts from before the lanes compute a new window of 32
-constexpr unsigned kMinRun = 16u;
+constexpr unsigned kMinRun = 24u;
 
 template <class R, bool G>
 __device__ __forceinline__ bool interactions_at_once(const KParams<R>& P, WarpRng& rng, const DevModel<R>& M, Pkt<R>& s,
