@@ -328,8 +328,10 @@ def equal_accuracy(g, d, args):
     (tests/test_gpu_mrw_validation.py). Both methods are swept over packet counts (other seeds) with the
     benchmark's event cap; each point's time is the transport kernels' device time plus the PDA call. The
     accuracy level is the lowest RMS error both methods reach over those cells (plain MC: cells it never
-    reaches count with their full error); each method's time is interpolated in log-log between sweep
-    points, and the ratio is plain MC's time over MRW + PDA's."""
+    reaches count with their full error); each method's time to come within 5 % of it (relative) is
+    interpolated in log-log between sweep points, and the ratio is plain MC's time over MRW + PDA's. (On
+    the whole midplane the level is plain MC's floor, where its error no longer falls with more packets:
+    the 5 % makes the time to reach it a property of the curve rather than of the noise of its flat end.)"""
     from paper_0902_3092_gb300 import mcrt
     cap = int(args.max_events)
     j = d.ntheta // 2
@@ -354,9 +356,9 @@ def equal_accuracy(g, d, args):
     # with a 1e6- and a 1e7-event cap agree within 1 %), so both methods are compared on equal terms
     rc = 0.5 * (d.r_faces_cm[1:] + d.r_faces_cm[:-1])
     outer = conv & (rc >= 7.0 * 1.495978707e13)[:, None]
-    sweeps = {"plain MC": (False, False, [10 ** 6, 3 * 10 ** 6, 10 ** 7, 3 * 10 ** 7, 10 ** 8]),
-              "MRW+PDA": (True, True, [10 ** 4, 3 * 10 ** 4, 10 ** 5, 3 * 10 ** 5, 10 ** 6, 3 * 10 ** 6, 10 ** 7,
-                                       3 * 10 ** 7, 10 ** 8])}
+    sweeps = {"plain MC": (False, False, [10 ** 5, 3 * 10 ** 5, 10 ** 6, 3 * 10 ** 6, 10 ** 7, 3 * 10 ** 7, 10 ** 8]),
+              "MRW+PDA": (True, True, [3 * 10 ** 3, 10 ** 4, 3 * 10 ** 4, 10 ** 5, 3 * 10 ** 5, 10 ** 6, 3 * 10 ** 6,
+                                       10 ** 7, 3 * 10 ** 7, 10 ** 8])}
     pts = {}
     for name, (mrw, pda, ns) in sweeps.items():
         pts[name] = []
@@ -377,25 +379,29 @@ def equal_accuracy(g, d, args):
             pts[name].append({"packets": n, "seconds": t, "rms": rms, "max": mx, "rms_outer": rms_o, "max_outer": mx_o,
                               "cells_reached": reached})
 
-    def compare(key):
-        """The lowest error `key` both methods reach, the time each needs for it, and the ratio."""
+    def compare(key, tol=0.05):
+        """The lowest error `key` both methods reach, the time each needs to come within `tol` of it, and
+        the ratio."""
         level = max(min(p[key] for p in pts[k]) for k in pts)
+        target = level * (1 + tol)
         reach = {}
         for k in pts:
             seq = pts[k]
-            i = next(i for i, p in enumerate(seq) if p[key] <= level * (1 + 1e-12))
+            i = next(i for i, p in enumerate(seq) if p[key] <= target)
             t, n = seq[i]["seconds"], float(seq[i]["packets"])
-            if i > 0 and seq[i - 1][key] > level and seq[i][key] < level:
+            if i > 0 and seq[i - 1][key] > target and seq[i][key] < target:
                 # between two sweep points: log time and log packets linear in log error
                 a, b = seq[i - 1], seq[i]
-                f = math.log(a[key] / level) / math.log(a[key] / b[key])
+                f = math.log(a[key] / target) / math.log(a[key] / b[key])
                 t = math.exp(math.log(a["seconds"]) + f * math.log(b["seconds"] / a["seconds"]))
                 n = math.exp(math.log(a["packets"]) + f * math.log(b["packets"] / a["packets"]))
-            # the first sweep point already below the level: the time there bounds the time to reach it
-            reach[k] = {"seconds": t, "packets": n, "upper_bound": i == 0 and seq[0][key] < level}
-        return {"level_rms": level, "plain_mc": reach["plain MC"], "mrw_pda": reach["MRW+PDA"],
+            # the first sweep point already below the target: the time there bounds the time to reach it
+            reach[k] = {"seconds": t, "packets": n, "upper_bound": i == 0 and seq[0][key] < target}
+        up_p, up_m = reach["plain MC"]["upper_bound"], reach["MRW+PDA"]["upper_bound"]
+        return {"level_rms": level, "target_rms": target, "plain_mc": reach["plain MC"], "mrw_pda": reach["MRW+PDA"],
                 "speedup": reach["plain MC"]["seconds"] / reach["MRW+PDA"]["seconds"],
-                "speedup_is_lower_bound": bool(reach["MRW+PDA"]["upper_bound"])}
+                "speedup_is_lower_bound": bool(up_m and not up_p), "speedup_is_upper_bound": bool(up_p and not up_m),
+                "speedup_is_bounded_only": bool(up_p and up_m)}
 
     whole, out = compare("rms"), compare("rms_outer")
     best = min(pts["MRW+PDA"], key=lambda p: p["rms"])
@@ -408,10 +414,11 @@ def equal_accuracy(g, d, args):
                           "validation": "MRW vs plain MC without an event cap on the tau_mid=1e4 and 1e5 disks: "
                                         "1.5 % and 1.3 % RMS in the midplane"},
             "sweeps": pts, "event_cap": cap,
-            "note": "time to reach the lowest midplane RMS error both methods reach (interpolated in log-log "
-                    "between sweep points); transport device time + PDA call; plain MC's floor is set by the "
-                    "packets its event cap drops, which are the ones that heat the inner midplane; "
-                    "outer_midplane: the same where plain MC converges too"}
+            "note": "time to come within 5 % of the lowest midplane RMS error both methods reach (interpolated "
+                    "in log-log between sweep points); transport device time + PDA call; on the whole midplane "
+                    "that level is plain MC's floor, set by the packets its event cap drops (the ones that heat "
+                    "the inner midplane), which it does not pass with any number of packets while MRW+PDA goes "
+                    "on to mrw_pda_best; outer_midplane: the same where plain MC converges too"}
 
 
 def pda_stress(args):
