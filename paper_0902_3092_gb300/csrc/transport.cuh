@@ -723,8 +723,9 @@ __device__ __forceinline__ float dmin_faces(const CellFaces& f, float px, float 
 // bin's uniform and the new direction -- does not depend on where the packet is, so the lanes evaluate the
 // next jumps at once (lane 2k the first of jump k's two blocks, lane 2k+1 the second; up to 16 jumps
 // from the blocks the lanes hold); only p <- p + d_min(p) h_k, with the Eq. 11 test at every point, runs
-// jump after jump. The draws and the arithmetic of each jump are mrw_chain's; the deposits of the jumps
-// of one window are one atomic.
+// jump after jump, and each jump's deposit (Eq. 9) is computed after the loop by the lane that holds its
+// first block. The draws and the arithmetic of each jump are mrw_chain's; the deposits of the jumps of
+// one window are one atomic.
 __device__ __forceinline__ void mrw_chain_warp(const KParams<float>& P, WarpRng& rng, const DevModel<float>& M,
                                                Pkt<float>& s, int c, Acc& acc) {
   const unsigned lane = threadIdx.x & 31u;
@@ -745,23 +746,15 @@ __device__ __forceinline__ void mrw_chain_warp(const KParams<float>& P, WarpRng&
     iso_dir<float>(w.y, w.z, hx, hy, hz);
     iso_dir<float>(w.x, w.y, nx, ny, nz);
     const float ul = uni<float>(w.w);
-    unsigned long long dep = 0ull;
     int k = 0;
     more = false;
+    float mydm = 0.f;  // lane 2k: d_min of jump k
     for (; k < kmax; ++k) {
       if (s.events >= P.max_events) break;
       const float dm = dmin_faces(f, s.px, s.py, s.pz);
       s.dsafe = dm * dsafe_margin<float>();
       if (!(dm * rho * chiR > P.gamma)) break;  // Eq. 11
-      const float xk = __shfl_sync(full, x, 2 * k);
-      const float tau0 = dm * rho;
-      const float E = 3.f * xk * tau0 * tau0 * chiR * kb;  // Eq. 9, as mrw_chain
-      float units = floorf(E * (float)kEUnit + 0.5f);
-      if (!(units < 1.8e19f)) {
-        units = 1.8e19f;
-        acc.err |= kErrMrwClip;
-      }
-      dep += (unsigned long long)units;
+      mydm = (int)lane == 2 * k ? dm : mydm;
       s.px += dm * __shfl_sync(full, hx, 2 * k);
       s.py += dm * __shfl_sync(full, hy, 2 * k);
       s.pz += dm * __shfl_sync(full, hz, 2 * k);
@@ -770,6 +763,22 @@ __device__ __forceinline__ void mrw_chain_warp(const KParams<float>& P, WarpRng&
       s.dsafe = 0.f;
       more = k == kmax - 1;
     }
+    // the deposits of the jumps made (lane 2j: jump j), summed over the warp
+    unsigned long long du = 0ull;
+    if ((lane & 1u) == 0u && (int)lane < 2 * k) {
+      const float tau0 = mydm * rho;
+      const float E = 3.f * x * tau0 * tau0 * chiR * kb;  // Eq. 9, as mrw_chain
+      float units = floorf(E * (float)kEUnit + 0.5f);
+      if (!(units < 1.8e19f)) {
+        units = 1.8e19f;
+        acc.err |= kErrMrwClip;
+      }
+      du = (unsigned long long)units;
+    }
+    unsigned long long dep = du;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) dep += __shfl_xor_sync(full, dep, o);
+    acc.err |= __reduce_or_sync(full, acc.err);
     if (k > 0) {
       if (lane == 0) atomicAdd(M.tally + c, dep);
       add_deposit(acc, dep);
@@ -1305,6 +1314,7 @@ __device__ __forceinline__ bool interactions_at_once(const KParams<R>& P, WarpRn
   const unsigned full = 0xffffffffu;
   const int c = s.ir * M.nt + s.it;
   const R om = M.alb0;
+  const R rho_c = __ldg(M.rho + c);
   // lane k: block of interaction k; what it draws for interaction k (albedo test) and for flight k+1.
   // Lanes from m on hold no block of this packet's run: the run stops at interaction m - 1 at the latest.
   const uint32_t blk0 = s.blk;
@@ -1351,18 +1361,15 @@ __device__ __forceinline__ bool interactions_at_once(const KParams<R>& P, WarpRn
   const R dq = dmin_cell(M, s.ir, s.it, qx, qy, qz);
   R dstart = __shfl_up_sync(full, dq * dsafe_margin<R>(), 1);
   if (lane == 0) dstart = s.dsafe;
-  bool hit = f < dstart;
-  R sf = inf_<R>();
+  // the face distance of every flight, whether or not d_min already decides (it overlaps with d_min)
   int face = 1;
-  if (__ballot_sync(full, !hit) & win) {
-    sf = next_face(M, s.ir, s.it, px, py, pz, ux, uy, uz, face);
-    if (sizeof(R) == 4 && lane == 0 && s.xcross) {
-      // flight 0 after a crossing: advance()'s minimum move
-      const R mv = (R)1e-6 * (fabs(s.px) + fabs(s.py) + fabs(s.pz));
-      sf = sf > mv ? sf : mv;
-    }
-    hit = hit || f < sf;
+  R sf = next_face(M, s.ir, s.it, px, py, pz, ux, uy, uz, face);
+  if (sizeof(R) == 4 && lane == 0 && s.xcross) {
+    // flight 0 after a crossing: advance()'s minimum move
+    const R mv = (R)1e-6 * (fabs(s.px) + fabs(s.py) + fabs(s.pz));
+    sf = sf > mv ? sf : mv;
   }
+  const bool hit = f < dstart || f < sf;
   const unsigned miss = __ballot_sync(full, !hit) & win;
   const int h = miss ? __ffs(miss) - 1 : (int)m;  // flights 0 .. h-1 end inside the cell
   if (h == 0) {
@@ -1377,7 +1384,7 @@ __device__ __forceinline__ bool interactions_at_once(const KParams<R>& P, WarpRn
     if (!cross_face<R, false, G, false, WarpRng>(P, M, s, acc, s_face, fc, s.alpha)) ended = true;
     return true;
   }
-  const bool mrw = P.mrw && s.ninc + (int)lane + 1 >= P.nmin && dq * M.rho[c] * M.chiR0 > P.gamma;  // Eq. 11
+  const bool mrw = P.mrw && s.ninc + (int)lane + 1 >= P.nmin && dq * rho_c * M.chiR0 > P.gamma;  // Eq. 11
   const unsigned mrws = __ballot_sync(full, mrw) & (h == 32 ? full : ((1u << h) - 1u));
   const int n = mrws ? __ffs(mrws) : h;  // interactions done; an MRW chain follows interaction n-1 if mrws
   const unsigned done_mask = n == 32 ? full : ((1u << n) - 1u);
