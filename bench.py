@@ -421,6 +421,11 @@ def equal_accuracy(g, d, args):
                     "on to mrw_pda_best; outer_midplane: the same where plain MC converges too"}
 
 
+# algorithmic bytes per PDA cell and FP32 CG iteration: kernel A reads r, p_old and the two couplings and
+# writes p, Ap; kernel B reads p, Ap, y, r and writes y, r (4-byte values; neighbour values are re-reads)
+PDA_BYTES_PER_CELL_ITER = 4 * (4 + 2) + 4 * (4 + 2)
+
+
 def pda_stress(args):
     """PDA solve on an N x N grid of the benchmark disk made 100 times more massive (midplane optical
     depth 1e8), so that most cells of the midplane band |theta - pi/2| < 0.3 are optically thick at
