@@ -469,7 +469,9 @@ def pda_stress(args):
     _, t_b = solve(2 * m)
     t_it = (t_b - t_a) / m  # the setup, the mask checks and the final residual cancel
     byts = PDA_BYTES_PER_CELL_ITER * npda
-    peak = measured_peaks().get("hbm_gbs", 6800.0) * 1e9
+    mp = measured_peaks()
+    peak = mp.get("hbm_gbs", 6800.0) * 1e9
+    peak_src = "measured (MEASURED_PEAKS.json hbm_gbs)" if "hbm_gbs" in mp else "fallback (6.8 TB/s copy, one earlier GB300 measurement)"
     line = {"metric": "PDA FP32 CG iteration bandwidth (stress grid)", "value": byts / t_it / 1e9, "unit": "GB/s",
             "n_gpus": 1, "higher_is_better": True, "dtype": "f32", "data": "synthetic",
             "config": {"workload": f"PDA on a {n}x{n} gray disk of midplane optical depth 1e8, thick cells of the "
@@ -477,7 +479,7 @@ def pda_stress(args):
                        "cells": n * n, "pda_cells": npda, "cg_iterations_timed": args.pda_iters},
             "us_per_iteration": 1e6 * t_it, "setup_ms": 1e3 * (t_a - m * t_it),
             "roofline": {"bound": "hbm", "achieved": byts / t_it / 1e9, "peak": peak / 1e9, "unit": "GB/s",
-                         "frac": byts / t_it / peak, "traffic": None,
+                         "frac": byts / t_it / peak, "peak_source": peak_src, "traffic": None,
                          "note": f"{PDA_BYTES_PER_CELL_ITER} B per PDA cell per iteration (kernels A+B), "
                                  "host-timed difference of two solves"}}
     print(json.dumps(line), flush=True)
