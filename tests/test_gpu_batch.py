@@ -112,3 +112,24 @@ def test_batch_model_with_sources_equals_single_disk_run(M):
     t, _, _ = ga.tallies()
     assert int(t.sum()) == st[0]["deposit_sum"]
     B.close()
+
+
+def test_warp_wide_mrw_chains_equal_per_lane_chains(M):
+    """A single gray FP32 disk's transport kernel makes the MRW chains of its lanes warp-wide (the random
+    blocks of every chaining lane computed by the 32 lanes together, each lane's jumps read from the lanes
+    that hold its blocks); the batch kernel makes each lane's chain alone. Same Philox counters, same
+    arithmetic per jump: without the tail kernel, tallies, entries and absorption counts are bitwise equal,
+    on a disk where MRW jumps are a large share of the events (Sect. 2.2.2, Eq. 9-11)."""
+    d = disks.config_thick_gray(100, 60, 1e5)
+    single = M.Disk.from_model(d)
+    st = single.run_photons(200_000, seed=7, mrw=True, gamma=2.0, max_events=10 ** 6, tail_warps=-1, want_sed=False)
+    assert st["mrw_jumps"] > 0.1 * st["events"], (st["mrw_jumps"], st["events"])
+    g = M.Disk.from_model(d)
+    B = M.Batch([g], [200_000], mrw=True, gamma=2.0, max_events=10 ** 6, tail_warps=-1, want_sed=False)
+    (sb,) = B.run(seed=7)
+    assert sb["mrw_jumps"] == st["mrw_jumps"] and sb["events"] == st["events"]
+    for x, y in zip(single.tallies(), g.tallies()):
+        assert np.array_equal(x, y)
+    B.close()
+    single.close()
+    g.close()
