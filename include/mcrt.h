@@ -117,7 +117,8 @@ typedef struct {
                                    0 means the n_packets of this call */
   int block_size;               /* threads per block of the transport kernel (multiple of 32, <= 256);
                                    0: tuned default */
-  int refill_interval;          /* steps between refills of finished lanes; 0: tuned default */
+  int refill_interval;          /* steps between refills of finished lanes; 0: the default (8 for a single
+                                   disk, tuned for a batch) */
   int want_sed;                 /* gray dust only: 0 skips the emission-bin sampling (no SED) */
   int tail_warps_per_sm;        /* single-disk runs: the packets still in flight when the packet queue
                                    drains finish one per warp, this many warps per SM (0: 20; -1: no

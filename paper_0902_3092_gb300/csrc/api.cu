@@ -542,7 +542,7 @@ static void fill_params(KParams<R>& P, const mcrt_run_opts* o, uint64_t seed, co
   P.mrw = o->mrw ? 1 : 0;
   P.nmin = o->mrw_min_interactions;
   P.exit_dir = o->mrw_exit_dir;
-  P.refill = o->refill_interval > 0 ? o->refill_interval : 4;
+  P.refill = o->refill_interval > 0 ? o->refill_interval : 8;  // (single disks; batches tune theirs)
   P.defer = o->interact_batch > 0 ? o->interact_batch : 8;
   P.gamma = (R)o->gamma;
   P.seed = seed;
