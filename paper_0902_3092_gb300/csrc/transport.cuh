@@ -765,20 +765,21 @@ __device__ __forceinline__ void mrw_chain_warp(const KParams<float>& P, WarpRng&
     }
     // the deposits of the jumps made (lane 2j: jump j), summed over the warp
     unsigned long long du = 0ull;
+    bool clip = false;
     if ((lane & 1u) == 0u && (int)lane < 2 * k) {
       const float tau0 = mydm * rho;
       const float E = 3.f * x * tau0 * tau0 * chiR * kb;  // Eq. 9, as mrw_chain
       float units = floorf(E * (float)kEUnit + 0.5f);
       if (!(units < 1.8e19f)) {
         units = 1.8e19f;
-        acc.err |= kErrMrwClip;
+        clip = true;
       }
       du = (unsigned long long)units;
     }
     unsigned long long dep = du;
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) dep += __shfl_xor_sync(full, dep, o);
-    acc.err |= __reduce_or_sync(full, acc.err);
+    if (__any_sync(full, clip)) acc.err |= kErrMrwClip;
     if (k > 0) {
       if (lane == 0) atomicAdd(M.tally + c, dep);
       add_deposit(acc, dep);
