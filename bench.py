@@ -63,13 +63,37 @@ def transport_counts():
     return out
 
 
-def transport_source_hash():
-    """Hash of the transport kernels' sources: counts taken from another version are not used."""
+def code_only(src):
+    """C/C++ source without its comments, whitespace runs collapsed (string and character literals kept)."""
+    out, i, n = [], 0, len(src)
+    while i < n:
+        if src.startswith("//", i):
+            j = src.find("\n", i)
+            i = n if j < 0 else j
+        elif src.startswith("/*", i):
+            j = src.find("*/", i + 2)
+            i = n if j < 0 else j + 2
+            out.append(" ")
+        elif src[i] in "\"'":
+            j = i + 1
+            while j < n and src[j] != src[i]:
+                j += 2 if src[j] == "\\" else 1
+            out.append(src[i:j + 1])
+            i = j + 1
+        else:
+            out.append(src[i])
+            i += 1
+    return " ".join("".join(out).split())
+
+
+def transport_source_hash(root=None):
+    """Hash of the transport kernels' code (comments and layout left out): counts taken from another
+    version of the code are not used."""
     import hashlib
     h = hashlib.sha256()
     for f in ("common.cuh", "transport.cuh", "transport_f32.cu"):
-        with open(os.path.join(ROOT, "paper_0902_3092_gb300", "csrc", f), "rb") as fh:
-            h.update(fh.read())
+        with open(os.path.join(root or ROOT, "paper_0902_3092_gb300", "csrc", f), encoding="utf-8") as fh:
+            h.update(code_only(fh.read()).encode())
     return h.hexdigest()[:16]
 
 

@@ -1294,6 +1294,9 @@ __device__ __forceinline__ int find_model(const KParams<R>& P, unsigned long lon
   return lo;
 }
 
+// fewest blocks a run of interactions starts from before the lanes compute a new window of 32
+constexpr unsigned kMinRun = 24u;
+
 // Several interactions of one packet at once, in a warp whose 32 lanes all carry the packet (gray,
 // isotropic dust). Lane k evaluates the packet's k-th next interaction: its Philox block (the packet's
 // blocks are consumed one per interaction), the flight that leads to it (direction and optical depth
@@ -1305,9 +1308,6 @@ __device__ __forceinline__ int find_model(const KParams<R>& P, unsigned long lon
 // cell. False when the call did nothing (advance()'s guard on crossings is due; the caller then takes a
 // normal step); sets `ended` when the packet ended (its MRW chain reached the event cap, or the crossing
 // left the grid).
-// fewest blocks a run of interactions starts from before the lanes compute a new window of 32
-constexpr unsigned kMinRun = 24u;
-
 template <class R, bool G>
 __device__ __forceinline__ bool interactions_at_once(const KParams<R>& P, WarpRng& rng, const DevModel<R>& M, Pkt<R>& s,
                                                     Acc& acc, bool& ended) {
@@ -1447,7 +1447,7 @@ __device__ __forceinline__ bool interactions_at_once(const KParams<R>& P, WarpRn
   return true;
 }
 
-// Tail of a single-disk launch. When the queue drains, the packets still in flight are mostly long
+// Tail of a transport launch (single disk or batch). When the queue drains, the packets still in flight are mostly long
 // ones (a lane holds a long packet for long), and lanes of one warp that follow different branches
 // share its issue slots, so in the transport kernel a long packet would then advance at a fraction of
 // its speed alone. The transport kernel therefore stores them (state unchanged, so the random stream
