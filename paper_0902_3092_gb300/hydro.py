@@ -4,7 +4,9 @@ Transport -> temperatures (Monte Carlo + PDA) -> density in hydrostatic equilibr
 (`Disk.hydrostatic_density`, one GPU thread per radial shell) -> transport again, until the mean
 change of the temperatures between two iterations is below `tol_sigma` (3) of their Monte Carlo
 errors, as the paper's convergence criterion states (the statistic, a driver-side reading, is
-`temperature_change`). Each radial shell keeps its dust mass.
+`temperature_change`, with the counting error of each cell as its sigma, or `temperature_change_halves`,
+with sigma measured from two independent halves of each iteration's packets). Each radial shell keeps
+its dust mass.
 
 Two schemes. "picard", the paper's: the next density is the Eq. 20 density of the last temperatures.
 "adjoint": a damped step per radial shell, log rho <- log rho + a_i (log rho_Eq20 - log rho), with
@@ -26,7 +28,7 @@ import time
 
 import numpy as np
 
-from . import disks, mcrt
+from . import disks, dist, mcrt
 
 
 def temperature_change(T_old, err_old, T_new, err_new):
@@ -38,6 +40,42 @@ def temperature_change(T_old, err_old, T_new, err_new):
         return float("inf")
     s_old, s_new = T_old[ok] * err_old[ok], T_new[ok] * err_new[ok]
     return float(np.mean(np.abs(T_new[ok] - T_old[ok]) / np.hypot(s_old, s_new)))
+
+
+def temperature_change_halves(T_old, s_old, T_new, s_new):
+    """Mean |T_new - T_old| over the mean of sqrt(sigma_old^2 + sigma_new^2), over the cells with a
+    temperature and a sigma in both iterations, where sigma = |T_a - T_b| / 2 is measured from the two
+    independent halves a, b of an iteration's packets (the error of their mean). In optically thick
+    cells a packet is absorbed many times, and the MRW deposits many packet energies at once, so the
+    counting error 1/(4 sqrt N) understates the scatter; the halves measure it. A single pair gives each
+    cell's sigma with one degree of freedom, so the statistic is a ratio of means over the cells rather
+    than a mean of per-cell ratios; when the temperatures change by noise alone it is near 1."""
+    ok = (T_old > 0) & (T_new > 0) & np.isfinite(s_old) & np.isfinite(s_new)
+    if not ok.any():
+        return float("inf")
+    den = float(np.mean(np.hypot(s_old[ok], s_new[ok])))
+    if not den > 0:
+        return float("inf")
+    return float(np.mean(np.abs(T_new[ok] - T_old[ok]))) / den
+
+
+def transport_halves(g, packets, seed, **kw):
+    """One iteration's transport in two independent halves of the packet ids (each its own run, with its
+    own packet energy), then their sum: returns the run statistics of both, the temperatures of the sum,
+    their Monte Carlo relative errors, and sigma = |T_a - T_b| / 2 per cell (NaN where a half has no
+    temperature). Gray tallies of the sum equal one run over all the packets."""
+    half = packets // 2
+    blobs, Ts, sts = [], [], []
+    for first, n in ((0, half), (half, packets - half)):
+        g.reset()
+        sts.append(g.run_photons(n, seed=seed, first_id=first, n_total=n, **kw))
+        Ts.append(g.temperatures()[0])
+        blobs.append(g.checkpoint())
+    g.restore(dist.combine_blobs(blobs))
+    T, err, _ = g.temperatures()
+    with np.errstate(invalid="ignore"):
+        sig = np.where((Ts[0] > 0) & (Ts[1] > 0), np.abs(Ts[0] - Ts[1]) / 2.0, np.nan)
+    return sts, T, err, sig
 
 
 def midplane_rows(ntheta):
@@ -80,32 +118,47 @@ def g_cell_volumes(g):
 
 
 def iterate(model, packets, max_iter=8, seed=1, mrw=True, gamma=2.0, max_events=1e6, pda=True, min_visits=30,
-            M_star_g=None, tol_sigma=3.0, disk=None, scheme="picard", on_update=None):
+            M_star_g=None, tol_sigma=3.0, disk=None, scheme="picard", on_update=None, sigma="counting"):
     """Runs the iteration on `model` (a disks.Disk); returns the mcrt.Disk and one record per iteration.
     scheme: "picard" or "adjoint" (see the module docstring; "adjoint" needs the PDA). on_update(g, rho_cur,
     relax, rho_new): called with the disk, each update's current density, step factors (None for Picard)
-    and new density, before the new density is installed, e.g. to check them."""
+    and new density, before the new density is installed, e.g. to check them. sigma: "counting" (each
+    cell's counting error, `temperature_change`) or "halves" (each iteration's packets in two independent
+    halves, `temperature_change_halves`; the record then carries both statistics)."""
     if scheme not in ("picard", "adjoint"):
         raise ValueError("scheme must be picard or adjoint")
+    if sigma not in ("counting", "halves"):
+        raise ValueError("sigma must be counting or halves")
     if scheme == "adjoint" and not pda:
         raise ValueError("the adjoint scheme needs the PDA")
     g = disk if disk is not None else mcrt.Disk.from_model(model)
     hist, prev, k = [], None, 0
     for it in range(max_iter):
         t0 = time.perf_counter()
-        g.reset()
-        st = g.run_photons(packets, seed=seed + it, mrw=mrw, gamma=gamma, max_events=max_events, want_sed=False)
-        T_mc, err, _ = g.temperatures()
+        kw = dict(mrw=mrw, gamma=gamma, max_events=max_events, want_sed=False)
+        if sigma == "halves":
+            sts, T_mc, err, sig = transport_halves(g, packets, seed + it, **kw)
+            st = {"seconds": sum(x["seconds"] for x in sts)}
+        else:
+            g.reset()
+            st = g.run_photons(packets, seed=seed + it, **kw)
+            T_mc, err, _ = g.temperatures()
+            sig = None
         npda = 0
         if pda:
             npda, _ = g.solve_pda(min_visits=min_visits)
             T = g.temperatures(mcrt.T_PDA)[0]
         else:
             T = T_mc
-        change = temperature_change(prev[0], prev[1], T_mc, err) if prev is not None else float("inf")
-        rec = {"iteration": it, "transport_s": st["seconds"], "pda_cells": npda, "change_sigma": change,
+        counting = temperature_change(prev[0], prev[1], T_mc, err) if prev is not None else float("inf")
+        change = counting
+        rec = {"iteration": it, "transport_s": st["seconds"], "pda_cells": npda,
                "midplane_T_mean": float(np.mean(T[:, [g.ntheta // 2 - 1, g.ntheta // 2]]))}
-        prev = (T_mc, err)
+        if sigma == "halves":
+            change = temperature_change_halves(prev[0], prev[2], T_mc, sig) if prev is not None else float("inf")
+            rec["change_sigma_counting"] = counting
+        rec["change_sigma"] = change
+        prev = (T_mc, err, sig)
         if change < tol_sigma:
             rec["wall_s"] = time.perf_counter() - t0
             hist.append(rec)
@@ -137,10 +190,11 @@ def main(argv=None):
     p.add_argument("--ntheta", type=int, default=120)
     p.add_argument("--tau", type=float, default=1e6)
     p.add_argument("--scheme", default="picard", choices=["picard", "adjoint"])
+    p.add_argument("--sigma", default="counting", choices=["counting", "halves"])
     a = p.parse_args(argv)
     d = disks.config_thick_gray(a.nr, a.ntheta, a.tau)
     _, hist = iterate(d, int(a.packets), max_iter=a.iterations,
-                      min_visits=max(30, int(30 * a.packets / 1e5)), scheme=a.scheme)
+                      min_visits=max(30, int(30 * a.packets / 1e5)), scheme=a.scheme, sigma=a.sigma)
     for h in hist:
         print(json.dumps(h), flush=True)
 

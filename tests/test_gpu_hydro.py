@@ -98,3 +98,28 @@ def test_adjoint_scheme_reaches_the_3_sigma_criterion_before_picard(M, oracle):
     assert np.mean(cp[2:]) > 3.0, cp              # Picard's plateau
     assert any(checked) and not all(checked)
     assert all(h["gain_range"][1] < 1.0 for h in ha if "gain_range" in h)
+
+
+def test_two_half_sigma_meets_the_3_sigma_criterion_with_mrw(M):
+    """With MRW on an optically thick disk the counting error 1/(4 sqrt N) understates the Monte Carlo
+    scatter (a packet is absorbed many times in a thick cell and a jump deposits many packet energies), so
+    the counting statistic stays far above 3 while the temperatures move by noise alone. Measured from two
+    independent halves of each iteration's packets, sigma lets the iteration meet the 3-sigma criterion
+    (Sect. 2.5, Sect. 3.4), and once the density has settled the statistic is at the noise-only value of
+    temperature_change_halves, 2 sqrt(2) / pi = 0.90."""
+    from paper_0902_3092_gb300 import hydro
+    d = disks.config_thick_gray(60, 40, 1e5)
+    g, hist = hydro.iterate(d, 2_000_000, max_iter=6, mrw=True, gamma=2.0, min_visits=600, sigma="halves",
+                            scheme="adjoint", tol_sigma=0.0)
+    g.close()
+    halves = [h["change_sigma"] for h in hist[1:]]
+    counting = [h["change_sigma_counting"] for h in hist[1:]]
+    assert min(counting) > 10.0, counting
+    first = next(i for i, x in enumerate(halves) if x < 3.0)
+    assert first <= 2, halves
+    tail = halves[first + 1:]
+    assert len(tail) >= 2 and all(0.6 < x < 1.5 for x in tail), halves
+    # the stop at tol_sigma = 3 comes at that iteration
+    _, hist3 = hydro.iterate(d, 2_000_000, max_iter=6, mrw=True, gamma=2.0, min_visits=600, sigma="halves",
+                             scheme="adjoint")
+    assert hist3[-1]["change_sigma"] < 3.0 and len(hist3) <= 4, [h["change_sigma"] for h in hist3]

@@ -78,3 +78,34 @@ def test_hydro_relax_matches_oracle(lib):
     assert big.sum() > 500
     assert np.max(np.abs(got[big] / want[big] - 1)) < 1e-12
     assert np.allclose(H.shell_masses(d.r_faces_cm, d.theta_faces, got), shell, rtol=1e-12, atol=0)
+
+
+def test_halves_statistic_is_0_9_for_noise_and_grows_with_a_change():
+    """temperature_change_halves on synthetic Monte Carlo noise: each iteration's T is the mean of two
+    halves with N(0, 2 s^2) errors, so T has error s and sigma = |T_a - T_b| / 2 is half-normal with
+    scale s. Then E|T_new - T_old| = 2 s / sqrt(pi) and E sqrt(sigma_old^2 + sigma_new^2) = s sqrt(pi / 2)
+    (Rayleigh): a ratio of 2 sqrt(2) / pi = 0.900 for noise alone, whatever s is per cell. A systematic
+    change of 3 s in every cell raises it (to ~2.4)."""
+    from paper_0902_3092_gb300.hydro import temperature_change_halves
+    rng = np.random.default_rng(21)
+    n = 200_000
+    mu = rng.uniform(20.0, 800.0, n)
+    s = mu * rng.uniform(0.002, 0.05, n)  # per-cell error of the mean of the two halves
+
+    def iteration(shift=0.0):
+        a = mu + shift + rng.normal(0.0, np.sqrt(2.0) * s)
+        b = mu + shift + rng.normal(0.0, np.sqrt(2.0) * s)
+        return 0.5 * (a + b), np.abs(a - b) / 2.0
+
+    T0, s0 = iteration()
+    T1, s1 = iteration()
+    x = temperature_change_halves(T0, s0, T1, s1)
+    assert abs(x - 2.0 * np.sqrt(2.0) / np.pi) < 0.01, x
+    T2, s2 = iteration(shift=3.0 * s)
+    y = temperature_change_halves(T1, s1, T2, s2)
+    assert y > 2.0, y
+    # cells without a temperature or a sigma in either iteration are left out
+    s1_nan = s1.copy()
+    s1_nan[: n // 2] = np.nan
+    z = temperature_change_halves(T0, s0, T1, s1_nan)
+    assert abs(z - 2.0 * np.sqrt(2.0) / np.pi) < 0.015, z
