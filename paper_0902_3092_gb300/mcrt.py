@@ -192,8 +192,6 @@ class Disk:
         _check(L.mcrt_disk_create(C.byref(g), C.byref(s), int(device), stream, C.byref(h)))
         self._h = h
         self.nlam = 0
-        self.L_star = 4 * np.pi * R_star_cm ** 2 * (2 * np.pi ** 5 * 1.380649e-16 ** 4 /
-                                                      (15 * 6.62607015e-27 ** 3 * 2.99792458e10 ** 2)) * T_star_K ** 4
 
     @classmethod
     def from_model(cls, d, device=0, stream=None):
